@@ -1,0 +1,370 @@
+"""Seeded synthetic workloads: Haar wavelet bases and compressed kernel matrices.
+
+This module only builds INPUTS (a sparse symmetric matrix, its geometry and
+right-hand sides).  It holds none of the solver's arithmetic: no ordering,
+no factorization, no triangular solve.  Both the CPU oracle and the CUDA path
+consume what it produces.
+
+What it builds (the paper's Sections 2 and 3, restated):
+
+* Haar multiresolution bases on a uniform grid of 2^J cells per axis
+  (1D or 2D).  Level 0 is the single scaling function (Psi_0 := Phi_0,
+  Section 2); level j = 1..J holds wavelets living on the dyadic cells of
+  side 2^(1-j) of the unit interval/square (diam supp psi_{j,k} ~ 2^-j).
+  1D: psi = (phi_left - phi_right)/sqrt(2) per dyadic interval.
+  2D (isotropic): per dyadic square the three tensor wavelets
+  psi(x)phi(y), phi(x)psi(y), psi(x)psi(y), sign "+" on the left/bottom half.
+  All functions are L2-normalized, so the basis is orthonormal.
+* Galerkin matrix in wavelet coordinates (Section 3): with the L2-normalized
+  cell indicators as single-scale basis and the one-point (cell-centroid)
+  rule,  K_ss[c, c'] = sqrt(|c||c'|) k(x_c, x_c'),  and  A = T K_ss T^T  with
+  T the orthonormal fast wavelet transform.
+* A-priori compression (Theorem 3.1), first cut-off term with a = 2: the
+  entry (lambda, lambda') is kept iff
+      dist(D_lambda, D_lambda') <= 2 * 2^(-min(j, j')),
+  dist being the Euclidean distance of the closed support boxes, evaluated
+  exactly on integers in finest-cell units.  Then the nugget eps*I is added
+  (the mass matrix of an orthonormal basis is the identity).
+
+Index order ("canonical levelwise ordering", Section 4): level 0, then level
+1, ..., level J; inside a level 1D wavelets by position k, 2D wavelets by
+square (row p = y index major, column q = x index) and then by type 0,1,2.
+Level j >= 1 starts at index 2^(j-1) in 1D and 4^(j-1) in 2D.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# bases
+# --------------------------------------------------------------------------
+
+
+@dataclass
+class Basis:
+    """Geometry of a Haar wavelet basis (finest-cell integer units)."""
+
+    dim: int
+    J: int
+    level: np.ndarray        # int32 [N]
+    box_lo: np.ndarray       # int32 [N, dim]   lower corner of supp psi
+    box_side: np.ndarray     # int32 [N]        side length of supp psi
+    patch: np.ndarray | None = None  # int32 [N] or None
+
+    @property
+    def N(self) -> int:
+        return int(self.level.shape[0])
+
+    @property
+    def n_side(self) -> int:
+        return 1 << self.J
+
+
+def _positions(dim: int, j: int) -> int:
+    return 1 if j == 0 else (1 << (j - 1))
+
+
+def level_side(J: int, j: int) -> int:
+    """Support side of a level-j function in finest-cell units."""
+    return (1 << J) if j == 0 else (1 << (J + 1 - j))
+
+
+def haar_basis(dim: int, J: int) -> Basis:
+    if dim not in (1, 2):
+        raise ValueError("dim must be 1 or 2")
+    lev, lo, side = [], [], []
+    for j in range(J + 1):
+        n = _positions(dim, j)
+        s = level_side(J, j)
+        if dim == 1:
+            k = np.arange(n, dtype=np.int64)
+            lev.append(np.full(n, j, np.int32))
+            lo.append((k * s)[:, None])
+            side.append(np.full(n, s, np.int32))
+        else:
+            ntype = 1 if j == 0 else 3
+            p, q = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+            p = np.repeat(p.reshape(-1), ntype)
+            q = np.repeat(q.reshape(-1), ntype)
+            lev.append(np.full(p.size, j, np.int32))
+            lo.append(np.stack([q * s, p * s], axis=1))
+            side.append(np.full(p.size, s, np.int32))
+    return Basis(dim, J, np.concatenate(lev), np.concatenate(lo).astype(np.int32),
+                 np.concatenate(side))
+
+
+def fwt(x, dim: int, J: int, xp=np):
+    """Orthonormal Haar transform over the trailing cell axes.
+
+    x: (..., n) in 1D or (..., n, n) indexed [iy, ix] in 2D, holding the
+    coefficients in the normalized cell basis.  Returns (..., N) wavelet
+    coefficients in the canonical levelwise order.  Works for numpy arrays
+    and torch tensors (xp = numpy or torch).
+    """
+    parts = []
+    a = x
+    r2 = 1.0 / math.sqrt(2.0)
+    for _ in range(J, 0, -1):
+        if dim == 1:
+            a0 = a[..., 0::2]
+            a1 = a[..., 1::2]
+            parts.append((a0 - a1) * r2)
+            a = (a0 + a1) * r2
+        else:
+            a00 = a[..., 0::2, 0::2]
+            a01 = a[..., 0::2, 1::2]
+            a10 = a[..., 1::2, 0::2]
+            a11 = a[..., 1::2, 1::2]
+            d0 = ((a00 + a10) - (a01 + a11)) * 0.5
+            d1 = ((a00 + a01) - (a10 + a11)) * 0.5
+            d2 = ((a00 + a11) - (a01 + a10)) * 0.5
+            a = ((a00 + a01) + (a10 + a11)) * 0.5
+            st = xp.stack([d0, d1, d2], -1)
+            parts.append(st.reshape(tuple(st.shape[:-3]) + (-1,)))
+    parts.append(a.reshape(tuple(a.shape[: a.ndim - dim]) + (1,)))
+    parts.reverse()
+    if xp is np:
+        return np.concatenate(parts, -1)
+    return xp.cat(parts, -1)
+
+
+# --------------------------------------------------------------------------
+# compression pattern
+# --------------------------------------------------------------------------
+
+
+def _axis_pairs(J: int, j: int, jp: int):
+    """All (k, k', gap) along one axis with gap <= 2*2^(J-min(j,j'))."""
+    n, np_ = _positions(1, j), _positions(1, jp)
+    s, sp = level_side(J, j), level_side(J, jp)
+    thr = 2 * (1 << (J - min(j, jp)))
+    k = np.arange(n, dtype=np.int64)
+    # k' with  k'*sp - (k+1)*s <= thr  and  k*s - (k'+1)*sp <= thr
+    khi = np.minimum(((k + 1) * s + thr) // sp, np_ - 1)
+    klo = np.maximum(-((-(k * s - thr)) // sp) - 1, 0)
+    cnt = np.maximum(khi - klo + 1, 0)
+    kk = np.repeat(k, cnt)
+    off = np.arange(int(cnt.sum()), dtype=np.int64) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+    kp = np.repeat(klo, cnt) + off
+    lo, lop = kk * s, kp * sp
+    gap = np.maximum(np.maximum(lop - (lo + s), lo - (lop + sp)), 0)
+    keep = gap <= thr
+    return kk[keep], kp[keep], gap[keep], thr
+
+
+def _level_offset(dim: int, j: int) -> int:
+    if j == 0:
+        return 0
+    return (1 << (j - 1)) if dim == 1 else (1 << (2 * (j - 1)))
+
+
+def compressed_pattern(basis: Basis):
+    """Lower CSC pattern (incl. diagonal, rows sorted) of the a=2 mask.
+
+    Returns colptr int64 [N+1], rowidx int32 [nnz_lower].
+    """
+    dim, J, N = basis.dim, basis.J, basis.N
+    rows, cols = [], []
+    for j in range(J + 1):
+        for jp in range(j, J + 1):
+            kk, kp, gap, thr = _axis_pairs(J, j, jp)
+            if dim == 1:
+                a = _level_offset(1, j) + kk
+                b = _level_offset(1, jp) + kp
+            else:
+                # combine an x-pair and a y-pair: square (p,q) x square (p',q')
+                ny = kk.size
+                ia = np.repeat(np.arange(ny), ny)   # y pair
+                ib = np.tile(np.arange(ny), ny)     # x pair
+                ok = gap[ia] ** 2 + gap[ib] ** 2 <= thr * thr
+                ia, ib = ia[ok], ib[ok]
+                n, np_ = _positions(2, j), _positions(2, jp)
+                sq = kk[ia] * n + kk[ib]
+                sqp = kp[ia] * np_ + kp[ib]
+                t = 1 if j == 0 else 3
+                tp = 1 if jp == 0 else 3
+                ta = np.repeat(np.arange(t), tp)
+                tb = np.tile(np.arange(tp), t)
+                a = (_level_offset(2, j) + t * sq)[:, None] + ta[None, :]
+                b = (_level_offset(2, jp) + tp * sqp)[:, None] + tb[None, :]
+                a = a.reshape(-1)
+                b = b.reshape(-1)
+            r = np.maximum(a, b)
+            c = np.minimum(a, b)
+            rows.append(r)
+            cols.append(c)
+    r = np.concatenate(rows).astype(np.int64)
+    c = np.concatenate(cols).astype(np.int64)
+    key = np.unique(c * N + r)          # same-level pairs appear twice
+    c = key // N
+    r = key % N
+    colptr = np.zeros(N + 1, np.int64)
+    np.cumsum(np.bincount(c, minlength=N), out=colptr[1:])
+    return colptr, r.astype(np.int32)
+
+
+# --------------------------------------------------------------------------
+# kernels and values
+# --------------------------------------------------------------------------
+
+
+@dataclass
+class Kernel:
+    """Isotropic covariance k(r) = sigma2 * f(r / ell)."""
+
+    kind: str = "exponential"     # exponential | matern32 | matern12
+    ell: float = 0.2
+    sigma2: float = 1.0
+
+    def __call__(self, r, xp=np):
+        t = r / self.ell
+        if self.kind in ("exponential", "matern12"):
+            return self.sigma2 * xp.exp(-t)
+        if self.kind == "matern32":
+            u = math.sqrt(3.0) * t
+            return self.sigma2 * (1.0 + u) * xp.exp(-u)
+        raise ValueError(self.kind)
+
+
+def _cell_centroids(dim: int, J: int, xp=np, device=None):
+    n = 1 << J
+    if xp is np:
+        c = (np.arange(n, dtype=np.float64) + 0.5) / n
+        if dim == 1:
+            return c[:, None]
+        yy, xx = np.meshgrid(c, c, indexing="ij")
+        return np.stack([xx.reshape(-1), yy.reshape(-1)], 1)
+    c = (xp.arange(n, dtype=xp.float64, device=device) + 0.5) / n
+    if dim == 1:
+        return c[:, None]
+    yy, xx = xp.meshgrid(c, c, indexing="ij")
+    return xp.stack([xx.reshape(-1), yy.reshape(-1)], 1)
+
+
+def _dist(a, b, xp):
+    d2 = None
+    for ax in range(a.shape[1]):
+        d = a[:, None, ax] - b[None, :, ax]
+        d2 = d * d if d2 is None else d2 + d * d
+    return xp.sqrt(d2)
+
+
+def compressed_values(basis: Basis, colptr, rowidx, kernel: Kernel, nugget: float,
+                      device: str = "cpu", chunk: int = 2048):
+    """Values of the compressed matrix on a lower CSC pattern (float64, numpy).
+
+    A = mask(T K_ss T^T) + nugget*I, with the one-point cell-centroid rule.
+    device='cpu' uses numpy; a CUDA device uses torch (the result is the same
+    up to rounding; only needed when N^2 doubles do not fit the host).
+    """
+    dim, J, N = basis.dim, basis.J, basis.N
+    n = 1 << J
+    vol = 1.0 / float(N)                      # |c| = n^-dim = 1/N
+    if device == "cpu":
+        xp = np
+        X = _cell_centroids(dim, J)
+    else:
+        import torch as xp  # noqa: N812
+        X = _cell_centroids(dim, J, xp, device)
+    shape = (n,) if dim == 1 else (n, n)
+    # pass 1: Y1 = K_ss T^T  (rows: cells, cols: wavelets)
+    if xp is np:
+        Y1 = np.empty((N, N), np.float64)
+    else:
+        Y1 = xp.empty((N, N), dtype=xp.float64, device=device)
+    for c0 in range(0, N, chunk):
+        c1 = min(N, c0 + chunk)
+        K = kernel(_dist(X[c0:c1], X, xp), xp) * vol
+        Y1[c0:c1] = fwt(K.reshape((c1 - c0,) + shape), dim, J, xp)
+        del K
+    # pass 2: A rows = T Y1 (columns of Y1 are cell vectors), gather the pattern
+    cp = np.asarray(colptr)
+    ri = np.asarray(rowidx).astype(np.int64)
+    vals = np.empty(ri.size, np.float64)
+    for c0 in range(0, N, chunk):
+        c1 = min(N, c0 + chunk)
+        Yc = Y1[:, c0:c1].T
+        Yc = Yc.copy() if xp is np else Yc.contiguous()
+        Arows = fwt(Yc.reshape((c1 - c0,) + shape), dim, J, xp)   # A[c0:c1, :]
+        e0, e1 = int(cp[c0]), int(cp[c1])
+        colid = np.repeat(np.arange(c0, c1), np.diff(cp[c0:c1 + 1])) - c0
+        flat = colid * N + ri[e0:e1]
+        if xp is np:
+            vals[e0:e1] = Arows.reshape(-1)[flat]
+        else:
+            idx = xp.from_numpy(flat).to(device)
+            vals[e0:e1] = Arows.reshape(-1)[idx].cpu().numpy()
+        del Arows, Yc
+    del Y1
+    # nugget on the diagonal (first entry of every column)
+    vals[cp[:-1]] += nugget
+    return vals
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+
+
+@dataclass
+class Workload:
+    name: str
+    basis: Basis
+    colptr: np.ndarray
+    rowidx: np.ndarray
+    values: np.ndarray
+    B: np.ndarray            # (N, nrhs) float64, column-major (Fortran order)
+    kernel: Kernel
+    nugget: float
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def N(self) -> int:
+        return self.basis.N
+
+    @property
+    def nnz_lower(self) -> int:
+        return int(self.rowidx.size)
+
+    @property
+    def nnz_full(self) -> int:
+        return 2 * self.nnz_lower - self.N
+
+
+def rhs(N: int, nrhs: int, seed: int = 0) -> np.ndarray:
+    """nrhs standard normal vectors, (N, nrhs) column-major, original order."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((nrhs, N)).T
+
+
+def haar_workload(dim: int, J: int, kernel: Kernel, nugget: float, nrhs: int = 1,
+                  seed: int = 0, device: str = "cpu", name: str | None = None,
+                  values: bool = True) -> Workload:
+    basis = haar_basis(dim, J)
+    colptr, rowidx = compressed_pattern(basis)
+    vals = (compressed_values(basis, colptr, rowidx, kernel, nugget, device)
+            if values else np.empty(0))
+    return Workload(name or f"haar{dim}d_J{J}", basis, colptr, rowidx, vals,
+                    rhs(basis.N, nrhs, seed), kernel, nugget)
+
+
+def workload_1d(J: int = 10, nrhs: int = 1, **kw) -> Workload:
+    """1D: [0,1], 2^J cells, exponential kernel ell=0.2, nugget 1e-2."""
+    return haar_workload(1, J, Kernel("exponential", 0.2), 1e-2, nrhs,
+                         name=f"1d_haar_J{J}_exp0.2", **kw)
+
+
+def workload_2d(J: int = 8, nrhs: int = 64, **kw) -> Workload:
+    """2D: unit square 2^J x 2^J, Matern-3/2 ell=0.1, nugget 1e-3."""
+    return haar_workload(2, J, Kernel("matern32", 0.1), 1e-3, nrhs,
+                         name=f"2d_haar_{1 << J}x{1 << J}_matern32", **kw)
+
+
+def workload_autograd(J: int = 7, nrhs: int = 32, ell: float = 0.15, sigma2: float = 1.0,
+                      nugget: float = 1e-2, **kw) -> Workload:
+    """2D Matern-1/2 workload of the gradient experiment."""
+    return haar_workload(2, J, Kernel("matern12", ell, sigma2), nugget, nrhs,
+                         name=f"2d_haar_{1 << J}x{1 << J}_matern12", **kw)
