@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark: factor + solve of the wavelet-compressed 2D kernel matrix.
+
+Workload (default): unit square with 256 x 256 cells, isotropic Haar
+wavelets (N = 65,536), Matern-3/2 kernel (ell = 0.1) by the cell-centroid
+rule, a = 2 compression, nugget 1e-3, 64 right-hand sides ~ N(0, 1), seed 0.
+Inputs are synthetic (seeded generator; no dataset).
+
+One step = wd_factor + wd_solve (64 RHS, refined in FP64 to a backward error
+<= 1e-12 in mixed precision) + wd_logdet, with the matrix values and the
+right-hand sides already resident in HBM.  The front pool (about 4 GB) is
+far larger than L2, so no L2 flush is needed between steps.
+
+value = (sum_j c_j^2 + 4 nnz(L) nrhs) / step time, in TFLOP/s, for the mixed
+path.  The FP64 path is measured the same way and reported beside it.
+
+--impl reference times the CPU oracle (plain left-looking FP64 Cholesky) on
+the host cores, on a bounded prefix of the same factorization.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# derived ALU peaks (unit counts x maximum SM clock), see the design doc
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+FP64_FLOPS_PER_SM_CLK = 4     # 2 FP64 FMA per SM per clock (GB300: 1.25 TFLOP/s nominal)
+MAX_SM_MHZ = 2070.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["2d", "1d"], default="2d")
+    p.add_argument("--nrhs", type=int, default=None)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--cpu-flops", type=float, default=1.2e10,
+                   help="flop budget of the oracle's bounded sample")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Dist:
+    def __init__(self, backend):
+        self.ws, self.rank, self.local = dist_env()
+        self.pg = None
+        if self.ws > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64,
+                         device="cuda" if torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64,
+                         device="cuda" if torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_id_for_smi():
+    try:
+        import torch
+        u = getattr(torch.cuda.get_device_properties(torch.cuda.current_device()), "uuid", None)
+        if u is not None:
+            s = str(u)
+            return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        pass
+    v = os.environ.get("CUDA_VISIBLE_DEVICES")
+    return v.split(",")[0] if v else None
+
+
+def load_peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+def make_workload(kind: str, nrhs: int | None, device: str):
+    from wdgen import Kernel, compressed_pattern, compressed_values, haar_basis, rhs
+
+    if kind == "2d":
+        dim, J, ker, nug, nr = 2, 8, Kernel("matern32", 0.1), 1e-3, 64
+        name = "2d_haar_256x256_matern32_l0.1_nugget1e-3"
+    else:
+        dim, J, ker, nug, nr = 1, 10, Kernel("exponential", 0.2), 1e-2, 1
+        name = "1d_haar_1024_exp_l0.2_nugget1e-2"
+    nr = nrhs or nr
+    b = haar_basis(dim, J)
+    cp, ri = compressed_pattern(b)
+    vals = compressed_values(b, cp, ri, ker, nug, device=device)
+    B = rhs(b.N, nr, seed=0)
+    return dict(name=f"{name}_{nr}rhs", basis=b, colptr=cp, rowidx=ri, values=vals, B=B, nrhs=nr)
+
+
+def cpu_sample(w, budget_flops: float):
+    """Oracle left-looking factor of a prefix of P A P^T's columns, timed."""
+    import numpy as np
+
+    import oracle
+
+    o = oracle.Oracle(w["colptr"], w["rowidx"], w["basis"])
+    c2 = np.cumsum(o.colcount.astype(np.float64) ** 2)
+    ncols = int(np.searchsorted(c2, budget_flops, side="right"))
+    ncols = max(1, min(ncols, o.n))
+    flops = float(c2[ncols - 1])
+    return o, ncols, flops
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    try:
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+    except Exception:
+        dev = "cpu"
+    w = make_workload(args.workload, args.nrhs, dev)
+    o, ncols, flops = cpu_sample(w, args.cpu_flops / 4)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        rc = o.factor_prefix(w["values"], ncols)
+        dt = time.perf_counter() - t
+        if rc != 0:
+            raise RuntimeError(f"oracle factor failed: {rc}")
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = flops * len(times) / tot / 1e12
+    sample = (f"left-looking FP64 factor of the first {ncols} of {o.n} columns of P A P^T "
+              f"(sum c_j^2 = {flops:.3e} flop, bottom of the elimination tree); solve not sampled")
+    line = {"impl": "reference", "metric": "factor+solve TFLOP/s (mixed+IR path)",
+            "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot / len(times) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "N": int(o.n), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2007_01541_gb300 as wd
+    from paper_2007_01541_gb300 import build as wdbuild
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = Dist("nccl")
+    wdbuild.build()
+    w = make_workload(args.workload, args.nrhs, "cuda")
+    N, nr = w["basis"].N, w["nrhs"]
+    s = wd.Solver(profile=True).analyze(w["colptr"], w["rowidx"], w["basis"])
+    info = s.info()
+    flops_factor = info["flops_factor"]
+    flops_solve = 4.0 * info["nnz_L"] * nr
+    flops_step = flops_factor + flops_solve
+    vals = torch.from_numpy(w["values"]).cuda()
+    B0 = torch.from_numpy(np.ascontiguousarray(w["B"].T)).cuda()   # (nrhs, N) = column-major B
+    Bw = torch.empty_like(B0)
+    stream = torch.cuda.current_stream()
+
+    def step(prec):
+        s.factor(vals, prec)
+        Bw.copy_(B0)
+        s.solve(Bw.T)
+        s.logdet()
+
+    def timed(prec, K, W):
+        for _ in range(W):
+            step(prec)
+        s.kernel_stats(reset=True)
+        s.launch_count(reset=True)
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            step(prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        ms = e0.elapsed_time(e1) / K
+        return dist.max(ms), s.kernel_stats(reset=True), s.launch_count(reset=True), dict(s.last_solve)
+
+    clocks = ClockSampler(gpu_id_for_smi())
+    clocks.start()
+    ms_mixed, kstats, launches, solve_info = timed("mixed", args.steps, args.warmup)
+    clk = clocks.stop()
+    res_fp64 = None
+    if not args.no_fp64:
+        ms64, kst64, _, si64 = timed("fp64", max(2, args.steps // 2), 2)
+        res_fp64 = {"ms_per_step": ms64,
+                    "tflops": dist.sum(flops_step) / (ms64 / 1e3) / 1e12,
+                    "backward_error": si64["backward_error"],
+                    "top_kernels": _top(kst64, 3)}
+    value = dist.sum(flops_step) / (ms_mixed / 1e3) / 1e12
+
+    # roofline of the dominant kernel of the mixed step
+    peaks = load_peaks()
+    top = max(kstats, key=lambda k: k["ms"]) if kstats else None
+    roof = None
+    if top:
+        alu = top["name"].startswith(("schur_update", "panel_trsm", "potrf_first", "fwd_update",
+                                      "bwd_init", "bwd_step", "fwd_diag_first"))
+        if alu:
+            fp64 = top["name"].endswith("_fp64")
+            per_clk = FP64_FLOPS_PER_SM_CLK if fp64 else 2 * FP32_LANES_PER_SM
+            peak = SM_COUNT * per_clk * MAX_SM_MHZ * 1e6 / 1e12
+            ach = top["flops"] / (top["ms"] / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None, "kernel": top["name"],
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if not fp64
+                    else "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz"}
+        else:
+            peak = peaks.get("hbm_gbs", 6800.0)
+            ach = top["bytes"] / (top["ms"] / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "traffic": None, "kernel": top["name"],
+                    "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+        roof["launches_per_step"] = top["launches"] / args.steps
+        roof["ms_per_launch"] = top["ms"] / max(1, top["launches"])
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        vh = torch.from_numpy(w["values"]).pin_memory()
+        Bh0 = torch.from_numpy(np.ascontiguousarray(w["B"].T)).pin_memory()
+        Bh = torch.empty_like(Bh0).pin_memory()
+
+        def step_host():
+            s.factor(vh, "mixed")
+            Bh.copy_(Bh0)
+            s.solve(Bh.T)
+            s.logdet()
+
+        for _ in range(2):
+            step_host()
+        dist.barrier()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        torch.cuda.synchronize()
+        dt = dist.max((time.perf_counter() - t) / args.steps)
+        e2e = {"value": dist.sum(flops_step) / dt / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": 8 * int(w["rowidx"].size) + 8 * N * nr,
+               "d2h_bytes_per_step": 8 * N * nr + 8 + 8 * 3 * nr * (1 + solve_info["iterations"]),
+               "ms_per_step": dt * 1e3}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        o, ncols, fl = cpu_sample({**w, "values": w["values"]}, args.cpu_flops)
+        t = time.perf_counter()
+        rc = o.factor_prefix(w["values"], ncols)
+        dt = time.perf_counter() - t
+        cpu = {"value": fl / dt / 1e12 if rc == 0 else None, "unit": "TFLOP/s", "cores": 1,
+               "kind": "oracle",
+               "sample": (f"left-looking FP64 factor of the first {ncols} of {o.n} columns of "
+                          f"P A P^T ({fl:.3e} flop, bottom of the elimination tree) in "
+                          f"{dt:.1f} s; solve not sampled")}
+
+    if rank == 0:
+        line = {
+            "metric": "factor+solve TFLOP/s (mixed+IR path; FP64 path beside it) at backward error <= 1e-12",
+            "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": w["name"], "N": N, "nnz_A": 2 * int(w["rowidx"].size) - N,
+                       "nnz_L": info["nnz_L"], "flops_factor": flops_factor, "nrhs": nr,
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (front pool %.1f GB)" % (info["front_bytes"] / 1e9)},
+            "backward_error": solve_info["backward_error"], "ir_iterations": solve_info["iterations"],
+            "fp64": res_fp64,
+            "speedup_mixed_vs_fp64": (res_fp64["ms_per_step"] / ms_mixed) if res_fp64 else None,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "top_kernels": _top(kstats, 5),
+            "analyze_s": info["analyze_seconds"],
+        }
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
+def _top(kstats, n):
+    out = []
+    for k in sorted(kstats, key=lambda k: -k["ms"])[:n]:
+        out.append({"name": k["name"], "ms": round(k["ms"], 3), "launches": k["launches"],
+                    "tflops": k["flops"] / max(k["ms"], 1e-9) / 1e9,
+                    "gbs": k["bytes"] / max(k["ms"], 1e-9) / 1e6})
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * wd.h — C ABI of the GB300 sparse direct solver for wavelet-compressed
+ * nonlocal operators (Harbrecht & Multerer, "A fast direct solver for nonlocal
+ * operators in wavelet coordinates").
+ *
+ * The operation: given the symmetric positive definite compressed system
+ * matrix A (Theorem 3.1), compute a nested-dissection permutation P and the
+ * Cholesky factor P A P^T = L L^T (Section 4, Lemma and the block form of
+ * P A P^T), then apply the exact inverse of the compressed matrix to
+ * right-hand sides, log det A, and Gaussian random field samples P^T L z
+ * (Section 5.3, Eq. CholFastField with an orthonormal basis, G = I).
+ *
+ * Conventions for every call:
+ *  - A is passed as its LOWER triangle in compressed sparse column form,
+ *    0-based, diagonal first in every column, row indices strictly
+ *    increasing: colptr[n+1] (int64), rowidx[nnz] (int32), values[nnz]
+ *    (double, same order as rowidx).
+ *  - Dense blocks (right-hand sides, samples) are column-major with a leading
+ *    dimension, in the ORIGINAL (unpermuted) index order.
+ *  - Pointers are borrowed for the duration of the call; the library copies
+ *    what it keeps.  The handle owns all internal host and device memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls are ordered on that stream; every call documented as
+ *    synchronous synchronizes it before returning.
+ *  - Calls come in the order create -> analyze -> factor -> {solve, logdet,
+ *    apply_L, selinv}; out of order calls return WD_ERR_STATE.  A new
+ *    wd_factor on the same pattern reuses the analysis.
+ *  - Errors leave the handle usable; an error in wd_factor leaves no factor.
+ *  - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef WD_H
+#define WD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wd_ctx *wd_handle;
+
+typedef enum {
+    WD_OK = 0,
+    WD_ERR_INVALID_ARG = 1,     /* null pointer, negative size, bad option   */
+    WD_ERR_PATTERN = 2,         /* malformed CSC (unsorted, missing diagonal,
+                                   out of range, duplicate)                  */
+    WD_ERR_STATE = 3,           /* call out of order                          */
+    WD_ERR_NOT_SPD = 4,         /* a pivot <= 0; wd_status_detail gives the
+                                   smallest failing column (permuted order)  */
+    WD_ERR_OOM = 5,             /* host or device allocation failed           */
+    WD_ERR_CUDA = 6,            /* a CUDA runtime error (message in detail)   */
+    WD_ERR_TIMEOUT = 7,         /* a bounded device wait expired              */
+    WD_ERR_NO_CONVERGENCE = 8   /* iterative refinement did not reach the
+                                   requested backward error                   */
+} wd_status;
+
+typedef enum {
+    WD_FP64 = 0,       /* fronts, factor and solves in FP64                     */
+    WD_MIXED = 1       /* fronts and solves in FP32 (Schur updates on tensor
+                          cores where available), FP64 residuals and iterative
+                          refinement to the requested backward error           */
+} wd_precision;
+
+typedef struct {
+    int32_t nd_leaf;        /* ND stops at <= nd_leaf vertices (default 64)      */
+    int32_t relax_k;        /* amalgamation: merge while width <= relax_k (16)   */
+    int32_t relax_pct;      /* ... or explicit zeros <= relax_pct % (10)         */
+    int32_t ir_max_iter;    /* refinement steps in WD_MIXED (default 10)         */
+    double ir_tol;          /* target normwise backward error (default 1e-12)    */
+    int32_t use_graphs;     /* capture factor/solve launch sequences (1)         */
+    int32_t symbolic_only;  /* 1: host-only handle, no GPU is touched; only
+                               wd_analyze, wd_symbolic_export and wd_get_info
+                               are available (numeric calls: WD_ERR_STATE) (0) */
+    int32_t profile;        /* 1: bracket every kernel launch of wd_factor and
+                               wd_solve with CUDA events on the caller's stream
+                               and accumulate per-kernel times (0)            */
+    int32_t reserved[5];
+} wd_options;
+
+/* Optional geometry for the nested-dissection ordering.  Per vertex (basis
+   function) lambda: its level j = |lambda| (Section 2), the lower corner and
+   side of the axis-aligned box supp psi_lambda in integer finest-cell units.
+   box_lo is n x dim row-major.  patch is reserved and must be NULL. */
+typedef struct {
+    int32_t dim;                 /* 1, 2 or 3                                  */
+    const int32_t *level;        /* [n]                                        */
+    const int32_t *box_lo;       /* [n * dim]                                  */
+    const int32_t *box_side;     /* [n]                                        */
+    const int32_t *patch;        /* must be NULL                               */
+} wd_geometry;
+
+typedef struct {
+    int64_t n;
+    int64_t nnz_A_lower;
+    int64_t nnz_L;              /* structural nonzeros of L (incl. diagonal)   */
+    int64_t nnz_L_stored;       /* stored entries incl. amalgamation zeros     */
+    double flops_factor;        /* sum_j c_j^2 (structural)                    */
+    int32_t nsuper;
+    int32_t nlevels;            /* height of the supernodal tree               */
+    int32_t max_front;          /* largest front order m_s                     */
+    int32_t max_width;          /* widest supernode k_s                        */
+    int64_t front_bytes;        /* device bytes of the front pool (FP64)       */
+    int64_t factor_launches;    /* kernels launched per wd_factor              */
+    double analyze_seconds;
+} wd_info;
+
+typedef struct {
+    int32_t iterations;         /* refinement steps taken (0 in WD_FP64)       */
+    double backward_error;      /* max over columns of
+                                   ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf),
+                                   residual in FP64; -1 if not computed        */
+} wd_solve_info;
+
+/* Fill *opt with the defaults listed above. */
+void wd_default_options(wd_options *opt);
+
+/* Create a handle bound to the current CUDA device.  opt may be NULL. */
+wd_status wd_create(wd_handle *h, const wd_options *opt);
+
+/* Free the handle and all its memory.  NULL is ignored. */
+void wd_destroy(wd_handle h);
+
+/* Symbolic analysis (host): validate the lower CSC pattern, compute the
+   nested-dissection permutation (Section 4), the elimination tree, column
+   counts, supernodes with relaxed amalgamation, extend-add maps and the level
+   schedule, and upload the index arrays.  Synchronous.  colptr/rowidx are
+   host arrays.  geom may be NULL: then the identity order is used. */
+wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, const int32_t *rowidx,
+                     const wd_geometry *geom);
+
+/* Copy the symbolic result into caller-allocated host arrays (any may be
+   NULL): perm[n] (perm[new] = old), parent[n] (elimination tree of P A P^T,
+   -1 for roots), colcount[n] (nonzeros of column j of L incl. diagonal),
+   super_first[nsuper+1], super_rowptr[nsuper+1] and super_rows[...] (sorted
+   row indices of each supernode's front, its own columns first). */
+wd_status wd_symbolic_export(wd_handle h, int32_t *perm, int32_t *parent, int64_t *colcount,
+                             int32_t *super_first, int64_t *super_rowptr, int32_t *super_rows);
+
+wd_status wd_get_info(wd_handle h, wd_info *info);
+
+/* Numeric factorization P A P^T = L L^T (multifrontal, on the GPU).
+   values: nnz doubles in the order of the analyzed rowidx, on the host
+   (values_on_device = 0) or on the device (1).  Synchronous: returns
+   WD_ERR_NOT_SPD if a pivot is not positive. */
+wd_status wd_factor(wd_handle h, const double *values, int values_on_device, wd_precision prec,
+                    void *stream);
+
+/* B := A^-1 B for nrhs columns of leading dimension ldb >= n, original
+   order.  B on the device (B_on_device = 1) or the host (0).  In WD_MIXED the
+   solve is refined in FP64 until the backward error is <= ir_tol
+   (WD_ERR_NO_CONVERGENCE after ir_max_iter steps).  In WD_FP64 the backward
+   error is computed only if info is not NULL.  Synchronous. */
+wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb, int B_on_device,
+                   void *stream, wd_solve_info *info);
+
+/* log det A = 2 sum_j log L_jj (compensated sum).  Synchronous. */
+wd_status wd_logdet(wd_handle h, double *out);
+
+/* S := P^T L Z, both n x nrhs with leading dimension ld; Z is indexed in the
+   factor's (permuted) order, S in the original order.  Gaussian random field
+   samples for Z ~ N(0, I) (Section 5.3).  Device (1) or host (0) arrays.
+   Synchronous. */
+wd_status wd_apply_L(wd_handle h, const double *Z, double *S, int64_t nrhs, int64_t ld,
+                     int on_device, void *stream);
+
+/* Copy the stored factor (supernodal panels, FP64) to a host array of
+   info.nnz_L_stored doubles: for each supernode s, its m_s x k_s lower
+   panel, column-major (ld m_s), rows as in super_rows.  Entries above the
+   diagonal of the panel are zero.  Synchronous. */
+wd_status wd_export_L(wd_handle h, double *panels);
+
+/* Per-kernel statistics accumulated while wd_options.profile = 1: name (the
+   kernel and its precision), launches, summed event time, and the
+   algorithmic flops and bytes of those launches (flops of the arithmetic the
+   method needs on the stored fronts; bytes of the front, update-matrix and
+   A entries each launch must read or write once).  Up to cap entries are
+   written to out; *count receives the number of kernels.  reset != 0 clears
+   the statistics after copying. */
+typedef struct {
+    char name[40];
+    int64_t launches;
+    double milliseconds;
+    double flops;
+    double bytes;
+} wd_kernel_stat;
+
+wd_status wd_kernel_stats(wd_handle h, wd_kernel_stat *out, int32_t cap, int32_t *count,
+                          int reset);
+
+/* Number of CUDA kernels this handle has launched (all calls); reset != 0
+   sets the counter back to zero after reading it. */
+wd_status wd_launch_count(wd_handle h, int64_t *count, int reset);
+
+/* Detail of the last error: failing column (or -1) and a message. */
+wd_status wd_status_detail(wd_handle h, int64_t *column, char *msg, size_t len);
+
+const char *wd_status_string(wd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WD_H */

@@ -67,6 +67,8 @@ def _load():
             lib.or_get_Lpattern.argtypes = [ctypes.c_void_p, _i64p, _i32p]
             lib.or_factor.restype = ctypes.c_int64
             lib.or_factor.argtypes = [ctypes.c_void_p, _f64p]
+            lib.or_factor_cols.restype = ctypes.c_int64
+            lib.or_factor_cols.argtypes = [ctypes.c_void_p, _f64p, ctypes.c_int64]
             lib.or_get_L.argtypes = [ctypes.c_void_p, _f64p]
             lib.or_solve.restype = ctypes.c_int
             lib.or_solve.argtypes = [ctypes.c_void_p, _f64p, ctypes.c_int64, ctypes.c_int64]
@@ -164,6 +166,14 @@ class Oracle:
         v = np.ascontiguousarray(values, np.float64)
         rc = int(self._lib.or_factor(self._ctx, _p(v, _f64p)))
         self.factored = rc == 0
+        return rc
+
+    def factor_prefix(self, values, ncols: int) -> int:
+        """Factor only the first ncols columns of P A P^T (a bounded sample
+        of the full factorization, for timing)."""
+        v = np.ascontiguousarray(values, np.float64)
+        rc = int(self._lib.or_factor_cols(self._ctx, _p(v, _f64p), int(ncols)))
+        self.factored = rc == 0 and ncols >= self.n
         return rc
 
     def L_values(self) -> np.ndarray:

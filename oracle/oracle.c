@@ -475,10 +475,13 @@ void or_get_Lpattern(const or_ctx *c, int64_t *Lp, int32_t *Li) {
 /* numeric                                                             */
 /* ------------------------------------------------------------------ */
 
-/* left-looking Cholesky.  Returns 0, or -(j+1) if the pivot of column j of
-   P A P^T is not positive (j = the first such column). */
-int64_t or_factor(or_ctx *c, const double *values) {
+/* left-looking Cholesky of the first ncols columns of P A P^T (all of them
+   if ncols < 0 or ncols > n).  Returns 0, or -(j+1) if the pivot of column j
+   is not positive (j = the first such column).  Only a full factorization
+   leaves the context factored. */
+int64_t or_factor_cols(or_ctx *c, const double *values, int64_t ncols) {
     int64_t n = c->n;
+    int64_t stop = (ncols < 0 || ncols > n) ? n : ncols;
     free_numeric(c);
     c->Lx = (double *)malloc(sizeof(double) * (size_t)c->Lp[n]);
     double *w = (double *)calloc((size_t)n, sizeof(double));
@@ -488,7 +491,7 @@ int64_t or_factor(or_ctx *c, const double *values) {
     int32_t *ks = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     for (int64_t j = 0; j < n; ++j) head[j] = -1;
     int64_t status = 0;
-    for (int64_t j = 0; j < n; ++j) {
+    for (int64_t j = 0; j < stop; ++j) {
         for (int64_t q = c->pcolptr[j]; q < c->pcolptr[j + 1]; ++q)
             w[c->prow[q]] = values[c->psrc[q]];
         /* columns k < j with L_jk != 0, ascending */
@@ -526,9 +529,11 @@ int64_t or_factor(or_ctx *c, const double *values) {
     }
     free(w); free(next); free(head); free(link); free(ks);
     if (status) { free_numeric(c); return status; }
-    c->factored = 1;
+    c->factored = (stop == n);
     return 0;
 }
+
+int64_t or_factor(or_ctx *c, const double *values) { return or_factor_cols(c, values, -1); }
 
 void or_get_L(const or_ctx *c, double *Lx) {
     memcpy(Lx, c->Lx, sizeof(double) * (size_t)c->Lp[c->n]);

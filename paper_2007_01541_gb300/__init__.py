@@ -1,0 +1,331 @@
+"""Python binding of libwd (argument marshalling only).
+
+Every step of the solver runs in the C/CUDA library ``_build/libwd.so``; this
+module converts numpy arrays and torch tensors to pointers, sizes and
+streams.  The library is loaded eagerly on first use and its absence is an
+error: there is no fallback implementation.
+
+Names follow the C ABI in ``include/wd.h``: analyze -> factor -> solve /
+logdet / apply_L.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "_build", "libwd.so")
+_lock = threading.Lock()
+_lib = None
+
+WD_OK, WD_ERR_INVALID_ARG, WD_ERR_PATTERN, WD_ERR_STATE, WD_ERR_NOT_SPD, WD_ERR_OOM, \
+    WD_ERR_CUDA, WD_ERR_TIMEOUT, WD_ERR_NO_CONVERGENCE = range(9)
+WD_FP64, WD_MIXED = 0, 1
+_PREC = {"fp64": WD_FP64, "mixed": WD_MIXED, WD_FP64: WD_FP64, WD_MIXED: WD_MIXED}
+
+EXPORTED = ["wd_default_options", "wd_create", "wd_destroy", "wd_analyze", "wd_symbolic_export",
+            "wd_get_info", "wd_factor", "wd_solve", "wd_logdet", "wd_apply_L", "wd_export_L",
+            "wd_status_detail", "wd_status_string", "wd_kernel_stats", "wd_launch_count"]
+
+
+class WdOptions(ctypes.Structure):
+    _fields_ = [("nd_leaf", ctypes.c_int32), ("relax_k", ctypes.c_int32),
+                ("relax_pct", ctypes.c_int32), ("ir_max_iter", ctypes.c_int32),
+                ("ir_tol", ctypes.c_double), ("use_graphs", ctypes.c_int32),
+                ("symbolic_only", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class WdGeometry(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("level", ctypes.c_void_p), ("box_lo", ctypes.c_void_p),
+                ("box_side", ctypes.c_void_p), ("patch", ctypes.c_void_p)]
+
+
+class WdInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz_A_lower", ctypes.c_int64), ("nnz_L", ctypes.c_int64),
+                ("nnz_L_stored", ctypes.c_int64), ("flops_factor", ctypes.c_double),
+                ("nsuper", ctypes.c_int32), ("nlevels", ctypes.c_int32),
+                ("max_front", ctypes.c_int32), ("max_width", ctypes.c_int32),
+                ("front_bytes", ctypes.c_int64), ("factor_launches", ctypes.c_int64),
+                ("analyze_seconds", ctypes.c_double)]
+
+
+class WdKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64),
+                ("milliseconds", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+class WdSolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("backward_error", ctypes.c_double)]
+
+
+class WdError(RuntimeError):
+    def __init__(self, status, msg, column=-1):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+        self.column = column
+
+
+def library_path() -> str:
+    return _LIBPATH
+
+
+def load():
+    """Load libwd.so (built by build.py).  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIBPATH):
+            raise RuntimeError(f"libwd.so not built ({_LIBPATH}); run build.build() first")
+        lib = ctypes.CDLL(_LIBPATH)
+        vp, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        lib.wd_default_options.argtypes = [ctypes.POINTER(WdOptions)]
+        lib.wd_default_options.restype = None
+        lib.wd_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(WdOptions)]
+        lib.wd_destroy.argtypes = [vp]
+        lib.wd_destroy.restype = None
+        lib.wd_analyze.argtypes = [vp, i64, vp, vp, ctypes.POINTER(WdGeometry)]
+        lib.wd_symbolic_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        lib.wd_get_info.argtypes = [vp, ctypes.POINTER(WdInfo)]
+        lib.wd_factor.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp]
+        lib.wd_solve.argtypes = [vp, vp, i64, i64, ctypes.c_int, vp, ctypes.POINTER(WdSolveInfo)]
+        lib.wd_logdet.argtypes = [vp, ctypes.POINTER(f64)]
+        lib.wd_apply_L.argtypes = [vp, vp, vp, i64, i64, ctypes.c_int, vp]
+        lib.wd_export_L.argtypes = [vp, vp]
+        lib.wd_status_detail.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_char_p, ctypes.c_size_t]
+        lib.wd_kernel_stats.argtypes = [vp, ctypes.POINTER(WdKernelStat), i32, ctypes.POINTER(i32),
+                                        ctypes.c_int]
+        lib.wd_launch_count.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_int]
+        lib.wd_status_string.argtypes = [ctypes.c_int]
+        lib.wd_status_string.restype = ctypes.c_char_p
+        for f in ("wd_create", "wd_analyze", "wd_symbolic_export", "wd_get_info", "wd_factor",
+                  "wd_solve", "wd_logdet", "wd_apply_L", "wd_export_L", "wd_status_detail",
+                  "wd_kernel_stats", "wd_launch_count"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _status_name(s):
+    try:
+        return load().wd_status_string(int(s)).decode()
+    except Exception:
+        return f"status {s}"
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or torch tensor."""
+    if _is_torch(a):
+        return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    return ctypes.c_void_p(a.ctypes.data), 0
+
+
+def _stream(stream, needed):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    if needed:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+class Solver:
+    """One sparse SPD system: analyze once, factor (re)peatedly, solve many."""
+
+    def __init__(self, nd_leaf=64, relax_k=16, relax_pct=10, ir_max_iter=10, ir_tol=1e-12,
+                 symbolic_only=False, profile=False):
+        self._lib = load()
+        o = WdOptions()
+        self._lib.wd_default_options(ctypes.byref(o))
+        o.nd_leaf, o.relax_k, o.relax_pct = nd_leaf, relax_k, relax_pct
+        o.ir_max_iter, o.ir_tol = ir_max_iter, ir_tol
+        o.symbolic_only = 1 if symbolic_only else 0
+        o.profile = 1 if profile else 0
+        self._h = ctypes.c_void_p()
+        self._check(self._lib.wd_create(ctypes.byref(self._h), ctypes.byref(o)))
+        self.n = None
+        self.precision = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.wd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != WD_OK:
+            col = ctypes.c_int64(-1)
+            buf = ctypes.create_string_buffer(512)
+            if getattr(self, "_h", None):
+                self._lib.wd_status_detail(self._h, ctypes.byref(col), buf, 512)
+            raise WdError(st, buf.value.decode(errors="replace"), col.value)
+
+    # -- analysis --------------------------------------------------------------
+    def analyze(self, colptr, rowidx, basis=None):
+        """basis: an object with dim, level, box_lo, box_side (or None)."""
+        cp = np.ascontiguousarray(colptr, np.int64)
+        ri = np.ascontiguousarray(rowidx, np.int32)
+        n = cp.size - 1
+        g = None
+        keep = []
+        if basis is not None:
+            lev = np.ascontiguousarray(basis.level, np.int32)
+            lo = np.ascontiguousarray(basis.box_lo, np.int32)
+            side = np.ascontiguousarray(basis.box_side, np.int32)
+            keep = [lev, lo, side]
+            g = WdGeometry(int(basis.dim), lev.ctypes.data, lo.ctypes.data, side.ctypes.data, None)
+        self._check(self._lib.wd_analyze(self._h, n, cp.ctypes.data, ri.ctypes.data,
+                                         ctypes.byref(g) if g is not None else None))
+        del keep
+        self.n = n
+        self.nnz = int(cp[-1])
+        return self
+
+    def info(self) -> dict:
+        i = WdInfo()
+        self._check(self._lib.wd_get_info(self._h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in WdInfo._fields_}
+
+    def symbolic(self) -> dict:
+        inf = self.info()
+        n, ns = self.n, inf["nsuper"]
+        perm = np.empty(n, np.int32)
+        parent = np.empty(n, np.int32)
+        cc = np.empty(n, np.int64)
+        sf = np.empty(ns + 1, np.int32)
+        srp = np.empty(ns + 1, np.int64)
+        self._check(self._lib.wd_symbolic_export(self._h, perm.ctypes.data, parent.ctypes.data,
+                                                 cc.ctypes.data, sf.ctypes.data, srp.ctypes.data,
+                                                 None))
+        rows = np.empty(max(int(srp[-1]), 1), np.int32)
+        self._check(self._lib.wd_symbolic_export(self._h, None, None, None, None, None,
+                                                 rows.ctypes.data))
+        return dict(perm=perm, parent=parent, colcount=cc, super_first=sf, super_rowptr=srp,
+                    super_rows=rows[: int(srp[-1])])
+
+    # -- numeric -----------------------------------------------------------------
+    def factor(self, values, precision="fp64", stream=None):
+        p, dev = _ptr(values)
+        self._check(self._lib.wd_factor(self._h, p, dev, _PREC[precision], _stream(stream, dev)))
+        self.precision = precision
+        return self
+
+    def solve(self, B, stream=None, with_info=True):
+        """Solve A X = B.  A CUDA tensor (n x nrhs, column-major: pass B with
+        B.stride(0) == 1, e.g. the transpose of a contiguous (nrhs, n) tensor)
+        is overwritten in place; a numpy array gives a new array."""
+        info = WdSolveInfo()
+        if _is_torch(B):
+            if B.dim() == 1:
+                B = B.unsqueeze(1)
+            if B.stride(0) != 1:
+                raise ValueError("B must be column-major (stride(0) == 1)")
+            ldb = B.stride(1) if B.shape[1] > 1 else B.shape[0]
+            p, dev = _ptr(B)
+            self._check(self._lib.wd_solve(self._h, p, B.shape[1], ldb, dev, _stream(stream, dev),
+                                           ctypes.byref(info) if with_info else None))
+            out = B
+        else:
+            X = np.array(B, dtype=np.float64, order="F", copy=True)
+            if X.ndim == 1:
+                X = X[:, None]
+            self._check(self._lib.wd_solve(self._h, ctypes.c_void_p(X.ctypes.data), X.shape[1],
+                                           X.shape[0], 0, _stream(stream, False),
+                                           ctypes.byref(info) if with_info else None))
+            out = X
+        self.last_solve = {"iterations": info.iterations, "backward_error": info.backward_error}
+        return out
+
+    def logdet(self) -> float:
+        v = ctypes.c_double()
+        self._check(self._lib.wd_logdet(self._h, ctypes.byref(v)))
+        return v.value
+
+    def apply_L(self, Z, S=None, stream=None):
+        """S = P^T L Z (Z in factor order).  Torch CUDA tensors (column-major)
+        or numpy arrays."""
+        if _is_torch(Z):
+            import torch
+            if Z.dim() == 1:
+                Z = Z.unsqueeze(1)
+            if S is None:
+                S = torch.empty((Z.shape[1], Z.shape[0]), dtype=torch.float64, device=Z.device).T
+            pz, dev = _ptr(Z)
+            ps, _ = _ptr(S)
+            ld = Z.shape[0]
+            if Z.stride(0) != 1 or S.stride(0) != 1 or (Z.shape[1] > 1 and (Z.stride(1) != ld or S.stride(1) != ld)):
+                raise ValueError("Z and S must be column-major with leading dimension n")
+            self._check(self._lib.wd_apply_L(self._h, pz, ps, Z.shape[1], ld, dev, _stream(stream, dev)))
+            return S
+        Zc = np.array(Z, dtype=np.float64, order="F", copy=True)
+        if Zc.ndim == 1:
+            Zc = Zc[:, None]
+        So = np.empty_like(Zc, order="F")
+        self._check(self._lib.wd_apply_L(self._h, ctypes.c_void_p(Zc.ctypes.data),
+                                         ctypes.c_void_p(So.ctypes.data), Zc.shape[1], Zc.shape[0], 0,
+                                         _stream(stream, False)))
+        return So
+
+    def kernel_stats(self, reset=False) -> list:
+        """Per-kernel launches, event time and algorithmic flops/bytes
+        accumulated while profiling (Solver(profile=True))."""
+        cnt = ctypes.c_int32()
+        self._check(self._lib.wd_kernel_stats(self._h, None, 0, ctypes.byref(cnt), 0))
+        arr = (WdKernelStat * max(cnt.value, 1))()
+        self._check(self._lib.wd_kernel_stats(self._h, arr, cnt.value, ctypes.byref(cnt),
+                                              1 if reset else 0))
+        return [dict(name=a.name.decode(), launches=a.launches, ms=a.milliseconds, flops=a.flops,
+                     bytes=a.bytes) for a in arr[: cnt.value]]
+
+    def launch_count(self, reset=False) -> int:
+        c = ctypes.c_int64()
+        self._check(self._lib.wd_launch_count(self._h, ctypes.byref(c), 1 if reset else 0))
+        return c.value
+
+    def export_L(self) -> np.ndarray:
+        """Stored supernodal panels (see wd_export_L)."""
+        out = np.empty(self._panel_size(), np.float64)
+        self._check(self._lib.wd_export_L(self._h, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def _panel_size(self) -> int:
+        sym = self.symbolic()
+        k = np.diff(sym["super_first"]).astype(np.int64)
+        m = np.diff(sym["super_rowptr"]).astype(np.int64)
+        return int((k * m).sum())
+
+    def L_csc_like(self, Lp, Li):
+        """The factor's entries at the positions of a CSC pattern of L
+        (e.g. the oracle's): values of stored panels, structural entries only."""
+        sym = self.symbolic()
+        panels = self.export_L()
+        sf, srp, rows = sym["super_first"], sym["super_rowptr"], sym["super_rows"]
+        n = self.n
+        col2s = np.repeat(np.arange(sf.size - 1), np.diff(sf))
+        k = np.diff(sf).astype(np.int64)
+        m = np.diff(srp).astype(np.int64)
+        poff = np.concatenate([[0], np.cumsum(k * m)])
+        out = np.empty(Li.size, np.float64)
+        for j in range(n):
+            s = col2s[j]
+            r = rows[srp[s]: srp[s + 1]]
+            loc = np.searchsorted(r, Li[Lp[j]: Lp[j + 1]])
+            if np.any(loc >= r.size) or np.any(r[np.minimum(loc, r.size - 1)] != Li[Lp[j]: Lp[j + 1]]):
+                raise ValueError(f"pattern of column {j} not inside its supernode")
+            c = j - sf[s]
+            out[Lp[j]: Lp[j + 1]] = panels[poff[s] + c * m[s] + loc]
+        return out

@@ -1,0 +1,986 @@
+// C ABI of the solver: handle, analysis, launch plans and the numeric calls.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/wd.h"
+#include "engine.h"
+#include "symbolic.h"
+
+using wd::DevSym;
+using wd::NB;
+using wd::RB;
+using wd::SOLVE_RB;
+using wd::status_t;
+
+namespace {
+
+constexpr int RG = 16;             // right-hand sides per solve block (solve_kernels.cu)
+constexpr int ROWS_PER_CTA = 256;  // one thread per front row (gather / apply_L)
+
+enum LaunchKind {
+    K_INIT, K_POTRF_FIRST, K_PANEL, K_UPDATE,                  // factor
+    K_FWD_GATHER, K_FWD_DIAG_FIRST, K_FWD_UPDATE,              // forward solve
+    K_BWD_INIT, K_BWD_STEP,                                    // backward solve
+    K_APPLY_L
+};
+
+struct Launch {
+    int kind;
+    int64_t off;   // into the item array
+    int count;
+    int arg;       // kb or ib
+    double flops = 0;        // algorithmic flops of the launch
+    double elems = 0;        // front / vector elements moved (x sizeof(T))
+    double bytes = 0;        // other bytes (A values and indices)
+};
+
+const char *kind_name(int k) {
+    static const char *names[] = {"front_init", "potrf_first", "panel_trsm", "schur_update",
+                                  "fwd_gather", "fwd_diag_first", "fwd_update", "bwd_init",
+                                  "bwd_step", "apply_L"};
+    return names[k];
+}
+
+struct KStat {
+    int64_t launches = 0;
+    double ms = 0, flops = 0, bytes = 0;
+};
+
+struct Plan {
+    std::vector<int4> items;
+    std::vector<Launch> launches;
+    int4 *d_items = nullptr;
+};
+
+struct DevMem {
+    std::vector<void *> ptrs;
+    cudaError_t alloc(void **p, size_t bytes) {
+        *p = nullptr;
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+    void release(void *p) {
+        if (!p) return;
+        auto it = std::find(ptrs.begin(), ptrs.end(), p);
+        if (it != ptrs.end()) {
+            cudaFree(p);
+            ptrs.erase(it);
+        }
+    }
+    void free_all() {
+        for (void *p : ptrs) cudaFree(p);
+        ptrs.clear();
+    }
+};
+
+}  // namespace
+
+struct wd_ctx {
+    wd_options opt;
+    int device = 0;
+    bool analyzed = false, factored = false;
+    wd_precision prec = WD_FP64;
+    wd::Symbolic S;
+    DevMem mem;        // analysis lifetime
+    DevMem work;       // numeric workspaces (factor / solve)
+    DevSym dsym{};
+    int32_t *d_csr_src = nullptr;
+    double *d_csr_val = nullptr;
+    double *d_values_stage = nullptr;
+    void *d_front = nullptr;
+    size_t front_elems = 0;
+    status_t *d_status = nullptr;
+    double *d_scalars = nullptr;   // [0] = ||A||_inf, [1] = logdet, [2..] partials
+    Plan fplan;
+    Plan splan;
+    int splan_nrhs = -1;
+    Plan aplan;
+    int aplan_nrhs = -1;
+    // solve workspaces (sized for ws_cols right-hand sides)
+    int64_t ws_cols = 0;
+    void *d_Y = nullptr, *d_W = nullptr;
+    double *d_B = nullptr, *d_Bp = nullptr, *d_X = nullptr, *d_R = nullptr, *d_cm = nullptr;
+    int64_t W_rows = 0;   // sum of (m_s - k_s)
+    int64_t nnz_full = 0;  // stored entries of the full CSR of P A P^T
+    double normA = 0.0;
+    wd_info info{};
+    // profiling
+    int64_t launches = 0;  // kernels launched by this handle
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<std::pair<std::string, KStat>> prof;
+    std::string msg;
+    int64_t errcol = -1;
+};
+
+static wd_status fail(wd_handle h, wd_status s, const std::string &m, int64_t col = -1) {
+    if (h) {
+        h->msg = m;
+        h->errcol = col;
+    }
+    return s;
+}
+
+static wd_status cuda_fail(wd_handle h, cudaError_t e, const char *where) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(h, WD_ERR_OOM, std::string(where) + ": " + cudaGetErrorString(e));
+    }
+    return fail(h, WD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                     \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+    } while (0)
+
+extern "C" {
+
+const char *wd_status_string(wd_status s) {
+    switch (s) {
+        case WD_OK: return "WD_OK";
+        case WD_ERR_INVALID_ARG: return "WD_ERR_INVALID_ARG";
+        case WD_ERR_PATTERN: return "WD_ERR_PATTERN";
+        case WD_ERR_STATE: return "WD_ERR_STATE";
+        case WD_ERR_NOT_SPD: return "WD_ERR_NOT_SPD";
+        case WD_ERR_OOM: return "WD_ERR_OOM";
+        case WD_ERR_CUDA: return "WD_ERR_CUDA";
+        case WD_ERR_TIMEOUT: return "WD_ERR_TIMEOUT";
+        case WD_ERR_NO_CONVERGENCE: return "WD_ERR_NO_CONVERGENCE";
+    }
+    return "unknown";
+}
+
+void wd_default_options(wd_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->nd_leaf = 64;
+    o->relax_k = 16;
+    o->relax_pct = 10;
+    o->ir_max_iter = 10;
+    o->ir_tol = 1e-12;
+    o->use_graphs = 1;
+}
+
+wd_status wd_create(wd_handle *out, const wd_options *opt) {
+    if (!out) return WD_ERR_INVALID_ARG;
+    *out = nullptr;
+    wd_ctx *h = new (std::nothrow) wd_ctx();
+    if (!h) return WD_ERR_OOM;
+    wd_default_options(&h->opt);
+    if (opt) h->opt = *opt;
+    if (h->opt.nd_leaf < 1 || h->opt.relax_k < 0 || h->opt.relax_pct < 0 || h->opt.ir_max_iter < 0 ||
+        !(h->opt.ir_tol > 0)) {
+        delete h;
+        return WD_ERR_INVALID_ARG;
+    }
+    if (!h->opt.symbolic_only && cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return WD_ERR_CUDA;
+    }
+    *out = h;
+    return WD_OK;
+}
+
+void wd_destroy(wd_handle h) {
+    if (!h) return;
+    if (!h->opt.symbolic_only) {
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(h->device);
+        for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+        h->work.free_all();
+        h->mem.free_all();
+        cudaSetDevice(prev);
+    }
+    delete h;
+}
+
+wd_status wd_status_detail(wd_handle h, int64_t *column, char *msg, size_t len) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (column) *column = h->errcol;
+    if (msg && len) {
+        std::snprintf(msg, len, "%s", h->msg.c_str());
+    }
+    return WD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// plans
+// ---------------------------------------------------------------------------
+static void add_launch(Plan &p, int kind, size_t first, int arg, double flops = 0,
+                       double elems = 0, double bytes = 0) {
+    const int count = (int)(p.items.size() - first);
+    if (count > 0) {
+        Launch L;
+        L.kind = kind;
+        L.off = (int64_t)first;
+        L.count = count;
+        L.arg = arg;
+        L.flops = flops;
+        L.elems = elems;
+        L.bytes = bytes;
+        p.launches.push_back(L);
+    }
+}
+
+// lower-triangle entries (r >= c) of the tile rows [r0, r1) x cols [c0, c1)
+static double lower_count(int64_t r0, int64_t r1, int64_t c0, int64_t c1) {
+    double cnt = 0;
+    for (int64_t c = c0; c < c1; ++c) cnt += (double)std::max<int64_t>(0, r1 - std::max(r0, c));
+    return cnt;
+}
+
+static void build_factor_plan(const wd::Symbolic &S, Plan &p) {
+    p.items.clear();
+    p.launches.clear();
+    for (int l = 0; l < S.nlevels; ++l) {
+        const int b = S.level_ptr[l], e = S.level_ptr[l + 1];
+        size_t f0 = p.items.size();
+        double el = 0, by = 0;
+        for (int i = b; i < e; ++i) {
+            const int s = S.level_nodes[i];
+            const double m = S.m(s);
+            for (int q = 0; q < S.m(s); ++q) p.items.push_back({s, q, 0, 0});
+            el += m * (m + 1) / 2;  // every lower front entry written once
+            for (int c = S.child_ptr[s]; c < S.child_ptr[s + 1]; ++c) {
+                const double u = S.m(S.children[c]) - S.k(S.children[c]);
+                el += u * (u + 1) / 2;  // every child update entry read once
+            }
+            by += 12.0 * (double)(S.pcp[S.sfirst[s + 1]] - S.pcp[S.sfirst[s]]);
+        }
+        add_launch(p, K_INIT, f0, 0, 0, el, by);
+        f0 = p.items.size();
+        int kmax = 0;
+        double fl = 0;
+        el = 0;
+        for (int i = b; i < e; ++i) {
+            const int s = S.level_nodes[i];
+            p.items.push_back({s, 0, 0, 0});
+            kmax = std::max(kmax, S.k(s));
+            const double nb = std::min(NB, S.k(s));
+            fl += nb * nb * nb / 3;
+            el += nb * (nb + 1);
+        }
+        add_launch(p, K_POTRF_FIRST, f0, 0, fl, el, 0);
+        for (int kb = 0; kb < kmax; kb += NB) {
+            f0 = p.items.size();
+            fl = el = 0;
+            for (int i = b; i < e; ++i) {
+                const int s = S.level_nodes[i], k = S.k(s), m = S.m(s);
+                if (k <= kb) continue;
+                const int nb = std::min(NB, k - kb);
+                const int t0 = kb + nb;
+                for (int rb = 0; rb * RB < m - t0; ++rb) p.items.push_back({s, rb, 0, 0});
+                fl += (double)(m - t0) * nb * nb;
+                el += 2.0 * (m - t0) * nb + (double)nb * (nb + 1) / 2;
+            }
+            add_launch(p, K_PANEL, f0, kb, fl, el, 0);
+            f0 = p.items.size();
+            fl = el = 0;
+            for (int i = b; i < e; ++i) {
+                const int s = S.level_nodes[i], k = S.k(s), m = S.m(s);
+                if (k <= kb) continue;
+                const int nb = std::min(NB, k - kb);
+                const int t0 = kb + nb;
+                const int nt = (m - t0 + NB - 1) / NB;
+                for (int ti = 0; ti < nt; ++ti)
+                    for (int tj = 0; tj <= ti; ++tj) p.items.push_back({s, ti, tj, 0});
+                const double tri = (double)(m - t0) * (m - t0 + 1) / 2;
+                fl += 2.0 * nb * tri;
+                el += 2.0 * tri + (double)(m - t0) * nb;  // read+write trailing, read panel
+                if (t0 < k) {
+                    const double nb2 = std::min(NB, k - t0);
+                    fl += nb2 * nb2 * nb2 / 3;
+                }
+            }
+            add_launch(p, K_UPDATE, f0, kb, fl, el, 0);
+        }
+    }
+}
+
+static void build_solve_plan(const wd::Symbolic &S, int nrhs, Plan &p) {
+    p.items.clear();
+    p.launches.clear();
+    const int ng = (nrhs + RG - 1) / RG;
+    const double R = nrhs;
+    for (int l = 0; l < S.nlevels; ++l) {
+        const int b = S.level_ptr[l], e = S.level_ptr[l + 1];
+        size_t f0 = p.items.size();
+        int kmax = 0;
+        double el = 0, fl = 0;
+        for (int i = b; i < e; ++i) {
+            const int s = S.level_nodes[i];
+            for (int rc = 0; rc * ROWS_PER_CTA < S.m(s); ++rc) p.items.push_back({s, rc, 0, 0});
+            kmax = std::max(kmax, S.k(s));
+            el += R * S.m(s);
+            for (int c = S.child_ptr[s]; c < S.child_ptr[s + 1]; ++c)
+                el += R * (S.m(S.children[c]) - S.k(S.children[c]));
+        }
+        add_launch(p, K_FWD_GATHER, f0, 0, 0, el, 0);
+        f0 = p.items.size();
+        el = fl = 0;
+        for (int i = b; i < e; ++i) {
+            const double nb = std::min(NB, S.k(S.level_nodes[i]));
+            for (int g = 0; g < ng; ++g) p.items.push_back({S.level_nodes[i], g, 0, 0});
+            fl += nb * nb * R;
+            el += nb * (nb + 1) / 2 + 2 * nb * R;
+        }
+        add_launch(p, K_FWD_DIAG_FIRST, f0, 0, fl, el, 0);
+        for (int kb = 0; kb < kmax; kb += NB) {
+            f0 = p.items.size();
+            el = fl = 0;
+            for (int i = b; i < e; ++i) {
+                const int s = S.level_nodes[i], k = S.k(s), m = S.m(s);
+                if (k <= kb) continue;
+                const int nb = std::min(NB, k - kb);
+                const int t0 = kb + nb;
+                for (int rb = 0; rb * SOLVE_RB < m - t0; ++rb)
+                    for (int g = 0; g < ng; ++g) p.items.push_back({s, rb, g, 0});
+                fl += 2.0 * (m - t0) * nb * R;
+                el += (double)(m - t0) * nb + 2.0 * (m - t0) * R + nb * R;
+                if (t0 < k) {
+                    const double nb2 = std::min(NB, k - t0);
+                    fl += nb2 * nb2 * R;
+                    el += nb2 * (nb2 + 1) / 2;
+                }
+            }
+            add_launch(p, K_FWD_UPDATE, f0, kb, fl, el, 0);
+        }
+    }
+    for (int l = S.nlevels - 1; l >= 0; --l) {
+        const int b = S.level_ptr[l], e = S.level_ptr[l + 1];
+        size_t f0 = p.items.size();
+        int maxblk = 0;
+        double el = 0, fl = 0;
+        for (int i = b; i < e; ++i) {
+            const int s = S.level_nodes[i];
+            const int k = S.k(s), m = S.m(s);
+            const int nblk = (k + NB - 1) / NB;
+            maxblk = std::max(maxblk, nblk);
+            for (int jb = 0; jb < nblk; ++jb)
+                for (int g = 0; g < ng; ++g) p.items.push_back({s, jb, g, 0});
+            fl += 2.0 * (m - k) * k * R;
+            el += (double)(m - k) * k + (m - k) * R + 2.0 * k * R;
+            const double nbl = k - (nblk - 1) * NB;
+            fl += nbl * nbl * R;
+            el += nbl * (nbl + 1) / 2;
+        }
+        add_launch(p, K_BWD_INIT, f0, 0, fl, el, 0);
+        for (int ib = maxblk - 2; ib >= 0; --ib) {
+            f0 = p.items.size();
+            el = fl = 0;
+            for (int i = b; i < e; ++i) {
+                const int s = S.level_nodes[i];
+                const int k = S.k(s);
+                const int nblk = (k + NB - 1) / NB;
+                if (nblk < ib + 2) continue;
+                for (int jb = 0; jb <= ib; ++jb)
+                    for (int g = 0; g < ng; ++g) p.items.push_back({s, jb, g, 0});
+                const double nr = std::min(NB, k - (ib + 1) * NB);
+                fl += 2.0 * nr * (ib + 1) * NB * R + (double)NB * NB * R;
+                el += nr * (ib + 1) * NB + nr * R + 2.0 * (ib + 1) * NB * R + NB * (NB + 1) / 2.0;
+            }
+            add_launch(p, K_BWD_STEP, f0, ib, fl, el, 0);
+        }
+    }
+}
+
+static void build_apply_plan(const wd::Symbolic &S, Plan &p) {
+    p.items.clear();
+    p.launches.clear();
+    for (int l = 0; l < S.nlevels; ++l) {
+        size_t f0 = p.items.size();
+        for (int i = S.level_ptr[l]; i < S.level_ptr[l + 1]; ++i) {
+            const int s = S.level_nodes[i];
+            for (int rc = 0; rc * ROWS_PER_CTA < S.m(s); ++rc) p.items.push_back({s, rc, 0, 0});
+        }
+        add_launch(p, K_APPLY_L, f0, 0);
+    }
+}
+
+static wd_status upload_plan(wd_handle h, DevMem &mem, Plan &p) {
+    if (p.d_items) mem.release(p.d_items);
+    p.d_items = nullptr;
+    CK(mem.alloc((void **)&p.d_items, p.items.size() * sizeof(int4)), "plan alloc");
+    CK(cudaMemcpy(p.d_items, p.items.data(), p.items.size() * sizeof(int4), cudaMemcpyHostToDevice),
+       "plan upload");
+    return WD_OK;
+}
+
+template <class V>
+static wd_status upload(wd_handle h, const std::vector<V> &v, const V **dst) {
+    V *p = nullptr;
+    CK(h->mem.alloc((void **)&p, v.size() * sizeof(V)), "analysis alloc");
+    if (!v.empty()) CK(cudaMemcpy(p, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice), "upload");
+    *dst = p;
+    return WD_OK;
+}
+
+#define UP(vec, field)                                  \
+    do {                                                \
+        wd_status s_ = upload(h, vec, &(field));        \
+        if (s_ != WD_OK) return s_;                     \
+    } while (0)
+
+static void fill_info(wd_handle h, int64_t nnzl, int maxm, int maxk,
+                      std::chrono::steady_clock::time_point t0) {
+    const wd::Symbolic &S = h->S;
+    wd_info &I = h->info;
+    std::memset(&I, 0, sizeof(I));
+    I.n = S.n;
+    I.nnz_A_lower = nnzl;
+    I.nnz_L = S.nnzL;
+    I.nnz_L_stored = S.nnzL_stored;
+    I.flops_factor = S.flops;
+    I.nsuper = S.ns;
+    I.nlevels = S.nlevels;
+    I.max_front = maxm;
+    I.max_width = maxk;
+    I.front_bytes = (int64_t)h->front_elems * 8;
+    I.factor_launches = (int64_t)h->fplan.launches.size();
+    I.analyze_seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, const int32_t *rowidx,
+                                const wd_geometry *geom) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (n <= 0 || !colptr || !rowidx) return fail(h, WD_ERR_INVALID_ARG, "bad size or null pattern");
+    if (geom && (geom->patch || geom->dim < 0 || geom->dim > 3))
+        return fail(h, WD_ERR_INVALID_ARG, "unsupported geometry");
+    const bool host_only = h->opt.symbolic_only != 0;
+    if (!host_only) CK(cudaSetDevice(h->device), "set device");
+    auto t0 = std::chrono::steady_clock::now();
+    h->analyzed = h->factored = false;
+    if (!host_only) {
+        h->work.free_all();
+        h->mem.free_all();
+    }
+    h->fplan = Plan();
+    h->splan = Plan();
+    h->aplan = Plan();
+    h->splan_nrhs = h->aplan_nrhs = -1;
+    h->ws_cols = 0;
+    h->d_front = nullptr;
+    h->front_elems = 0;
+    std::string msg;
+    const int dim = geom ? geom->dim : 0;
+    int rc = wd::analyze(h->S, n, colptr, rowidx, dim, geom ? geom->level : nullptr,
+                         geom ? geom->box_lo : nullptr, geom ? geom->box_side : nullptr,
+                         h->opt.nd_leaf, h->opt.relax_k, h->opt.relax_pct, msg);
+    if (rc) return fail(h, (wd_status)rc, msg);
+    wd::Symbolic &S = h->S;
+    const int ns = S.ns;
+    // per-supernode arrays
+    std::vector<int32_t> sk(ns), sm(ns);
+    std::vector<int64_t> foff(ns), woff(ns);
+    int64_t fo = 0, wo = 0;
+    int maxm = 0, maxk = 0;
+    for (int s = 0; s < ns; ++s) {
+        sk[s] = S.k(s);
+        sm[s] = S.m(s);
+        foff[s] = fo;
+        woff[s] = wo;
+        fo += (int64_t)sm[s] * sm[s];
+        wo += sm[s] - sk[s];
+        maxm = std::max(maxm, sm[s]);
+        maxk = std::max(maxk, sk[s]);
+    }
+    h->front_elems = (size_t)fo;
+    h->W_rows = wo;
+    // full CSR of P A P^T with the source index of every value
+    std::vector<int64_t> cptr(n + 1, 0), cdiag(n);
+    const int64_t nnzl = S.pcp[n];
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t e = S.pcp[j]; e < S.pcp[j + 1]; ++e) {
+            ++cptr[S.prow[e] + 1];
+            if (S.prow[e] != j) ++cptr[j + 1];
+        }
+    for (int64_t i = 0; i < n; ++i) cptr[i + 1] += cptr[i];
+    const int64_t nnzf = cptr[n];
+    h->nnz_full = nnzf;
+    std::vector<int32_t> ccol(nnzf), csrc(nnzf);
+    {
+        std::vector<int64_t> fill(cptr.begin(), cptr.end() - 1);
+        // row i gets, in column order: entries (i, j<i) from lower columns j,
+        // then the diagonal and (i, j>i) from lower column i
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t e = S.pcp[j] + 1; e < S.pcp[j + 1]; ++e) {
+                const int32_t i = S.prow[e];
+                ccol[fill[i]] = (int32_t)j;
+                csrc[fill[i]++] = S.psrc[e];
+            }
+        for (int64_t j = 0; j < n; ++j) {
+            cdiag[j] = fill[j];
+            for (int64_t e = S.pcp[j]; e < S.pcp[j + 1]; ++e) {
+                ccol[fill[j]] = S.prow[e];
+                csrc[fill[j]++] = S.psrc[e];
+            }
+        }
+    }
+    build_factor_plan(S, h->fplan);
+    if (host_only) {
+        fill_info(h, nnzl, maxm, maxk, t0);
+        h->analyzed = true;
+        return WD_OK;
+    }
+    DevSym &d = h->dsym;
+    d.n = n;
+    d.ns = ns;
+    UP(S.sfirst, d.sfirst);
+    UP(sk, d.sk);
+    UP(sm, d.sm);
+    UP(foff, d.foff);
+    UP(S.srowptr, d.rowptr);
+    UP(S.srows, d.rows);
+    UP(S.child_ptr, d.child_ptr);
+    UP(S.children, d.children);
+    UP(S.mapoff, d.mapoff);
+    UP(S.relmap, d.relmap);
+    UP(S.pcp, d.pcp);
+    UP(S.alrow, d.alrow);
+    UP(cptr, d.csr_ptr);
+    UP(ccol, d.csr_col);
+    UP(cdiag, d.csr_diag);
+    UP(woff, d.woff);
+    UP(S.perm, d.perm);
+    {
+        const int32_t *p = nullptr;
+        UP(csrc, p);
+        h->d_csr_src = const_cast<int32_t *>(p);
+    }
+    CK(h->mem.alloc((void **)&h->d_csr_val, nnzf * sizeof(double)), "values alloc");
+    d.csr_val = h->d_csr_val;
+    CK(h->mem.alloc((void **)&h->d_status, sizeof(status_t)), "status alloc");
+    CK(h->mem.alloc((void **)&h->d_scalars, 1024 * sizeof(double)), "scalars alloc");
+    {
+        wd_status st = upload_plan(h, h->mem, h->fplan);
+        if (st != WD_OK) return st;
+    }
+    fill_info(h, nnzl, maxm, maxk, t0);
+    h->analyzed = true;
+    return WD_OK;
+}
+
+extern "C" wd_status wd_symbolic_export(wd_handle h, int32_t *perm, int32_t *parent,
+                                        int64_t *colcount, int32_t *super_first,
+                                        int64_t *super_rowptr, int32_t *super_rows) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!h->analyzed) return fail(h, WD_ERR_STATE, "not analyzed");
+    const wd::Symbolic &S = h->S;
+    if (perm) std::memcpy(perm, S.perm.data(), S.n * sizeof(int32_t));
+    if (parent) std::memcpy(parent, S.parent.data(), S.n * sizeof(int32_t));
+    if (colcount) std::memcpy(colcount, S.colcount.data(), S.n * sizeof(int64_t));
+    if (super_first) std::memcpy(super_first, S.sfirst.data(), S.sfirst.size() * sizeof(int32_t));
+    if (super_rowptr) std::memcpy(super_rowptr, S.srowptr.data(), S.srowptr.size() * sizeof(int64_t));
+    if (super_rows) std::memcpy(super_rows, S.srows.data(), S.srows.size() * sizeof(int32_t));
+    return WD_OK;
+}
+
+extern "C" wd_status wd_get_info(wd_handle h, wd_info *info) {
+    if (!h || !info) return WD_ERR_INVALID_ARG;
+    if (!h->analyzed) return fail(h, WD_ERR_STATE, "not analyzed");
+    *info = h->info;
+    return WD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// factor
+// ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// profiling: events around every launch of a plan, accumulated per kernel
+// ---------------------------------------------------------------------------
+static bool prof_begin(wd_handle h, size_t nlaunch) {
+    if (!h->opt.profile) return false;
+    while (h->prof_ev.size() < 2 * nlaunch) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return false;
+        h->prof_ev.push_back(e);
+    }
+    return true;
+}
+
+static void prof_end(wd_handle h, const Plan &p, size_t elem_size, const char *suffix) {
+    const size_t nl = p.launches.size();
+    if (nl == 0) return;
+    cudaEventSynchronize(h->prof_ev[2 * nl - 1]);
+    for (size_t i = 0; i < nl; ++i) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]);
+        const Launch &L = p.launches[i];
+        std::string name = std::string(kind_name(L.kind)) + suffix;
+        KStat *st = nullptr;
+        for (auto &kv : h->prof)
+            if (kv.first == name) st = &kv.second;
+        if (!st) {
+            h->prof.push_back({name, KStat()});
+            st = &h->prof.back().second;
+        }
+        st->launches += 1;
+        st->ms += ms;
+        st->flops += L.flops;
+        st->bytes += L.elems * (double)elem_size + L.bytes;
+    }
+}
+
+extern "C" wd_status wd_launch_count(wd_handle h, int64_t *count, int reset) {
+    if (!h || !count) return WD_ERR_INVALID_ARG;
+    *count = h->launches;
+    if (reset) h->launches = 0;
+    return WD_OK;
+}
+
+extern "C" wd_status wd_kernel_stats(wd_handle h, wd_kernel_stat *out, int32_t cap, int32_t *count,
+                                     int reset) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (count) *count = (int32_t)h->prof.size();
+    for (int32_t i = 0; out && i < cap && i < (int32_t)h->prof.size(); ++i) {
+        std::memset(&out[i], 0, sizeof(out[i]));
+        std::snprintf(out[i].name, sizeof(out[i].name), "%s", h->prof[i].first.c_str());
+        out[i].launches = h->prof[i].second.launches;
+        out[i].milliseconds = h->prof[i].second.ms;
+        out[i].flops = h->prof[i].second.flops;
+        out[i].bytes = h->prof[i].second.bytes;
+    }
+    if (reset) h->prof.clear();
+    return WD_OK;
+}
+
+template <class T>
+static void run_factor_plan(wd_handle h, cudaStream_t st) {
+    T *F = static_cast<T *>(h->d_front);
+    const DevSym &d = h->dsym;
+    const bool prof = prof_begin(h, h->fplan.launches.size());
+    size_t li = 0;
+    for (const Launch &L : h->fplan.launches) {
+        const int4 *it = h->fplan.d_items + L.off;
+        if (prof) cudaEventRecord(h->prof_ev[2 * li], st);
+        switch (L.kind) {
+            case K_INIT: wd::launch_front_init<T>(d, F, it, L.count, st); break;
+            case K_POTRF_FIRST: wd::launch_potrf_first<T>(d, F, it, L.count, h->d_status, st); break;
+            case K_PANEL: wd::launch_panel<T>(d, F, it, L.count, L.arg, st); break;
+            case K_UPDATE: wd::launch_update<T>(d, F, it, L.count, L.arg, h->d_status, st); break;
+        }
+        if (prof) cudaEventRecord(h->prof_ev[2 * li + 1], st);
+        ++li;
+    }
+    h->launches += (int64_t)h->fplan.launches.size();
+    if (prof) prof_end(h, h->fplan, sizeof(T), sizeof(T) == 8 ? "_fp64" : "_fp32");
+}
+
+extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_device,
+                               wd_precision prec, void *stream) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!h->analyzed || h->opt.symbolic_only)
+        return fail(h, WD_ERR_STATE, "wd_factor before wd_analyze (or on a host-only handle)");
+    if (!values || (prec != WD_FP64 && prec != WD_MIXED))
+        return fail(h, WD_ERR_INVALID_ARG, "null values or bad precision");
+    CK(cudaSetDevice(h->device), "set device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    h->factored = false;
+    const int64_t nnzl = h->S.pcp[h->S.n];
+    if (!h->d_front) {
+        CK(h->mem.alloc(&h->d_front, h->front_elems * sizeof(double)), "front pool alloc");
+    }
+    const double *vals = values;
+    if (!values_on_device) {
+        if (!h->d_values_stage)
+            CK(h->mem.alloc((void **)&h->d_values_stage, nnzl * sizeof(double)), "stage alloc");
+        CK(cudaMemcpyAsync(h->d_values_stage, values, nnzl * sizeof(double), cudaMemcpyHostToDevice, st),
+           "values H2D");
+        vals = h->d_values_stage;
+    }
+    wd::launch_gather_values(h->d_csr_src, vals, h->d_csr_val, h->nnz_full, st);
+    h->launches += 1;
+    CK(cudaMemsetAsync(h->d_status, 0xFF, sizeof(status_t), st), "status reset");
+    if (prec == WD_FP64) run_factor_plan<double>(h, st);
+    else run_factor_plan<float>(h, st);
+    wd::launch_norm_inf_rows(h->dsym, h->d_scalars, st);
+    h->launches += 1;
+    CK(cudaGetLastError(), "factor launch");
+    status_t status = 0;
+    CK(cudaMemcpyAsync(&status, h->d_status, sizeof(status_t), cudaMemcpyDeviceToHost, st), "status D2H");
+    CK(cudaMemcpyAsync(&h->normA, h->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, st), "norm D2H");
+    CK(cudaStreamSynchronize(st), "factor");
+    if (status != ~0ULL)
+        return fail(h, WD_ERR_NOT_SPD, "pivot not positive at column " + std::to_string(status),
+                    (int64_t)status);
+    h->prec = prec;
+    h->factored = true;
+    return WD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solve
+// ---------------------------------------------------------------------------
+static wd_status ensure_solve_ws(wd_handle h, int64_t nrhs) {
+    if (h->ws_cols >= nrhs) return WD_OK;
+    h->work.free_all();
+    h->d_Y = h->d_W = nullptr;
+    h->d_B = h->d_Bp = h->d_X = h->d_R = h->d_cm = nullptr;
+    h->splan = Plan();
+    h->aplan = Plan();
+    h->splan_nrhs = h->aplan_nrhs = -1;
+    const int64_t n = h->S.n;
+    CK(h->work.alloc(&h->d_Y, n * nrhs * sizeof(double)), "solve ws");
+    CK(h->work.alloc(&h->d_W, std::max<int64_t>(h->W_rows, 1) * nrhs * sizeof(double)), "solve ws");
+    CK(h->work.alloc((void **)&h->d_B, n * nrhs * sizeof(double)), "solve ws");
+    CK(h->work.alloc((void **)&h->d_Bp, n * nrhs * sizeof(double)), "solve ws");
+    CK(h->work.alloc((void **)&h->d_X, n * nrhs * sizeof(double)), "solve ws");
+    CK(h->work.alloc((void **)&h->d_R, n * nrhs * sizeof(double)), "solve ws");
+    CK(h->work.alloc((void **)&h->d_cm, 3 * nrhs * sizeof(double)), "solve ws");
+    h->ws_cols = nrhs;
+    return WD_OK;
+}
+
+template <class T>
+static void run_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st) {
+    const T *F = static_cast<const T *>(h->d_front);
+    T *W = static_cast<T *>(h->d_W);
+    const DevSym &d = h->dsym;
+    const bool prof = prof_begin(h, h->splan.launches.size());
+    size_t li = 0;
+    for (const Launch &L : h->splan.launches) {
+        const int4 *it = h->splan.d_items + L.off;
+        if (prof) cudaEventRecord(h->prof_ev[2 * li], st);
+        switch (L.kind) {
+            case K_FWD_GATHER: wd::launch_fwd_gather<T>(d, F, Y, W, it, L.count, nrhs, st); break;
+            case K_FWD_DIAG_FIRST: wd::launch_fwd_diag_first<T>(d, F, Y, it, L.count, nrhs, st); break;
+            case K_FWD_UPDATE: wd::launch_fwd_update<T>(d, F, Y, W, it, L.count, L.arg, nrhs, st); break;
+            case K_BWD_INIT: wd::launch_bwd_init<T>(d, F, Y, it, L.count, nrhs, st); break;
+            case K_BWD_STEP: wd::launch_bwd_step<T>(d, F, Y, it, L.count, L.arg, nrhs, st); break;
+        }
+        if (prof) cudaEventRecord(h->prof_ev[2 * li + 1], st);
+        ++li;
+    }
+    h->launches += (int64_t)h->splan.launches.size();
+    if (prof) prof_end(h, h->splan, sizeof(T), sizeof(T) == 8 ? "_fp64" : "_fp32");
+}
+
+static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cudaStream_t st,
+                                 double *be_max) {
+    const int64_t n = h->S.n;
+    wd::launch_spmv_residual(h->dsym, X, h->d_Bp, h->d_R, nrhs, st);
+    wd::launch_colmax3(h->d_R, X, h->d_Bp, n, nrhs, h->d_cm, st);
+    h->launches += 2;
+    std::vector<double> cm(3 * nrhs);
+    CK(cudaMemcpyAsync(cm.data(), h->d_cm, cm.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "be D2H");
+    CK(cudaStreamSynchronize(st), "backward error");
+    double mx = 0.0;
+    for (int64_t c = 0; c < nrhs; ++c) {
+        const double den = h->normA * cm[3 * c + 1] + cm[3 * c + 2];
+        const double be = den > 0 ? cm[3 * c] / den : 0.0;
+        mx = std::max(mx, be);
+    }
+    *be_max = mx;
+    return WD_OK;
+}
+
+extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb, int B_on_device,
+                              void *stream, wd_solve_info *info) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!h->factored) return fail(h, WD_ERR_STATE, "wd_solve before a successful wd_factor");
+    const int64_t n = h->S.n;
+    if (!B || nrhs < 0 || ldb < n || nrhs > (1 << 20)) return fail(h, WD_ERR_INVALID_ARG, "bad B");
+    if (info) {
+        info->iterations = 0;
+        info->backward_error = -1.0;
+    }
+    if (nrhs == 0) return WD_OK;
+    CK(cudaSetDevice(h->device), "set device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    wd_status s = ensure_solve_ws(h, nrhs);
+    if (s != WD_OK) return s;
+    if (h->splan_nrhs != nrhs) {
+        build_solve_plan(h->S, (int)nrhs, h->splan);
+        s = upload_plan(h, h->work, h->splan);
+        if (s != WD_OK) return s;
+        h->splan_nrhs = (int)nrhs;
+    }
+    double *Bd = B;
+    int64_t ld = ldb;
+    if (!B_on_device) {
+        CK(cudaMemcpy2DAsync(h->d_B, n * sizeof(double), B, ldb * sizeof(double), n * sizeof(double),
+                             nrhs, cudaMemcpyHostToDevice, st),
+           "B H2D");
+        Bd = h->d_B;
+        ld = n;
+    }
+    const int nr = (int)nrhs;
+    wd::launch_permute_in<double>(Bd, ld, h->d_Bp, h->dsym.perm, n, nrhs, st);
+    h->launches += 1;
+    if (h->prec == WD_FP64) {
+        double *Y = static_cast<double *>(h->d_Y);
+        CK(cudaMemcpyAsync(Y, h->d_Bp, n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy");
+        run_solve_plan<double>(h, Y, nr, st);
+        CK(cudaGetLastError(), "solve launch");
+        if (info) {
+            double be;
+            s = backward_errors(h, Y, nrhs, st, &be);
+            if (s != WD_OK) return s;
+            info->backward_error = be;
+        }
+        wd::launch_permute_out<double>(Y, Bd, ld, h->dsym.perm, n, nrhs, st);
+        h->launches += 1;
+    } else {
+        float *Y = static_cast<float *>(h->d_Y);
+        wd::launch_cast<float>(h->d_Bp, Y, n * nrhs, st);
+        run_solve_plan<float>(h, Y, nr, st);
+        wd::launch_axpy_into<float>(h->d_X, Y, n * nrhs, 0, st);
+        h->launches += 2;
+        CK(cudaGetLastError(), "solve launch");
+        double be = 1.0;
+        int it = 0;
+        for (;;) {
+            s = backward_errors(h, h->d_X, nrhs, st, &be);
+            if (s != WD_OK) return s;
+            if (be <= h->opt.ir_tol || it >= h->opt.ir_max_iter) break;
+            wd::launch_cast<float>(h->d_R, Y, n * nrhs, st);
+            run_solve_plan<float>(h, Y, nr, st);
+            wd::launch_axpy_into<float>(h->d_X, Y, n * nrhs, 1, st);
+            h->launches += 2;
+            CK(cudaGetLastError(), "refinement launch");
+            ++it;
+        }
+        if (info) {
+            info->iterations = it;
+            info->backward_error = be;
+        }
+        wd::launch_permute_out<double>(h->d_X, Bd, ld, h->dsym.perm, n, nrhs, st);
+        h->launches += 1;
+        if (be > h->opt.ir_tol) {
+            if (!B_on_device)
+                cudaMemcpy2DAsync(B, ldb * sizeof(double), h->d_B, n * sizeof(double), n * sizeof(double),
+                                  nrhs, cudaMemcpyDeviceToHost, st);
+            cudaStreamSynchronize(st);
+            return fail(h, WD_ERR_NO_CONVERGENCE,
+                        "refinement stopped at backward error " + std::to_string(be) + " after " +
+                            std::to_string(it) + " steps");
+        }
+    }
+    if (!B_on_device)
+        CK(cudaMemcpy2DAsync(B, ldb * sizeof(double), h->d_B, n * sizeof(double), n * sizeof(double), nrhs,
+                             cudaMemcpyDeviceToHost, st),
+           "B D2H");
+    CK(cudaStreamSynchronize(st), "solve");
+    return WD_OK;
+}
+
+extern "C" wd_status wd_logdet(wd_handle h, double *out) {
+    if (!h || !out) return WD_ERR_INVALID_ARG;
+    if (!h->factored) return fail(h, WD_ERR_STATE, "wd_logdet before a successful wd_factor");
+    CK(cudaSetDevice(h->device), "set device");
+    const int nb = 256;
+    double *partial = h->d_scalars + 8;
+    if (h->prec == WD_FP64)
+        wd::launch_logdet_partial<double>(h->dsym, static_cast<const double *>(h->d_front), partial, nb, 0);
+    else
+        wd::launch_logdet_partial<float>(h->dsym, static_cast<const float *>(h->d_front), partial, nb, 0);
+    wd::launch_sum_final(partial, nb, h->d_scalars + 1, 0);
+    h->launches += 2;
+    CK(cudaGetLastError(), "logdet launch");
+    CK(cudaMemcpy(out, h->d_scalars + 1, sizeof(double), cudaMemcpyDeviceToHost), "logdet D2H");
+    return WD_OK;
+}
+
+extern "C" wd_status wd_apply_L(wd_handle h, const double *Z, double *S_out, int64_t nrhs, int64_t ld,
+                                int on_device, void *stream) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!h->factored) return fail(h, WD_ERR_STATE, "wd_apply_L before a successful wd_factor");
+    const int64_t n = h->S.n;
+    if (!Z || !S_out || nrhs < 0 || ld < n) return fail(h, WD_ERR_INVALID_ARG, "bad arguments");
+    if (nrhs == 0) return WD_OK;
+    CK(cudaSetDevice(h->device), "set device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    wd_status s = ensure_solve_ws(h, nrhs);
+    if (s != WD_OK) return s;
+    if (h->aplan_nrhs < 0) {
+        build_apply_plan(h->S, h->aplan);
+        s = upload_plan(h, h->work, h->aplan);
+        if (s != WD_OK) return s;
+        h->aplan_nrhs = 1;
+    }
+    const double *Zd = Z;
+    double *Sd = S_out;
+    if (!on_device) {
+        CK(cudaMemcpy2DAsync(h->d_B, n * sizeof(double), Z, ld * sizeof(double), n * sizeof(double), nrhs,
+                             cudaMemcpyHostToDevice, st),
+           "Z H2D");
+        Zd = h->d_B;
+        Sd = h->d_B;
+    }
+    const int64_t ldo = on_device ? ld : n;
+    // Z is indexed in factor order: copy it (column by column) into Bp with ld = n
+    CK(cudaMemcpy2DAsync(h->d_Bp, n * sizeof(double), Zd, (on_device ? ld : n) * sizeof(double),
+                         n * sizeof(double), nrhs, cudaMemcpyDeviceToDevice, st),
+       "Z copy");
+    const DevSym &d = h->dsym;
+    if (h->prec == WD_FP64) {
+        double *Out = static_cast<double *>(h->d_Y);
+        for (const Launch &L : h->aplan.launches)
+            wd::launch_apply_L<double>(d, static_cast<const double *>(h->d_front), h->d_Bp, Out,
+                                       static_cast<double *>(h->d_W), h->aplan.d_items + L.off, L.count,
+                                       (int)nrhs, st);
+        wd::launch_permute_out<double>(Out, Sd, ldo, d.perm, n, nrhs, st);
+        h->launches += (int64_t)h->aplan.launches.size() + 1;
+    } else {
+        float *Zf = reinterpret_cast<float *>(h->d_R);
+        wd::launch_cast<float>(h->d_Bp, Zf, n * nrhs, st);
+        float *Out = static_cast<float *>(h->d_Y);
+        for (const Launch &L : h->aplan.launches)
+            wd::launch_apply_L<float>(d, static_cast<const float *>(h->d_front), Zf, Out,
+                                      static_cast<float *>(h->d_W), h->aplan.d_items + L.off, L.count,
+                                      (int)nrhs, st);
+        wd::launch_permute_out<float>(Out, Sd, ldo, d.perm, n, nrhs, st);
+        h->launches += (int64_t)h->aplan.launches.size() + 2;
+    }
+    CK(cudaGetLastError(), "apply_L launch");
+    if (!on_device)
+        CK(cudaMemcpy2DAsync(S_out, ld * sizeof(double), h->d_B, n * sizeof(double), n * sizeof(double), nrhs,
+                             cudaMemcpyDeviceToHost, st),
+           "S D2H");
+    CK(cudaStreamSynchronize(st), "apply_L");
+    return WD_OK;
+}
+
+extern "C" wd_status wd_export_L(wd_handle h, double *panels) {
+    if (!h || !panels) return WD_ERR_INVALID_ARG;
+    if (!h->factored) return fail(h, WD_ERR_STATE, "wd_export_L before a successful wd_factor");
+    CK(cudaSetDevice(h->device), "set device");
+    const wd::Symbolic &S = h->S;
+    std::vector<int64_t> poff(S.ns);
+    int64_t tot = 0;
+    for (int s = 0; s < S.ns; ++s) {
+        poff[s] = tot;
+        tot += (int64_t)S.m(s) * S.k(s);
+    }
+    int64_t *d_poff = nullptr;
+    double *d_out = nullptr;
+    CK(cudaMalloc((void **)&d_poff, S.ns * sizeof(int64_t)), "export alloc");
+    if (cudaMalloc((void **)&d_out, tot * sizeof(double)) != cudaSuccess) {
+        cudaFree(d_poff);
+        return cuda_fail(h, cudaErrorMemoryAllocation, "export alloc");
+    }
+    cudaMemcpy(d_poff, poff.data(), S.ns * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (h->prec == WD_FP64)
+        wd::launch_export_panels<double>(h->dsym, static_cast<const double *>(h->d_front), d_out, d_poff, 0);
+    else
+        wd::launch_export_panels<float>(h->dsym, static_cast<const float *>(h->d_front), d_out, d_poff, 0);
+    cudaError_t e = cudaMemcpy(panels, d_out, tot * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d_out);
+    cudaFree(d_poff);
+    if (e != cudaSuccess) return cuda_fail(h, e, "export");
+    return WD_OK;
+}

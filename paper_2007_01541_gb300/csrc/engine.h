@@ -1,0 +1,96 @@
+// Device-side data of the multifrontal engine and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace wd {
+
+constexpr int NB = 64;        // pivot block width and Schur tile size
+constexpr int RB = 64;        // rows per panel (TRSM) block
+constexpr int SOLVE_RB = 64;  // rows per solve block
+
+// Device pointers of the analysis (all arrays are owned by the handle).
+struct DevSym {
+    int64_t n;
+    int32_t ns;
+    const int32_t *sfirst;      // ns+1: first column of each supernode
+    const int32_t *sk;          // ns: width k_s
+    const int32_t *sm;          // ns: front order m_s
+    const int64_t *foff;        // ns: offset of front s in the front pool
+    const int64_t *rowptr;      // ns+1: offset of the rows of s
+    const int32_t *rows;        // front rows (global permuted indices)
+    const int32_t *child_ptr;   // ns+1
+    const int32_t *children;
+    const int64_t *mapoff;      // ns: offset of child's gather map (length m_parent)
+    const int32_t *relmap;
+    const int64_t *pcp;         // n+1: lower CSC of P A P^T
+    const int32_t *alrow;       // local front row of each lower entry
+    const int64_t *csr_ptr;     // n+1: full CSR of P A P^T
+    const int32_t *csr_col;
+    const int64_t *csr_diag;    // n: position of the diagonal in each CSR row
+    const double *csr_val;      // FP64 values of P A P^T (full)
+    const int64_t *woff;        // ns: prefix sum of (m_s - k_s) (solve workspace)
+    const int32_t *perm;        // n
+};
+
+// status word of a factorization: smallest failing column (UINT64_MAX = none)
+using status_t = unsigned long long;
+
+// ---- factorization (front_kernels.cu) ------------------------------------
+template <class T>
+void launch_front_init(const DevSym &d, T *front, const int4 *items, int count, cudaStream_t st);
+template <class T>
+void launch_potrf_first(const DevSym &d, T *front, const int4 *items, int count,
+                        status_t *status, cudaStream_t st);
+template <class T>
+void launch_panel(const DevSym &d, T *front, const int4 *items, int count, int kb,
+                  cudaStream_t st);
+template <class T>
+void launch_update(const DevSym &d, T *front, const int4 *items, int count, int kb,
+                   status_t *status, cudaStream_t st);
+
+// ---- values, solves and reductions (solve_kernels.cu) ---------------------
+void launch_gather_values(const int32_t *csr_src, const double *values, double *csr_val,
+                          int64_t nnz, cudaStream_t st);
+template <class T>
+void launch_permute_in(const double *B, int64_t ldb, T *Y, const int32_t *perm, int64_t n,
+                       int64_t nrhs, cudaStream_t st);
+template <class T>
+void launch_permute_out(const T *Y, double *B, int64_t ldb, const int32_t *perm, int64_t n,
+                        int64_t nrhs, cudaStream_t st);
+template <class T>
+void launch_fwd_gather(const DevSym &d, const T *front, T *Y, T *W, const int4 *items,
+                       int count, int nrhs, cudaStream_t st);
+template <class T>
+void launch_fwd_diag_first(const DevSym &d, const T *front, T *Y, const int4 *items, int count,
+                           int nrhs, cudaStream_t st);
+template <class T>
+void launch_fwd_update(const DevSym &d, const T *front, T *Y, T *W, const int4 *items,
+                       int count, int kb, int nrhs, cudaStream_t st);
+template <class T>
+void launch_bwd_init(const DevSym &d, const T *front, T *Y, const int4 *items, int count,
+                     int nrhs, cudaStream_t st);
+template <class T>
+void launch_bwd_step(const DevSym &d, const T *front, T *Y, const int4 *items, int count,
+                     int ib, int nrhs, cudaStream_t st);
+template <class T>
+void launch_apply_L(const DevSym &d, const T *front, const T *Z, T *Out, T *W,
+                    const int4 *items, int count, int nrhs, cudaStream_t st);
+void launch_spmv_residual(const DevSym &d, const double *X, const double *Bp, double *R,
+                          int64_t nrhs, cudaStream_t st);
+void launch_norm_inf_rows(const DevSym &d, double *rowsum_max, cudaStream_t st);
+void launch_colmax3(const double *R, const double *X, const double *Bp, int64_t n,
+                    int64_t nrhs, double *out3, cudaStream_t st);
+template <class T>
+void launch_axpy_into(double *X, const T *D, int64_t count, int accumulate, cudaStream_t st);
+template <class T>
+void launch_cast(const double *src, T *dst, int64_t count, cudaStream_t st);
+template <class T>
+void launch_logdet_partial(const DevSym &d, const T *front, double *partial, int nblocks,
+                           cudaStream_t st);
+void launch_sum_final(const double *partial, int count, double *out, cudaStream_t st);
+template <class T>
+void launch_export_panels(const DevSym &d, const T *front, double *panels,
+                          const int64_t *poff, cudaStream_t st);
+
+}  // namespace wd

@@ -1,0 +1,637 @@
+// Supernodal triangular solves, P^T L z, FP64 residuals and reductions.
+//
+// The solve applies the exact inverse of the compressed matrix (Sections 1
+// and 5):  x = P^T L^-T L^-1 P b.  Both substitutions walk the supernodal
+// tree level by level; inside a supernode they proceed by pivot blocks of NB
+// columns.  Forward: every supernode produces an update vector u_s for the
+// rows below its diagonal block, which its parent gathers through the same
+// relative row maps as the factorization (no atomics).  Backward: every
+// supernode reads the already final x of its front rows.
+#include "engine.h"
+
+namespace wd {
+namespace {
+
+constexpr int THREADS = 256;
+constexpr int RG = 16;  // right-hand sides per block
+
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void permute_in_kernel(const double *__restrict__ B, int64_t ldb, T *__restrict__ Y,
+                                  const int32_t *__restrict__ perm, int64_t n, int64_t nrhs) {
+    const int64_t tot = n * nrhs;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t % n, c = t / n;
+        Y[t] = (T)B[perm[i] + c * ldb];
+    }
+}
+
+template <class T>
+__global__ void permute_out_kernel(const T *__restrict__ Y, double *__restrict__ B, int64_t ldb,
+                                   const int32_t *__restrict__ perm, int64_t n, int64_t nrhs) {
+    const int64_t tot = n * nrhs;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t % n, c = t / n;
+        B[perm[i] + c * ldb] = (double)Y[t];
+    }
+}
+
+__global__ void gather_values_kernel(const int32_t *__restrict__ src, const double *__restrict__ v,
+                                     double *__restrict__ out, int64_t nnz) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = v[src[e]];
+}
+
+// ---------------------------------------------------------------------------
+// forward: t = [b_J; 0] + sum over children of their update vectors
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(THREADS) fwd_gather_kernel(DevSym d, T *__restrict__ Y,
+                                                             T *__restrict__ W,
+                                                             const int4 *__restrict__ items,
+                                                             int nrhs) {
+    const int4 it = items[blockIdx.x];
+    const int s = it.x;
+    const int r = it.y * THREADS + threadIdx.x;
+    const int m = d.sm[s], k = d.sk[s];
+    if (r >= m) return;
+    const int64_t n = d.n;
+    const int f = d.sfirst[s];
+    const int cb = d.child_ptr[s], ce = d.child_ptr[s + 1];
+    T *Ws = W + d.woff[s] * nrhs;
+    for (int col = 0; col < nrhs; ++col) {
+        T t = (r < k) ? Y[f + r + col * n] : T(0);
+        for (int ci = cb; ci < ce; ++ci) {
+            const int c = d.children[ci];
+            const int ic = d.relmap[d.mapoff[c] + r];
+            if (ic >= 0) {
+                const int ldc = d.sm[c] - d.sk[c];
+                t += W[d.woff[c] * nrhs + (int64_t)col * ldc + ic];
+            }
+        }
+        if (r < k) Y[f + r + col * n] = t;
+        else Ws[(int64_t)col * (m - k) + (r - k)] = t;
+    }
+}
+
+// solve D y = t in place for rows [f+j0, f+j0+nb) of Y, rhs columns [c0, c0+nc)
+template <class T>
+__device__ void diag_forward(const T *F, int m, int j0, int nb, T *Y, int64_t n, int64_t rowbase,
+                             int c0, int nc, T *smem) {
+    T(*D)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
+    T(*Ts)[RG] = reinterpret_cast<T(*)[RG]>(smem + NB * (NB + 1));
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < nb * nb; idx += THREADS) {
+        const int r = idx % nb, c = idx / nb;
+        if (r >= c) D[r][c] = F[(int64_t)(j0 + c) * m + j0 + r];
+    }
+    for (int idx = tid; idx < nb * RG; idx += THREADS) {
+        const int r = idx % nb, c = idx / nb;
+        if (c < nc) Ts[r][c] = Y[rowbase + j0 + r + (int64_t)(c0 + c) * n];
+    }
+    __syncthreads();
+    const int c = tid % RG, rg = tid / RG;  // 16 row groups
+    for (int j = 0; j < nb; ++j) {
+        if (rg == 0 && c < nc) Ts[j][c] = Ts[j][c] / D[j][j];
+        __syncthreads();
+        if (c < nc) {
+            const T yj = Ts[j][c];
+            for (int r = j + 1 + rg; r < nb; r += THREADS / RG) Ts[r][c] -= D[r][j] * yj;
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < nb * RG; idx += THREADS) {
+        const int r = idx % nb, cc = idx / nb;
+        if (cc < nc) Y[rowbase + j0 + r + (int64_t)(c0 + cc) * n] = Ts[r][cc];
+    }
+    __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(THREADS) fwd_diag_first_kernel(DevSym d,
+                                                                 const T *__restrict__ front,
+                                                                 T *__restrict__ Y,
+                                                                 const int4 *__restrict__ items,
+                                                                 int nrhs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, c0 = it.y * RG;
+    const int m = d.sm[s], k = d.sk[s];
+    diag_forward<T>(front + d.foff[s], m, 0, min(NB, k), Y, d.n, d.sfirst[s], c0,
+                    min(RG, nrhs - c0), reinterpret_cast<T *>(smem_raw));
+}
+
+// rows [t0 + rb*SOLVE_RB, ...) -= L(rows, kb:kb+nb) y(kb:kb+nb); the block
+// holding the next diagonal block then solves it.
+template <class T>
+__global__ void __launch_bounds__(THREADS) fwd_update_kernel(DevSym d, const T *__restrict__ front,
+                                                             T *__restrict__ Y, T *__restrict__ W,
+                                                             const int4 *__restrict__ items,
+                                                             int kb, int nrhs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    T(*Ys)[RG] = reinterpret_cast<T(*)[RG]>(sm);
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, rb = it.y, c0 = it.z * RG;
+    const int m = d.sm[s], k = d.sk[s];
+    const int nb = min(NB, k - kb), t0 = kb + nb;
+    const int nc = min(RG, nrhs - c0);
+    const int64_t n = d.n;
+    const int f = d.sfirst[s];
+    const T *F = front + d.foff[s];
+    T *Ws = W + d.woff[s] * nrhs;
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < nb * RG; idx += THREADS) {
+        const int p = idx % nb, c = idx / nb;
+        Ys[p][c] = (c < nc) ? Y[f + kb + p + (int64_t)(c0 + c) * n] : T(0);
+    }
+    __syncthreads();
+    const int rl = tid % SOLVE_RB, cg = tid / SOLVE_RB;  // 4 column groups
+    const int r = t0 + rb * SOLVE_RB + rl;
+    if (r < m) {
+        T acc[RG / 4];
+#pragma unroll
+        for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
+        for (int p = 0; p < nb; ++p) {
+            const T l = F[(int64_t)(kb + p) * m + r];
+#pragma unroll
+            for (int u = 0; u < RG / 4; ++u) acc[u] += l * Ys[p][cg + 4 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < RG / 4; ++u) {
+            const int c = cg + 4 * u;
+            if (c < nc) {
+                if (r < k) Y[f + r + (int64_t)(c0 + c) * n] -= acc[u];
+                else Ws[(int64_t)(c0 + c) * (m - k) + (r - k)] -= acc[u];
+            }
+        }
+    }
+    if (rb == 0 && t0 < k) {
+        __syncthreads();
+        diag_forward<T>(F, m, t0, min(NB, k - t0), Y, n, f, c0, nc, sm);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// backward
+// ---------------------------------------------------------------------------
+// solve D^T x = y in place for rows [rowbase+j0, +nb), rhs columns [c0, c0+nc)
+template <class T>
+__device__ void diag_backward(const T *F, int m, int j0, int nb, T *Y, int64_t n, int64_t rowbase,
+                              int c0, int nc, T *smem) {
+    T(*D)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
+    T(*Ts)[RG] = reinterpret_cast<T(*)[RG]>(smem + NB * (NB + 1));
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < nb * nb; idx += THREADS) {
+        const int r = idx % nb, c = idx / nb;
+        if (r >= c) D[r][c] = F[(int64_t)(j0 + c) * m + j0 + r];
+    }
+    for (int idx = tid; idx < nb * RG; idx += THREADS) {
+        const int r = idx % nb, c = idx / nb;
+        if (c < nc) Ts[r][c] = Y[rowbase + j0 + r + (int64_t)(c0 + c) * n];
+    }
+    __syncthreads();
+    const int c = tid % RG, rg = tid / RG;
+    for (int j = nb - 1; j >= 0; --j) {
+        if (rg == 0 && c < nc) Ts[j][c] = Ts[j][c] / D[j][j];
+        __syncthreads();
+        if (c < nc) {
+            const T xj = Ts[j][c];
+            for (int r = rg; r < j; r += THREADS / RG) Ts[r][c] -= D[j][r] * xj;
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < nb * RG; idx += THREADS) {
+        const int r = idx % nb, cc = idx / nb;
+        if (cc < nc) Y[rowbase + j0 + r + (int64_t)(c0 + cc) * n] = Ts[r][cc];
+    }
+    __syncthreads();
+}
+
+// y(J block jb) -= L(R, jb)^T x(R) with x(R) read at the front rows beyond the
+// supernode; the last block of J is then solved.
+template <class T>
+__global__ void __launch_bounds__(THREADS) bwd_init_kernel(DevSym d, const T *__restrict__ front,
+                                                           T *__restrict__ Y,
+                                                           const int4 *__restrict__ items,
+                                                           int nrhs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    T(*Ls)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(sm);             // [64 rows][NB cols]
+    T(*Xs)[RG] = reinterpret_cast<T(*)[RG]>(sm + 64 * (NB + 1));      // [64 rows][RG]
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, jblk = it.y, c0 = it.z * RG;
+    const int m = d.sm[s], k = d.sk[s];
+    const int j0 = jblk * NB, nb = min(NB, k - j0);
+    const int nc = min(RG, nrhs - c0);
+    const int64_t n = d.n;
+    const int f = d.sfirst[s];
+    const T *F = front + d.foff[s];
+    const int32_t *rows = d.rows + d.rowptr[s];
+    const int tid = threadIdx.x;
+    const int cl = tid % NB, cg = tid / NB;  // column of the block, rhs group of 4
+    T acc[RG / 4];
+#pragma unroll
+    for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
+    for (int r0 = k; r0 < m; r0 += 64) {
+        const int nr = min(64, m - r0);
+        for (int idx = tid; idx < 64 * NB; idx += THREADS) {
+            const int rr = idx % 64, c = idx / 64;
+            Ls[rr][c] = (rr < nr && c < nb) ? F[(int64_t)(j0 + c) * m + r0 + rr] : T(0);
+        }
+        for (int idx = tid; idx < 64 * RG; idx += THREADS) {
+            const int rr = idx % 64, c = idx / 64;
+            Xs[rr][c] = (rr < nr && c < nc) ? Y[rows[r0 + rr] + (int64_t)(c0 + c) * n] : T(0);
+        }
+        __syncthreads();
+        for (int rr = 0; rr < nr; ++rr) {
+            const T l = Ls[rr][cl];
+#pragma unroll
+            for (int u = 0; u < RG / 4; ++u) acc[u] += l * Xs[rr][cg + 4 * u];
+        }
+        __syncthreads();
+    }
+    if (cl < nb) {
+#pragma unroll
+        for (int u = 0; u < RG / 4; ++u) {
+            const int c = cg + 4 * u;
+            if (c < nc) Y[f + j0 + cl + (int64_t)(c0 + c) * n] -= acc[u];
+        }
+    }
+    if (j0 + nb == k) {
+        __syncthreads();
+        diag_backward<T>(F, m, j0, nb, Y, n, f, c0, nc, sm);
+    }
+}
+
+// y(block jb) -= L(block ib+1, jb)^T x(block ib+1); block ib is then solved
+template <class T>
+__global__ void __launch_bounds__(THREADS) bwd_step_kernel(DevSym d, const T *__restrict__ front,
+                                                           T *__restrict__ Y,
+                                                           const int4 *__restrict__ items,
+                                                           int ib, int nrhs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    T(*Ls)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(sm);
+    T(*Xs)[RG] = reinterpret_cast<T(*)[RG]>(sm + NB * (NB + 1));
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, jblk = it.y, c0 = it.z * RG;
+    const int m = d.sm[s], k = d.sk[s];
+    const int j0 = jblk * NB, nbj = min(NB, k - j0);
+    const int r0 = (ib + 1) * NB, nr = min(NB, k - r0);
+    const int nc = min(RG, nrhs - c0);
+    const int64_t n = d.n;
+    const int f = d.sfirst[s];
+    const T *F = front + d.foff[s];
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < NB * NB; idx += THREADS) {
+        const int rr = idx % NB, c = idx / NB;
+        Ls[rr][c] = (rr < nr && c < nbj) ? F[(int64_t)(j0 + c) * m + r0 + rr] : T(0);
+    }
+    for (int idx = tid; idx < NB * RG; idx += THREADS) {
+        const int rr = idx % NB, c = idx / NB;
+        Xs[rr][c] = (rr < nr && c < nc) ? Y[f + r0 + rr + (int64_t)(c0 + c) * n] : T(0);
+    }
+    __syncthreads();
+    const int cl = tid % NB, cg = tid / NB;
+    if (cl < nbj) {
+        T acc[RG / 4];
+#pragma unroll
+        for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
+        for (int rr = 0; rr < nr; ++rr) {
+            const T l = Ls[rr][cl];
+#pragma unroll
+            for (int u = 0; u < RG / 4; ++u) acc[u] += l * Xs[rr][cg + 4 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < RG / 4; ++u) {
+            const int c = cg + 4 * u;
+            if (c < nc) Y[f + j0 + cl + (int64_t)(c0 + c) * n] -= acc[u];
+        }
+    }
+    if (jblk == ib) {
+        __syncthreads();
+        diag_backward<T>(F, m, j0, nbj, Y, n, f, c0, nc, sm);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// out = L z, multifrontal: rows of J go to Out, rows of R to the update
+// vector gathered by the parent.  One thread per front row.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(THREADS) apply_L_kernel(DevSym d, const T *__restrict__ front,
+                                                          const T *__restrict__ Z,
+                                                          T *__restrict__ Out, T *__restrict__ W,
+                                                          const int4 *__restrict__ items,
+                                                          int nrhs) {
+    const int4 it = items[blockIdx.x];
+    const int s = it.x;
+    const int r = it.y * THREADS + threadIdx.x;
+    const int m = d.sm[s], k = d.sk[s];
+    if (r >= m) return;
+    const int64_t n = d.n;
+    const int f = d.sfirst[s];
+    const T *F = front + d.foff[s];
+    const int cb = d.child_ptr[s], ce = d.child_ptr[s + 1];
+    const int pmax = min(r + 1, k);
+    for (int col = 0; col < nrhs; ++col) {
+        T t = T(0);
+        for (int ci = cb; ci < ce; ++ci) {
+            const int c = d.children[ci];
+            const int ic = d.relmap[d.mapoff[c] + r];
+            if (ic >= 0) t += W[d.woff[c] * nrhs + (int64_t)col * (d.sm[c] - d.sk[c]) + ic];
+        }
+        const T *z = Z + f + (int64_t)col * n;
+        for (int p = 0; p < pmax; ++p) t += F[(int64_t)p * m + r] * z[p];
+        if (r < k) Out[f + r + (int64_t)col * n] = t;
+        else W[d.woff[s] * nrhs + (int64_t)col * (m - k) + (r - k)] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 residual R = Bp - A_p X on the full CSR of P A P^T; one warp per row
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(THREADS) spmv_residual_kernel(DevSym d, const double *__restrict__ X,
+                                                                const double *__restrict__ Bp,
+                                                                double *__restrict__ R,
+                                                                int64_t nrhs) {
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= d.n) return;
+    const int64_t e0 = d.csr_ptr[row], e1 = d.csr_ptr[row + 1];
+    for (int64_t c = 0; c < nrhs; ++c) {
+        const double *x = X + c * d.n;
+        double acc = 0.0;
+        for (int64_t e = e0 + lane; e < e1; e += 32) acc += d.csr_val[e] * x[d.csr_col[e]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) R[row + c * d.n] = Bp[row + c * d.n] - acc;
+    }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
+    // non-negative doubles order like their bit patterns
+    atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void norm_inf_kernel(DevSym d, double *out) {
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= d.n) return;
+    double acc = 0.0;
+    for (int64_t e = d.csr_ptr[row] + lane; e < d.csr_ptr[row + 1]; e += 32) acc += fabs(d.csr_val[e]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) atomic_max_nonneg(out, acc);
+}
+
+__global__ void colmax3_kernel(const double *__restrict__ R, const double *__restrict__ X,
+                               const double *__restrict__ B, int64_t n, double *out) {
+    __shared__ double red[3][THREADS];
+    const int64_t c = blockIdx.x;
+    double a = 0, b = 0, e = 0;
+    for (int64_t i = threadIdx.x; i < n; i += THREADS) {
+        a = fmax(a, fabs(R[i + c * n]));
+        b = fmax(b, fabs(X[i + c * n]));
+        e = fmax(e, fabs(B[i + c * n]));
+    }
+    red[0][threadIdx.x] = a;
+    red[1][threadIdx.x] = b;
+    red[2][threadIdx.x] = e;
+    __syncthreads();
+    for (int o = THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int q = 0; q < 3; ++q)
+                red[q][threadIdx.x] = fmax(red[q][threadIdx.x], red[q][threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) out[3 * c + threadIdx.x] = red[threadIdx.x][0];
+}
+
+template <class T>
+__global__ void axpy_into_kernel(double *__restrict__ X, const T *__restrict__ D, int64_t cnt,
+                                 int acc) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt;
+         t += (int64_t)gridDim.x * blockDim.x)
+        X[t] = acc ? X[t] + (double)D[t] : (double)D[t];
+}
+
+template <class T>
+__global__ void cast_kernel(const double *__restrict__ src, T *__restrict__ dst, int64_t cnt) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt;
+         t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = (T)src[t];
+}
+
+// block-wise pairwise sums of 2 log L_jj (fixed order, deterministic)
+template <class T>
+__global__ void logdet_partial_kernel(DevSym d, const T *__restrict__ front, double *partial) {
+    __shared__ double red[THREADS];
+    double acc = 0.0;
+    for (int s = blockIdx.x; s < d.ns; s += gridDim.x) {
+        const int m = d.sm[s], k = d.sk[s];
+        const T *F = front + d.foff[s];
+        for (int j = threadIdx.x; j < k; j += THREADS) acc += 2.0 * log((double)F[(int64_t)j * m + j]);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void sum_final_kernel(const double *partial, int cnt, double *out) {
+    __shared__ double red[THREADS];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < cnt; i += THREADS) acc += partial[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+template <class T>
+__global__ void export_panels_kernel(DevSym d, const T *__restrict__ front,
+                                     double *__restrict__ out, const int64_t *__restrict__ poff) {
+    const int s = blockIdx.x;
+    const int m = d.sm[s], k = d.sk[s];
+    const T *F = front + d.foff[s];
+    double *P = out + poff[s];
+    for (int64_t idx = threadIdx.x; idx < (int64_t)m * k; idx += THREADS) {
+        const int r = (int)(idx % m), c = (int)(idx / m);
+        P[idx] = (r >= c) ? (double)F[(int64_t)c * m + r] : 0.0;
+    }
+}
+
+inline int grid_for(int64_t work) {
+    int64_t g = (work + THREADS - 1) / THREADS;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <class T>
+constexpr size_t diag_smem() { return sizeof(T) * (NB * (NB + 1) + NB * RG); }
+template <class T>
+constexpr size_t bwd_init_smem() { return sizeof(T) * (64 * (NB + 1) + 64 * RG); }
+
+template <class T>
+void set_attrs() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(fwd_diag_first_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)diag_smem<T>());
+    cudaFuncSetAttribute(fwd_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)diag_smem<T>());
+    cudaFuncSetAttribute(bwd_init_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwd_init_smem<T>());
+    cudaFuncSetAttribute(bwd_step_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)diag_smem<T>());
+    done = true;
+}
+
+}  // namespace
+
+void launch_gather_values(const int32_t *src, const double *values, double *out, int64_t nnz,
+                          cudaStream_t st) {
+    if (nnz <= 0) return;
+    gather_values_kernel<<<grid_for(nnz), THREADS, 0, st>>>(src, values, out, nnz);
+}
+
+template <class T>
+void launch_permute_in(const double *B, int64_t ldb, T *Y, const int32_t *perm, int64_t n,
+                       int64_t nrhs, cudaStream_t st) {
+    permute_in_kernel<T><<<grid_for(n * nrhs), THREADS, 0, st>>>(B, ldb, Y, perm, n, nrhs);
+}
+
+template <class T>
+void launch_permute_out(const T *Y, double *B, int64_t ldb, const int32_t *perm, int64_t n,
+                        int64_t nrhs, cudaStream_t st) {
+    permute_out_kernel<T><<<grid_for(n * nrhs), THREADS, 0, st>>>(Y, B, ldb, perm, n, nrhs);
+}
+
+template <class T>
+void launch_fwd_gather(const DevSym &d, const T *, T *Y, T *W, const int4 *items, int count,
+                       int nrhs, cudaStream_t st) {
+    if (count <= 0) return;
+    fwd_gather_kernel<T><<<count, THREADS, 0, st>>>(d, Y, W, items, nrhs);
+}
+
+template <class T>
+void launch_fwd_diag_first(const DevSym &d, const T *front, T *Y, const int4 *items, int count,
+                           int nrhs, cudaStream_t st) {
+    if (count <= 0) return;
+    set_attrs<T>();
+    fwd_diag_first_kernel<T><<<count, THREADS, diag_smem<T>(), st>>>(d, front, Y, items, nrhs);
+}
+
+template <class T>
+void launch_fwd_update(const DevSym &d, const T *front, T *Y, T *W, const int4 *items,
+                       int count, int kb, int nrhs, cudaStream_t st) {
+    if (count <= 0) return;
+    set_attrs<T>();
+    fwd_update_kernel<T><<<count, THREADS, diag_smem<T>(), st>>>(d, front, Y, W, items, kb, nrhs);
+}
+
+template <class T>
+void launch_bwd_init(const DevSym &d, const T *front, T *Y, const int4 *items, int count,
+                     int nrhs, cudaStream_t st) {
+    if (count <= 0) return;
+    set_attrs<T>();
+    bwd_init_kernel<T><<<count, THREADS, bwd_init_smem<T>(), st>>>(d, front, Y, items, nrhs);
+}
+
+template <class T>
+void launch_bwd_step(const DevSym &d, const T *front, T *Y, const int4 *items, int count,
+                     int ib, int nrhs, cudaStream_t st) {
+    if (count <= 0) return;
+    set_attrs<T>();
+    bwd_step_kernel<T><<<count, THREADS, diag_smem<T>(), st>>>(d, front, Y, items, ib, nrhs);
+}
+
+template <class T>
+void launch_apply_L(const DevSym &d, const T *front, const T *Z, T *Out, T *W,
+                    const int4 *items, int count, int nrhs, cudaStream_t st) {
+    if (count <= 0) return;
+    apply_L_kernel<T><<<count, THREADS, 0, st>>>(d, front, Z, Out, W, items, nrhs);
+}
+
+void launch_spmv_residual(const DevSym &d, const double *X, const double *Bp, double *R,
+                          int64_t nrhs, cudaStream_t st) {
+    const int64_t warps = d.n;
+    spmv_residual_kernel<<<(int)((warps * 32 + THREADS - 1) / THREADS), THREADS, 0, st>>>(d, X, Bp, R,
+                                                                                       nrhs);
+}
+
+void launch_norm_inf_rows(const DevSym &d, double *out, cudaStream_t st) {
+    cudaMemsetAsync(out, 0, sizeof(double), st);
+    norm_inf_kernel<<<(int)((d.n * 32 + THREADS - 1) / THREADS), THREADS, 0, st>>>(d, out);
+}
+
+void launch_colmax3(const double *R, const double *X, const double *Bp, int64_t n, int64_t nrhs,
+                    double *out3, cudaStream_t st) {
+    colmax3_kernel<<<(int)nrhs, THREADS, 0, st>>>(R, X, Bp, n, out3);
+}
+
+template <class T>
+void launch_axpy_into(double *X, const T *D, int64_t cnt, int acc, cudaStream_t st) {
+    axpy_into_kernel<T><<<grid_for(cnt), THREADS, 0, st>>>(X, D, cnt, acc);
+}
+
+template <class T>
+void launch_cast(const double *src, T *dst, int64_t cnt, cudaStream_t st) {
+    cast_kernel<T><<<grid_for(cnt), THREADS, 0, st>>>(src, dst, cnt);
+}
+
+template <class T>
+void launch_logdet_partial(const DevSym &d, const T *front, double *partial, int nblocks,
+                           cudaStream_t st) {
+    logdet_partial_kernel<T><<<nblocks, THREADS, 0, st>>>(d, front, partial);
+}
+
+void launch_sum_final(const double *partial, int cnt, double *out, cudaStream_t st) {
+    sum_final_kernel<<<1, THREADS, 0, st>>>(partial, cnt, out);
+}
+
+template <class T>
+void launch_export_panels(const DevSym &d, const T *front, double *panels, const int64_t *poff,
+                          cudaStream_t st) {
+    export_panels_kernel<T><<<d.ns, THREADS, 0, st>>>(d, front, panels, poff);
+}
+
+#define WD_INST(T)                                                                               \
+    template void launch_permute_in<T>(const double *, int64_t, T *, const int32_t *, int64_t,   \
+                                       int64_t, cudaStream_t);                                   \
+    template void launch_permute_out<T>(const T *, double *, int64_t, const int32_t *, int64_t,  \
+                                        int64_t, cudaStream_t);                                  \
+    template void launch_fwd_gather<T>(const DevSym &, const T *, T *, T *, const int4 *, int,   \
+                                       int, cudaStream_t);                                       \
+    template void launch_fwd_diag_first<T>(const DevSym &, const T *, T *, const int4 *, int,    \
+                                           int, cudaStream_t);                                   \
+    template void launch_fwd_update<T>(const DevSym &, const T *, T *, T *, const int4 *, int,   \
+                                       int, int, cudaStream_t);                                  \
+    template void launch_bwd_init<T>(const DevSym &, const T *, T *, const int4 *, int, int,     \
+                                     cudaStream_t);                                              \
+    template void launch_bwd_step<T>(const DevSym &, const T *, T *, const int4 *, int, int,     \
+                                     int, cudaStream_t);                                         \
+    template void launch_apply_L<T>(const DevSym &, const T *, const T *, T *, T *,              \
+                                    const int4 *, int, int, cudaStream_t);                       \
+    template void launch_axpy_into<T>(double *, const T *, int64_t, int, cudaStream_t);          \
+    template void launch_cast<T>(const double *, T *, int64_t, cudaStream_t);                    \
+    template void launch_logdet_partial<T>(const DevSym &, const T *, double *, int,             \
+                                           cudaStream_t);                                        \
+    template void launch_export_panels<T>(const DevSym &, const T *, double *, const int64_t *,  \
+                                          cudaStream_t);
+WD_INST(double)
+WD_INST(float)
+#undef WD_INST
+
+}  // namespace wd

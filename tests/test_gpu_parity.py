@@ -1,0 +1,204 @@
+"""CUDA path against the CPU oracle, through the C ABI (needs a GB300).
+
+Tolerances (derived from the arithmetic):
+  * FP64 factor: per column ||L_gpu(:,j) - L_or(:,j)||_2 <= 1e-10 ||L_or(:,j)||_2;
+    amalgamation zeros stay exactly 0.
+  * solves: normwise backward error <= 1e-12 per right-hand side, residual in
+    FP64 by the oracle's own sparse product.
+  * logdet: FP64 within 1e-12 relative; apply_L within 1e-12 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from wdgen import Kernel, compressed_pattern, compressed_values, haar_basis, rhs
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "1d_J10": (1, 10, Kernel("exponential", 0.2), 1e-2),
+    "2d_J5": (2, 5, Kernel("matern32", 0.1), 1e-3),
+    "2d_J6": (2, 6, Kernel("matern32", 0.1), 1e-3),
+    "2d_J7_exp": (2, 7, Kernel("exponential", 0.3), 1e-2),
+}
+_cache = {}
+
+
+def _case(name):
+    if name not in _cache:
+        dim, J, ker, nug = CASES[name]
+        b = haar_basis(dim, J)
+        cp, ri = compressed_pattern(b)
+        v = compressed_values(b, cp, ri, ker, nug)
+        o = oracle.Oracle(cp, ri, b)
+        assert o.factor(v) == 0
+        _cache[name] = (b, cp, ri, v, o)
+    return _cache[name]
+
+
+def _panel_mask_check(s, o):
+    """Stored entries outside L's structure (amalgamation zeros) are 0."""
+    sym = s.symbolic()
+    panels = s.export_L()
+    sf, srp, rows = sym["super_first"], sym["super_rowptr"], sym["super_rows"]
+    k = np.diff(sf).astype(np.int64)
+    m = np.diff(srp).astype(np.int64)
+    poff = np.concatenate([[0], np.cumsum(k * m)])
+    bad = 0.0
+    for sn in range(k.size):
+        r = rows[srp[sn]: srp[sn + 1]]
+        for c in range(k[sn]):
+            j = sf[sn] + c
+            struct = set(o.Li[o.Lp[j]: o.Lp[j + 1]].tolist())
+            col = panels[poff[sn] + c * m[sn]: poff[sn] + (c + 1) * m[sn]]
+            zero = np.array([ri not in struct for ri in r])
+            if zero.any():
+                bad = max(bad, float(np.abs(col[zero]).max()))
+    return bad
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_factor_fp64_entries(wdlib, cuda, name):
+    b, cp, ri, v, o = _case(name)
+    s = wdlib.Solver().analyze(cp, ri, b)
+    s.factor(v, "fp64")
+    L = s.L_csc_like(o.Lp, o.Li)
+    Lo = o.L_values()
+    for j in range(o.n):
+        a, e = o.Lp[j], o.Lp[j + 1]
+        assert np.linalg.norm(L[a:e] - Lo[a:e]) <= 1e-10 * np.linalg.norm(Lo[a:e]), j
+    if name in ("1d_J10", "2d_J5"):
+        assert _panel_mask_check(s, o) == 0.0
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("nrhs", [1, 5, 33])
+def test_solve_fp64(wdlib, cuda, name, nrhs):
+    b, cp, ri, v, o = _case(name)
+    s = wdlib.Solver().analyze(cp, ri, b).factor(v, "fp64")
+    B = rhs(o.n, nrhs, seed=nrhs)
+    X = s.solve(B)
+    be = oracle.backward_error(cp, ri, v, X, B)
+    assert be.max() <= 1e-12
+    Xo = o.solve(B)
+    assert np.abs(X - Xo).max() <= 1e-8 * np.abs(Xo).max()
+    assert 0 <= s.last_solve["backward_error"] <= 1e-12
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_solve_mixed_refined(wdlib, cuda, name):
+    b, cp, ri, v, o = _case(name)
+    s = wdlib.Solver().analyze(cp, ri, b).factor(v, "mixed")
+    B = rhs(o.n, 7, seed=11)
+    X = s.solve(B)
+    be = oracle.backward_error(cp, ri, v, X, B)
+    assert be.max() <= 1e-12
+    assert s.last_solve["iterations"] >= 1
+    assert s.last_solve["backward_error"] <= 1e-12
+
+
+def test_solve_device_tensor_in_place(wdlib, cuda):
+    torch = cuda
+    b, cp, ri, v, o = _case("2d_J6")
+    s = wdlib.Solver().analyze(cp, ri, b)
+    s.factor(torch.from_numpy(v).cuda(), "fp64")
+    B = rhs(o.n, 4, seed=5)
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda().T   # column-major view
+    s.solve(Bt)
+    torch.cuda.synchronize()
+    X = Bt.cpu().numpy()
+    assert oracle.backward_error(cp, ri, v, X, B).max() <= 1e-12
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_logdet(wdlib, cuda, name):
+    b, cp, ri, v, o = _case(name)
+    s = wdlib.Solver().analyze(cp, ri, b).factor(v, "fp64")
+    ref = o.logdet()
+    assert abs(s.logdet() - ref) <= 1e-12 * abs(ref)
+    s.factor(v, "mixed")
+    assert abs(s.logdet() - ref) <= 1e-5 * abs(ref)
+
+
+@pytest.mark.parametrize("name", ["1d_J10", "2d_J6"])
+def test_apply_L(wdlib, cuda, name):
+    b, cp, ri, v, o = _case(name)
+    s = wdlib.Solver().analyze(cp, ri, b).factor(v, "fp64")
+    Z = rhs(o.n, 9, seed=2)
+    S = s.apply_L(Z)
+    So = o.apply_L(Z)
+    assert np.abs(S - So).max() <= 1e-12 * np.abs(So).max()
+    s.factor(v, "mixed")
+    S32 = s.apply_L(Z)
+    assert np.abs(S32 - So).max() <= 1e-5 * np.abs(So).max()
+
+
+def _dense_lower(A):
+    n = A.shape[0]
+    cp, ri, vv = [0], [], []
+    for j in range(n):
+        rows = [i for i in range(j, n) if i == j or A[i, j] != 0.0]
+        ri += rows
+        vv += [A[i, j] for i in rows]
+        cp.append(len(ri))
+    return np.array(cp, np.int64), np.array(ri, np.int32), np.array(vv)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_not_spd_first_column(wdlib, cuda, prec):
+    n = 300
+    A = 4 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    A[120, 120] = -2.0
+    A[250, 250] = -2.0
+    cp, ri, v = _dense_lower(A)
+    o = oracle.Oracle(cp, ri)
+    col = -o.factor(v) - 1
+    s = wdlib.Solver().analyze(cp, ri)
+    with pytest.raises(wdlib.WdError) as e:
+        s.factor(v, prec)
+    assert e.value.status == wdlib.WD_ERR_NOT_SPD
+    assert e.value.column == col == 120
+    with pytest.raises(wdlib.WdError) as e2:
+        s.solve(np.ones(n))
+    assert e2.value.status == wdlib.WD_ERR_STATE
+
+
+@pytest.mark.parametrize("kind", ["n1", "diagonal", "tridiagonal", "dense200", "random"])
+def test_edge_structures(wdlib, cuda, kind):
+    rng = np.random.default_rng(7)
+    if kind == "n1":
+        A = np.array([[3.0]])
+    elif kind == "diagonal":
+        A = np.diag(rng.random(77) + 0.5)
+    elif kind == "tridiagonal":
+        n = 1000
+        A = 4 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    elif kind == "dense200":
+        M = rng.standard_normal((200, 200))
+        A = M @ M.T + 200 * np.eye(200)
+    else:
+        n = 700
+        M = (rng.random((n, n)) < 0.01) * rng.standard_normal((n, n))
+        A = np.tril(M, -1)
+        A = A + A.T + np.diag(np.abs(A).sum(1) + 1)
+    cp, ri, v = _dense_lower(A)
+    o = oracle.Oracle(cp, ri)
+    assert o.factor(v) == 0
+    s = wdlib.Solver().analyze(cp, ri).factor(v, "fp64")
+    L = s.L_csc_like(o.Lp, o.Li)
+    np.testing.assert_allclose(L, o.L_values(), rtol=0, atol=1e-12 * np.abs(o.L_values()).max())
+    B = rhs(A.shape[0], 3)
+    X = s.solve(B)
+    assert oracle.backward_error(cp, ri, v, X, B).max() <= 1e-12
+    assert abs(s.logdet() - o.logdet()) <= 1e-12 * max(1.0, abs(o.logdet()))
+
+
+def test_refactor_same_pattern_and_zero_rhs(wdlib, cuda):
+    b, cp, ri, v, o = _case("1d_J10")
+    s = wdlib.Solver().analyze(cp, ri, b)
+    for scale in (1.0, 2.0):
+        s.factor(v * scale, "fp64")
+        assert abs(s.logdet() - (o.logdet() + o.n * math.log(scale))) <= 1e-11 * abs(o.logdet())
+    assert s.solve(np.zeros((o.n, 0))).shape == (o.n, 0)

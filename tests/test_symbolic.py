@@ -1,0 +1,98 @@
+"""Host symbolic analysis of the library against the independent oracle
+(bit-exact), input validation, and the exported C ABI (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from wdgen import compressed_pattern, haar_basis
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _compare(wd, cp, ri, basis, **opt):
+    o = oracle.Oracle(cp, ri, basis, leaf=opt.get("nd_leaf", 64), relax_k=opt.get("relax_k", 16),
+                      relax_pct=opt.get("relax_pct", 10))
+    s = wd.Solver(symbolic_only=True, **opt).analyze(cp, ri, basis)
+    sy = s.symbolic()
+    for key in ("perm", "parent", "colcount", "super_first", "super_rowptr", "super_rows"):
+        np.testing.assert_array_equal(sy[key], getattr(o, key), err_msg=key)
+    inf = s.info()
+    assert inf["nnz_L"] == o.nnzL
+    assert inf["flops_factor"] == float(np.sum(o.colcount.astype(np.float64) ** 2))
+    return s, o
+
+
+@pytest.mark.parametrize("dim,J", [(1, 10), (2, 4), (2, 5), (2, 6), (2, 7)])
+def test_symbolic_bitexact(wdlib, dim, J):
+    b = haar_basis(dim, J)
+    cp, ri = compressed_pattern(b)
+    _compare(wdlib, cp, ri, b)
+
+
+@pytest.mark.parametrize("opt", [dict(nd_leaf=16), dict(relax_k=1, relax_pct=0),
+                                 dict(relax_k=64, relax_pct=30), dict(nd_leaf=200)])
+def test_symbolic_bitexact_options(wdlib, opt):
+    b = haar_basis(2, 6)
+    cp, ri = compressed_pattern(b)
+    _compare(wdlib, cp, ri, b, **opt)
+
+
+@pytest.mark.slow
+def test_symbolic_bitexact_full_2d(wdlib):
+    """The 2D 256 x 256 workload (N = 65,536), at full size."""
+    b = haar_basis(2, 8)
+    cp, ri = compressed_pattern(b)
+    s, o = _compare(wdlib, cp, ri, b)
+    assert s.info()["n"] == 65536
+
+
+def test_symbolic_no_geometry(wdlib):
+    rng = np.random.default_rng(3)
+    n = 300
+    M = np.tril((rng.random((n, n)) < 0.02), -1)
+    cp = [0]
+    ri = []
+    for j in range(n):
+        rows = [j] + [i for i in range(j + 1, n) if M[i, j]]
+        ri += rows
+        cp.append(len(ri))
+    _compare(wdlib, np.array(cp), np.array(ri), None)
+
+
+@pytest.mark.parametrize("bad", ["unsorted", "nodiag", "range", "dup"])
+def test_malformed_pattern(wdlib, bad):
+    cp = np.array([0, 3, 5, 6], np.int64)
+    ri = {"unsorted": [0, 2, 1, 1, 2, 2], "nodiag": [1, 2, 0, 1, 2, 2],
+          "range": [0, 1, 7, 1, 2, 2], "dup": [0, 1, 1, 1, 2, 2]}[bad]
+    s = wdlib.Solver(symbolic_only=True)
+    with pytest.raises(wdlib.WdError) as e:
+        s.analyze(cp, np.array(ri, np.int32))
+    assert e.value.status == wdlib.WD_ERR_PATTERN
+
+
+def test_state_errors_host_only(wdlib):
+    s = wdlib.Solver(symbolic_only=True)
+    with pytest.raises(wdlib.WdError) as e:
+        s.info()
+    assert e.value.status == wdlib.WD_ERR_STATE
+    b = haar_basis(1, 6)
+    cp, ri = compressed_pattern(b)
+    s.analyze(cp, ri, b)
+    with pytest.raises(wdlib.WdError) as e:
+        s.factor(np.ones(ri.size))
+    assert e.value.status == wdlib.WD_ERR_STATE
+
+
+def test_library_exports_every_declared_symbol(wdlib):
+    hdr = open(os.path.join(ROOT, "include", "wd.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = set(re.findall(r"\b(wd_[A-Za-z_0-9]+)\s*\(", hdr))
+    assert len(names) >= 12
+    lib = ctypes.CDLL(wdlib.library_path())
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(wdlib.EXPORTED) <= names

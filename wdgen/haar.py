@@ -268,6 +268,8 @@ def compressed_values(basis: Basis, colptr, rowidx, kernel: Kernel, nugget: floa
         X = _cell_centroids(dim, J)
     else:
         import torch as xp  # noqa: N812
+        if device.startswith("torch:"):       # torch on an explicit device, e.g. "torch:cpu"
+            device = device[len("torch:"):]
         X = _cell_centroids(dim, J, xp, device)
     shape = (n,) if dim == 1 else (n, n)
     # pass 1: Y1 = K_ss T^T  (rows: cells, cols: wavelets)
