@@ -268,11 +268,21 @@ def run_ours(args):
     Bw = torch.empty_like(B0)
     stream = torch.cuda.current_stream()
 
-    def step(prec):
+    phase = {"factor": 0.0, "solve": 0.0, "logdet": 0.0}
+
+    def step(prec, record=False):
+        t0 = time.perf_counter()
         s.factor(vals, prec)
+        t1 = time.perf_counter()
         Bw.copy_(B0)
         s.solve(Bw.T)
+        t2 = time.perf_counter()
         s.logdet()
+        t3 = time.perf_counter()
+        if record:
+            phase["factor"] += t1 - t0
+            phase["solve"] += t2 - t1
+            phase["logdet"] += t3 - t2
 
     def timed(prec, K, W):
         for _ in range(W):
@@ -283,14 +293,17 @@ def run_ours(args):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        for key in phase:
+            phase[key] = 0.0
         e0.record(stream)
         for _ in range(K):
-            step(prec)
+            step(prec, record=True)
         e1.record(stream)
         torch.cuda.synchronize()
         dist.barrier()
         ms = e0.elapsed_time(e1) / K
-        return dist.max(ms), s.kernel_stats(reset=True), s.launch_count(reset=True), dict(s.last_solve)
+        ph = {k: round(v / K * 1e3, 3) for k, v in phase.items()}
+        return dist.max(ms), s.kernel_stats(reset=True), s.launch_count(reset=True), dict(s.last_solve, phases_ms=ph)
 
     clocks = ClockSampler(gpu_id_for_smi())
     clocks.start()
@@ -301,7 +314,7 @@ def run_ours(args):
         ms64, kst64, _, si64 = timed("fp64", max(2, args.steps // 2), 2)
         res_fp64 = {"ms_per_step": ms64,
                     "tflops": dist.sum(flops_step) / (ms64 / 1e3) / 1e12,
-                    "backward_error": si64["backward_error"],
+                    "backward_error": si64["backward_error"], "phases_ms": si64["phases_ms"],
                     "top_kernels": _top(kst64, 3)}
     value = dist.sum(flops_step) / (ms_mixed / 1e3) / 1e12
 
@@ -380,10 +393,11 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (front pool %.1f GB)" % (info["front_bytes"] / 1e9)},
             "backward_error": solve_info["backward_error"], "ir_iterations": solve_info["iterations"],
+            "phases_ms": solve_info["phases_ms"],
             "fp64": res_fp64,
             "speedup_mixed_vs_fp64": (res_fp64["ms_per_step"] / ms_mixed) if res_fp64 else None,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "top_kernels": _top(kstats, 5),
+            "clocks": clk, "top_kernels": _top(kstats, 12),
             "analyze_s": info["analyze_seconds"],
         }
         print(json.dumps(line), flush=True)

@@ -24,8 +24,8 @@ constexpr int RG = 16;             // right-hand sides per solve block (solve_ke
 constexpr int ROWS_PER_CTA = 256;  // one thread per front row (gather / apply_L)
 
 enum LaunchKind {
-    K_INIT, K_POTRF_FIRST, K_PANEL, K_UPDATE,                  // factor
-    K_FWD_GATHER, K_FWD_DIAG_FIRST, K_FWD_UPDATE,              // forward solve
+    K_INIT, K_POTRF_FIRST, K_PANEL, K_UPDATE, K_SYRK,          // factor
+    K_FWD_GATHER, K_FWD_DIAG_FIRST, K_FWD_UPDATE, K_FWD_RGEMM, // forward solve
     K_BWD_INIT, K_BWD_STEP,                                    // backward solve
     K_APPLY_L
 };
@@ -42,8 +42,8 @@ struct Launch {
 
 const char *kind_name(int k) {
     static const char *names[] = {"front_init", "potrf_first", "panel_trsm", "schur_update",
-                                  "fwd_gather", "fwd_diag_first", "fwd_update", "bwd_init",
-                                  "bwd_step", "apply_L"};
+                                  "schur_syrk", "fwd_gather", "fwd_diag_first", "fwd_update",
+                                  "fwd_rgemm", "bwd_init", "bwd_step", "apply_L"};
     return names[k];
 }
 
@@ -56,6 +56,16 @@ struct Plan {
     std::vector<int4> items;
     std::vector<Launch> launches;
     int4 *d_items = nullptr;
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int64_t key = -1;
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        key = -1;
+    }
 };
 
 struct DevMem {
@@ -97,6 +107,10 @@ struct wd_ctx {
     double *d_values_stage = nullptr;
     void *d_front = nullptr;
     size_t front_elems = 0;
+    void *d_dinv = nullptr;        // inverses of the NB x NB diagonal blocks
+    size_t dinv_elems = 0;
+    cudaStream_t cap_stream = nullptr;
+    GraphCache g_factor, g_solve;
     status_t *d_status = nullptr;
     double *d_scalars = nullptr;   // [0] = ||A||_inf, [1] = logdet, [2..] partials
     Plan fplan;
@@ -198,6 +212,9 @@ void wd_destroy(wd_handle h) {
         cudaGetDevice(&prev);
         cudaSetDevice(h->device);
         for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+        h->g_factor.reset();
+        h->g_solve.reset();
+        if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
         h->work.free_all();
         h->mem.free_all();
         cudaSetDevice(prev);
@@ -243,6 +260,8 @@ static double lower_count(int64_t r0, int64_t r1, int64_t c0, int64_t c1) {
 }
 
 static void build_factor_plan(const wd::Symbolic &S, Plan &p) {
+    using wd::SCHUR_BM;
+    using wd::SCHUR_BN;
     p.items.clear();
     p.launches.clear();
     for (int l = 0; l < S.nlevels; ++l) {
@@ -270,8 +289,8 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p) {
             p.items.push_back({s, 0, 0, 0});
             kmax = std::max(kmax, S.k(s));
             const double nb = std::min(NB, S.k(s));
-            fl += nb * nb * nb / 3;
-            el += nb * (nb + 1);
+            fl += 2 * nb * nb * nb / 3;
+            el += nb * (nb + 1) + NB * NB;
         }
         add_launch(p, K_POTRF_FIRST, f0, 0, fl, el, 0);
         for (int kb = 0; kb < kmax; kb += NB) {
@@ -284,7 +303,7 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p) {
                 const int t0 = kb + nb;
                 for (int rb = 0; rb * RB < m - t0; ++rb) p.items.push_back({s, rb, 0, 0});
                 fl += (double)(m - t0) * nb * nb;
-                el += 2.0 * (m - t0) * nb + (double)nb * (nb + 1) / 2;
+                el += 2.0 * (m - t0) * nb + (double)NB * NB;
             }
             add_launch(p, K_PANEL, f0, kb, fl, el, 0);
             f0 = p.items.size();
@@ -294,19 +313,37 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p) {
                 if (k <= kb) continue;
                 const int nb = std::min(NB, k - kb);
                 const int t0 = kb + nb;
-                const int nt = (m - t0 + NB - 1) / NB;
-                for (int ti = 0; ti < nt; ++ti)
-                    for (int tj = 0; tj <= ti; ++tj) p.items.push_back({s, ti, tj, 0});
-                const double tri = (double)(m - t0) * (m - t0 + 1) / 2;
-                fl += 2.0 * nb * tri;
-                el += 2.0 * tri + (double)(m - t0) * nb;  // read+write trailing, read panel
-                if (t0 < k) {
-                    const double nb2 = std::min(NB, k - t0);
-                    fl += nb2 * nb2 * nb2 / 3;
-                }
+                if (t0 >= k) continue;
+                const int nrt = (m - t0 + SCHUR_BM - 1) / SCHUR_BM;
+                const int nct = (k - t0 + SCHUR_BN - 1) / SCHUR_BN;
+                for (int tj = 0; tj < nct; ++tj)
+                    for (int ti = (tj * SCHUR_BN) / SCHUR_BM; ti < nrt; ++ti)
+                        p.items.push_back({s, ti, tj, 0});
+                const double cw = k - t0, below = m - k;
+                const double ent = cw * (cw + 1) / 2 + below * cw;
+                fl += 2.0 * nb * ent;
+                el += 2.0 * ent + (double)(m - t0) * nb;
+                const double nb2 = std::min(NB, k - t0);
+                fl += 2 * nb2 * nb2 * nb2 / 3;
             }
             add_launch(p, K_UPDATE, f0, kb, fl, el, 0);
         }
+        f0 = p.items.size();
+        fl = el = 0;
+        for (int i = b; i < e; ++i) {
+            const int s = S.level_nodes[i], k = S.k(s), m = S.m(s);
+            if (m <= k) continue;
+            const int u = m - k;
+            const int nrt = (u + SCHUR_BM - 1) / SCHUR_BM;
+            const int nct = (u + SCHUR_BN - 1) / SCHUR_BN;
+            for (int tj = 0; tj < nct; ++tj)
+                for (int ti = (tj * SCHUR_BN) / SCHUR_BM; ti < nrt; ++ti)
+                    p.items.push_back({s, ti, tj, 0});
+            const double tri = (double)u * (u + 1) / 2;
+            fl += 2.0 * k * tri;
+            el += 2.0 * tri + (double)u * k;
+        }
+        add_launch(p, K_SYRK, f0, 0, fl, el, 0);
     }
 }
 
@@ -335,29 +372,39 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, Plan &p) {
             const double nb = std::min(NB, S.k(S.level_nodes[i]));
             for (int g = 0; g < ng; ++g) p.items.push_back({S.level_nodes[i], g, 0, 0});
             fl += nb * nb * R;
-            el += nb * (nb + 1) / 2 + 2 * nb * R;
+            el += (double)NB * NB + 2 * nb * R;
         }
         add_launch(p, K_FWD_DIAG_FIRST, f0, 0, fl, el, 0);
         for (int kb = 0; kb < kmax; kb += NB) {
             f0 = p.items.size();
             el = fl = 0;
             for (int i = b; i < e; ++i) {
-                const int s = S.level_nodes[i], k = S.k(s), m = S.m(s);
+                const int s = S.level_nodes[i], k = S.k(s);
                 if (k <= kb) continue;
                 const int nb = std::min(NB, k - kb);
                 const int t0 = kb + nb;
-                for (int rb = 0; rb * SOLVE_RB < m - t0; ++rb)
+                if (t0 >= k) continue;
+                for (int rb = 0; rb * SOLVE_RB < k - t0; ++rb)
                     for (int g = 0; g < ng; ++g) p.items.push_back({s, rb, g, 0});
-                fl += 2.0 * (m - t0) * nb * R;
-                el += (double)(m - t0) * nb + 2.0 * (m - t0) * R + nb * R;
-                if (t0 < k) {
-                    const double nb2 = std::min(NB, k - t0);
-                    fl += nb2 * nb2 * R;
-                    el += nb2 * (nb2 + 1) / 2;
-                }
+                fl += 2.0 * (k - t0) * nb * R;
+                el += (double)(k - t0) * nb + 2.0 * (k - t0) * R + nb * R;
+                const double nb2 = std::min(NB, k - t0);
+                fl += nb2 * nb2 * R;
+                el += (double)NB * NB;
             }
             add_launch(p, K_FWD_UPDATE, f0, kb, fl, el, 0);
         }
+        f0 = p.items.size();
+        el = fl = 0;
+        for (int i = b; i < e; ++i) {
+            const int s = S.level_nodes[i], k = S.k(s), m = S.m(s);
+            if (m <= k) continue;
+            for (int rb = 0; rb * SOLVE_RB < m - k; ++rb)
+                for (int g = 0; g < ng; ++g) p.items.push_back({s, rb, g, 0});
+            fl += 2.0 * (m - k) * k * R;
+            el += (double)(m - k) * k + 2.0 * (m - k) * R + k * R;
+        }
+        add_launch(p, K_FWD_RGEMM, f0, 0, fl, el, 0);
     }
     for (int l = S.nlevels - 1; l >= 0; --l) {
         const int b = S.level_ptr[l], e = S.level_ptr[l + 1];
@@ -375,7 +422,7 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, Plan &p) {
             el += (double)(m - k) * k + (m - k) * R + 2.0 * k * R;
             const double nbl = k - (nblk - 1) * NB;
             fl += nbl * nbl * R;
-            el += nbl * (nbl + 1) / 2;
+            el += (double)NB * NB;
         }
         add_launch(p, K_BWD_INIT, f0, 0, fl, el, 0);
         for (int ib = maxblk - 2; ib >= 0; --ib) {
@@ -390,7 +437,7 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, Plan &p) {
                     for (int g = 0; g < ng; ++g) p.items.push_back({s, jb, g, 0});
                 const double nr = std::min(NB, k - (ib + 1) * NB);
                 fl += 2.0 * nr * (ib + 1) * NB * R + (double)NB * NB * R;
-                el += nr * (ib + 1) * NB + nr * R + 2.0 * (ib + 1) * NB * R + NB * (NB + 1) / 2.0;
+                el += nr * (ib + 1) * NB + nr * R + 2.0 * (ib + 1) * NB * R + NB * NB;
             }
             add_launch(p, K_BWD_STEP, f0, ib, fl, el, 0);
         }
@@ -461,7 +508,12 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
     if (geom && (geom->patch || geom->dim < 0 || geom->dim > 3))
         return fail(h, WD_ERR_INVALID_ARG, "unsupported geometry");
     const bool host_only = h->opt.symbolic_only != 0;
-    if (!host_only) CK(cudaSetDevice(h->device), "set device");
+    if (!host_only) {
+        CK(cudaSetDevice(h->device), "set device");
+        wd::init_kernel_attributes();
+        if (!h->cap_stream)
+            CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "stream");
+    }
     auto t0 = std::chrono::steady_clock::now();
     h->analyzed = h->factored = false;
     if (!host_only) {
@@ -474,7 +526,10 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
     h->splan_nrhs = h->aplan_nrhs = -1;
     h->ws_cols = 0;
     h->d_front = nullptr;
+    h->d_dinv = nullptr;
     h->front_elems = 0;
+    h->g_factor.reset();
+    h->g_solve.reset();
     std::string msg;
     const int dim = geom ? geom->dim : 0;
     int rc = wd::analyze(h->S, n, colptr, rowidx, dim, geom ? geom->level : nullptr,
@@ -485,20 +540,23 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
     const int ns = S.ns;
     // per-supernode arrays
     std::vector<int32_t> sk(ns), sm(ns);
-    std::vector<int64_t> foff(ns), woff(ns);
-    int64_t fo = 0, wo = 0;
+    std::vector<int64_t> foff(ns), woff(ns), dioff(ns);
+    int64_t fo = 0, wo = 0, dio = 0;
     int maxm = 0, maxk = 0;
     for (int s = 0; s < ns; ++s) {
         sk[s] = S.k(s);
         sm[s] = S.m(s);
         foff[s] = fo;
         woff[s] = wo;
+        dioff[s] = dio;
         fo += (int64_t)sm[s] * sm[s];
         wo += sm[s] - sk[s];
+        dio += (int64_t)((sk[s] + NB - 1) / NB) * NB * NB;
         maxm = std::max(maxm, sm[s]);
         maxk = std::max(maxk, sk[s]);
     }
     h->front_elems = (size_t)fo;
+    h->dinv_elems = (size_t)dio;
     h->W_rows = wo;
     // full CSR of P A P^T with the source index of every value
     std::vector<int64_t> cptr(n + 1, 0), cdiag(n);
@@ -555,6 +613,7 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
     UP(ccol, d.csr_col);
     UP(cdiag, d.csr_diag);
     UP(woff, d.woff);
+    UP(dioff, d.dinvoff);
     UP(S.perm, d.perm);
     {
         const int32_t *p = nullptr;
@@ -659,25 +718,64 @@ extern "C" wd_status wd_kernel_stats(wd_handle h, wd_kernel_stat *out, int32_t c
 }
 
 template <class T>
-static void run_factor_plan(wd_handle h, cudaStream_t st) {
+static void enqueue_factor_plan(wd_handle h, cudaStream_t st, bool prof) {
     T *F = static_cast<T *>(h->d_front);
+    T *Dv = static_cast<T *>(h->d_dinv);
     const DevSym &d = h->dsym;
-    const bool prof = prof_begin(h, h->fplan.launches.size());
     size_t li = 0;
     for (const Launch &L : h->fplan.launches) {
         const int4 *it = h->fplan.d_items + L.off;
         if (prof) cudaEventRecord(h->prof_ev[2 * li], st);
         switch (L.kind) {
             case K_INIT: wd::launch_front_init<T>(d, F, it, L.count, st); break;
-            case K_POTRF_FIRST: wd::launch_potrf_first<T>(d, F, it, L.count, h->d_status, st); break;
-            case K_PANEL: wd::launch_panel<T>(d, F, it, L.count, L.arg, st); break;
-            case K_UPDATE: wd::launch_update<T>(d, F, it, L.count, L.arg, h->d_status, st); break;
+            case K_POTRF_FIRST: wd::launch_potrf_first<T>(d, F, Dv, it, L.count, h->d_status, st); break;
+            case K_PANEL: wd::launch_panel<T>(d, F, Dv, it, L.count, L.arg, st); break;
+            case K_UPDATE: wd::launch_schur<T>(d, F, Dv, it, L.count, L.arg, 0, h->d_status, st); break;
+            case K_SYRK: wd::launch_schur<T>(d, F, Dv, it, L.count, 0, 1, h->d_status, st); break;
         }
         if (prof) cudaEventRecord(h->prof_ev[2 * li + 1], st);
         ++li;
     }
+}
+
+// Run a launch sequence: captured once into a CUDA graph (keyed), replayed on
+// the caller's stream; or launched directly when graphs are disabled.
+template <class Body>
+static wd_status run_graph(wd_handle h, GraphCache &gc, int64_t key, cudaStream_t st, Body body) {
+    if (!h->opt.use_graphs) {
+        body(st);
+        CK(cudaGetLastError(), "launch");
+        return WD_OK;
+    }
+    if (gc.key != key || !gc.exec) {
+        gc.reset();
+        CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
+        body(h->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+        if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+        e = cudaGraphInstantiate(&gc.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            gc.exec = nullptr;
+            return cuda_fail(h, e, "graph instantiate");
+        }
+        gc.key = key;
+    }
+    CK(cudaGraphLaunch(gc.exec, st), "graph launch");
+    return WD_OK;
+}
+
+template <class T>
+static wd_status run_factor_plan(wd_handle h, cudaStream_t st) {
+    const bool prof = prof_begin(h, h->fplan.launches.size());
+    const int64_t key = (sizeof(T) == 8 ? 1 : 2) + (prof ? 10 : 0);
+    wd_status s = run_graph(h, h->g_factor, key, st,
+                            [&](cudaStream_t cs) { enqueue_factor_plan<T>(h, cs, prof); });
+    if (s != WD_OK) return s;
     h->launches += (int64_t)h->fplan.launches.size();
     if (prof) prof_end(h, h->fplan, sizeof(T), sizeof(T) == 8 ? "_fp64" : "_fp32");
+    return WD_OK;
 }
 
 extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_device,
@@ -693,6 +791,7 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
     const int64_t nnzl = h->S.pcp[h->S.n];
     if (!h->d_front) {
         CK(h->mem.alloc(&h->d_front, h->front_elems * sizeof(double)), "front pool alloc");
+        CK(h->mem.alloc(&h->d_dinv, h->dinv_elems * sizeof(double)), "inverse blocks alloc");
     }
     const double *vals = values;
     if (!values_on_device) {
@@ -705,8 +804,10 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
     wd::launch_gather_values(h->d_csr_src, vals, h->d_csr_val, h->nnz_full, st);
     h->launches += 1;
     CK(cudaMemsetAsync(h->d_status, 0xFF, sizeof(status_t), st), "status reset");
-    if (prec == WD_FP64) run_factor_plan<double>(h, st);
-    else run_factor_plan<float>(h, st);
+    {
+        wd_status fs = (prec == WD_FP64) ? run_factor_plan<double>(h, st) : run_factor_plan<float>(h, st);
+        if (fs != WD_OK) return fs;
+    }
     wd::launch_norm_inf_rows(h->dsym, h->d_scalars, st);
     h->launches += 1;
     CK(cudaGetLastError(), "factor launch");
@@ -733,6 +834,7 @@ static wd_status ensure_solve_ws(wd_handle h, int64_t nrhs) {
     h->splan = Plan();
     h->aplan = Plan();
     h->splan_nrhs = h->aplan_nrhs = -1;
+    h->g_solve.reset();
     const int64_t n = h->S.n;
     CK(h->work.alloc(&h->d_Y, n * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc(&h->d_W, std::max<int64_t>(h->W_rows, 1) * nrhs * sizeof(double)), "solve ws");
@@ -746,27 +848,38 @@ static wd_status ensure_solve_ws(wd_handle h, int64_t nrhs) {
 }
 
 template <class T>
-static void run_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st) {
+static void enqueue_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st, bool prof) {
     const T *F = static_cast<const T *>(h->d_front);
+    const T *Dv = static_cast<const T *>(h->d_dinv);
     T *W = static_cast<T *>(h->d_W);
     const DevSym &d = h->dsym;
-    const bool prof = prof_begin(h, h->splan.launches.size());
     size_t li = 0;
     for (const Launch &L : h->splan.launches) {
         const int4 *it = h->splan.d_items + L.off;
         if (prof) cudaEventRecord(h->prof_ev[2 * li], st);
         switch (L.kind) {
             case K_FWD_GATHER: wd::launch_fwd_gather<T>(d, F, Y, W, it, L.count, nrhs, st); break;
-            case K_FWD_DIAG_FIRST: wd::launch_fwd_diag_first<T>(d, F, Y, it, L.count, nrhs, st); break;
-            case K_FWD_UPDATE: wd::launch_fwd_update<T>(d, F, Y, W, it, L.count, L.arg, nrhs, st); break;
-            case K_BWD_INIT: wd::launch_bwd_init<T>(d, F, Y, it, L.count, nrhs, st); break;
-            case K_BWD_STEP: wd::launch_bwd_step<T>(d, F, Y, it, L.count, L.arg, nrhs, st); break;
+            case K_FWD_DIAG_FIRST: wd::launch_fwd_diag_first<T>(d, Dv, Y, it, L.count, nrhs, st); break;
+            case K_FWD_UPDATE: wd::launch_fwd_update<T>(d, F, Dv, Y, it, L.count, L.arg, nrhs, st); break;
+            case K_FWD_RGEMM: wd::launch_fwd_rgemm<T>(d, F, Y, W, it, L.count, nrhs, st); break;
+            case K_BWD_INIT: wd::launch_bwd_init<T>(d, F, Dv, Y, it, L.count, nrhs, st); break;
+            case K_BWD_STEP: wd::launch_bwd_step<T>(d, F, Dv, Y, it, L.count, L.arg, nrhs, st); break;
         }
         if (prof) cudaEventRecord(h->prof_ev[2 * li + 1], st);
         ++li;
     }
+}
+
+template <class T>
+static wd_status run_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st) {
+    const bool prof = prof_begin(h, h->splan.launches.size());
+    const int64_t key = ((int64_t)nrhs << 8) + (sizeof(T) == 8 ? 1 : 2) + (prof ? 10 : 0);
+    wd_status s = run_graph(h, h->g_solve, key, st,
+                            [&](cudaStream_t cs) { enqueue_solve_plan<T>(h, Y, nrhs, cs, prof); });
+    if (s != WD_OK) return s;
     h->launches += (int64_t)h->splan.launches.size();
     if (prof) prof_end(h, h->splan, sizeof(T), sizeof(T) == 8 ? "_fp64" : "_fp32");
+    return WD_OK;
 }
 
 static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cudaStream_t st,
@@ -808,6 +921,7 @@ extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb,
         s = upload_plan(h, h->work, h->splan);
         if (s != WD_OK) return s;
         h->splan_nrhs = (int)nrhs;
+        h->g_solve.reset();
     }
     double *Bd = B;
     int64_t ld = ldb;
@@ -824,8 +938,8 @@ extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb,
     if (h->prec == WD_FP64) {
         double *Y = static_cast<double *>(h->d_Y);
         CK(cudaMemcpyAsync(Y, h->d_Bp, n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy");
-        run_solve_plan<double>(h, Y, nr, st);
-        CK(cudaGetLastError(), "solve launch");
+        s = run_solve_plan<double>(h, Y, nr, st);
+        if (s != WD_OK) return s;
         if (info) {
             double be;
             s = backward_errors(h, Y, nrhs, st, &be);
@@ -837,7 +951,8 @@ extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb,
     } else {
         float *Y = static_cast<float *>(h->d_Y);
         wd::launch_cast<float>(h->d_Bp, Y, n * nrhs, st);
-        run_solve_plan<float>(h, Y, nr, st);
+        s = run_solve_plan<float>(h, Y, nr, st);
+        if (s != WD_OK) return s;
         wd::launch_axpy_into<float>(h->d_X, Y, n * nrhs, 0, st);
         h->launches += 2;
         CK(cudaGetLastError(), "solve launch");
@@ -848,7 +963,8 @@ extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb,
             if (s != WD_OK) return s;
             if (be <= h->opt.ir_tol || it >= h->opt.ir_max_iter) break;
             wd::launch_cast<float>(h->d_R, Y, n * nrhs, st);
-            run_solve_plan<float>(h, Y, nr, st);
+            s = run_solve_plan<float>(h, Y, nr, st);
+            if (s != WD_OK) return s;
             wd::launch_axpy_into<float>(h->d_X, Y, n * nrhs, 1, st);
             h->launches += 2;
             CK(cudaGetLastError(), "refinement launch");

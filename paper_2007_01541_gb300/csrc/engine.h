@@ -30,8 +30,18 @@ struct DevSym {
     const int64_t *csr_diag;    // n: position of the diagonal in each CSR row
     const double *csr_val;      // FP64 values of P A P^T (full)
     const int64_t *woff;        // ns: prefix sum of (m_s - k_s) (solve workspace)
+    const int64_t *dinvoff;     // ns: offset of the supernode's inverse diagonal blocks
     const int32_t *perm;        // n
 };
+
+// Set the dynamic shared-memory limits of all kernels (once per process,
+// before any stream capture).
+void init_front_attributes();
+void init_solve_attributes();
+inline void init_kernel_attributes() {
+    init_front_attributes();
+    init_solve_attributes();
+}
 
 // status word of a factorization: smallest failing column (UINT64_MAX = none)
 using status_t = unsigned long long;
@@ -40,14 +50,16 @@ using status_t = unsigned long long;
 template <class T>
 void launch_front_init(const DevSym &d, T *front, const int4 *items, int count, cudaStream_t st);
 template <class T>
-void launch_potrf_first(const DevSym &d, T *front, const int4 *items, int count,
+void launch_potrf_first(const DevSym &d, T *front, T *dinv, const int4 *items, int count,
                         status_t *status, cudaStream_t st);
 template <class T>
-void launch_panel(const DevSym &d, T *front, const int4 *items, int count, int kb,
+void launch_panel(const DevSym &d, T *front, const T *dinv, const int4 *items, int count, int kb,
                   cudaStream_t st);
+// mode 0: pivot-column update of step kb; mode 1: final update matrix (syrk)
 template <class T>
-void launch_update(const DevSym &d, T *front, const int4 *items, int count, int kb,
-                   status_t *status, cudaStream_t st);
+void launch_schur(const DevSym &d, T *front, T *dinv, const int4 *items, int count, int kb,
+                  int mode, status_t *status, cudaStream_t st);
+constexpr int SCHUR_BM = 128, SCHUR_BN = 64;
 
 // ---- values, solves and reductions (solve_kernels.cu) ---------------------
 void launch_gather_values(const int32_t *csr_src, const double *values, double *csr_val,
@@ -62,17 +74,20 @@ template <class T>
 void launch_fwd_gather(const DevSym &d, const T *front, T *Y, T *W, const int4 *items,
                        int count, int nrhs, cudaStream_t st);
 template <class T>
-void launch_fwd_diag_first(const DevSym &d, const T *front, T *Y, const int4 *items, int count,
+void launch_fwd_diag_first(const DevSym &d, const T *dinv, T *Y, const int4 *items, int count,
                            int nrhs, cudaStream_t st);
 template <class T>
-void launch_fwd_update(const DevSym &d, const T *front, T *Y, T *W, const int4 *items,
+void launch_fwd_update(const DevSym &d, const T *front, const T *dinv, T *Y, const int4 *items,
                        int count, int kb, int nrhs, cudaStream_t st);
 template <class T>
-void launch_bwd_init(const DevSym &d, const T *front, T *Y, const int4 *items, int count,
-                     int nrhs, cudaStream_t st);
+void launch_fwd_rgemm(const DevSym &d, const T *front, const T *Y, T *W, const int4 *items,
+                      int count, int nrhs, cudaStream_t st);
 template <class T>
-void launch_bwd_step(const DevSym &d, const T *front, T *Y, const int4 *items, int count,
-                     int ib, int nrhs, cudaStream_t st);
+void launch_bwd_init(const DevSym &d, const T *front, const T *dinv, T *Y, const int4 *items,
+                     int count, int nrhs, cudaStream_t st);
+template <class T>
+void launch_bwd_step(const DevSym &d, const T *front, const T *dinv, T *Y, const int4 *items,
+                     int count, int ib, int nrhs, cudaStream_t st);
 template <class T>
 void launch_apply_L(const DevSym &d, const T *front, const T *Z, T *Out, T *W,
                     const int4 *items, int count, int nrhs, cudaStream_t st);

@@ -11,11 +11,15 @@
 //   front_init   assemble A's entries and gather the children's update
 //                matrices through relative row maps (no atomics: every front
 //                entry is written by exactly one thread)
-//   potrf_first  Cholesky of the first NB x NB diagonal block
+//   potrf_first  Cholesky of the first NB x NB diagonal block and the
+//                inverse of that block (kept for the panel and the solves)
 //   per pivot block kb = 0, NB, 2NB, ... < k_s:
-//     panel      L21 := F21 L11^-T for the rows below the diagonal block
-//     update     trailing lower tiles -= L21 L21^T; the tile holding the next
-//                diagonal block also factors it (so no extra launch)
+//     panel      L21 := F21 L11^-T  as a product with the stored inverse
+//     update     pivot columns [kb+nb, k) of the trailing rows -= L21 L21^T;
+//                the tile holding the next diagonal block also factors and
+//                inverts it
+//   syrk         U = F22 - L(k:m, 0:k) L(k:m, 0:k)^T, one product with the
+//                whole pivot width as inner dimension
 #include "engine.h"
 
 #include <cstdio>
@@ -24,7 +28,9 @@ namespace wd {
 namespace {
 
 constexpr int THREADS = 256;
-constexpr int KC = 32;  // k-chunk of the Schur tile update
+constexpr int BM = 128;   // rows of a Schur tile
+constexpr int BN = 64;    // columns of a Schur tile
+constexpr int BK = 32;    // inner-dimension chunk
 
 template <class T>
 __device__ __forceinline__ T dev_sqrt(T x);
@@ -81,18 +87,25 @@ __global__ void __launch_bounds__(THREADS) front_init_kernel(DevSym d, T *__rest
 }
 
 // ---------------------------------------------------------------------------
-// Cholesky of an nb x nb diagonal block (nb <= NB) in shared memory.  A pivot
-// that is not positive records its global column in *status (smallest wins)
-// and is replaced by 1 so that the arithmetic stays finite.
-// Must be called by all THREADS threads of the block.
+// Cholesky of an nb x nb diagonal block (nb <= NB) in shared memory, then the
+// inverse of the factor, written zero-padded as an NB x NB lower-triangular
+// matrix (column-major) to Dinv.  A pivot that is not positive records its
+// global column in *status (smallest wins) and is replaced by 1 so that the
+// arithmetic stays finite.  Must be called by all THREADS threads.
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ void block_potrf(T *F, int ld, int nb, int64_t gcol0, status_t *status, T *smem) {
+__device__ void block_potrf_inv(T *F, int ld, int nb, int64_t gcol0, status_t *status, T *Dinv,
+                                T *smem) {
     T(*A)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
+    T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem + NB * (NB + 1));
     const int tid = threadIdx.x;
     for (int idx = tid; idx < nb * nb; idx += THREADS) {
         const int r = idx % nb, c = idx / nb;
         if (r >= c) A[r][c] = F[(int64_t)c * ld + r];
+    }
+    for (int idx = tid; idx < NB * NB; idx += THREADS) {
+        const int r = idx % NB, c = idx / NB;
+        X[r][c] = (r == c && r < nb) ? T(1) : T(0);
     }
     __syncthreads();
     const int r = tid % NB, cg = tid / NB;
@@ -118,28 +131,44 @@ __device__ void block_potrf(T *F, int ld, int nb, int64_t gcol0, status_t *statu
         const int rr = idx % nb, c = idx / nb;
         if (rr >= c) F[(int64_t)c * ld + rr] = A[rr][c];
     }
+    // X := A^-1 by forward substitution on all columns at once
+    for (int i = 0; i < nb; ++i) {
+        if (cg == 0 && r <= i) X[i][r] = X[i][r] / A[i][i];
+        __syncthreads();
+        if (r > i && r < nb) {
+            const T ari = A[r][i];
+            for (int c = cg; c <= i; c += THREADS / NB) X[r][c] -= ari * X[i][c];
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < NB * NB; idx += THREADS) {
+        const int rr = idx % NB, c = idx / NB;
+        Dinv[idx] = (rr >= c) ? X[rr][c] : T(0);
+    }
     __syncthreads();
 }
 
 template <class T>
 __global__ void __launch_bounds__(THREADS) potrf_first_kernel(DevSym d, T *__restrict__ front,
+                                                              T *__restrict__ dinv,
                                                               const int4 *__restrict__ items,
                                                               status_t *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int s = items[blockIdx.x].x;
     const int m = d.sm[s], k = d.sk[s];
-    block_potrf<T>(front + d.foff[s], m, min(NB, k), d.sfirst[s], status,
-                   reinterpret_cast<T *>(smem_raw));
+    block_potrf_inv<T>(front + d.foff[s], m, min(NB, k), d.sfirst[s], status,
+                       dinv + d.dinvoff[s], reinterpret_cast<T *>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
-// panel: rows [r0, r1) of columns [kb, kb+nb):  X := X L11^-T
+// panel: rows [r0, r0+RB) of columns [kb, kb+nb):  X := X Linv^T
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(THREADS) panel_kernel(DevSym d, T *__restrict__ front,
+                                                        const T *__restrict__ dinv,
                                                         const int4 *__restrict__ items, int kb) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T(*D)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);
+    T(*Di)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);
     T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw + sizeof(T) * NB * (NB + 1));
     const int4 it = items[blockIdx.x];
     const int s = it.x, rb = it.y;
@@ -147,76 +176,97 @@ __global__ void __launch_bounds__(THREADS) panel_kernel(DevSym d, T *__restrict_
     const int nb = min(NB, k - kb);
     const int r0 = kb + nb + rb * RB;
     const int nr = min(RB, m - r0);
-    const T *Fc = front + d.foff[s];
     T *F = front + d.foff[s];
+    const T *Dv = dinv + d.dinvoff[s] + (int64_t)(kb / NB) * NB * NB;
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < nb * nb; idx += THREADS) {
-        const int r = idx % nb, c = idx / nb;
-        if (r >= c) D[r][c] = Fc[(int64_t)(kb + c) * m + kb + r];
+    for (int idx = tid; idx < NB * NB; idx += THREADS) {
+        const int r = idx % NB, c = idx / NB;
+        Di[r][c] = Dv[idx];
     }
-    for (int idx = tid; idx < RB * nb; idx += THREADS) {
+    for (int idx = tid; idx < RB * NB; idx += THREADS) {
         const int r = idx % RB, c = idx / RB;
-        if (r < nr) X[r][c] = Fc[(int64_t)(kb + c) * m + r0 + r];
+        X[r][c] = (r < nr && c < nb) ? F[(int64_t)(kb + c) * m + r0 + r] : T(0);
     }
     __syncthreads();
+    // out[r][c] = sum_{p <= c} X[r][p] Di[c][p]; thread: row tid % 64, 16 cols
     const int r = tid % RB, cg = tid / RB;
-    for (int j = 0; j < nb; ++j) {
-        if (cg == 0 && r < nr) X[r][j] = X[r][j] / D[j][j];
-        __syncthreads();
-        if (r < nr) {
-            const T xrj = X[r][j];
-            for (int c = j + 1 + cg; c < nb; c += THREADS / RB) X[r][c] -= xrj * D[c][j];
-        }
-        __syncthreads();
+    T acc[NB / 4];
+#pragma unroll
+    for (int u = 0; u < NB / 4; ++u) acc[u] = T(0);
+    for (int p = 0; p < nb; ++p) {
+        const T x = X[r][p];
+#pragma unroll
+        for (int u = 0; u < NB / 4; ++u) acc[u] += x * Di[cg + 4 * u][p];
     }
-    for (int idx = tid; idx < RB * nb; idx += THREADS) {
-        const int rr = idx % RB, c = idx / RB;
-        if (rr < nr) F[(int64_t)(kb + c) * m + r0 + rr] = X[rr][c];
+    if (r < nr) {
+#pragma unroll
+        for (int u = 0; u < NB / 4; ++u) {
+            const int c = cg + 4 * u;
+            if (c < nb) F[(int64_t)(kb + c) * m + r0 + r] = acc[u];
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
-// Schur update of one NB x NB lower tile of the trailing matrix:
-//   C(rows I, cols J) -= L(I, kb:kb+nb) L(J, kb:kb+nb)^T
-// thread (tx, ty) owns rows tx + 16 i and columns ty + 16 j (i, j < 4).
+// Schur tile: C(rows [r0, r0+BM), cols [c0, c0+BN)) -= A(rows, ka:ka+K) A(cols, ka:ka+K)^T
+// restricted to r >= c, r < m, c < cmax.  thread (tx, ty): rows tx + 16 i,
+// columns ty + 16 j (i < 8, j < 4).
+//   mode 0 (step):  base = kb + nb, ka = kb, K = nb, cmax = k
+//   mode 1 (syrk):  base = k, ka = 0, K = k, cmax = m
+// In mode 0 the tile (0, 0) then factors and inverts the next diagonal block.
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(THREADS) update_kernel(DevSym d, T *__restrict__ front,
-                                                         const int4 *__restrict__ items, int kb,
-                                                         status_t *status) {
+__global__ void __launch_bounds__(THREADS) schur_kernel(DevSym d, T *__restrict__ front,
+                                                        T *__restrict__ dinv,
+                                                        const int4 *__restrict__ items, int kb,
+                                                        int mode, status_t *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T(*As)[NB] = reinterpret_cast<T(*)[NB]>(smem_raw);
-    T(*Bs)[NB] = reinterpret_cast<T(*)[NB]>(smem_raw + sizeof(T) * KC * NB);
+    T(*As)[BM] = reinterpret_cast<T(*)[BM]>(smem_raw);
+    T(*Bs)[BN] = reinterpret_cast<T(*)[BN]>(smem_raw + sizeof(T) * BK * BM);
     const int4 it = items[blockIdx.x];
     const int s = it.x, ti = it.y, tj = it.z;
     const int m = d.sm[s], k = d.sk[s];
-    const int nb = min(NB, k - kb);
-    const int t0 = kb + nb;
-    const int rbase = t0 + ti * NB, cbase = t0 + tj * NB;
+    int base, ka, K, cmax;
+    if (mode == 0) {
+        const int nb = min(NB, k - kb);
+        base = kb + nb;
+        ka = kb;
+        K = nb;
+        cmax = k;
+    } else {
+        base = k;
+        ka = 0;
+        K = k;
+        cmax = m;
+    }
+    const int r0 = base + ti * BM, c0 = base + tj * BN;
     T *F = front + d.foff[s];
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    T acc[4][4];
+    T acc[8][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-    for (int k0 = 0; k0 < nb; k0 += KC) {
-        const int kc = min(KC, nb - k0);
-        for (int idx = tid; idx < KC * NB; idx += THREADS) {
-            const int kk = idx / NB, rr = idx % NB;
-            const int64_t col = (int64_t)(kb + k0 + kk) * m;
-            As[kk][rr] = (kk < kc && rbase + rr < m) ? F[col + rbase + rr] : T(0);
-            Bs[kk][rr] = (kk < kc && cbase + rr < m) ? F[col + cbase + rr] : T(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        const int kc = min(BK, K - k0);
+        for (int idx = tid; idx < BK * BM; idx += THREADS) {
+            const int kk = idx / BM, rr = idx % BM;
+            As[kk][rr] = (kk < kc && r0 + rr < m) ? F[(int64_t)(ka + k0 + kk) * m + r0 + rr] : T(0);
+        }
+        for (int idx = tid; idx < BK * BN; idx += THREADS) {
+            const int kk = idx / BN, cc = idx % BN;
+            Bs[kk][cc] = (kk < kc && c0 + cc < cmax) ? F[(int64_t)(ka + k0 + kk) * m + c0 + cc] : T(0);
         }
         __syncthreads();
+#pragma unroll 4
         for (int kk = 0; kk < kc; ++kk) {
-            T a[4], b[4];
+            T a[8], b[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+            for (int i = 0; i < 8; ++i) a[i] = As[kk][tx + 16 * i];
 #pragma unroll
             for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
         }
@@ -224,40 +274,51 @@ __global__ void __launch_bounds__(THREADS) update_kernel(DevSym d, T *__restrict
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const int c = cbase + ty + 16 * j;
-        if (c >= m) continue;
+        const int c = c0 + ty + 16 * j;
+        if (c >= cmax) continue;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = rbase + tx + 16 * i;
+        for (int i = 0; i < 8; ++i) {
+            const int r = r0 + tx + 16 * i;
             if (r < m && r >= c) F[(int64_t)c * m + r] -= acc[i][j];
         }
     }
-    if (ti == 0 && tj == 0 && t0 < k) {
+    if (mode == 0 && ti == 0 && tj == 0 && base < k) {
         __syncthreads();
-        block_potrf<T>(F + (int64_t)t0 * m + t0, m, min(NB, k - t0), d.sfirst[s] + t0, status,
-                       reinterpret_cast<T *>(smem_raw));
+        block_potrf_inv<T>(F + (int64_t)base * m + base, m, min(NB, k - base), d.sfirst[s] + base,
+                           status, dinv + d.dinvoff[s] + (int64_t)(base / NB) * NB * NB,
+                           reinterpret_cast<T *>(smem_raw));
     }
 }
 
 template <class T>
-constexpr size_t potrf_smem() { return sizeof(T) * NB * (NB + 1); }
+constexpr size_t potrf_smem() { return 2 * sizeof(T) * NB * (NB + 1); }
 template <class T>
 constexpr size_t panel_smem() { return sizeof(T) * (NB + RB) * (NB + 1); }
 template <class T>
-constexpr size_t update_smem() {
-    return (2 * sizeof(T) * KC * NB > potrf_smem<T>()) ? 2 * sizeof(T) * KC * NB : potrf_smem<T>();
+constexpr size_t schur_smem() {
+    return (sizeof(T) * BK * (BM + BN) > potrf_smem<T>()) ? sizeof(T) * BK * (BM + BN)
+                                                          : potrf_smem<T>();
 }
 
 template <class T>
 void set_smem_attrs() {
     static bool done = false;  // per instantiation and process
     if (done) return;
+    cudaFuncSetAttribute(potrf_first_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)potrf_smem<T>());
     cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)panel_smem<T>());
+    cudaFuncSetAttribute(schur_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)schur_smem<T>());
     done = true;
 }
 
 }  // namespace
+
+void init_front_attributes() {
+    set_smem_attrs<double>();
+    set_smem_attrs<float>();
+}
 
 template <class T>
 void launch_front_init(const DevSym &d, T *front, const int4 *items, int count, cudaStream_t st) {
@@ -267,34 +328,37 @@ void launch_front_init(const DevSym &d, T *front, const int4 *items, int count, 
 }
 
 template <class T>
-void launch_potrf_first(const DevSym &d, T *front, const int4 *items, int count,
+void launch_potrf_first(const DevSym &d, T *front, T *dinv, const int4 *items, int count,
                         status_t *status, cudaStream_t st) {
     if (count <= 0) return;
-    potrf_first_kernel<T><<<count, THREADS, potrf_smem<T>(), st>>>(d, front, items, status);
+    set_smem_attrs<T>();
+    potrf_first_kernel<T><<<count, THREADS, potrf_smem<T>(), st>>>(d, front, dinv, items, status);
 }
 
 template <class T>
-void launch_panel(const DevSym &d, T *front, const int4 *items, int count, int kb,
+void launch_panel(const DevSym &d, T *front, const T *dinv, const int4 *items, int count, int kb,
                   cudaStream_t st) {
     if (count <= 0) return;
     set_smem_attrs<T>();
-    panel_kernel<T><<<count, THREADS, panel_smem<T>(), st>>>(d, front, items, kb);
+    panel_kernel<T><<<count, THREADS, panel_smem<T>(), st>>>(d, front, dinv, items, kb);
 }
 
 template <class T>
-void launch_update(const DevSym &d, T *front, const int4 *items, int count, int kb,
-                   status_t *status, cudaStream_t st) {
+void launch_schur(const DevSym &d, T *front, T *dinv, const int4 *items, int count, int kb,
+                  int mode, status_t *status, cudaStream_t st) {
     if (count <= 0) return;
-    update_kernel<T><<<count, THREADS, update_smem<T>(), st>>>(d, front, items, kb, status);
+    set_smem_attrs<T>();
+    schur_kernel<T><<<count, THREADS, schur_smem<T>(), st>>>(d, front, dinv, items, kb, mode, status);
 }
 
-#define WD_INST(T)                                                                              \
-    template void launch_front_init<T>(const DevSym &, T *, const int4 *, int, cudaStream_t);   \
-    template void launch_potrf_first<T>(const DevSym &, T *, const int4 *, int, status_t *,     \
-                                        cudaStream_t);                                          \
-    template void launch_panel<T>(const DevSym &, T *, const int4 *, int, int, cudaStream_t);   \
-    template void launch_update<T>(const DevSym &, T *, const int4 *, int, int, status_t *,     \
-                                   cudaStream_t);
+#define WD_INST(T)                                                                               \
+    template void launch_front_init<T>(const DevSym &, T *, const int4 *, int, cudaStream_t);    \
+    template void launch_potrf_first<T>(const DevSym &, T *, T *, const int4 *, int, status_t *, \
+                                        cudaStream_t);                                           \
+    template void launch_panel<T>(const DevSym &, T *, const T *, const int4 *, int, int,        \
+                                  cudaStream_t);                                                 \
+    template void launch_schur<T>(const DevSym &, T *, T *, const int4 *, int, int, int,         \
+                                  status_t *, cudaStream_t);
 WD_INST(double)
 WD_INST(float)
 #undef WD_INST

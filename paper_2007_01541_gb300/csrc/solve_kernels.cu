@@ -77,58 +77,64 @@ __global__ void __launch_bounds__(THREADS) fwd_gather_kernel(DevSym d, T *__rest
     }
 }
 
-// solve D y = t in place for rows [f+j0, f+j0+nb) of Y, rhs columns [c0, c0+nc)
+// Y rows [rowbase + j0, +nb), rhs [c0, c0+nc) := Dinv Y (trans = 0) or Dinv^T Y
+// (trans = 1), Dinv the stored NB x NB inverse of the diagonal block (zero
+// beyond nb).  Must be called by all THREADS threads.
 template <class T>
-__device__ void diag_forward(const T *F, int m, int j0, int nb, T *Y, int64_t n, int64_t rowbase,
-                             int c0, int nc, T *smem) {
-    T(*D)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
+__device__ void diag_apply(const T *Dv, int trans, int nb, T *Y, int64_t n, int64_t rowbase,
+                           int j0, int c0, int nc, T *smem) {
+    T(*Di)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
     T(*Ts)[RG] = reinterpret_cast<T(*)[RG]>(smem + NB * (NB + 1));
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < nb * nb; idx += THREADS) {
-        const int r = idx % nb, c = idx / nb;
-        if (r >= c) D[r][c] = F[(int64_t)(j0 + c) * m + j0 + r];
+    for (int idx = tid; idx < NB * NB; idx += THREADS) {
+        const int r = idx % NB, c = idx / NB;
+        if (trans) Di[c][r] = Dv[idx];
+        else Di[r][c] = Dv[idx];
     }
-    for (int idx = tid; idx < nb * RG; idx += THREADS) {
-        const int r = idx % nb, c = idx / nb;
-        if (c < nc) Ts[r][c] = Y[rowbase + j0 + r + (int64_t)(c0 + c) * n];
+    for (int idx = tid; idx < NB * RG; idx += THREADS) {
+        const int r = idx % NB, c = idx / NB;
+        Ts[r][c] = (r < nb && c < nc) ? Y[rowbase + j0 + r + (int64_t)(c0 + c) * n] : T(0);
     }
     __syncthreads();
-    const int c = tid % RG, rg = tid / RG;  // 16 row groups
-    for (int j = 0; j < nb; ++j) {
-        if (rg == 0 && c < nc) Ts[j][c] = Ts[j][c] / D[j][j];
-        __syncthreads();
-        if (c < nc) {
-            const T yj = Ts[j][c];
-            for (int r = j + 1 + rg; r < nb; r += THREADS / RG) Ts[r][c] -= D[r][j] * yj;
-        }
-        __syncthreads();
+    const int r = tid % NB, cg = tid / NB;
+    T acc[RG / 4];
+#pragma unroll
+    for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
+    for (int p = 0; p < nb; ++p) {
+        const T dv = Di[r][p];
+#pragma unroll
+        for (int u = 0; u < RG / 4; ++u) acc[u] += dv * Ts[p][cg + 4 * u];
     }
-    for (int idx = tid; idx < nb * RG; idx += THREADS) {
-        const int r = idx % nb, cc = idx / nb;
-        if (cc < nc) Y[rowbase + j0 + r + (int64_t)(c0 + cc) * n] = Ts[r][cc];
+    __syncthreads();
+    if (r < nb) {
+#pragma unroll
+        for (int u = 0; u < RG / 4; ++u) {
+            const int c = cg + 4 * u;
+            if (c < nc) Y[rowbase + j0 + r + (int64_t)(c0 + c) * n] = acc[u];
+        }
     }
     __syncthreads();
 }
 
 template <class T>
-__global__ void __launch_bounds__(THREADS) fwd_diag_first_kernel(DevSym d,
-                                                                 const T *__restrict__ front,
+__global__ void __launch_bounds__(THREADS) fwd_diag_first_kernel(DevSym d, const T *__restrict__ dinv,
                                                                  T *__restrict__ Y,
                                                                  const int4 *__restrict__ items,
                                                                  int nrhs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int4 it = items[blockIdx.x];
     const int s = it.x, c0 = it.y * RG;
-    const int m = d.sm[s], k = d.sk[s];
-    diag_forward<T>(front + d.foff[s], m, 0, min(NB, k), Y, d.n, d.sfirst[s], c0,
-                    min(RG, nrhs - c0), reinterpret_cast<T *>(smem_raw));
+    const int k = d.sk[s];
+    diag_apply<T>(dinv + d.dinvoff[s], 0, min(NB, k), Y, d.n, d.sfirst[s], 0, c0,
+                  min(RG, nrhs - c0), reinterpret_cast<T *>(smem_raw));
 }
 
-// rows [t0 + rb*SOLVE_RB, ...) -= L(rows, kb:kb+nb) y(kb:kb+nb); the block
-// holding the next diagonal block then solves it.
+// pivot rows [t0 + rb*SOLVE_RB, k) -= L(rows, kb:kb+nb) y(kb:kb+nb); the block
+// holding the next diagonal block then applies its inverse.
 template <class T>
 __global__ void __launch_bounds__(THREADS) fwd_update_kernel(DevSym d, const T *__restrict__ front,
-                                                             T *__restrict__ Y, T *__restrict__ W,
+                                                             const T *__restrict__ dinv,
+                                                             T *__restrict__ Y,
                                                              const int4 *__restrict__ items,
                                                              int kb, int nrhs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -142,16 +148,15 @@ __global__ void __launch_bounds__(THREADS) fwd_update_kernel(DevSym d, const T *
     const int64_t n = d.n;
     const int f = d.sfirst[s];
     const T *F = front + d.foff[s];
-    T *Ws = W + d.woff[s] * nrhs;
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < nb * RG; idx += THREADS) {
-        const int p = idx % nb, c = idx / nb;
-        Ys[p][c] = (c < nc) ? Y[f + kb + p + (int64_t)(c0 + c) * n] : T(0);
+    for (int idx = tid; idx < NB * RG; idx += THREADS) {
+        const int p = idx % NB, c = idx / NB;
+        Ys[p][c] = (p < nb && c < nc) ? Y[f + kb + p + (int64_t)(c0 + c) * n] : T(0);
     }
     __syncthreads();
     const int rl = tid % SOLVE_RB, cg = tid / SOLVE_RB;  // 4 column groups
     const int r = t0 + rb * SOLVE_RB + rl;
-    if (r < m) {
+    if (r < k) {
         T acc[RG / 4];
 #pragma unroll
         for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
@@ -163,58 +168,71 @@ __global__ void __launch_bounds__(THREADS) fwd_update_kernel(DevSym d, const T *
 #pragma unroll
         for (int u = 0; u < RG / 4; ++u) {
             const int c = cg + 4 * u;
-            if (c < nc) {
-                if (r < k) Y[f + r + (int64_t)(c0 + c) * n] -= acc[u];
-                else Ws[(int64_t)(c0 + c) * (m - k) + (r - k)] -= acc[u];
-            }
+            if (c < nc) Y[f + r + (int64_t)(c0 + c) * n] -= acc[u];
         }
     }
     if (rb == 0 && t0 < k) {
         __syncthreads();
-        diag_forward<T>(F, m, t0, min(NB, k - t0), Y, n, f, c0, nc, sm);
+        diag_apply<T>(dinv + d.dinvoff[s] + (int64_t)(t0 / NB) * NB * NB, 0, min(NB, k - t0), Y, n,
+                      f, t0, c0, nc, sm);
+    }
+}
+
+// rows of R: W_s -= L(R, 0:k) y(0:k), once the whole pivot block is solved
+template <class T>
+__global__ void __launch_bounds__(THREADS) fwd_rgemm_kernel(DevSym d, const T *__restrict__ front,
+                                                            const T *__restrict__ Y,
+                                                            T *__restrict__ W,
+                                                            const int4 *__restrict__ items,
+                                                            int nrhs) {
+    __shared__ T Ys[NB][RG];
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, rb = it.y, c0 = it.z * RG;
+    const int m = d.sm[s], k = d.sk[s];
+    const int nc = min(RG, nrhs - c0);
+    const int64_t n = d.n;
+    const int f = d.sfirst[s];
+    const T *F = front + d.foff[s];
+    T *Ws = W + d.woff[s] * nrhs;
+    const int tid = threadIdx.x;
+    const int rl = tid % SOLVE_RB, cg = tid / SOLVE_RB;
+    const int r = k + rb * SOLVE_RB + rl;
+    T acc[RG / 4];
+#pragma unroll
+    for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
+    for (int p0 = 0; p0 < k; p0 += NB) {
+        const int np = min(NB, k - p0);
+        __syncthreads();
+        for (int idx = tid; idx < NB * RG; idx += THREADS) {
+            const int p = idx % NB, c = idx / NB;
+            Ys[p][c] = (p < np && c < nc) ? Y[f + p0 + p + (int64_t)(c0 + c) * n] : T(0);
+        }
+        __syncthreads();
+        if (r < m) {
+            for (int p = 0; p < np; ++p) {
+                const T l = F[(int64_t)(p0 + p) * m + r];
+#pragma unroll
+                for (int u = 0; u < RG / 4; ++u) acc[u] += l * Ys[p][cg + 4 * u];
+            }
+        }
+    }
+    if (r < m) {
+#pragma unroll
+        for (int u = 0; u < RG / 4; ++u) {
+            const int c = cg + 4 * u;
+            if (c < nc) Ws[(int64_t)(c0 + c) * (m - k) + (r - k)] -= acc[u];
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
 // backward
 // ---------------------------------------------------------------------------
-// solve D^T x = y in place for rows [rowbase+j0, +nb), rhs columns [c0, c0+nc)
-template <class T>
-__device__ void diag_backward(const T *F, int m, int j0, int nb, T *Y, int64_t n, int64_t rowbase,
-                              int c0, int nc, T *smem) {
-    T(*D)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
-    T(*Ts)[RG] = reinterpret_cast<T(*)[RG]>(smem + NB * (NB + 1));
-    const int tid = threadIdx.x;
-    for (int idx = tid; idx < nb * nb; idx += THREADS) {
-        const int r = idx % nb, c = idx / nb;
-        if (r >= c) D[r][c] = F[(int64_t)(j0 + c) * m + j0 + r];
-    }
-    for (int idx = tid; idx < nb * RG; idx += THREADS) {
-        const int r = idx % nb, c = idx / nb;
-        if (c < nc) Ts[r][c] = Y[rowbase + j0 + r + (int64_t)(c0 + c) * n];
-    }
-    __syncthreads();
-    const int c = tid % RG, rg = tid / RG;
-    for (int j = nb - 1; j >= 0; --j) {
-        if (rg == 0 && c < nc) Ts[j][c] = Ts[j][c] / D[j][j];
-        __syncthreads();
-        if (c < nc) {
-            const T xj = Ts[j][c];
-            for (int r = rg; r < j; r += THREADS / RG) Ts[r][c] -= D[j][r] * xj;
-        }
-        __syncthreads();
-    }
-    for (int idx = tid; idx < nb * RG; idx += THREADS) {
-        const int r = idx % nb, cc = idx / nb;
-        if (cc < nc) Y[rowbase + j0 + r + (int64_t)(c0 + cc) * n] = Ts[r][cc];
-    }
-    __syncthreads();
-}
-
 // y(J block jb) -= L(R, jb)^T x(R) with x(R) read at the front rows beyond the
-// supernode; the last block of J is then solved.
+// supernode; the last block of J then applies its inverse.
 template <class T>
 __global__ void __launch_bounds__(THREADS) bwd_init_kernel(DevSym d, const T *__restrict__ front,
+                                                           const T *__restrict__ dinv,
                                                            T *__restrict__ Y,
                                                            const int4 *__restrict__ items,
                                                            int nrhs) {
@@ -263,13 +281,15 @@ __global__ void __launch_bounds__(THREADS) bwd_init_kernel(DevSym d, const T *__
     }
     if (j0 + nb == k) {
         __syncthreads();
-        diag_backward<T>(F, m, j0, nb, Y, n, f, c0, nc, sm);
+        diag_apply<T>(dinv + d.dinvoff[s] + (int64_t)jblk * NB * NB, 1, nb, Y, n, f, j0, c0, nc, sm);
     }
 }
 
-// y(block jb) -= L(block ib+1, jb)^T x(block ib+1); block ib is then solved
+// y(block jb) -= L(block ib+1, jb)^T x(block ib+1); block ib then applies
+// its inverse
 template <class T>
 __global__ void __launch_bounds__(THREADS) bwd_step_kernel(DevSym d, const T *__restrict__ front,
+                                                           const T *__restrict__ dinv,
                                                            T *__restrict__ Y,
                                                            const int4 *__restrict__ items,
                                                            int ib, int nrhs) {
@@ -314,7 +334,7 @@ __global__ void __launch_bounds__(THREADS) bwd_step_kernel(DevSym d, const T *__
     }
     if (jblk == ib) {
         __syncthreads();
-        diag_backward<T>(F, m, j0, nbj, Y, n, f, c0, nc, sm);
+        diag_apply<T>(dinv + d.dinvoff[s] + (int64_t)jblk * NB * NB, 1, nbj, Y, n, f, j0, c0, nc, sm);
     }
 }
 
@@ -500,6 +520,11 @@ void set_attrs() {
 
 }  // namespace
 
+void init_solve_attributes() {
+    set_attrs<double>();
+    set_attrs<float>();
+}
+
 void launch_gather_values(const int32_t *src, const double *values, double *out, int64_t nnz,
                           cudaStream_t st) {
     if (nnz <= 0) return;
@@ -526,35 +551,42 @@ void launch_fwd_gather(const DevSym &d, const T *, T *Y, T *W, const int4 *items
 }
 
 template <class T>
-void launch_fwd_diag_first(const DevSym &d, const T *front, T *Y, const int4 *items, int count,
+void launch_fwd_diag_first(const DevSym &d, const T *dinv, T *Y, const int4 *items, int count,
                            int nrhs, cudaStream_t st) {
     if (count <= 0) return;
     set_attrs<T>();
-    fwd_diag_first_kernel<T><<<count, THREADS, diag_smem<T>(), st>>>(d, front, Y, items, nrhs);
+    fwd_diag_first_kernel<T><<<count, THREADS, diag_smem<T>(), st>>>(d, dinv, Y, items, nrhs);
 }
 
 template <class T>
-void launch_fwd_update(const DevSym &d, const T *front, T *Y, T *W, const int4 *items,
+void launch_fwd_update(const DevSym &d, const T *front, const T *dinv, T *Y, const int4 *items,
                        int count, int kb, int nrhs, cudaStream_t st) {
     if (count <= 0) return;
     set_attrs<T>();
-    fwd_update_kernel<T><<<count, THREADS, diag_smem<T>(), st>>>(d, front, Y, W, items, kb, nrhs);
+    fwd_update_kernel<T><<<count, THREADS, diag_smem<T>(), st>>>(d, front, dinv, Y, items, kb, nrhs);
 }
 
 template <class T>
-void launch_bwd_init(const DevSym &d, const T *front, T *Y, const int4 *items, int count,
-                     int nrhs, cudaStream_t st) {
+void launch_fwd_rgemm(const DevSym &d, const T *front, const T *Y, T *W, const int4 *items,
+                      int count, int nrhs, cudaStream_t st) {
     if (count <= 0) return;
-    set_attrs<T>();
-    bwd_init_kernel<T><<<count, THREADS, bwd_init_smem<T>(), st>>>(d, front, Y, items, nrhs);
+    fwd_rgemm_kernel<T><<<count, THREADS, 0, st>>>(d, front, Y, W, items, nrhs);
 }
 
 template <class T>
-void launch_bwd_step(const DevSym &d, const T *front, T *Y, const int4 *items, int count,
-                     int ib, int nrhs, cudaStream_t st) {
+void launch_bwd_init(const DevSym &d, const T *front, const T *dinv, T *Y, const int4 *items,
+                     int count, int nrhs, cudaStream_t st) {
     if (count <= 0) return;
     set_attrs<T>();
-    bwd_step_kernel<T><<<count, THREADS, diag_smem<T>(), st>>>(d, front, Y, items, ib, nrhs);
+    bwd_init_kernel<T><<<count, THREADS, bwd_init_smem<T>(), st>>>(d, front, dinv, Y, items, nrhs);
+}
+
+template <class T>
+void launch_bwd_step(const DevSym &d, const T *front, const T *dinv, T *Y, const int4 *items,
+                     int count, int ib, int nrhs, cudaStream_t st) {
+    if (count <= 0) return;
+    set_attrs<T>();
+    bwd_step_kernel<T><<<count, THREADS, diag_smem<T>(), st>>>(d, front, dinv, Y, items, ib, nrhs);
 }
 
 template <class T>
@@ -616,12 +648,14 @@ void launch_export_panels(const DevSym &d, const T *front, double *panels, const
                                        int, cudaStream_t);                                       \
     template void launch_fwd_diag_first<T>(const DevSym &, const T *, T *, const int4 *, int,    \
                                            int, cudaStream_t);                                   \
-    template void launch_fwd_update<T>(const DevSym &, const T *, T *, T *, const int4 *, int,   \
-                                       int, int, cudaStream_t);                                  \
-    template void launch_bwd_init<T>(const DevSym &, const T *, T *, const int4 *, int, int,     \
-                                     cudaStream_t);                                              \
-    template void launch_bwd_step<T>(const DevSym &, const T *, T *, const int4 *, int, int,     \
-                                     int, cudaStream_t);                                         \
+    template void launch_fwd_update<T>(const DevSym &, const T *, const T *, T *, const int4 *,  \
+                                       int, int, int, cudaStream_t);                             \
+    template void launch_fwd_rgemm<T>(const DevSym &, const T *, const T *, T *, const int4 *,   \
+                                      int, int, cudaStream_t);                                   \
+    template void launch_bwd_init<T>(const DevSym &, const T *, const T *, T *, const int4 *,    \
+                                     int, int, cudaStream_t);                                    \
+    template void launch_bwd_step<T>(const DevSym &, const T *, const T *, T *, const int4 *,    \
+                                     int, int, int, cudaStream_t);                               \
     template void launch_apply_L<T>(const DevSym &, const T *, const T *, T *, T *,              \
                                     const int4 *, int, int, cudaStream_t);                       \
     template void launch_axpy_into<T>(double *, const T *, int64_t, int, cudaStream_t);          \

@@ -182,7 +182,8 @@ def test_edge_structures(wdlib, cuda, kind):
         n = 700
         M = (rng.random((n, n)) < 0.01) * rng.standard_normal((n, n))
         A = np.tril(M, -1)
-        A = A + A.T + np.diag(np.abs(A).sum(1) + 1)
+        A = A + A.T
+        A += np.diag(np.abs(A).sum(1) + 1)
     cp, ri, v = _dense_lower(A)
     o = oracle.Oracle(cp, ri)
     assert o.factor(v) == 0
