@@ -142,7 +142,7 @@ class Solver:
     """One sparse SPD system: analyze once, factor (re)peatedly, solve many."""
 
     def __init__(self, nd_leaf=64, relax_k=16, relax_pct=10, ir_max_iter=10, ir_tol=1e-12,
-                 symbolic_only=False, profile=False):
+                 symbolic_only=False, profile=False, use_graphs=True):
         self._lib = load()
         o = WdOptions()
         self._lib.wd_default_options(ctypes.byref(o))
@@ -150,6 +150,7 @@ class Solver:
         o.ir_max_iter, o.ir_tol = ir_max_iter, ir_tol
         o.symbolic_only = 1 if symbolic_only else 0
         o.profile = 1 if profile else 0
+        o.use_graphs = 1 if use_graphs else 0
         self._h = ctypes.c_void_p()
         self._check(self._lib.wd_create(ctypes.byref(self._h), ctypes.byref(o)))
         self.n = None

@@ -259,6 +259,10 @@ static double lower_count(int64_t r0, int64_t r1, int64_t c0, int64_t c1) {
     return cnt;
 }
 
+static int kpad(int k) { return (k + 31) / 32 * 32; }
+// rows of a front: pivot rows, zero padding to a multiple of 32, rows below
+static int front_order(const wd::Symbolic &S, int s) { return kpad(S.k(s)) + S.m(s) - S.k(s); }
+
 static void build_factor_plan(const wd::Symbolic &S, Plan &p) {
     using wd::SCHUR_BM;
     using wd::SCHUR_BN;
@@ -271,7 +275,8 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p) {
         for (int i = b; i < e; ++i) {
             const int s = S.level_nodes[i];
             const double m = S.m(s);
-            for (int q = 0; q < S.m(s); ++q) p.items.push_back({s, q, 0, 0});
+            const int mp = front_order(S, s);
+            for (int q = 0; q < mp; ++q) p.items.push_back({s, q, 0, 0});
             el += m * (m + 1) / 2;  // every lower front entry written once
             for (int c = S.child_ptr[s]; c < S.child_ptr[s + 1]; ++c) {
                 const double u = S.m(S.children[c]) - S.k(S.children[c]);
@@ -301,7 +306,9 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p) {
                 if (k <= kb) continue;
                 const int nb = std::min(NB, k - kb);
                 const int t0 = kb + nb;
-                for (int rb = 0; rb * RB < m - t0; ++rb) p.items.push_back({s, rb, 0, 0});
+                const int mp = front_order(S, s);
+                const int rs = (t0 == k) ? kpad(k) : t0;
+                for (int rb = 0; rb * RB < mp - rs; ++rb) p.items.push_back({s, rb, 0, 0});
                 fl += (double)(m - t0) * nb * nb;
                 el += 2.0 * (m - t0) * nb + (double)NB * NB;
             }
@@ -314,7 +321,7 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p) {
                 const int nb = std::min(NB, k - kb);
                 const int t0 = kb + nb;
                 if (t0 >= k) continue;
-                const int nrt = (m - t0 + SCHUR_BM - 1) / SCHUR_BM;
+                const int nrt = (front_order(S, s) - t0 + SCHUR_BM - 1) / SCHUR_BM;
                 const int nct = (k - t0 + SCHUR_BN - 1) / SCHUR_BN;
                 for (int tj = 0; tj < nct; ++tj)
                     for (int ti = (tj * SCHUR_BN) / SCHUR_BM; ti < nrt; ++ti)
@@ -539,17 +546,20 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
     wd::Symbolic &S = h->S;
     const int ns = S.ns;
     // per-supernode arrays
-    std::vector<int32_t> sk(ns), sm(ns);
+    std::vector<int32_t> sk(ns), sm(ns), skp(ns), sld(ns);
     std::vector<int64_t> foff(ns), woff(ns), dioff(ns);
     int64_t fo = 0, wo = 0, dio = 0;
     int maxm = 0, maxk = 0;
     for (int s = 0; s < ns; ++s) {
         sk[s] = S.k(s);
         sm[s] = S.m(s);
+        skp[s] = (sk[s] + 31) / 32 * 32;
+        const int mp = skp[s] + sm[s] - sk[s];
+        sld[s] = (mp + 31) / 32 * 32;
         foff[s] = fo;
         woff[s] = wo;
         dioff[s] = dio;
-        fo += (int64_t)sm[s] * sm[s];
+        fo += (int64_t)sld[s] * mp;
         wo += sm[s] - sk[s];
         dio += (int64_t)((sk[s] + NB - 1) / NB) * NB * NB;
         maxm = std::max(maxm, sm[s]);
@@ -600,6 +610,8 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
     UP(S.sfirst, d.sfirst);
     UP(sk, d.sk);
     UP(sm, d.sm);
+    UP(skp, d.skp);
+    UP(sld, d.sld);
     UP(foff, d.foff);
     UP(S.srowptr, d.rowptr);
     UP(S.srows, d.rows);
@@ -608,7 +620,16 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
     UP(S.mapoff, d.mapoff);
     UP(S.relmap, d.relmap);
     UP(S.pcp, d.pcp);
-    UP(S.alrow, d.alrow);
+    {
+        std::vector<int32_t> afr(S.alrow.size());
+        for (int s = 0; s < ns; ++s)
+            for (int j = S.sfirst[s]; j < S.sfirst[s + 1]; ++j)
+                for (int64_t e = S.pcp[j]; e < S.pcp[j + 1]; ++e) {
+                    const int r = S.alrow[e];
+                    afr[e] = r < sk[s] ? r : r + skp[s] - sk[s];
+                }
+        UP(afr, d.alrow);
+    }
     UP(cptr, d.csr_ptr);
     UP(ccol, d.csr_col);
     UP(cdiag, d.csr_diag);
@@ -661,6 +682,15 @@ extern "C" wd_status wd_get_info(wd_handle h, wd_info *info) {
 // ---------------------------------------------------------------------------
 // profiling: events around every launch of a plan, accumulated per kernel
 // ---------------------------------------------------------------------------
+// inside a stream capture an event becomes a timing node of the graph only
+// with cudaEventRecordExternal; outside a capture the plain record is used
+static void record_event(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
+}
+
 static bool prof_begin(wd_handle h, size_t nlaunch) {
     if (!h->opt.profile) return false;
     while (h->prof_ev.size() < 2 * nlaunch) {
@@ -677,7 +707,10 @@ static void prof_end(wd_handle h, const Plan &p, size_t elem_size, const char *s
     cudaEventSynchronize(h->prof_ev[2 * nl - 1]);
     for (size_t i = 0; i < nl; ++i) {
         float ms = 0;
-        cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]);
+        if (cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]) != cudaSuccess) {
+            cudaGetLastError();  // a profiling failure must not poison later calls
+            ms = 0;
+        }
         const Launch &L = p.launches[i];
         std::string name = std::string(kind_name(L.kind)) + suffix;
         KStat *st = nullptr;
@@ -725,7 +758,7 @@ static void enqueue_factor_plan(wd_handle h, cudaStream_t st, bool prof) {
     size_t li = 0;
     for (const Launch &L : h->fplan.launches) {
         const int4 *it = h->fplan.d_items + L.off;
-        if (prof) cudaEventRecord(h->prof_ev[2 * li], st);
+        if (prof) record_event(h->prof_ev[2 * li], st);
         switch (L.kind) {
             case K_INIT: wd::launch_front_init<T>(d, F, it, L.count, st); break;
             case K_POTRF_FIRST: wd::launch_potrf_first<T>(d, F, Dv, it, L.count, h->d_status, st); break;
@@ -733,7 +766,7 @@ static void enqueue_factor_plan(wd_handle h, cudaStream_t st, bool prof) {
             case K_UPDATE: wd::launch_schur<T>(d, F, Dv, it, L.count, L.arg, 0, h->d_status, st); break;
             case K_SYRK: wd::launch_schur<T>(d, F, Dv, it, L.count, 0, 1, h->d_status, st); break;
         }
-        if (prof) cudaEventRecord(h->prof_ev[2 * li + 1], st);
+        if (prof) record_event(h->prof_ev[2 * li + 1], st);
         ++li;
     }
 }
@@ -792,6 +825,8 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
     if (!h->d_front) {
         CK(h->mem.alloc(&h->d_front, h->front_elems * sizeof(double)), "front pool alloc");
         CK(h->mem.alloc(&h->d_dinv, h->dinv_elems * sizeof(double)), "inverse blocks alloc");
+        // padding rows stay zero forever: no kernel writes them
+        CK(cudaMemsetAsync(h->d_front, 0, h->front_elems * sizeof(double), st), "front pool clear");
     }
     const double *vals = values;
     if (!values_on_device) {
@@ -856,7 +891,7 @@ static void enqueue_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st, boo
     size_t li = 0;
     for (const Launch &L : h->splan.launches) {
         const int4 *it = h->splan.d_items + L.off;
-        if (prof) cudaEventRecord(h->prof_ev[2 * li], st);
+        if (prof) record_event(h->prof_ev[2 * li], st);
         switch (L.kind) {
             case K_FWD_GATHER: wd::launch_fwd_gather<T>(d, F, Y, W, it, L.count, nrhs, st); break;
             case K_FWD_DIAG_FIRST: wd::launch_fwd_diag_first<T>(d, Dv, Y, it, L.count, nrhs, st); break;
@@ -865,7 +900,7 @@ static void enqueue_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st, boo
             case K_BWD_INIT: wd::launch_bwd_init<T>(d, F, Dv, Y, it, L.count, nrhs, st); break;
             case K_BWD_STEP: wd::launch_bwd_step<T>(d, F, Dv, Y, it, L.count, L.arg, nrhs, st); break;
         }
-        if (prof) cudaEventRecord(h->prof_ev[2 * li + 1], st);
+        if (prof) record_event(h->prof_ev[2 * li + 1], st);
         ++li;
     }
 }

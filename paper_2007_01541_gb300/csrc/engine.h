@@ -15,7 +15,9 @@ struct DevSym {
     int32_t ns;
     const int32_t *sfirst;      // ns+1: first column of each supernode
     const int32_t *sk;          // ns: width k_s
-    const int32_t *sm;          // ns: front order m_s
+    const int32_t *sm;          // ns: number of front rows m_s
+    const int32_t *skp;         // ns: k_s rounded up to 32 (first row of R in the front)
+    const int32_t *sld;         // ns: leading dimension of the front (multiple of 32)
     const int64_t *foff;        // ns: offset of front s in the front pool
     const int64_t *rowptr;      // ns+1: offset of the rows of s
     const int32_t *rows;        // front rows (global permuted indices)
@@ -24,7 +26,7 @@ struct DevSym {
     const int64_t *mapoff;      // ns: offset of child's gather map (length m_parent)
     const int32_t *relmap;
     const int64_t *pcp;         // n+1: lower CSC of P A P^T
-    const int32_t *alrow;       // local front row of each lower entry
+    const int32_t *alrow;       // front row of each lower entry in its supernode's front
     const int64_t *csr_ptr;     // n+1: full CSR of P A P^T
     const int32_t *csr_col;
     const int64_t *csr_diag;    // n: position of the diagonal in each CSR row

@@ -1,11 +1,16 @@
 // Multifrontal numeric factorization kernels (FP64 and FP32 fronts).
 //
-// Each supernode s owns a dense front F_s of order m_s (column-major, lower
-// triangle used).  Its first k_s columns become the supernode's columns of L;
-// its trailing block becomes the update matrix U_s = F22 - L21 L21^T that the
+// Each supernode s owns a dense front F_s (column-major, lower triangle used)
+// whose rows are: its k_s pivot rows, zero padding up to kp_s = k_s rounded
+// up to 32, then the m_s - k_s rows below the supernode.  Its leading
+// dimension ld_s is a multiple of 32 elements, so every column and every tile
+// starting at a multiple of 32 rows is 128-byte aligned.  The first k_s
+// columns become the supernode's columns of L; the trailing block from
+// (kp_s, kp_s) on becomes the update matrix U_s = F22 - L21 L21^T that the
 // parent gathers (extend-add).  This is the block form of P A P^T under
-// nested dissection (Section 4): fronts of disjoint subtrees are independent,
-// so every level of the supernodal tree is processed by one launch per phase.
+// nested dissection (Section 4): fronts of disjoint subtrees are
+// independent, so every level of the supernodal tree is processed by one
+// launch per phase.
 //
 // Phases for the fronts of one level:
 //   front_init   assemble A's entries and gather the children's update
@@ -15,22 +20,23 @@
 //                inverse of that block (kept for the panel and the solves)
 //   per pivot block kb = 0, NB, 2NB, ... < k_s:
 //     panel      L21 := F21 L11^-T  as a product with the stored inverse
-//     update     pivot columns [kb+nb, k) of the trailing rows -= L21 L21^T;
+//     update     pivot columns [kb+NB, k) of the trailing rows -= L21 L21^T;
 //                the tile holding the next diagonal block also factors and
 //                inverts it
-//   syrk         U = F22 - L(k:m, 0:k) L(k:m, 0:k)^T, one product with the
-//                whole pivot width as inner dimension
+//   syrk         U = F22 - L(R, 0:k) L(R, 0:k)^T, one product with the whole
+//                pivot width as inner dimension
+// Tiles are staged into shared memory with cp.async (many loads in flight
+// per thread) and double buffered along the inner dimension.
+#include "dev_common.cuh"
 #include "engine.h"
-
-#include <cstdio>
 
 namespace wd {
 namespace {
 
 constexpr int THREADS = 256;
-constexpr int BM = 128;   // rows of a Schur tile
-constexpr int BN = 64;    // columns of a Schur tile
-constexpr int BK = 32;    // inner-dimension chunk
+constexpr int BM = SCHUR_BM;   // rows of a Schur tile
+constexpr int BN = SCHUR_BN;   // columns of a Schur tile
+constexpr int BK = 32;         // inner-dimension chunk
 
 template <class T>
 __device__ __forceinline__ T dev_sqrt(T x);
@@ -38,6 +44,19 @@ template <>
 __device__ __forceinline__ double dev_sqrt<double>(double x) { return sqrt(x); }
 template <>
 __device__ __forceinline__ float dev_sqrt<float>(float x) { return sqrtf(x); }
+
+struct Dims {
+    int k, m, kp, mp, ld;
+};
+__device__ __forceinline__ Dims dims(const DevSym &d, int s) {
+    Dims z;
+    z.k = d.sk[s];
+    z.m = d.sm[s];
+    z.kp = d.skp[s];
+    z.mp = z.kp + z.m - z.k;
+    z.ld = d.sld[s];
+    return z;
+}
 
 // ---------------------------------------------------------------------------
 // assemble + extend-add, one warp per front column
@@ -51,35 +70,40 @@ __global__ void __launch_bounds__(THREADS) front_init_kernel(DevSym d, T *__rest
     if (w >= count) return;
     const int4 it = items[w];
     const int s = it.x, q = it.y;
-    const int m = d.sm[s], k = d.sk[s];
-    T *F = front + d.foff[s] + (int64_t)q * m;
+    const Dims z = dims(d, s);
+    const int pad = z.kp - z.k;
+    const int qc = q < z.k ? q : (q < z.kp ? -1 : q - pad);  // local column
+    T *F = front + d.foff[s] + (int64_t)q * z.ld;
     const int cb = d.child_ptr[s], ce = d.child_ptr[s + 1];
-    for (int r0 = q; r0 < m; r0 += 128) {
+    for (int r0 = q; r0 < z.mp; r0 += 128) {
         T acc[4] = {T(0), T(0), T(0), T(0)};
-        for (int ci = cb; ci < ce; ++ci) {
-            const int c = d.children[ci];
-            const int32_t *map = d.relmap + d.mapoff[c];
-            const int ic = map[q];
-            if (ic < 0) continue;
-            const int mc = d.sm[c], kc = d.sk[c];
-            const T *U = front + d.foff[c] + (int64_t)(kc + ic) * mc + kc;
+        if (qc >= 0) {
+            for (int ci = cb; ci < ce; ++ci) {
+                const int c = d.children[ci];
+                const int32_t *map = d.relmap + d.mapoff[c];
+                const int ic = map[qc];
+                if (ic < 0) continue;
+                const int kpc = d.skp[c], ldc = d.sld[c];
+                const T *U = front + d.foff[c] + (int64_t)(kpc + ic) * ldc + kpc;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int r = r0 + u * 32 + lane;
-                if (r < m) {
-                    const int ir = map[r];
-                    if (ir >= 0) acc[u] += U[ir];
+                for (int u = 0; u < 4; ++u) {
+                    const int fr = r0 + u * 32 + lane;
+                    const int r = fr < z.k ? fr : (fr < z.kp ? -1 : fr - pad);
+                    if (fr < z.mp && r >= 0) {
+                        const int ir = map[r];
+                        if (ir >= 0) acc[u] += U[ir];
+                    }
                 }
             }
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int r = r0 + u * 32 + lane;
-            if (r < m) F[r] = acc[u];
+            const int fr = r0 + u * 32 + lane;
+            if (fr < z.mp) F[fr] = acc[u];
         }
     }
     __syncwarp();
-    if (q < k) {
+    if (q < z.k) {
         const int64_t j = d.sfirst[s] + q;
         const int64_t e0 = d.csr_diag[j], e1 = d.csr_ptr[j + 1], l0 = d.pcp[j];
         for (int64_t e = e0 + lane; e < e1; e += 32) F[d.alrow[l0 + (e - e0)]] += (T)d.csr_val[e];
@@ -153,66 +177,64 @@ __global__ void __launch_bounds__(THREADS) potrf_first_kernel(DevSym d, T *__res
                                                               T *__restrict__ dinv,
                                                               const int4 *__restrict__ items,
                                                               status_t *status) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int s = items[blockIdx.x].x;
-    const int m = d.sm[s], k = d.sk[s];
-    block_potrf_inv<T>(front + d.foff[s], m, min(NB, k), d.sfirst[s], status,
+    const Dims z = dims(d, s);
+    block_potrf_inv<T>(front + d.foff[s], z.ld, min(NB, z.k), d.sfirst[s], status,
                        dinv + d.dinvoff[s], reinterpret_cast<T *>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
-// panel: rows [r0, r0+RB) of columns [kb, kb+nb):  X := X Linv^T
+// panel: rows [r0, r0+RB) of columns [kb, kb+nb):  X := X Linv^T.  The rows
+// start at kb+NB, or at kp when kb is the last block (rows [k, kp) are zero
+// padding).
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(THREADS) panel_kernel(DevSym d, T *__restrict__ front,
                                                         const T *__restrict__ dinv,
                                                         const int4 *__restrict__ items, int kb) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T(*Di)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);
-    T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw + sizeof(T) * NB * (NB + 1));
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *Xs = reinterpret_cast<T *>(smem_raw);         // [p][r], ld RB
+    T *Ds = Xs + NB * RB;                            // [p][c] = Linv(c, p), ld NB
     const int4 it = items[blockIdx.x];
     const int s = it.x, rb = it.y;
-    const int m = d.sm[s], k = d.sk[s];
-    const int nb = min(NB, k - kb);
-    const int r0 = kb + nb + rb * RB;
-    const int nr = min(RB, m - r0);
+    const Dims z = dims(d, s);
+    const int nb = min(NB, z.k - kb);
+    const int t0 = kb + nb;
+    const int r0 = (t0 == z.k ? z.kp : t0) + rb * RB;
     T *F = front + d.foff[s];
-    const T *Dv = dinv + d.dinvoff[s] + (int64_t)(kb / NB) * NB * NB;
-    const int tid = threadIdx.x;
-    for (int idx = tid; idx < NB * NB; idx += THREADS) {
-        const int r = idx % NB, c = idx / NB;
-        Di[r][c] = Dv[idx];
-    }
-    for (int idx = tid; idx < RB * NB; idx += THREADS) {
-        const int r = idx % RB, c = idx / RB;
-        X[r][c] = (r < nr && c < nb) ? F[(int64_t)(kb + c) * m + r0 + r] : T(0);
-    }
+    stage_tile<T, THREADS>(Xs, RB, F + (int64_t)kb * z.ld + r0, z.ld, RB, NB, z.mp - r0, nb);
+    stage_tile<T, THREADS>(Ds, NB, dinv + d.dinvoff[s] + (int64_t)(kb / NB) * NB * NB, NB, NB, NB,
+                           NB, NB);
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
-    // out[r][c] = sum_{p <= c} X[r][p] Di[c][p]; thread: row tid % 64, 16 cols
+    // out[r][c] = sum_{p <= c} X[r][p] Linv(c, p); thread: row tid % 64, 16 cols
+    const int tid = threadIdx.x;
     const int r = tid % RB, cg = tid / RB;
     T acc[NB / 4];
 #pragma unroll
     for (int u = 0; u < NB / 4; ++u) acc[u] = T(0);
     for (int p = 0; p < nb; ++p) {
-        const T x = X[r][p];
+        const T x = Xs[p * RB + r];
 #pragma unroll
-        for (int u = 0; u < NB / 4; ++u) acc[u] += x * Di[cg + 4 * u][p];
+        for (int u = 0; u < NB / 4; ++u) acc[u] += x * Ds[p * NB + cg + 4 * u];
     }
-    if (r < nr) {
+    if (r0 + r < z.mp) {
 #pragma unroll
         for (int u = 0; u < NB / 4; ++u) {
             const int c = cg + 4 * u;
-            if (c < nb) F[(int64_t)(kb + c) * m + r0 + r] = acc[u];
+            if (c < nb) F[(int64_t)(kb + c) * z.ld + r0 + r] = acc[u];
         }
     }
 }
 
 // ---------------------------------------------------------------------------
 // Schur tile: C(rows [r0, r0+BM), cols [c0, c0+BN)) -= A(rows, ka:ka+K) A(cols, ka:ka+K)^T
-// restricted to r >= c, r < m, c < cmax.  thread (tx, ty): rows tx + 16 i,
+// restricted to r >= c, r < mp, c < cmax.  thread (tx, ty): rows tx + 16 i,
 // columns ty + 16 j (i < 8, j < 4).
-//   mode 0 (step):  base = kb + nb, ka = kb, K = nb, cmax = k
-//   mode 1 (syrk):  base = k, ka = 0, K = k, cmax = m
+//   mode 0 (step):  base = kb + NB, ka = kb, K = NB, cmax = k
+//   mode 1 (syrk):  base = kp, ka = 0, K = k, cmax = mp
 // In mode 0 the tile (0, 0) then factors and inverts the next diagonal block.
 // ---------------------------------------------------------------------------
 template <class T>
@@ -220,51 +242,62 @@ __global__ void __launch_bounds__(THREADS) schur_kernel(DevSym d, T *__restrict_
                                                         T *__restrict__ dinv,
                                                         const int4 *__restrict__ items, int kb,
                                                         int mode, status_t *status) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T(*As)[BM] = reinterpret_cast<T(*)[BM]>(smem_raw);
-    T(*Bs)[BN] = reinterpret_cast<T(*)[BN]>(smem_raw + sizeof(T) * BK * BM);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    T *As[2] = {sm, sm + BK * (BM + BN)};
+    T *Bs[2] = {sm + BK * BM, sm + BK * (BM + BN) + BK * BM};
     const int4 it = items[blockIdx.x];
     const int s = it.x, ti = it.y, tj = it.z;
-    const int m = d.sm[s], k = d.sk[s];
+    const Dims z = dims(d, s);
     int base, ka, K, cmax;
     if (mode == 0) {
-        const int nb = min(NB, k - kb);
-        base = kb + nb;
+        base = kb + NB;
         ka = kb;
-        K = nb;
-        cmax = k;
+        K = NB;
+        cmax = z.k;
     } else {
-        base = k;
+        base = z.kp;
         ka = 0;
-        K = k;
-        cmax = m;
+        K = z.k;
+        cmax = z.mp;
     }
     const int r0 = base + ti * BM, c0 = base + tj * BN;
     T *F = front + d.foff[s];
+    const T *Ar = F + (int64_t)ka * z.ld + r0;
+    const T *Bc = F + (int64_t)ka * z.ld + c0;
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     T acc[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        const int kc = min(BK, K - k0);
-        for (int idx = tid; idx < BK * BM; idx += THREADS) {
-            const int kk = idx / BM, rr = idx % BM;
-            As[kk][rr] = (kk < kc && r0 + rr < m) ? F[(int64_t)(ka + k0 + kk) * m + r0 + rr] : T(0);
-        }
-        for (int idx = tid; idx < BK * BN; idx += THREADS) {
-            const int kk = idx / BN, cc = idx % BN;
-            Bs[kk][cc] = (kk < kc && c0 + cc < cmax) ? F[(int64_t)(ka + k0 + kk) * m + c0 + cc] : T(0);
+    const int nk = (K + BK - 1) / BK;
+    stage_tile<T, THREADS>(As[0], BM, Ar, z.ld, BM, BK, z.mp - r0, min(BK, K));
+    stage_tile<T, THREADS>(Bs[0], BN, Bc, z.ld, BN, BK, cmax - c0, min(BK, K));
+    cp_async_commit();
+    for (int kt = 0; kt < nk; ++kt) {
+        const int cur = kt & 1;
+        if (kt + 1 < nk) {
+            const int k1 = (kt + 1) * BK;
+            stage_tile<T, THREADS>(As[cur ^ 1], BM, Ar + (int64_t)k1 * z.ld, z.ld, BM, BK, z.mp - r0,
+                                   min(BK, K - k1));
+            stage_tile<T, THREADS>(Bs[cur ^ 1], BN, Bc + (int64_t)k1 * z.ld, z.ld, BN, BK, cmax - c0,
+                                   min(BK, K - k1));
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < kc; ++kk) {
+        const T *A = As[cur];
+        const T *B = Bs[cur];
+#pragma unroll 8
+        for (int kk = 0; kk < BK; ++kk) {
             T a[8], b[4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) a[i] = As[kk][tx + 16 * i];
+            for (int i = 0; i < 8; ++i) a[i] = A[kk * BM + tx + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+            for (int j = 0; j < 4; ++j) b[j] = B[kk * BN + ty + 16 * j];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -279,13 +312,14 @@ __global__ void __launch_bounds__(THREADS) schur_kernel(DevSym d, T *__restrict_
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int r = r0 + tx + 16 * i;
-            if (r < m && r >= c) F[(int64_t)c * m + r] -= acc[i][j];
+            if (r < z.mp && r >= c) F[(int64_t)c * z.ld + r] -= acc[i][j];
         }
     }
-    if (mode == 0 && ti == 0 && tj == 0 && base < k) {
+    if (mode == 0 && ti == 0 && tj == 0 && base < z.k) {
         __syncthreads();
-        block_potrf_inv<T>(F + (int64_t)base * m + base, m, min(NB, k - base), d.sfirst[s] + base,
-                           status, dinv + d.dinvoff[s] + (int64_t)(base / NB) * NB * NB,
+        block_potrf_inv<T>(F + (int64_t)base * z.ld + base, z.ld, min(NB, z.k - base),
+                           d.sfirst[s] + base, status,
+                           dinv + d.dinvoff[s] + (int64_t)(base / NB) * NB * NB,
                            reinterpret_cast<T *>(smem_raw));
     }
 }
@@ -293,11 +327,11 @@ __global__ void __launch_bounds__(THREADS) schur_kernel(DevSym d, T *__restrict_
 template <class T>
 constexpr size_t potrf_smem() { return 2 * sizeof(T) * NB * (NB + 1); }
 template <class T>
-constexpr size_t panel_smem() { return sizeof(T) * (NB + RB) * (NB + 1); }
+constexpr size_t panel_smem() { return sizeof(T) * (NB * RB + NB * NB); }
 template <class T>
 constexpr size_t schur_smem() {
-    return (sizeof(T) * BK * (BM + BN) > potrf_smem<T>()) ? sizeof(T) * BK * (BM + BN)
-                                                          : potrf_smem<T>();
+    return (2 * sizeof(T) * BK * (BM + BN) > potrf_smem<T>()) ? 2 * sizeof(T) * BK * (BM + BN)
+                                                              : potrf_smem<T>();
 }
 
 template <class T>

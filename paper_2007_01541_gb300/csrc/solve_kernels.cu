@@ -7,6 +7,7 @@
 // rows below its diagonal block, which its parent gathers through the same
 // relative row maps as the factorization (no atomics).  Backward: every
 // supernode reads the already final x of its front rows.
+#include "dev_common.cuh"
 #include "engine.h"
 
 namespace wd {
@@ -83,25 +84,30 @@ __global__ void __launch_bounds__(THREADS) fwd_gather_kernel(DevSym d, T *__rest
 template <class T>
 __device__ void diag_apply(const T *Dv, int trans, int nb, T *Y, int64_t n, int64_t rowbase,
                            int j0, int c0, int nc, T *smem) {
-    T(*Di)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
-    T(*Ts)[RG] = reinterpret_cast<T(*)[RG]>(smem + NB * (NB + 1));
+    T *Ds = smem;  // Ds[p * NB + r] = (trans ? Dinv(p, r) : Dinv(r, p))
+    T(*Ts)[RG] = reinterpret_cast<T(*)[RG]>(smem + NB * NB);
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < NB * NB; idx += THREADS) {
-        const int r = idx % NB, c = idx / NB;
-        if (trans) Di[c][r] = Dv[idx];
-        else Di[r][c] = Dv[idx];
+    if (!trans) {
+        stage_tile<T, THREADS>(Ds, NB, Dv, NB, NB, NB, NB, NB);
+    } else {
+        for (int idx = tid; idx < NB * NB; idx += THREADS) {
+            const int p = idx % NB, r = idx / NB;  // Dv[idx] = Dinv(p, r)
+            cp_async_elem(Ds + p * NB + r, Dv + idx, true);
+        }
     }
     for (int idx = tid; idx < NB * RG; idx += THREADS) {
         const int r = idx % NB, c = idx / NB;
-        Ts[r][c] = (r < nb && c < nc) ? Y[rowbase + j0 + r + (int64_t)(c0 + c) * n] : T(0);
+        cp_async_elem(&Ts[r][c], Y + rowbase + j0 + r + (int64_t)(c0 + c) * n, r < nb && c < nc);
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     const int r = tid % NB, cg = tid / NB;
     T acc[RG / 4];
 #pragma unroll
     for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
     for (int p = 0; p < nb; ++p) {
-        const T dv = Di[r][p];
+        const T dv = Ds[p * NB + r];
 #pragma unroll
         for (int u = 0; u < RG / 4; ++u) acc[u] += dv * Ts[p][cg + 4 * u];
     }
@@ -121,7 +127,7 @@ __global__ void __launch_bounds__(THREADS) fwd_diag_first_kernel(DevSym d, const
                                                                  T *__restrict__ Y,
                                                                  const int4 *__restrict__ items,
                                                                  int nrhs) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int4 it = items[blockIdx.x];
     const int s = it.x, c0 = it.y * RG;
     const int k = d.sk[s];
@@ -129,7 +135,7 @@ __global__ void __launch_bounds__(THREADS) fwd_diag_first_kernel(DevSym d, const
                   min(RG, nrhs - c0), reinterpret_cast<T *>(smem_raw));
 }
 
-// pivot rows [t0 + rb*SOLVE_RB, k) -= L(rows, kb:kb+nb) y(kb:kb+nb); the block
+// pivot rows [t0 + rb*SOLVE_RB, k) -= L(rows, kb:kb+NB) y(kb:kb+NB); the block
 // holding the next diagonal block then applies its inverse.
 template <class T>
 __global__ void __launch_bounds__(THREADS) fwd_update_kernel(DevSym d, const T *__restrict__ front,
@@ -137,90 +143,116 @@ __global__ void __launch_bounds__(THREADS) fwd_update_kernel(DevSym d, const T *
                                                              T *__restrict__ Y,
                                                              const int4 *__restrict__ items,
                                                              int kb, int nrhs) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
-    T(*Ys)[RG] = reinterpret_cast<T(*)[RG]>(sm);
+    T *Ls = sm;                                                  // [p][r], ld SOLVE_RB
+    T(*Ys)[RG] = reinterpret_cast<T(*)[RG]>(sm + NB * SOLVE_RB);  // [p][c]
     const int4 it = items[blockIdx.x];
     const int s = it.x, rb = it.y, c0 = it.z * RG;
-    const int m = d.sm[s], k = d.sk[s];
-    const int nb = min(NB, k - kb), t0 = kb + nb;
+    const int k = d.sk[s], ld = d.sld[s];
+    const int t0 = kb + NB;  // only blocks followed by another pivot block
     const int nc = min(RG, nrhs - c0);
     const int64_t n = d.n;
     const int f = d.sfirst[s];
     const T *F = front + d.foff[s];
+    const int r0 = t0 + rb * SOLVE_RB;
     const int tid = threadIdx.x;
+    stage_tile<T, THREADS>(Ls, SOLVE_RB, F + (int64_t)kb * ld + r0, ld, SOLVE_RB, NB, k - r0, NB);
     for (int idx = tid; idx < NB * RG; idx += THREADS) {
         const int p = idx % NB, c = idx / NB;
-        Ys[p][c] = (p < nb && c < nc) ? Y[f + kb + p + (int64_t)(c0 + c) * n] : T(0);
+        cp_async_elem(&Ys[p][c], Y + f + kb + p + (int64_t)(c0 + c) * n, c < nc);
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     const int rl = tid % SOLVE_RB, cg = tid / SOLVE_RB;  // 4 column groups
-    const int r = t0 + rb * SOLVE_RB + rl;
+    const int r = r0 + rl;
+    T acc[RG / 4];
+#pragma unroll
+    for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
+#pragma unroll 8
+    for (int p = 0; p < NB; ++p) {
+        const T l = Ls[p * SOLVE_RB + rl];
+#pragma unroll
+        for (int u = 0; u < RG / 4; ++u) acc[u] += l * Ys[p][cg + 4 * u];
+    }
     if (r < k) {
-        T acc[RG / 4];
-#pragma unroll
-        for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
-        for (int p = 0; p < nb; ++p) {
-            const T l = F[(int64_t)(kb + p) * m + r];
-#pragma unroll
-            for (int u = 0; u < RG / 4; ++u) acc[u] += l * Ys[p][cg + 4 * u];
-        }
 #pragma unroll
         for (int u = 0; u < RG / 4; ++u) {
             const int c = cg + 4 * u;
             if (c < nc) Y[f + r + (int64_t)(c0 + c) * n] -= acc[u];
         }
     }
-    if (rb == 0 && t0 < k) {
+    if (rb == 0) {
         __syncthreads();
         diag_apply<T>(dinv + d.dinvoff[s] + (int64_t)(t0 / NB) * NB * NB, 0, min(NB, k - t0), Y, n,
                       f, t0, c0, nc, sm);
     }
 }
 
-// rows of R: W_s -= L(R, 0:k) y(0:k), once the whole pivot block is solved
+// rows of R: W_s -= L(R, 0:k) y(0:k), once the whole pivot block is solved;
+// the pivot columns are streamed in chunks of NB, double buffered.
 template <class T>
 __global__ void __launch_bounds__(THREADS) fwd_rgemm_kernel(DevSym d, const T *__restrict__ front,
                                                             const T *__restrict__ Y,
                                                             T *__restrict__ W,
                                                             const int4 *__restrict__ items,
                                                             int nrhs) {
-    __shared__ T Ys[NB][RG];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    T *Ls[2] = {sm, sm + NB * SOLVE_RB};
+    T *Ys[2] = {sm + 2 * NB * SOLVE_RB, sm + 2 * NB * SOLVE_RB + NB * RG};
     const int4 it = items[blockIdx.x];
     const int s = it.x, rb = it.y, c0 = it.z * RG;
-    const int m = d.sm[s], k = d.sk[s];
+    const int m = d.sm[s], k = d.sk[s], kp = d.skp[s], ld = d.sld[s];
     const int nc = min(RG, nrhs - c0);
     const int64_t n = d.n;
     const int f = d.sfirst[s];
-    const T *F = front + d.foff[s];
+    const int i0 = rb * SOLVE_RB;  // first local row of R
+    const T *F = front + d.foff[s] + kp + i0;
     T *Ws = W + d.woff[s] * nrhs;
     const int tid = threadIdx.x;
     const int rl = tid % SOLVE_RB, cg = tid / SOLVE_RB;
-    const int r = k + rb * SOLVE_RB + rl;
+    auto stage = [&](int buf, int p0) {
+        stage_tile<T, THREADS>(Ls[buf], SOLVE_RB, F + (int64_t)p0 * ld, ld, SOLVE_RB, NB,
+                               (m - k) - i0, k - p0);
+        for (int idx = tid; idx < NB * RG; idx += THREADS) {
+            const int p = idx % NB, c = idx / NB;
+            cp_async_elem(Ys[buf] + p * RG + c, Y + f + p0 + p + (int64_t)(c0 + c) * n,
+                          p0 + p < k && c < nc);
+        }
+        cp_async_commit();
+    };
     T acc[RG / 4];
 #pragma unroll
     for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
-    for (int p0 = 0; p0 < k; p0 += NB) {
-        const int np = min(NB, k - p0);
-        __syncthreads();
-        for (int idx = tid; idx < NB * RG; idx += THREADS) {
-            const int p = idx % NB, c = idx / NB;
-            Ys[p][c] = (p < np && c < nc) ? Y[f + p0 + p + (int64_t)(c0 + c) * n] : T(0);
+    const int nchunk = (k + NB - 1) / NB;
+    stage(0, 0);
+    for (int ch = 0; ch < nchunk; ++ch) {
+        const int cur = ch & 1;
+        if (ch + 1 < nchunk) {
+            stage(cur ^ 1, (ch + 1) * NB);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
-        if (r < m) {
-            for (int p = 0; p < np; ++p) {
-                const T l = F[(int64_t)(p0 + p) * m + r];
+        const T *L = Ls[cur];
+        const T *Yc = Ys[cur];
+#pragma unroll 8
+        for (int p = 0; p < NB; ++p) {
+            const T l = L[p * SOLVE_RB + rl];
 #pragma unroll
-                for (int u = 0; u < RG / 4; ++u) acc[u] += l * Ys[p][cg + 4 * u];
-            }
+            for (int u = 0; u < RG / 4; ++u) acc[u] += l * Yc[p * RG + cg + 4 * u];
         }
+        __syncthreads();
     }
-    if (r < m) {
+    const int i = i0 + rl;
+    if (i < m - k) {
 #pragma unroll
         for (int u = 0; u < RG / 4; ++u) {
             const int c = cg + 4 * u;
-            if (c < nc) Ws[(int64_t)(c0 + c) * (m - k) + (r - k)] -= acc[u];
+            if (c < nc) Ws[(int64_t)(c0 + c) * (m - k) + i] -= acc[u];
         }
     }
 }
@@ -229,46 +261,65 @@ __global__ void __launch_bounds__(THREADS) fwd_rgemm_kernel(DevSym d, const T *_
 // backward
 // ---------------------------------------------------------------------------
 // y(J block jb) -= L(R, jb)^T x(R) with x(R) read at the front rows beyond the
-// supernode; the last block of J then applies its inverse.
+// supernode (64-row chunks, double buffered); the last block of J then
+// applies its inverse.
 template <class T>
 __global__ void __launch_bounds__(THREADS) bwd_init_kernel(DevSym d, const T *__restrict__ front,
                                                            const T *__restrict__ dinv,
                                                            T *__restrict__ Y,
                                                            const int4 *__restrict__ items,
                                                            int nrhs) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
-    T(*Ls)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(sm);             // [64 rows][NB cols]
-    T(*Xs)[RG] = reinterpret_cast<T(*)[RG]>(sm + 64 * (NB + 1));      // [64 rows][RG]
+    constexpr int LST = 64 * (NB + 1), XST = 64 * RG;
+    T *Ls[2] = {sm, sm + LST + XST};     // [rr][c], ld NB + 1
+    T *Xs[2] = {sm + LST, sm + 2 * LST + XST};  // [rr][c], ld RG
     const int4 it = items[blockIdx.x];
     const int s = it.x, jblk = it.y, c0 = it.z * RG;
-    const int m = d.sm[s], k = d.sk[s];
+    const int m = d.sm[s], k = d.sk[s], kp = d.skp[s], ld = d.sld[s];
     const int j0 = jblk * NB, nb = min(NB, k - j0);
     const int nc = min(RG, nrhs - c0);
     const int64_t n = d.n;
     const int f = d.sfirst[s];
-    const T *F = front + d.foff[s];
-    const int32_t *rows = d.rows + d.rowptr[s];
+    const T *F = front + d.foff[s] + (int64_t)j0 * ld + kp;
+    const int32_t *rows = d.rows + d.rowptr[s] + k;
     const int tid = threadIdx.x;
     const int cl = tid % NB, cg = tid / NB;  // column of the block, rhs group of 4
-    T acc[RG / 4];
-#pragma unroll
-    for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
-    for (int r0 = k; r0 < m; r0 += 64) {
-        const int nr = min(64, m - r0);
+    const int nR = m - k;
+    auto stage = [&](int buf, int i0) {
+        const int nr = min(64, nR - i0);
         for (int idx = tid; idx < 64 * NB; idx += THREADS) {
             const int rr = idx % 64, c = idx / 64;
-            Ls[rr][c] = (rr < nr && c < nb) ? F[(int64_t)(j0 + c) * m + r0 + rr] : T(0);
+            cp_async_elem(Ls[buf] + rr * (NB + 1) + c, F + (int64_t)c * ld + i0 + rr, rr < nr && c < nb);
         }
         for (int idx = tid; idx < 64 * RG; idx += THREADS) {
             const int rr = idx % 64, c = idx / 64;
-            Xs[rr][c] = (rr < nr && c < nc) ? Y[rows[r0 + rr] + (int64_t)(c0 + c) * n] : T(0);
+            const bool v = rr < nr && c < nc;
+            cp_async_elem(Xs[buf] + rr * RG + c, v ? Y + rows[i0 + rr] + (int64_t)(c0 + c) * n : Y, v);
+        }
+        cp_async_commit();
+    };
+    T acc[RG / 4];
+#pragma unroll
+    for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
+    const int nchunk = (nR + 63) / 64;
+    if (nchunk > 0) stage(0, 0);
+    for (int ch = 0; ch < nchunk; ++ch) {
+        const int cur = ch & 1;
+        if (ch + 1 < nchunk) {
+            stage(cur ^ 1, (ch + 1) * 64);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
-        for (int rr = 0; rr < nr; ++rr) {
-            const T l = Ls[rr][cl];
+        const T *L = Ls[cur];
+        const T *X = Xs[cur];
+#pragma unroll 8
+        for (int rr = 0; rr < 64; ++rr) {
+            const T l = L[rr * (NB + 1) + cl];
 #pragma unroll
-            for (int u = 0; u < RG / 4; ++u) acc[u] += l * Xs[rr][cg + 4 * u];
+            for (int u = 0; u < RG / 4; ++u) acc[u] += l * X[rr * RG + cg + 4 * u];
         }
         __syncthreads();
     }
@@ -293,13 +344,13 @@ __global__ void __launch_bounds__(THREADS) bwd_step_kernel(DevSym d, const T *__
                                                            T *__restrict__ Y,
                                                            const int4 *__restrict__ items,
                                                            int ib, int nrhs) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
-    T(*Ls)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(sm);
-    T(*Xs)[RG] = reinterpret_cast<T(*)[RG]>(sm + NB * (NB + 1));
+    T *Ls = sm;                        // [rr][c], ld NB + 1
+    T *Xs = sm + NB * (NB + 1);        // [rr][c], ld RG
     const int4 it = items[blockIdx.x];
     const int s = it.x, jblk = it.y, c0 = it.z * RG;
-    const int m = d.sm[s], k = d.sk[s];
+    const int k = d.sk[s], ld = d.sld[s];
     const int j0 = jblk * NB, nbj = min(NB, k - j0);
     const int r0 = (ib + 1) * NB, nr = min(NB, k - r0);
     const int nc = min(RG, nrhs - c0);
@@ -309,23 +360,26 @@ __global__ void __launch_bounds__(THREADS) bwd_step_kernel(DevSym d, const T *__
     const int tid = threadIdx.x;
     for (int idx = tid; idx < NB * NB; idx += THREADS) {
         const int rr = idx % NB, c = idx / NB;
-        Ls[rr][c] = (rr < nr && c < nbj) ? F[(int64_t)(j0 + c) * m + r0 + rr] : T(0);
+        cp_async_elem(Ls + rr * (NB + 1) + c, F + (int64_t)(j0 + c) * ld + r0 + rr, rr < nr && c < nbj);
     }
     for (int idx = tid; idx < NB * RG; idx += THREADS) {
         const int rr = idx % NB, c = idx / NB;
-        Xs[rr][c] = (rr < nr && c < nc) ? Y[f + r0 + rr + (int64_t)(c0 + c) * n] : T(0);
+        cp_async_elem(Xs + rr * RG + c, Y + f + r0 + rr + (int64_t)(c0 + c) * n, rr < nr && c < nc);
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     const int cl = tid % NB, cg = tid / NB;
+    T acc[RG / 4];
+#pragma unroll
+    for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
+#pragma unroll 8
+    for (int rr = 0; rr < NB; ++rr) {
+        const T l = Ls[rr * (NB + 1) + cl];
+#pragma unroll
+        for (int u = 0; u < RG / 4; ++u) acc[u] += l * Xs[rr * RG + cg + 4 * u];
+    }
     if (cl < nbj) {
-        T acc[RG / 4];
-#pragma unroll
-        for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
-        for (int rr = 0; rr < nr; ++rr) {
-            const T l = Ls[rr][cl];
-#pragma unroll
-            for (int u = 0; u < RG / 4; ++u) acc[u] += l * Xs[rr][cg + 4 * u];
-        }
 #pragma unroll
         for (int u = 0; u < RG / 4; ++u) {
             const int c = cg + 4 * u;
@@ -351,11 +405,11 @@ __global__ void __launch_bounds__(THREADS) apply_L_kernel(DevSym d, const T *__r
     const int4 it = items[blockIdx.x];
     const int s = it.x;
     const int r = it.y * THREADS + threadIdx.x;
-    const int m = d.sm[s], k = d.sk[s];
+    const int m = d.sm[s], k = d.sk[s], kp = d.skp[s], ld = d.sld[s];
     if (r >= m) return;
     const int64_t n = d.n;
     const int f = d.sfirst[s];
-    const T *F = front + d.foff[s];
+    const T *F = front + d.foff[s] + (r < k ? r : r + kp - k);
     const int cb = d.child_ptr[s], ce = d.child_ptr[s + 1];
     const int pmax = min(r + 1, k);
     for (int col = 0; col < nrhs; ++col) {
@@ -366,7 +420,7 @@ __global__ void __launch_bounds__(THREADS) apply_L_kernel(DevSym d, const T *__r
             if (ic >= 0) t += W[d.woff[c] * nrhs + (int64_t)col * (d.sm[c] - d.sk[c]) + ic];
         }
         const T *z = Z + f + (int64_t)col * n;
-        for (int p = 0; p < pmax; ++p) t += F[(int64_t)p * m + r] * z[p];
+        for (int p = 0; p < pmax; ++p) t += F[(int64_t)p * ld] * z[p];
         if (r < k) Out[f + r + (int64_t)col * n] = t;
         else W[d.woff[s] * nrhs + (int64_t)col * (m - k) + (r - k)] = t;
     }
@@ -453,9 +507,9 @@ __global__ void logdet_partial_kernel(DevSym d, const T *__restrict__ front, dou
     __shared__ double red[THREADS];
     double acc = 0.0;
     for (int s = blockIdx.x; s < d.ns; s += gridDim.x) {
-        const int m = d.sm[s], k = d.sk[s];
+        const int k = d.sk[s], ld = d.sld[s];
         const T *F = front + d.foff[s];
-        for (int j = threadIdx.x; j < k; j += THREADS) acc += 2.0 * log((double)F[(int64_t)j * m + j]);
+        for (int j = threadIdx.x; j < k; j += THREADS) acc += 2.0 * log((double)F[(int64_t)j * ld + j]);
     }
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -483,12 +537,13 @@ template <class T>
 __global__ void export_panels_kernel(DevSym d, const T *__restrict__ front,
                                      double *__restrict__ out, const int64_t *__restrict__ poff) {
     const int s = blockIdx.x;
-    const int m = d.sm[s], k = d.sk[s];
+    const int m = d.sm[s], k = d.sk[s], kp = d.skp[s], ld = d.sld[s];
     const T *F = front + d.foff[s];
     double *P = out + poff[s];
     for (int64_t idx = threadIdx.x; idx < (int64_t)m * k; idx += THREADS) {
         const int r = (int)(idx % m), c = (int)(idx / m);
-        P[idx] = (r >= c) ? (double)F[(int64_t)c * m + r] : 0.0;
+        const int fr = r < k ? r : r + kp - k;
+        P[idx] = (r >= c) ? (double)F[(int64_t)c * ld + fr] : 0.0;
     }
 }
 
@@ -501,7 +556,9 @@ inline int grid_for(int64_t work) {
 template <class T>
 constexpr size_t diag_smem() { return sizeof(T) * (NB * (NB + 1) + NB * RG); }
 template <class T>
-constexpr size_t bwd_init_smem() { return sizeof(T) * (64 * (NB + 1) + 64 * RG); }
+constexpr size_t bwd_init_smem() { return 2 * sizeof(T) * (64 * (NB + 1) + 64 * RG); }
+template <class T>
+constexpr size_t rgemm_smem() { return 2 * sizeof(T) * (NB * SOLVE_RB + NB * RG); }
 
 template <class T>
 void set_attrs() {
@@ -515,6 +572,8 @@ void set_attrs() {
                          (int)bwd_init_smem<T>());
     cudaFuncSetAttribute(bwd_step_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)diag_smem<T>());
+    cudaFuncSetAttribute(fwd_rgemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)rgemm_smem<T>());
     done = true;
 }
 
@@ -570,7 +629,8 @@ template <class T>
 void launch_fwd_rgemm(const DevSym &d, const T *front, const T *Y, T *W, const int4 *items,
                       int count, int nrhs, cudaStream_t st) {
     if (count <= 0) return;
-    fwd_rgemm_kernel<T><<<count, THREADS, 0, st>>>(d, front, Y, W, items, nrhs);
+    set_attrs<T>();
+    fwd_rgemm_kernel<T><<<count, THREADS, rgemm_smem<T>(), st>>>(d, front, Y, W, items, nrhs);
 }
 
 template <class T>

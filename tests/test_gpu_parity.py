@@ -203,3 +203,20 @@ def test_refactor_same_pattern_and_zero_rhs(wdlib, cuda):
         s.factor(v * scale, "fp64")
         assert abs(s.logdet() - (o.logdet() + o.n * math.log(scale))) <= 1e-11 * abs(o.logdet())
     assert s.solve(np.zeros((o.n, 0))).shape == (o.n, 0)
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_profiled_and_direct_launches(wdlib, cuda, graphs):
+    b, cp, ri, v, o = _case("2d_J6")
+    s = wdlib.Solver(profile=True, use_graphs=graphs).analyze(cp, ri, b)
+    B = rhs(o.n, 3, seed=4)
+    for prec in ("fp64", "mixed"):
+        s.factor(v, prec)
+        X = s.solve(B)
+        assert oracle.backward_error(cp, ri, v, X, B).max() <= 1e-12
+    st = s.kernel_stats(reset=True)
+    names = {k["name"] for k in st}
+    assert {"schur_update_fp64", "schur_syrk_fp32", "fwd_update_fp32", "bwd_init_fp64"} <= names
+    assert all(k["launches"] > 0 and k["ms"] > 0 for k in st)
+    assert s.kernel_stats() == []
+    assert s.launch_count() > 0
