@@ -129,6 +129,7 @@ struct wd_ctx {
     // profiling
     int64_t launches = 0;  // kernels launched by this handle
     std::vector<cudaEvent_t> prof_ev;
+    cudaEvent_t single_ev[2] = {nullptr, nullptr};
     std::vector<std::pair<std::string, KStat>> prof;
     std::string msg;
     int64_t errcol = -1;
@@ -212,6 +213,8 @@ void wd_destroy(wd_handle h) {
         cudaGetDevice(&prev);
         cudaSetDevice(h->device);
         for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+        for (cudaEvent_t e : h->single_ev)
+            if (e) cudaEventDestroy(e);
         h->g_factor.reset();
         h->g_solve.reset();
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -727,6 +730,41 @@ static void prof_end(wd_handle h, const Plan &p, size_t elem_size, const char *s
     }
 }
 
+// profiling of a single launch outside the plans (events, synchronizing)
+static void prof_single(wd_handle h, const char *name, double flops, double bytes, cudaStream_t st,
+                        bool begin) {
+    if (!h->opt.profile) return;
+    if (h->single_ev[0] == nullptr) {
+        if (cudaEventCreate(&h->single_ev[0]) != cudaSuccess ||
+            cudaEventCreate(&h->single_ev[1]) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+    }
+    if (begin) {
+        cudaEventRecord(h->single_ev[0], st);
+        return;
+    }
+    cudaEventRecord(h->single_ev[1], st);
+    cudaEventSynchronize(h->single_ev[1]);
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, h->single_ev[0], h->single_ev[1]) != cudaSuccess) {
+        cudaGetLastError();
+        ms = 0;
+    }
+    KStat *stt = nullptr;
+    for (auto &kv : h->prof)
+        if (kv.first == name) stt = &kv.second;
+    if (!stt) {
+        h->prof.push_back({name, KStat()});
+        stt = &h->prof.back().second;
+    }
+    stt->launches += 1;
+    stt->ms += ms;
+    stt->flops += flops;
+    stt->bytes += bytes;
+}
+
 extern "C" wd_status wd_launch_count(wd_handle h, int64_t *count, int reset) {
     if (!h || !count) return WD_ERR_INVALID_ARG;
     *count = h->launches;
@@ -917,10 +955,15 @@ static wd_status run_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st) {
     return WD_OK;
 }
 
+// R = Bp - A X (FP64, row-major n x nrhs) and the largest normwise backward
+// error over the columns
 static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cudaStream_t st,
                                  double *be_max) {
     const int64_t n = h->S.n;
+    const double nf = (double)h->nnz_full;
+    prof_single(h, "spmv_residual_fp64", 0, 0, st, true);
     wd::launch_spmv_residual(h->dsym, X, h->d_Bp, h->d_R, nrhs, st);
+    prof_single(h, "spmv_residual_fp64", 2.0 * nf * nrhs, 12.0 * nf + 24.0 * n * nrhs, st, false);
     wd::launch_colmax3(h->d_R, X, h->d_Bp, n, nrhs, h->d_cm, st);
     h->launches += 2;
     std::vector<double> cm(3 * nrhs);
@@ -968,16 +1011,20 @@ extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb,
         ld = n;
     }
     const int nr = (int)nrhs;
-    wd::launch_permute_in<double>(Bd, ld, h->d_Bp, h->dsym.perm, n, nrhs, st);
+    // right-hand sides in factor order, row-major, FP64
+    wd::launch_permute_in_rm(Bd, ld, h->d_Bp, h->dsym.perm, n, nrhs, st);
     h->launches += 1;
     if (h->prec == WD_FP64) {
         double *Y = static_cast<double *>(h->d_Y);
-        CK(cudaMemcpyAsync(Y, h->d_Bp, n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy");
+        wd::launch_transpose<double>(Y, h->d_Bp, n, nrhs, 0, 0, st);
+        h->launches += 1;
         s = run_solve_plan<double>(h, Y, nr, st);
         if (s != WD_OK) return s;
         if (info) {
+            wd::launch_transpose<double>(Y, h->d_X, n, nrhs, 1, 0, st);
+            h->launches += 1;
             double be;
-            s = backward_errors(h, Y, nrhs, st, &be);
+            s = backward_errors(h, h->d_X, nrhs, st, &be);
             if (s != WD_OK) return s;
             info->backward_error = be;
         }
@@ -985,10 +1032,10 @@ extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb,
         h->launches += 1;
     } else {
         float *Y = static_cast<float *>(h->d_Y);
-        wd::launch_cast<float>(h->d_Bp, Y, n * nrhs, st);
+        wd::launch_transpose<float>(Y, h->d_Bp, n, nrhs, 0, 0, st);
         s = run_solve_plan<float>(h, Y, nr, st);
         if (s != WD_OK) return s;
-        wd::launch_axpy_into<float>(h->d_X, Y, n * nrhs, 0, st);
+        wd::launch_transpose<float>(Y, h->d_X, n, nrhs, 1, 0, st);
         h->launches += 2;
         CK(cudaGetLastError(), "solve launch");
         double be = 1.0;
@@ -997,10 +1044,10 @@ extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb,
             s = backward_errors(h, h->d_X, nrhs, st, &be);
             if (s != WD_OK) return s;
             if (be <= h->opt.ir_tol || it >= h->opt.ir_max_iter) break;
-            wd::launch_cast<float>(h->d_R, Y, n * nrhs, st);
+            wd::launch_transpose<float>(Y, h->d_R, n, nrhs, 0, 0, st);
             s = run_solve_plan<float>(h, Y, nr, st);
             if (s != WD_OK) return s;
-            wd::launch_axpy_into<float>(h->d_X, Y, n * nrhs, 1, st);
+            wd::launch_transpose<float>(Y, h->d_X, n, nrhs, 1, 1, st);
             h->launches += 2;
             CK(cudaGetLastError(), "refinement launch");
             ++it;
@@ -1009,7 +1056,7 @@ extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb,
             info->iterations = it;
             info->backward_error = be;
         }
-        wd::launch_permute_out<double>(h->d_X, Bd, ld, h->dsym.perm, n, nrhs, st);
+        wd::launch_permute_out_rm(h->d_X, Bd, ld, h->dsym.perm, n, nrhs, st);
         h->launches += 1;
         if (be > h->opt.ir_tol) {
             if (!B_on_device)

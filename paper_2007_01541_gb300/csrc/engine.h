@@ -93,6 +93,15 @@ void launch_bwd_step(const DevSym &d, const T *front, const T *dinv, T *Y, const
 template <class T>
 void launch_apply_L(const DevSym &d, const T *front, const T *Z, T *Out, T *W,
                     const int4 *items, int count, int nrhs, cudaStream_t st);
+// refinement vectors are row-major (n x nrhs, right-hand sides contiguous)
+void launch_permute_in_rm(const double *B, int64_t ldb, double *Bp, const int32_t *perm, int64_t n,
+                          int64_t nrhs, cudaStream_t st);
+void launch_permute_out_rm(const double *X, double *B, int64_t ldb, const int32_t *perm, int64_t n,
+                           int64_t nrhs, cudaStream_t st);
+// dir 0: C (column-major) = Rm; dir 1: Rm (=, or += if accumulate) C
+template <class Tc>
+void launch_transpose(Tc *C, double *Rm, int64_t n, int64_t nrhs, int dir, int accumulate,
+                      cudaStream_t st);
 void launch_spmv_residual(const DevSym &d, const double *X, const double *Bp, double *R,
                           int64_t nrhs, cudaStream_t st);
 void launch_norm_inf_rows(const DevSym &d, double *rowsum_max, cudaStream_t st);

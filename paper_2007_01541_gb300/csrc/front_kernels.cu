@@ -113,41 +113,84 @@ __global__ void __launch_bounds__(THREADS) front_init_kernel(DevSym d, T *__rest
 // ---------------------------------------------------------------------------
 // Cholesky of an nb x nb diagonal block (nb <= NB) in shared memory, then the
 // inverse of the factor, written zero-padded as an NB x NB lower-triangular
-// matrix (column-major) to Dinv.  A pivot that is not positive records its
-// global column in *status (smallest wins) and is replaced by 1 so that the
-// arithmetic stays finite.  Must be called by all THREADS threads.
+// matrix (column-major) to Dinv.  Blocked by 16: each 16 x 16 diagonal
+// sub-block is factored by one warp in registers (shuffles, no block
+// barrier), followed by the sub-panel solve and the trailing update.  A pivot
+// that is not positive records its global column in *status (smallest wins)
+// and is replaced by 1 so that the arithmetic stays finite.
+// Must be called by all THREADS threads.
 // ---------------------------------------------------------------------------
+constexpr int SB = 16;
+
 template <class T>
 __device__ void block_potrf_inv(T *F, int ld, int nb, int64_t gcol0, status_t *status, T *Dinv,
                                 T *smem) {
     T(*A)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
     T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem + NB * (NB + 1));
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     for (int idx = tid; idx < nb * nb; idx += THREADS) {
         const int r = idx % nb, c = idx / nb;
         if (r >= c) A[r][c] = F[(int64_t)c * ld + r];
     }
-    for (int idx = tid; idx < NB * NB; idx += THREADS) {
-        const int r = idx % NB, c = idx / NB;
-        X[r][c] = (r == c && r < nb) ? T(1) : T(0);
-    }
     __syncthreads();
-    const int r = tid % NB, cg = tid / NB;
-    for (int j = 0; j < nb; ++j) {
-        if (tid == 0) {
-            T dj = A[j][j];
-            if (!(dj > T(0))) {
-                atomicMin(status, (status_t)(gcol0 + j));
-                dj = T(1);
+    for (int jb = 0; jb < nb; jb += SB) {
+        const int w = min(SB, nb - jb);
+        if (warp == 0) {
+            T v[SB];
+#pragma unroll
+            for (int c = 0; c < SB; ++c) v[c] = (lane < w && c <= lane) ? A[jb + lane][jb + c] : T(0);
+#pragma unroll
+            for (int c = 0; c < SB; ++c) {
+                if (c < w) {
+                    T dcc = __shfl_sync(0xffffffffu, v[c], c);
+                    if (!(dcc > T(0))) {
+                        if (lane == 0) atomicMin(status, (status_t)(gcol0 + jb + c));
+                        dcc = T(1);
+                    }
+                    const T piv = dev_sqrt(dcc);
+                    if (lane == c) v[c] = piv;
+                    else if (lane > c) v[c] = v[c] / piv;
+#pragma unroll
+                    for (int c2 = c + 1; c2 < SB; ++c2) {
+                        const T lc2 = __shfl_sync(0xffffffffu, v[c], c2);
+                        if (lane >= c2) v[c2] -= v[c] * lc2;
+                    }
+                }
             }
-            A[j][j] = dev_sqrt(dj);
+            if (lane < w) {
+#pragma unroll
+                for (int c = 0; c < SB; ++c)
+                    if (c <= lane) A[jb + lane][jb + c] = v[c];
+            }
         }
         __syncthreads();
-        if (cg == 0 && r > j && r < nb) A[r][j] = A[r][j] / A[j][j];
+        const int rem = nb - jb - w;
+        if (tid < rem) {
+            const int i = jb + w + tid;
+            T x[SB];
+#pragma unroll
+            for (int c = 0; c < SB; ++c) x[c] = c < w ? A[i][jb + c] : T(0);
+#pragma unroll
+            for (int c = 0; c < SB; ++c) {
+                if (c < w) {
+                    T acc = x[c];
+#pragma unroll
+                    for (int p = 0; p < c; ++p) acc -= x[p] * A[jb + c][jb + p];
+                    x[c] = acc / A[jb + c][jb + c];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < SB; ++c)
+                if (c < w) A[i][jb + c] = x[c];
+        }
         __syncthreads();
-        if (r > j && r < nb) {
-            const T arj = A[r][j];
-            for (int c = j + 1 + cg; c <= r; c += THREADS / NB) A[r][c] -= arj * A[c][j];
+        for (int idx = tid; idx < rem * rem; idx += THREADS) {
+            const int i = jb + w + idx % rem, j = jb + w + idx / rem;
+            if (i >= j) {
+                T acc = T(0);
+                for (int c = 0; c < w; ++c) acc += A[i][jb + c] * A[j][jb + c];
+                A[i][j] -= acc;
+            }
         }
         __syncthreads();
     }
@@ -155,13 +198,58 @@ __device__ void block_potrf_inv(T *F, int ld, int nb, int64_t gcol0, status_t *s
         const int rr = idx % nb, c = idx / nb;
         if (rr >= c) F[(int64_t)c * ld + rr] = A[rr][c];
     }
-    // X := A^-1 by forward substitution on all columns at once
-    for (int i = 0; i < nb; ++i) {
-        if (cg == 0 && r <= i) X[i][r] = X[i][r] / A[i][i];
+    // X := A^-1, blocked by 16: diagonal inverses (one warp each), then the
+    // off-diagonal blocks X(bi, bj) = -X(bi, bi) sum_k A(bi, k) X(k, bj)
+    const int nsb = (nb + SB - 1) / SB;
+    for (int idx = tid; idx < NB * NB; idx += THREADS) X[idx % NB][idx / NB] = T(0);
+    __syncthreads();
+    if (warp < nsb && lane < SB) {
+        const int b0 = warp * SB, c = lane;
+        const int wv = min(SB, nb - b0);
+        T x[SB];
+#pragma unroll
+        for (int r = 0; r < SB; ++r) {
+            if (r < wv) {
+                T acc = (r == c) ? T(1) : T(0);
+#pragma unroll
+                for (int p = 0; p < r; ++p) acc -= A[b0 + r][b0 + p] * x[p];
+                x[r] = acc / A[b0 + r][b0 + r];
+            } else {
+                x[r] = T(0);
+            }
+        }
+        if (c < wv) {
+#pragma unroll
+            for (int r = 0; r < SB; ++r)
+                if (r < wv && r >= c) X[b0 + r][b0 + c] = x[r];
+        }
+    }
+    __syncthreads();
+    for (int bi = 1; bi < nsb; ++bi) {
+        const int r0 = bi * SB, wr = min(SB, nb - r0);
+        // T(bj) = sum_{k = bj .. bi-1} A(bi, k) X(k, bj), stored in X(bi, bj)
+        for (int idx = tid; idx < bi * SB * SB; idx += THREADS) {
+            const int bj = idx / (SB * SB), r = idx % SB, c = (idx / SB) % SB;
+            if (r < wr) {
+                T acc = T(0);
+                for (int p = bj * SB + c; p < r0; ++p) acc += A[r0 + r][p] * X[p][bj * SB + c];
+                X[r0 + r][bj * SB + c] = acc;
+            }
+        }
         __syncthreads();
-        if (r > i && r < nb) {
-            const T ari = A[r][i];
-            for (int c = cg; c <= i; c += THREADS / NB) X[r][c] -= ari * X[i][c];
+        T out[(SB * SB * (NB / SB)) / THREADS + 1];
+        int q = 0;
+        for (int idx = tid; idx < bi * SB * SB; idx += THREADS, ++q) {
+            const int bj = idx / (SB * SB), r = idx % SB, c = (idx / SB) % SB;
+            T acc = T(0);
+            for (int p = 0; p <= r && p < wr; ++p) acc += X[r0 + r][r0 + p] * X[r0 + p][bj * SB + c];
+            out[q] = -acc;
+        }
+        __syncthreads();
+        q = 0;
+        for (int idx = tid; idx < bi * SB * SB; idx += THREADS, ++q) {
+            const int bj = idx / (SB * SB), r = idx % SB, c = (idx / SB) % SB;
+            if (r < wr) X[r0 + r][bj * SB + c] = out[q];
         }
         __syncthreads();
     }

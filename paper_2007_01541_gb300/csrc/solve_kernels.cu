@@ -427,23 +427,129 @@ __global__ void __launch_bounds__(THREADS) apply_L_kernel(DevSym d, const T *__r
 }
 
 // ---------------------------------------------------------------------------
-// FP64 residual R = Bp - A_p X on the full CSR of P A P^T; one warp per row
+// Refinement vectors live in row-major (right-hand sides contiguous) FP64
+// arrays, so that the sparse product reads x coalesced across lanes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(THREADS) spmv_residual_kernel(DevSym d, const double *__restrict__ X,
-                                                                const double *__restrict__ Bp,
-                                                                double *__restrict__ R,
-                                                                int64_t nrhs) {
+// Bp[i*nrhs + c] = B[perm[i] + c*ldb]
+__global__ void permute_in_rm_kernel(const double *__restrict__ B, int64_t ldb,
+                                     double *__restrict__ Bp, const int32_t *__restrict__ perm,
+                                     int64_t n, int64_t nrhs) {
+    const int64_t tot = n * nrhs;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / nrhs, c = t % nrhs;
+        Bp[t] = B[perm[i] + c * ldb];
+    }
+}
+
+// B[perm[i] + c*ldb] = X[i*nrhs + c]
+__global__ void permute_out_rm_kernel(const double *__restrict__ X, double *__restrict__ B,
+                                      int64_t ldb, const int32_t *__restrict__ perm, int64_t n,
+                                      int64_t nrhs) {
+    const int64_t tot = n * nrhs;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / nrhs, c = t % nrhs;
+        B[perm[i] + c * ldb] = X[t];
+    }
+}
+
+// tiled transposes between column-major C (ld n) and row-major Rm (ld nrhs)
+//   dir 0: C[i + c n] = (Tc) Rm[i nrhs + c]
+//   dir 1: Rm[i nrhs + c] (= or +=) (double) C[i + c n]
+template <class Tc>
+__global__ void transpose_kernel(Tc *__restrict__ C, double *__restrict__ Rm, int64_t n,
+                                 int64_t nrhs, int dir, int accumulate) {
+    __shared__ double tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    if (dir == 0) {
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t i = i0 + j, c = c0 + tx;
+            tile[j][tx] = (i < n && c < nrhs) ? Rm[i * nrhs + c] : 0.0;
+        }
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t i = i0 + tx, c = c0 + j;
+            if (i < n && c < nrhs) C[i + c * n] = (Tc)tile[tx][j];
+        }
+    } else {
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t i = i0 + tx, c = c0 + j;
+            tile[j][tx] = (i < n && c < nrhs) ? (double)C[i + c * n] : 0.0;
+        }
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t i = i0 + j, c = c0 + tx;
+            if (i < n && c < nrhs) {
+                const double v = tile[tx][j];
+                Rm[i * nrhs + c] = accumulate ? Rm[i * nrhs + c] + v : v;
+            }
+        }
+    }
+}
+
+// R = Bp - A_p X in FP64 on the full CSR of P A P^T (row-major vectors).
+// Many right-hand sides: one warp per row, lanes over right-hand sides.
+__global__ void __launch_bounds__(THREADS) spmv_rm_wide_kernel(DevSym d, const double *__restrict__ X,
+                                                               const double *__restrict__ Bp,
+                                                               double *__restrict__ R, int nrhs) {
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= d.n) return;
     const int64_t e0 = d.csr_ptr[row], e1 = d.csr_ptr[row + 1];
-    for (int64_t c = 0; c < nrhs; ++c) {
-        const double *x = X + c * d.n;
-        double acc = 0.0;
-        for (int64_t e = e0 + lane; e < e1; e += 32) acc += d.csr_val[e] * x[d.csr_col[e]];
+    for (int c0 = 0; c0 < nrhs; c0 += 64) {
+        const int ca = c0 + lane, cb = c0 + 32 + lane;
+        double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+        int64_t e = e0;
+        for (; e + 1 < e1; e += 2) {
+            const double v0 = d.csr_val[e], v1 = d.csr_val[e + 1];
+            const double *x0 = X + (int64_t)d.csr_col[e] * nrhs;
+            const double *x1 = X + (int64_t)d.csr_col[e + 1] * nrhs;
+            if (ca < nrhs) {
+                a0 += v0 * x0[ca];
+                a1 += v1 * x1[ca];
+            }
+            if (cb < nrhs) {
+                b0 += v0 * x0[cb];
+                b1 += v1 * x1[cb];
+            }
+        }
+        if (e < e1) {
+            const double v0 = d.csr_val[e];
+            const double *x0 = X + (int64_t)d.csr_col[e] * nrhs;
+            if (ca < nrhs) a0 += v0 * x0[ca];
+            if (cb < nrhs) b0 += v0 * x0[cb];
+        }
+        if (ca < nrhs) R[row * nrhs + ca] = Bp[row * nrhs + ca] - (a0 + a1);
+        if (cb < nrhs) R[row * nrhs + cb] = Bp[row * nrhs + cb] - (b0 + b1);
+    }
+}
+
+// Few right-hand sides (<= 8): lanes over the entries of the row.
+__global__ void __launch_bounds__(THREADS) spmv_rm_narrow_kernel(DevSym d,
+                                                                 const double *__restrict__ X,
+                                                                 const double *__restrict__ Bp,
+                                                                 double *__restrict__ R, int nrhs) {
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= d.n) return;
+    double acc[8];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) R[row + c * d.n] = Bp[row + c * d.n] - acc;
+    for (int c = 0; c < 8; ++c) acc[c] = 0.0;
+    for (int64_t e = d.csr_ptr[row] + lane; e < d.csr_ptr[row + 1]; e += 32) {
+        const double v = d.csr_val[e];
+        const double *x = X + (int64_t)d.csr_col[e] * nrhs;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c < nrhs) acc[c] += v * x[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        double a = acc[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0 && c < nrhs) R[row * nrhs + c] = Bp[row * nrhs + c] - a;
     }
 }
 
@@ -463,27 +569,24 @@ __global__ void norm_inf_kernel(DevSym d, double *out) {
     if (lane == 0) atomic_max_nonneg(out, acc);
 }
 
-__global__ void colmax3_kernel(const double *__restrict__ R, const double *__restrict__ X,
-                               const double *__restrict__ B, int64_t n, double *out) {
-    __shared__ double red[3][THREADS];
-    const int64_t c = blockIdx.x;
-    double a = 0, b = 0, e = 0;
-    for (int64_t i = threadIdx.x; i < n; i += THREADS) {
-        a = fmax(a, fabs(R[i + c * n]));
-        b = fmax(b, fabs(X[i + c * n]));
-        e = fmax(e, fabs(B[i + c * n]));
+// per column c: out[3c] = max|R|, out[3c+1] = max|X|, out[3c+2] = max|B|
+// (row-major arrays; out must be zeroed; blocks take chunks of rows)
+__global__ void colmax3_rm_kernel(const double *__restrict__ R, const double *__restrict__ X,
+                                  const double *__restrict__ B, int64_t n, int nrhs,
+                                  int64_t rows_per_block, double *out) {
+    const int64_t r0 = blockIdx.x * rows_per_block;
+    const int64_t r1 = min(n, r0 + rows_per_block);
+    for (int c = threadIdx.x; c < nrhs; c += blockDim.x) {
+        double a = 0, b = 0, e = 0;
+        for (int64_t i = r0; i < r1; ++i) {
+            a = fmax(a, fabs(R[i * nrhs + c]));
+            b = fmax(b, fabs(X[i * nrhs + c]));
+            e = fmax(e, fabs(B[i * nrhs + c]));
+        }
+        atomic_max_nonneg(out + 3 * c, a);
+        atomic_max_nonneg(out + 3 * c + 1, b);
+        atomic_max_nonneg(out + 3 * c + 2, e);
     }
-    red[0][threadIdx.x] = a;
-    red[1][threadIdx.x] = b;
-    red[2][threadIdx.x] = e;
-    __syncthreads();
-    for (int o = THREADS / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o)
-            for (int q = 0; q < 3; ++q)
-                red[q][threadIdx.x] = fmax(red[q][threadIdx.x], red[q][threadIdx.x + o]);
-        __syncthreads();
-    }
-    if (threadIdx.x < 3) out[3 * c + threadIdx.x] = red[threadIdx.x][0];
 }
 
 template <class T>
@@ -656,11 +759,28 @@ void launch_apply_L(const DevSym &d, const T *front, const T *Z, T *Out, T *W,
     apply_L_kernel<T><<<count, THREADS, 0, st>>>(d, front, Z, Out, W, items, nrhs);
 }
 
+void launch_permute_in_rm(const double *B, int64_t ldb, double *Bp, const int32_t *perm, int64_t n,
+                          int64_t nrhs, cudaStream_t st) {
+    permute_in_rm_kernel<<<grid_for(n * nrhs), THREADS, 0, st>>>(B, ldb, Bp, perm, n, nrhs);
+}
+
+void launch_permute_out_rm(const double *X, double *B, int64_t ldb, const int32_t *perm, int64_t n,
+                           int64_t nrhs, cudaStream_t st) {
+    permute_out_rm_kernel<<<grid_for(n * nrhs), THREADS, 0, st>>>(X, B, ldb, perm, n, nrhs);
+}
+
+template <class Tc>
+void launch_transpose(Tc *C, double *Rm, int64_t n, int64_t nrhs, int dir, int accumulate,
+                      cudaStream_t st) {
+    dim3 grid((unsigned)((n + 31) / 32), (unsigned)((nrhs + 31) / 32));
+    transpose_kernel<Tc><<<grid, dim3(32, 8), 0, st>>>(C, Rm, n, nrhs, dir, accumulate);
+}
+
 void launch_spmv_residual(const DevSym &d, const double *X, const double *Bp, double *R,
                           int64_t nrhs, cudaStream_t st) {
-    const int64_t warps = d.n;
-    spmv_residual_kernel<<<(int)((warps * 32 + THREADS - 1) / THREADS), THREADS, 0, st>>>(d, X, Bp, R,
-                                                                                       nrhs);
+    const int blocks = (int)((d.n * 32 + THREADS - 1) / THREADS);
+    if (nrhs <= 8) spmv_rm_narrow_kernel<<<blocks, THREADS, 0, st>>>(d, X, Bp, R, (int)nrhs);
+    else spmv_rm_wide_kernel<<<blocks, THREADS, 0, st>>>(d, X, Bp, R, (int)nrhs);
 }
 
 void launch_norm_inf_rows(const DevSym &d, double *out, cudaStream_t st) {
@@ -670,7 +790,9 @@ void launch_norm_inf_rows(const DevSym &d, double *out, cudaStream_t st) {
 
 void launch_colmax3(const double *R, const double *X, const double *Bp, int64_t n, int64_t nrhs,
                     double *out3, cudaStream_t st) {
-    colmax3_kernel<<<(int)nrhs, THREADS, 0, st>>>(R, X, Bp, n, out3);
+    cudaMemsetAsync(out3, 0, 3 * nrhs * sizeof(double), st);
+    const int64_t rpb = 512;
+    colmax3_rm_kernel<<<(int)((n + rpb - 1) / rpb), 64, 0, st>>>(R, X, Bp, n, (int)nrhs, rpb, out3);
 }
 
 template <class T>
@@ -719,6 +841,7 @@ void launch_export_panels(const DevSym &d, const T *front, double *panels, const
     template void launch_apply_L<T>(const DevSym &, const T *, const T *, T *, T *,              \
                                     const int4 *, int, int, cudaStream_t);                       \
     template void launch_axpy_into<T>(double *, const T *, int64_t, int, cudaStream_t);          \
+    template void launch_transpose<T>(T *, double *, int64_t, int64_t, int, int, cudaStream_t);  \
     template void launch_cast<T>(const double *, T *, int64_t, cudaStream_t);                    \
     template void launch_logdet_partial<T>(const DevSym &, const T *, double *, int,             \
                                            cudaStream_t);                                        \
