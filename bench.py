@@ -46,11 +46,15 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["2d", "1d"], default="2d")
+    p.add_argument("--workload", choices=["2d", "2d_small", "1d"], default="2d",
+                   help="2d: 256x256 cells (N=65,536, the benchmark); 2d_small: 128x128 "
+                        "(N=16,384, for profiler captures); 1d: 1024 cells")
     p.add_argument("--nrhs", type=int, default=None)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-replay", action="store_true",
+                   help="skip the profiled replay (per-kernel events)")
     p.add_argument("--cpu-flops", type=float, default=1.2e10,
                    help="flop budget of the oracle's bounded sample")
     return p.parse_args()
@@ -181,6 +185,9 @@ def make_workload(kind: str, nrhs: int | None, device: str):
     if kind == "2d":
         dim, J, ker, nug, nr = 2, 8, Kernel("matern32", 0.1), 1e-3, 64
         name = "2d_haar_256x256_matern32_l0.1_nugget1e-3"
+    elif kind == "2d_small":
+        dim, J, ker, nug, nr = 2, 7, Kernel("matern32", 0.1), 1e-3, 64
+        name = "2d_haar_128x128_matern32_l0.1_nugget1e-3"
     else:
         dim, J, ker, nug, nr = 1, 10, Kernel("exponential", 0.2), 1e-2, 1
         name = "1d_haar_1024_exp_l0.2_nugget1e-2"
@@ -259,7 +266,8 @@ def run_ours(args):
     w = make_workload(args.workload, args.nrhs, "cuda")
     N, nr = w["basis"].N, w["nrhs"]
     s = wd.Solver(profile=False).analyze(w["colptr"], w["rowidx"], w["basis"])
-    sp = wd.Solver(profile=True).analyze(w["colptr"], w["rowidx"], w["basis"])
+    sp = None if args.no_replay else wd.Solver(profile=True).analyze(w["colptr"], w["rowidx"],
+                                                                      w["basis"])
     info = s.info()
     flops_factor = info["flops_factor"]
     flops_solve = 4.0 * info["nnz_L"] * nr
@@ -313,11 +321,13 @@ def run_ours(args):
     ms_mixed, _, launches, solve_info = timed(s, "mixed", args.steps, args.warmup)
     clk = clocks.stop()
     # the same steps again with CUDA events around every kernel launch
-    ms_mixed_prof, kstats, _, _ = timed(sp, "mixed", args.steps, 1)
+    ms_mixed_prof, kstats = None, []
+    if not args.no_replay:
+        ms_mixed_prof, kstats, _, _ = timed(sp, "mixed", args.steps, 1)
     res_fp64 = None
     if not args.no_fp64:
         ms64, _, _, si64 = timed(s, "fp64", max(2, args.steps // 2), 2)
-        _, kst64, _, _ = timed(sp, "fp64", 1, 1)
+        kst64 = [] if args.no_replay else timed(sp, "fp64", 1, 1)[1]
         res_fp64 = {"ms_per_step": ms64,
                     "tflops": dist.sum(flops_step) / (ms64 / 1e3) / 1e12,
                     "backward_error": si64["backward_error"], "phases_ms": si64["phases_ms"],
