@@ -24,7 +24,7 @@ constexpr int RG = 16;             // right-hand sides per solve block (solve_ke
 constexpr int ROWS_PER_CTA = 256;  // one thread per front row (gather / apply_L)
 
 enum LaunchKind {
-    K_INIT, K_POTRF_FIRST, K_PANEL, K_UPDATE, K_SYRK,          // factor
+    K_INIT, K_POTRF, K_PANEL, K_UPDATE, K_SYRK,          // factor
     K_FWD_GATHER, K_FWD_DIAG_FIRST, K_FWD_UPDATE, K_FWD_RGEMM, // forward solve
     K_BWD_INIT, K_BWD_STEP,                                    // backward solve
     K_APPLY_L
@@ -41,7 +41,7 @@ struct Launch {
 };
 
 const char *kind_name(int k) {
-    static const char *names[] = {"front_init", "potrf_first", "panel_trsm", "schur_update",
+    static const char *names[] = {"front_init", "potrf_diag", "panel_trsm", "schur_update",
                                   "schur_syrk", "fwd_gather", "fwd_diag_first", "fwd_update",
                                   "fwd_rgemm", "bwd_init", "bwd_step", "apply_L"};
     return names[k];
@@ -124,6 +124,9 @@ struct wd_ctx {
     double *d_B = nullptr, *d_Bp = nullptr, *d_X = nullptr, *d_R = nullptr, *d_cm = nullptr;
     int64_t W_rows = 0;   // sum of (m_s - k_s)
     int64_t nnz_full = 0;  // stored entries of the full CSR of P A P^T
+    int4 *d_spmv_chunks = nullptr, *d_spmv_fin = nullptr;
+    int n_spmv_chunks = 0, n_spmv_fin = 0, n_spmv_slots = 0;
+    double *d_P = nullptr;  // partial sums of chunked rows (slots x nrhs)
     double normA = 0.0;
     wd_info info{};
     // profiling
@@ -288,20 +291,21 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p) {
             by += 12.0 * (double)(S.pcp[S.sfirst[s + 1]] - S.pcp[S.sfirst[s]]);
         }
         add_launch(p, K_INIT, f0, 0, 0, el, by);
-        f0 = p.items.size();
         int kmax = 0;
         double fl = 0;
-        el = 0;
-        for (int i = b; i < e; ++i) {
-            const int s = S.level_nodes[i];
-            p.items.push_back({s, 0, 0, 0});
-            kmax = std::max(kmax, S.k(s));
-            const double nb = std::min(NB, S.k(s));
-            fl += 2 * nb * nb * nb / 3;
-            el += nb * (nb + 1) + NB * NB;
-        }
-        add_launch(p, K_POTRF_FIRST, f0, 0, fl, el, 0);
+        for (int i = b; i < e; ++i) kmax = std::max(kmax, S.k(S.level_nodes[i]));
         for (int kb = 0; kb < kmax; kb += NB) {
+            f0 = p.items.size();
+            fl = el = 0;
+            for (int i = b; i < e; ++i) {
+                const int s = S.level_nodes[i];
+                if (S.k(s) <= kb) continue;
+                p.items.push_back({s, kb, 0, 0});
+                const double nb = std::min(NB, S.k(s) - kb);
+                fl += 2 * nb * nb * nb / 3;
+                el += nb * (nb + 1) + NB * NB;
+            }
+            add_launch(p, K_POTRF, f0, kb, fl, el, 0);
             f0 = p.items.size();
             fl = el = 0;
             for (int i = b; i < e; ++i) {
@@ -333,8 +337,6 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p) {
                 const double ent = cw * (cw + 1) / 2 + below * cw;
                 fl += 2.0 * nb * ent;
                 el += 2.0 * ent + (double)(m - t0) * nb;
-                const double nb2 = std::min(NB, k - t0);
-                fl += 2 * nb2 * nb2 * nb2 / 3;
             }
             add_launch(p, K_UPDATE, f0, kb, fl, el, 0);
         }
@@ -645,6 +647,32 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
         h->d_csr_src = const_cast<int32_t *>(p);
     }
     CK(h->mem.alloc((void **)&h->d_csr_val, nnzf * sizeof(double)), "values alloc");
+    {
+        // residual work items: rows cut into chunks of at most SPMV_CHUNK entries
+        std::vector<int4> ch, fin;
+        int slots = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t b0 = cptr[i], b1 = cptr[i + 1];
+            const int64_t nc = (b1 - b0 + wd::SPMV_CHUNK - 1) / wd::SPMV_CHUNK;
+            if (nc <= 1) {
+                ch.push_back({(int)i, (int)b0, (int)b1, -1});
+                continue;
+            }
+            fin.push_back({(int)i, slots, (int)nc, 0});
+            for (int64_t q = 0; q < nc; ++q) {
+                const int64_t e0 = b0 + q * wd::SPMV_CHUNK;
+                ch.push_back({(int)i, (int)e0, (int)std::min(b1, e0 + wd::SPMV_CHUNK), slots++});
+            }
+        }
+        h->n_spmv_chunks = (int)ch.size();
+        h->n_spmv_fin = (int)fin.size();
+        h->n_spmv_slots = slots;
+        CK(h->mem.alloc((void **)&h->d_spmv_chunks, ch.size() * sizeof(int4)), "spmv items");
+        CK(cudaMemcpy(h->d_spmv_chunks, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice), "upload");
+        CK(h->mem.alloc((void **)&h->d_spmv_fin, std::max<size_t>(fin.size(), 1) * sizeof(int4)), "spmv items");
+        if (!fin.empty())
+            CK(cudaMemcpy(h->d_spmv_fin, fin.data(), fin.size() * sizeof(int4), cudaMemcpyHostToDevice), "upload");
+    }
     d.csr_val = h->d_csr_val;
     CK(h->mem.alloc((void **)&h->d_status, sizeof(status_t)), "status alloc");
     CK(h->mem.alloc((void **)&h->d_scalars, 1024 * sizeof(double)), "scalars alloc");
@@ -799,7 +827,7 @@ static void enqueue_factor_plan(wd_handle h, cudaStream_t st, bool prof) {
         if (prof) record_event(h->prof_ev[2 * li], st);
         switch (L.kind) {
             case K_INIT: wd::launch_front_init<T>(d, F, it, L.count, st); break;
-            case K_POTRF_FIRST: wd::launch_potrf_first<T>(d, F, Dv, it, L.count, h->d_status, st); break;
+            case K_POTRF: wd::launch_potrf<T>(d, F, Dv, it, L.count, h->d_status, st); break;
             case K_PANEL: wd::launch_panel<T>(d, F, Dv, it, L.count, L.arg, st); break;
             case K_UPDATE: wd::launch_schur<T>(d, F, Dv, it, L.count, L.arg, 0, h->d_status, st); break;
             case K_SYRK: wd::launch_schur<T>(d, F, Dv, it, L.count, 0, 1, h->d_status, st); break;
@@ -903,7 +931,7 @@ static wd_status ensure_solve_ws(wd_handle h, int64_t nrhs) {
     if (h->ws_cols >= nrhs) return WD_OK;
     h->work.free_all();
     h->d_Y = h->d_W = nullptr;
-    h->d_B = h->d_Bp = h->d_X = h->d_R = h->d_cm = nullptr;
+    h->d_B = h->d_Bp = h->d_X = h->d_R = h->d_cm = h->d_P = nullptr;
     h->splan = Plan();
     h->aplan = Plan();
     h->splan_nrhs = h->aplan_nrhs = -1;
@@ -916,6 +944,7 @@ static wd_status ensure_solve_ws(wd_handle h, int64_t nrhs) {
     CK(h->work.alloc((void **)&h->d_X, n * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc((void **)&h->d_R, n * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc((void **)&h->d_cm, 3 * nrhs * sizeof(double)), "solve ws");
+    CK(h->work.alloc((void **)&h->d_P, std::max(h->n_spmv_slots, 1) * nrhs * sizeof(double)), "solve ws");
     h->ws_cols = nrhs;
     return WD_OK;
 }
@@ -962,7 +991,8 @@ static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cud
     const int64_t n = h->S.n;
     const double nf = (double)h->nnz_full;
     prof_single(h, "spmv_residual_fp64", 0, 0, st, true);
-    wd::launch_spmv_residual(h->dsym, X, h->d_Bp, h->d_R, nrhs, st);
+    wd::launch_spmv_residual(h->dsym, h->d_spmv_chunks, h->n_spmv_chunks, h->d_spmv_fin,
+                             h->n_spmv_fin, X, h->d_Bp, h->d_R, h->d_P, nrhs, st);
     prof_single(h, "spmv_residual_fp64", 2.0 * nf * nrhs, 12.0 * nf + 24.0 * n * nrhs, st, false);
     wd::launch_colmax3(h->d_R, X, h->d_Bp, n, nrhs, h->d_cm, st);
     h->launches += 2;

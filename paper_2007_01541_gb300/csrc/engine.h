@@ -51,9 +51,10 @@ using status_t = unsigned long long;
 // ---- factorization (front_kernels.cu) ------------------------------------
 template <class T>
 void launch_front_init(const DevSym &d, T *front, const int4 *items, int count, cudaStream_t st);
+// diagonal block Cholesky + inverse; item = (front, first pivot column)
 template <class T>
-void launch_potrf_first(const DevSym &d, T *front, T *dinv, const int4 *items, int count,
-                        status_t *status, cudaStream_t st);
+void launch_potrf(const DevSym &d, T *front, T *dinv, const int4 *items, int count,
+                  status_t *status, cudaStream_t st);
 template <class T>
 void launch_panel(const DevSym &d, T *front, const T *dinv, const int4 *items, int count, int kb,
                   cudaStream_t st);
@@ -102,7 +103,10 @@ void launch_permute_out_rm(const double *X, double *B, int64_t ldb, const int32_
 template <class Tc>
 void launch_transpose(Tc *C, double *Rm, int64_t n, int64_t nrhs, int dir, int accumulate,
                       cudaStream_t st);
-void launch_spmv_residual(const DevSym &d, const double *X, const double *Bp, double *R,
+// chunks: (row, first entry, end, slot or -1); fin: (row, first slot, slots)
+constexpr int SPMV_CHUNK = 512;
+void launch_spmv_residual(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin,
+                          int nfin, const double *X, const double *Bp, double *R, double *P,
                           int64_t nrhs, cudaStream_t st);
 void launch_norm_inf_rows(const DevSym &d, double *rowsum_max, cudaStream_t st);
 void launch_colmax3(const double *R, const double *X, const double *Bp, int64_t n,

@@ -16,13 +16,11 @@
 //   front_init   assemble A's entries and gather the children's update
 //                matrices through relative row maps (no atomics: every front
 //                entry is written by exactly one thread)
-//   potrf_first  Cholesky of the first NB x NB diagonal block and the
-//                inverse of that block (kept for the panel and the solves)
 //   per pivot block kb = 0, NB, 2NB, ... < k_s:
+//     potrf      Cholesky of the NB x NB diagonal block and the inverse of
+//                that block (kept for the panel and the solves)
 //     panel      L21 := F21 L11^-T  as a product with the stored inverse
-//     update     pivot columns [kb+NB, k) of the trailing rows -= L21 L21^T;
-//                the tile holding the next diagonal block also factors and
-//                inverts it
+//     update     pivot columns [kb+NB, k) of the trailing rows -= L21 L21^T
 //   syrk         U = F22 - L(R, 0:k) L(R, 0:k)^T, one product with the whole
 //                pivot width as inner dimension
 // Tiles are staged into shared memory with cp.async (many loads in flight
@@ -111,165 +109,181 @@ __global__ void __launch_bounds__(THREADS) front_init_kernel(DevSym d, T *__rest
 }
 
 // ---------------------------------------------------------------------------
-// Cholesky of an nb x nb diagonal block (nb <= NB) in shared memory, then the
-// inverse of the factor, written zero-padded as an NB x NB lower-triangular
-// matrix (column-major) to Dinv.  Blocked by 16: each 16 x 16 diagonal
-// sub-block is factored by one warp in registers (shuffles, no block
-// barrier), followed by the sub-panel solve and the trailing update.  A pivot
-// that is not positive records its global column in *status (smallest wins)
-// and is replaced by 1 so that the arithmetic stays finite.
-// Must be called by all THREADS threads.
+// Cholesky of an nb x nb diagonal block (nb <= NB = 64) and the inverse of the
+// factor, written zero-padded as an NB x NB lower-triangular matrix
+// (column-major) to Dinv.  2 x 2 blocks of 32: each 32 x 32 diagonal block is
+// factored by one warp with one row per lane in registers (shuffles, no block
+// barrier); the off-diagonal block is solved and the trailing block updated
+// by both warps; the two diagonal inverses are computed one column per lane,
+// and X21 = -X22 L21 X11.  A pivot that is not positive records its global
+// column in *status (smallest wins) and is replaced by 1 so that the
+// arithmetic stays finite.  Must be called by a block of exactly NB threads.
 // ---------------------------------------------------------------------------
-constexpr int SB = 16;
+constexpr int HB = 32;
+
+// factor A[o:o+w, o:o+w] in place (w <= 32); one warp, lane = row
+template <class T>
+__device__ __forceinline__ void chol32_warp(T (*A)[NB + 1], int o, int w, int64_t gcol0,
+                                            status_t *status, T *invd) {
+    const int lane = threadIdx.x & 31;
+    T a[HB];
+#pragma unroll
+    for (int c = 0; c < HB; ++c) a[c] = (lane < w && c <= lane) ? A[o + lane][o + c] : T(0);
+#pragma unroll
+    for (int j = 0; j < HB; ++j) {
+        if (j < w) {
+            T dj = __shfl_sync(0xffffffffu, a[j], j);
+            if (!(dj > T(0))) {
+                if (lane == 0) atomicMin(status, (status_t)(gcol0 + o + j));
+                dj = T(1);
+            }
+            const T sj = dev_sqrt(dj);
+            if (lane == j) a[j] = sj;
+            else if (lane > j) a[j] = a[j] / sj;
+#pragma unroll
+            for (int c = j + 1; c < HB; ++c) {
+                const T lc = __shfl_sync(0xffffffffu, a[j], c);
+                if (lane >= c) a[c] -= a[j] * lc;
+            }
+        }
+    }
+    if (lane < w) {
+#pragma unroll
+        for (int c = 0; c < HB; ++c)
+            if (c <= lane) A[o + lane][o + c] = a[c];
+        invd[o + lane] = T(1) / a[lane];
+    }
+}
+
+// column `lane` of inv(A[o:o+w, o:o+w]) (lower) into X[o:o+w, o+lane]
+template <class T>
+__device__ __forceinline__ void inv32_warp(const T (*A)[NB + 1], T (*X)[NB + 1], int o, int w,
+                                           const T *invd) {
+    const int c = threadIdx.x & 31;
+    T x[HB];
+#pragma unroll
+    for (int r = 0; r < HB; ++r) {
+        T acc0 = (r == c) ? T(1) : T(0), acc1 = T(0);
+#pragma unroll
+        for (int p = 0; p + 1 < r; p += 2) {
+            acc0 -= A[o + r][o + p] * x[p];
+            acc1 -= A[o + r][o + p + 1] * x[p + 1];
+        }
+        if (r & 1) acc0 -= A[o + r][o + r - 1] * x[r - 1];
+        x[r] = (r >= c && r < w && c < w) ? (acc0 + acc1) * invd[o + r] : T(0);
+    }
+#pragma unroll
+    for (int r = 0; r < HB; ++r) X[o + r][o + c] = x[r];
+}
 
 template <class T>
 __device__ void block_potrf_inv(T *F, int ld, int nb, int64_t gcol0, status_t *status, T *Dinv,
                                 T *smem) {
     T(*A)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
     T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem + NB * (NB + 1));
-    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-    for (int idx = tid; idx < nb * nb; idx += THREADS) {
-        const int r = idx % nb, c = idx / nb;
-        if (r >= c) A[r][c] = F[(int64_t)c * ld + r];
-    }
+    T *invd = smem + 2 * NB * (NB + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int w1 = min(HB, nb), w2 = nb - w1;
+    for (int c = 0; c < nb; ++c)
+        if (tid >= c && tid < nb) cp_async_elem(&A[tid][c], F + (int64_t)c * ld + tid, true);
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
-    for (int jb = 0; jb < nb; jb += SB) {
-        const int w = min(SB, nb - jb);
-        if (warp == 0) {
-            T v[SB];
+    if (warp == 0) chol32_warp<T>(A, 0, w1, gcol0, status, invd);
+    __syncthreads();
+    if (w2 > 0) {
+        // L21 = A21 L11^-T, one row per thread of warp 1
+        if (warp == 1 && lane < w2) {
+            const int r = HB + lane;
+            T x[HB];
 #pragma unroll
-            for (int c = 0; c < SB; ++c) v[c] = (lane < w && c <= lane) ? A[jb + lane][jb + c] : T(0);
+            for (int c = 0; c < HB; ++c) x[c] = A[r][c];
 #pragma unroll
-            for (int c = 0; c < SB; ++c) {
-                if (c < w) {
-                    T dcc = __shfl_sync(0xffffffffu, v[c], c);
-                    if (!(dcc > T(0))) {
-                        if (lane == 0) atomicMin(status, (status_t)(gcol0 + jb + c));
-                        dcc = T(1);
-                    }
-                    const T piv = dev_sqrt(dcc);
-                    if (lane == c) v[c] = piv;
-                    else if (lane > c) v[c] = v[c] / piv;
+            for (int c = 0; c < HB; ++c) {
+                T acc0 = x[c], acc1 = T(0);
 #pragma unroll
-                    for (int c2 = c + 1; c2 < SB; ++c2) {
-                        const T lc2 = __shfl_sync(0xffffffffu, v[c], c2);
-                        if (lane >= c2) v[c2] -= v[c] * lc2;
-                    }
+                for (int p = 0; p + 1 < c; p += 2) {
+                    acc0 -= x[p] * A[c][p];
+                    acc1 -= x[p + 1] * A[c][p + 1];
                 }
+                if (c & 1) acc0 -= x[c - 1] * A[c][c - 1];
+                x[c] = (acc0 + acc1) * invd[c];
             }
-            if (lane < w) {
 #pragma unroll
-                for (int c = 0; c < SB; ++c)
-                    if (c <= lane) A[jb + lane][jb + c] = v[c];
-            }
+            for (int c = 0; c < HB; ++c) A[r][c] = x[c];
         }
+        if (warp == 0) inv32_warp<T>(A, X, 0, w1, invd);
         __syncthreads();
-        const int rem = nb - jb - w;
-        if (tid < rem) {
-            const int i = jb + w + tid;
-            T x[SB];
+        // A22 -= L21 L21^T (lower)
+        for (int idx = tid; idx < HB * HB; idx += NB) {
+            const int r = idx % HB, c = idx / HB;
+            if (r >= c && r < w2) {
+                T acc0 = T(0), acc1 = T(0);
 #pragma unroll
-            for (int c = 0; c < SB; ++c) x[c] = c < w ? A[i][jb + c] : T(0);
-#pragma unroll
-            for (int c = 0; c < SB; ++c) {
-                if (c < w) {
-                    T acc = x[c];
-#pragma unroll
-                    for (int p = 0; p < c; ++p) acc -= x[p] * A[jb + c][jb + p];
-                    x[c] = acc / A[jb + c][jb + c];
+                for (int p = 0; p < HB; p += 2) {
+                    acc0 += A[HB + r][p] * A[HB + c][p];
+                    acc1 += A[HB + r][p + 1] * A[HB + c][p + 1];
                 }
-            }
-#pragma unroll
-            for (int c = 0; c < SB; ++c)
-                if (c < w) A[i][jb + c] = x[c];
-        }
-        __syncthreads();
-        for (int idx = tid; idx < rem * rem; idx += THREADS) {
-            const int i = jb + w + idx % rem, j = jb + w + idx / rem;
-            if (i >= j) {
-                T acc = T(0);
-                for (int c = 0; c < w; ++c) acc += A[i][jb + c] * A[j][jb + c];
-                A[i][j] -= acc;
+                A[HB + r][HB + c] -= acc0 + acc1;
             }
         }
         __syncthreads();
-    }
-    for (int idx = tid; idx < nb * nb; idx += THREADS) {
-        const int rr = idx % nb, c = idx / nb;
-        if (rr >= c) F[(int64_t)c * ld + rr] = A[rr][c];
-    }
-    // X := A^-1, blocked by 16: diagonal inverses (one warp each), then the
-    // off-diagonal blocks X(bi, bj) = -X(bi, bi) sum_k A(bi, k) X(k, bj)
-    const int nsb = (nb + SB - 1) / SB;
-    for (int idx = tid; idx < NB * NB; idx += THREADS) X[idx % NB][idx / NB] = T(0);
-    __syncthreads();
-    if (warp < nsb && lane < SB) {
-        const int b0 = warp * SB, c = lane;
-        const int wv = min(SB, nb - b0);
-        T x[SB];
-#pragma unroll
-        for (int r = 0; r < SB; ++r) {
-            if (r < wv) {
-                T acc = (r == c) ? T(1) : T(0);
-#pragma unroll
-                for (int p = 0; p < r; ++p) acc -= A[b0 + r][b0 + p] * x[p];
-                x[r] = acc / A[b0 + r][b0 + r];
-            } else {
-                x[r] = T(0);
-            }
-        }
-        if (c < wv) {
-#pragma unroll
-            for (int r = 0; r < SB; ++r)
-                if (r < wv && r >= c) X[b0 + r][b0 + c] = x[r];
-        }
-    }
-    __syncthreads();
-    for (int bi = 1; bi < nsb; ++bi) {
-        const int r0 = bi * SB, wr = min(SB, nb - r0);
-        // T(bj) = sum_{k = bj .. bi-1} A(bi, k) X(k, bj), stored in X(bi, bj)
-        for (int idx = tid; idx < bi * SB * SB; idx += THREADS) {
-            const int bj = idx / (SB * SB), r = idx % SB, c = (idx / SB) % SB;
-            if (r < wr) {
-                T acc = T(0);
-                for (int p = bj * SB + c; p < r0; ++p) acc += A[r0 + r][p] * X[p][bj * SB + c];
-                X[r0 + r][bj * SB + c] = acc;
-            }
+        if (warp == 1) {
+            chol32_warp<T>(A, HB, w2, gcol0, status, invd);
+            __syncwarp();
+            inv32_warp<T>(A, X, HB, w2, invd);
         }
         __syncthreads();
-        T out[(SB * SB * (NB / SB)) / THREADS + 1];
-        int q = 0;
-        for (int idx = tid; idx < bi * SB * SB; idx += THREADS, ++q) {
-            const int bj = idx / (SB * SB), r = idx % SB, c = (idx / SB) % SB;
+        // X21 = -X22 (L21 X11): first T = L21 X11 into X[HB + r][c]
+        for (int idx = tid; idx < HB * HB; idx += NB) {
+            const int r = idx % HB, c = idx / HB;
             T acc = T(0);
-            for (int p = 0; p <= r && p < wr; ++p) acc += X[r0 + r][r0 + p] * X[r0 + p][bj * SB + c];
+            if (r < w2 && c < w1)
+                for (int p = c; p < HB; ++p) acc += A[HB + r][p] * X[p][c];
+            X[HB + r][c] = acc;
+        }
+        __syncthreads();
+        T out[HB * HB / NB];
+#pragma unroll
+        for (int q = 0; q < HB * HB / NB; ++q) {
+            const int idx = tid + q * NB, r = idx % HB, c = idx / HB;
+            T acc = T(0);
+            for (int p = 0; p <= r; ++p) acc += X[HB + r][HB + p] * X[HB + p][c];
             out[q] = -acc;
         }
         __syncthreads();
-        q = 0;
-        for (int idx = tid; idx < bi * SB * SB; idx += THREADS, ++q) {
-            const int bj = idx / (SB * SB), r = idx % SB, c = (idx / SB) % SB;
-            if (r < wr) X[r0 + r][bj * SB + c] = out[q];
+#pragma unroll
+        for (int q = 0; q < HB * HB / NB; ++q) {
+            const int idx = tid + q * NB, r = idx % HB, c = idx / HB;
+            X[HB + r][c] = (r < w2 && c < w1) ? out[q] : T(0);
         }
-        __syncthreads();
+    } else {
+        if (warp == 0) inv32_warp<T>(A, X, 0, w1, invd);
+        for (int idx = tid; idx < NB * NB; idx += NB) {
+            const int r = idx % NB, c = idx / NB;
+            if (r >= HB || c >= HB) X[r][c] = T(0);
+        }
     }
-    for (int idx = tid; idx < NB * NB; idx += THREADS) {
-        const int rr = idx % NB, c = idx / NB;
-        Dinv[idx] = (rr >= c) ? X[rr][c] : T(0);
-    }
+    __syncthreads();
+    for (int c = 0; c < nb; ++c)
+        if (tid >= c && tid < nb) F[(int64_t)c * ld + tid] = A[tid][c];
+    for (int c = 0; c < NB; ++c) Dinv[(int64_t)c * NB + tid] = (tid >= c) ? X[tid][c] : T(0);
     __syncthreads();
 }
 
+// diagonal block starting at pivot column j0 = item.y of front item.x
 template <class T>
-__global__ void __launch_bounds__(THREADS) potrf_first_kernel(DevSym d, T *__restrict__ front,
-                                                              T *__restrict__ dinv,
-                                                              const int4 *__restrict__ items,
-                                                              status_t *status) {
+__global__ void __launch_bounds__(NB, 1) potrf_kernel(DevSym d, T *__restrict__ front,
+                                                   T *__restrict__ dinv,
+                                                   const int4 *__restrict__ items,
+                                                   status_t *status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int s = items[blockIdx.x].x;
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, j0 = it.y;
     const Dims z = dims(d, s);
-    block_potrf_inv<T>(front + d.foff[s], z.ld, min(NB, z.k), d.sfirst[s], status,
-                       dinv + d.dinvoff[s], reinterpret_cast<T *>(smem_raw));
+    block_potrf_inv<T>(front + d.foff[s] + (int64_t)j0 * z.ld + j0, z.ld, min(NB, z.k - j0),
+                       d.sfirst[s] + j0, status, dinv + d.dinvoff[s] + (int64_t)(j0 / NB) * NB * NB,
+                       reinterpret_cast<T *>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
@@ -323,7 +337,6 @@ __global__ void __launch_bounds__(THREADS) panel_kernel(DevSym d, T *__restrict_
 // columns ty + 16 j (i < 8, j < 4).
 //   mode 0 (step):  base = kb + NB, ka = kb, K = NB, cmax = k
 //   mode 1 (syrk):  base = kp, ka = 0, K = k, cmax = mp
-// In mode 0 the tile (0, 0) then factors and inverts the next diagonal block.
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(THREADS) schur_kernel(DevSym d, T *__restrict__ front,
@@ -403,30 +416,20 @@ __global__ void __launch_bounds__(THREADS) schur_kernel(DevSym d, T *__restrict_
             if (r < z.mp && r >= c) F[(int64_t)c * z.ld + r] -= acc[i][j];
         }
     }
-    if (mode == 0 && ti == 0 && tj == 0 && base < z.k) {
-        __syncthreads();
-        block_potrf_inv<T>(F + (int64_t)base * z.ld + base, z.ld, min(NB, z.k - base),
-                           d.sfirst[s] + base, status,
-                           dinv + d.dinvoff[s] + (int64_t)(base / NB) * NB * NB,
-                           reinterpret_cast<T *>(smem_raw));
-    }
 }
 
 template <class T>
-constexpr size_t potrf_smem() { return 2 * sizeof(T) * NB * (NB + 1); }
+constexpr size_t potrf_smem() { return sizeof(T) * (2 * NB * (NB + 1) + NB); }
 template <class T>
 constexpr size_t panel_smem() { return sizeof(T) * (NB * RB + NB * NB); }
 template <class T>
-constexpr size_t schur_smem() {
-    return (2 * sizeof(T) * BK * (BM + BN) > potrf_smem<T>()) ? 2 * sizeof(T) * BK * (BM + BN)
-                                                              : potrf_smem<T>();
-}
+constexpr size_t schur_smem() { return 2 * sizeof(T) * BK * (BM + BN); }
 
 template <class T>
 void set_smem_attrs() {
     static bool done = false;  // per instantiation and process
     if (done) return;
-    cudaFuncSetAttribute(potrf_first_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(potrf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)potrf_smem<T>());
     cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)panel_smem<T>());
@@ -450,11 +453,11 @@ void launch_front_init(const DevSym &d, T *front, const int4 *items, int count, 
 }
 
 template <class T>
-void launch_potrf_first(const DevSym &d, T *front, T *dinv, const int4 *items, int count,
-                        status_t *status, cudaStream_t st) {
+void launch_potrf(const DevSym &d, T *front, T *dinv, const int4 *items, int count,
+                  status_t *status, cudaStream_t st) {
     if (count <= 0) return;
     set_smem_attrs<T>();
-    potrf_first_kernel<T><<<count, THREADS, potrf_smem<T>(), st>>>(d, front, dinv, items, status);
+    potrf_kernel<T><<<count, NB, potrf_smem<T>(), st>>>(d, front, dinv, items, status);
 }
 
 template <class T>
@@ -475,8 +478,8 @@ void launch_schur(const DevSym &d, T *front, T *dinv, const int4 *items, int cou
 
 #define WD_INST(T)                                                                               \
     template void launch_front_init<T>(const DevSym &, T *, const int4 *, int, cudaStream_t);    \
-    template void launch_potrf_first<T>(const DevSym &, T *, T *, const int4 *, int, status_t *, \
-                                        cudaStream_t);                                           \
+    template void launch_potrf<T>(const DevSym &, T *, T *, const int4 *, int, status_t *,       \
+                                  cudaStream_t);                                                 \
     template void launch_panel<T>(const DevSym &, T *, const T *, const int4 *, int, int,        \
                                   cudaStream_t);                                                 \
     template void launch_schur<T>(const DevSym &, T *, T *, const int4 *, int, int, int,         \

@@ -490,18 +490,26 @@ __global__ void transpose_kernel(Tc *__restrict__ C, double *__restrict__ Rm, in
 }
 
 // R = Bp - A_p X in FP64 on the full CSR of P A P^T (row-major vectors).
-// Many right-hand sides: one warp per row, lanes over right-hand sides.
-__global__ void __launch_bounds__(THREADS) spmv_rm_wide_kernel(DevSym d, const double *__restrict__ X,
-                                                               const double *__restrict__ Bp,
-                                                               double *__restrict__ R, int nrhs) {
-    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+// The rows of the coarsest wavelets are dense, so rows are cut into chunks
+// of at most SPMV_CHUNK entries: a chunk item is (row, first entry, end,
+// slot); slot < 0 means the whole row, written to R directly; otherwise the
+// partial sums go to P[slot] and a second pass adds a row's slots in order.
+// Many right-hand sides: one warp per chunk, lanes over right-hand sides.
+__global__ void __launch_bounds__(THREADS) spmv_wide_kernel(DevSym d, const int4 *__restrict__ items,
+                                                            int count, const double *__restrict__ X,
+                                                            const double *__restrict__ Bp,
+                                                            double *__restrict__ R,
+                                                            double *__restrict__ P, int nrhs) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (row >= d.n) return;
-    const int64_t e0 = d.csr_ptr[row], e1 = d.csr_ptr[row + 1];
+    if (w >= count) return;
+    const int4 it = items[w];
+    const int64_t row = it.x;
+    const int e0 = it.y, e1 = it.z, slot = it.w;
     for (int c0 = 0; c0 < nrhs; c0 += 64) {
         const int ca = c0 + lane, cb = c0 + 32 + lane;
         double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
-        int64_t e = e0;
+        int e = e0;
         for (; e + 1 < e1; e += 2) {
             const double v0 = d.csr_val[e], v1 = d.csr_val[e + 1];
             const double *x0 = X + (int64_t)d.csr_col[e] * nrhs;
@@ -521,23 +529,32 @@ __global__ void __launch_bounds__(THREADS) spmv_rm_wide_kernel(DevSym d, const d
             if (ca < nrhs) a0 += v0 * x0[ca];
             if (cb < nrhs) b0 += v0 * x0[cb];
         }
-        if (ca < nrhs) R[row * nrhs + ca] = Bp[row * nrhs + ca] - (a0 + a1);
-        if (cb < nrhs) R[row * nrhs + cb] = Bp[row * nrhs + cb] - (b0 + b1);
+        if (slot < 0) {
+            if (ca < nrhs) R[row * nrhs + ca] = Bp[row * nrhs + ca] - (a0 + a1);
+            if (cb < nrhs) R[row * nrhs + cb] = Bp[row * nrhs + cb] - (b0 + b1);
+        } else {
+            if (ca < nrhs) P[(int64_t)slot * nrhs + ca] = a0 + a1;
+            if (cb < nrhs) P[(int64_t)slot * nrhs + cb] = b0 + b1;
+        }
     }
 }
 
-// Few right-hand sides (<= 8): lanes over the entries of the row.
-__global__ void __launch_bounds__(THREADS) spmv_rm_narrow_kernel(DevSym d,
-                                                                 const double *__restrict__ X,
-                                                                 const double *__restrict__ Bp,
-                                                                 double *__restrict__ R, int nrhs) {
-    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+// Few right-hand sides (<= 8): lanes over the entries of the chunk.
+__global__ void __launch_bounds__(THREADS) spmv_narrow_kernel(DevSym d, const int4 *__restrict__ items,
+                                                              int count, const double *__restrict__ X,
+                                                              const double *__restrict__ Bp,
+                                                              double *__restrict__ R,
+                                                              double *__restrict__ P, int nrhs) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (row >= d.n) return;
+    if (w >= count) return;
+    const int4 it = items[w];
+    const int64_t row = it.x;
+    const int slot = it.w;
     double acc[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc[c] = 0.0;
-    for (int64_t e = d.csr_ptr[row] + lane; e < d.csr_ptr[row + 1]; e += 32) {
+    for (int e = it.y + lane; e < it.z; e += 32) {
         const double v = d.csr_val[e];
         const double *x = X + (int64_t)d.csr_col[e] * nrhs;
 #pragma unroll
@@ -549,7 +566,25 @@ __global__ void __launch_bounds__(THREADS) spmv_rm_narrow_kernel(DevSym d,
         double a = acc[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0 && c < nrhs) R[row * nrhs + c] = Bp[row * nrhs + c] - a;
+        if (lane == 0 && c < nrhs) {
+            if (slot < 0) R[row * nrhs + c] = Bp[row * nrhs + c] - a;
+            else P[(int64_t)slot * nrhs + c] = a;
+        }
+    }
+}
+
+// rows cut into several chunks: item = (row, first slot, number of slots)
+__global__ void spmv_finish_kernel(const int4 *__restrict__ items, int count,
+                                   const double *__restrict__ Bp, double *__restrict__ R,
+                                   const double *__restrict__ P, int nrhs) {
+    const int i = blockIdx.x;
+    if (i >= count) return;
+    const int4 it = items[i];
+    const int64_t row = it.x;
+    for (int c = threadIdx.x; c < nrhs; c += blockDim.x) {
+        double acc = 0.0;
+        for (int q = 0; q < it.z; ++q) acc += P[(int64_t)(it.y + q) * nrhs + c];
+        R[row * nrhs + c] = Bp[row * nrhs + c] - acc;
     }
 }
 
@@ -776,11 +811,15 @@ void launch_transpose(Tc *C, double *Rm, int64_t n, int64_t nrhs, int dir, int a
     transpose_kernel<Tc><<<grid, dim3(32, 8), 0, st>>>(C, Rm, n, nrhs, dir, accumulate);
 }
 
-void launch_spmv_residual(const DevSym &d, const double *X, const double *Bp, double *R,
+void launch_spmv_residual(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin,
+                          int nfin, const double *X, const double *Bp, double *R, double *P,
                           int64_t nrhs, cudaStream_t st) {
-    const int blocks = (int)((d.n * 32 + THREADS - 1) / THREADS);
-    if (nrhs <= 8) spmv_rm_narrow_kernel<<<blocks, THREADS, 0, st>>>(d, X, Bp, R, (int)nrhs);
-    else spmv_rm_wide_kernel<<<blocks, THREADS, 0, st>>>(d, X, Bp, R, (int)nrhs);
+    const int blocks = (int)(((int64_t)nchunks * 32 + THREADS - 1) / THREADS);
+    if (nrhs <= 8)
+        spmv_narrow_kernel<<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, X, Bp, R, P, (int)nrhs);
+    else
+        spmv_wide_kernel<<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, X, Bp, R, P, (int)nrhs);
+    if (nfin > 0) spmv_finish_kernel<<<nfin, 64, 0, st>>>(fin, nfin, Bp, R, P, (int)nrhs);
 }
 
 void launch_norm_inf_rows(const DevSym &d, double *out, cudaStream_t st) {
