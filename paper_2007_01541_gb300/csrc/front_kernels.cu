@@ -43,6 +43,19 @@ __device__ __forceinline__ double dev_sqrt<double>(double x) { return sqrt(x); }
 template <>
 __device__ __forceinline__ float dev_sqrt<float>(float x) { return sqrtf(x); }
 
+// pivot d > 0 -> (sqrt(d), 1/sqrt(d)).  FP64: correctly rounded square root
+// and division.  FP32 (the refined mixed-precision path): the hardware
+// reciprocal square root, which keeps the serial pivot chain short; its few
+// ulps of error are far below what iterative refinement removes.
+__device__ __forceinline__ void pivot_root(double d, double &s, double &is) {
+    s = sqrt(d);
+    is = 1.0 / s;
+}
+__device__ __forceinline__ void pivot_root(float d, float &s, float &is) {
+    is = rsqrtf(d);
+    s = d * is;
+}
+
 struct Dims {
     int k, m, kp, mp, ld;
 };
@@ -111,70 +124,53 @@ __global__ void __launch_bounds__(THREADS) front_init_kernel(DevSym d, T *__rest
 // ---------------------------------------------------------------------------
 // Cholesky of an nb x nb diagonal block (nb <= NB = 64) and the inverse of the
 // factor, written zero-padded as an NB x NB lower-triangular matrix
-// (column-major) to Dinv.  2 x 2 blocks of 32: each 32 x 32 diagonal block is
-// factored by one warp with one row per lane in registers (shuffles, no block
-// barrier); the off-diagonal block is solved and the trailing block updated
-// by both warps; the two diagonal inverses are computed one column per lane,
-// and X21 = -X22 L21 X11.  A pivot that is not positive records its global
-// column in *status (smallest wins) and is replaced by 1 so that the
-// arithmetic stays finite.  Must be called by a block of exactly NB threads.
+// (column-major) to Dinv.  Right-looking by sub-blocks of 16 (loop not
+// unrolled, to keep the code small):
+//   1. one warp factors the 16 x 16 diagonal sub-block, one row per lane in
+//      registers (shuffles, no block barrier);
+//   2. the rows below are solved against it, one row per thread;
+//   3. the trailing lower part is updated with register tiles of 4 x 4.
+// The inverse: the four 16 x 16 diagonal inverses (one warp each, one column
+// per lane), then X(bi, bj) = -X(bi, bi) sum_k L(bi, k) X(k, bj) for
+// bi = 1, 2, 3.  A pivot that is not positive records its global column in
+// *status (smallest wins) and is replaced by 1 so that the arithmetic stays
+// finite.  Must be called by a block of POTRF_THREADS threads.
 // ---------------------------------------------------------------------------
-constexpr int HB = 32;
+constexpr int SB = 16;
+constexpr int POTRF_THREADS = 256;
 
-// factor A[o:o+w, o:o+w] in place (w <= 32); one warp, lane = row
-template <class T>
-__device__ __forceinline__ void chol32_warp(T (*A)[NB + 1], int o, int w, int64_t gcol0,
-                                            status_t *status, T *invd) {
-    const int lane = threadIdx.x & 31;
-    T a[HB];
-#pragma unroll
-    for (int c = 0; c < HB; ++c) a[c] = (lane < w && c <= lane) ? A[o + lane][o + c] : T(0);
-#pragma unroll
-    for (int j = 0; j < HB; ++j) {
-        if (j < w) {
-            T dj = __shfl_sync(0xffffffffu, a[j], j);
-            if (!(dj > T(0))) {
-                if (lane == 0) atomicMin(status, (status_t)(gcol0 + o + j));
-                dj = T(1);
-            }
-            const T sj = dev_sqrt(dj);
-            if (lane == j) a[j] = sj;
-            else if (lane > j) a[j] = a[j] / sj;
-#pragma unroll
-            for (int c = j + 1; c < HB; ++c) {
-                const T lc = __shfl_sync(0xffffffffu, a[j], c);
-                if (lane >= c) a[c] -= a[j] * lc;
-            }
+// Pivot C of a 16 x 16 Cholesky held by one warp, one row per lane (v),
+// then pivots C+1, ...: compile-time recursion, so every register index is a
+// constant.
+template <class T, int C>
+struct WarpChol {
+    static __device__ __forceinline__ void step(T (&v)[SB], T &myinv, int lane, int w,
+                                                int64_t gcol0, status_t *status) {
+        T dc = __shfl_sync(0xffffffffu, v[C], C);
+        if (C < w && !(dc > T(0))) {
+            if (lane == 0) atomicMin(status, (status_t)(gcol0 + C));
+            dc = T(1);
         }
-    }
-    if (lane < w) {
-#pragma unroll
-        for (int c = 0; c < HB; ++c)
-            if (c <= lane) A[o + lane][o + c] = a[c];
-        invd[o + lane] = T(1) / a[lane];
-    }
-}
-
-// column `lane` of inv(A[o:o+w, o:o+w]) (lower) into X[o:o+w, o+lane]
-template <class T>
-__device__ __forceinline__ void inv32_warp(const T (*A)[NB + 1], T (*X)[NB + 1], int o, int w,
-                                           const T *invd) {
-    const int c = threadIdx.x & 31;
-    T x[HB];
-#pragma unroll
-    for (int r = 0; r < HB; ++r) {
-        T acc0 = (r == c) ? T(1) : T(0), acc1 = T(0);
-#pragma unroll
-        for (int p = 0; p + 1 < r; p += 2) {
-            acc0 -= A[o + r][o + p] * x[p];
-            acc1 -= A[o + r][o + p + 1] * x[p + 1];
+        if (C >= w) dc = T(1);
+        T sc, ic;
+        pivot_root(dc, sc, ic);
+        if (lane == C) {
+            v[C] = sc;
+            myinv = ic;
         }
-        if (r & 1) acc0 -= A[o + r][o + r - 1] * x[r - 1];
-        x[r] = (r >= c && r < w && c < w) ? (acc0 + acc1) * invd[o + r] : T(0);
-    }
+        else if (lane > C) v[C] *= ic;
 #pragma unroll
-    for (int r = 0; r < HB; ++r) X[o + r][o + c] = x[r];
-}
+        for (int c2 = C + 1; c2 < SB; ++c2) {
+            const T lc = __shfl_sync(0xffffffffu, v[C], c2);
+            if (lane >= c2) v[c2] -= v[C] * lc;
+        }
+        WarpChol<T, C + 1>::step(v, myinv, lane, w, gcol0, status);
+    }
+};
+template <class T>
+struct WarpChol<T, SB> {
+    static __device__ __forceinline__ void step(T (&)[SB], T &, int, int, int64_t, status_t *) {}
+};
 
 template <class T>
 __device__ void block_potrf_inv(T *F, int ld, int nb, int64_t gcol0, status_t *status, T *Dinv,
@@ -183,97 +179,155 @@ __device__ void block_potrf_inv(T *F, int ld, int nb, int64_t gcol0, status_t *s
     T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem + NB * (NB + 1));
     T *invd = smem + 2 * NB * (NB + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int w1 = min(HB, nb), w2 = nb - w1;
-    for (int c = 0; c < nb; ++c)
-        if (tid >= c && tid < nb) cp_async_elem(&A[tid][c], F + (int64_t)c * ld + tid, true);
+    for (int idx = tid; idx < NB * NB; idx += POTRF_THREADS) {
+        const int r = idx % NB, c = idx / NB;
+        cp_async_elem(&A[r][c], F + (int64_t)c * ld + r, r >= c && r < nb && c < nb);
+        X[r][c] = T(0);
+    }
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    if (warp == 0) chol32_warp<T>(A, 0, w1, gcol0, status, invd);
-    __syncthreads();
-    if (w2 > 0) {
-        // L21 = A21 L11^-T, one row per thread of warp 1
-        if (warp == 1 && lane < w2) {
-            const int r = HB + lane;
-            T x[HB];
-#pragma unroll
-            for (int c = 0; c < HB; ++c) x[c] = A[r][c];
-#pragma unroll
-            for (int c = 0; c < HB; ++c) {
+#pragma unroll 1
+    for (int jb = 0; jb < nb; jb += SB) {
+        const int w = min(SB, nb - jb);
+        if (warp == 0) {
+            T v[SB], myinv = T(1);
+#pragma unroll 16
+            for (int c = 0; c < SB; ++c) v[c] = (lane < w && c <= lane) ? A[jb + lane][jb + c] : T(0);
+            WarpChol<T, 0>::step(v, myinv, lane, w, gcol0 + jb, status);
+            if (lane < w) {
+#pragma unroll 16
+                for (int c = 0; c < SB; ++c)
+                    if (c <= lane) A[jb + lane][jb + c] = v[c];
+                invd[jb + lane] = myinv;
+            }
+        }
+        __syncthreads();
+        const int rem = nb - jb - w;
+        if (tid < rem) {
+            const int i = jb + w + tid;
+            T x[SB];
+#pragma unroll 16
+            for (int c = 0; c < SB; ++c) x[c] = A[i][jb + c];
+#pragma unroll 16
+            for (int c = 0; c < SB; ++c) {
                 T acc0 = x[c], acc1 = T(0);
-#pragma unroll
+#pragma unroll 8
                 for (int p = 0; p + 1 < c; p += 2) {
-                    acc0 -= x[p] * A[c][p];
-                    acc1 -= x[p + 1] * A[c][p + 1];
+                    acc0 -= x[p] * A[jb + c][jb + p];
+                    acc1 -= x[p + 1] * A[jb + c][jb + p + 1];
                 }
-                if (c & 1) acc0 -= x[c - 1] * A[c][c - 1];
-                x[c] = (acc0 + acc1) * invd[c];
+                if (c & 1) acc0 -= x[c - 1] * A[jb + c][jb + c - 1];
+                x[c] = (acc0 + acc1) * invd[jb + c];
             }
-#pragma unroll
-            for (int c = 0; c < HB; ++c) A[r][c] = x[c];
+#pragma unroll 16
+            for (int c = 0; c < SB; ++c) A[i][jb + c] = x[c];
         }
-        if (warp == 0) inv32_warp<T>(A, X, 0, w1, invd);
         __syncthreads();
-        // A22 -= L21 L21^T (lower)
-        for (int idx = tid; idx < HB * HB; idx += NB) {
-            const int r = idx % HB, c = idx / HB;
-            if (r >= c && r < w2) {
-                T acc0 = T(0), acc1 = T(0);
-#pragma unroll
-                for (int p = 0; p < HB; p += 2) {
-                    acc0 += A[HB + r][p] * A[HB + c][p];
-                    acc1 += A[HB + r][p + 1] * A[HB + c][p + 1];
+        // trailing lower part, 2 x 4 register tiles
+        const int t0 = jb + w, ntr = (rem + 1) / 2, ntc = (rem + 3) / 4;
+        for (int q = tid; q < ntr * ntc; q += POTRF_THREADS) {
+            const int bi = q % ntr, bj = q / ntr;
+            const int r0 = t0 + 2 * bi, c0 = t0 + 4 * bj;
+            if (r0 + 1 < c0) continue;
+            T acc[2][4];
+#pragma unroll 2
+            for (int i = 0; i < 2; ++i)
+#pragma unroll 4
+                for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+#pragma unroll 4
+            for (int p = 0; p < SB; ++p) {
+                T ar[2], ac[4];
+#pragma unroll 2
+                for (int i = 0; i < 2; ++i) ar[i] = A[min(r0 + i, NB - 1)][jb + p];
+#pragma unroll 4
+                for (int j = 0; j < 4; ++j) ac[j] = A[min(c0 + j, NB - 1)][jb + p];
+#pragma unroll 2
+                for (int i = 0; i < 2; ++i)
+#pragma unroll 4
+                    for (int j = 0; j < 4; ++j) acc[i][j] += ar[i] * ac[j];
+            }
+#pragma unroll 2
+            for (int i = 0; i < 2; ++i)
+#pragma unroll 4
+                for (int j = 0; j < 4; ++j) {
+                    const int r = r0 + i, c = c0 + j;
+                    if (r < nb && c <= r) A[r][c] -= acc[i][j];
                 }
-                A[HB + r][HB + c] -= acc0 + acc1;
+        }
+        __syncthreads();
+    }
+    // X = A^-1: diagonal 16 x 16 inverses, one warp each, one column per lane
+    const int nsb = (nb + SB - 1) / SB;
+    if (warp < nsb && lane < SB) {
+        const int b0 = warp * SB, wv = min(SB, nb - b0), c = lane;
+        T x[SB];
+#pragma unroll 16
+        for (int r = 0; r < SB; ++r) {
+            T acc0 = (r == c) ? T(1) : T(0), acc1 = T(0);
+#pragma unroll 8
+            for (int p = 0; p + 1 < r; p += 2) {
+                acc0 -= A[b0 + r][b0 + p] * x[p];
+                acc1 -= A[b0 + r][b0 + p + 1] * x[p + 1];
             }
+            if (r & 1) acc0 -= A[b0 + r][b0 + r - 1] * x[r - 1];
+            x[r] = (r < wv && c < wv) ? (acc0 + acc1) * invd[min(b0 + r, NB - 1)] : T(0);
+        }
+#pragma unroll 16
+        for (int r = 0; r < SB; ++r)
+            if (r >= c) X[b0 + r][b0 + c] = x[r];
+    }
+    __syncthreads();
+    // off-diagonal blocks, one 16 x 16 block row at a time
+#pragma unroll 1
+    for (int bi = 1; bi < nsb; ++bi) {
+        const int r0 = bi * SB;
+        // Tm(bj) = sum_{p in [bj*16, r0)} L(r0 + r, p) X(p, bj*16 + c)  -> X(r0 + r, bj*16 + c)
+        for (int idx = tid; idx < bi * SB * SB; idx += POTRF_THREADS) {
+            const int bj = idx / (SB * SB), r = idx % SB, c = (idx / SB) % SB;
+            T acc0 = T(0), acc1 = T(0);
+            const int p0 = bj * SB;
+#pragma unroll 4
+            for (int p = p0; p < r0; p += 2) {
+                acc0 += A[r0 + r][p] * X[p][p0 + c];
+                acc1 += A[r0 + r][p + 1] * X[p + 1][p0 + c];
+            }
+            X[r0 + r][p0 + c] = acc0 + acc1;
         }
         __syncthreads();
-        if (warp == 1) {
-            chol32_warp<T>(A, HB, w2, gcol0, status, invd);
-            __syncwarp();
-            inv32_warp<T>(A, X, HB, w2, invd);
-        }
-        __syncthreads();
-        // X21 = -X22 (L21 X11): first T = L21 X11 into X[HB + r][c]
-        for (int idx = tid; idx < HB * HB; idx += NB) {
-            const int r = idx % HB, c = idx / HB;
+        constexpr int QMAX = SB * SB * (NB / SB - 1) / POTRF_THREADS;
+        T out[QMAX];
+#pragma unroll 6
+        for (int q = 0; q < QMAX; ++q) {
+            const int idx = tid + q * POTRF_THREADS;
+            const int bj = idx / (SB * SB), r = idx % SB, c = (idx / SB) % SB;
             T acc = T(0);
-            if (r < w2 && c < w1)
-                for (int p = c; p < HB; ++p) acc += A[HB + r][p] * X[p][c];
-            X[HB + r][c] = acc;
-        }
-        __syncthreads();
-        T out[HB * HB / NB];
-#pragma unroll
-        for (int q = 0; q < HB * HB / NB; ++q) {
-            const int idx = tid + q * NB, r = idx % HB, c = idx / HB;
-            T acc = T(0);
-            for (int p = 0; p <= r; ++p) acc += X[HB + r][HB + p] * X[HB + p][c];
+            if (idx < bi * SB * SB) {
+#pragma unroll 4
+                for (int p = 0; p < SB; ++p) acc += X[r0 + r][r0 + p] * X[r0 + p][bj * SB + c];
+            }
             out[q] = -acc;
         }
         __syncthreads();
-#pragma unroll
-        for (int q = 0; q < HB * HB / NB; ++q) {
-            const int idx = tid + q * NB, r = idx % HB, c = idx / HB;
-            X[HB + r][c] = (r < w2 && c < w1) ? out[q] : T(0);
+#pragma unroll 6
+        for (int q = 0; q < QMAX; ++q) {
+            const int idx = tid + q * POTRF_THREADS;
+            const int bj = idx / (SB * SB), r = idx % SB, c = (idx / SB) % SB;
+            if (idx < bi * SB * SB) X[r0 + r][bj * SB + c] = (r0 + r < nb) ? out[q] : T(0);
         }
-    } else {
-        if (warp == 0) inv32_warp<T>(A, X, 0, w1, invd);
-        for (int idx = tid; idx < NB * NB; idx += NB) {
-            const int r = idx % NB, c = idx / NB;
-            if (r >= HB || c >= HB) X[r][c] = T(0);
-        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int c = 0; c < nb; ++c)
-        if (tid >= c && tid < nb) F[(int64_t)c * ld + tid] = A[tid][c];
-    for (int c = 0; c < NB; ++c) Dinv[(int64_t)c * NB + tid] = (tid >= c) ? X[tid][c] : T(0);
+    for (int idx = tid; idx < NB * NB; idx += POTRF_THREADS) {
+        const int r = idx % NB, c = idx / NB;
+        if (r >= c && r < nb) F[(int64_t)c * ld + r] = A[r][c];
+        Dinv[idx] = (r >= c) ? X[r][c] : T(0);
+    }
     __syncthreads();
 }
 
 // diagonal block starting at pivot column j0 = item.y of front item.x
 template <class T>
-__global__ void __launch_bounds__(NB, 1) potrf_kernel(DevSym d, T *__restrict__ front,
+__global__ void __launch_bounds__(POTRF_THREADS) potrf_kernel(DevSym d, T *__restrict__ front,
                                                    T *__restrict__ dinv,
                                                    const int4 *__restrict__ items,
                                                    status_t *status) {
@@ -457,7 +511,7 @@ void launch_potrf(const DevSym &d, T *front, T *dinv, const int4 *items, int cou
                   status_t *status, cudaStream_t st) {
     if (count <= 0) return;
     set_smem_attrs<T>();
-    potrf_kernel<T><<<count, NB, potrf_smem<T>(), st>>>(d, front, dinv, items, status);
+    potrf_kernel<T><<<count, POTRF_THREADS, potrf_smem<T>(), st>>>(d, front, dinv, items, status);
 }
 
 template <class T>
