@@ -339,8 +339,11 @@ def run_ours(args):
     top = max(kstats, key=lambda k: k["ms"]) if kstats else None
     roof = None
     if top:
-        alu = top["name"].startswith(("schur_update", "panel_trsm", "potrf_first", "fwd_update",
-                                      "bwd_init", "bwd_step", "fwd_diag_first"))
+        # the residual product with many right-hand sides does ~10 flops per byte of
+        # A in FP64, above GB300's FP64 ridge point: bounded by the FP64 pipe
+        alu = top["name"].startswith(("schur_", "panel_trsm", "potrf_diag", "fwd_update", "fwd_rgemm",
+                                      "bwd_init", "bwd_step", "fwd_diag_first")) or (
+            top["name"].startswith("spmv_residual") and nr >= 8)
         if alu:
             fp64 = top["name"].endswith("_fp64")
             per_clk = FP64_FLOPS_PER_SM_CLK if fp64 else 2 * FP32_LANES_PER_SM
