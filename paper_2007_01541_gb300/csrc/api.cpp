@@ -24,7 +24,7 @@ constexpr int RG = 16;             // right-hand sides per solve block (solve_ke
 constexpr int ROWS_PER_CTA = 256;  // one thread per front row (gather / apply_L)
 
 enum LaunchKind {
-    K_INIT, K_POTRF, K_PANEL, K_UPDATE, K_SYRK,          // factor
+    K_INIT, K_POTRF, K_PANEL, K_UPDATE, K_SYRK, K_UPDATE_TC, K_SYRK_TC,  // factor
     K_FWD_GATHER, K_FWD_DIAG_FIRST, K_FWD_UPDATE, K_FWD_RGEMM, // forward solve
     K_BWD_INIT, K_BWD_STEP,                                    // backward solve
     K_APPLY_L
@@ -42,8 +42,9 @@ struct Launch {
 
 const char *kind_name(int k) {
     static const char *names[] = {"front_init", "potrf_diag", "panel_trsm", "schur_update",
-                                  "schur_syrk", "fwd_gather", "fwd_diag_first", "fwd_update",
-                                  "fwd_rgemm", "bwd_init", "bwd_step", "apply_L"};
+                                  "schur_syrk", "tc_schur_update", "tc_schur_syrk", "fwd_gather",
+                                  "fwd_diag_first", "fwd_update", "fwd_rgemm", "bwd_init",
+                                  "bwd_step", "apply_L"};
     return names[k];
 }
 
@@ -109,11 +110,15 @@ struct wd_ctx {
     size_t front_elems = 0;
     void *d_dinv = nullptr;        // inverses of the NB x NB diagonal blocks
     size_t dinv_elems = 0;
+    unsigned char *d_pack = nullptr;  // packed tf32 panel lines (FP32 fronts)
+    int64_t pack_total = 0;
+    status_t *d_tstatus = nullptr;    // nonzero: a bounded device wait expired
     cudaStream_t cap_stream = nullptr;
     GraphCache g_factor, g_solve;
     status_t *d_status = nullptr;
     double *d_scalars = nullptr;   // [0] = ||A||_inf, [1] = logdet, [2..] partials
-    Plan fplan;
+    Plan fplan;        // FP64 fronts (SIMT Schur tiles)
+    Plan fplan_tc;     // FP32 fronts (tensor-core Schur tiles)
     Plan splan;
     int splan_nrhs = -1;
     Plan aplan;
@@ -269,9 +274,9 @@ static int kpad(int k) { return (k + 31) / 32 * 32; }
 // rows of a front: pivot rows, zero padding to a multiple of 32, rows below
 static int front_order(const wd::Symbolic &S, int s) { return kpad(S.k(s)) + S.m(s) - S.k(s); }
 
-static void build_factor_plan(const wd::Symbolic &S, Plan &p) {
-    using wd::SCHUR_BM;
-    using wd::SCHUR_BN;
+static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
+    const int SCHUR_BM = tc ? wd::TC_BM : wd::SCHUR_BM;
+    const int SCHUR_BN = tc ? wd::TC_BN : wd::SCHUR_BN;
     p.items.clear();
     p.launches.clear();
     for (int l = 0; l < S.nlevels; ++l) {
@@ -338,7 +343,7 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p) {
                 fl += 2.0 * nb * ent;
                 el += 2.0 * ent + (double)(m - t0) * nb;
             }
-            add_launch(p, K_UPDATE, f0, kb, fl, el, 0);
+            add_launch(p, tc ? K_UPDATE_TC : K_UPDATE, f0, kb, fl, el, 0);
         }
         f0 = p.items.size();
         fl = el = 0;
@@ -355,7 +360,7 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p) {
             fl += 2.0 * k * tri;
             el += 2.0 * tri + (double)u * k;
         }
-        add_launch(p, K_SYRK, f0, 0, fl, el, 0);
+        add_launch(p, tc ? K_SYRK_TC : K_SYRK, f0, 0, fl, el, 0);
     }
 }
 
@@ -508,7 +513,7 @@ static void fill_info(wd_handle h, int64_t nnzl, int maxm, int maxk,
     I.max_front = maxm;
     I.max_width = maxk;
     I.front_bytes = (int64_t)h->front_elems * 8;
-    I.factor_launches = (int64_t)h->fplan.launches.size();
+    I.factor_launches = (int64_t)h->fplan_tc.launches.size();
     I.analyze_seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -533,6 +538,8 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
         h->mem.free_all();
     }
     h->fplan = Plan();
+    h->fplan_tc = Plan();
+    h->d_pack = nullptr;
     h->splan = Plan();
     h->aplan = Plan();
     h->splan_nrhs = h->aplan_nrhs = -1;
@@ -552,8 +559,8 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
     const int ns = S.ns;
     // per-supernode arrays
     std::vector<int32_t> sk(ns), sm(ns), skp(ns), sld(ns);
-    std::vector<int64_t> foff(ns), woff(ns), dioff(ns);
-    int64_t fo = 0, wo = 0, dio = 0;
+    std::vector<int64_t> foff(ns), woff(ns), dioff(ns), pkoff(ns);
+    int64_t fo = 0, wo = 0, dio = 0, pko = 0;
     int maxm = 0, maxk = 0;
     for (int s = 0; s < ns; ++s) {
         sk[s] = S.k(s);
@@ -567,11 +574,14 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
         fo += (int64_t)sld[s] * mp;
         wo += sm[s] - sk[s];
         dio += (int64_t)((sk[s] + NB - 1) / NB) * NB * NB;
+        pkoff[s] = pko;
+        pko += wd::pack_bytes(sk[s], mp);
         maxm = std::max(maxm, sm[s]);
         maxk = std::max(maxk, sk[s]);
     }
     h->front_elems = (size_t)fo;
     h->dinv_elems = (size_t)dio;
+    h->pack_total = pko;
     h->W_rows = wo;
     // full CSR of P A P^T with the source index of every value
     std::vector<int64_t> cptr(n + 1, 0), cdiag(n);
@@ -603,7 +613,8 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
             }
         }
     }
-    build_factor_plan(S, h->fplan);
+    build_factor_plan(S, h->fplan, false);
+    build_factor_plan(S, h->fplan_tc, true);
     if (host_only) {
         fill_info(h, nnzl, maxm, maxk, t0);
         h->analyzed = true;
@@ -640,6 +651,7 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
     UP(cdiag, d.csr_diag);
     UP(woff, d.woff);
     UP(dioff, d.dinvoff);
+    UP(pkoff, d.pkoff);
     UP(S.perm, d.perm);
     {
         const int32_t *p = nullptr;
@@ -679,7 +691,10 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
     {
         wd_status st = upload_plan(h, h->mem, h->fplan);
         if (st != WD_OK) return st;
+        st = upload_plan(h, h->mem, h->fplan_tc);
+        if (st != WD_OK) return st;
     }
+    CK(h->mem.alloc((void **)&h->d_tstatus, sizeof(status_t)), "status alloc");
     fill_info(h, nnzl, maxm, maxk, t0);
     h->analyzed = true;
     return WD_OK;
@@ -821,16 +836,27 @@ static void enqueue_factor_plan(wd_handle h, cudaStream_t st, bool prof) {
     T *F = static_cast<T *>(h->d_front);
     T *Dv = static_cast<T *>(h->d_dinv);
     const DevSym &d = h->dsym;
+    const bool fp32 = sizeof(T) == 4;
+    const Plan &P = fp32 ? h->fplan_tc : h->fplan;
+    unsigned char *pk = fp32 ? h->d_pack : nullptr;
     size_t li = 0;
-    for (const Launch &L : h->fplan.launches) {
-        const int4 *it = h->fplan.d_items + L.off;
+    for (const Launch &L : P.launches) {
+        const int4 *it = P.d_items + L.off;
         if (prof) record_event(h->prof_ev[2 * li], st);
         switch (L.kind) {
             case K_INIT: wd::launch_front_init<T>(d, F, it, L.count, st); break;
             case K_POTRF: wd::launch_potrf<T>(d, F, Dv, it, L.count, h->d_status, st); break;
-            case K_PANEL: wd::launch_panel<T>(d, F, Dv, it, L.count, L.arg, st); break;
+            case K_PANEL: wd::launch_panel<T>(d, F, Dv, pk, it, L.count, L.arg, st); break;
             case K_UPDATE: wd::launch_schur<T>(d, F, Dv, it, L.count, L.arg, 0, h->d_status, st); break;
             case K_SYRK: wd::launch_schur<T>(d, F, Dv, it, L.count, 0, 1, h->d_status, st); break;
+            case K_UPDATE_TC:
+                wd::launch_tc_schur(d, reinterpret_cast<float *>(F), pk, it, L.count, L.arg, 0,
+                                    h->d_tstatus, st);
+                break;
+            case K_SYRK_TC:
+                wd::launch_tc_schur(d, reinterpret_cast<float *>(F), pk, it, L.count, 0, 1,
+                                    h->d_tstatus, st);
+                break;
         }
         if (prof) record_event(h->prof_ev[2 * li + 1], st);
         ++li;
@@ -867,13 +893,14 @@ static wd_status run_graph(wd_handle h, GraphCache &gc, int64_t key, cudaStream_
 
 template <class T>
 static wd_status run_factor_plan(wd_handle h, cudaStream_t st) {
-    const bool prof = prof_begin(h, h->fplan.launches.size());
+    const Plan &P = sizeof(T) == 4 ? h->fplan_tc : h->fplan;
+    const bool prof = prof_begin(h, P.launches.size());
     const int64_t key = (sizeof(T) == 8 ? 1 : 2) + (prof ? 10 : 0);
     wd_status s = run_graph(h, h->g_factor, key, st,
                             [&](cudaStream_t cs) { enqueue_factor_plan<T>(h, cs, prof); });
     if (s != WD_OK) return s;
-    h->launches += (int64_t)h->fplan.launches.size();
-    if (prof) prof_end(h, h->fplan, sizeof(T), sizeof(T) == 8 ? "_fp64" : "_fp32");
+    h->launches += (int64_t)P.launches.size();
+    if (prof) prof_end(h, P, sizeof(T), sizeof(T) == 8 ? "_fp64" : "_fp32");
     return WD_OK;
 }
 
@@ -894,6 +921,12 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
         // padding rows stay zero forever: no kernel writes them
         CK(cudaMemsetAsync(h->d_front, 0, h->front_elems * sizeof(double), st), "front pool clear");
     }
+    if (prec == WD_MIXED && !h->d_pack) {
+        CK(h->mem.alloc((void **)&h->d_pack, h->pack_total), "packed panel alloc");
+        // rows no panel writes (slack, padding of the last block) stay zero
+        CK(cudaMemsetAsync(h->d_pack, 0, h->pack_total, st), "packed panel clear");
+        h->g_factor.reset();
+    }
     const double *vals = values;
     if (!values_on_device) {
         if (!h->d_values_stage)
@@ -905,6 +938,7 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
     wd::launch_gather_values(h->d_csr_src, vals, h->d_csr_val, h->nnz_full, st);
     h->launches += 1;
     CK(cudaMemsetAsync(h->d_status, 0xFF, sizeof(status_t), st), "status reset");
+    CK(cudaMemsetAsync(h->d_tstatus, 0, sizeof(status_t), st), "status reset");
     {
         wd_status fs = (prec == WD_FP64) ? run_factor_plan<double>(h, st) : run_factor_plan<float>(h, st);
         if (fs != WD_OK) return fs;
@@ -912,10 +946,12 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
     wd::launch_norm_inf_rows(h->dsym, h->d_scalars, st);
     h->launches += 1;
     CK(cudaGetLastError(), "factor launch");
-    status_t status = 0;
+    status_t status = 0, tstatus = 0;
     CK(cudaMemcpyAsync(&status, h->d_status, sizeof(status_t), cudaMemcpyDeviceToHost, st), "status D2H");
+    CK(cudaMemcpyAsync(&tstatus, h->d_tstatus, sizeof(status_t), cudaMemcpyDeviceToHost, st), "status D2H");
     CK(cudaMemcpyAsync(&h->normA, h->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, st), "norm D2H");
     CK(cudaStreamSynchronize(st), "factor");
+    if (tstatus != 0) return fail(h, WD_ERR_TIMEOUT, "a bounded wait of the tensor-core update expired");
     if (status != ~0ULL)
         return fail(h, WD_ERR_NOT_SPD, "pivot not positive at column " + std::to_string(status),
                     (int64_t)status);

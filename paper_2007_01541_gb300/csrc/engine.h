@@ -5,6 +5,9 @@
 
 namespace wd {
 
+// status word of a factorization: smallest failing column (UINT64_MAX = none)
+using status_t = unsigned long long;
+
 constexpr int NB = 64;        // pivot block width and Schur tile size
 constexpr int RB = 64;        // rows per panel (TRSM) block
 constexpr int SOLVE_RB = 64;  // rows per solve block
@@ -33,6 +36,7 @@ struct DevSym {
     const double *csr_val;      // FP64 values of P A P^T (full)
     const int64_t *woff;        // ns: prefix sum of (m_s - k_s) (solve workspace)
     const int64_t *dinvoff;     // ns: offset of the supernode's inverse diagonal blocks
+    const int64_t *pkoff;       // ns: byte offset of the supernode's packed tf32 panel lines
     const int32_t *perm;        // n
 };
 
@@ -40,13 +44,13 @@ struct DevSym {
 // before any stream capture).
 void init_front_attributes();
 void init_solve_attributes();
+void init_tc_attributes();
 inline void init_kernel_attributes() {
     init_front_attributes();
     init_solve_attributes();
+    init_tc_attributes();
 }
 
-// status word of a factorization: smallest failing column (UINT64_MAX = none)
-using status_t = unsigned long long;
 
 // ---- factorization (front_kernels.cu) ------------------------------------
 template <class T>
@@ -55,14 +59,38 @@ void launch_front_init(const DevSym &d, T *front, const int4 *items, int count, 
 template <class T>
 void launch_potrf(const DevSym &d, T *front, T *dinv, const int4 *items, int count,
                   status_t *status, cudaStream_t st);
+// pk != nullptr (FP32 only): also write the packed tf32 lines of the new panel
 template <class T>
-void launch_panel(const DevSym &d, T *front, const T *dinv, const int4 *items, int count, int kb,
-                  cudaStream_t st);
+void launch_panel(const DevSym &d, T *front, const T *dinv, unsigned char *pk, const int4 *items,
+                  int count, int kb, cudaStream_t st);
 // mode 0: pivot-column update of step kb; mode 1: final update matrix (syrk)
 template <class T>
 void launch_schur(const DevSym &d, T *front, T *dinv, const int4 *items, int count, int kb,
                   int mode, status_t *status, cudaStream_t st);
 constexpr int SCHUR_BM = 128, SCHUR_BN = 64;
+
+// Packed tf32 operand lines of a supernode's L panel (FP32 fronts, tensor-core
+// Schur updates): for each chunk kc of 32 pivot columns and plane p (0 = hi,
+// 1 = lo part of the split), one 128-byte line per front row holding the 32
+// tf32 values, its 16-byte groups XOR-swizzled by (row & 7) -- the 128-byte
+// swizzled K-major image of the MMA operand, so rows [r, r + 128) of a chunk
+// (r a multiple of 8) form one contiguous 16 KB tile.  Rows are padded by 128
+// so that every window starting below mp stays inside the allocation.
+__host__ __device__ inline int pack_rows(int mp) { return ((mp + 7) / 8) * 8 + 128; }
+__host__ __device__ inline int pack_chunks(int k) { return 2 * ((k + 63) / 64); }
+__host__ __device__ inline int64_t pack_offset(int kc, int p, int row, int prow) {
+    return ((int64_t)(kc * 2 + p) * prow + row) * 128;
+}
+__host__ __device__ inline int64_t pack_bytes(int k, int mp) {
+    return (int64_t)pack_chunks(k) * 2 * pack_rows(mp) * 128;
+}
+
+// tensor-core Schur update of FP32 fronts (tc_schur.cu); 128 x 128 tiles;
+// tstatus != 0 after the launch means a bounded wait expired
+constexpr int TC_BM = 128, TC_BN = 128;
+void launch_tc_schur(const DevSym &d, float *front, const unsigned char *pk, const int4 *items,
+                     int count, int kb, int mode, status_t *tstatus, cudaStream_t st);
+void init_tc_attributes();
 
 // ---- values, solves and reductions (solve_kernels.cu) ---------------------
 void launch_gather_values(const int32_t *csr_src, const double *values, double *csr_val,

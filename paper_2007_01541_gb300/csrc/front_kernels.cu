@@ -56,6 +56,13 @@ __device__ __forceinline__ void pivot_root(float d, float &s, float &is) {
     s = d * is;
 }
 
+// x = hi + lo, hi = x rounded to tf32 (cvt.rna), lo = (x - hi) rounded to tf32
+__device__ __forceinline__ void split_tf32_bits(float x, uint32_t &hi, uint32_t &lo) {
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(hi) : "f"(x));
+    const float rem = x - __uint_as_float(hi);
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(lo) : "f"(rem));
+}
+
 struct Dims {
     int k, m, kp, mp, ld;
 };
@@ -348,6 +355,7 @@ __global__ void __launch_bounds__(POTRF_THREADS) potrf_kernel(DevSym d, T *__res
 template <class T>
 __global__ void __launch_bounds__(THREADS) panel_kernel(DevSym d, T *__restrict__ front,
                                                         const T *__restrict__ dinv,
+                                                        unsigned char *__restrict__ pk,
                                                         const int4 *__restrict__ items, int kb) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *Xs = reinterpret_cast<T *>(smem_raw);         // [p][r], ld RB
@@ -381,6 +389,30 @@ __global__ void __launch_bounds__(THREADS) panel_kernel(DevSym d, T *__restrict_
         for (int u = 0; u < NB / 4; ++u) {
             const int c = cg + 4 * u;
             if (c < nb) F[(int64_t)(kb + c) * z.ld + r0 + r] = acc[u];
+        }
+    }
+    if (pk != nullptr) {
+        // packed tf32 hi/lo lines of these rows for the tensor-core updates
+        __syncthreads();
+        T *Os = Xs;  // [c][r], ld RB
+#pragma unroll
+        for (int u = 0; u < NB / 4; ++u) Os[(cg + 4 * u) * RB + r] = acc[u];
+        __syncthreads();
+        unsigned char *P = pk + d.pkoff[s];
+        const int prow = pack_rows(z.mp);
+        for (int q = tid; q < RB * (NB / 4); q += THREADS) {
+            const int rr = q % RB, g = q / RB;  // row, group of 4 columns
+            const int row = r0 + rr;
+            if (row >= z.mp) continue;
+            const int kc = kb / 32 + g / 8, gg = g % 8;
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) split_tf32_bits((float)Os[(4 * g + j) * RB + rr], hi[j], lo[j]);
+            const int64_t sw = (int64_t)((gg ^ (row & 7)) * 16);
+            *reinterpret_cast<uint4 *>(P + pack_offset(kc, 0, row, prow) + sw) =
+                make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4 *>(P + pack_offset(kc, 1, row, prow) + sw) =
+                make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
     }
 }
@@ -515,11 +547,11 @@ void launch_potrf(const DevSym &d, T *front, T *dinv, const int4 *items, int cou
 }
 
 template <class T>
-void launch_panel(const DevSym &d, T *front, const T *dinv, const int4 *items, int count, int kb,
-                  cudaStream_t st) {
+void launch_panel(const DevSym &d, T *front, const T *dinv, unsigned char *pk, const int4 *items,
+                  int count, int kb, cudaStream_t st) {
     if (count <= 0) return;
     set_smem_attrs<T>();
-    panel_kernel<T><<<count, THREADS, panel_smem<T>(), st>>>(d, front, dinv, items, kb);
+    panel_kernel<T><<<count, THREADS, panel_smem<T>(), st>>>(d, front, dinv, pk, items, kb);
 }
 
 template <class T>
@@ -534,8 +566,8 @@ void launch_schur(const DevSym &d, T *front, T *dinv, const int4 *items, int cou
     template void launch_front_init<T>(const DevSym &, T *, const int4 *, int, cudaStream_t);    \
     template void launch_potrf<T>(const DevSym &, T *, T *, const int4 *, int, status_t *,       \
                                   cudaStream_t);                                                 \
-    template void launch_panel<T>(const DevSym &, T *, const T *, const int4 *, int, int,        \
-                                  cudaStream_t);                                                 \
+    template void launch_panel<T>(const DevSym &, T *, const T *, unsigned char *, const int4 *, \
+                                  int, int, cudaStream_t);                                       \
     template void launch_schur<T>(const DevSym &, T *, T *, const int4 *, int, int, int,         \
                                   status_t *, cudaStream_t);
 WD_INST(double)

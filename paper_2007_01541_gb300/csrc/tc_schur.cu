@@ -1,0 +1,189 @@
+// Schur updates of FP32 fronts on the 5th-generation tensor cores (tcgen05),
+// 3xTF32: every L value x is split into x = hi + lo (tf32 each) and
+//   C -= A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
+// with FP32 accumulation in tensor memory (the lo*lo term is dropped), which
+// keeps FP32-level accuracy (the mixed path is then refined in FP64).
+//
+// Operands come pre-split and pre-swizzled: when the panel kernel finishes a
+// block of L it also writes the block's rows as tf32 hi/lo lines in the
+// 128-byte-swizzled K-major layout of the MMA (see pack_offset below), so a
+// 128-row x 32-column operand tile is one contiguous 16 KB range that the
+// Tensor Memory Accelerator copies into shared memory with a single bulk copy.
+//
+// One CTA per 128 x 128 output tile, warp-specialized:
+//   warp 0: producer (bulk copies of A_hi, A_lo, B_hi, B_lo per 32-wide
+//           chunk of the inner dimension into a 3-stage ring)
+//   warp 1: allocates 128 TMEM columns; one lane issues the 12 MMAs of a
+//           chunk and commits them to the stage's "empty" barrier
+//   warps 2-5: epilogue (TMEM -> registers -> C -= acc, lower part only)
+// Every wait is bounded; on expiry the CTA records WD timeout status, still
+// frees its TMEM and returns.
+#include "engine.h"
+#include "tc_common.cuh"
+
+namespace wd {
+namespace {
+
+constexpr int TBM = 128, TBN = 128, TBK = 32;
+constexpr int STAGES = 3;
+constexpr int TILE_BYTES = TBM * TBK * 4;           // 16 KB per operand plane
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;          // A hi, A lo, B hi, B lo
+constexpr int TC_THREADS = 192;
+constexpr uint32_t WAIT_LIMIT = 1u << 26;
+
+__device__ __forceinline__ void bulk_copy(void *dst_smem, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            tc::smem_u32(dst_smem)),
+        "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tc::smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_schur_kernel(DevSym d, float *__restrict__ front, const unsigned char *__restrict__ pk,
+                    const int4 *__restrict__ items, int kb, int mode, status_t *tstatus) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *done = empty + STAGES;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, ti = it.y, tj = it.z;
+    const int k = d.sk[s], m = d.sm[s], kp = d.skp[s], ld = d.sld[s];
+    const int mp = kp + m - k;
+    int base, ka, K, cmax;
+    if (mode == 0) {
+        base = kb + NB;
+        ka = kb;
+        K = NB;
+        cmax = k;
+    } else {
+        base = kp;
+        ka = 0;
+        K = k;
+        cmax = mp;
+    }
+    const int r0 = base + ti * TBM, c0 = base + tj * TBN;
+    const int nk = (K + TBK - 1) / TBK;
+    const int prow = pack_rows(mp);
+    const unsigned char *P = pk + d.pkoff[s];
+
+    if (tid == 0) {
+        for (int i = 0; i < STAGES; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        tc::mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 1) tc::tmem_alloc(tslot, TBN);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kt = 0; kt < nk; ++kt) {
+                const int st = kt % STAGES;
+                if (kt >= STAGES && !tc::mbar_wait(&empty[st], ((kt / STAGES) - 1) & 1, WAIT_LIMIT)) {
+                    atomicExch(abort_flag, 1);
+                    break;
+                }
+                unsigned char *stg = sm + st * STAGE_BYTES;
+                const int kc = (ka / TBK) + kt;
+                mbar_expect_tx(&full[st], STAGE_BYTES);
+                bulk_copy(stg, P + pack_offset(kc, 0, r0, prow), TILE_BYTES, &full[st]);
+                bulk_copy(stg + TILE_BYTES, P + pack_offset(kc, 1, r0, prow), TILE_BYTES, &full[st]);
+                bulk_copy(stg + 2 * TILE_BYTES, P + pack_offset(kc, 0, c0, prow), TILE_BYTES, &full[st]);
+                bulk_copy(stg + 3 * TILE_BYTES, P + pack_offset(kc, 1, c0, prow), TILE_BYTES, &full[st]);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_tf32(TBM, TBN);
+            bool ok = true;
+            for (int kt = 0; kt < nk; ++kt) {
+                const int st = kt % STAGES;
+                if (!tc::mbar_wait(&full[st], (kt / STAGES) & 1, WAIT_LIMIT)) {
+                    atomicExch(abort_flag, 1);
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t a0 = tc::smem_u32(sm + st * STAGE_BYTES);
+#pragma unroll
+                for (int j = 0; j < TBK / 8; ++j) {
+                    const uint64_t ah = tc::desc_kmajor_sw128(a0 + 32 * j);
+                    const uint64_t al = tc::desc_kmajor_sw128(a0 + TILE_BYTES + 32 * j);
+                    const uint64_t bh = tc::desc_kmajor_sw128(a0 + 2 * TILE_BYTES + 32 * j);
+                    const uint64_t bl = tc::desc_kmajor_sw128(a0 + 3 * TILE_BYTES + 32 * j);
+                    tc::mma_tf32(tmem, ah, bh, idesc, (kt > 0 || j > 0) ? 1u : 0u);
+                    tc::mma_tf32(tmem, ah, bl, idesc, 1u);
+                    tc::mma_tf32(tmem, al, bh, idesc, 1u);
+                }
+                tc::mma_commit(&empty[st]);
+            }
+            if (ok) tc::mma_commit(done);
+            else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tc::smem_u32(done))
+                              : "memory");
+        }
+    } else {
+        // epilogue: warps 2..5 cover TMEM lane groups 2, 3, 0, 1
+        const int lg = warp & 3;
+        const bool ok = tc::mbar_wait(done, 0, WAIT_LIMIT);
+        tc::tc_fence_after();
+        if (ok && *abort_flag == 0) {
+            const int r = r0 + 32 * lg + lane;
+            float *Fs = front + d.foff[s];
+            for (int cb = 0; cb < TBN; cb += 16) {
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + cb, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int c = c0 + cb + i;
+                    if (r < mp && c < cmax && r >= c) Fs[(int64_t)c * ld + r] -= v[i];
+                }
+            }
+        } else if (lane == 0) {
+            atomicExch(abort_flag, 1);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tmem, TBN);
+    if (tid == 0 && *abort_flag) atomicMax(tstatus, 1ull);
+}
+
+}  // namespace
+
+size_t tc_schur_smem() { return (size_t)STAGES * STAGE_BYTES + 1024 + 128; }
+
+void init_tc_attributes() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(tc_schur_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tc_schur_smem());
+    done = true;
+}
+
+void launch_tc_schur(const DevSym &d, float *front, const unsigned char *pk, const int4 *items,
+                     int count, int kb, int mode, status_t *tstatus, cudaStream_t st) {
+    if (count <= 0) return;
+    init_tc_attributes();
+    tc_schur_kernel<<<count, TC_THREADS, tc_schur_smem(), st>>>(d, front, pk, items, kb, mode, tstatus);
+}
+
+}  // namespace wd

@@ -220,3 +220,22 @@ def test_profiled_and_direct_launches(wdlib, cuda, graphs):
     assert all(k["launches"] > 0 and k["ms"] > 0 for k in st)
     assert s.kernel_stats() == []
     assert s.launch_count() > 0
+
+
+@pytest.mark.parametrize("name", ["1d_J10", "2d_J6", "2d_J7_exp"])
+def test_factor_mixed_entries(wdlib, cuda, name):
+    """FP32 fronts with tensor-core (3xTF32) Schur updates: every column of L
+    within 2e-5 of the FP64 oracle (relative 2-norm), amalgamation zeros
+    exactly 0 in the 1D case."""
+    b, cp, ri, v, o = _case(name)
+    s = wdlib.Solver().analyze(cp, ri, b)
+    s.factor(v, "mixed")
+    L = s.L_csc_like(o.Lp, o.Li)
+    Lo = o.L_values()
+    worst = 0.0
+    for j in range(o.n):
+        a, e = o.Lp[j], o.Lp[j + 1]
+        worst = max(worst, np.linalg.norm(L[a:e] - Lo[a:e]) / np.linalg.norm(Lo[a:e]))
+    assert worst <= 2e-5, worst
+    if name == "1d_J10":
+        assert _panel_mask_check(s, o) == 0.0
