@@ -15,7 +15,9 @@
 //           chunk of the inner dimension into a 3-stage ring)
 //   warp 1: allocates 128 TMEM columns; one lane issues the 12 MMAs of a
 //           chunk and commits them to the stage's "empty" barrier
-//   warps 2-5: epilogue (TMEM -> registers -> C -= acc, lower part only)
+//   warps 2-9: epilogue, each thread one row and 64 columns of the tile: its
+//           part of C is loaded into registers while the MMAs run, then
+//           C -= acc (TMEM -> registers), lower part only
 // Every wait is bounded; on expiry the CTA records WD timeout status, still
 // frees its TMEM and returns.
 #include "engine.h"
@@ -28,7 +30,7 @@ constexpr int TBM = 128, TBN = 128, TBK = 32;
 constexpr int STAGES = 3;
 constexpr int TILE_BYTES = TBM * TBK * 4;           // 16 KB per operand plane
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;          // A hi, A lo, B hi, B lo
-constexpr int TC_THREADS = 192;
+constexpr int TC_THREADS = 320;
 constexpr uint32_t WAIT_LIMIT = 1u << 26;
 
 __device__ __forceinline__ void bulk_copy(void *dst_smem, const void *src, uint32_t bytes,
@@ -141,22 +143,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                               : "memory");
         }
     } else {
-        // epilogue: warps 2..5 cover TMEM lane groups 2, 3, 0, 1
-        const int lg = warp & 3;
+        // epilogue: warps 2..9; TMEM lane group = warp % 4, column half = (warp - 2) / 4
+        const int lg = warp & 3, half = (warp - 2) >> 2;
+        const int r = r0 + 32 * lg + lane;
+        const int cb0 = c0 + 64 * half;
+        // this thread's row of the tile, columns cb0 .. cb0+63 (stride ld)
+        float *rowp = front + d.foff[s] + (int64_t)cb0 * ld + r;
+        const int cend = min(64, cmax - cb0);     // columns below cmax
+        const int cdiag = r - cb0 + 1;            // columns with c <= r
+        const int nc = (r < mp) ? max(0, min(cend, cdiag)) : 0;
+        float cur[64];
+#pragma unroll
+        for (int i = 0; i < 64; ++i) cur[i] = (i < nc) ? rowp[i * ld] : 0.0f;
         const bool ok = tc::mbar_wait(done, 0, WAIT_LIMIT);
         tc::tc_fence_after();
         if (ok && *abort_flag == 0) {
-            const int r = r0 + 32 * lg + lane;
-            float *Fs = front + d.foff[s];
-            for (int cb = 0; cb < TBN; cb += 16) {
-                float v[16];
-                tc::tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + cb, v);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int c = c0 + cb + i;
-                    if (r < mp && c < cmax && r >= c) Fs[(int64_t)c * ld + r] -= v[i];
-                }
+            for (int q = 0; q < 4; ++q) {
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 64 * half + 16 * q, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) cur[16 * q + i] -= v[i];
             }
+#pragma unroll
+            for (int i = 0; i < 64; ++i)
+                if (i < nc) rowp[i * ld] = cur[i];
         } else if (lane == 0) {
             atomicExch(abort_flag, 1);
         }
