@@ -132,6 +132,7 @@ struct wd_ctx {
     int4 *d_spmv_chunks = nullptr, *d_spmv_fin = nullptr;
     int n_spmv_chunks = 0, n_spmv_fin = 0, n_spmv_slots = 0;
     double *d_P = nullptr;  // partial sums of chunked rows (slots x nrhs)
+    double *d_norm_part = nullptr;  // partial row sums of |a| of chunked rows
     double normA = 0.0;
     wd_info info{};
     // profiling
@@ -684,6 +685,7 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
         CK(h->mem.alloc((void **)&h->d_spmv_fin, std::max<size_t>(fin.size(), 1) * sizeof(int4)), "spmv items");
         if (!fin.empty())
             CK(cudaMemcpy(h->d_spmv_fin, fin.data(), fin.size() * sizeof(int4), cudaMemcpyHostToDevice), "upload");
+        CK(h->mem.alloc((void **)&h->d_norm_part, std::max(slots, 1) * sizeof(double)), "norm partials");
     }
     d.csr_val = h->d_csr_val;
     CK(h->mem.alloc((void **)&h->d_status, sizeof(status_t)), "status alloc");
@@ -943,8 +945,9 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
         wd_status fs = (prec == WD_FP64) ? run_factor_plan<double>(h, st) : run_factor_plan<float>(h, st);
         if (fs != WD_OK) return fs;
     }
-    wd::launch_norm_inf_rows(h->dsym, h->d_scalars, st);
-    h->launches += 1;
+    wd::launch_norm_inf_rows(h->dsym, h->d_spmv_chunks, h->n_spmv_chunks, h->d_spmv_fin, h->n_spmv_fin,
+                             h->d_norm_part, h->d_scalars, st);
+    h->launches += h->n_spmv_fin > 0 ? 2 : 1;
     CK(cudaGetLastError(), "factor launch");
     status_t status = 0, tstatus = 0;
     CK(cudaMemcpyAsync(&status, h->d_status, sizeof(status_t), cudaMemcpyDeviceToHost, st), "status D2H");

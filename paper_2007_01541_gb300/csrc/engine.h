@@ -136,7 +136,8 @@ constexpr int SPMV_CHUNK = 512;
 void launch_spmv_residual(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin,
                           int nfin, const double *X, const double *Bp, double *R, double *P,
                           int64_t nrhs, cudaStream_t st);
-void launch_norm_inf_rows(const DevSym &d, double *rowsum_max, cudaStream_t st);
+void launch_norm_inf_rows(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin,
+                          int nfin, double *partial, double *out, cudaStream_t st);
 void launch_colmax3(const double *R, const double *X, const double *Bp, int64_t n,
                     int64_t nrhs, double *out3, cudaStream_t st);
 template <class T>

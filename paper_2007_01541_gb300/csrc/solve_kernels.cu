@@ -593,15 +593,31 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
     atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-__global__ void norm_inf_kernel(DevSym d, double *out) {
-    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+// ||A||_inf: row sums of |a| over the chunk items of the residual product
+// (single-chunk rows go straight to the maximum, cut rows through partial[])
+__global__ void norm_inf_chunks_kernel(DevSym d, const int4 *__restrict__ items, int count,
+                                       double *__restrict__ partial, double *out) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (row >= d.n) return;
+    if (w >= count) return;
+    const int4 it = items[w];
     double acc = 0.0;
-    for (int64_t e = d.csr_ptr[row] + lane; e < d.csr_ptr[row + 1]; e += 32) acc += fabs(d.csr_val[e]);
+    for (int e = it.y + lane; e < it.z; e += 32) acc += fabs(d.csr_val[e]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) atomic_max_nonneg(out, acc);
+    if (lane == 0) {
+        if (it.w < 0) atomic_max_nonneg(out, acc);
+        else partial[it.w] = acc;
+    }
+}
+
+__global__ void norm_inf_finish_kernel(const int4 *__restrict__ fin, int nfin,
+                                       const double *__restrict__ partial, double *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nfin) return;
+    double acc = 0.0;
+    for (int q = 0; q < fin[i].z; ++q) acc += partial[fin[i].y + q];
+    atomic_max_nonneg(out, acc);
 }
 
 // per column c: out[3c] = max|R|, out[3c+1] = max|X|, out[3c+2] = max|B|
@@ -822,15 +838,18 @@ void launch_spmv_residual(const DevSym &d, const int4 *chunks, int nchunks, cons
     if (nfin > 0) spmv_finish_kernel<<<nfin, 64, 0, st>>>(fin, nfin, Bp, R, P, (int)nrhs);
 }
 
-void launch_norm_inf_rows(const DevSym &d, double *out, cudaStream_t st) {
+void launch_norm_inf_rows(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin,
+                          int nfin, double *partial, double *out, cudaStream_t st) {
     cudaMemsetAsync(out, 0, sizeof(double), st);
-    norm_inf_kernel<<<(int)((d.n * 32 + THREADS - 1) / THREADS), THREADS, 0, st>>>(d, out);
+    norm_inf_chunks_kernel<<<(int)(((int64_t)nchunks * 32 + THREADS - 1) / THREADS), THREADS, 0, st>>>(
+        d, chunks, nchunks, partial, out);
+    if (nfin > 0) norm_inf_finish_kernel<<<(nfin + 127) / 128, 128, 0, st>>>(fin, nfin, partial, out);
 }
 
 void launch_colmax3(const double *R, const double *X, const double *Bp, int64_t n, int64_t nrhs,
                     double *out3, cudaStream_t st) {
     cudaMemsetAsync(out3, 0, 3 * nrhs * sizeof(double), st);
-    const int64_t rpb = 512;
+    const int64_t rpb = 32;
     colmax3_rm_kernel<<<(int)((n + rpb - 1) / rpb), 64, 0, st>>>(R, X, Bp, n, (int)nrhs, rpb, out3);
 }
 
