@@ -164,6 +164,43 @@ wd_status wd_logdet(wd_handle h, double *out);
 wd_status wd_apply_L(wd_handle h, const double *Z, double *S, int64_t nrhs, int64_t ld,
                      int on_device, void *stream);
 
+/* Selected inverse: out[e] = (A^-1)(i, j) for every stored lower entry e = (i, j)
+   of A, in the order of the analyzed rowidx.  Computed from the FP64 factor by
+   Takahashi's recurrences in supernodal form, top-down over the supernodal
+   tree (for supernode columns J and rows R below them: W = L_RJ L_JJ^-1,
+   Z_RJ = -Z_RR W, Z_JJ = L_JJ^-T L_JJ^-1 - W^T Z_RJ).  This is the gradient of
+   log det A with respect to the stored entries (off-diagonal entries stand for
+   both (i, j) and (j, i): multiply them by 2).  Needs a WD_FP64 factorization
+   (WD_ERR_STATE otherwise).  out on the device (1) or the host (0).  The
+   first call allocates the workspace (about twice the factor's memory).
+   Synchronous. */
+wd_status wd_selinv(wd_handle h, double *out, int on_device, void *stream);
+
+/* Pattern part of the gradient of x^T A^-1 y-type terms: for every stored lower
+   entry e = (i, j) of A (analyzed order)
+     out[e] = sum_c U(i, c) V(j, c) + U(j, c) V(i, c)   (i != j)
+     out[e] = sum_c U(i, c) V(i, c)                     (i == j)
+   U, V: n x ncols, column-major, leading dimension ld, original order; device
+   (1) or host (0) arrays; ncols may be 0 (U and V may then be NULL).  Needs
+   wd_analyze only.  Synchronous. */
+wd_status wd_sym_pattern_outer(wd_handle h, const double *U, const double *V, int64_t ncols,
+                               int64_t ld, double *out, int on_device, void *stream);
+
+/* Gradient of a loss l with respect to the stored values of A, for a loss that
+   depends on A through log det A and X = A^-1 B:
+     out[e] = g_logdet * w_e * (A^-1)(i, j) - (G(i,:) . X(j,:) + G(j,:) . X(i,:))   (i != j)
+     out[e] = g_logdet * (A^-1)(i, i)       -  G(i,:) . X(i,:)                      (i == j)
+   with w_e = 2 (an off-diagonal value stands for both (i, j) and (j, i)),
+   g_logdet = dl/d(log det A), G = A^-1 (dl/dX) (the caller's solve).  This
+   is dl/dA = g_logdet A^-1 - G X^T restricted to the pattern (the adjoint of
+   the factorization of Section 4 and of the solves).  X, G: n x ncols,
+   column-major, leading dimension ld, original order; out: one value per
+   stored lower entry, analyzed order; all on the device (1) or the host (0).
+   g_logdet != 0 needs a WD_FP64 factorization (WD_ERR_STATE otherwise).
+   ncols may be 0 (X and G may then be NULL).  Synchronous. */
+wd_status wd_value_gradient(wd_handle h, double g_logdet, const double *X, const double *G,
+                            int64_t ncols, int64_t ld, double *out, int on_device, void *stream);
+
 /* Copy the stored factor (supernodal panels, FP64) to a host array of
    info.nnz_L_stored doubles: for each supernode s, its m_s x k_s lower
    panel, column-major (ld m_s), rows as in super_rows.  Entries above the

@@ -28,7 +28,8 @@ _PREC = {"fp64": WD_FP64, "mixed": WD_MIXED, WD_FP64: WD_FP64, WD_MIXED: WD_MIXE
 
 EXPORTED = ["wd_default_options", "wd_create", "wd_destroy", "wd_analyze", "wd_symbolic_export",
             "wd_get_info", "wd_factor", "wd_solve", "wd_logdet", "wd_apply_L", "wd_export_L",
-            "wd_status_detail", "wd_status_string", "wd_kernel_stats", "wd_launch_count"]
+            "wd_status_detail", "wd_status_string", "wd_kernel_stats", "wd_launch_count",
+            "wd_selinv", "wd_sym_pattern_outer", "wd_value_gradient"]
 
 
 class WdOptions(ctypes.Structure):
@@ -97,6 +98,9 @@ def load():
         lib.wd_logdet.argtypes = [vp, ctypes.POINTER(f64)]
         lib.wd_apply_L.argtypes = [vp, vp, vp, i64, i64, ctypes.c_int, vp]
         lib.wd_export_L.argtypes = [vp, vp]
+        lib.wd_selinv.argtypes = [vp, vp, ctypes.c_int, vp]
+        lib.wd_sym_pattern_outer.argtypes = [vp, vp, vp, i64, i64, vp, ctypes.c_int, vp]
+        lib.wd_value_gradient.argtypes = [vp, f64, vp, vp, i64, i64, vp, ctypes.c_int, vp]
         lib.wd_status_detail.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_char_p, ctypes.c_size_t]
         lib.wd_kernel_stats.argtypes = [vp, ctypes.POINTER(WdKernelStat), i32, ctypes.POINTER(i32),
                                         ctypes.c_int]
@@ -280,6 +284,85 @@ class Solver:
                                          ctypes.c_void_p(So.ctypes.data), Zc.shape[1], Zc.shape[0], 0,
                                          _stream(stream, False)))
         return So
+
+    def selinv(self, out=None, stream=None):
+        """(A^-1)(i, j) at every stored lower entry of A, in the analyzed order
+        (needs an fp64 factorization).  out: CUDA float64 tensor (filled in
+        place) or None (a new numpy array)."""
+        if out is not None and _is_torch(out):
+            if out.numel() != self.nnz or not out.is_contiguous():
+                raise ValueError("out must be a contiguous tensor with one entry per stored value")
+            p, dev = _ptr(out)
+            self._check(self._lib.wd_selinv(self._h, p, dev, _stream(stream, dev)))
+            return out
+        res = np.empty(self.nnz, np.float64)
+        self._check(self._lib.wd_selinv(self._h, ctypes.c_void_p(res.ctypes.data), 0,
+                                        _stream(stream, False)))
+        return res
+
+    def sym_pattern_outer(self, U, V, out=None, stream=None):
+        """out[e] = sum_c U(i,c) V(j,c) + U(j,c) V(i,c) (i != j), sum_c U(i,c) V(i,c)
+        (i == j) at every stored lower entry e = (i, j).  U, V: n x ncols,
+        column-major (torch CUDA tensors with leading dimension n, or numpy)."""
+        if _is_torch(U):
+            import torch
+            if U.dim() == 1:
+                U, V = U.unsqueeze(1), V.unsqueeze(1)
+            n = U.shape[0]
+            for t in (U, V):
+                if t.stride(0) != 1 or (t.shape[1] > 1 and t.stride(1) != n) or t.shape != U.shape:
+                    raise ValueError("U and V must be column-major n x ncols with leading dimension n")
+            if out is None:
+                out = torch.empty(self.nnz, dtype=torch.float64, device=U.device)
+            pu, dev = _ptr(U)
+            pv, _ = _ptr(V)
+            po, _ = _ptr(out)
+            self._check(self._lib.wd_sym_pattern_outer(self._h, pu, pv, U.shape[1], n, po, dev,
+                                                       _stream(stream, dev)))
+            return out
+        Uc = np.array(U, dtype=np.float64, order="F", copy=True)
+        Vc = np.array(V, dtype=np.float64, order="F", copy=True)
+        if Uc.ndim == 1:
+            Uc, Vc = Uc[:, None], Vc[:, None]
+        if Uc.shape != Vc.shape:
+            raise ValueError("U and V must have the same shape")
+        res = np.empty(self.nnz, np.float64)
+        self._check(self._lib.wd_sym_pattern_outer(self._h, ctypes.c_void_p(Uc.ctypes.data),
+                                                   ctypes.c_void_p(Vc.ctypes.data), Uc.shape[1],
+                                                   Uc.shape[0], ctypes.c_void_p(res.ctypes.data), 0,
+                                                   _stream(stream, False)))
+        return res
+
+    def value_gradient(self, g_logdet, X, G, out=None, stream=None):
+        """dl/d(values) = g_logdet * w * A^-1 - pattern(G X^T + X G^T) at the stored
+        lower entries (w = 2 off the diagonal); X = A^-1 B, G = A^-1 dl/dX.
+        Torch CUDA tensors (column-major, leading dimension n) or numpy arrays."""
+        if _is_torch(X):
+            import torch
+            if X.dim() == 1:
+                X, G = X.unsqueeze(1), G.unsqueeze(1)
+            n = X.shape[0]
+            for t in (X, G):
+                if t.stride(0) != 1 or (t.shape[1] > 1 and t.stride(1) != n) or t.shape != X.shape:
+                    raise ValueError("X and G must be column-major n x ncols with leading dimension n")
+            if out is None:
+                out = torch.empty(self.nnz, dtype=torch.float64, device=X.device)
+            px, dev = _ptr(X)
+            pg, _ = _ptr(G)
+            po, _ = _ptr(out)
+            self._check(self._lib.wd_value_gradient(self._h, float(g_logdet), px, pg, X.shape[1], n, po,
+                                                    dev, _stream(stream, dev)))
+            return out
+        Xc = np.array(X, dtype=np.float64, order="F", copy=True)
+        Gc = np.array(G, dtype=np.float64, order="F", copy=True)
+        if Xc.ndim == 1:
+            Xc, Gc = Xc[:, None], Gc[:, None]
+        res = np.empty(self.nnz, np.float64)
+        self._check(self._lib.wd_value_gradient(self._h, float(g_logdet), ctypes.c_void_p(Xc.ctypes.data),
+                                                ctypes.c_void_p(Gc.ctypes.data), Xc.shape[1], Xc.shape[0],
+                                                ctypes.c_void_p(res.ctypes.data), 0,
+                                                _stream(stream, False)))
+        return res
 
     def kernel_stats(self, reset=False) -> list:
         """Per-kernel launches, event time and algorithmic flops/bytes

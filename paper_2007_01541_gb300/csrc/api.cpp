@@ -134,6 +134,22 @@ struct wd_ctx {
     double *d_P = nullptr;  // partial sums of chunked rows (slots x nrhs)
     double *d_norm_part = nullptr;  // partial row sums of |a| of chunked rows
     double normA = 0.0;
+    // selected inverse (built on first use; pointers into mem)
+    struct SelStep {
+        int kind;  // 0 trinv, 1 gemm, 2 zgather
+        int64_t off;
+        int count;
+    };
+    std::vector<SelStep> sel_steps;
+    bool sel_ready = false;
+    double *d_zpool = nullptr, *d_xw = nullptr, *d_sel_out = nullptr;
+    int64_t *d_xoff = nullptr, *d_upoff = nullptr;
+    int32_t *d_upmap = nullptr, *d_col2s = nullptr, *d_prow = nullptr, *d_psrc = nullptr;
+    int4 *d_sel_items = nullptr;
+    wd::GemmItem *d_sel_gemm = nullptr;
+    double sel_flops = 0.0;
+    std::vector<int64_t> h_foff;   // host copies of the front layout
+    std::vector<int32_t> h_sld;
     wd_info info{};
     // profiling
     int64_t launches = 0;  // kernels launched by this handle
@@ -550,6 +566,13 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
     h->front_elems = 0;
     h->g_factor.reset();
     h->g_solve.reset();
+    h->sel_ready = false;
+    h->sel_steps.clear();
+    h->d_zpool = h->d_xw = h->d_sel_out = nullptr;
+    h->d_xoff = h->d_upoff = nullptr;
+    h->d_upmap = h->d_col2s = h->d_prow = h->d_psrc = nullptr;
+    h->d_sel_items = nullptr;
+    h->d_sel_gemm = nullptr;
     std::string msg;
     const int dim = geom ? geom->dim : 0;
     int rc = wd::analyze(h->S, n, colptr, rowidx, dim, geom ? geom->level : nullptr,
@@ -581,6 +604,8 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
         maxk = std::max(maxk, sk[s]);
     }
     h->front_elems = (size_t)fo;
+    h->h_foff = foff;
+    h->h_sld = sld;
     h->dinv_elems = (size_t)dio;
     h->pack_total = pko;
     h->W_rows = wo;
@@ -1250,4 +1275,314 @@ extern "C" wd_status wd_export_L(wd_handle h, double *panels) {
     cudaFree(d_poff);
     if (e != cudaSuccess) return cuda_fail(h, e, "export");
     return WD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// selected inverse (Takahashi recurrences, supernodal, FP64)
+// ---------------------------------------------------------------------------
+static wd_status upload_pattern_maps(wd_handle h) {
+    const wd::Symbolic &S = h->S;
+    if (!h->d_prow) {
+        const int32_t *p = nullptr;
+        UP(S.prow, p);
+        h->d_prow = const_cast<int32_t *>(p);
+        UP(S.psrc, p);
+        h->d_psrc = const_cast<int32_t *>(p);
+    }
+    return WD_OK;
+}
+
+// X_s = L_JJ^-1 and W_s = L_RJ X_s depend on the factor only; Z_JJ starts as
+// X^T X; then, top-down by tree level: gather Z_RR from the parent's Z front,
+// Z_RJ = -Z_RR W, Z_JJ -= W^T Z_RJ.  Items carry device pointers of the front,
+// Z and X/W pools, which stay put until the next wd_analyze.
+static wd_status build_selinv(wd_handle h) {
+    const wd::Symbolic &S = h->S;
+    const int ns = S.ns;
+    std::vector<int64_t> xoff(ns), upoff(ns, 0);
+    int64_t xw = 0, up = 0;
+    for (int s = 0; s < ns; ++s) {
+        xoff[s] = xw;
+        xw += (int64_t)S.m(s) * S.k(s);
+        upoff[s] = up;
+        up += S.m(s) - S.k(s);
+        if (S.sparent[s] < 0 && S.m(s) != S.k(s))
+            return fail(h, WD_ERR_STATE, "root supernode with update rows");
+    }
+    std::vector<int32_t> upmap(std::max<int64_t>(up, 1), -1), col2s(S.n);
+    for (int c = 0; c < ns; ++c) {
+        for (int j = S.sfirst[c]; j < S.sfirst[c + 1]; ++j) col2s[j] = c;
+        const int p = S.sparent[c];
+        if (p < 0) continue;
+        const int kp_p = kpad(S.k(p)), k_p = S.k(p);
+        for (int r = 0; r < S.m(p); ++r) {
+            const int i = S.relmap[S.mapoff[c] + r];
+            if (i >= 0) upmap[upoff[c] + i] = r < k_p ? r : r + kp_p - k_p;
+        }
+    }
+    for (int c = 0; c < ns; ++c)
+        for (int i = 0; i < S.m(c) - S.k(c); ++i)
+            if (upmap[upoff[c] + i] < 0) return fail(h, WD_ERR_STATE, "update row missing in parent front");
+    CK(h->mem.alloc((void **)&h->d_zpool, h->front_elems * sizeof(double)), "selinv alloc");
+    CK(h->mem.alloc((void **)&h->d_xw, std::max<int64_t>(xw, 1) * sizeof(double)), "selinv alloc");
+    CK(cudaMemset(h->d_xw, 0, std::max<int64_t>(xw, 1) * sizeof(double)), "selinv clear");
+    CK(cudaMemset(h->d_zpool, 0, h->front_elems * sizeof(double)), "selinv clear");
+    {
+        const int64_t *p64 = nullptr;
+        const int32_t *p32 = nullptr;
+        UP(xoff, p64);
+        h->d_xoff = const_cast<int64_t *>(p64);
+        UP(upoff, p64);
+        h->d_upoff = const_cast<int64_t *>(p64);
+        UP(upmap, p32);
+        h->d_upmap = const_cast<int32_t *>(p32);
+        UP(col2s, p32);
+        h->d_col2s = const_cast<int32_t *>(p32);
+    }
+    {
+        wd_status st = upload_pattern_maps(h);
+        if (st != WD_OK) return st;
+    }
+    CK(h->mem.alloc((void **)&h->d_sel_out, std::max<int64_t>(S.pcp[S.n], 1) * sizeof(double)),
+       "selinv alloc");
+
+    const double *F = static_cast<const double *>(h->d_front);
+    double *Z = h->d_zpool, *XW = h->d_xw;
+    std::vector<int4> items;
+    std::vector<wd::GemmItem> gemm;
+    auto &steps = h->sel_steps;
+    steps.clear();
+    double flops = 0.0;
+    auto push_step = [&](int kind, int64_t off, int64_t end) {
+        if (end > off) steps.push_back({kind, off, (int)(end - off)});
+    };
+    auto tiles = [](int x) { return (x + 63) / 64; };
+    // 1) X = L_JJ^-1 by block rows
+    int maxblk = 0;
+    for (int s = 0; s < ns; ++s) maxblk = std::max(maxblk, tiles(S.k(s)));
+    for (int t = 0; t < maxblk; ++t) {
+        const int64_t o = (int64_t)items.size();
+        for (int s = 0; s < ns; ++s)
+            if (tiles(S.k(s)) > t)
+                for (int bj = 0; bj <= t; ++bj) items.push_back({s, t, bj, 0});
+        push_step(0, o, (int64_t)items.size());
+    }
+    auto gi = [](const double *A, int64_t ars, int64_t acs, const double *B, int64_t brs, int64_t bcs,
+                 double *C, int64_t crs, int64_t ccs, int M, int N, int p0, int p1, int i0, int j0,
+                 int flags, double alpha) {
+        wd::GemmItem g;
+        g.A = A;
+        g.B = B;
+        g.C = C;
+        g.a_rs = ars;
+        g.a_cs = acs;
+        g.b_rs = brs;
+        g.b_cs = bcs;
+        g.c_rs = crs;
+        g.c_cs = ccs;
+        g.M = M;
+        g.N = N;
+        g.p0 = p0;
+        g.p1 = p1;
+        g.i0 = i0;
+        g.j0 = j0;
+        g.flags = flags;
+        g.pad = 0;
+        g.alpha = alpha;
+        return g;
+    };
+    // 2) W = L_RJ X (X lower triangular: p from the tile's first column) and
+    //    Z_JJ = X^T X (lower tiles, p from the tile's first row)
+    {
+        const int64_t o = (int64_t)gemm.size();
+        for (int s = 0; s < ns; ++s) {
+            const int k = S.k(s), r = S.m(s) - S.k(s), kp = kpad(k), ld = h->h_sld[s];
+            const int64_t fo = h->h_foff[s];
+            double *X = XW + xoff[s], *W = X + (int64_t)k * k;
+            for (int ti = 0; ti < tiles(r); ++ti)
+                for (int tj = 0; tj < tiles(k); ++tj)
+                    gemm.push_back(gi(F + fo + kp, 1, ld, X, k, 1, W, 1, r, r, k, 64 * tj, k, 64 * ti,
+                                      64 * tj, 0, 1.0));
+            flops += (double)r * k * k;
+            for (int ti = 0; ti < tiles(k); ++ti)
+                for (int tj = 0; tj <= ti; ++tj)
+                    gemm.push_back(gi(X, k, 1, X, k, 1, Z + fo, 1, ld, k, k, 64 * ti, k, 64 * ti, 64 * tj,
+                                      wd::GEMM_C_LOWER, 1.0));
+            flops += (double)k * k * k / 3.0;
+        }
+        push_step(1, o, (int64_t)gemm.size());
+    }
+    // 3) top-down over the tree levels
+    for (int lv = S.nlevels - 1; lv >= 0; --lv) {
+        const int64_t oz = (int64_t)items.size();
+        for (int q = S.level_ptr[lv]; q < S.level_ptr[lv + 1]; ++q) {
+            const int s = S.level_nodes[q];
+            const int r = S.m(s) - S.k(s);
+            for (int j = 0; j < r; ++j) items.push_back({s, j, S.sparent[s], 0});
+        }
+        push_step(2, oz, (int64_t)items.size());
+        const int64_t o1 = (int64_t)gemm.size();
+        for (int q = S.level_ptr[lv]; q < S.level_ptr[lv + 1]; ++q) {
+            const int s = S.level_nodes[q];
+            const int k = S.k(s), r = S.m(s) - S.k(s), kp = kpad(k), ld = h->h_sld[s];
+            if (r == 0) continue;
+            const int64_t fo = h->h_foff[s];
+            const double *W = XW + xoff[s] + (int64_t)k * k;
+            // Z_RJ = -Z_RR W
+            for (int ti = 0; ti < tiles(r); ++ti)
+                for (int tj = 0; tj < tiles(k); ++tj)
+                    gemm.push_back(gi(Z + fo + (int64_t)kp * ld + kp, 1, ld, W, r, 1, Z + fo + kp, 1, ld, r,
+                                      k, 0, r, 64 * ti, 64 * tj, wd::GEMM_A_SYM_LOWER, -1.0));
+            flops += 2.0 * r * r * k;
+        }
+        push_step(1, o1, (int64_t)gemm.size());
+        const int64_t o2 = (int64_t)gemm.size();
+        for (int q = S.level_ptr[lv]; q < S.level_ptr[lv + 1]; ++q) {
+            const int s = S.level_nodes[q];
+            const int k = S.k(s), r = S.m(s) - S.k(s), kp = kpad(k), ld = h->h_sld[s];
+            if (r == 0) continue;
+            const int64_t fo = h->h_foff[s];
+            const double *W = XW + xoff[s] + (int64_t)k * k;
+            // Z_JJ -= W^T Z_RJ (lower)
+            for (int ti = 0; ti < tiles(k); ++ti)
+                for (int tj = 0; tj <= ti; ++tj)
+                    gemm.push_back(gi(W, r, 1, Z + fo + kp, ld, 1, Z + fo, 1, ld, k, k, 0, r, 64 * ti,
+                                      64 * tj, wd::GEMM_C_LOWER | wd::GEMM_ACCUMULATE, -1.0));
+            flops += (double)r * k * k;
+        }
+        push_step(1, o2, (int64_t)gemm.size());
+    }
+    CK(h->mem.alloc((void **)&h->d_sel_items, std::max<size_t>(items.size(), 1) * sizeof(int4)),
+       "selinv alloc");
+    if (!items.empty())
+        CK(cudaMemcpy(h->d_sel_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice),
+           "selinv upload");
+    CK(h->mem.alloc((void **)&h->d_sel_gemm, std::max<size_t>(gemm.size(), 1) * sizeof(wd::GemmItem)),
+       "selinv alloc");
+    if (!gemm.empty())
+        CK(cudaMemcpy(h->d_sel_gemm, gemm.data(), gemm.size() * sizeof(wd::GemmItem),
+                      cudaMemcpyHostToDevice),
+           "selinv upload");
+    h->sel_flops = flops;
+    h->sel_ready = true;
+    return WD_OK;
+}
+
+// Z at A's stored entries into dst (device), enqueued on st
+static wd_status selinv_enqueue(wd_handle h, double *dst, cudaStream_t st) {
+    if (!h->sel_ready) {
+        wd_status s = build_selinv(h);
+        if (s != WD_OK) return s;
+    }
+    const DevSym &d = h->dsym;
+    const double *F = static_cast<const double *>(h->d_front);
+    const double *Dv = static_cast<const double *>(h->d_dinv);
+    prof_single(h, "selinv_fp64", 0, 0, st, true);
+    for (const auto &sp : h->sel_steps) {
+        switch (sp.kind) {
+            case 0:
+                wd::launch_trinv(d, F, Dv, h->d_xw, h->d_xoff, h->d_sel_items + sp.off, sp.count, st);
+                break;
+            case 1: wd::launch_gemm_items(h->d_sel_gemm + sp.off, sp.count, st); break;
+            case 2:
+                wd::launch_zgather(d, h->d_zpool, h->d_upmap, h->d_upoff, h->d_sel_items + sp.off, sp.count,
+                                   st);
+                break;
+        }
+    }
+    wd::launch_zextract(d, h->d_zpool, h->d_col2s, h->d_psrc, dst, st);
+    prof_single(h, "selinv_fp64", h->sel_flops, 0, st, false);
+    h->launches += (int64_t)h->sel_steps.size() + 1;
+    CK(cudaGetLastError(), "selinv launch");
+    return WD_OK;
+}
+
+extern "C" wd_status wd_selinv(wd_handle h, double *out, int on_device, void *stream) {
+    if (!h || !out) return WD_ERR_INVALID_ARG;
+    if (!h->factored || h->prec != WD_FP64)
+        return fail(h, WD_ERR_STATE, "wd_selinv needs a successful WD_FP64 factorization");
+    CK(cudaSetDevice(h->device), "set device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!h->sel_ready) {
+        wd_status s = build_selinv(h);
+        if (s != WD_OK) return s;
+    }
+    wd_status s = selinv_enqueue(h, on_device ? out : h->d_sel_out, st);
+    if (s != WD_OK) return s;
+    if (!on_device)
+        CK(cudaMemcpyAsync(out, h->d_sel_out, h->S.pcp[h->S.n] * sizeof(double), cudaMemcpyDeviceToHost, st),
+           "selinv D2H");
+    CK(cudaStreamSynchronize(st), "selinv");
+    return WD_OK;
+}
+
+// out = alpha * pattern(U V^T + V U^T) + zscale * w * Z (zscale != 0 needs the
+// FP64 factor); host or device operands
+static wd_status pattern_outer(wd_handle h, const double *U, const double *V, int64_t ncols, int64_t ld,
+                               double alpha, double zscale, double *out, int on_device, void *stream) {
+    const int64_t n = h->S.n, nnz = h->S.pcp[n];
+    if (!out || ncols < 0 || (ncols > 0 && (!U || !V || ld < n)))
+        return fail(h, WD_ERR_INVALID_ARG, "bad arguments");
+    if (ncols == 0) ld = n;
+    CK(cudaSetDevice(h->device), "set device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    wd_status s = upload_pattern_maps(h);
+    if (s != WD_OK) return s;
+    const double *Zsel = nullptr;
+    if (zscale != 0.0) {
+        if (!h->factored || h->prec != WD_FP64)
+            return fail(h, WD_ERR_STATE, "the log-determinant term needs a WD_FP64 factorization");
+        if (!h->sel_ready) {
+            s = build_selinv(h);
+            if (s != WD_OK) return s;
+        }
+        s = selinv_enqueue(h, h->d_sel_out, st);
+        if (s != WD_OK) return s;
+        Zsel = h->d_sel_out;
+    }
+    const double *Ud = U, *Vd = V;
+    double *Od = out;
+    DevMem tmp;
+    if (!on_device) {
+        double *u = nullptr, *v = nullptr, *o = nullptr;
+        CK(tmp.alloc((void **)&u, std::max<int64_t>(n * ncols, 1) * sizeof(double)), "outer alloc");
+        CK(tmp.alloc((void **)&v, std::max<int64_t>(n * ncols, 1) * sizeof(double)), "outer alloc");
+        CK(tmp.alloc((void **)&o, std::max<int64_t>(nnz, 1) * sizeof(double)), "outer alloc");
+        if (ncols > 0) {
+            CK(cudaMemcpy2DAsync(u, n * sizeof(double), U, ld * sizeof(double), n * sizeof(double), ncols,
+                                 cudaMemcpyHostToDevice, st),
+               "U H2D");
+            CK(cudaMemcpy2DAsync(v, n * sizeof(double), V, ld * sizeof(double), n * sizeof(double), ncols,
+                                 cudaMemcpyHostToDevice, st),
+               "V H2D");
+        }
+        Ud = u;
+        Vd = v;
+        Od = o;
+        ld = n;
+    }
+    wd::launch_sym_outer(h->dsym, h->d_prow, h->d_psrc, Ud, Vd, ncols, ld, alpha, Zsel, zscale, Od, st);
+    h->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !on_device)
+        e = cudaMemcpyAsync(out, Od, nnz * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    tmp.free_all();
+    if (e != cudaSuccess) return cuda_fail(h, e, "pattern outer product");
+    return WD_OK;
+}
+
+extern "C" wd_status wd_sym_pattern_outer(wd_handle h, const double *U, const double *V, int64_t ncols,
+                                          int64_t ld, double *out, int on_device, void *stream) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!h->analyzed || h->opt.symbolic_only)
+        return fail(h, WD_ERR_STATE, "wd_sym_pattern_outer before wd_analyze (or on a host-only handle)");
+    return pattern_outer(h, U, V, ncols, ld, 1.0, 0.0, out, on_device, stream);
+}
+
+extern "C" wd_status wd_value_gradient(wd_handle h, double g_logdet, const double *X, const double *G,
+                                       int64_t ncols, int64_t ld, double *out, int on_device, void *stream) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!h->factored) return fail(h, WD_ERR_STATE, "wd_value_gradient before a successful wd_factor");
+    return pattern_outer(h, G, X, ncols, ld, -1.0, g_logdet, out, on_device, stream);
 }

@@ -152,4 +152,28 @@ template <class T>
 void launch_export_panels(const DevSym &d, const T *front, double *panels,
                           const int64_t *poff, cudaStream_t st);
 
+// ---- selected inverse (selinv.cu), FP64 --------------------------------------
+// C(i, j) (+)= alpha sum_{p in [p0, p1)} A(i, p) B(j, p) on the 64 x 64 tile at
+// (i0, j0) of an M x N matrix C; element (r, c) of X at X[r * x_rs + c * x_cs]
+enum { GEMM_A_SYM_LOWER = 1, GEMM_C_LOWER = 2, GEMM_ACCUMULATE = 4 };
+struct GemmItem {
+    const double *A;
+    const double *B;
+    double *C;
+    int64_t a_rs, a_cs, b_rs, b_cs, c_rs, c_cs;
+    int M, N, p0, p1, i0, j0, flags, pad;
+    double alpha;
+};
+void launch_gemm_items(const GemmItem *items, int count, cudaStream_t st);
+void launch_trinv(const DevSym &d, const double *front, const double *dinv, double *xpool,
+                  const int64_t *xoff, const int4 *items, int count, cudaStream_t st);
+void launch_zgather(const DevSym &d, double *zpool, const int32_t *upmap, const int64_t *upoff,
+                    const int4 *items, int count, cudaStream_t st);
+void launch_zextract(const DevSym &d, const double *zpool, const int32_t *col2s, const int32_t *psrc,
+                     double *out, cudaStream_t st);
+// out[src] = alpha * (pattern part of U V^T + V U^T) + zscale * w * Zsel[src] (Zsel nullable)
+void launch_sym_outer(const DevSym &d, const int32_t *prow, const int32_t *psrc, const double *U,
+                      const double *V, int64_t ncols, int64_t ld, double alpha, const double *Zsel,
+                      double zscale, double *out, cudaStream_t st);
+
 }  // namespace wd

@@ -118,3 +118,17 @@ def test_sizes_of_paper_like_configs():
     b = haar_basis(1, 10)
     cp, ri = compressed_pattern(b)
     assert 2 * ri.size - b.N == 51892
+
+
+@pytest.mark.parametrize("kind", ["exponential", "matern32"])
+@pytest.mark.parametrize("param", ["ell", "sigma2"])
+def test_kernel_parameter_derivatives(kind, param):
+    """dk/d(param) against central differences of k (relative step 1e-6)."""
+    r = np.linspace(0.0, 1.5, 301)
+    k = Kernel(kind, 0.17, 1.3)
+    d = k.derivative(param)(r)
+    h = 1e-6 * getattr(k, param)
+    kp = Kernel(kind, **{**dict(ell=0.17, sigma2=1.3), param: getattr(k, param) + h})
+    km = Kernel(kind, **{**dict(ell=0.17, sigma2=1.3), param: getattr(k, param) - h})
+    fd = (kp(r) - km(r)) / (2 * h)
+    np.testing.assert_allclose(d, fd, rtol=1e-7, atol=1e-9)

@@ -218,15 +218,30 @@ class Kernel:
     kind: str = "exponential"     # exponential | matern32 | matern12
     ell: float = 0.2
     sigma2: float = 1.0
+    wrt: str = ""                 # "" -> k itself; "ell" / "sigma2" -> dk/d(parameter)
 
     def __call__(self, r, xp=np):
         t = r / self.ell
         if self.kind in ("exponential", "matern12"):
-            return self.sigma2 * xp.exp(-t)
+            e = xp.exp(-t)
+            if self.wrt == "ell":
+                return self.sigma2 * t * e / self.ell
+            return (1.0 if self.wrt == "sigma2" else self.sigma2) * e
         if self.kind == "matern32":
             u = math.sqrt(3.0) * t
-            return self.sigma2 * (1.0 + u) * xp.exp(-u)
+            e = xp.exp(-u)
+            if self.wrt == "ell":
+                return self.sigma2 * u * u * e / self.ell
+            return (1.0 if self.wrt == "sigma2" else self.sigma2) * (1.0 + u) * e
         raise ValueError(self.kind)
+
+    def derivative(self, param: str) -> "Kernel":
+        """dk/d(param) for param in ("ell", "sigma2") as a kernel of the same
+        family (the compressed matrix is linear in k, so mask(T dK T^T) is
+        dA/d(param); the nugget's derivative is the identity)."""
+        if param not in ("ell", "sigma2"):
+            raise ValueError(param)
+        return Kernel(self.kind, self.ell, self.sigma2, param)
 
 
 def _cell_centroids(dim: int, J: int, xp=np, device=None):
