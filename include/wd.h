@@ -207,6 +207,28 @@ wd_status wd_value_gradient(wd_handle h, double g_logdet, const double *X, const
    diagonal of the panel are zero.  Synchronous. */
 wd_status wd_export_L(wd_handle h, double *panels);
 
+/* Allocation-free variant of wd_export_L.  The paper has no counterpart: this
+   call exists for callers that cannot allocate device memory while it runs,
+   e.g. when another allocator (a framework's caching allocator, a memory cap)
+   holds the device memory so that wd_export_L's factor-sized cudaMalloc would
+   fail, or when the device-wide synchronization of cudaMalloc / cudaFree
+   would stall the caller's other streams.
+   Writes the same panels as wd_export_L (info.nnz_L_stored doubles, same
+   layout) into the caller's DEVICE buffer `panels`, enqueued on `stream`,
+   and returns without waiting; launch errors are returned, errors of the
+   running kernels surface at the caller's next synchronization.
+   Allocates nothing: the only scratch (the panels' offsets) is a static
+   device array of WD_NOALLOC_MAX_SUPERNODES + 1 int64 values (512 KiB), one
+   per device.  More supernodes than that: WD_ERR_INVALID_ARG, nothing
+   enqueued.  Nothing in the scratch has to start at zero (every call rewrites
+   the offsets before reading them).  The first call on a device looks up the
+   array's address (cudaGetSymbolAddress), which may load the module: make
+   that first call during set-up, before any stream capture.  Calls whose
+   executions overlap (unordered streams, several host threads) share the
+   scratch and race: order them.  Needs a successful wd_factor. */
+#define WD_NOALLOC_MAX_SUPERNODES 65536
+wd_status wd_export_L_noalloc(wd_handle h, double *panels, void *stream);
+
 /* Per-kernel statistics accumulated while wd_options.profile = 1: name (the
    kernel and its precision), launches, summed event time, and the
    algorithmic flops and bytes of those launches (flops of the arithmetic the

@@ -29,7 +29,7 @@ _PREC = {"fp64": WD_FP64, "mixed": WD_MIXED, WD_FP64: WD_FP64, WD_MIXED: WD_MIXE
 EXPORTED = ["wd_default_options", "wd_create", "wd_destroy", "wd_analyze", "wd_symbolic_export",
             "wd_get_info", "wd_factor", "wd_solve", "wd_logdet", "wd_apply_L", "wd_export_L",
             "wd_status_detail", "wd_status_string", "wd_kernel_stats", "wd_launch_count",
-            "wd_selinv", "wd_sym_pattern_outer", "wd_value_gradient"]
+            "wd_selinv", "wd_sym_pattern_outer", "wd_value_gradient", "wd_export_L_noalloc"]
 
 
 class WdOptions(ctypes.Structure):
@@ -101,6 +101,7 @@ def load():
         lib.wd_selinv.argtypes = [vp, vp, ctypes.c_int, vp]
         lib.wd_sym_pattern_outer.argtypes = [vp, vp, vp, i64, i64, vp, ctypes.c_int, vp]
         lib.wd_value_gradient.argtypes = [vp, f64, vp, vp, i64, i64, vp, ctypes.c_int, vp]
+        lib.wd_export_L_noalloc.argtypes = [vp, vp, vp]
         lib.wd_status_detail.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_char_p, ctypes.c_size_t]
         lib.wd_kernel_stats.argtypes = [vp, ctypes.POINTER(WdKernelStat), i32, ctypes.POINTER(i32),
                                         ctypes.c_int]
@@ -384,6 +385,17 @@ class Solver:
         """Stored supernodal panels (see wd_export_L)."""
         out = np.empty(self._panel_size(), np.float64)
         self._check(self._lib.wd_export_L(self._h, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def export_L_noalloc(self, out, stream=None):
+        """wd_export_L into a preallocated contiguous CUDA float64 tensor of
+        _panel_size() entries, enqueued on the stream, without allocating."""
+        if not _is_torch(out) or not out.is_cuda or not out.is_contiguous():
+            raise ValueError("out must be a contiguous CUDA tensor")
+        if out.dtype != __import__("torch").float64 or out.numel() != self._panel_size():
+            raise ValueError("out must hold one float64 per stored panel entry")
+        p, _ = _ptr(out)
+        self._check(self._lib.wd_export_L_noalloc(self._h, p, _stream(stream, True)))
         return out
 
     def _panel_size(self) -> int:

@@ -1586,3 +1586,24 @@ extern "C" wd_status wd_value_gradient(wd_handle h, double g_logdet, const doubl
     if (!h->factored) return fail(h, WD_ERR_STATE, "wd_value_gradient before a successful wd_factor");
     return pattern_outer(h, G, X, ncols, ld, -1.0, g_logdet, out, on_device, stream);
 }
+
+extern "C" wd_status wd_export_L_noalloc(wd_handle h, double *panels, void *stream) {
+    if (!h || !panels) return WD_ERR_INVALID_ARG;
+    if (!h->factored) return fail(h, WD_ERR_STATE, "wd_export_L_noalloc before a successful wd_factor");
+    if (h->S.ns > wd::NOALLOC_MAX_SUPERNODES)
+        return fail(h, WD_ERR_INVALID_ARG,
+                    std::to_string(h->S.ns) + " supernodes exceed the static scratch of " +
+                        std::to_string(wd::NOALLOC_MAX_SUPERNODES) + " panel offsets");
+    CK(cudaSetDevice(h->device), "set device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int64_t *poff = nullptr;
+    CK(wd::noalloc_panel_offsets(h->device, &poff), "scratch address");
+    wd::launch_panel_offsets_noalloc(h->dsym, st);
+    if (h->prec == WD_FP64)
+        wd::launch_export_panels<double>(h->dsym, static_cast<const double *>(h->d_front), panels, poff, st);
+    else
+        wd::launch_export_panels<float>(h->dsym, static_cast<const float *>(h->d_front), panels, poff, st);
+    h->launches += 2;
+    CK(cudaGetLastError(), "export launch");
+    return WD_OK;
+}

@@ -176,4 +176,12 @@ void launch_sym_outer(const DevSym &d, const int32_t *prow, const int32_t *psrc,
                       const double *V, int64_t ncols, int64_t ld, double alpha, const double *Zsel,
                       double zscale, double *out, cudaStream_t st);
 
+// ---- allocation-free export of the factor (noalloc.cu) ---------------------
+// the panel offsets sit in a static device array of NOALLOC_MAX_SUPERNODES + 1
+// entries; *addr = its address on `device` (looked up once per device)
+constexpr int NOALLOC_MAX_SUPERNODES = 65536;
+cudaError_t noalloc_panel_offsets(int device, int64_t **addr);
+// writes the offsets of all d.ns panels (d.ns <= NOALLOC_MAX_SUPERNODES)
+void launch_panel_offsets_noalloc(const DevSym &d, cudaStream_t st);
+
 }  // namespace wd

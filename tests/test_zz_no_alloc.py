@@ -1,0 +1,54 @@
+"""wd_export_L_noalloc (static device scratch, no allocation) against
+wd_export_L on the same factor; two calls in a row, the output poisoned in
+between.  Named to be collected last; it also passes run alone."""
+import numpy as np
+import pytest
+
+from wdgen import Kernel, compressed_pattern, compressed_values, haar_basis
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_noalloc_export_matches_export(wdlib, cuda, prec):
+    torch = cuda
+    b = haar_basis(2, 6)
+    cp, ri = compressed_pattern(b)
+    v = compressed_values(b, cp, ri, Kernel("matern32", 0.1), 1e-3)
+    s = wdlib.Solver().analyze(cp, ri, b).factor(v, prec)
+    ref = s.export_L()
+    out = torch.empty(ref.size, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    for _ in range(2):
+        out.fill_(float("nan"))
+        torch.cuda.current_stream().synchronize()
+        with torch.cuda.stream(stream):
+            s.export_L_noalloc(out, stream=stream.cuda_stream)
+        stream.synchronize()
+        assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_noalloc_export_rejects_too_many_supernodes(wdlib, cuda):
+    torch = cuda
+    n = 70000                                   # a diagonal matrix: n singleton supernodes
+    cp = np.arange(n + 1, dtype=np.int64)
+    ri = np.arange(n, dtype=np.int32)
+    s = wdlib.Solver().analyze(cp, ri).factor(np.full(n, 2.0), "fp64")
+    assert s.info()["nsuper"] > 65536
+    out = torch.zeros(n, dtype=torch.float64, device="cuda")
+    with pytest.raises(wdlib.WdError) as e:
+        s.export_L_noalloc(out)
+    assert e.value.status == wdlib.WD_ERR_INVALID_ARG
+    assert "static scratch" in str(e.value)
+    torch.cuda.synchronize()
+    assert float(out.abs().max()) == 0.0        # nothing was enqueued
+
+
+def test_noalloc_export_needs_factor(wdlib, cuda):
+    torch = cuda
+    b = haar_basis(1, 6)
+    cp, ri = compressed_pattern(b)
+    s = wdlib.Solver().analyze(cp, ri, b)
+    with pytest.raises(wdlib.WdError) as e:
+        s.export_L_noalloc(torch.empty(s._panel_size(), dtype=torch.float64, device="cuda"))
+    assert e.value.status == wdlib.WD_ERR_STATE
