@@ -129,6 +129,25 @@ void wd_destroy(wd_handle h);
 wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, const int32_t *rowidx,
                      const wd_geometry *geom);
 
+/* Batch of independent systems (Section 5's many-instance use, one GPU):
+   count instances, instance i with its own lower CSC pattern (n[i], colptr[i],
+   rowidx[i]) and optional geometry geom[i] (geom may be NULL for none).  The
+   handle then holds the block-diagonal matrix diag(A_0, ..., A_{count-1}):
+   its analysis is the union of the instances' analyses, and every later call
+   works on it as one matrix, so one launch per tree level covers all
+   instances.  wd_factor takes the instances' values concatenated in instance
+   order (instance i's values in its rowidx order); wd_solve / wd_apply_L take
+   right-hand sides whose rows are the instances' rows concatenated (sum n[i]
+   rows).  Refinement, and the backward error reported by wd_solve, use each
+   instance's own normwise backward error (the largest over instances and
+   columns is reported).  Instances given with identical pointers (n, colptr,
+   rowidx and geometry arrays) are analyzed once.  Host, multithreaded. */
+wd_status wd_analyze_batch(wd_handle h, int32_t count, const int64_t *n, const int64_t *const *colptr,
+                           const int32_t *const *rowidx, const wd_geometry *geom);
+
+/* log det A_i of every instance of a batch (host array of count doubles). */
+wd_status wd_logdet_batch(wd_handle h, double *out);
+
 /* Copy the symbolic result into caller-allocated host arrays (any may be
    NULL): perm[n] (perm[new] = old), parent[n] (elimination tree of P A P^T,
    -1 for roots), colcount[n] (nonzeros of column j of L incl. diagonal),

@@ -29,7 +29,8 @@ _PREC = {"fp64": WD_FP64, "mixed": WD_MIXED, WD_FP64: WD_FP64, WD_MIXED: WD_MIXE
 EXPORTED = ["wd_default_options", "wd_create", "wd_destroy", "wd_analyze", "wd_symbolic_export",
             "wd_get_info", "wd_factor", "wd_solve", "wd_logdet", "wd_apply_L", "wd_export_L",
             "wd_status_detail", "wd_status_string", "wd_kernel_stats", "wd_launch_count",
-            "wd_selinv", "wd_sym_pattern_outer", "wd_value_gradient", "wd_export_L_noalloc"]
+            "wd_selinv", "wd_sym_pattern_outer", "wd_value_gradient", "wd_export_L_noalloc",
+            "wd_analyze_batch", "wd_logdet_batch"]
 
 
 class WdOptions(ctypes.Structure):
@@ -102,6 +103,8 @@ def load():
         lib.wd_sym_pattern_outer.argtypes = [vp, vp, vp, i64, i64, vp, ctypes.c_int, vp]
         lib.wd_value_gradient.argtypes = [vp, f64, vp, vp, i64, i64, vp, ctypes.c_int, vp]
         lib.wd_export_L_noalloc.argtypes = [vp, vp, vp]
+        lib.wd_analyze_batch.argtypes = [vp, i32, vp, vp, vp, vp]
+        lib.wd_logdet_batch.argtypes = [vp, vp]
         lib.wd_status_detail.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_char_p, ctypes.c_size_t]
         lib.wd_kernel_stats.argtypes = [vp, ctypes.POINTER(WdKernelStat), i32, ctypes.POINTER(i32),
                                         ctypes.c_int]
@@ -200,6 +203,45 @@ class Solver:
         self.n = n
         self.nnz = int(cp[-1])
         return self
+
+    def analyze_batch(self, patterns, bases=None):
+        """Independent instances as one block-diagonal matrix.  patterns: list
+        of (colptr, rowidx); bases: list of objects with dim, level, box_lo,
+        box_side (or None).  Instances passing the very same arrays share one
+        analysis."""
+        cnt = len(patterns)
+        keep = []
+        conv = {}
+
+        def arr(a, dt):
+            key = (id(a), dt)
+            if key not in conv:
+                conv[key] = np.ascontiguousarray(a, dt)
+                keep.append(a)
+            return conv[key]
+
+        cps = [arr(cp, np.int64) for cp, _ in patterns]
+        ris = [arr(ri, np.int32) for _, ri in patterns]
+        ns = np.array([c.size - 1 for c in cps], np.int64)
+        pcp = (ctypes.c_void_p * cnt)(*[c.ctypes.data for c in cps])
+        pri = (ctypes.c_void_p * cnt)(*[r.ctypes.data for r in ris])
+        geo = None
+        if bases is not None:
+            geo = (WdGeometry * cnt)()
+            for i, b in enumerate(bases):
+                lev, lo, side = arr(b.level, np.int32), arr(b.box_lo, np.int32), arr(b.box_side, np.int32)
+                geo[i] = WdGeometry(int(b.dim), lev.ctypes.data, lo.ctypes.data, side.ctypes.data, None)
+        self._check(self._lib.wd_analyze_batch(self._h, cnt, ns.ctypes.data, pcp, pri, geo))
+        del keep
+        self.n = int(ns.sum())
+        self.nnz = int(sum(int(c[-1]) for c in cps))
+        self.batch_sizes = ns
+        return self
+
+    def logdet_batch(self) -> np.ndarray:
+        out = np.empty(len(self.batch_sizes), np.float64)
+        self._check(self._lib.wd_logdet_batch(self._h, ctypes.c_void_p(out.ctypes.data)))
+        return out
 
     def info(self) -> dict:
         i = WdInfo()

@@ -2,7 +2,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <thread>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -148,6 +150,16 @@ struct wd_ctx {
     int4 *d_sel_items = nullptr;
     wd::GemmItem *d_sel_gemm = nullptr;
     double sel_flops = 0.0;
+    // batch of independent instances (wd_analyze_batch): column and supernode offsets
+    int32_t batch_count = 0;
+    std::vector<int64_t> batch_coff;
+    std::vector<int32_t> batch_soff;
+    int32_t *d_batch_soff = nullptr;
+    int64_t *d_batch_coff = nullptr;
+    double *d_batch_norm = nullptr;   // per-instance ||A_i||_inf
+    double *d_batch_ld = nullptr;     // per-instance log det
+    double *d_batch_cm = nullptr;     // per-instance column maxima (solve workspace)
+    std::vector<double> batch_normA;
     std::vector<int64_t> h_foff;   // host copies of the front layout
     std::vector<int32_t> h_sld;
     wd_info info{};
@@ -535,12 +547,8 @@ static void fill_info(wd_handle h, int64_t nnzl, int maxm, int maxk,
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
-extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, const int32_t *rowidx,
-                                const wd_geometry *geom) {
-    if (!h) return WD_ERR_INVALID_ARG;
-    if (n <= 0 || !colptr || !rowidx) return fail(h, WD_ERR_INVALID_ARG, "bad size or null pattern");
-    if (geom && (geom->patch || geom->dim < 0 || geom->dim > 3))
-        return fail(h, WD_ERR_INVALID_ARG, "unsupported geometry");
+// drop everything of a previous analysis; set up the device and stream
+static wd_status reset_analysis(wd_handle h) {
     const bool host_only = h->opt.symbolic_only != 0;
     if (!host_only) {
         CK(cudaSetDevice(h->device), "set device");
@@ -548,7 +556,6 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
         if (!h->cap_stream)
             CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "stream");
     }
-    auto t0 = std::chrono::steady_clock::now();
     h->analyzed = h->factored = false;
     if (!host_only) {
         h->work.free_all();
@@ -563,6 +570,7 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
     h->ws_cols = 0;
     h->d_front = nullptr;
     h->d_dinv = nullptr;
+    h->d_values_stage = nullptr;
     h->front_elems = 0;
     h->g_factor.reset();
     h->g_solve.reset();
@@ -573,13 +581,121 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
     h->d_upmap = h->d_col2s = h->d_prow = h->d_psrc = nullptr;
     h->d_sel_items = nullptr;
     h->d_sel_gemm = nullptr;
-    std::string msg;
+    h->batch_count = 0;
+    h->batch_coff.clear();
+    h->batch_soff.clear();
+    h->d_batch_soff = nullptr;
+    h->d_batch_coff = nullptr;
+    h->d_batch_norm = nullptr;
+    h->d_batch_ld = nullptr;
+    h->d_batch_cm = nullptr;
+    h->batch_normA.clear();
+    return WD_OK;
+}
+
+static wd_status finish_analysis(wd_handle h, std::chrono::steady_clock::time_point t0);
+
+static wd_status check_geometry(wd_handle h, const wd_geometry *geom) {
+    if (geom && (geom->patch || geom->dim < 0 || geom->dim > 3))
+        return fail(h, WD_ERR_INVALID_ARG, "unsupported geometry");
+    return WD_OK;
+}
+
+static int analyze_one(wd_handle h, wd::Symbolic &S, int64_t n, const int64_t *colptr,
+                       const int32_t *rowidx, const wd_geometry *geom, std::string &msg) {
     const int dim = geom ? geom->dim : 0;
-    int rc = wd::analyze(h->S, n, colptr, rowidx, dim, geom ? geom->level : nullptr,
-                         geom ? geom->box_lo : nullptr, geom ? geom->box_side : nullptr,
-                         h->opt.nd_leaf, h->opt.relax_k, h->opt.relax_pct, msg);
+    return wd::analyze(S, n, colptr, rowidx, dim, geom ? geom->level : nullptr,
+                       geom ? geom->box_lo : nullptr, geom ? geom->box_side : nullptr, h->opt.nd_leaf,
+                       h->opt.relax_k, h->opt.relax_pct, msg);
+}
+
+extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, const int32_t *rowidx,
+                                const wd_geometry *geom) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (n <= 0 || !colptr || !rowidx) return fail(h, WD_ERR_INVALID_ARG, "bad size or null pattern");
+    wd_status st = check_geometry(h, geom);
+    if (st != WD_OK) return st;
+    auto t0 = std::chrono::steady_clock::now();
+    st = reset_analysis(h);
+    if (st != WD_OK) return st;
+    std::string msg;
+    int rc = analyze_one(h, h->S, n, colptr, rowidx, geom, msg);
     if (rc) return fail(h, (wd_status)rc, msg);
+    return finish_analysis(h, t0);
+}
+
+extern "C" wd_status wd_analyze_batch(wd_handle h, int32_t count, const int64_t *n,
+                                      const int64_t *const *colptr, const int32_t *const *rowidx,
+                                      const wd_geometry *geom) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (count <= 0 || !n || !colptr || !rowidx) return fail(h, WD_ERR_INVALID_ARG, "bad batch");
+    for (int32_t i = 0; i < count; ++i) {
+        if (n[i] <= 0 || !colptr[i] || !rowidx[i])
+            return fail(h, WD_ERR_INVALID_ARG, "bad size or null pattern of instance " + std::to_string(i));
+        wd_status st = check_geometry(h, geom ? geom + i : nullptr);
+        if (st != WD_OK) return st;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    wd_status st = reset_analysis(h);
+    if (st != WD_OK) return st;
+    // instances with the same pattern and geometry arrays (same pointers) share one analysis
+    std::vector<int32_t> uniq(count, -1);
+    std::vector<int32_t> reps;
+    for (int32_t i = 0; i < count; ++i) {
+        for (size_t q = 0; q < reps.size(); ++q) {
+            const int32_t r = reps[q];
+            const bool same_geom =
+                (!geom) || (geom[r].dim == geom[i].dim && geom[r].level == geom[i].level &&
+                            geom[r].box_lo == geom[i].box_lo && geom[r].box_side == geom[i].box_side);
+            if (n[r] == n[i] && colptr[r] == colptr[i] && rowidx[r] == rowidx[i] && same_geom) {
+                uniq[i] = (int32_t)q;
+                break;
+            }
+        }
+        if (uniq[i] < 0) {
+            uniq[i] = (int32_t)reps.size();
+            reps.push_back(i);
+        }
+    }
+    std::vector<wd::Symbolic> parts(reps.size());
+    std::vector<int> rcs(reps.size(), 0);
+    std::vector<std::string> msgs(reps.size());
+    {
+        const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::atomic<size_t> next{0};
+        auto work = [&]() {
+            for (size_t q = next++; q < reps.size(); q = next++) {
+                const int32_t i = reps[q];
+                rcs[q] = analyze_one(h, parts[q], n[i], colptr[i], rowidx[i], geom ? geom + i : nullptr,
+                                     msgs[q]);
+            }
+        };
+        std::vector<std::thread> pool;
+        for (unsigned t = 1; t < std::min<size_t>(hw, reps.size()); ++t) pool.emplace_back(work);
+        work();
+        for (auto &t : pool) t.join();
+    }
+    for (size_t q = 0; q < reps.size(); ++q)
+        if (rcs[q]) return fail(h, (wd_status)rcs[q], "instance " + std::to_string(reps[q]) + ": " + msgs[q]);
+    std::vector<const wd::Symbolic *> seq(count);
+    for (int32_t i = 0; i < count; ++i) seq[i] = &parts[uniq[i]];
+    std::string msg;
+    int rc = wd::merge(h->S, seq, msg);
+    if (rc) return fail(h, (wd_status)rc, msg);
+    h->batch_count = count;
+    h->batch_coff.assign(count + 1, 0);
+    h->batch_soff.assign(count + 1, 0);
+    for (int32_t i = 0; i < count; ++i) {
+        h->batch_coff[i + 1] = h->batch_coff[i] + seq[i]->n;
+        h->batch_soff[i + 1] = h->batch_soff[i] + seq[i]->ns;
+    }
+    return finish_analysis(h, t0);
+}
+
+static wd_status finish_analysis(wd_handle h, std::chrono::steady_clock::time_point t0) {
+    const bool host_only = h->opt.symbolic_only != 0;
     wd::Symbolic &S = h->S;
+    const int64_t n = S.n;
     const int ns = S.ns;
     // per-supernode arrays
     std::vector<int32_t> sk(ns), sm(ns), skp(ns), sld(ns);
@@ -722,6 +838,16 @@ extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, c
         if (st != WD_OK) return st;
     }
     CK(h->mem.alloc((void **)&h->d_tstatus, sizeof(status_t)), "status alloc");
+    if (h->batch_count > 0) {
+        const int64_t *pc = nullptr;
+        const int32_t *ps = nullptr;
+        UP(h->batch_coff, pc);
+        UP(h->batch_soff, ps);
+        h->d_batch_coff = const_cast<int64_t *>(pc);
+        h->d_batch_soff = const_cast<int32_t *>(ps);
+        CK(h->mem.alloc((void **)&h->d_batch_norm, h->batch_count * sizeof(double)), "batch alloc");
+        CK(h->mem.alloc((void **)&h->d_batch_ld, h->batch_count * sizeof(double)), "batch alloc");
+    }
     fill_info(h, nnzl, maxm, maxk, t0);
     h->analyzed = true;
     return WD_OK;
@@ -973,6 +1099,14 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
     wd::launch_norm_inf_rows(h->dsym, h->d_spmv_chunks, h->n_spmv_chunks, h->d_spmv_fin, h->n_spmv_fin,
                              h->d_norm_part, h->d_scalars, st);
     h->launches += h->n_spmv_fin > 0 ? 2 : 1;
+    if (h->batch_count > 0) {
+        wd::launch_seg_norm_inf(h->dsym, h->d_batch_coff, h->batch_count, h->d_batch_norm, st);
+        h->launches += 1;
+        h->batch_normA.resize(h->batch_count);
+        CK(cudaMemcpyAsync(h->batch_normA.data(), h->d_batch_norm, h->batch_count * sizeof(double),
+                           cudaMemcpyDeviceToHost, st),
+           "norm D2H");
+    }
     CK(cudaGetLastError(), "factor launch");
     status_t status = 0, tstatus = 0;
     CK(cudaMemcpyAsync(&status, h->d_status, sizeof(status_t), cudaMemcpyDeviceToHost, st), "status D2H");
@@ -980,9 +1114,16 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
     CK(cudaMemcpyAsync(&h->normA, h->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, st), "norm D2H");
     CK(cudaStreamSynchronize(st), "factor");
     if (tstatus != 0) return fail(h, WD_ERR_TIMEOUT, "a bounded wait of the tensor-core update expired");
-    if (status != ~0ULL)
-        return fail(h, WD_ERR_NOT_SPD, "pivot not positive at column " + std::to_string(status),
-                    (int64_t)status);
+    if (status != ~0ULL) {
+        std::string where = "pivot not positive at column " + std::to_string(status);
+        if (h->batch_count > 0) {
+            const auto it = std::upper_bound(h->batch_coff.begin(), h->batch_coff.end(), (int64_t)status);
+            const int64_t inst = (it - h->batch_coff.begin()) - 1;
+            where += " (instance " + std::to_string(inst) + ", its column " +
+                     std::to_string((int64_t)status - h->batch_coff[inst]) + " in factor order)";
+        }
+        return fail(h, WD_ERR_NOT_SPD, where, (int64_t)status);
+    }
     h->prec = prec;
     h->factored = true;
     return WD_OK;
@@ -1009,6 +1150,10 @@ static wd_status ensure_solve_ws(wd_handle h, int64_t nrhs) {
     CK(h->work.alloc((void **)&h->d_R, n * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc((void **)&h->d_cm, 3 * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc((void **)&h->d_P, std::max(h->n_spmv_slots, 1) * nrhs * sizeof(double)), "solve ws");
+    h->d_batch_cm = nullptr;
+    if (h->batch_count > 0)
+        CK(h->work.alloc((void **)&h->d_batch_cm, 3 * (int64_t)h->batch_count * nrhs * sizeof(double)),
+           "solve ws");
     h->ws_cols = nrhs;
     return WD_OK;
 }
@@ -1058,6 +1203,25 @@ static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cud
     wd::launch_spmv_residual(h->dsym, h->d_spmv_chunks, h->n_spmv_chunks, h->d_spmv_fin,
                              h->n_spmv_fin, X, h->d_Bp, h->d_R, h->d_P, nrhs, st);
     prof_single(h, "spmv_residual_fp64", 2.0 * nf * nrhs, 12.0 * nf + 24.0 * n * nrhs, st, false);
+    if (h->batch_count > 0) {
+        // per instance and column: each instance is its own system
+        const int cnt = h->batch_count;
+        wd::launch_seg_colmax3(h->d_R, X, h->d_Bp, h->d_batch_coff, cnt, (int)nrhs, h->d_batch_cm, st);
+        h->launches += 2;
+        std::vector<double> cm(3 * (size_t)cnt * nrhs);
+        CK(cudaMemcpyAsync(cm.data(), h->d_batch_cm, cm.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
+           "be D2H");
+        CK(cudaStreamSynchronize(st), "backward error");
+        double mx = 0.0;
+        for (int i = 0; i < cnt; ++i)
+            for (int64_t c = 0; c < nrhs; ++c) {
+                const double *q = cm.data() + ((size_t)i * nrhs + c) * 3;
+                const double den = h->batch_normA[i] * q[1] + q[2];
+                mx = std::max(mx, den > 0 ? q[0] / den : 0.0);
+            }
+        *be_max = mx;
+        return WD_OK;
+    }
     wd::launch_colmax3(h->d_R, X, h->d_Bp, n, nrhs, h->d_cm, st);
     h->launches += 2;
     std::vector<double> cm(3 * nrhs);
@@ -1184,6 +1348,24 @@ extern "C" wd_status wd_logdet(wd_handle h, double *out) {
     h->launches += 2;
     CK(cudaGetLastError(), "logdet launch");
     CK(cudaMemcpy(out, h->d_scalars + 1, sizeof(double), cudaMemcpyDeviceToHost), "logdet D2H");
+    return WD_OK;
+}
+
+extern "C" wd_status wd_logdet_batch(wd_handle h, double *out) {
+    if (!h || !out) return WD_ERR_INVALID_ARG;
+    if (!h->factored) return fail(h, WD_ERR_STATE, "wd_logdet_batch before a successful wd_factor");
+    if (h->batch_count == 0) return fail(h, WD_ERR_STATE, "not a batch (use wd_analyze_batch)");
+    CK(cudaSetDevice(h->device), "set device");
+    double *dst = h->d_batch_ld;
+    if (h->prec == WD_FP64)
+        wd::launch_seg_logdet<double>(h->dsym, static_cast<const double *>(h->d_front), h->d_batch_soff,
+                                      h->batch_count, dst, 0);
+    else
+        wd::launch_seg_logdet<float>(h->dsym, static_cast<const float *>(h->d_front), h->d_batch_soff,
+                                     h->batch_count, dst, 0);
+    h->launches += 1;
+    CK(cudaGetLastError(), "logdet launch");
+    CK(cudaMemcpy(out, dst, h->batch_count * sizeof(double), cudaMemcpyDeviceToHost), "logdet D2H");
     return WD_OK;
 }
 

@@ -176,6 +176,14 @@ void launch_sym_outer(const DevSym &d, const int32_t *prow, const int32_t *psrc,
                       const double *V, int64_t ncols, int64_t ld, double alpha, const double *Zsel,
                       double zscale, double *out, cudaStream_t st);
 
+// ---- per-instance reductions of a block-diagonal batch (batch.cu) ----------
+void launch_seg_norm_inf(const DevSym &d, const int64_t *coff, int count, double *out, cudaStream_t st);
+void launch_seg_colmax3(const double *R, const double *X, const double *B, const int64_t *coff, int count,
+                        int nrhs, double *out, cudaStream_t st);
+template <class T>
+void launch_seg_logdet(const DevSym &d, const T *front, const int32_t *soff, int count, double *out,
+                       cudaStream_t st);
+
 // ---- allocation-free export of the factor (noalloc.cu) ---------------------
 // the panel offsets sit in a static device array of NOALLOC_MAX_SUPERNODES + 1
 // entries; *addr = its address on `device` (looked up once per device)

@@ -399,4 +399,100 @@ int analyze(Symbolic &S, int64_t n, const int64_t *cp, const int32_t *ri, int di
     return OK;
 }
 
+// Block-diagonal union of independent analyses: instance i occupies columns
+// [coff_i, coff_i + n_i), its supernodes, rows, stored values and maps are
+// shifted by the running totals; levels (tree heights) merge, so one launch
+// per level covers every instance.
+int merge(Symbolic &S, const std::vector<const Symbolic *> &parts, std::string &msg) {
+    S = Symbolic();
+    int64_t n = 0, nnz = 0, nrows = 0, nmap = 0;
+    int64_t ns = 0;
+    int32_t nlev = 0;
+    for (const Symbolic *P : parts) {
+        n += P->n;
+        nnz += P->pcp[P->n];
+        nrows += (int64_t)P->srows.size();
+        nmap += (int64_t)P->relmap.size();
+        ns += P->ns;
+        nlev = std::max(nlev, P->nlevels);
+    }
+    if (n > INT32_MAX || nnz > INT32_MAX || ns > INT32_MAX || nrows > INT64_MAX / 2) {
+        msg = "batch too large for 32-bit column / value indices";
+        return ERR_INVALID_ARG;
+    }
+    S.n = n;
+    S.perm.reserve(n);
+    S.iperm.reserve(n);
+    S.parent.reserve(n);
+    S.colcount.reserve(n);
+    S.pcp.assign(1, 0);
+    S.pcp.reserve(n + 1);
+    S.prow.reserve(nnz);
+    S.psrc.reserve(nnz);
+    S.alrow.reserve(nnz);
+    S.sfirst.reserve(ns + 1);
+    S.srowptr.assign(1, 0);
+    S.srowptr.reserve(ns + 1);
+    S.srows.reserve(nrows);
+    S.sparent.reserve(ns);
+    S.slevel.reserve(ns);
+    S.mapoff.reserve(ns);
+    S.relmap.reserve(nmap);
+    int32_t coff = 0, soff = 0;
+    int64_t voff = 0, roff = 0, moff = 0;
+    for (const Symbolic *P : parts) {
+        for (int64_t j = 0; j < P->n; ++j) {
+            S.perm.push_back(P->perm[j] + coff);
+            S.iperm.push_back(P->iperm[j] + coff);
+            S.parent.push_back(P->parent[j] < 0 ? -1 : P->parent[j] + coff);
+            S.colcount.push_back(P->colcount[j]);
+            S.pcp.push_back(P->pcp[j + 1] + voff);
+        }
+        for (size_t e = 0; e < P->prow.size(); ++e) {
+            S.prow.push_back(P->prow[e] + coff);
+            S.psrc.push_back((int32_t)(P->psrc[e] + voff));
+            S.alrow.push_back(P->alrow[e]);
+        }
+        for (int32_t t = 0; t < P->ns; ++t) {
+            S.sfirst.push_back(P->sfirst[t] + coff);
+            S.srowptr.push_back(P->srowptr[t + 1] + roff);
+            S.sparent.push_back(P->sparent[t] < 0 ? -1 : P->sparent[t] + soff);
+            S.slevel.push_back(P->slevel[t]);
+            S.mapoff.push_back(P->mapoff[t] < 0 ? -1 : P->mapoff[t] + moff);
+        }
+        for (int32_t r : P->srows) S.srows.push_back(r + coff);
+        S.relmap.insert(S.relmap.end(), P->relmap.begin(), P->relmap.end());
+        S.flops += P->flops;
+        S.nnzL += P->nnzL;
+        S.nnzL_stored += P->nnzL_stored;
+        coff += (int32_t)P->n;
+        soff += P->ns;
+        voff += P->pcp[P->n];
+        roff += (int64_t)P->srows.size();
+        moff += (int64_t)P->relmap.size();
+    }
+    S.sfirst.push_back((int32_t)n);
+    S.ns = (int32_t)ns;
+    S.child_ptr.assign(ns + 1, 0);
+    for (int32_t t = 0; t < S.ns; ++t)
+        if (S.sparent[t] >= 0) ++S.child_ptr[S.sparent[t] + 1];
+    for (int32_t t = 0; t < S.ns; ++t) S.child_ptr[t + 1] += S.child_ptr[t];
+    S.children.resize(S.child_ptr[ns]);
+    {
+        std::vector<int32_t> fill(S.child_ptr.begin(), S.child_ptr.end() - 1);
+        for (int32_t t = 0; t < S.ns; ++t)
+            if (S.sparent[t] >= 0) S.children[fill[S.sparent[t]]++] = t;
+    }
+    S.nlevels = nlev;
+    S.level_ptr.assign(nlev + 1, 0);
+    for (int32_t t = 0; t < S.ns; ++t) ++S.level_ptr[S.slevel[t] + 1];
+    for (int32_t l = 0; l < nlev; ++l) S.level_ptr[l + 1] += S.level_ptr[l];
+    S.level_nodes.resize(ns);
+    {
+        std::vector<int32_t> fill(S.level_ptr.begin(), S.level_ptr.end() - 1);
+        for (int32_t t = 0; t < S.ns; ++t) S.level_nodes[fill[S.slevel[t]]++] = t;
+    }
+    return OK;
+}
+
 }  // namespace wd

@@ -47,4 +47,7 @@ int analyze(Symbolic &S, int64_t n, const int64_t *colptr, const int32_t *rowidx
             const int32_t *level, const int32_t *box_lo, const int32_t *box_side, int leaf,
             int relax_k, int relax_pct, std::string &msg);
 
+// Block-diagonal union of independent analyses (instances in order).
+int merge(Symbolic &S, const std::vector<const Symbolic *> &parts, std::string &msg);
+
 }  // namespace wd

@@ -96,3 +96,53 @@ def test_library_exports_every_declared_symbol(wdlib):
     missing = [n for n in sorted(names) if not hasattr(lib, n)]
     assert not missing, missing
     assert set(wdlib.EXPORTED) <= names
+
+
+def test_batch_analysis_is_the_block_diagonal_union(wdlib):
+    """wd_analyze_batch equals the instances' own analyses, shifted by the
+    running column / row offsets (and instances passing the same arrays share
+    one analysis)."""
+    specs = [(1, 7), (2, 4), (1, 7), (2, 5), (1, 6)]
+    cache = {}
+    pats, bases = [], []
+    for d, J in specs:
+        if (d, J) not in cache:
+            b = haar_basis(d, J)
+            cache[(d, J)] = (b, compressed_pattern(b))
+        b, p = cache[(d, J)]
+        bases.append(b)
+        pats.append(p)
+    sb = wdlib.Solver(symbolic_only=True).analyze_batch(pats, bases)
+    got = sb.symbolic()
+    coff = roff = 0
+    perm, parent, cc, sf, srp, rows = [], [], [], [], [0], []
+    for (cp, ri), b in zip(pats, bases):
+        one = wdlib.Solver(symbolic_only=True).analyze(cp, ri, b).symbolic()
+        n = cp.size - 1
+        perm.append(one["perm"] + coff)
+        parent.append(np.where(one["parent"] < 0, -1, one["parent"] + coff))
+        cc.append(one["colcount"])
+        sf.append(one["super_first"][:-1] + coff)
+        srp.extend((one["super_rowptr"][1:] + roff).tolist())
+        rows.append(one["super_rows"] + coff)
+        coff += n
+        roff += int(one["super_rowptr"][-1])
+    assert np.array_equal(got["perm"], np.concatenate(perm))
+    assert np.array_equal(got["parent"], np.concatenate(parent))
+    assert np.array_equal(got["colcount"], np.concatenate(cc))
+    assert np.array_equal(got["super_first"], np.concatenate(sf + [[coff]]))
+    assert np.array_equal(got["super_rowptr"], np.array(srp))
+    assert np.array_equal(got["super_rows"], np.concatenate(rows))
+    inf = sb.info()
+    assert inf["n"] == coff and inf["nnz_A_lower"] == sum(p[1].size for p in pats)
+
+
+def test_batch_analysis_rejects_bad_instance(wdlib):
+    b = haar_basis(1, 5)
+    cp, ri = compressed_pattern(b)
+    bad = cp.copy()
+    bad[-1] += 1
+    s = wdlib.Solver(symbolic_only=True)
+    with pytest.raises(wdlib.WdError) as e:
+        s.analyze_batch([(cp, ri), (bad, ri)], [b, b])
+    assert "instance 1" in str(e.value)

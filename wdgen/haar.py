@@ -385,3 +385,59 @@ def workload_autograd(J: int = 7, nrhs: int = 32, ell: float = 0.15, sigma2: flo
     """2D Matern-1/2 workload of the gradient experiment."""
     return haar_workload(2, J, Kernel("matern12", ell, sigma2), nugget, nrhs,
                          name=f"2d_haar_{1 << J}x{1 << J}_matern12", **kw)
+
+
+# --------------------------------------------------------------------------
+# batch of independent instances
+# --------------------------------------------------------------------------
+BATCH_LEVELS = {1: (10, 11, 12, 13, 14), 2: (5, 6, 7)}
+
+
+def batch_instances(count: int = 256, seed: int = 0):
+    """Parameters of the batched configuration: instance i has dim 1 (even i)
+    or 2 (odd i); J uniform over BATCH_LEVELS[dim] (N = 2^J or 4^J, from 1024
+    to 16384); ell ~ U[0.05, 0.5]; exponential kernel, sigma^2 = 1, nugget
+    1e-2.  Draw order per instance: J, then ell, from default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        dim = 1 if i % 2 == 0 else 2
+        levels = BATCH_LEVELS[dim]
+        J = int(levels[int(rng.integers(len(levels)))])
+        ell = float(rng.uniform(0.05, 0.5))
+        out.append(dict(dim=dim, J=J, ell=ell, N=(1 << J) ** dim, nugget=1e-2))
+    return out
+
+
+@dataclass
+class BatchWorkload:
+    params: list
+    bases: list              # one Basis per instance (shared objects per (dim, J))
+    patterns: list           # (colptr, rowidx) per instance (shared per (dim, J))
+    values: list             # per instance: float64 numpy array
+    B: np.ndarray            # (sum N, nrhs): rows of the instances concatenated
+
+    @property
+    def N(self) -> int:
+        return int(sum(p["N"] for p in self.params))
+
+
+def batch_workload(count: int = 256, seed: int = 0, nrhs: int = 1, device: str = "cpu",
+                   params=None) -> BatchWorkload:
+    """The instances of batch_instances(count, seed) (or params): patterns and
+    bases are built once per (dim, J) and shared; values per instance; right-
+    hand sides rhs(sum N, nrhs, seed) over the concatenated rows."""
+    params = batch_instances(count, seed) if params is None else params
+    cache = {}
+    bases, patterns, values = [], [], []
+    for p in params:
+        key = (p["dim"], p["J"])
+        if key not in cache:
+            b = haar_basis(p["dim"], p["J"])
+            cache[key] = (b, compressed_pattern(b))
+        b, (cp, ri) = cache[key]
+        bases.append(b)
+        patterns.append((cp, ri))
+        values.append(compressed_values(b, cp, ri, Kernel("exponential", p["ell"]), p["nugget"], device))
+    N = int(sum(p["N"] for p in params))
+    return BatchWorkload(params, bases, patterns, values, rhs(N, nrhs, seed))
