@@ -80,14 +80,19 @@ typedef struct {
 
 /* Optional geometry for the nested-dissection ordering.  Per vertex (basis
    function) lambda: its level j = |lambda| (Section 2), the lower corner and
-   side of the axis-aligned box supp psi_lambda in integer finest-cell units.
-   box_lo is n x dim row-major.  patch is reserved and must be NULL. */
+   side of the axis-aligned box supp psi_lambda in integer finest-cell units
+   of its parameter domain.  box_lo is n x dim row-major.  patch (may be
+   NULL): for a surface made of several parameter domains (e.g. the six
+   faces of a cubed sphere), the domain of each vertex, 0..31; boxes are then
+   in their own domain's units, and the dissection first cuts along domain
+   boundaries (lowest two domains against the rest, then one against the
+   other) before cutting boxes inside a domain. */
 typedef struct {
     int32_t dim;                 /* 1, 2 or 3                                  */
     const int32_t *level;        /* [n]                                        */
     const int32_t *box_lo;       /* [n * dim]                                  */
     const int32_t *box_side;     /* [n]                                        */
-    const int32_t *patch;        /* must be NULL                               */
+    const int32_t *patch;        /* [n] or NULL                                */
 } wd_geometry;
 
 typedef struct {

@@ -51,11 +51,11 @@ def _load():
             lib.or_destroy.argtypes = [ctypes.c_void_p]
             lib.or_analyze.restype = ctypes.c_int
             lib.or_analyze.argtypes = [ctypes.c_void_p, ctypes.c_int64, _i64p, _i32p, ctypes.c_int,
-                                       _i32p, _i32p, _i32p, ctypes.c_int32, ctypes.c_int32,
+                                       _i32p, _i32p, _i32p, _i32p, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, _i32p]
             lib.or_nd_order_tree.restype = ctypes.c_int
             lib.or_nd_order_tree.argtypes = [ctypes.c_int64, _i64p, _i32p, ctypes.c_int, _i32p,
-                                             _i32p, _i32p, ctypes.c_int32, _i32p, _i64p,
+                                             _i32p, _i32p, _i32p, ctypes.c_int32, _i32p, _i64p,
                                              ctypes.c_int64, _i64p]
             for f in ("or_n", "or_nnzL", "or_nsuper_rows"):
                 getattr(lib, f).restype = ctypes.c_int64
@@ -90,11 +90,13 @@ def _p(a, t):
 
 def _geom(basis):
     if basis is None:
-        return 0, None, None, None
+        return 0, None, None, None, None
     lev = np.ascontiguousarray(basis.level, np.int32)
     lo = np.ascontiguousarray(basis.box_lo, np.int32)
     side = np.ascontiguousarray(basis.box_side, np.int32)
-    return basis.dim, lev, lo, side
+    patch = getattr(basis, "patch", None)
+    patch = None if patch is None else np.ascontiguousarray(patch, np.int32)
+    return basis.dim, lev, lo, side, patch
 
 
 def nd_order(colptr, rowidx, basis, leaf: int = 64, want_tree: bool = False):
@@ -104,13 +106,13 @@ def nd_order(colptr, rowidx, basis, leaf: int = 64, want_tree: bool = False):
     cp = np.ascontiguousarray(colptr, np.int64)
     ri = np.ascontiguousarray(rowidx, np.int32)
     n = cp.size - 1
-    dim, lev, lo, side = _geom(basis)
+    dim, lev, lo, side, patch = _geom(basis)
     perm = np.empty(n, np.int32)
     cap = n + 1
     tree = np.empty((cap, 4), np.int64)
     nt = np.zeros(1, np.int64)
     rc = lib.or_nd_order_tree(n, _p(cp, _i64p), _p(ri, _i32p), dim, _p(lev, _i32p),
-                              _p(lo, _i32p), _p(side, _i32p), leaf, _p(perm, _i32p),
+                              _p(lo, _i32p), _p(side, _i32p), _p(patch, _i32p), leaf, _p(perm, _i32p),
                               _p(tree, _i64p), cap, _p(nt, _i64p))
     if rc:
         raise RuntimeError(f"or_nd_order failed: {rc}")
@@ -128,11 +130,12 @@ class Oracle:
         self.colptr = np.ascontiguousarray(colptr, np.int64)
         self.rowidx = np.ascontiguousarray(rowidx, np.int32)
         self.n = self.colptr.size - 1
-        dim, lev, lo, side = _geom(basis)
+        dim, lev, lo, side, patch = _geom(basis)
         pin = None if perm is None else np.ascontiguousarray(perm, np.int32)
         rc = self._lib.or_analyze(self._ctx, self.n, _p(self.colptr, _i64p),
                                   _p(self.rowidx, _i32p), dim, _p(lev, _i32p), _p(lo, _i32p),
-                                  _p(side, _i32p), leaf, relax_k, relax_pct, _p(pin, _i32p))
+                                  _p(side, _i32p), _p(patch, _i32p), leaf, relax_k, relax_pct,
+                                  _p(pin, _i32p))
         if rc:
             raise ValueError(f"or_analyze failed: {rc}")
         n = self.n

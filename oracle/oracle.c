@@ -7,7 +7,11 @@
  * benchmark's CPU-baseline leg load it; the product never does.
  *
  *  - or_analyze   : geometric nested-dissection ordering (Section 4, the block
- *                   form of P A P^T with V1, V2 before the separator S), then
+ *                   form of P A P^T with V1, V2 before the separator S; with
+ *                   patch ids, e.g. the six faces of a cubed sphere, the
+ *                   patch sets are dissected first: the lowest two patches
+ *                   against the rest, two patches one against the other),
+ *                   then
  *                   the structure of L by explicit set unions over the
  *                   elimination tree (the fill characterisation of the
  *                   Lemma in Section 4), the elimination tree parent and
@@ -86,6 +90,7 @@ typedef struct {
     const int64_t *adjp; /* full adjacency without the diagonal */
     const int32_t *adj;
     const int32_t *level, *lo, *side;
+    const int32_t *patch; /* optional patch id per vertex (NULL: one patch) */
     int32_t leaf;
     int32_t *stamp;  /* membership stamp per vertex */
     int32_t *inS;
@@ -111,14 +116,74 @@ static int cmp_sep(const void *a, const void *b) {
     return (x > y) - (x < y);
 }
 
-static void nd_rec(nd_state *st, int32_t *V, int64_t nv, const int64_t *rlo, const int64_t *rhi) {
+/* Split of a set of patches (bit mask, more than one bit): the lowest two
+   patches against the rest, or the lower against the higher of two. */
+static uint32_t patch_split(uint32_t mask) {
+    uint32_t first = mask & (~mask + 1u);
+    uint32_t rest = mask & ~first;
+    if ((rest & (rest - 1u)) == 0u) return first; /* two patches: {p0} | {p1} */
+    return first | (rest & (~rest + 1u));         /* {p0, p1} | rest */
+}
+
+static void nd_rec(nd_state *st, int32_t *V, int64_t nv, const int64_t *rlo, const int64_t *rhi,
+                   uint32_t pmask) {
     int dim = st->dim;
     int one_cell = 1;
     for (int a = 0; a < dim; ++a)
         if (rhi[a] - rlo[a] > 1) one_cell = 0;
-    if (nv <= st->leaf || one_cell) {
+    int multi = st->patch && (pmask & (pmask - 1u)) != 0u;
+    if (nv <= st->leaf || (one_cell && !multi)) {
         qsort(V, (size_t)nv, sizeof(int32_t), cmp_int32);
         for (int64_t i = 0; i < nv; ++i) st->out[st->pos++] = V[i];
+        return;
+    }
+    if (multi) {
+        /* the patches first: side 0 = the patches of the first group */
+        uint32_t ma = patch_split(pmask), mb = pmask & ~ma;
+        int32_t stamp = ++st->cur;
+        for (int64_t i = 0; i < nv; ++i) {
+            int32_t v = V[i];
+            st->stamp[v] = stamp;
+            st->inS[v] = 0;
+            st->sd[v] = ((ma >> st->patch[v]) & 1u) ? 0 : 1;
+        }
+        for (int64_t i = 0; i < nv; ++i) {
+            int32_t u = V[i];
+            for (int64_t q = st->adjp[u]; q < st->adjp[u + 1]; ++q) {
+                int32_t w = st->adj[q];
+                if (st->stamp[w] != stamp || st->sd[w] == st->sd[u]) continue;
+                int32_t pick;
+                if (st->level[u] != st->level[w])
+                    pick = (st->level[u] < st->level[w]) ? u : w;
+                else if (st->side[u] != st->side[w])
+                    pick = (st->side[u] > st->side[w]) ? u : w;
+                else
+                    pick = (st->sd[u] == 0) ? u : w;
+                st->inS[pick] = 1;
+            }
+        }
+        int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
+        int64_t n0 = 0, n1 = 0, ns = 0;
+        for (int64_t i = 0; i < nv; ++i)
+            if (!st->inS[V[i]] && st->sd[V[i]] == 0) buf[n0++] = V[i];
+        for (int64_t i = 0; i < nv; ++i)
+            if (!st->inS[V[i]] && st->sd[V[i]] == 1) buf[n0 + n1++] = V[i];
+        for (int64_t i = 0; i < nv; ++i)
+            if (st->inS[V[i]]) buf[n0 + n1 + ns++] = V[i];
+        int32_t *S = buf + n0 + n1;
+        int64_t p0 = st->pos;
+        nd_rec(st, buf, n0, rlo, rhi, ma);
+        int64_t p1 = st->pos;
+        nd_rec(st, buf + n0, n1, rlo, rhi, mb);
+        int64_t p2 = st->pos;
+        if (st->tree && st->ntree < st->tree_cap) {
+            int64_t *t = st->tree + 4 * st->ntree++;
+            t[0] = p0; t[1] = p1; t[2] = p2; t[3] = p2 + ns;
+        }
+        g_level_for_sort = st->level;
+        qsort(S, (size_t)ns, sizeof(int32_t), cmp_sep);
+        for (int64_t i = 0; i < ns; ++i) st->out[st->pos++] = S[i];
+        free(buf);
         return;
     }
     int axis = 0;
@@ -166,9 +231,9 @@ static void nd_rec(nd_state *st, int32_t *V, int64_t nv, const int64_t *rlo, con
     /* copy the separator out before recursion reuses the stamps */
     int32_t *S = buf + n0 + n1;
     int64_t p0 = st->pos;
-    nd_rec(st, buf, n0, llo, lhi);
+    nd_rec(st, buf, n0, llo, lhi, pmask);
     int64_t p1 = st->pos;
-    nd_rec(st, buf + n0, n1, hlo, hhi);
+    nd_rec(st, buf + n0, n1, hlo, hhi, pmask);
     int64_t p2 = st->pos;
     if (st->tree && st->ntree < st->tree_cap) {
         int64_t *t = st->tree + 4 * st->ntree++;
@@ -212,16 +277,25 @@ static void full_adjacency(int64_t n, const int64_t *cp, const int32_t *ri, int6
    nodes are recorded as 4 positions (V1 start, V2 start, S start, S end) and
    their number is stored in *ntree. */
 int or_nd_order_tree(int64_t n, const int64_t *cp, const int32_t *ri, int dim,
-                     const int32_t *level, const int32_t *lo, const int32_t *side, int32_t leaf,
-                     int32_t *perm, int64_t *tree, int64_t tree_cap, int64_t *ntree) {
+                     const int32_t *level, const int32_t *lo, const int32_t *side,
+                     const int32_t *patch, int32_t leaf, int32_t *perm, int64_t *tree,
+                     int64_t tree_cap, int64_t *ntree) {
     if (n <= 0 || dim < 1 || dim > 3) return -1;
+    uint32_t pmask = 1u; /* one patch unless patch ids are given */
+    if (patch) {
+        pmask = 0u;
+        for (int64_t v = 0; v < n; ++v) {
+            if (patch[v] < 0 || patch[v] > 31) return -1;
+            pmask |= 1u << patch[v];
+        }
+    }
     int64_t *adjp;
     int32_t *adj;
     full_adjacency(n, cp, ri, &adjp, &adj);
     nd_state st;
     memset(&st, 0, sizeof(st));
     st.n = n; st.dim = dim; st.adjp = adjp; st.adj = adj;
-    st.level = level; st.lo = lo; st.side = side; st.leaf = leaf;
+    st.level = level; st.lo = lo; st.side = side; st.patch = patch; st.leaf = leaf;
     st.stamp = (int32_t *)calloc((size_t)n, sizeof(int32_t));
     st.inS = (int32_t *)calloc((size_t)n, sizeof(int32_t));
     st.sd = (int32_t *)calloc((size_t)n, sizeof(int32_t));
@@ -236,7 +310,7 @@ int or_nd_order_tree(int64_t n, const int64_t *cp, const int32_t *ri, int dim,
         }
     int32_t *V = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     for (int64_t v = 0; v < n; ++v) V[v] = (int32_t)v;
-    nd_rec(&st, V, n, rlo, rhi);
+    nd_rec(&st, V, n, rlo, rhi, pmask);
     free(V);
     free(st.stamp); free(st.inS); free(st.sd); free(adjp); free(adj);
     if (ntree) *ntree = st.ntree;
@@ -244,8 +318,9 @@ int or_nd_order_tree(int64_t n, const int64_t *cp, const int32_t *ri, int dim,
 }
 
 int or_nd_order(int64_t n, const int64_t *cp, const int32_t *ri, int dim, const int32_t *level,
-                const int32_t *lo, const int32_t *side, int32_t leaf, int32_t *perm) {
-    return or_nd_order_tree(n, cp, ri, dim, level, lo, side, leaf, perm, NULL, 0, NULL);
+                const int32_t *lo, const int32_t *side, const int32_t *patch, int32_t leaf,
+                int32_t *perm) {
+    return or_nd_order_tree(n, cp, ri, dim, level, lo, side, patch, leaf, perm, NULL, 0, NULL);
 }
 
 /* ------------------------------------------------------------------ */
@@ -417,8 +492,8 @@ static void supernodes(or_ctx *c, int32_t relax_k, int32_t relax_pct) {
  * perm_in is given.
  */
 int or_analyze(or_ctx *c, int64_t n, const int64_t *cp, const int32_t *ri, int dim,
-               const int32_t *level, const int32_t *lo, const int32_t *side, int32_t leaf,
-               int32_t relax_k, int32_t relax_pct, const int32_t *perm_in) {
+               const int32_t *level, const int32_t *lo, const int32_t *side, const int32_t *patch,
+               int32_t leaf, int32_t relax_k, int32_t relax_pct, const int32_t *perm_in) {
     free_all(c);
     if (n <= 0) return -1;
     /* validation: sorted, in range, diagonal first */
@@ -433,7 +508,7 @@ int or_analyze(or_ctx *c, int64_t n, const int64_t *cp, const int32_t *ri, int d
     if (perm_in) {
         memcpy(c->perm, perm_in, sizeof(int32_t) * (size_t)n);
     } else if (dim > 0 && level) {
-        int rc = or_nd_order(n, cp, ri, dim, level, lo, side, leaf, c->perm);
+        int rc = or_nd_order(n, cp, ri, dim, level, lo, side, patch, leaf, c->perm);
         if (rc) return rc;
     } else {
         for (int64_t i = 0; i < n; ++i) c->perm[i] = (int32_t)i;

@@ -195,8 +195,11 @@ class Solver:
             lev = np.ascontiguousarray(basis.level, np.int32)
             lo = np.ascontiguousarray(basis.box_lo, np.int32)
             side = np.ascontiguousarray(basis.box_side, np.int32)
-            keep = [lev, lo, side]
-            g = WdGeometry(int(basis.dim), lev.ctypes.data, lo.ctypes.data, side.ctypes.data, None)
+            patch = getattr(basis, "patch", None)
+            patch = None if patch is None else np.ascontiguousarray(patch, np.int32)
+            keep = [lev, lo, side, patch]
+            g = WdGeometry(int(basis.dim), lev.ctypes.data, lo.ctypes.data, side.ctypes.data,
+                           None if patch is None else patch.ctypes.data)
         self._check(self._lib.wd_analyze(self._h, n, cp.ctypes.data, ri.ctypes.data,
                                          ctypes.byref(g) if g is not None else None))
         del keep
@@ -230,7 +233,10 @@ class Solver:
             geo = (WdGeometry * cnt)()
             for i, b in enumerate(bases):
                 lev, lo, side = arr(b.level, np.int32), arr(b.box_lo, np.int32), arr(b.box_side, np.int32)
-                geo[i] = WdGeometry(int(b.dim), lev.ctypes.data, lo.ctypes.data, side.ctypes.data, None)
+                pt = getattr(b, "patch", None)
+                pt = None if pt is None else arr(pt, np.int32)
+                geo[i] = WdGeometry(int(b.dim), lev.ctypes.data, lo.ctypes.data, side.ctypes.data,
+                                    None if pt is None else pt.ctypes.data)
         self._check(self._lib.wd_analyze_batch(self._h, cnt, ns.ctypes.data, pcp, pri, geo))
         del keep
         self.n = int(ns.sum())

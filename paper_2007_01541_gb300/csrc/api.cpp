@@ -596,7 +596,7 @@ static wd_status reset_analysis(wd_handle h) {
 static wd_status finish_analysis(wd_handle h, std::chrono::steady_clock::time_point t0);
 
 static wd_status check_geometry(wd_handle h, const wd_geometry *geom) {
-    if (geom && (geom->patch || geom->dim < 0 || geom->dim > 3))
+    if (geom && (geom->dim < 0 || geom->dim > 3))
         return fail(h, WD_ERR_INVALID_ARG, "unsupported geometry");
     return WD_OK;
 }
@@ -605,8 +605,9 @@ static int analyze_one(wd_handle h, wd::Symbolic &S, int64_t n, const int64_t *c
                        const int32_t *rowidx, const wd_geometry *geom, std::string &msg) {
     const int dim = geom ? geom->dim : 0;
     return wd::analyze(S, n, colptr, rowidx, dim, geom ? geom->level : nullptr,
-                       geom ? geom->box_lo : nullptr, geom ? geom->box_side : nullptr, h->opt.nd_leaf,
-                       h->opt.relax_k, h->opt.relax_pct, msg);
+                       geom ? geom->box_lo : nullptr, geom ? geom->box_side : nullptr,
+                       geom ? geom->patch : nullptr, h->opt.nd_leaf, h->opt.relax_k, h->opt.relax_pct,
+                       msg);
 }
 
 extern "C" wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, const int32_t *rowidx,
@@ -646,7 +647,8 @@ extern "C" wd_status wd_analyze_batch(wd_handle h, int32_t count, const int64_t 
             const int32_t r = reps[q];
             const bool same_geom =
                 (!geom) || (geom[r].dim == geom[i].dim && geom[r].level == geom[i].level &&
-                            geom[r].box_lo == geom[i].box_lo && geom[r].box_side == geom[i].box_side);
+                            geom[r].box_lo == geom[i].box_lo && geom[r].box_side == geom[i].box_side &&
+                            geom[r].patch == geom[i].patch);
             if (n[r] == n[i] && colptr[r] == colptr[i] && rowidx[r] == rowidx[i] && same_geom) {
                 uniq[i] = (int32_t)q;
                 break;

@@ -39,16 +39,30 @@ void build_graph(int64_t n, const int64_t *cp, const int32_t *ri, std::vector<in
 // level, then the larger support, then the side-0 vertex.  Order: V1, V2
 // (recursively), then S with finer levels first and the coarsest functions
 // last.  Regions of one cell or sets of <= leaf vertices are emitted in index
-// order.  Implemented with an explicit task stack.
+// order.  With patch ids (several parameter domains, e.g. the faces of a
+// cubed sphere) a set spanning more than one patch is first cut along patch
+// boundaries: its lowest two patches against the others, or, for two patches,
+// one against the other; the side of a vertex is its patch's group and the
+// separator rule is the same.  Implemented with an explicit task stack.
 struct NDTask {
     int kind;                 // 0 = dissect, 1 = emit separator
     std::vector<int32_t> V;
     int64_t lo[3], hi[3];
+    uint32_t pmask;           // patches of V (bit p)
 };
+
+// patch group of the first side: {p0} of {p0, p1}, else {p0, p1} of more
+uint32_t first_patch_group(uint32_t mask) {
+    const uint32_t low = mask & (~mask + 1u);
+    const uint32_t others = mask & ~low;
+    if ((others & (others - 1u)) == 0u) return low;
+    return low | (others & (~others + 1u));
+}
 
 void nested_dissection(int64_t n, int dim, const std::vector<int64_t> &xadj,
                        const std::vector<int32_t> &adj, const int32_t *level, const int32_t *blo,
-                       const int32_t *bside, int leaf, std::vector<int32_t> &perm) {
+                       const int32_t *bside, const int32_t *patch, int leaf,
+                       std::vector<int32_t> &perm) {
     perm.clear();
     perm.reserve(n);
     std::vector<int64_t> tag(n, -1);
@@ -62,6 +76,11 @@ void nested_dissection(int64_t n, int dim, const std::vector<int64_t> &xadj,
     for (int64_t v = 0; v < n; ++v)
         for (int a = 0; a < dim; ++a)
             root.hi[a] = std::max<int64_t>(root.hi[a], (int64_t)blo[v * dim + a] + bside[v]);
+    root.pmask = 1u;
+    if (patch) {
+        root.pmask = 0u;
+        for (int64_t v = 0; v < n; ++v) root.pmask |= 1u << patch[v];
+    }
     stack.push_back(std::move(root));
     int64_t next_tag = 0;
     while (!stack.empty()) {
@@ -81,17 +100,22 @@ void nested_dissection(int64_t n, int dim, const std::vector<int64_t> &xadj,
             if (t.hi[a] - t.lo[a] > 1) single = false;
             if (t.hi[a] - t.lo[a] > t.hi[axis] - t.lo[axis]) axis = a;
         }
-        if ((int64_t)t.V.size() <= leaf || single) {
+        const bool multi = patch && (t.pmask & (t.pmask - 1u)) != 0u;
+        if ((int64_t)t.V.size() <= leaf || (single && !multi)) {
             std::sort(t.V.begin(), t.V.end());
             perm.insert(perm.end(), t.V.begin(), t.V.end());
             continue;
         }
         const int64_t cut = t.lo[axis] + (t.hi[axis] - t.lo[axis]) / 2;
+        const uint32_t group0 = multi ? first_patch_group(t.pmask) : 0u;
         const int64_t id = next_tag++;
         for (int32_t v : t.V) {
             tag[v] = id;
             sep[v] = 0;
-            side[v] = (2 * (int64_t)blo[(int64_t)v * dim + axis] + bside[v] < 2 * cut) ? 0 : 1;
+            if (multi)
+                side[v] = ((group0 >> patch[v]) & 1u) ? 0 : 1;
+            else
+                side[v] = (2 * (int64_t)blo[(int64_t)v * dim + axis] + bside[v] < 2 * cut) ? 0 : 1;
         }
         for (int32_t u : t.V) {
             for (int64_t q = xadj[u]; q < xadj[u + 1]; ++q) {
@@ -116,8 +140,14 @@ void nested_dissection(int64_t n, int dim, const std::vector<int64_t> &xadj,
             a.lo[d] = b.lo[d] = t.lo[d];
             a.hi[d] = b.hi[d] = t.hi[d];
         }
-        a.hi[axis] = cut;
-        b.lo[axis] = cut;
+        if (multi) {
+            a.pmask = group0;
+            b.pmask = t.pmask & ~group0;
+        } else {
+            a.pmask = b.pmask = t.pmask;
+            a.hi[axis] = cut;
+            b.lo[axis] = cut;
+        }
         stack.push_back(std::move(s));
         stack.push_back(std::move(b));
         stack.push_back(std::move(a));
@@ -127,8 +157,8 @@ void nested_dissection(int64_t n, int dim, const std::vector<int64_t> &xadj,
 }  // namespace
 
 int analyze(Symbolic &S, int64_t n, const int64_t *cp, const int32_t *ri, int dim,
-            const int32_t *level, const int32_t *blo, const int32_t *bside, int leaf, int relax_k,
-            int relax_pct, std::string &msg) {
+            const int32_t *level, const int32_t *blo, const int32_t *bside, const int32_t *patch,
+            int leaf, int relax_k, int relax_pct, std::string &msg) {
     S = Symbolic();
     if (n <= 0 || n > INT32_MAX - 1 || !cp || !ri) {
         msg = "invalid size or null pattern";
@@ -166,10 +196,16 @@ int analyze(Symbolic &S, int64_t n, const int64_t *cp, const int32_t *ri, int di
             msg = "geometry dim must be 1..3";
             return ERR_INVALID_ARG;
         }
+        if (patch)
+            for (int64_t v = 0; v < n; ++v)
+                if (patch[v] < 0 || patch[v] > 31) {
+                    msg = "patch ids must be 0..31";
+                    return ERR_INVALID_ARG;
+                }
         std::vector<int64_t> xadj;
         std::vector<int32_t> adj;
         build_graph(n, cp, ri, xadj, adj);
-        nested_dissection(n, dim, xadj, adj, level, blo, bside, std::max(leaf, 1), S.perm);
+        nested_dissection(n, dim, xadj, adj, level, blo, bside, patch, std::max(leaf, 1), S.perm);
     } else {
         S.perm.resize(n);
         std::iota(S.perm.begin(), S.perm.end(), 0);

@@ -43,9 +43,10 @@ struct Symbolic {
 };
 
 // Returns 0 or a wd_status code, with msg describing the failure.
+// patch: optional patch id (0..31) per vertex, NULL for a single domain.
 int analyze(Symbolic &S, int64_t n, const int64_t *colptr, const int32_t *rowidx, int dim,
-            const int32_t *level, const int32_t *box_lo, const int32_t *box_side, int leaf,
-            int relax_k, int relax_pct, std::string &msg);
+            const int32_t *level, const int32_t *box_lo, const int32_t *box_side,
+            const int32_t *patch, int leaf, int relax_k, int relax_pct, std::string &msg);
 
 // Block-diagonal union of independent analyses (instances in order).
 int merge(Symbolic &S, const std::vector<const Symbolic *> &parts, std::string &msg);
