@@ -225,3 +225,61 @@ def test_autograd_hyperparameter_finite_differences(wdlib, cuda):
 
     fd_n = (nll_nug(eps) - nll_nug(-eps)) / (2 * eps)
     assert abs(d_nug - fd_n) <= 1e-6 * max(1.0, abs(fd_n))
+
+
+def test_autograd_configuration_full_size(wdlib, cuda):
+    """The gradient configuration at full size (2D 128^2, N = 16,384, Matern-1/2
+    l = 0.15, sigma^2 = 1, nugget 1e-2, 32 observation vectors): selected-
+    inverse entries of sampled columns against solves with unit vectors
+    (refined to backward error 1e-12 against A itself), the value gradient
+    against central differences of the loss in a random direction, and the
+    l-derivative against central differences in l."""
+    import torch
+    from paper_2007_01541_gb300.autograd import SPDSystem, gp_negative_log_likelihood
+    from wdgen import workload_autograd
+    w = workload_autograd(device="cuda")
+    b, cp, ri = w.basis, w.colptr, w.rowidx
+    n = b.N
+    assert n == 16384 and w.B.shape[1] == 32
+    sysm = SPDSystem(cp, ri, b)
+    vals = torch.tensor(w.values, device="cuda", requires_grad=True)
+    Y = torch.tensor(np.ascontiguousarray(w.B.T), device="cuda").T
+    loss = gp_negative_log_likelihood(sysm, vals, Y)
+    loss.backward()
+    g = vals.grad.cpu().numpy()
+    assert np.all(np.isfinite(g))
+    # selected inverse at sampled columns: A^-1 e_j by the refined FP64 solve
+    s = sysm.solver
+    s.factor(w.values, "fp64")
+    z = s.selinv()
+    rng = np.random.default_rng(3)
+    cols = rng.choice(n, 8, replace=False)
+    E = np.zeros((n, cols.size))
+    E[cols, np.arange(cols.size)] = 1.0
+    Xe = s.solve(E)
+    assert s.last_solve["backward_error"] <= 1e-12
+    i, j = _lower_entries(cp, ri)
+    scale = np.abs(z).max()
+    for q, c in enumerate(cols):
+        sel = np.nonzero(j == c)[0]                  # stored entries (i, c), i >= c
+        assert np.abs(z[sel] - Xe[i[sel], q]).max() <= 1e-10 * scale
+        sel = np.nonzero(i == c)[0]                  # stored entries (c, j), j < c
+        assert np.abs(z[sel] - Xe[j[sel], q]).max() <= 1e-10 * scale
+    # value gradient: directional central difference
+    d = rng.standard_normal(ri.size) * np.abs(w.values)
+    h = 1e-6
+
+    def nll(v):
+        return gp_negative_log_likelihood(sysm, torch.tensor(v, device="cuda"), Y).item()
+
+    fd = (nll(w.values + h * d) - nll(w.values - h * d)) / (2 * h)
+    assert abs(float(g @ d) - fd) <= 1e-6 * max(1.0, abs(fd))
+    # hyperparameter l through dA/dl
+    ker = w.kernel
+    dA = compressed_values(b, cp, ri, ker.derivative("ell"), 0.0, "cuda")
+    d_ell = float(g @ dA)
+    he = 1e-5 * ker.ell
+    vp = compressed_values(b, cp, ri, Kernel(ker.kind, ker.ell + he, ker.sigma2), w.nugget, "cuda")
+    vm = compressed_values(b, cp, ri, Kernel(ker.kind, ker.ell - he, ker.sigma2), w.nugget, "cuda")
+    fd_ell = (nll(vp) - nll(vm)) / (2 * he)
+    assert abs(d_ell - fd_ell) <= 1e-6 * max(1.0, abs(fd_ell))
