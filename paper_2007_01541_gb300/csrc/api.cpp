@@ -27,8 +27,9 @@ constexpr int ROWS_PER_CTA = 256;  // one thread per front row (gather / apply_L
 
 enum LaunchKind {
     K_INIT, K_POTRF, K_PANEL, K_UPDATE, K_SYRK, K_UPDATE_TC, K_SYRK_TC,  // factor
-    K_FWD_GATHER, K_FWD_DIAG_FIRST, K_FWD_UPDATE, K_FWD_RGEMM, // forward solve
-    K_BWD_INIT, K_BWD_STEP,                                    // backward solve
+    K_SBINV_DIAG, K_SBINV_STAGE, K_SBINV_T,                    // super-block inverses
+    K_FWD_GATHER, K_FWD_XAPPLY, K_FWD_BUPDATE,                 // forward solve
+    K_BWD_REDUCE, K_BWD_FINISH, K_BWD_XAPPLY,                  // backward solve
     K_APPLY_L
 };
 
@@ -44,9 +45,10 @@ struct Launch {
 
 const char *kind_name(int k) {
     static const char *names[] = {"front_init", "potrf_diag", "panel_trsm", "schur_update",
-                                  "schur_syrk", "tc_schur_update", "tc_schur_syrk", "fwd_gather",
-                                  "fwd_diag_first", "fwd_update", "fwd_rgemm", "bwd_init",
-                                  "bwd_step", "apply_L"};
+                                  "schur_syrk", "tc_schur_update", "tc_schur_syrk", "sbinv_diag",
+                                  "sbinv_stage", "sbinv_transpose", "fwd_gather", "fwd_xapply",
+                                  "fwd_bupdate", "bwd_reduce", "bwd_finish", "bwd_xapply",
+                                  "apply_L"};
     return names[k];
 }
 
@@ -59,6 +61,8 @@ struct Plan {
     std::vector<int4> items;
     std::vector<Launch> launches;
     int4 *d_items = nullptr;
+    int rgt = 16;            // solve plans: right-hand sides per CTA tile
+    int64_t slots = 0;       // solve plans: partial-sum slots of the largest split step
 };
 
 struct GraphCache {
@@ -112,6 +116,9 @@ struct wd_ctx {
     size_t front_elems = 0;
     void *d_dinv = nullptr;        // inverses of the NB x NB diagonal blocks
     size_t dinv_elems = 0;
+    void *d_xs = nullptr, *d_xts = nullptr;  // super-block inverses and their transposes
+    int64_t *d_xsoff = nullptr;
+    size_t xs_elems = 0;
     unsigned char *d_pack = nullptr;  // packed tf32 panel lines (FP32 fronts)
     int64_t pack_total = 0;
     status_t *d_tstatus = nullptr;    // nonzero: a bounded device wait expired
@@ -127,7 +134,9 @@ struct wd_ctx {
     int aplan_nrhs = -1;
     // solve workspaces (sized for ws_cols right-hand sides)
     int64_t ws_cols = 0;
-    void *d_Y = nullptr, *d_W = nullptr;
+    void *d_Y = nullptr, *d_W = nullptr, *d_T = nullptr;
+    void *d_part = nullptr;        // partial sums of the backward split reduction
+    int64_t part_elems = 0;
     double *d_B = nullptr, *d_Bp = nullptr, *d_X = nullptr, *d_R = nullptr, *d_cm = nullptr;
     int64_t W_rows = 0;   // sum of (m_s - k_s)
     int64_t nnz_full = 0;  // stored entries of the full CSR of P A P^T
@@ -391,101 +400,154 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
         }
         add_launch(p, tc ? K_SYRK_TC : K_SYRK, f0, 0, fl, el, 0);
     }
+    // explicit inverses of the super-blocks' diagonal blocks (for the solves)
+    constexpr int BPS = wd::SB / NB;  // 64-blocks per super-block
+    auto nblk_of = [&](int s, int sb) { return (std::min(wd::SB, S.k(s) - sb * wd::SB) + NB - 1) / NB; };
+    {
+        const size_t f0 = p.items.size();
+        double el = 0;
+        for (int s = 0; s < S.ns; ++s)
+            for (int sb = 0; sb * wd::SB < S.k(s); ++sb)
+                for (int t = 0; t < nblk_of(s, sb); ++t) {
+                    p.items.push_back({s, sb, t, 0});
+                    el += 2.0 * NB * NB;
+                }
+        add_launch(p, K_SBINV_DIAG, f0, 0, 0, el, 0);
+    }
+    for (int t = 1; t < BPS; ++t) {
+        const size_t f0 = p.items.size();
+        double fl = 0, el = 0;
+        for (int s = 0; s < S.ns; ++s)
+            for (int sb = 0; sb * wd::SB < S.k(s); ++sb) {
+                if (nblk_of(s, sb) <= t) continue;
+                for (int bj = 0; bj < t; ++bj) {
+                    p.items.push_back({s, sb, bj, 0});
+                    fl += 2.0 * NB * NB * NB * (t - bj) + (double)NB * NB * NB;
+                    el += 2.0 * NB * NB * (t - bj) + 2.0 * NB * NB;
+                }
+            }
+        add_launch(p, K_SBINV_STAGE, f0, t, fl, el, 0);
+    }
+    {
+        const size_t f0 = p.items.size();
+        double el = 0;
+        for (int s = 0; s < S.ns; ++s)
+            for (int sb = 0; sb * wd::SB < S.k(s); ++sb) {
+                const int nb = nblk_of(s, sb);
+                for (int bi = 0; bi < nb; ++bi)
+                    for (int bj = 0; bj <= bi; ++bj) {
+                        p.items.push_back({s, sb, bi, bj});
+                        el += 2.0 * NB * NB;
+                    }
+            }
+        add_launch(p, K_SBINV_T, f0, 0, 0, el, 0);
+    }
 }
 
 static void build_solve_plan(const wd::Symbolic &S, int nrhs, Plan &p) {
     p.items.clear();
     p.launches.clear();
-    const int ng = (nrhs + RG - 1) / RG;
+    const int rgt = nrhs >= 48 ? 64 : 16;   // right-hand sides per gather CTA
+    p.rgt = rgt;
+    p.slots = 0;
+    const int ngg = (nrhs + rgt - 1) / rgt;
+    const int ng = (nrhs + wd::SOLVE_TN - 1) / wd::SOLVE_TN;
     const double R = nrhs;
+    const int SBW = wd::SB, KSR = wd::SOLVE_KSR;
+    auto nsb = [&](int s) { return (S.k(s) + SBW - 1) / SBW; };
+    auto width = [&](int s, int sb) { return std::min(SBW, S.k(s) - sb * SBW); };
+    auto wpad = [&](int s, int sb) { return (width(s, sb) + NB - 1) / NB * NB; };
     for (int l = 0; l < S.nlevels; ++l) {
         const int b = S.level_ptr[l], e = S.level_ptr[l + 1];
         size_t f0 = p.items.size();
-        int kmax = 0;
+        int maxsb = 0;
         double el = 0, fl = 0;
         for (int i = b; i < e; ++i) {
             const int s = S.level_nodes[i];
-            for (int rc = 0; rc * ROWS_PER_CTA < S.m(s); ++rc) p.items.push_back({s, rc, 0, 0});
-            kmax = std::max(kmax, S.k(s));
-            el += R * S.m(s);
+            for (int rc = 0; rc * 32 < S.m(s); ++rc)
+                for (int g = 0; g < ngg; ++g) p.items.push_back({s, rc, g, 0});
+            maxsb = std::max(maxsb, nsb(s));
+            el += R * (S.m(s) + S.k(s));
             for (int c = S.child_ptr[s]; c < S.child_ptr[s + 1]; ++c)
                 el += R * (S.m(S.children[c]) - S.k(S.children[c]));
         }
         add_launch(p, K_FWD_GATHER, f0, 0, 0, el, 0);
-        f0 = p.items.size();
-        el = fl = 0;
-        for (int i = b; i < e; ++i) {
-            const double nb = std::min(NB, S.k(S.level_nodes[i]));
-            for (int g = 0; g < ng; ++g) p.items.push_back({S.level_nodes[i], g, 0, 0});
-            fl += nb * nb * R;
-            el += (double)NB * NB + 2 * nb * R;
-        }
-        add_launch(p, K_FWD_DIAG_FIRST, f0, 0, fl, el, 0);
-        for (int kb = 0; kb < kmax; kb += NB) {
-            f0 = p.items.size();
-            el = fl = 0;
-            for (int i = b; i < e; ++i) {
-                const int s = S.level_nodes[i], k = S.k(s);
-                if (k <= kb) continue;
-                const int nb = std::min(NB, k - kb);
-                const int t0 = kb + nb;
-                if (t0 >= k) continue;
-                for (int rb = 0; rb * SOLVE_RB < k - t0; ++rb)
-                    for (int g = 0; g < ng; ++g) p.items.push_back({s, rb, g, 0});
-                fl += 2.0 * (k - t0) * nb * R;
-                el += (double)(k - t0) * nb + 2.0 * (k - t0) * R + nb * R;
-                const double nb2 = std::min(NB, k - t0);
-                fl += nb2 * nb2 * R;
-                el += (double)NB * NB;
-            }
-            add_launch(p, K_FWD_UPDATE, f0, kb, fl, el, 0);
-        }
-        f0 = p.items.size();
-        el = fl = 0;
-        for (int i = b; i < e; ++i) {
-            const int s = S.level_nodes[i], k = S.k(s), m = S.m(s);
-            if (m <= k) continue;
-            for (int rb = 0; rb * SOLVE_RB < m - k; ++rb)
-                for (int g = 0; g < ng; ++g) p.items.push_back({s, rb, g, 0});
-            fl += 2.0 * (m - k) * k * R;
-            el += (double)(m - k) * k + 2.0 * (m - k) * R + k * R;
-        }
-        add_launch(p, K_FWD_RGEMM, f0, 0, fl, el, 0);
-    }
-    for (int l = S.nlevels - 1; l >= 0; --l) {
-        const int b = S.level_ptr[l], e = S.level_ptr[l + 1];
-        size_t f0 = p.items.size();
-        int maxblk = 0;
-        double el = 0, fl = 0;
-        for (int i = b; i < e; ++i) {
-            const int s = S.level_nodes[i];
-            const int k = S.k(s), m = S.m(s);
-            const int nblk = (k + NB - 1) / NB;
-            maxblk = std::max(maxblk, nblk);
-            for (int jb = 0; jb < nblk; ++jb)
-                for (int g = 0; g < ng; ++g) p.items.push_back({s, jb, g, 0});
-            fl += 2.0 * (m - k) * k * R;
-            el += (double)(m - k) * k + (m - k) * R + 2.0 * k * R;
-            const double nbl = k - (nblk - 1) * NB;
-            fl += nbl * nbl * R;
-            el += (double)NB * NB;
-        }
-        add_launch(p, K_BWD_INIT, f0, 0, fl, el, 0);
-        for (int ib = maxblk - 2; ib >= 0; --ib) {
+        for (int sb = 0; sb < maxsb; ++sb) {
             f0 = p.items.size();
             el = fl = 0;
             for (int i = b; i < e; ++i) {
                 const int s = S.level_nodes[i];
-                const int k = S.k(s);
-                const int nblk = (k + NB - 1) / NB;
-                if (nblk < ib + 2) continue;
-                for (int jb = 0; jb <= ib; ++jb)
-                    for (int g = 0; g < ng; ++g) p.items.push_back({s, jb, g, 0});
-                const double nr = std::min(NB, k - (ib + 1) * NB);
-                fl += 2.0 * nr * (ib + 1) * NB * R + (double)NB * NB * R;
-                el += nr * (ib + 1) * NB + nr * R + 2.0 * (ib + 1) * NB * R + NB * NB;
+                if (nsb(s) <= sb) continue;
+                const int w = width(s, sb), wp = wpad(s, sb);
+                for (int rb = 0; rb * NB < wp; ++rb)
+                    for (int g = 0; g < ng; ++g) p.items.push_back({s, sb, rb, g});
+                fl += (double)w * (w + 1) * R;
+                el += (double)w * (w + 1) / 2 + 2.0 * w * R;
             }
-            add_launch(p, K_BWD_STEP, f0, ib, fl, el, 0);
+            add_launch(p, K_FWD_XAPPLY, f0, sb, fl, el, 0);
+            f0 = p.items.size();
+            el = fl = 0;
+            for (int i = b; i < e; ++i) {
+                const int s = S.level_nodes[i];
+                if (nsb(s) <= sb) continue;
+                const int k = S.k(s), m = S.m(s), w = width(s, sb);
+                const int nJ = k - (sb * SBW + w), nR = m - k;
+                for (int rb = 0; rb * 64 < nJ; ++rb)
+                    for (int g = 0; g < ng; ++g) p.items.push_back({s, sb, rb, g});
+                for (int rb = 0; rb * 64 < nR; ++rb)
+                    for (int g = 0; g < ng; ++g) p.items.push_back({s, sb, rb, g + 65536});
+                fl += 2.0 * (nJ + nR) * w * R;
+                el += (double)(nJ + nR) * w + 2.0 * (nJ + nR) * R + w * R;
+            }
+            add_launch(p, K_FWD_BUPDATE, f0, sb, fl, el, 0);
+        }
+    }
+    for (int l = S.nlevels - 1; l >= 0; --l) {
+        const int b = S.level_ptr[l], e = S.level_ptr[l + 1];
+        int maxsb = 0;
+        for (int i = b; i < e; ++i) maxsb = std::max(maxsb, nsb(S.level_nodes[i]));
+        for (int sb = maxsb - 1; sb >= 0; --sb) {
+            // partial sums over splits of the rows below the super-block
+            size_t f0 = p.items.size();
+            double el = 0, fl = 0;
+            int slot = 0;
+            std::vector<int4> fin;
+            for (int i = b; i < e; ++i) {
+                const int s = S.level_nodes[i];
+                if (nsb(s) <= sb) continue;
+                const int m = S.m(s), w = width(s, sb);
+                const int below = m - (sb * SBW + w);
+                const int nsplit = (below + KSR - 1) / KSR;
+                for (int cb = 0; cb * NB < w; ++cb)
+                    for (int g = 0; g < ng; ++g) {
+                        fin.push_back({s, sb * 8 + cb, g + 65536 * nsplit, slot});
+                        for (int ks = 0; ks < nsplit; ++ks)
+                            p.items.push_back({s, sb * 8 + cb, g + 65536 * ks, slot++});
+                    }
+                fl += 2.0 * below * w * R;
+                el += (double)below * w + below * R;
+            }
+            p.slots = std::max<int64_t>(p.slots, slot);
+            add_launch(p, K_BWD_REDUCE, f0, sb, fl, el, 0);
+            f0 = p.items.size();
+            el = 0;
+            for (const int4 &q : fin) {
+                p.items.push_back(q);
+                el += 2.0 * NB * R + (double)(q.z >> 16) * NB * wd::SOLVE_TN;
+            }
+            add_launch(p, K_BWD_FINISH, f0, sb, 0, el, 0);
+            f0 = p.items.size();
+            el = fl = 0;
+            for (int i = b; i < e; ++i) {
+                const int s = S.level_nodes[i];
+                if (nsb(s) <= sb) continue;
+                const int w = width(s, sb), wp = wpad(s, sb);
+                for (int rb = 0; rb * NB < wp; ++rb)
+                    for (int g = 0; g < ng; ++g) p.items.push_back({s, sb, rb, g});
+                fl += (double)w * (w + 1) * R;
+                el += (double)w * (w + 1) / 2 + 2.0 * w * R;
+            }
+            add_launch(p, K_BWD_XAPPLY, f0, sb, fl, el, 0);
         }
     }
 }
@@ -570,6 +632,9 @@ static wd_status reset_analysis(wd_handle h) {
     h->ws_cols = 0;
     h->d_front = nullptr;
     h->d_dinv = nullptr;
+    h->d_xs = h->d_xts = nullptr;
+    h->d_xsoff = nullptr;
+    h->xs_elems = 0;
     h->d_values_stage = nullptr;
     h->front_elems = 0;
     h->g_factor.reset();
@@ -722,6 +787,17 @@ static wd_status finish_analysis(wd_handle h, std::chrono::steady_clock::time_po
         maxk = std::max(maxk, sk[s]);
     }
     h->front_elems = (size_t)fo;
+    std::vector<int64_t> xsoff(ns);
+    {
+        int64_t xo = 0;
+        for (int s = 0; s < ns; ++s) {
+            xsoff[s] = xo;
+            const int nsb = (sk[s] + wd::SB - 1) / wd::SB;
+            const int wl = sk[s] - (nsb - 1) * wd::SB, wpl = (wl + NB - 1) / NB * NB;
+            xo += (int64_t)(nsb - 1) * wd::SB * wd::SB + (int64_t)wpl * wpl;
+        }
+        h->xs_elems = (size_t)xo;
+    }
     h->h_foff = foff;
     h->h_sld = sld;
     h->dinv_elems = (size_t)dio;
@@ -797,6 +873,11 @@ static wd_status finish_analysis(wd_handle h, std::chrono::steady_clock::time_po
     UP(dioff, d.dinvoff);
     UP(pkoff, d.pkoff);
     UP(S.perm, d.perm);
+    {
+        const int64_t *p = nullptr;
+        UP(xsoff, p);
+        h->d_xsoff = const_cast<int64_t *>(p);
+    }
     {
         const int32_t *p = nullptr;
         UP(csrc, p);
@@ -1012,6 +1093,17 @@ static void enqueue_factor_plan(wd_handle h, cudaStream_t st, bool prof) {
                 wd::launch_tc_schur(d, reinterpret_cast<float *>(F), pk, it, L.count, 0, 1,
                                     h->d_tstatus, st);
                 break;
+            case K_SBINV_DIAG:
+                wd::launch_sbinv_diag<T>(d, Dv, static_cast<T *>(h->d_xs), h->d_xsoff, it, L.count, st);
+                break;
+            case K_SBINV_STAGE:
+                wd::launch_sbinv_stage<T>(d, F, Dv, static_cast<T *>(h->d_xs), h->d_xsoff, it, L.count, L.arg,
+                                          st);
+                break;
+            case K_SBINV_T:
+                wd::launch_sbinv_transpose<T>(d, static_cast<const T *>(h->d_xs), static_cast<T *>(h->d_xts),
+                                              h->d_xsoff, it, L.count, st);
+                break;
         }
         if (prof) record_event(h->prof_ev[2 * li + 1], st);
         ++li;
@@ -1073,6 +1165,8 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
     if (!h->d_front) {
         CK(h->mem.alloc(&h->d_front, h->front_elems * sizeof(double)), "front pool alloc");
         CK(h->mem.alloc(&h->d_dinv, h->dinv_elems * sizeof(double)), "inverse blocks alloc");
+        CK(h->mem.alloc(&h->d_xs, h->xs_elems * sizeof(double)), "super-block inverse alloc");
+        CK(h->mem.alloc(&h->d_xts, h->xs_elems * sizeof(double)), "super-block inverse alloc");
         // padding rows stay zero forever: no kernel writes them
         CK(cudaMemsetAsync(h->d_front, 0, h->front_elems * sizeof(double), st), "front pool clear");
     }
@@ -1137,7 +1231,8 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
 static wd_status ensure_solve_ws(wd_handle h, int64_t nrhs) {
     if (h->ws_cols >= nrhs) return WD_OK;
     h->work.free_all();
-    h->d_Y = h->d_W = nullptr;
+    h->d_Y = h->d_W = h->d_T = h->d_part = nullptr;
+    h->part_elems = 0;
     h->d_B = h->d_Bp = h->d_X = h->d_R = h->d_cm = h->d_P = nullptr;
     h->splan = Plan();
     h->aplan = Plan();
@@ -1145,6 +1240,7 @@ static wd_status ensure_solve_ws(wd_handle h, int64_t nrhs) {
     h->g_solve.reset();
     const int64_t n = h->S.n;
     CK(h->work.alloc(&h->d_Y, n * nrhs * sizeof(double)), "solve ws");
+    CK(h->work.alloc(&h->d_T, n * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc(&h->d_W, std::max<int64_t>(h->W_rows, 1) * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc((void **)&h->d_B, n * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc((void **)&h->d_Bp, n * nrhs * sizeof(double)), "solve ws");
@@ -1163,20 +1259,28 @@ static wd_status ensure_solve_ws(wd_handle h, int64_t nrhs) {
 template <class T>
 static void enqueue_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st, bool prof) {
     const T *F = static_cast<const T *>(h->d_front);
-    const T *Dv = static_cast<const T *>(h->d_dinv);
+    const T *Xs = static_cast<const T *>(h->d_xs);
+    const T *XTs = static_cast<const T *>(h->d_xts);
     T *W = static_cast<T *>(h->d_W);
+    T *Tt = static_cast<T *>(h->d_T);
+    T *P = static_cast<T *>(h->d_part);
     const DevSym &d = h->dsym;
+    const int rgt = h->splan.rgt;
     size_t li = 0;
     for (const Launch &L : h->splan.launches) {
         const int4 *it = h->splan.d_items + L.off;
         if (prof) record_event(h->prof_ev[2 * li], st);
         switch (L.kind) {
-            case K_FWD_GATHER: wd::launch_fwd_gather<T>(d, F, Y, W, it, L.count, nrhs, st); break;
-            case K_FWD_DIAG_FIRST: wd::launch_fwd_diag_first<T>(d, Dv, Y, it, L.count, nrhs, st); break;
-            case K_FWD_UPDATE: wd::launch_fwd_update<T>(d, F, Dv, Y, it, L.count, L.arg, nrhs, st); break;
-            case K_FWD_RGEMM: wd::launch_fwd_rgemm<T>(d, F, Y, W, it, L.count, nrhs, st); break;
-            case K_BWD_INIT: wd::launch_bwd_init<T>(d, F, Dv, Y, it, L.count, nrhs, st); break;
-            case K_BWD_STEP: wd::launch_bwd_step<T>(d, F, Dv, Y, it, L.count, L.arg, nrhs, st); break;
+            case K_FWD_GATHER: wd::launch_bfwd_gather<T>(d, Y, Tt, W, it, L.count, rgt, nrhs, st); break;
+            case K_FWD_XAPPLY:
+                wd::launch_xapply<T>(d, Xs, h->d_xsoff, Tt, Y, it, L.count, 0, nrhs, st);
+                break;
+            case K_FWD_BUPDATE: wd::launch_bupdate<T>(d, F, Y, Tt, W, it, L.count, nrhs, st); break;
+            case K_BWD_REDUCE: wd::launch_breduce<T>(d, F, Y, P, it, L.count, nrhs, st); break;
+            case K_BWD_FINISH: wd::launch_breduce_finish<T>(d, Y, Tt, P, it, L.count, nrhs, st); break;
+            case K_BWD_XAPPLY:
+                wd::launch_xapply<T>(d, XTs, h->d_xsoff, Tt, Y, it, L.count, 1, nrhs, st);
+                break;
         }
         if (prof) record_event(h->prof_ev[2 * li + 1], st);
         ++li;
@@ -1258,6 +1362,14 @@ extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb,
         build_solve_plan(h->S, (int)nrhs, h->splan);
         s = upload_plan(h, h->work, h->splan);
         if (s != WD_OK) return s;
+        const int64_t need = std::max<int64_t>(h->splan.slots, 1) * NB * wd::SOLVE_TN;
+        if (need > h->part_elems) {
+            if (h->d_part) h->work.release(h->d_part);
+            h->d_part = nullptr;
+            h->part_elems = 0;
+            CK(h->work.alloc(&h->d_part, need * sizeof(double)), "solve ws");
+            h->part_elems = need;
+        }
         h->splan_nrhs = (int)nrhs;
         h->g_solve.reset();
     }

@@ -45,10 +45,12 @@ struct DevSym {
 void init_front_attributes();
 void init_solve_attributes();
 void init_tc_attributes();
+void init_blocked_attributes();
 inline void init_kernel_attributes() {
     init_front_attributes();
     init_solve_attributes();
     init_tc_attributes();
+    init_blocked_attributes();
 }
 
 
@@ -175,6 +177,43 @@ void launch_zextract(const DevSym &d, const double *zpool, const int32_t *col2s,
 void launch_sym_outer(const DevSym &d, const int32_t *prow, const int32_t *psrc, const double *U,
                       const double *V, int64_t ncols, int64_t ld, double alpha, const double *Zsel,
                       double zscale, double *out, cudaStream_t st);
+
+// ---- solves by super-blocks (solve_blocked.cu) ----------------------------
+// A supernode's pivot columns are cut into super-blocks of SB columns; the
+// explicit inverse of every super-block's diagonal block is stored (X, and
+// its transpose XT) at xsoff[s] + sb * SB * SB, column-major with leading
+// dimension wp = roundup(width, NB).
+constexpr int SB = 512;
+template <class T>
+void launch_sbinv_diag(const DevSym &d, const T *dinv, T *xpool, const int64_t *xsoff, const int4 *items,
+                       int count, cudaStream_t st);
+template <class T>
+void launch_sbinv_stage(const DevSym &d, const T *front, const T *dinv, T *xpool, const int64_t *xsoff,
+                        const int4 *items, int count, int t, cudaStream_t st);
+template <class T>
+void launch_sbinv_transpose(const DevSym &d, const T *xpool, T *xtpool, const int64_t *xsoff,
+                            const int4 *items, int count, cudaStream_t st);
+// rgt: right-hand sides per CTA tile (64 or 16)
+template <class T>
+void launch_bfwd_gather(const DevSym &d, const T *Y, T *Tt, T *W, const int4 *items, int count, int rgt,
+                        int nrhs, cudaStream_t st);
+// xapply / bupdate / breduce: 64 rows x SOLVE_TN right-hand sides per CTA
+constexpr int SOLVE_TN = 32;
+template <class T>
+void launch_xapply(const DevSym &d, const T *xp, const int64_t *xsoff, const T *in, T *out,
+                   const int4 *items, int count, int upper, int nrhs, cudaStream_t st);
+template <class T>
+void launch_bupdate(const DevSym &d, const T *front, const T *Y, T *Tt, T *W, const int4 *items, int count,
+                    int nrhs, cudaStream_t st);
+// split reduction of the backward pass: partial sums of KSR-row splits into
+// P (SOLVE_TN x 64 per slot), then Tt = y - sum over the splits in order
+constexpr int SOLVE_KSR = 128;
+template <class T>
+void launch_breduce(const DevSym &d, const T *front, const T *Y, T *P, const int4 *items, int count,
+                    int nrhs, cudaStream_t st);
+template <class T>
+void launch_breduce_finish(const DevSym &d, const T *Y, T *Tt, const T *P, const int4 *items, int count,
+                           int nrhs, cudaStream_t st);
 
 // ---- per-instance reductions of a block-diagonal batch (batch.cu) ----------
 void launch_seg_norm_inf(const DevSym &d, const int64_t *coff, int count, double *out, cudaStream_t st);

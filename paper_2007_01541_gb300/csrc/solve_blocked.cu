@@ -1,0 +1,593 @@
+// Supernodal triangular solves by super-blocks of SB pivot columns.
+//
+// x = P^T L^-T L^-1 P b (the exact inverse of the compressed matrix applied to
+// right-hand sides, Sections 1 and 5).  Both substitutions walk the supernodal
+// tree level by level.  Inside a supernode they step over super-blocks of
+// SB = 512 pivot columns, using the explicit inverse X of each super-block's
+// diagonal block (lower triangular, built once per factorization from the
+// stored 64 x 64 inverses), so a supernode of width k takes ceil(k / SB)
+// dependent steps instead of ceil(k / 64):
+//   forward:  y_B = X_B t_B;  t(rows below B) -= L(rows below, B) y_B
+//   backward: t_B = y_B - L(rows below, B)^T x(rows below);  x_B = X_B^T t_B
+// Rows below a supernode's pivot block go to its update vector, which the
+// parent gathers through the extend-add row maps (no atomics).
+//
+// Buffers (column-major n x nrhs, factor order): Y holds b on entry and x on
+// exit; Tt holds the pending right-hand side of pivot rows during the forward
+// pass and t during the backward pass.
+#include "dev_common.cuh"
+#include "engine.h"
+
+namespace wd {
+namespace {
+
+constexpr int THREADS = 256;
+constexpr int RG = 16;      // right-hand sides per CTA
+constexpr int TR = 64;      // rows per CTA
+
+// ---------------------------------------------------------------------------
+// super-block inverses
+// ---------------------------------------------------------------------------
+// X(t, t) = Dinv of pivot block sb*8 + t; item = (s, sb, t)
+template <class T>
+__global__ void __launch_bounds__(THREADS) sbinv_diag_kernel(DevSym d, const T *__restrict__ dinv,
+                                                             T *__restrict__ xpool,
+                                                             const int64_t *__restrict__ xsoff,
+                                                             const int4 *__restrict__ items) {
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, sb = it.y, t = it.z;
+    const int k = d.sk[s];
+    const int w = min(SB, k - sb * SB), wp = (w + NB - 1) / NB * NB;
+    const T *D = dinv + d.dinvoff[s] + (int64_t)(sb * (SB / NB) + t) * NB * NB;
+    T *X = xpool + xsoff[s] + (int64_t)sb * SB * SB + (int64_t)(t * NB) * wp + t * NB;
+    for (int idx = threadIdx.x; idx < NB * NB; idx += THREADS) {
+        const int r = idx % NB, c = idx / NB;
+        X[(int64_t)c * wp + r] = D[idx];
+    }
+}
+
+// X(t, bj) = -D_t sum_{p = bj}^{t-1} L(t, p) X(p, bj), 64 x 64 blocks of the
+// super-block; item = (s, sb, bj), stage t = the launch argument
+template <class T>
+__global__ void __launch_bounds__(THREADS) sbinv_stage_kernel(DevSym d, const T *__restrict__ front,
+                                                              const T *__restrict__ dinv,
+                                                              T *__restrict__ xpool,
+                                                              const int64_t *__restrict__ xsoff,
+                                                              const int4 *__restrict__ items, int t) {
+    constexpr int TK = 16;
+    // staging of the product, then (after it) the 64 x 64 result
+    __shared__ T smem[NB * (NB + 1)];
+    static_assert(2 * TK * (NB + 1) <= NB * (NB + 1), "staging fits");
+    T(*As)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
+    T(*Bs)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem + TK * (NB + 1));
+    T(*Ts)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, sb = it.y, bj = it.z;
+    const int k = d.sk[s], ld = d.sld[s];
+    const int c0 = sb * SB;                          // first column of the super-block
+    const int w = min(SB, k - c0), wp = (w + NB - 1) / NB * NB;
+    const T *L = front + d.foff[s] + (int64_t)c0 * ld + c0;   // L(c0 + r, c0 + c) at L[c * ld + r]
+    T *X = xpool + xsoff[s] + (int64_t)sb * SB * SB;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int rmax = w - t * NB;                     // valid rows of block t
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    // T = sum_p L(t, p) X(p, bj) over p in [bj*64, t*64)
+    for (int k0 = bj * NB; k0 < t * NB; k0 += TK) {
+        for (int idx = tid; idx < TK * NB; idx += THREADS) {
+            const int kk = idx / NB, r = idx % NB;      // rows of L contiguous
+            As[kk][r] = (r < rmax) ? L[(int64_t)(k0 + kk) * ld + t * NB + r] : T(0);
+        }
+        for (int idx = tid; idx < TK * NB; idx += THREADS) {
+            const int kk = idx % TK, r = idx / TK;      // rows of X contiguous
+            Bs[kk][r] = X[(int64_t)(bj * NB + r) * wp + k0 + kk];
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < TK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) Ts[tx + 16 * i][ty + 16 * j] = acc[i][j];
+    __syncthreads();
+    // X(t, bj) = -D_t T  (D_t lower triangular, column-major, zero beyond the block)
+    const T *D = dinv + d.dinvoff[s] + (int64_t)(sb * (SB / NB) + t) * NB * NB;
+    for (int idx = tid; idx < NB * NB; idx += THREADS) {
+        const int r = idx % NB, c = idx / NB;
+        T v = T(0);
+        if (r < rmax)
+            for (int p = 0; p <= r; ++p) v += D[(int64_t)p * NB + r] * Ts[p][c];
+        X[(int64_t)(bj * NB + c) * wp + t * NB + r] = -v;
+    }
+}
+
+// XT = X^T per super-block, 64 x 64 tiles: item = (s, sb, i, j), i >= j:
+// XT(j, i) = X(i, j)^T
+template <class T>
+__global__ void __launch_bounds__(THREADS) sbinv_transpose_kernel(DevSym d, const T *__restrict__ xpool,
+                                                                  T *__restrict__ xtpool,
+                                                                  const int64_t *__restrict__ xsoff,
+                                                                  const int4 *__restrict__ items) {
+    __shared__ T tile[NB][NB + 1];
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, sb = it.y, bi = it.z, bj = it.w;
+    const int k = d.sk[s];
+    const int w = min(SB, k - sb * SB), wp = (w + NB - 1) / NB * NB;
+    const int64_t base = xsoff[s] + (int64_t)sb * SB * SB;
+    const T *X = xpool + base + (int64_t)(bj * NB) * wp + bi * NB;   // X(bi, bj) tile
+    T *XT = xtpool + base + (int64_t)(bi * NB) * wp + bj * NB;       // XT(bj, bi) tile
+    for (int idx = threadIdx.x; idx < NB * NB; idx += THREADS) {
+        const int r = idx % NB, c = idx / NB;
+        tile[r][c] = X[(int64_t)c * wp + r];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NB * NB; idx += THREADS) {
+        const int r = idx % NB, c = idx / NB;
+        XT[(int64_t)c * wp + r] = tile[c][r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------
+// Right-hand-side tiles: RGT (64 or 16) columns per CTA; 256 threads = 64 rows
+// (or pivot columns) x 4 groups of NPT = RGT / 4 right-hand sides.  Operand
+// rows of right-hand sides are staged RHS-contiguous, so a thread reads its
+// NPT values with 16-byte shared-memory loads.
+
+// 16-byte vector of T
+template <class T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+};
+template <>
+struct Vec16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+};
+
+// acc[j] += a * v[j], j < NPT, v 16-byte aligned in shared memory
+template <class T, int NPT>
+__device__ __forceinline__ void axpy_row(T (&acc)[NPT], T a, const T *v) {
+    using V = typename Vec16<T>::type;
+    constexpr int E = Vec16<T>::n;
+#pragma unroll
+    for (int j = 0; j < NPT; j += E) {
+        const V q = *reinterpret_cast<const V *>(v + j);
+        const T *e = reinterpret_cast<const T *>(&q);
+#pragma unroll
+        for (int u = 0; u < E; ++u) acc[j + u] += a * e[u];
+    }
+}
+
+// pivot rows: Tt = b_J + children's update vectors; rows below: W_s = the
+// children's update vectors.  item = (s, 32-row block, rhs tile); lane = row,
+// warp w takes right-hand sides w, w + 8, ... of the tile.
+template <class T, int RGT>
+__global__ void __launch_bounds__(THREADS) bfwd_gather_kernel(DevSym d, const T *__restrict__ Y,
+                                                              T *__restrict__ Tt, T *__restrict__ W,
+                                                              const int4 *__restrict__ items,
+                                                              int nrhs) {
+    constexpr int PW = RGT / 8;  // right-hand sides per thread
+    const int4 it = items[blockIdx.x];
+    const int s = it.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = it.y * 32 + lane;
+    const int m = d.sm[s], k = d.sk[s];
+    if (r >= m) return;
+    const int64_t n = d.n;
+    const int f = d.sfirst[s];
+    const int c0 = it.z * RGT;
+    T t[PW];
+#pragma unroll
+    for (int j = 0; j < PW; ++j) {
+        const int c = c0 + warp + 8 * j;
+        t[j] = (r < k && c < nrhs) ? Y[f + r + (int64_t)c * n] : T(0);
+    }
+    for (int ci = d.child_ptr[s]; ci < d.child_ptr[s + 1]; ++ci) {
+        const int ch = d.children[ci];
+        const int ic = d.relmap[d.mapoff[ch] + r];
+        if (ic < 0) continue;
+        const int ldc = d.sm[ch] - d.sk[ch];
+        const T *Wc = W + d.woff[ch] * nrhs + ic;
+#pragma unroll
+        for (int j = 0; j < PW; ++j) {
+            const int c = c0 + warp + 8 * j;
+            if (c < nrhs) t[j] += Wc[(int64_t)c * ldc];
+        }
+    }
+    T *Ws = W + d.woff[s] * nrhs;
+#pragma unroll
+    for (int j = 0; j < PW; ++j) {
+        const int c = c0 + warp + 8 * j;
+        if (c >= nrhs) continue;
+        if (r < k) Tt[f + r + (int64_t)c * n] = t[j];
+        else Ws[(int64_t)c * (m - k) + (r - k)] = t[j];
+    }
+}
+
+// Tiles of the dependent solve products: 64 rows (or pivot columns) x 32
+// right-hand sides per CTA; warp w owns 8 rows, lane = right-hand side.  The
+// matrix tile is staged with rows contiguous (A[p * lda + row]) and read by a
+// whole warp at once (broadcast 16-byte loads), the right-hand-side tile is
+// staged right-hand-side major with an odd stride (R[c * LDR + p]), so both
+// the staging writes and the reads are free of bank conflicts.
+constexpr int TN = SOLVE_TN;      // right-hand sides per CTA tile
+constexpr int LDR = NB + 1;       // stride of a staged right-hand side
+
+template <class T, int LDA>
+__device__ __forceinline__ void tile_accumulate(T (&acc)[8], const T *A, const T *R, int np) {
+    using V = typename Vec16<T>::type;
+    constexpr int E = Vec16<T>::n;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T *a = A + 8 * w;
+    const T *r = R + lane * LDR;
+#pragma unroll 4
+    for (int p = 0; p < np; ++p) {
+        const T x = r[p];
+#pragma unroll
+        for (int j = 0; j < 8; j += E) {
+            const V q = *reinterpret_cast<const V *>(a + p * LDA + j);
+            const T *e = reinterpret_cast<const T *>(&q);
+#pragma unroll
+            for (int u = 0; u < E; ++u) acc[j + u] += e[u] * x;
+        }
+    }
+}
+
+// the CTA's 64 x 32 result into O[c * LDR + r] (r = row of the tile, c =
+// right-hand side), so that it can be written out with rows contiguous
+template <class T>
+__device__ __forceinline__ void tile_to_smem(const T (&acc)[8], T *O) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) O[lane * LDR + 8 * w + i] = acc[i];
+}
+
+// rows [p0, p0 + 64) of right-hand sides c0 .. c0 + 31 (column-major, ld n,
+// first row `row0`) into R[c * LDR + p]; rows >= valid (and columns >= nc) zero
+template <class T>
+__device__ __forceinline__ void stage_rhs(T *R, const T *src, int64_t row0, int p0, int valid, int c0,
+                                          int nc, int64_t n) {
+    for (int idx = threadIdx.x; idx < NB * TN; idx += THREADS) {
+        const int p = idx % NB, c = idx / NB;
+        const bool v = p0 + p < valid && c < nc;
+        cp_async_elem(R + c * LDR + p, v ? src + row0 + p0 + p + (int64_t)(c0 + c) * n : src, v);
+    }
+}
+
+template <class T>
+constexpr int tile_smem_elems() {
+    return 2 * NB * TR + 2 * TN * LDR + 8;
+}
+
+// out(B rows 64 rb .. +64) = X_B in_B (upper = 0) or X_B^T in_B (upper = 1,
+// using the stored transpose); item = (s, sb, rb, rhs tile)
+template <class T>
+__global__ void __launch_bounds__(THREADS) xapply_kernel(DevSym d, const T *__restrict__ xp,
+                                                         const int64_t *__restrict__ xsoff,
+                                                         const T *__restrict__ in, T *__restrict__ out,
+                                                         const int4 *__restrict__ items, int upper,
+                                                         int nrhs) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    T *Xs[2] = {sm, sm + NB * TR};                                  // [p][r], ld TR
+    T *Rs[2] = {sm + 2 * NB * TR, sm + 2 * NB * TR + TN * LDR};     // [c][p], ld LDR
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, sb = it.y, rb = it.z, c0 = it.w * TN;
+    const int k = d.sk[s];
+    const int b0 = sb * SB;
+    const int w = min(SB, k - b0), wp = (w + NB - 1) / NB * NB;
+    const int nb = wp / NB;
+    const int nc = min(TN, nrhs - c0);
+    const int64_t n = d.n;
+    const int64_t row0 = d.sfirst[s] + b0;
+    const T *X = xp + xsoff[s] + (int64_t)sb * SB * SB;
+    const int q0 = upper ? rb : 0, q1 = upper ? nb : rb + 1;
+    auto stage = [&](int buf, int q) {
+        stage_tile<T, THREADS>(Xs[buf], TR, X + (int64_t)(q * NB) * wp + rb * NB, wp, TR, NB, TR, NB);
+        stage_rhs<T>(Rs[buf], in, row0, q * NB, w, c0, nc, n);
+        cp_async_commit();
+    };
+    T acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = T(0);
+    stage(0, q0);
+    for (int q = q0; q < q1; ++q) {
+        const int cur = (q - q0) & 1;
+        if (q + 1 < q1) {
+            stage(cur ^ 1, q + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        tile_accumulate<T, TR>(acc, Xs[cur], Rs[cur], NB);
+        __syncthreads();
+    }
+    T *O = Rs[0];
+    tile_to_smem<T>(acc, O);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NB * TN; idx += THREADS) {
+        const int r = idx % NB, c = idx / NB;
+        const int rr = rb * NB + r;
+        if (rr < w && c < nc) out[row0 + rr + (int64_t)(c0 + c) * n] = O[c * LDR + r];
+    }
+}
+
+// rows below super-block B: target -= L(rows, B) y_B.  item = (s, sb, rb,
+// tile + 65536 * seg): seg 0 = pivot rows after B (target Tt), seg 1 = rows
+// of R (target the update vector W_s)
+template <class T>
+__global__ void __launch_bounds__(THREADS) bupdate_kernel(DevSym d, const T *__restrict__ front,
+                                                          const T *__restrict__ Y, T *__restrict__ Tt,
+                                                          T *__restrict__ W, const int4 *__restrict__ items,
+                                                          int nrhs) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    T *Ls[2] = {sm, sm + NB * TR};
+    T *Rs[2] = {sm + 2 * NB * TR, sm + 2 * NB * TR + TN * LDR};
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, sb = it.y, rb = it.z, g = it.w & 0xFFFF, seg = it.w >> 16;
+    const int m = d.sm[s], k = d.sk[s], kp = d.skp[s], ld = d.sld[s];
+    const int b0 = sb * SB, w = min(SB, k - b0);
+    const int c0 = g * TN, nc = min(TN, nrhs - c0);
+    const int64_t n = d.n;
+    const int f = d.sfirst[s];
+    const int i0 = seg == 0 ? b0 + w + rb * TR : rb * TR;        // seg 1: index into R
+    const int nrow = seg == 0 ? k - i0 : (m - k) - i0;
+    const int mrow = seg == 0 ? i0 : kp + i0;
+    const T *F = front + d.foff[s] + mrow;
+    auto stage = [&](int buf, int p0) {
+        stage_tile<T, THREADS>(Ls[buf], TR, F + (int64_t)(b0 + p0) * ld, ld, TR, NB, nrow, w - p0);
+        stage_rhs<T>(Rs[buf], Y, f + b0, p0, w, c0, nc, n);
+        cp_async_commit();
+    };
+    T acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = T(0);
+    const int nchunk = (w + NB - 1) / NB;
+    stage(0, 0);
+    for (int ch = 0; ch < nchunk; ++ch) {
+        const int cur = ch & 1;
+        if (ch + 1 < nchunk) {
+            stage(cur ^ 1, (ch + 1) * NB);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        tile_accumulate<T, TR>(acc, Ls[cur], Rs[cur], NB);
+        __syncthreads();
+    }
+    T *O = Rs[0];
+    tile_to_smem<T>(acc, O);
+    __syncthreads();
+    T *dst;
+    int64_t ldd;
+    if (seg == 0) {
+        dst = Tt + f + i0;
+        ldd = n;
+    } else {
+        dst = W + d.woff[s] * nrhs + i0;
+        ldd = m - k;
+    }
+    for (int idx = threadIdx.x; idx < NB * TN; idx += THREADS) {
+        const int r = idx % NB, c = idx / NB;
+        if (r < nrow && c < nc) dst[r + (int64_t)(c0 + c) * ldd] -= O[c * LDR + r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// backward
+// ---------------------------------------------------------------------------
+constexpr int KSR = SOLVE_KSR;    // rows below B per split of the reduction
+constexpr int LDT = NB + 4;       // row stride of the staged L^T tile (16-byte multiple)
+
+template <class T>
+constexpr int breduce_smem_elems() {
+    return 2 * (64 * LDT + TN * LDR) + 8;
+}
+
+// Partial reduction of t_B = y_B - L(rows below B, B)^T x(rows below) over the
+// rows [ks * KSR, (ks + 1) * KSR) of the "rows below" list (pivot rows after B,
+// then the rows of R; x of a front row read at its global row):
+// P[slot] (32 x 64, [rhs][c]) = sum_i L(i, j0 + c) x(i, rhs).
+// item = (s, sb * 8 + cb, tile + 65536 * ks, slot)
+template <class T>
+__global__ void __launch_bounds__(THREADS) breduce_kernel(DevSym d, const T *__restrict__ front,
+                                                          const T *__restrict__ Y, T *__restrict__ P,
+                                                          const int4 *__restrict__ items, int nrhs) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    T *Ls[2] = {sm, sm + 64 * LDT};                                  // [rr][c], ld LDT
+    T *Rs[2] = {sm + 2 * 64 * LDT, sm + 2 * 64 * LDT + TN * LDR};    // [rhs][rr], ld LDR
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, sb = it.y >> 3, cb = it.y & 7, g = it.z & 0xFFFF, ks = it.z >> 16;
+    const int m = d.sm[s], k = d.sk[s], kp = d.skp[s], ld = d.sld[s];
+    const int b0 = sb * SB, w = min(SB, k - b0);
+    const int j0 = b0 + cb * NB, nb = min(NB, k - j0);
+    const int c0 = g * TN, nc = min(TN, nrhs - c0);
+    const int64_t n = d.n;
+    const T *F = front + d.foff[s] + (int64_t)j0 * ld;
+    const int32_t *rows = d.rows + d.rowptr[s];
+    const int tid = threadIdx.x;
+    const int nJ = k - (b0 + w), nbelow = nJ + (m - k);
+    const int u0 = ks * KSR, u1 = min(nbelow, u0 + KSR);
+    auto stage = [&](int buf, int ua) {
+        for (int idx = tid; idx < 64 * NB; idx += THREADS) {
+            const int rr = idx % 64, c = idx / 64;
+            const int u = ua + rr;
+            const bool v = u < u1 && c < nb;
+            const int mrow = u < nJ ? b0 + w + u : kp + (u - nJ);
+            cp_async_elem(Ls[buf] + rr * LDT + c, v ? F + (int64_t)c * ld + mrow : F, v);
+        }
+        for (int idx = tid; idx < 64 * TN; idx += THREADS) {
+            const int rr = idx % 64, c = idx / 64;
+            const int u = ua + rr;
+            const bool v = u < u1 && c < nc;
+            const int lr = u < nJ ? b0 + w + u : k + (u - nJ);
+            cp_async_elem(Rs[buf] + c * LDR + rr, v ? Y + rows[lr] + (int64_t)(c0 + c) * n : Y, v);
+        }
+        cp_async_commit();
+    };
+    T acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = T(0);
+    const int nchunk = (u1 - u0 + 63) / 64;
+    stage(0, u0);
+    for (int ch = 0; ch < nchunk; ++ch) {
+        const int cur = ch & 1;
+        if (ch + 1 < nchunk) {
+            stage(cur ^ 1, u0 + (ch + 1) * 64);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        tile_accumulate<T, LDT>(acc, Ls[cur], Rs[cur], 64);
+        __syncthreads();
+    }
+    T *O = Rs[0];
+    tile_to_smem<T>(acc, O);
+    __syncthreads();
+    T *Pt = P + (int64_t)it.w * TN * NB;
+    for (int idx = tid; idx < NB * TN; idx += THREADS) {
+        const int r = idx % NB, c = idx / NB;
+        Pt[c * NB + r] = O[c * LDR + r];
+    }
+}
+
+// Tt(B columns) = y - sum of the splits' partial sums, in split order.
+// item = (s, sb * 8 + cb, tile + 65536 * nsplit, first slot)
+template <class T>
+__global__ void __launch_bounds__(THREADS) breduce_finish_kernel(DevSym d, const T *__restrict__ Y,
+                                                                 T *__restrict__ Tt, const T *__restrict__ P,
+                                                                 const int4 *__restrict__ items, int nrhs) {
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, sb = it.y >> 3, cb = it.y & 7, g = it.z & 0xFFFF, nsplit = it.z >> 16;
+    const int k = d.sk[s];
+    const int j0 = sb * SB + cb * NB, nb = min(NB, k - j0);
+    const int c0 = g * TN, nc = min(TN, nrhs - c0);
+    const int64_t n = d.n;
+    const int f = d.sfirst[s];
+    for (int idx = threadIdx.x; idx < NB * TN; idx += THREADS) {
+        const int cl = idx % NB, c = idx / NB;
+        if (cl >= nb || c >= nc) continue;
+        T sum = T(0);
+        for (int q = 0; q < nsplit; ++q) sum += P[((int64_t)(it.w + q) * TN + c) * NB + cl];
+        const int64_t o = f + j0 + cl + (int64_t)(c0 + c) * n;
+        Tt[o] = Y[o] - sum;
+    }
+}
+
+}  // namespace
+
+template <class T>
+void set_blocked_attributes() {
+    cudaFuncSetAttribute(xapply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(tile_smem_elems<T>() * sizeof(T)));
+    cudaFuncSetAttribute(bupdate_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(tile_smem_elems<T>() * sizeof(T)));
+    cudaFuncSetAttribute(breduce_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(breduce_smem_elems<T>() * sizeof(T)));
+}
+
+void init_blocked_attributes() {
+    static bool done = false;
+    if (done) return;
+    set_blocked_attributes<float>();
+    set_blocked_attributes<double>();
+    done = true;
+}
+
+template <class T>
+void launch_sbinv_diag(const DevSym &d, const T *dinv, T *xpool, const int64_t *xsoff, const int4 *items,
+                       int count, cudaStream_t st) {
+    if (count > 0) sbinv_diag_kernel<T><<<count, THREADS, 0, st>>>(d, dinv, xpool, xsoff, items);
+}
+template <class T>
+void launch_sbinv_stage(const DevSym &d, const T *front, const T *dinv, T *xpool, const int64_t *xsoff,
+                        const int4 *items, int count, int t, cudaStream_t st) {
+    if (count > 0)
+        sbinv_stage_kernel<T><<<count, THREADS, 0, st>>>(d, front, dinv, xpool, xsoff, items, t);
+}
+template <class T>
+void launch_sbinv_transpose(const DevSym &d, const T *xpool, T *xtpool, const int64_t *xsoff,
+                            const int4 *items, int count, cudaStream_t st) {
+    if (count > 0) sbinv_transpose_kernel<T><<<count, THREADS, 0, st>>>(d, xpool, xtpool, xsoff, items);
+}
+template <class T>
+void launch_bfwd_gather(const DevSym &d, const T *Y, T *Tt, T *W, const int4 *items, int count, int rgt,
+                        int nrhs, cudaStream_t st) {
+    if (count <= 0) return;
+    if (rgt == 64) bfwd_gather_kernel<T, 64><<<count, THREADS, 0, st>>>(d, Y, Tt, W, items, nrhs);
+    else bfwd_gather_kernel<T, 16><<<count, THREADS, 0, st>>>(d, Y, Tt, W, items, nrhs);
+}
+template <class T>
+void launch_xapply(const DevSym &d, const T *xp, const int64_t *xsoff, const T *in, T *out,
+                   const int4 *items, int count, int upper, int nrhs, cudaStream_t st) {
+    if (count <= 0) return;
+    xapply_kernel<T><<<count, THREADS, tile_smem_elems<T>() * sizeof(T), st>>>(d, xp, xsoff, in, out, items,
+                                                                             upper, nrhs);
+}
+template <class T>
+void launch_bupdate(const DevSym &d, const T *front, const T *Y, T *Tt, T *W, const int4 *items, int count,
+                    int nrhs, cudaStream_t st) {
+    if (count <= 0) return;
+    bupdate_kernel<T><<<count, THREADS, tile_smem_elems<T>() * sizeof(T), st>>>(d, front, Y, Tt, W, items,
+                                                                              nrhs);
+}
+template <class T>
+void launch_breduce(const DevSym &d, const T *front, const T *Y, T *P, const int4 *items, int count,
+                    int nrhs, cudaStream_t st) {
+    if (count <= 0) return;
+    breduce_kernel<T><<<count, THREADS, breduce_smem_elems<T>() * sizeof(T), st>>>(d, front, Y, P, items,
+                                                                                 nrhs);
+}
+template <class T>
+void launch_breduce_finish(const DevSym &d, const T *Y, T *Tt, const T *P, const int4 *items, int count,
+                           int nrhs, cudaStream_t st) {
+    if (count <= 0) return;
+    breduce_finish_kernel<T><<<count, THREADS, 0, st>>>(d, Y, Tt, P, items, nrhs);
+}
+
+#define WD_BLOCKED_INST(T)                                                                              \
+    template void launch_sbinv_diag<T>(const DevSym &, const T *, T *, const int64_t *, const int4 *, int, \
+                                       cudaStream_t);                                                   \
+    template void launch_sbinv_stage<T>(const DevSym &, const T *, const T *, T *, const int64_t *,      \
+                                        const int4 *, int, int, cudaStream_t);                          \
+    template void launch_sbinv_transpose<T>(const DevSym &, const T *, T *, const int64_t *, const int4 *, \
+                                            int, cudaStream_t);                                         \
+    template void launch_bfwd_gather<T>(const DevSym &, const T *, T *, T *, const int4 *, int, int, int, \
+                                        cudaStream_t);                                                  \
+    template void launch_xapply<T>(const DevSym &, const T *, const int64_t *, const T *, T *,           \
+                                   const int4 *, int, int, int, cudaStream_t);                          \
+    template void launch_bupdate<T>(const DevSym &, const T *, const T *, T *, T *, const int4 *, int,   \
+                                    int, cudaStream_t);                                                 \
+    template void launch_breduce<T>(const DevSym &, const T *, const T *, T *, const int4 *, int, int,   \
+                                    cudaStream_t);                                                      \
+    template void launch_breduce_finish<T>(const DevSym &, const T *, T *, const T *, const int4 *, int, \
+                                           int, cudaStream_t);
+WD_BLOCKED_INST(float)
+WD_BLOCKED_INST(double)
+
+}  // namespace wd

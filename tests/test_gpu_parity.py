@@ -216,7 +216,8 @@ def test_profiled_and_direct_launches(wdlib, cuda, graphs):
         assert oracle.backward_error(cp, ri, v, X, B).max() <= 1e-12
     st = s.kernel_stats(reset=True)
     names = {k["name"] for k in st}
-    assert {"schur_update_fp64", "tc_schur_syrk_fp32", "fwd_update_fp32", "bwd_init_fp64"} <= names
+    assert {"schur_update_fp64", "tc_schur_syrk_fp32", "fwd_xapply_fp32", "bwd_reduce_fp64",
+            "sbinv_stage_fp32", "fwd_bupdate_fp64"} <= names
     assert all(k["launches"] > 0 and k["ms"] > 0 for k in st)
     assert s.kernel_stats() == []
     assert s.launch_count() > 0
