@@ -178,6 +178,17 @@ wd_status wd_factor(wd_handle h, const double *values, int values_on_device, wd_
 wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb, int B_on_device,
                    void *stream, wd_solve_info *info);
 
+/* Normwise backward error of given solutions, the test that stops the
+   refinement: *be = max over columns of
+     ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)
+   X, B: n x nrhs, column-major, leading dimension ld, original order, device
+   (1) or host (0).  The residual is formed from A's FP64 values: in FP64 for
+   up to 8 columns, in double-float arithmetic (about 48 bits) for more.  For
+   a batch, the largest of the instances' own backward errors.  Needs a
+   successful wd_factor (for ||A||_inf).  Synchronous. */
+wd_status wd_backward_error(wd_handle h, const double *X, const double *B, int64_t nrhs, int64_t ld,
+                            int on_device, void *stream, double *be);
+
 /* log det A = 2 sum_j log L_jj (compensated sum).  Synchronous. */
 wd_status wd_logdet(wd_handle h, double *out);
 

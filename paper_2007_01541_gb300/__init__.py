@@ -30,7 +30,7 @@ EXPORTED = ["wd_default_options", "wd_create", "wd_destroy", "wd_analyze", "wd_s
             "wd_get_info", "wd_factor", "wd_solve", "wd_logdet", "wd_apply_L", "wd_export_L",
             "wd_status_detail", "wd_status_string", "wd_kernel_stats", "wd_launch_count",
             "wd_selinv", "wd_sym_pattern_outer", "wd_value_gradient", "wd_export_L_noalloc",
-            "wd_analyze_batch", "wd_logdet_batch"]
+            "wd_analyze_batch", "wd_logdet_batch", "wd_backward_error"]
 
 
 class WdOptions(ctypes.Structure):
@@ -105,6 +105,7 @@ def load():
         lib.wd_export_L_noalloc.argtypes = [vp, vp, vp]
         lib.wd_analyze_batch.argtypes = [vp, i32, vp, vp, vp, vp]
         lib.wd_logdet_batch.argtypes = [vp, vp]
+        lib.wd_backward_error.argtypes = [vp, vp, vp, i64, i64, ctypes.c_int, vp, ctypes.POINTER(f64)]
         lib.wd_status_detail.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_char_p, ctypes.c_size_t]
         lib.wd_kernel_stats.argtypes = [vp, ctypes.POINTER(WdKernelStat), i32, ctypes.POINTER(i32),
                                         ctypes.c_int]
@@ -303,6 +304,31 @@ class Solver:
             out = X
         self.last_solve = {"iterations": info.iterations, "backward_error": info.backward_error}
         return out
+
+    def backward_error(self, X, B, stream=None) -> float:
+        """max over columns of ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)
+        (numpy arrays or column-major CUDA tensors with leading dimension n)."""
+        be = ctypes.c_double()
+        if _is_torch(X):
+            if X.dim() == 1:
+                X, B = X.unsqueeze(1), B.unsqueeze(1)
+            n = X.shape[0]
+            for t in (X, B):
+                if t.stride(0) != 1 or (t.shape[1] > 1 and t.stride(1) != n) or t.shape != X.shape:
+                    raise ValueError("X and B must be column-major n x nrhs with leading dimension n")
+            px, dev = _ptr(X)
+            pb, _ = _ptr(B)
+            self._check(self._lib.wd_backward_error(self._h, px, pb, X.shape[1], n, dev,
+                                                    _stream(stream, dev), ctypes.byref(be)))
+            return be.value
+        Xc = np.array(X, dtype=np.float64, order="F", copy=True)
+        Bc = np.array(B, dtype=np.float64, order="F", copy=True)
+        if Xc.ndim == 1:
+            Xc, Bc = Xc[:, None], Bc[:, None]
+        self._check(self._lib.wd_backward_error(self._h, ctypes.c_void_p(Xc.ctypes.data),
+                                                ctypes.c_void_p(Bc.ctypes.data), Xc.shape[1], Xc.shape[0],
+                                                0, _stream(stream, False), ctypes.byref(be)))
+        return be.value
 
     def logdet(self) -> float:
         v = ctypes.c_double()

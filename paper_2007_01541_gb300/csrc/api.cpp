@@ -17,12 +17,10 @@
 using wd::DevSym;
 using wd::NB;
 using wd::RB;
-using wd::SOLVE_RB;
 using wd::status_t;
 
 namespace {
 
-constexpr int RG = 16;             // right-hand sides per solve block (solve_kernels.cu)
 constexpr int ROWS_PER_CTA = 256;  // one thread per front row (gather / apply_L)
 
 enum LaunchKind {
@@ -111,6 +109,7 @@ struct wd_ctx {
     DevSym dsym{};
     int32_t *d_csr_src = nullptr;
     double *d_csr_val = nullptr;
+    float *d_csr_vh = nullptr, *d_csr_vl = nullptr;   // double-float split of csr_val
     double *d_values_stage = nullptr;
     void *d_front = nullptr;
     size_t front_elems = 0;
@@ -138,6 +137,7 @@ struct wd_ctx {
     void *d_part = nullptr;        // partial sums of the backward split reduction
     int64_t part_elems = 0;
     double *d_B = nullptr, *d_Bp = nullptr, *d_X = nullptr, *d_R = nullptr, *d_cm = nullptr;
+    float *d_Xh = nullptr, *d_Xl = nullptr;   // double-float split of the refinement vectors
     int64_t W_rows = 0;   // sum of (m_s - k_s)
     int64_t nnz_full = 0;  // stored entries of the full CSR of P A P^T
     int4 *d_spmv_chunks = nullptr, *d_spmv_fin = nullptr;
@@ -884,6 +884,8 @@ static wd_status finish_analysis(wd_handle h, std::chrono::steady_clock::time_po
         h->d_csr_src = const_cast<int32_t *>(p);
     }
     CK(h->mem.alloc((void **)&h->d_csr_val, nnzf * sizeof(double)), "values alloc");
+    CK(h->mem.alloc((void **)&h->d_csr_vh, nnzf * sizeof(float)), "values alloc");
+    CK(h->mem.alloc((void **)&h->d_csr_vl, nnzf * sizeof(float)), "values alloc");
     {
         // residual work items: rows cut into chunks of at most SPMV_CHUNK entries
         std::vector<int4> ch, fin;
@@ -1184,7 +1186,7 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
            "values H2D");
         vals = h->d_values_stage;
     }
-    wd::launch_gather_values(h->d_csr_src, vals, h->d_csr_val, h->nnz_full, st);
+    wd::launch_gather_values(h->d_csr_src, vals, h->d_csr_val, h->d_csr_vh, h->d_csr_vl, h->nnz_full, st);
     h->launches += 1;
     CK(cudaMemsetAsync(h->d_status, 0xFF, sizeof(status_t), st), "status reset");
     CK(cudaMemsetAsync(h->d_tstatus, 0, sizeof(status_t), st), "status reset");
@@ -1234,6 +1236,7 @@ static wd_status ensure_solve_ws(wd_handle h, int64_t nrhs) {
     h->d_Y = h->d_W = h->d_T = h->d_part = nullptr;
     h->part_elems = 0;
     h->d_B = h->d_Bp = h->d_X = h->d_R = h->d_cm = h->d_P = nullptr;
+    h->d_Xh = h->d_Xl = nullptr;
     h->splan = Plan();
     h->aplan = Plan();
     h->splan_nrhs = h->aplan_nrhs = -1;
@@ -1245,6 +1248,8 @@ static wd_status ensure_solve_ws(wd_handle h, int64_t nrhs) {
     CK(h->work.alloc((void **)&h->d_B, n * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc((void **)&h->d_Bp, n * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc((void **)&h->d_X, n * nrhs * sizeof(double)), "solve ws");
+    CK(h->work.alloc((void **)&h->d_Xh, n * nrhs * sizeof(float)), "solve ws");
+    CK(h->work.alloc((void **)&h->d_Xl, n * nrhs * sizeof(float)), "solve ws");
     CK(h->work.alloc((void **)&h->d_R, n * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc((void **)&h->d_cm, 3 * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc((void **)&h->d_P, std::max(h->n_spmv_slots, 1) * nrhs * sizeof(double)), "solve ws");
@@ -1305,10 +1310,20 @@ static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cud
                                  double *be_max) {
     const int64_t n = h->S.n;
     const double nf = (double)h->nnz_full;
-    prof_single(h, "spmv_residual_fp64", 0, 0, st, true);
-    wd::launch_spmv_residual(h->dsym, h->d_spmv_chunks, h->n_spmv_chunks, h->d_spmv_fin,
-                             h->n_spmv_fin, X, h->d_Bp, h->d_R, h->d_P, nrhs, st);
-    prof_single(h, "spmv_residual_fp64", 2.0 * nf * nrhs, 12.0 * nf + 24.0 * n * nrhs, st, false);
+    if (nrhs > 8) {
+        // many right-hand sides: double-float arithmetic on the FP32 pipes
+        prof_single(h, "spmv_residual_df", 0, 0, st, true);
+        wd::launch_spmv_residual_df(h->dsym, h->d_spmv_chunks, h->n_spmv_chunks, h->d_spmv_fin,
+                                    h->n_spmv_fin, h->d_csr_vh, h->d_csr_vl, X, h->d_Xh, h->d_Xl, h->d_Bp,
+                                    h->d_R, h->d_P, nrhs, st);
+        prof_single(h, "spmv_residual_df", 2.0 * nf * nrhs, 12.0 * nf + 24.0 * n * nrhs, st, false);
+        h->launches += 1;
+    } else {
+        prof_single(h, "spmv_residual_fp64", 0, 0, st, true);
+        wd::launch_spmv_residual(h->dsym, h->d_spmv_chunks, h->n_spmv_chunks, h->d_spmv_fin,
+                                 h->n_spmv_fin, X, h->d_Bp, h->d_R, h->d_P, nrhs, st);
+        prof_single(h, "spmv_residual_fp64", 2.0 * nf * nrhs, 12.0 * nf + 24.0 * n * nrhs, st, false);
+    }
     if (h->batch_count > 0) {
         // per instance and column: each instance is its own system
         const int cnt = h->batch_count;
@@ -1446,6 +1461,37 @@ extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb,
            "B D2H");
     CK(cudaStreamSynchronize(st), "solve");
     return WD_OK;
+}
+
+extern "C" wd_status wd_backward_error(wd_handle h, const double *X, const double *B, int64_t nrhs,
+                                       int64_t ld, int on_device, void *stream, double *be) {
+    if (!h || !be) return WD_ERR_INVALID_ARG;
+    if (!h->factored) return fail(h, WD_ERR_STATE, "wd_backward_error before a successful wd_factor");
+    const int64_t n = h->S.n;
+    if (!X || !B || nrhs <= 0 || ld < n) return fail(h, WD_ERR_INVALID_ARG, "bad arguments");
+    CK(cudaSetDevice(h->device), "set device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    wd_status s = ensure_solve_ws(h, nrhs);
+    if (s != WD_OK) return s;
+    const double *Xd = X, *Bd = B;
+    int64_t ldd = ld;
+    if (!on_device) {
+        // stage both through the solve workspaces (column-major, ld n)
+        CK(cudaMemcpy2DAsync(h->d_B, n * sizeof(double), B, ld * sizeof(double), n * sizeof(double), nrhs,
+                             cudaMemcpyHostToDevice, st),
+           "B H2D");
+        CK(cudaMemcpy2DAsync(h->d_R, n * sizeof(double), X, ld * sizeof(double), n * sizeof(double), nrhs,
+                             cudaMemcpyHostToDevice, st),
+           "X H2D");
+        Bd = h->d_B;
+        Xd = h->d_R;
+        ldd = n;
+    }
+    wd::launch_permute_in_rm(Bd, ldd, h->d_Bp, h->dsym.perm, n, nrhs, st);
+    wd::launch_permute_in_rm(Xd, ldd, h->d_X, h->dsym.perm, n, nrhs, st);
+    h->launches += 2;
+    CK(cudaGetLastError(), "permute launch");
+    return backward_errors(h, h->d_X, nrhs, st, be);
 }
 
 extern "C" wd_status wd_logdet(wd_handle h, double *out) {

@@ -10,7 +10,6 @@ using status_t = unsigned long long;
 
 constexpr int NB = 64;        // pivot block width and Schur tile size
 constexpr int RB = 64;        // rows per panel (TRSM) block
-constexpr int SOLVE_RB = 64;  // rows per solve block
 
 // Device pointers of the analysis (all arrays are owned by the handle).
 struct DevSym {
@@ -95,32 +94,15 @@ void launch_tc_schur(const DevSym &d, float *front, const unsigned char *pk, con
 void init_tc_attributes();
 
 // ---- values, solves and reductions (solve_kernels.cu) ---------------------
-void launch_gather_values(const int32_t *csr_src, const double *values, double *csr_val,
-                          int64_t nnz, cudaStream_t st);
+// csr_val = values in CSR order; hi / lo (nullable): its double-float split
+void launch_gather_values(const int32_t *csr_src, const double *values, double *csr_val, float *hi,
+                          float *lo, int64_t nnz, cudaStream_t st);
 template <class T>
 void launch_permute_in(const double *B, int64_t ldb, T *Y, const int32_t *perm, int64_t n,
                        int64_t nrhs, cudaStream_t st);
 template <class T>
 void launch_permute_out(const T *Y, double *B, int64_t ldb, const int32_t *perm, int64_t n,
                         int64_t nrhs, cudaStream_t st);
-template <class T>
-void launch_fwd_gather(const DevSym &d, const T *front, T *Y, T *W, const int4 *items,
-                       int count, int nrhs, cudaStream_t st);
-template <class T>
-void launch_fwd_diag_first(const DevSym &d, const T *dinv, T *Y, const int4 *items, int count,
-                           int nrhs, cudaStream_t st);
-template <class T>
-void launch_fwd_update(const DevSym &d, const T *front, const T *dinv, T *Y, const int4 *items,
-                       int count, int kb, int nrhs, cudaStream_t st);
-template <class T>
-void launch_fwd_rgemm(const DevSym &d, const T *front, const T *Y, T *W, const int4 *items,
-                      int count, int nrhs, cudaStream_t st);
-template <class T>
-void launch_bwd_init(const DevSym &d, const T *front, const T *dinv, T *Y, const int4 *items,
-                     int count, int nrhs, cudaStream_t st);
-template <class T>
-void launch_bwd_step(const DevSym &d, const T *front, const T *dinv, T *Y, const int4 *items,
-                     int count, int ib, int nrhs, cudaStream_t st);
 template <class T>
 void launch_apply_L(const DevSym &d, const T *front, const T *Z, T *Out, T *W,
                     const int4 *items, int count, int nrhs, cudaStream_t st);
@@ -138,6 +120,11 @@ constexpr int SPMV_CHUNK = 512;
 void launch_spmv_residual(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin,
                           int nfin, const double *X, const double *Bp, double *R, double *P,
                           int64_t nrhs, cudaStream_t st);
+// the same residual in double-float arithmetic (vh + vl = the CSR values;
+// Xh, Xl: n x nrhs scratch for the split of X)
+void launch_spmv_residual_df(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin, int nfin,
+                             const float *vh, const float *vl, const double *X, float *Xh, float *Xl,
+                             const double *Bp, double *R, double *P, int64_t nrhs, cudaStream_t st);
 void launch_norm_inf_rows(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin,
                           int nfin, double *partial, double *out, cudaStream_t st);
 void launch_colmax3(const double *R, const double *X, const double *Bp, int64_t n,

@@ -400,6 +400,7 @@ __global__ void __launch_bounds__(THREADS) bupdate_kernel(DevSym d, const T *__r
 // backward
 // ---------------------------------------------------------------------------
 constexpr int KSR = SOLVE_KSR;    // rows below B per split of the reduction
+constexpr int FIN_CTAS = NB * TN / THREADS;
 constexpr int LDT = NB + 4;       // row stride of the staged L^T tile (16-byte multiple)
 
 template <class T>
@@ -482,16 +483,18 @@ template <class T>
 __global__ void __launch_bounds__(THREADS) breduce_finish_kernel(DevSym d, const T *__restrict__ Y,
                                                                  T *__restrict__ Tt, const T *__restrict__ P,
                                                                  const int4 *__restrict__ items, int nrhs) {
-    const int4 it = items[blockIdx.x];
+    // FIN_CTAS CTAs per item, one element of the 64 x 32 tile per thread
+    const int4 it = items[blockIdx.x / FIN_CTAS];
     const int s = it.x, sb = it.y >> 3, cb = it.y & 7, g = it.z & 0xFFFF, nsplit = it.z >> 16;
     const int k = d.sk[s];
     const int j0 = sb * SB + cb * NB, nb = min(NB, k - j0);
     const int c0 = g * TN, nc = min(TN, nrhs - c0);
     const int64_t n = d.n;
     const int f = d.sfirst[s];
-    for (int idx = threadIdx.x; idx < NB * TN; idx += THREADS) {
+    {
+        const int idx = (blockIdx.x % FIN_CTAS) * THREADS + threadIdx.x;
         const int cl = idx % NB, c = idx / NB;
-        if (cl >= nb || c >= nc) continue;
+        if (cl >= nb || c >= nc) return;
         T sum = T(0);
         for (int q = 0; q < nsplit; ++q) sum += P[((int64_t)(it.w + q) * TN + c) * NB + cl];
         const int64_t o = f + j0 + cl + (int64_t)(c0 + c) * n;
@@ -567,7 +570,7 @@ template <class T>
 void launch_breduce_finish(const DevSym &d, const T *Y, T *Tt, const T *P, const int4 *items, int count,
                            int nrhs, cudaStream_t st) {
     if (count <= 0) return;
-    breduce_finish_kernel<T><<<count, THREADS, 0, st>>>(d, Y, Tt, P, items, nrhs);
+    breduce_finish_kernel<T><<<count * FIN_CTAS, THREADS, 0, st>>>(d, Y, Tt, P, items, nrhs);
 }
 
 #define WD_BLOCKED_INST(T)                                                                              \

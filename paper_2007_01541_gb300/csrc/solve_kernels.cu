@@ -1,12 +1,6 @@
-// Supernodal triangular solves, P^T L z, FP64 residuals and reductions.
-//
-// The solve applies the exact inverse of the compressed matrix (Sections 1
-// and 5):  x = P^T L^-T L^-1 P b.  Both substitutions walk the supernodal
-// tree level by level; inside a supernode they proceed by pivot blocks of NB
-// columns.  Forward: every supernode produces an update vector u_s for the
-// rows below its diagonal block, which its parent gathers through the same
-// relative row maps as the factorization (no atomics).  Backward: every
-// supernode reads the already final x of its front rows.
+// Permutations and transposes of right-hand sides, P^T L z, the FP64
+// residual of the refinement and the reductions (norms, log det).  The
+// triangular solves themselves are in solve_blocked.cu.
 #include "dev_common.cuh"
 #include "engine.h"
 
@@ -14,7 +8,6 @@ namespace wd {
 namespace {
 
 constexpr int THREADS = 256;
-constexpr int RG = 16;  // right-hand sides per block
 
 // ---------------------------------------------------------------------------
 template <class T>
@@ -39,356 +32,32 @@ __global__ void permute_out_kernel(const T *__restrict__ Y, double *__restrict__
     }
 }
 
+// out = values in CSR order; hi / lo (optional): the double-float split
+// out = hi + lo (hi = out rounded to FP32, lo = the rest rounded to FP32)
 __global__ void gather_values_kernel(const int32_t *__restrict__ src, const double *__restrict__ v,
-                                     double *__restrict__ out, int64_t nnz) {
+                                     double *__restrict__ out, float *__restrict__ hi,
+                                     float *__restrict__ lo, int64_t nnz) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
-         e += (int64_t)gridDim.x * blockDim.x)
-        out[e] = v[src[e]];
-}
-
-// ---------------------------------------------------------------------------
-// forward: t = [b_J; 0] + sum over children of their update vectors
-// ---------------------------------------------------------------------------
-template <class T>
-__global__ void __launch_bounds__(THREADS) fwd_gather_kernel(DevSym d, T *__restrict__ Y,
-                                                             T *__restrict__ W,
-                                                             const int4 *__restrict__ items,
-                                                             int nrhs) {
-    const int4 it = items[blockIdx.x];
-    const int s = it.x;
-    const int r = it.y * THREADS + threadIdx.x;
-    const int m = d.sm[s], k = d.sk[s];
-    if (r >= m) return;
-    const int64_t n = d.n;
-    const int f = d.sfirst[s];
-    const int cb = d.child_ptr[s], ce = d.child_ptr[s + 1];
-    T *Ws = W + d.woff[s] * nrhs;
-    for (int col = 0; col < nrhs; ++col) {
-        T t = (r < k) ? Y[f + r + col * n] : T(0);
-        for (int ci = cb; ci < ce; ++ci) {
-            const int c = d.children[ci];
-            const int ic = d.relmap[d.mapoff[c] + r];
-            if (ic >= 0) {
-                const int ldc = d.sm[c] - d.sk[c];
-                t += W[d.woff[c] * nrhs + (int64_t)col * ldc + ic];
-            }
-        }
-        if (r < k) Y[f + r + col * n] = t;
-        else Ws[(int64_t)col * (m - k) + (r - k)] = t;
-    }
-}
-
-// Y rows [rowbase + j0, +nb), rhs [c0, c0+nc) := Dinv Y (trans = 0) or Dinv^T Y
-// (trans = 1), Dinv the stored NB x NB inverse of the diagonal block (zero
-// beyond nb).  Must be called by all THREADS threads.
-template <class T>
-__device__ void diag_apply(const T *Dv, int trans, int nb, T *Y, int64_t n, int64_t rowbase,
-                           int j0, int c0, int nc, T *smem) {
-    T *Ds = smem;  // Ds[p * NB + r] = (trans ? Dinv(p, r) : Dinv(r, p))
-    T(*Ts)[RG] = reinterpret_cast<T(*)[RG]>(smem + NB * NB);
-    const int tid = threadIdx.x;
-    if (!trans) {
-        stage_tile<T, THREADS>(Ds, NB, Dv, NB, NB, NB, NB, NB);
-    } else {
-        for (int idx = tid; idx < NB * NB; idx += THREADS) {
-            const int p = idx % NB, r = idx / NB;  // Dv[idx] = Dinv(p, r)
-            cp_async_elem(Ds + p * NB + r, Dv + idx, true);
-        }
-    }
-    for (int idx = tid; idx < NB * RG; idx += THREADS) {
-        const int r = idx % NB, c = idx / NB;
-        cp_async_elem(&Ts[r][c], Y + rowbase + j0 + r + (int64_t)(c0 + c) * n, r < nb && c < nc);
-    }
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
-    const int r = tid % NB, cg = tid / NB;
-    T acc[RG / 4];
-#pragma unroll
-    for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
-    for (int p = 0; p < nb; ++p) {
-        const T dv = Ds[p * NB + r];
-#pragma unroll
-        for (int u = 0; u < RG / 4; ++u) acc[u] += dv * Ts[p][cg + 4 * u];
-    }
-    __syncthreads();
-    if (r < nb) {
-#pragma unroll
-        for (int u = 0; u < RG / 4; ++u) {
-            const int c = cg + 4 * u;
-            if (c < nc) Y[rowbase + j0 + r + (int64_t)(c0 + c) * n] = acc[u];
-        }
-    }
-    __syncthreads();
-}
-
-template <class T>
-__global__ void __launch_bounds__(THREADS) fwd_diag_first_kernel(DevSym d, const T *__restrict__ dinv,
-                                                                 T *__restrict__ Y,
-                                                                 const int4 *__restrict__ items,
-                                                                 int nrhs) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int4 it = items[blockIdx.x];
-    const int s = it.x, c0 = it.y * RG;
-    const int k = d.sk[s];
-    diag_apply<T>(dinv + d.dinvoff[s], 0, min(NB, k), Y, d.n, d.sfirst[s], 0, c0,
-                  min(RG, nrhs - c0), reinterpret_cast<T *>(smem_raw));
-}
-
-// pivot rows [t0 + rb*SOLVE_RB, k) -= L(rows, kb:kb+NB) y(kb:kb+NB); the block
-// holding the next diagonal block then applies its inverse.
-template <class T>
-__global__ void __launch_bounds__(THREADS) fwd_update_kernel(DevSym d, const T *__restrict__ front,
-                                                             const T *__restrict__ dinv,
-                                                             T *__restrict__ Y,
-                                                             const int4 *__restrict__ items,
-                                                             int kb, int nrhs) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);
-    T *Ls = sm;                                                  // [p][r], ld SOLVE_RB
-    T(*Ys)[RG] = reinterpret_cast<T(*)[RG]>(sm + NB * SOLVE_RB);  // [p][c]
-    const int4 it = items[blockIdx.x];
-    const int s = it.x, rb = it.y, c0 = it.z * RG;
-    const int k = d.sk[s], ld = d.sld[s];
-    const int t0 = kb + NB;  // only blocks followed by another pivot block
-    const int nc = min(RG, nrhs - c0);
-    const int64_t n = d.n;
-    const int f = d.sfirst[s];
-    const T *F = front + d.foff[s];
-    const int r0 = t0 + rb * SOLVE_RB;
-    const int tid = threadIdx.x;
-    stage_tile<T, THREADS>(Ls, SOLVE_RB, F + (int64_t)kb * ld + r0, ld, SOLVE_RB, NB, k - r0, NB);
-    for (int idx = tid; idx < NB * RG; idx += THREADS) {
-        const int p = idx % NB, c = idx / NB;
-        cp_async_elem(&Ys[p][c], Y + f + kb + p + (int64_t)(c0 + c) * n, c < nc);
-    }
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
-    const int rl = tid % SOLVE_RB, cg = tid / SOLVE_RB;  // 4 column groups
-    const int r = r0 + rl;
-    T acc[RG / 4];
-#pragma unroll
-    for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
-#pragma unroll 8
-    for (int p = 0; p < NB; ++p) {
-        const T l = Ls[p * SOLVE_RB + rl];
-#pragma unroll
-        for (int u = 0; u < RG / 4; ++u) acc[u] += l * Ys[p][cg + 4 * u];
-    }
-    if (r < k) {
-#pragma unroll
-        for (int u = 0; u < RG / 4; ++u) {
-            const int c = cg + 4 * u;
-            if (c < nc) Y[f + r + (int64_t)(c0 + c) * n] -= acc[u];
-        }
-    }
-    if (rb == 0) {
-        __syncthreads();
-        diag_apply<T>(dinv + d.dinvoff[s] + (int64_t)(t0 / NB) * NB * NB, 0, min(NB, k - t0), Y, n,
-                      f, t0, c0, nc, sm);
-    }
-}
-
-// rows of R: W_s -= L(R, 0:k) y(0:k), once the whole pivot block is solved;
-// the pivot columns are streamed in chunks of NB, double buffered.
-template <class T>
-__global__ void __launch_bounds__(THREADS) fwd_rgemm_kernel(DevSym d, const T *__restrict__ front,
-                                                            const T *__restrict__ Y,
-                                                            T *__restrict__ W,
-                                                            const int4 *__restrict__ items,
-                                                            int nrhs) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);
-    T *Ls[2] = {sm, sm + NB * SOLVE_RB};
-    T *Ys[2] = {sm + 2 * NB * SOLVE_RB, sm + 2 * NB * SOLVE_RB + NB * RG};
-    const int4 it = items[blockIdx.x];
-    const int s = it.x, rb = it.y, c0 = it.z * RG;
-    const int m = d.sm[s], k = d.sk[s], kp = d.skp[s], ld = d.sld[s];
-    const int nc = min(RG, nrhs - c0);
-    const int64_t n = d.n;
-    const int f = d.sfirst[s];
-    const int i0 = rb * SOLVE_RB;  // first local row of R
-    const T *F = front + d.foff[s] + kp + i0;
-    T *Ws = W + d.woff[s] * nrhs;
-    const int tid = threadIdx.x;
-    const int rl = tid % SOLVE_RB, cg = tid / SOLVE_RB;
-    auto stage = [&](int buf, int p0) {
-        stage_tile<T, THREADS>(Ls[buf], SOLVE_RB, F + (int64_t)p0 * ld, ld, SOLVE_RB, NB,
-                               (m - k) - i0, k - p0);
-        for (int idx = tid; idx < NB * RG; idx += THREADS) {
-            const int p = idx % NB, c = idx / NB;
-            cp_async_elem(Ys[buf] + p * RG + c, Y + f + p0 + p + (int64_t)(c0 + c) * n,
-                          p0 + p < k && c < nc);
-        }
-        cp_async_commit();
-    };
-    T acc[RG / 4];
-#pragma unroll
-    for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
-    const int nchunk = (k + NB - 1) / NB;
-    stage(0, 0);
-    for (int ch = 0; ch < nchunk; ++ch) {
-        const int cur = ch & 1;
-        if (ch + 1 < nchunk) {
-            stage(cur ^ 1, (ch + 1) * NB);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        const T *L = Ls[cur];
-        const T *Yc = Ys[cur];
-#pragma unroll 8
-        for (int p = 0; p < NB; ++p) {
-            const T l = L[p * SOLVE_RB + rl];
-#pragma unroll
-            for (int u = 0; u < RG / 4; ++u) acc[u] += l * Yc[p * RG + cg + 4 * u];
-        }
-        __syncthreads();
-    }
-    const int i = i0 + rl;
-    if (i < m - k) {
-#pragma unroll
-        for (int u = 0; u < RG / 4; ++u) {
-            const int c = cg + 4 * u;
-            if (c < nc) Ws[(int64_t)(c0 + c) * (m - k) + i] -= acc[u];
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const double x = v[src[e]];
+        out[e] = x;
+        if (hi) {
+            const float h = __double2float_rn(x);
+            hi[e] = h;
+            lo[e] = __double2float_rn(x - (double)h);
         }
     }
 }
 
-// ---------------------------------------------------------------------------
-// backward
-// ---------------------------------------------------------------------------
-// y(J block jb) -= L(R, jb)^T x(R) with x(R) read at the front rows beyond the
-// supernode (64-row chunks, double buffered); the last block of J then
-// applies its inverse.
-template <class T>
-__global__ void __launch_bounds__(THREADS) bwd_init_kernel(DevSym d, const T *__restrict__ front,
-                                                           const T *__restrict__ dinv,
-                                                           T *__restrict__ Y,
-                                                           const int4 *__restrict__ items,
-                                                           int nrhs) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);
-    constexpr int LST = 64 * (NB + 1), XST = 64 * RG;
-    T *Ls[2] = {sm, sm + LST + XST};     // [rr][c], ld NB + 1
-    T *Xs[2] = {sm + LST, sm + 2 * LST + XST};  // [rr][c], ld RG
-    const int4 it = items[blockIdx.x];
-    const int s = it.x, jblk = it.y, c0 = it.z * RG;
-    const int m = d.sm[s], k = d.sk[s], kp = d.skp[s], ld = d.sld[s];
-    const int j0 = jblk * NB, nb = min(NB, k - j0);
-    const int nc = min(RG, nrhs - c0);
-    const int64_t n = d.n;
-    const int f = d.sfirst[s];
-    const T *F = front + d.foff[s] + (int64_t)j0 * ld + kp;
-    const int32_t *rows = d.rows + d.rowptr[s] + k;
-    const int tid = threadIdx.x;
-    const int cl = tid % NB, cg = tid / NB;  // column of the block, rhs group of 4
-    const int nR = m - k;
-    auto stage = [&](int buf, int i0) {
-        const int nr = min(64, nR - i0);
-        for (int idx = tid; idx < 64 * NB; idx += THREADS) {
-            const int rr = idx % 64, c = idx / 64;
-            cp_async_elem(Ls[buf] + rr * (NB + 1) + c, F + (int64_t)c * ld + i0 + rr, rr < nr && c < nb);
-        }
-        for (int idx = tid; idx < 64 * RG; idx += THREADS) {
-            const int rr = idx % 64, c = idx / 64;
-            const bool v = rr < nr && c < nc;
-            cp_async_elem(Xs[buf] + rr * RG + c, v ? Y + rows[i0 + rr] + (int64_t)(c0 + c) * n : Y, v);
-        }
-        cp_async_commit();
-    };
-    T acc[RG / 4];
-#pragma unroll
-    for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
-    const int nchunk = (nR + 63) / 64;
-    if (nchunk > 0) stage(0, 0);
-    for (int ch = 0; ch < nchunk; ++ch) {
-        const int cur = ch & 1;
-        if (ch + 1 < nchunk) {
-            stage(cur ^ 1, (ch + 1) * 64);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        const T *L = Ls[cur];
-        const T *X = Xs[cur];
-#pragma unroll 8
-        for (int rr = 0; rr < 64; ++rr) {
-            const T l = L[rr * (NB + 1) + cl];
-#pragma unroll
-            for (int u = 0; u < RG / 4; ++u) acc[u] += l * X[rr * RG + cg + 4 * u];
-        }
-        __syncthreads();
-    }
-    if (cl < nb) {
-#pragma unroll
-        for (int u = 0; u < RG / 4; ++u) {
-            const int c = cg + 4 * u;
-            if (c < nc) Y[f + j0 + cl + (int64_t)(c0 + c) * n] -= acc[u];
-        }
-    }
-    if (j0 + nb == k) {
-        __syncthreads();
-        diag_apply<T>(dinv + d.dinvoff[s] + (int64_t)jblk * NB * NB, 1, nb, Y, n, f, j0, c0, nc, sm);
-    }
-}
-
-// y(block jb) -= L(block ib+1, jb)^T x(block ib+1); block ib then applies
-// its inverse
-template <class T>
-__global__ void __launch_bounds__(THREADS) bwd_step_kernel(DevSym d, const T *__restrict__ front,
-                                                           const T *__restrict__ dinv,
-                                                           T *__restrict__ Y,
-                                                           const int4 *__restrict__ items,
-                                                           int ib, int nrhs) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);
-    T *Ls = sm;                        // [rr][c], ld NB + 1
-    T *Xs = sm + NB * (NB + 1);        // [rr][c], ld RG
-    const int4 it = items[blockIdx.x];
-    const int s = it.x, jblk = it.y, c0 = it.z * RG;
-    const int k = d.sk[s], ld = d.sld[s];
-    const int j0 = jblk * NB, nbj = min(NB, k - j0);
-    const int r0 = (ib + 1) * NB, nr = min(NB, k - r0);
-    const int nc = min(RG, nrhs - c0);
-    const int64_t n = d.n;
-    const int f = d.sfirst[s];
-    const T *F = front + d.foff[s];
-    const int tid = threadIdx.x;
-    for (int idx = tid; idx < NB * NB; idx += THREADS) {
-        const int rr = idx % NB, c = idx / NB;
-        cp_async_elem(Ls + rr * (NB + 1) + c, F + (int64_t)(j0 + c) * ld + r0 + rr, rr < nr && c < nbj);
-    }
-    for (int idx = tid; idx < NB * RG; idx += THREADS) {
-        const int rr = idx % NB, c = idx / NB;
-        cp_async_elem(Xs + rr * RG + c, Y + f + r0 + rr + (int64_t)(c0 + c) * n, rr < nr && c < nc);
-    }
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
-    const int cl = tid % NB, cg = tid / NB;
-    T acc[RG / 4];
-#pragma unroll
-    for (int u = 0; u < RG / 4; ++u) acc[u] = T(0);
-#pragma unroll 8
-    for (int rr = 0; rr < NB; ++rr) {
-        const T l = Ls[rr * (NB + 1) + cl];
-#pragma unroll
-        for (int u = 0; u < RG / 4; ++u) acc[u] += l * Xs[rr * RG + cg + 4 * u];
-    }
-    if (cl < nbj) {
-#pragma unroll
-        for (int u = 0; u < RG / 4; ++u) {
-            const int c = cg + 4 * u;
-            if (c < nc) Y[f + j0 + cl + (int64_t)(c0 + c) * n] -= acc[u];
-        }
-    }
-    if (jblk == ib) {
-        __syncthreads();
-        diag_apply<T>(dinv + d.dinvoff[s] + (int64_t)jblk * NB * NB, 1, nbj, Y, n, f, j0, c0, nc, sm);
+// Xh + Xl = X (double-float split of the refinement vectors)
+__global__ void split_df_kernel(const double *__restrict__ X, float *__restrict__ Xh,
+                                float *__restrict__ Xl, int64_t cnt) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double x = X[t];
+        const float h = __double2float_rn(x);
+        Xh[t] = h;
+        Xl[t] = __double2float_rn(x - (double)h);
     }
 }
 
@@ -535,6 +204,98 @@ __global__ void __launch_bounds__(THREADS) spmv_wide_kernel(DevSym d, const int4
         } else {
             if (ca < nrhs) P[(int64_t)slot * nrhs + ca] = a0 + a1;
             if (cb < nrhs) P[(int64_t)slot * nrhs + cb] = b0 + b1;
+        }
+    }
+}
+
+// Double-float accumulator (hi, lo): a value hi + lo with |lo| <= ulp(hi)/2,
+// about 48 significant bits.  Products of double-float operands are formed
+// exactly up to the lo*lo term with FMA (Dekker / Ogita-Rump-Oishi TwoProd),
+// sums with Knuth's TwoSum and a renormalising FastTwoSum, all with
+// explicitly rounded intrinsics so that nothing is contracted.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ void df_add_prod(DF &s, float ah, float al, float xh, float xl) {
+    const float ph = __fmul_rn(ah, xh);
+    float pl = __fmaf_rn(ah, xh, -ph);          // exact error of ah * xh
+    pl = __fmaf_rn(ah, xl, pl);
+    pl = __fmaf_rn(al, xh, pl);
+    const float t = __fadd_rn(s.hi, ph);         // TwoSum(s.hi, ph)
+    const float z = __fsub_rn(t, s.hi);
+    float e = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(ph, z));
+    e = __fadd_rn(e, __fadd_rn(pl, s.lo));
+    s.hi = __fadd_rn(t, e);                      // FastTwoSum(t, e)
+    s.lo = __fsub_rn(e, __fsub_rn(s.hi, t));
+}
+// s += u (both double-float)
+__device__ __forceinline__ void df_add(DF &s, DF u) {
+    const float t = __fadd_rn(s.hi, u.hi);
+    const float z = __fsub_rn(t, s.hi);
+    float e = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(u.hi, z));
+    e = __fadd_rn(e, __fadd_rn(s.lo, u.lo));
+    s.hi = __fadd_rn(t, e);
+    s.lo = __fsub_rn(e, __fsub_rn(s.hi, t));
+}
+
+// The many-right-hand-side residual in double-float arithmetic on the FP32
+// pipes (about 48 bits: the residual of a refined solution is then exact to
+// ~1e-14 of ||A|| ||x||, far below the 1e-12 backward-error target), same
+// chunking as spmv_wide_kernel; partial and final sums in FP64.
+__global__ void __launch_bounds__(THREADS) spmv_df_kernel(DevSym d, const int4 *__restrict__ items,
+                                                          int count, const float *__restrict__ vh,
+                                                          const float *__restrict__ vl,
+                                                          const float *__restrict__ Xh,
+                                                          const float *__restrict__ Xl,
+                                                          const double *__restrict__ Bp,
+                                                          double *__restrict__ R, double *__restrict__ P,
+                                                          int nrhs) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= count) return;
+    const int4 it = items[w];
+    const int64_t row = it.x;
+    const int e0 = it.y, e1 = it.z, slot = it.w;
+    for (int c0 = 0; c0 < nrhs; c0 += 64) {
+        const int ca = c0 + lane, cb = c0 + 32 + lane;
+        const bool va = ca < nrhs, vb = cb < nrhs;
+        // four interleaved entry streams: independent accumulation chains
+        constexpr int NS = 4;
+        DF a[NS], b[NS];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) a[q] = b[q] = DF{0.f, 0.f};
+        int e = e0;
+        for (; e + NS <= e1; e += NS) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const float ah = vh[e + q], al = vl[e + q];
+                const int64_t xo = (int64_t)d.csr_col[e + q] * nrhs;
+                if (va) df_add_prod(a[q], ah, al, Xh[xo + ca], Xl[xo + ca]);
+                if (vb) df_add_prod(b[q], ah, al, Xh[xo + cb], Xl[xo + cb]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NS - 1; ++q) {
+            if (e + q < e1) {
+                const float ah = vh[e + q], al = vl[e + q];
+                const int64_t xo = (int64_t)d.csr_col[e + q] * nrhs;
+                if (va) df_add_prod(a[q], ah, al, Xh[xo + ca], Xl[xo + ca]);
+                if (vb) df_add_prod(b[q], ah, al, Xh[xo + cb], Xl[xo + cb]);
+            }
+        }
+        df_add(a[0], a[1]);
+        df_add(a[2], a[3]);
+        df_add(a[0], a[2]);
+        df_add(b[0], b[1]);
+        df_add(b[2], b[3]);
+        df_add(b[0], b[2]);
+        const double sa = (double)a[0].hi + (double)a[0].lo, sb = (double)b[0].hi + (double)b[0].lo;
+        if (slot < 0) {
+            if (va) R[row * nrhs + ca] = Bp[row * nrhs + ca] - sa;
+            if (vb) R[row * nrhs + cb] = Bp[row * nrhs + cb] - sb;
+        } else {
+            if (va) P[(int64_t)slot * nrhs + ca] = sa;
+            if (vb) P[(int64_t)slot * nrhs + cb] = sb;
         }
     }
 }
@@ -707,41 +468,14 @@ inline int grid_for(int64_t work) {
     return (int)(g < 1 ? 1 : g);
 }
 
-template <class T>
-constexpr size_t diag_smem() { return sizeof(T) * (NB * (NB + 1) + NB * RG); }
-template <class T>
-constexpr size_t bwd_init_smem() { return 2 * sizeof(T) * (64 * (NB + 1) + 64 * RG); }
-template <class T>
-constexpr size_t rgemm_smem() { return 2 * sizeof(T) * (NB * SOLVE_RB + NB * RG); }
-
-template <class T>
-void set_attrs() {
-    static bool done = false;
-    if (done) return;
-    cudaFuncSetAttribute(fwd_diag_first_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)diag_smem<T>());
-    cudaFuncSetAttribute(fwd_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)diag_smem<T>());
-    cudaFuncSetAttribute(bwd_init_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)bwd_init_smem<T>());
-    cudaFuncSetAttribute(bwd_step_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)diag_smem<T>());
-    cudaFuncSetAttribute(fwd_rgemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)rgemm_smem<T>());
-    done = true;
-}
-
 }  // namespace
 
-void init_solve_attributes() {
-    set_attrs<double>();
-    set_attrs<float>();
-}
+void init_solve_attributes() {}
 
-void launch_gather_values(const int32_t *src, const double *values, double *out, int64_t nnz,
-                          cudaStream_t st) {
+void launch_gather_values(const int32_t *src, const double *values, double *out, float *hi, float *lo,
+                          int64_t nnz, cudaStream_t st) {
     if (nnz <= 0) return;
-    gather_values_kernel<<<grid_for(nnz), THREADS, 0, st>>>(src, values, out, nnz);
+    gather_values_kernel<<<grid_for(nnz), THREADS, 0, st>>>(src, values, out, hi, lo, nnz);
 }
 
 template <class T>
@@ -754,53 +488,6 @@ template <class T>
 void launch_permute_out(const T *Y, double *B, int64_t ldb, const int32_t *perm, int64_t n,
                         int64_t nrhs, cudaStream_t st) {
     permute_out_kernel<T><<<grid_for(n * nrhs), THREADS, 0, st>>>(Y, B, ldb, perm, n, nrhs);
-}
-
-template <class T>
-void launch_fwd_gather(const DevSym &d, const T *, T *Y, T *W, const int4 *items, int count,
-                       int nrhs, cudaStream_t st) {
-    if (count <= 0) return;
-    fwd_gather_kernel<T><<<count, THREADS, 0, st>>>(d, Y, W, items, nrhs);
-}
-
-template <class T>
-void launch_fwd_diag_first(const DevSym &d, const T *dinv, T *Y, const int4 *items, int count,
-                           int nrhs, cudaStream_t st) {
-    if (count <= 0) return;
-    set_attrs<T>();
-    fwd_diag_first_kernel<T><<<count, THREADS, diag_smem<T>(), st>>>(d, dinv, Y, items, nrhs);
-}
-
-template <class T>
-void launch_fwd_update(const DevSym &d, const T *front, const T *dinv, T *Y, const int4 *items,
-                       int count, int kb, int nrhs, cudaStream_t st) {
-    if (count <= 0) return;
-    set_attrs<T>();
-    fwd_update_kernel<T><<<count, THREADS, diag_smem<T>(), st>>>(d, front, dinv, Y, items, kb, nrhs);
-}
-
-template <class T>
-void launch_fwd_rgemm(const DevSym &d, const T *front, const T *Y, T *W, const int4 *items,
-                      int count, int nrhs, cudaStream_t st) {
-    if (count <= 0) return;
-    set_attrs<T>();
-    fwd_rgemm_kernel<T><<<count, THREADS, rgemm_smem<T>(), st>>>(d, front, Y, W, items, nrhs);
-}
-
-template <class T>
-void launch_bwd_init(const DevSym &d, const T *front, const T *dinv, T *Y, const int4 *items,
-                     int count, int nrhs, cudaStream_t st) {
-    if (count <= 0) return;
-    set_attrs<T>();
-    bwd_init_kernel<T><<<count, THREADS, bwd_init_smem<T>(), st>>>(d, front, dinv, Y, items, nrhs);
-}
-
-template <class T>
-void launch_bwd_step(const DevSym &d, const T *front, const T *dinv, T *Y, const int4 *items,
-                     int count, int ib, int nrhs, cudaStream_t st) {
-    if (count <= 0) return;
-    set_attrs<T>();
-    bwd_step_kernel<T><<<count, THREADS, diag_smem<T>(), st>>>(d, front, dinv, Y, items, ib, nrhs);
 }
 
 template <class T>
@@ -835,6 +522,16 @@ void launch_spmv_residual(const DevSym &d, const int4 *chunks, int nchunks, cons
         spmv_narrow_kernel<<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, X, Bp, R, P, (int)nrhs);
     else
         spmv_wide_kernel<<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, X, Bp, R, P, (int)nrhs);
+    if (nfin > 0) spmv_finish_kernel<<<nfin, 64, 0, st>>>(fin, nfin, Bp, R, P, (int)nrhs);
+}
+
+void launch_spmv_residual_df(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin, int nfin,
+                             const float *vh, const float *vl, const double *X, float *Xh, float *Xl,
+                             const double *Bp, double *R, double *P, int64_t nrhs, cudaStream_t st) {
+    const int64_t cnt = d.n * nrhs;
+    split_df_kernel<<<grid_for(cnt), THREADS, 0, st>>>(X, Xh, Xl, cnt);
+    const int blocks = (int)(((int64_t)nchunks * 32 + THREADS - 1) / THREADS);
+    spmv_df_kernel<<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, vh, vl, Xh, Xl, Bp, R, P, (int)nrhs);
     if (nfin > 0) spmv_finish_kernel<<<nfin, 64, 0, st>>>(fin, nfin, Bp, R, P, (int)nrhs);
 }
 
@@ -884,18 +581,6 @@ void launch_export_panels(const DevSym &d, const T *front, double *panels, const
                                        int64_t, cudaStream_t);                                   \
     template void launch_permute_out<T>(const T *, double *, int64_t, const int32_t *, int64_t,  \
                                         int64_t, cudaStream_t);                                  \
-    template void launch_fwd_gather<T>(const DevSym &, const T *, T *, T *, const int4 *, int,   \
-                                       int, cudaStream_t);                                       \
-    template void launch_fwd_diag_first<T>(const DevSym &, const T *, T *, const int4 *, int,    \
-                                           int, cudaStream_t);                                   \
-    template void launch_fwd_update<T>(const DevSym &, const T *, const T *, T *, const int4 *,  \
-                                       int, int, int, cudaStream_t);                             \
-    template void launch_fwd_rgemm<T>(const DevSym &, const T *, const T *, T *, const int4 *,   \
-                                      int, int, cudaStream_t);                                   \
-    template void launch_bwd_init<T>(const DevSym &, const T *, const T *, T *, const int4 *,    \
-                                     int, int, cudaStream_t);                                    \
-    template void launch_bwd_step<T>(const DevSym &, const T *, const T *, T *, const int4 *,    \
-                                     int, int, int, cudaStream_t);                               \
     template void launch_apply_L<T>(const DevSym &, const T *, const T *, T *, T *,              \
                                     const int4 *, int, int, cudaStream_t);                       \
     template void launch_axpy_into<T>(double *, const T *, int64_t, int, cudaStream_t);          \

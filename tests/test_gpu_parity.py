@@ -240,3 +240,24 @@ def test_factor_mixed_entries(wdlib, cuda, name):
     assert worst <= 2e-5, worst
     if name == "1d_J10":
         assert _panel_mask_check(s, o) == 0.0
+
+
+@pytest.mark.parametrize("nrhs", [3, 40])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_backward_error_call_matches_fp64_residual(wdlib, cuda, nrhs, prec):
+    """wd_backward_error (FP64 residual up to 8 columns, double-float beyond)
+    against the oracle's FP64 residual, on solutions perturbed so that the
+    residual is well above rounding, and on exact solves (tiny residual)."""
+    b, cp, ri, v, o = _case("2d_J6")
+    s = wdlib.Solver().analyze(cp, ri, b).factor(v, prec)
+    B = rhs(o.n, nrhs, seed=9)
+    X = s.solve(B)
+    be0 = s.backward_error(X, B)
+    assert be0 <= 1e-12
+    assert abs(be0 - oracle.backward_error(cp, ri, v, X, B).max()) <= 2e-15
+    rng = np.random.default_rng(2)
+    for scale in (1e-13, 1e-9, 1e-5):
+        Xp = X + scale * np.abs(X).max() * rng.standard_normal(X.shape)
+        ref = oracle.backward_error(cp, ri, v, Xp, B).max()
+        got = s.backward_error(Xp, B)
+        assert abs(got - ref) <= 1e-6 * ref + 2e-15, (scale, got, ref)
