@@ -59,7 +59,8 @@ struct Plan {
     std::vector<int4> items;
     std::vector<Launch> launches;
     int4 *d_items = nullptr;
-    int rgt = 16;            // solve plans: right-hand sides per CTA tile
+    int rgt = 16;            // solve plans: right-hand sides per gather CTA
+    int large = 0;           // solve plans: 128 x 64 product tiles (else 64 x 32)
     int64_t slots = 0;       // solve plans: partial-sum slots of the largest split step
 };
 
@@ -444,14 +445,16 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
     }
 }
 
-static void build_solve_plan(const wd::Symbolic &S, int nrhs, Plan &p) {
+static void build_solve_plan(const wd::Symbolic &S, int nrhs, int large, Plan &p) {
     p.items.clear();
     p.launches.clear();
     const int rgt = nrhs >= 48 ? 64 : 16;   // right-hand sides per gather CTA
     p.rgt = rgt;
+    p.large = large;
     p.slots = 0;
     const int ngg = (nrhs + rgt - 1) / rgt;
-    const int ng = (nrhs + wd::SOLVE_TN - 1) / wd::SOLVE_TN;
+    const int TRW = wd::solve_tile_rows(large), TNW = wd::solve_tile_rhs(large);
+    const int ng = (nrhs + TNW - 1) / TNW;
     const double R = nrhs;
     const int SBW = wd::SB, KSR = wd::SOLVE_KSR;
     auto nsb = [&](int s) { return (S.k(s) + SBW - 1) / SBW; };
@@ -479,7 +482,7 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, Plan &p) {
                 const int s = S.level_nodes[i];
                 if (nsb(s) <= sb) continue;
                 const int w = width(s, sb), wp = wpad(s, sb);
-                for (int rb = 0; rb * NB < wp; ++rb)
+                for (int rb = 0; rb * TRW < wp; ++rb)
                     for (int g = 0; g < ng; ++g) p.items.push_back({s, sb, rb, g});
                 fl += (double)w * (w + 1) * R;
                 el += (double)w * (w + 1) / 2 + 2.0 * w * R;
@@ -492,9 +495,9 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, Plan &p) {
                 if (nsb(s) <= sb) continue;
                 const int k = S.k(s), m = S.m(s), w = width(s, sb);
                 const int nJ = k - (sb * SBW + w), nR = m - k;
-                for (int rb = 0; rb * 64 < nJ; ++rb)
+                for (int rb = 0; rb * TRW < nJ; ++rb)
                     for (int g = 0; g < ng; ++g) p.items.push_back({s, sb, rb, g});
-                for (int rb = 0; rb * 64 < nR; ++rb)
+                for (int rb = 0; rb * TRW < nR; ++rb)
                     for (int g = 0; g < ng; ++g) p.items.push_back({s, sb, rb, g + 65536});
                 fl += 2.0 * (nJ + nR) * w * R;
                 el += (double)(nJ + nR) * w + 2.0 * (nJ + nR) * R + w * R;
@@ -518,7 +521,7 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, Plan &p) {
                 const int m = S.m(s), w = width(s, sb);
                 const int below = m - (sb * SBW + w);
                 const int nsplit = (below + KSR - 1) / KSR;
-                for (int cb = 0; cb * NB < w; ++cb)
+                for (int cb = 0; cb * TRW < w; ++cb)
                     for (int g = 0; g < ng; ++g) {
                         fin.push_back({s, sb * 8 + cb, g + 65536 * nsplit, slot});
                         for (int ks = 0; ks < nsplit; ++ks)
@@ -533,7 +536,7 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, Plan &p) {
             el = 0;
             for (const int4 &q : fin) {
                 p.items.push_back(q);
-                el += 2.0 * NB * R + (double)(q.z >> 16) * NB * wd::SOLVE_TN;
+                el += 2.0 * TRW * R + (double)(q.z >> 16) * TRW * TNW;
             }
             add_launch(p, K_BWD_FINISH, f0, sb, 0, el, 0);
             f0 = p.items.size();
@@ -542,7 +545,7 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, Plan &p) {
                 const int s = S.level_nodes[i];
                 if (nsb(s) <= sb) continue;
                 const int w = width(s, sb), wp = wpad(s, sb);
-                for (int rb = 0; rb * NB < wp; ++rb)
+                for (int rb = 0; rb * TRW < wp; ++rb)
                     for (int g = 0; g < ng; ++g) p.items.push_back({s, sb, rb, g});
                 fl += (double)w * (w + 1) * R;
                 el += (double)w * (w + 1) / 2 + 2.0 * w * R;
@@ -1271,6 +1274,7 @@ static void enqueue_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st, boo
     T *P = static_cast<T *>(h->d_part);
     const DevSym &d = h->dsym;
     const int rgt = h->splan.rgt;
+    const int lg = h->splan.large;
     size_t li = 0;
     for (const Launch &L : h->splan.launches) {
         const int4 *it = h->splan.d_items + L.off;
@@ -1278,13 +1282,13 @@ static void enqueue_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st, boo
         switch (L.kind) {
             case K_FWD_GATHER: wd::launch_bfwd_gather<T>(d, Y, Tt, W, it, L.count, rgt, nrhs, st); break;
             case K_FWD_XAPPLY:
-                wd::launch_xapply<T>(d, Xs, h->d_xsoff, Tt, Y, it, L.count, 0, nrhs, st);
+                wd::launch_xapply<T>(d, Xs, h->d_xsoff, Tt, Y, it, L.count, 0, lg, nrhs, st);
                 break;
-            case K_FWD_BUPDATE: wd::launch_bupdate<T>(d, F, Y, Tt, W, it, L.count, nrhs, st); break;
-            case K_BWD_REDUCE: wd::launch_breduce<T>(d, F, Y, P, it, L.count, nrhs, st); break;
-            case K_BWD_FINISH: wd::launch_breduce_finish<T>(d, Y, Tt, P, it, L.count, nrhs, st); break;
+            case K_FWD_BUPDATE: wd::launch_bupdate<T>(d, F, Y, Tt, W, it, L.count, lg, nrhs, st); break;
+            case K_BWD_REDUCE: wd::launch_breduce<T>(d, F, Y, P, it, L.count, lg, nrhs, st); break;
+            case K_BWD_FINISH: wd::launch_breduce_finish<T>(d, Y, Tt, P, it, L.count, lg, nrhs, st); break;
             case K_BWD_XAPPLY:
-                wd::launch_xapply<T>(d, XTs, h->d_xsoff, Tt, Y, it, L.count, 1, nrhs, st);
+                wd::launch_xapply<T>(d, XTs, h->d_xsoff, Tt, Y, it, L.count, 1, lg, nrhs, st);
                 break;
         }
         if (prof) record_event(h->prof_ev[2 * li + 1], st);
@@ -1373,11 +1377,15 @@ extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     wd_status s = ensure_solve_ws(h, nrhs);
     if (s != WD_OK) return s;
-    if (h->splan_nrhs != nrhs) {
-        build_solve_plan(h->S, (int)nrhs, h->splan);
+    // 64 x 32 tiles: on the 2D 256^2 case the 128 x 64 tiles lost more to the
+    // halved CTA count of the narrow tree levels than they gained per tile
+    const int large = 0;
+    if (h->splan_nrhs != nrhs || h->splan.large != large) {
+        build_solve_plan(h->S, (int)nrhs, large, h->splan);
         s = upload_plan(h, h->work, h->splan);
         if (s != WD_OK) return s;
-        const int64_t need = std::max<int64_t>(h->splan.slots, 1) * NB * wd::SOLVE_TN;
+        const int64_t need = std::max<int64_t>(h->splan.slots, 1) * wd::solve_tile_rows(large) *
+                             wd::solve_tile_rhs(large);
         if (need > h->part_elems) {
             if (h->d_part) h->work.release(h->d_part);
             h->d_part = nullptr;

@@ -184,23 +184,25 @@ void launch_sbinv_transpose(const DevSym &d, const T *xpool, T *xtpool, const in
 template <class T>
 void launch_bfwd_gather(const DevSym &d, const T *Y, T *Tt, T *W, const int4 *items, int count, int rgt,
                         int nrhs, cudaStream_t st);
-// xapply / bupdate / breduce: 64 rows x SOLVE_TN right-hand sides per CTA
-constexpr int SOLVE_TN = 32;
+// xapply / bupdate / breduce tiles: large = 0 -> 64 rows x 32 right-hand
+// sides per CTA, large = 1 -> 128 x 64 (FP32 only); their sizes:
+int solve_tile_rows(int large);
+int solve_tile_rhs(int large);
 template <class T>
 void launch_xapply(const DevSym &d, const T *xp, const int64_t *xsoff, const T *in, T *out,
-                   const int4 *items, int count, int upper, int nrhs, cudaStream_t st);
+                   const int4 *items, int count, int upper, int large, int nrhs, cudaStream_t st);
 template <class T>
 void launch_bupdate(const DevSym &d, const T *front, const T *Y, T *Tt, T *W, const int4 *items, int count,
-                    int nrhs, cudaStream_t st);
+                    int large, int nrhs, cudaStream_t st);
 // split reduction of the backward pass: partial sums of KSR-row splits into
-// P (SOLVE_TN x 64 per slot), then Tt = y - sum over the splits in order
+// P (rows x rhs of the tile per slot), then Tt = y - sum over the splits in order
 constexpr int SOLVE_KSR = 128;
 template <class T>
 void launch_breduce(const DevSym &d, const T *front, const T *Y, T *P, const int4 *items, int count,
-                    int nrhs, cudaStream_t st);
+                    int large, int nrhs, cudaStream_t st);
 template <class T>
 void launch_breduce_finish(const DevSym &d, const T *Y, T *Tt, const T *P, const int4 *items, int count,
-                           int nrhs, cudaStream_t st);
+                           int large, int nrhs, cudaStream_t st);
 
 // ---- per-instance reductions of a block-diagonal batch (batch.cu) ----------
 void launch_seg_norm_inf(const DevSym &d, const int64_t *coff, int count, double *out, cudaStream_t st);

@@ -224,92 +224,119 @@ __global__ void __launch_bounds__(THREADS) bfwd_gather_kernel(DevSym d, const T 
     }
 }
 
-// Tiles of the dependent solve products: 64 rows (or pivot columns) x 32
-// right-hand sides per CTA; warp w owns 8 rows, lane = right-hand side.  The
-// matrix tile is staged with rows contiguous (A[p * lda + row]) and read by a
-// whole warp at once (broadcast 16-byte loads), the right-hand-side tile is
-// staged right-hand-side major with an odd stride (R[c * LDR + p]), so both
-// the staging writes and the reads are free of bank conflicts.
-constexpr int TN = SOLVE_TN;      // right-hand sides per CTA tile
-constexpr int LDR = NB + 1;       // stride of a staged right-hand side
+// Tiles of the dependent solve products: ROWS rows (or pivot columns) x RHS
+// right-hand sides per CTA; warp w owns RPW consecutive rows, lane l the
+// right-hand sides l, l + 32, ... (RPL of them).  The matrix tile is staged
+// with rows contiguous (A[p * lda + row]) and read by a whole warp at once
+// (broadcast 16-byte loads), the right-hand-side tile is staged right-hand-
+// side major with an odd stride (R[c * LDR + p]), so both the staging writes
+// and the reads are free of bank conflicts.  Two shapes: 64 x 32 (few
+// right-hand sides, FP64) and 128 x 64 (FP32 with 64 or more).
+template <int RPW_, int RPL_>
+struct TileCfg {
+    static constexpr int RPW = RPW_;
+    static constexpr int RPL = RPL_;
+    static constexpr int ROWS = 8 * RPW;
+    static constexpr int RHS = 32 * RPL;
+    static constexpr int LDO = ROWS + 1;     // stride of the staged result
+    static constexpr int MINB = RPW * RPL > 8 ? 2 : 4;   // resident CTAs per SM (register budget)
+};
+using TileS = TileCfg<8, 1>;
+using TileL = TileCfg<16, 2>;
+constexpr int LDR = NB + 1;                  // stride of a staged right-hand side
 
-template <class T, int LDA>
-__device__ __forceinline__ void tile_accumulate(T (&acc)[8], const T *A, const T *R, int np) {
+template <class T, class C, int LDA>
+__device__ __forceinline__ void tile_accumulate(T (&acc)[C::RPW][C::RPL], const T *A, const T *R, int np) {
     using V = typename Vec16<T>::type;
     constexpr int E = Vec16<T>::n;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const T *a = A + 8 * w;
+    const T *a = A + C::RPW * w;
     const T *r = R + lane * LDR;
-#pragma unroll 4
+#pragma unroll 2
     for (int p = 0; p < np; ++p) {
-        const T x = r[p];
+        T x[C::RPL];
 #pragma unroll
-        for (int j = 0; j < 8; j += E) {
-            const V q = *reinterpret_cast<const V *>(a + p * LDA + j);
-            const T *e = reinterpret_cast<const T *>(&q);
+        for (int q = 0; q < C::RPL; ++q) x[q] = r[q * 32 * LDR + p];
 #pragma unroll
-            for (int u = 0; u < E; ++u) acc[j + u] += e[u] * x;
+        for (int j = 0; j < C::RPW; j += E) {
+            const V v = *reinterpret_cast<const V *>(a + p * LDA + j);
+            const T *e = reinterpret_cast<const T *>(&v);
+#pragma unroll
+            for (int u = 0; u < E; ++u)
+#pragma unroll
+                for (int q = 0; q < C::RPL; ++q) acc[j + u][q] += e[u] * x[q];
         }
     }
 }
 
-// the CTA's 64 x 32 result into O[c * LDR + r] (r = row of the tile, c =
-// right-hand side), so that it can be written out with rows contiguous
-template <class T>
-__device__ __forceinline__ void tile_to_smem(const T (&acc)[8], T *O) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+template <class T, class C>
+__device__ __forceinline__ void tile_zero(T (&acc)[C::RPW][C::RPL]) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) O[lane * LDR + 8 * w + i] = acc[i];
+    for (int i = 0; i < C::RPW; ++i)
+#pragma unroll
+        for (int q = 0; q < C::RPL; ++q) acc[i][q] = T(0);
 }
 
-// rows [p0, p0 + 64) of right-hand sides c0 .. c0 + 31 (column-major, ld n,
-// first row `row0`) into R[c * LDR + p]; rows >= valid (and columns >= nc) zero
-template <class T>
+// the CTA's result into O[c * LDO + r] (r = row of the tile, c = right-hand
+// side), so that it can be written out with rows contiguous
+template <class T, class C>
+__device__ __forceinline__ void tile_to_smem(const T (&acc)[C::RPW][C::RPL], T *O) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < C::RPW; ++i)
+#pragma unroll
+        for (int q = 0; q < C::RPL; ++q) O[(lane + 32 * q) * C::LDO + C::RPW * w + i] = acc[i][q];
+}
+
+// rows [p0, p0 + 64) of right-hand sides c0 .. c0 + RHS - 1 (column-major,
+// ld n, first row `row0`) into R[c * LDR + p]; rows >= valid (and columns
+// >= nc) zero
+template <class T, class C>
 __device__ __forceinline__ void stage_rhs(T *R, const T *src, int64_t row0, int p0, int valid, int c0,
                                           int nc, int64_t n) {
-    for (int idx = threadIdx.x; idx < NB * TN; idx += THREADS) {
+    for (int idx = threadIdx.x; idx < NB * C::RHS; idx += THREADS) {
         const int p = idx % NB, c = idx / NB;
         const bool v = p0 + p < valid && c < nc;
         cp_async_elem(R + c * LDR + p, v ? src + row0 + p0 + p + (int64_t)(c0 + c) * n : src, v);
     }
 }
 
-template <class T>
+template <class T, class C>
 constexpr int tile_smem_elems() {
-    return 2 * NB * TR + 2 * TN * LDR + 8;
+    return 2 * NB * C::ROWS + 2 * C::RHS * LDR + 8;
 }
 
-// out(B rows 64 rb .. +64) = X_B in_B (upper = 0) or X_B^T in_B (upper = 1,
-// using the stored transpose); item = (s, sb, rb, rhs tile)
-template <class T>
-__global__ void __launch_bounds__(THREADS) xapply_kernel(DevSym d, const T *__restrict__ xp,
+// out(B rows ROWS rb .. +ROWS) = X_B in_B (upper = 0) or X_B^T in_B (upper =
+// 1, using the stored transpose); item = (s, sb, rb, rhs tile)
+template <class T, class C>
+__global__ void __launch_bounds__(THREADS, C::MINB) xapply_kernel(DevSym d, const T *__restrict__ xp,
                                                          const int64_t *__restrict__ xsoff,
                                                          const T *__restrict__ in, T *__restrict__ out,
                                                          const int4 *__restrict__ items, int upper,
                                                          int nrhs) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
-    T *Xs[2] = {sm, sm + NB * TR};                                  // [p][r], ld TR
-    T *Rs[2] = {sm + 2 * NB * TR, sm + 2 * NB * TR + TN * LDR};     // [c][p], ld LDR
+    T *Xs[2] = {sm, sm + NB * C::ROWS};                                    // [p][r], ld ROWS
+    T *Rs[2] = {sm + 2 * NB * C::ROWS, sm + 2 * NB * C::ROWS + C::RHS * LDR};  // [c][p], ld LDR
     const int4 it = items[blockIdx.x];
-    const int s = it.x, sb = it.y, rb = it.z, c0 = it.w * TN;
+    const int s = it.x, sb = it.y, rb = it.z, c0 = it.w * C::RHS;
     const int k = d.sk[s];
     const int b0 = sb * SB;
     const int w = min(SB, k - b0), wp = (w + NB - 1) / NB * NB;
     const int nb = wp / NB;
-    const int nc = min(TN, nrhs - c0);
+    const int nc = min(C::RHS, nrhs - c0);
     const int64_t n = d.n;
     const int64_t row0 = d.sfirst[s] + b0;
     const T *X = xp + xsoff[s] + (int64_t)sb * SB * SB;
-    const int q0 = upper ? rb : 0, q1 = upper ? nb : rb + 1;
+    const int r0 = rb * C::ROWS, rvalid = wp - r0;
+    const int q0 = upper ? r0 / NB : 0, q1 = upper ? nb : min(nb, (r0 + C::ROWS) / NB);
     auto stage = [&](int buf, int q) {
-        stage_tile<T, THREADS>(Xs[buf], TR, X + (int64_t)(q * NB) * wp + rb * NB, wp, TR, NB, TR, NB);
-        stage_rhs<T>(Rs[buf], in, row0, q * NB, w, c0, nc, n);
+        stage_tile<T, THREADS>(Xs[buf], C::ROWS, X + (int64_t)(q * NB) * wp + r0, wp, C::ROWS, NB, rvalid, NB);
+        stage_rhs<T, C>(Rs[buf], in, row0, q * NB, w, c0, nc, n);
         cp_async_commit();
     };
-    T acc[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i] = T(0);
+    T acc[C::RPW][C::RPL];
+    tile_zero<T, C>(acc);
     stage(0, q0);
     for (int q = q0; q < q1; ++q) {
         const int cur = (q - q0) & 1;
@@ -320,50 +347,49 @@ __global__ void __launch_bounds__(THREADS) xapply_kernel(DevSym d, const T *__re
             cp_async_wait<0>();
         }
         __syncthreads();
-        tile_accumulate<T, TR>(acc, Xs[cur], Rs[cur], NB);
+        tile_accumulate<T, C, C::ROWS>(acc, Xs[cur], Rs[cur], min(NB, w - q * NB));
         __syncthreads();
     }
-    T *O = Rs[0];
-    tile_to_smem<T>(acc, O);
+    T *O = sm;
+    tile_to_smem<T, C>(acc, O);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < NB * TN; idx += THREADS) {
-        const int r = idx % NB, c = idx / NB;
-        const int rr = rb * NB + r;
-        if (rr < w && c < nc) out[row0 + rr + (int64_t)(c0 + c) * n] = O[c * LDR + r];
+    for (int idx = threadIdx.x; idx < C::ROWS * C::RHS; idx += THREADS) {
+        const int r = idx % C::ROWS, c = idx / C::ROWS;
+        const int rr = r0 + r;
+        if (rr < w && c < nc) out[row0 + rr + (int64_t)(c0 + c) * n] = O[c * C::LDO + r];
     }
 }
 
 // rows below super-block B: target -= L(rows, B) y_B.  item = (s, sb, rb,
 // tile + 65536 * seg): seg 0 = pivot rows after B (target Tt), seg 1 = rows
 // of R (target the update vector W_s)
-template <class T>
-__global__ void __launch_bounds__(THREADS) bupdate_kernel(DevSym d, const T *__restrict__ front,
+template <class T, class C>
+__global__ void __launch_bounds__(THREADS, C::MINB) bupdate_kernel(DevSym d, const T *__restrict__ front,
                                                           const T *__restrict__ Y, T *__restrict__ Tt,
                                                           T *__restrict__ W, const int4 *__restrict__ items,
                                                           int nrhs) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
-    T *Ls[2] = {sm, sm + NB * TR};
-    T *Rs[2] = {sm + 2 * NB * TR, sm + 2 * NB * TR + TN * LDR};
+    T *Ls[2] = {sm, sm + NB * C::ROWS};
+    T *Rs[2] = {sm + 2 * NB * C::ROWS, sm + 2 * NB * C::ROWS + C::RHS * LDR};
     const int4 it = items[blockIdx.x];
     const int s = it.x, sb = it.y, rb = it.z, g = it.w & 0xFFFF, seg = it.w >> 16;
     const int m = d.sm[s], k = d.sk[s], kp = d.skp[s], ld = d.sld[s];
     const int b0 = sb * SB, w = min(SB, k - b0);
-    const int c0 = g * TN, nc = min(TN, nrhs - c0);
+    const int c0 = g * C::RHS, nc = min(C::RHS, nrhs - c0);
     const int64_t n = d.n;
     const int f = d.sfirst[s];
-    const int i0 = seg == 0 ? b0 + w + rb * TR : rb * TR;        // seg 1: index into R
+    const int i0 = seg == 0 ? b0 + w + rb * C::ROWS : rb * C::ROWS;     // seg 1: index into R
     const int nrow = seg == 0 ? k - i0 : (m - k) - i0;
     const int mrow = seg == 0 ? i0 : kp + i0;
     const T *F = front + d.foff[s] + mrow;
     auto stage = [&](int buf, int p0) {
-        stage_tile<T, THREADS>(Ls[buf], TR, F + (int64_t)(b0 + p0) * ld, ld, TR, NB, nrow, w - p0);
-        stage_rhs<T>(Rs[buf], Y, f + b0, p0, w, c0, nc, n);
+        stage_tile<T, THREADS>(Ls[buf], C::ROWS, F + (int64_t)(b0 + p0) * ld, ld, C::ROWS, NB, nrow, w - p0);
+        stage_rhs<T, C>(Rs[buf], Y, f + b0, p0, w, c0, nc, n);
         cp_async_commit();
     };
-    T acc[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i] = T(0);
+    T acc[C::RPW][C::RPL];
+    tile_zero<T, C>(acc);
     const int nchunk = (w + NB - 1) / NB;
     stage(0, 0);
     for (int ch = 0; ch < nchunk; ++ch) {
@@ -375,11 +401,11 @@ __global__ void __launch_bounds__(THREADS) bupdate_kernel(DevSym d, const T *__r
             cp_async_wait<0>();
         }
         __syncthreads();
-        tile_accumulate<T, TR>(acc, Ls[cur], Rs[cur], NB);
+        tile_accumulate<T, C, C::ROWS>(acc, Ls[cur], Rs[cur], min(NB, w - ch * NB));
         __syncthreads();
     }
-    T *O = Rs[0];
-    tile_to_smem<T>(acc, O);
+    T *O = sm;
+    tile_to_smem<T, C>(acc, O);
     __syncthreads();
     T *dst;
     int64_t ldd;
@@ -390,9 +416,9 @@ __global__ void __launch_bounds__(THREADS) bupdate_kernel(DevSym d, const T *__r
         dst = W + d.woff[s] * nrhs + i0;
         ldd = m - k;
     }
-    for (int idx = threadIdx.x; idx < NB * TN; idx += THREADS) {
-        const int r = idx % NB, c = idx / NB;
-        if (r < nrow && c < nc) dst[r + (int64_t)(c0 + c) * ldd] -= O[c * LDR + r];
+    for (int idx = threadIdx.x; idx < C::ROWS * C::RHS; idx += THREADS) {
+        const int r = idx % C::ROWS, c = idx / C::ROWS;
+        if (r < nrow && c < nc) dst[r + (int64_t)(c0 + c) * ldd] -= O[c * C::LDO + r];
     }
 }
 
@@ -400,33 +426,37 @@ __global__ void __launch_bounds__(THREADS) bupdate_kernel(DevSym d, const T *__r
 // backward
 // ---------------------------------------------------------------------------
 constexpr int KSR = SOLVE_KSR;    // rows below B per split of the reduction
-constexpr int FIN_CTAS = NB * TN / THREADS;
-constexpr int LDT = NB + 4;       // row stride of the staged L^T tile (16-byte multiple)
 
-template <class T>
+template <class C>
+struct ReduceCfg {
+    static constexpr int LDT = C::ROWS + 4;   // row stride of the staged L^T tile (16-byte multiple)
+};
+
+template <class T, class C>
 constexpr int breduce_smem_elems() {
-    return 2 * (64 * LDT + TN * LDR) + 8;
+    return 2 * (64 * ReduceCfg<C>::LDT + C::RHS * LDR) + 8;
 }
 
 // Partial reduction of t_B = y_B - L(rows below B, B)^T x(rows below) over the
 // rows [ks * KSR, (ks + 1) * KSR) of the "rows below" list (pivot rows after B,
 // then the rows of R; x of a front row read at its global row):
-// P[slot] (32 x 64, [rhs][c]) = sum_i L(i, j0 + c) x(i, rhs).
-// item = (s, sb * 8 + cb, tile + 65536 * ks, slot)
-template <class T>
-__global__ void __launch_bounds__(THREADS) breduce_kernel(DevSym d, const T *__restrict__ front,
+// P[slot] (RHS x ROWS, [rhs][c]) = sum_i L(i, j0 + c) x(i, rhs), j0 = b0 +
+// ROWS cb.  item = (s, sb * 8 + cb, tile + 65536 * ks, slot)
+template <class T, class C>
+__global__ void __launch_bounds__(THREADS, C::MINB) breduce_kernel(DevSym d, const T *__restrict__ front,
                                                           const T *__restrict__ Y, T *__restrict__ P,
                                                           const int4 *__restrict__ items, int nrhs) {
+    constexpr int LDT = ReduceCfg<C>::LDT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
-    T *Ls[2] = {sm, sm + 64 * LDT};                                  // [rr][c], ld LDT
-    T *Rs[2] = {sm + 2 * 64 * LDT, sm + 2 * 64 * LDT + TN * LDR};    // [rhs][rr], ld LDR
+    T *Ls[2] = {sm, sm + 64 * LDT};                                          // [rr][c], ld LDT
+    T *Rs[2] = {sm + 2 * 64 * LDT, sm + 2 * 64 * LDT + C::RHS * LDR};        // [rhs][rr], ld LDR
     const int4 it = items[blockIdx.x];
     const int s = it.x, sb = it.y >> 3, cb = it.y & 7, g = it.z & 0xFFFF, ks = it.z >> 16;
     const int m = d.sm[s], k = d.sk[s], kp = d.skp[s], ld = d.sld[s];
     const int b0 = sb * SB, w = min(SB, k - b0);
-    const int j0 = b0 + cb * NB, nb = min(NB, k - j0);
-    const int c0 = g * TN, nc = min(TN, nrhs - c0);
+    const int j0 = b0 + cb * C::ROWS, nb = min(C::ROWS, k - j0);
+    const int c0 = g * C::RHS, nc = min(C::RHS, nrhs - c0);
     const int64_t n = d.n;
     const T *F = front + d.foff[s] + (int64_t)j0 * ld;
     const int32_t *rows = d.rows + d.rowptr[s];
@@ -434,14 +464,14 @@ __global__ void __launch_bounds__(THREADS) breduce_kernel(DevSym d, const T *__r
     const int nJ = k - (b0 + w), nbelow = nJ + (m - k);
     const int u0 = ks * KSR, u1 = min(nbelow, u0 + KSR);
     auto stage = [&](int buf, int ua) {
-        for (int idx = tid; idx < 64 * NB; idx += THREADS) {
+        for (int idx = tid; idx < 64 * C::ROWS; idx += THREADS) {
             const int rr = idx % 64, c = idx / 64;
             const int u = ua + rr;
             const bool v = u < u1 && c < nb;
             const int mrow = u < nJ ? b0 + w + u : kp + (u - nJ);
             cp_async_elem(Ls[buf] + rr * LDT + c, v ? F + (int64_t)c * ld + mrow : F, v);
         }
-        for (int idx = tid; idx < 64 * TN; idx += THREADS) {
+        for (int idx = tid; idx < 64 * C::RHS; idx += THREADS) {
             const int rr = idx % 64, c = idx / 64;
             const int u = ua + rr;
             const bool v = u < u1 && c < nc;
@@ -450,9 +480,8 @@ __global__ void __launch_bounds__(THREADS) breduce_kernel(DevSym d, const T *__r
         }
         cp_async_commit();
     };
-    T acc[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i] = T(0);
+    T acc[C::RPW][C::RPL];
+    tile_zero<T, C>(acc);
     const int nchunk = (u1 - u0 + 63) / 64;
     stage(0, u0);
     for (int ch = 0; ch < nchunk; ++ch) {
@@ -464,63 +493,66 @@ __global__ void __launch_bounds__(THREADS) breduce_kernel(DevSym d, const T *__r
             cp_async_wait<0>();
         }
         __syncthreads();
-        tile_accumulate<T, LDT>(acc, Ls[cur], Rs[cur], 64);
+        tile_accumulate<T, C, LDT>(acc, Ls[cur], Rs[cur], min(64, u1 - u0 - ch * 64));
         __syncthreads();
     }
-    T *O = Rs[0];
-    tile_to_smem<T>(acc, O);
+    T *O = sm;
+    tile_to_smem<T, C>(acc, O);
     __syncthreads();
-    T *Pt = P + (int64_t)it.w * TN * NB;
-    for (int idx = tid; idx < NB * TN; idx += THREADS) {
-        const int r = idx % NB, c = idx / NB;
-        Pt[c * NB + r] = O[c * LDR + r];
+    T *Pt = P + (int64_t)it.w * C::RHS * C::ROWS;
+    for (int idx = tid; idx < C::ROWS * C::RHS; idx += THREADS) {
+        const int r = idx % C::ROWS, c = idx / C::ROWS;
+        Pt[c * C::ROWS + r] = O[c * C::LDO + r];
     }
 }
 
-// Tt(B columns) = y - sum of the splits' partial sums, in split order.
+// Tt(B columns) = y - sum of the splits' partial sums, in split order; one
+// element of the ROWS x RHS tile per thread.
 // item = (s, sb * 8 + cb, tile + 65536 * nsplit, first slot)
-template <class T>
+template <class T, class C>
 __global__ void __launch_bounds__(THREADS) breduce_finish_kernel(DevSym d, const T *__restrict__ Y,
                                                                  T *__restrict__ Tt, const T *__restrict__ P,
                                                                  const int4 *__restrict__ items, int nrhs) {
-    // FIN_CTAS CTAs per item, one element of the 64 x 32 tile per thread
-    const int4 it = items[blockIdx.x / FIN_CTAS];
+    constexpr int PER = C::ROWS * C::RHS / THREADS;   // CTAs per item
+    const int4 it = items[blockIdx.x / PER];
     const int s = it.x, sb = it.y >> 3, cb = it.y & 7, g = it.z & 0xFFFF, nsplit = it.z >> 16;
     const int k = d.sk[s];
-    const int j0 = sb * SB + cb * NB, nb = min(NB, k - j0);
-    const int c0 = g * TN, nc = min(TN, nrhs - c0);
+    const int j0 = sb * SB + cb * C::ROWS, nb = min(C::ROWS, k - j0);
+    const int c0 = g * C::RHS, nc = min(C::RHS, nrhs - c0);
     const int64_t n = d.n;
     const int f = d.sfirst[s];
-    {
-        const int idx = (blockIdx.x % FIN_CTAS) * THREADS + threadIdx.x;
-        const int cl = idx % NB, c = idx / NB;
-        if (cl >= nb || c >= nc) return;
-        T sum = T(0);
-        for (int q = 0; q < nsplit; ++q) sum += P[((int64_t)(it.w + q) * TN + c) * NB + cl];
-        const int64_t o = f + j0 + cl + (int64_t)(c0 + c) * n;
-        Tt[o] = Y[o] - sum;
-    }
+    const int idx = (blockIdx.x % PER) * THREADS + threadIdx.x;
+    const int cl = idx % C::ROWS, c = idx / C::ROWS;
+    if (cl >= nb || c >= nc) return;
+    T sum = T(0);
+    for (int q = 0; q < nsplit; ++q) sum += P[((int64_t)(it.w + q) * C::RHS + c) * C::ROWS + cl];
+    const int64_t o = f + j0 + cl + (int64_t)(c0 + c) * n;
+    Tt[o] = Y[o] - sum;
 }
 
 }  // namespace
 
-template <class T>
+template <class T, class C>
 void set_blocked_attributes() {
-    cudaFuncSetAttribute(xapply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(tile_smem_elems<T>() * sizeof(T)));
-    cudaFuncSetAttribute(bupdate_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(tile_smem_elems<T>() * sizeof(T)));
-    cudaFuncSetAttribute(breduce_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(breduce_smem_elems<T>() * sizeof(T)));
+    cudaFuncSetAttribute(xapply_kernel<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(tile_smem_elems<T, C>() * sizeof(T)));
+    cudaFuncSetAttribute(bupdate_kernel<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(tile_smem_elems<T, C>() * sizeof(T)));
+    cudaFuncSetAttribute(breduce_kernel<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(breduce_smem_elems<T, C>() * sizeof(T)));
 }
 
 void init_blocked_attributes() {
     static bool done = false;
     if (done) return;
-    set_blocked_attributes<float>();
-    set_blocked_attributes<double>();
+    set_blocked_attributes<float, TileS>();
+    set_blocked_attributes<float, TileL>();
+    set_blocked_attributes<double, TileS>();
     done = true;
 }
+
+int solve_tile_rows(int large) { return large ? TileL::ROWS : TileS::ROWS; }
+int solve_tile_rhs(int large) { return large ? TileL::RHS : TileS::RHS; }
 
 template <class T>
 void launch_sbinv_diag(const DevSym &d, const T *dinv, T *xpool, const int64_t *xsoff, const int4 *items,
@@ -545,32 +577,59 @@ void launch_bfwd_gather(const DevSym &d, const T *Y, T *Tt, T *W, const int4 *it
     if (rgt == 64) bfwd_gather_kernel<T, 64><<<count, THREADS, 0, st>>>(d, Y, Tt, W, items, nrhs);
     else bfwd_gather_kernel<T, 16><<<count, THREADS, 0, st>>>(d, Y, Tt, W, items, nrhs);
 }
+template <class T, class C>
+static void xapply_go(const DevSym &d, const T *xp, const int64_t *xsoff, const T *in, T *out,
+                      const int4 *items, int count, int upper, int nrhs, cudaStream_t st) {
+    xapply_kernel<T, C><<<count, THREADS, tile_smem_elems<T, C>() * sizeof(T), st>>>(d, xp, xsoff, in, out,
+                                                                                   items, upper, nrhs);
+}
+template <class T, class C>
+static void bupdate_go(const DevSym &d, const T *front, const T *Y, T *Tt, T *W, const int4 *items,
+                       int count, int nrhs, cudaStream_t st) {
+    bupdate_kernel<T, C><<<count, THREADS, tile_smem_elems<T, C>() * sizeof(T), st>>>(d, front, Y, Tt, W,
+                                                                                    items, nrhs);
+}
+template <class T, class C>
+static void breduce_go(const DevSym &d, const T *front, const T *Y, T *P, const int4 *items, int count,
+                       int nrhs, cudaStream_t st) {
+    breduce_kernel<T, C><<<count, THREADS, breduce_smem_elems<T, C>() * sizeof(T), st>>>(d, front, Y, P,
+                                                                                       items, nrhs);
+}
+template <class T, class C>
+static void finish_go(const DevSym &d, const T *Y, T *Tt, const T *P, const int4 *items, int count, int nrhs,
+                      cudaStream_t st) {
+    constexpr int PER = C::ROWS * C::RHS / THREADS;
+    breduce_finish_kernel<T, C><<<count * PER, THREADS, 0, st>>>(d, Y, Tt, P, items, nrhs);
+}
+
+// large = 1 selects the 128 x 64 tiles (FP32 only)
 template <class T>
 void launch_xapply(const DevSym &d, const T *xp, const int64_t *xsoff, const T *in, T *out,
-                   const int4 *items, int count, int upper, int nrhs, cudaStream_t st) {
+                   const int4 *items, int count, int upper, int large, int nrhs, cudaStream_t st) {
     if (count <= 0) return;
-    xapply_kernel<T><<<count, THREADS, tile_smem_elems<T>() * sizeof(T), st>>>(d, xp, xsoff, in, out, items,
-                                                                             upper, nrhs);
+    if (large && sizeof(T) == 4) xapply_go<T, TileL>(d, xp, xsoff, in, out, items, count, upper, nrhs, st);
+    else xapply_go<T, TileS>(d, xp, xsoff, in, out, items, count, upper, nrhs, st);
 }
 template <class T>
 void launch_bupdate(const DevSym &d, const T *front, const T *Y, T *Tt, T *W, const int4 *items, int count,
-                    int nrhs, cudaStream_t st) {
+                    int large, int nrhs, cudaStream_t st) {
     if (count <= 0) return;
-    bupdate_kernel<T><<<count, THREADS, tile_smem_elems<T>() * sizeof(T), st>>>(d, front, Y, Tt, W, items,
-                                                                              nrhs);
+    if (large && sizeof(T) == 4) bupdate_go<T, TileL>(d, front, Y, Tt, W, items, count, nrhs, st);
+    else bupdate_go<T, TileS>(d, front, Y, Tt, W, items, count, nrhs, st);
 }
 template <class T>
 void launch_breduce(const DevSym &d, const T *front, const T *Y, T *P, const int4 *items, int count,
-                    int nrhs, cudaStream_t st) {
+                    int large, int nrhs, cudaStream_t st) {
     if (count <= 0) return;
-    breduce_kernel<T><<<count, THREADS, breduce_smem_elems<T>() * sizeof(T), st>>>(d, front, Y, P, items,
-                                                                                 nrhs);
+    if (large && sizeof(T) == 4) breduce_go<T, TileL>(d, front, Y, P, items, count, nrhs, st);
+    else breduce_go<T, TileS>(d, front, Y, P, items, count, nrhs, st);
 }
 template <class T>
 void launch_breduce_finish(const DevSym &d, const T *Y, T *Tt, const T *P, const int4 *items, int count,
-                           int nrhs, cudaStream_t st) {
+                           int large, int nrhs, cudaStream_t st) {
     if (count <= 0) return;
-    breduce_finish_kernel<T><<<count * FIN_CTAS, THREADS, 0, st>>>(d, Y, Tt, P, items, nrhs);
+    if (large && sizeof(T) == 4) finish_go<T, TileL>(d, Y, Tt, P, items, count, nrhs, st);
+    else finish_go<T, TileS>(d, Y, Tt, P, items, count, nrhs, st);
 }
 
 #define WD_BLOCKED_INST(T)                                                                              \
@@ -583,13 +642,13 @@ void launch_breduce_finish(const DevSym &d, const T *Y, T *Tt, const T *P, const
     template void launch_bfwd_gather<T>(const DevSym &, const T *, T *, T *, const int4 *, int, int, int, \
                                         cudaStream_t);                                                  \
     template void launch_xapply<T>(const DevSym &, const T *, const int64_t *, const T *, T *,           \
-                                   const int4 *, int, int, int, cudaStream_t);                          \
+                                   const int4 *, int, int, int, int, cudaStream_t);                     \
     template void launch_bupdate<T>(const DevSym &, const T *, const T *, T *, T *, const int4 *, int,   \
-                                    int, cudaStream_t);                                                 \
+                                    int, int, cudaStream_t);                                            \
     template void launch_breduce<T>(const DevSym &, const T *, const T *, T *, const int4 *, int, int,   \
-                                    cudaStream_t);                                                      \
+                                    int, cudaStream_t);                                                 \
     template void launch_breduce_finish<T>(const DevSym &, const T *, T *, const T *, const int4 *, int, \
-                                           int, cudaStream_t);
+                                           int, int, cudaStream_t);
 WD_BLOCKED_INST(float)
 WD_BLOCKED_INST(double)
 

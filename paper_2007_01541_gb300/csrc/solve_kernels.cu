@@ -242,7 +242,7 @@ __device__ __forceinline__ void df_add(DF &s, DF u) {
 // pipes (about 48 bits: the residual of a refined solution is then exact to
 // ~1e-14 of ||A|| ||x||, far below the 1e-12 backward-error target), same
 // chunking as spmv_wide_kernel; partial and final sums in FP64.
-__global__ void __launch_bounds__(THREADS) spmv_df_kernel(DevSym d, const int4 *__restrict__ items,
+__global__ void __launch_bounds__(THREADS, 4) spmv_df_kernel(DevSym d, const int4 *__restrict__ items,
                                                           int count, const float *__restrict__ vh,
                                                           const float *__restrict__ vl,
                                                           const float *__restrict__ Xh,
@@ -259,28 +259,38 @@ __global__ void __launch_bounds__(THREADS) spmv_df_kernel(DevSym d, const int4 *
     for (int c0 = 0; c0 < nrhs; c0 += 64) {
         const int ca = c0 + lane, cb = c0 + 32 + lane;
         const bool va = ca < nrhs, vb = cb < nrhs;
-        // four interleaved entry streams: independent accumulation chains
+        // entries are fetched 32 at a time (lane i loads entry eb + i) and
+        // broadcast by shuffles; NS interleaved accumulation streams keep NS
+        // independent chains and NS entries' x loads in flight
         constexpr int NS = 4;
         DF a[NS], b[NS];
 #pragma unroll
         for (int q = 0; q < NS; ++q) a[q] = b[q] = DF{0.f, 0.f};
-        int e = e0;
-        for (; e + NS <= e1; e += NS) {
+        for (int eb = e0; eb < e1; eb += 32) {
+            const int my = eb + lane, cnt = min(32, e1 - eb);
+            const int col = my < e1 ? d.csr_col[my] : 0;
+            const float mh = my < e1 ? vh[my] : 0.f, ml = my < e1 ? vl[my] : 0.f;
+            for (int j = 0; j < cnt; j += NS) {
+                float xh[NS][2], xl[NS][2], ah[NS], al[NS];
 #pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                const float ah = vh[e + q], al = vl[e + q];
-                const int64_t xo = (int64_t)d.csr_col[e + q] * nrhs;
-                if (va) df_add_prod(a[q], ah, al, Xh[xo + ca], Xl[xo + ca]);
-                if (vb) df_add_prod(b[q], ah, al, Xh[xo + cb], Xl[xo + cb]);
-            }
-        }
+                for (int q = 0; q < NS; ++q) {
+                    const int src = (j + q) & 31;
+                    const int64_t xo = (int64_t)__shfl_sync(0xffffffffu, col, src) * nrhs;
+                    ah[q] = __shfl_sync(0xffffffffu, mh, src);
+                    al[q] = __shfl_sync(0xffffffffu, ml, src);
+                    const bool ok = j + q < cnt;
+                    xh[q][0] = (ok && va) ? Xh[xo + ca] : 0.f;
+                    xl[q][0] = (ok && va) ? Xl[xo + ca] : 0.f;
+                    xh[q][1] = (ok && vb) ? Xh[xo + cb] : 0.f;
+                    xl[q][1] = (ok && vb) ? Xl[xo + cb] : 0.f;
+                }
 #pragma unroll
-        for (int q = 0; q < NS - 1; ++q) {
-            if (e + q < e1) {
-                const float ah = vh[e + q], al = vl[e + q];
-                const int64_t xo = (int64_t)d.csr_col[e + q] * nrhs;
-                if (va) df_add_prod(a[q], ah, al, Xh[xo + ca], Xl[xo + ca]);
-                if (vb) df_add_prod(b[q], ah, al, Xh[xo + cb], Xl[xo + cb]);
+                for (int q = 0; q < NS; ++q) {
+                    if (j + q < cnt) {
+                        df_add_prod(a[q], ah[q], al[q], xh[q][0], xl[q][0]);
+                        df_add_prod(b[q], ah[q], al[q], xh[q][1], xl[q][1]);
+                    }
+                }
             }
         }
         df_add(a[0], a[1]);
