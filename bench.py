@@ -38,6 +38,32 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 FP64_FLOPS_PER_SM_CLK = 4     # 2 FP64 FMA per SM per clock (GB300: 1.25 TFLOP/s nominal)
 MAX_SM_MHZ = 2070.0
+DF_OPS_PER_TERM = 15          # FP32 instructions of one double-float multiply-add
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# kernel from one ncu capture of the full-size command, with the SHA-1 of the
+# source file the kernel was built from: reported as null once that file has
+# changed (profiles/launches_2d256_mixed.md gives the command).
+MEASURED_TRAFFIC = {
+    "spmv_residual_df": {"bytes": 357519104 + 39474432,
+                         "source": "paper_2007_01541_gb300/csrc/solve_kernels.cu",
+                         "sha1": "a76c0fe3b457d5403c6d5b631b946989a6d2f2ae"},
+}
+
+
+def measured_traffic(kernel):
+    import hashlib
+    t = MEASURED_TRAFFIC.get(kernel)
+    if not t:
+        return None
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), t["source"])
+    try:
+        with open(path, "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != t["sha1"]:
+                return None
+    except OSError:
+        return None
+    return t["bytes"]
 
 
 def parse():
@@ -344,7 +370,18 @@ def run_ours(args):
         alu = top["name"].startswith(("schur_", "panel_trsm", "potrf_diag", "fwd_xapply", "fwd_bupdate",
                                       "bwd_reduce", "bwd_xapply", "sbinv_stage")) or (
             top["name"].startswith("spmv_residual") and nr >= 8)
-        if alu:
+        if top["name"] == "spmv_residual_df":
+            # double-float multiply-add: 15 FP32 instructions per (entry, right-hand
+            # side) term (4 for the product, 11 for TwoSum + renormalisation); the
+            # bound is the FP32 lane-operation rate
+            terms = top["flops"] / 2.0
+            peak = SM_COUNT * FP32_LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
+            ach = DF_OPS_PER_TERM * terms / (top["ms"] / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s (FP32 lane operations)",
+                    "frac": ach / peak, "traffic": measured_traffic(top["name"]), "kernel": top["name"],
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+                    "work": "15 FP32 operations per stored entry of A and right-hand side"}
+        elif alu:
             fp64 = top["name"].endswith("_fp64")
             per_clk = FP64_FLOPS_PER_SM_CLK if fp64 else 2 * FP32_LANES_PER_SM
             peak = SM_COUNT * per_clk * MAX_SM_MHZ * 1e6 / 1e12
