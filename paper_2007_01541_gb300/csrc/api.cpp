@@ -326,7 +326,8 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
             const int s = S.level_nodes[i];
             const double m = S.m(s);
             const int mp = front_order(S, s);
-            for (int q = 0; q < mp; ++q) p.items.push_back({s, q, 0, 0});
+            // 8 columns per CTA, never two fronts in one CTA (padding items: q = -1)
+            for (int q = 0; q < (mp + 7) / 8 * 8; ++q) p.items.push_back({s, q < mp ? q : -1, 0, 0});
             el += m * (m + 1) / 2;  // every lower front entry written once
             for (int c = S.child_ptr[s]; c < S.child_ptr[s + 1]; ++c) {
                 const double u = S.m(S.children[c]) - S.k(S.children[c]);

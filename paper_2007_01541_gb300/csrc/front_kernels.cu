@@ -77,51 +77,74 @@ __device__ __forceinline__ Dims dims(const DevSym &d, int s) {
 }
 
 // ---------------------------------------------------------------------------
-// assemble + extend-add, one warp per front column
+// assemble + extend-add: a CTA = 8 consecutive columns of one front (one warp
+// each; the plan pads every front's column list to a multiple of 8, padding
+// items have q < 0).  Rows go in slices of 128: the children's relative maps
+// of the slice are staged in shared memory once for the 8 columns, so a front
+// entry costs one independent global load per child.
 // ---------------------------------------------------------------------------
+constexpr int INIT_ROWS = 128;
+constexpr int INIT_MAXCH = 16;   // children staged at once (more are taken in groups)
+
 template <class T>
 __global__ void __launch_bounds__(THREADS) front_init_kernel(DevSym d, T *__restrict__ front,
                                                              const int4 *__restrict__ items,
                                                              int count) {
-    const int w = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (w >= count) return;
-    const int4 it = items[w];
-    const int s = it.x, q = it.y;
+    __shared__ int32_t smap[INIT_MAXCH][INIT_ROWS];
+    __shared__ int32_t sch[INIT_MAXCH];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = blockIdx.x * (THREADS / 32) + warp;
+    const int4 it = items[min(w, count - 1)];
+    const int s = items[blockIdx.x * (THREADS / 32)].x;   // all 8 items of a CTA share the front
+    const int q = (w < count && it.x == s) ? it.y : -1;
     const Dims z = dims(d, s);
     const int pad = z.kp - z.k;
-    const int qc = q < z.k ? q : (q < z.kp ? -1 : q - pad);  // local column
-    T *F = front + d.foff[s] + (int64_t)q * z.ld;
+    const int qc = q < 0 ? -1 : (q < z.k ? q : (q < z.kp ? -1 : q - pad));   // local column
+    T *F = front + d.foff[s] + (int64_t)max(q, 0) * z.ld;
     const int cb = d.child_ptr[s], ce = d.child_ptr[s + 1];
-    for (int r0 = q; r0 < z.mp; r0 += 128) {
-        T acc[4] = {T(0), T(0), T(0), T(0)};
-        if (qc >= 0) {
-            for (int ci = cb; ci < ce; ++ci) {
-                const int c = d.children[ci];
-                const int32_t *map = d.relmap + d.mapoff[c];
-                const int ic = map[qc];
-                if (ic < 0) continue;
-                const int kpc = d.skp[c], ldc = d.sld[c];
-                const T *U = front + d.foff[c] + (int64_t)(kpc + ic) * ldc + kpc;
+    // first row slice of the CTA: its smallest column
+    const int qmin = items[blockIdx.x * (THREADS / 32)].y;
+    for (int r0 = (qmin / INIT_ROWS) * INIT_ROWS; r0 < z.mp; r0 += INIT_ROWS) {
+        T acc[INIT_ROWS / 32];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int fr = r0 + u * 32 + lane;
-                    const int r = fr < z.k ? fr : (fr < z.kp ? -1 : fr - pad);
-                    if (fr < z.mp && r >= 0) {
-                        const int ir = map[r];
+        for (int u = 0; u < INIT_ROWS / 32; ++u) acc[u] = T(0);
+        for (int g0 = cb; g0 < ce; g0 += INIT_MAXCH) {
+            const int ng = min(INIT_MAXCH, ce - g0);
+            __syncthreads();
+            if (threadIdx.x < ng) sch[threadIdx.x] = d.children[g0 + threadIdx.x];
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < ng * INIT_ROWS; idx += THREADS) {
+                const int gi = idx / INIT_ROWS, rr = idx % INIT_ROWS;
+                const int fr = r0 + rr;
+                const int r = fr < z.k ? fr : (fr < z.kp ? -1 : fr - pad);
+                smap[gi][rr] = (fr < z.mp && r >= 0) ? d.relmap[d.mapoff[sch[gi]] + r] : -1;
+            }
+            __syncthreads();
+            if (qc >= 0) {
+                for (int gi = 0; gi < ng; ++gi) {
+                    const int c = sch[gi];
+                    const int ic = d.relmap[d.mapoff[c] + qc];
+                    if (ic < 0) continue;
+                    const int kpc = d.skp[c], ldc = d.sld[c];
+                    const T *U = front + d.foff[c] + (int64_t)(kpc + ic) * ldc + kpc;
+#pragma unroll
+                    for (int u = 0; u < INIT_ROWS / 32; ++u) {
+                        const int ir = smap[gi][u * 32 + lane];
                         if (ir >= 0) acc[u] += U[ir];
                     }
                 }
             }
         }
+        if (q >= 0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int fr = r0 + u * 32 + lane;
-            if (fr < z.mp) F[fr] = acc[u];
+            for (int u = 0; u < INIT_ROWS / 32; ++u) {
+                const int fr = r0 + u * 32 + lane;
+                if (fr >= q && fr < z.mp) F[fr] = acc[u];
+            }
         }
     }
     __syncwarp();
-    if (q < z.k) {
+    if (q >= 0 && q < z.k) {
         const int64_t j = d.sfirst[s] + q;
         const int64_t e0 = d.csr_diag[j], e1 = d.csr_ptr[j + 1], l0 = d.pcp[j];
         for (int64_t e = e0 + lane; e < e1; e += 32) F[d.alrow[l0 + (e - e0)]] += (T)d.csr_val[e];
