@@ -367,7 +367,7 @@ def run_ours(args):
     if top:
         # the residual product with many right-hand sides does ~10 flops per byte of
         # A in FP64, above GB300's FP64 ridge point: bounded by the FP64 pipe
-        alu = top["name"].startswith(("schur_", "panel_trsm", "potrf_diag", "fwd_xapply", "fwd_bupdate",
+        alu = top["name"].startswith(("schur_", "potrf_panel", "fwd_xapply", "fwd_bupdate",
                                       "bwd_reduce", "bwd_xapply", "sbinv_stage")) or (
             top["name"].startswith("spmv_residual") and nr >= 8)
         if top["name"] == "spmv_residual_df":

@@ -24,7 +24,7 @@ namespace {
 constexpr int ROWS_PER_CTA = 256;  // one thread per front row (gather / apply_L)
 
 enum LaunchKind {
-    K_INIT, K_POTRF, K_PANEL, K_UPDATE, K_SYRK, K_UPDATE_TC, K_SYRK_TC,  // factor
+    K_INIT, K_PANEL, K_UPDATE, K_SYRK, K_UPDATE_TC, K_SYRK_TC, K_DIAG_COPY,  // factor
     K_SBINV_DIAG, K_SBINV_STAGE, K_SBINV_T,                    // super-block inverses
     K_FWD_GATHER, K_FWD_XAPPLY, K_FWD_BUPDATE,                 // forward solve
     K_BWD_REDUCE, K_BWD_FINISH, K_BWD_XAPPLY,                  // backward solve
@@ -42,8 +42,8 @@ struct Launch {
 };
 
 const char *kind_name(int k) {
-    static const char *names[] = {"front_init", "potrf_diag", "panel_trsm", "schur_update",
-                                  "schur_syrk", "tc_schur_update", "tc_schur_syrk", "sbinv_diag",
+    static const char *names[] = {"front_init", "potrf_panel", "schur_update", "schur_syrk",
+                                  "tc_schur_update", "tc_schur_syrk", "diag_copy", "sbinv_diag",
                                   "sbinv_stage", "sbinv_transpose", "fwd_gather", "fwd_xapply",
                                   "fwd_bupdate", "bwd_reduce", "bwd_finish", "bwd_xapply",
                                   "apply_L"};
@@ -115,6 +115,7 @@ struct wd_ctx {
     void *d_front = nullptr;
     size_t front_elems = 0;
     void *d_dinv = nullptr;        // inverses of the NB x NB diagonal blocks
+    void *d_ldiag = nullptr;       // factored NB x NB diagonal blocks (before their copy into the fronts)
     size_t dinv_elems = 0;
     void *d_xs = nullptr, *d_xts = nullptr;  // super-block inverses and their transposes
     int64_t *d_xsoff = nullptr;
@@ -340,17 +341,7 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
         double fl = 0;
         for (int i = b; i < e; ++i) kmax = std::max(kmax, S.k(S.level_nodes[i]));
         for (int kb = 0; kb < kmax; kb += NB) {
-            f0 = p.items.size();
-            fl = el = 0;
-            for (int i = b; i < e; ++i) {
-                const int s = S.level_nodes[i];
-                if (S.k(s) <= kb) continue;
-                p.items.push_back({s, kb, 0, 0});
-                const double nb = std::min(NB, S.k(s) - kb);
-                fl += 2 * nb * nb * nb / 3;
-                el += nb * (nb + 1) + NB * NB;
-            }
-            add_launch(p, K_POTRF, f0, kb, fl, el, 0);
+            // diagonal block factorization (in every CTA) + panel rows
             f0 = p.items.size();
             fl = el = 0;
             for (int i = b; i < e; ++i) {
@@ -360,9 +351,10 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
                 const int t0 = kb + nb;
                 const int mp = front_order(S, s);
                 const int rs = (t0 == k) ? kpad(k) : t0;
-                for (int rb = 0; rb * RB < mp - rs; ++rb) p.items.push_back({s, rb, 0, 0});
-                fl += (double)(m - t0) * nb * nb;
-                el += 2.0 * (m - t0) * nb + (double)NB * NB;
+                const int nrb = std::max(1, (mp - rs + RB - 1) / RB);
+                for (int rb = 0; rb < nrb; ++rb) p.items.push_back({s, rb, 0, 0});
+                fl += (double)(m - t0) * nb * nb + 2.0 * nb * nb * nb / 3;
+                el += 2.0 * (m - t0) * nb + nb * (nb + 1) + 2.0 * NB * NB;
             }
             add_launch(p, K_PANEL, f0, kb, fl, el, 0);
             f0 = p.items.size();
@@ -401,6 +393,16 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
             el += 2.0 * tri + (double)u * k;
         }
         add_launch(p, tc ? K_SYRK_TC : K_SYRK, f0, 0, fl, el, 0);
+    }
+    {
+        const size_t f0 = p.items.size();
+        double el = 0;
+        for (int s = 0; s < S.ns; ++s)
+            for (int kb = 0; kb < S.k(s); kb += NB) {
+                p.items.push_back({s, kb, 0, 0});
+                el += 2.0 * NB * NB;
+            }
+        add_launch(p, K_DIAG_COPY, f0, 0, 0, el, 0);
     }
     // explicit inverses of the super-blocks' diagonal blocks (for the solves)
     constexpr int BPS = wd::SB / NB;  // 64-blocks per super-block
@@ -636,6 +638,7 @@ static wd_status reset_analysis(wd_handle h) {
     h->ws_cols = 0;
     h->d_front = nullptr;
     h->d_dinv = nullptr;
+    h->d_ldiag = nullptr;
     h->d_xs = h->d_xts = nullptr;
     h->d_xsoff = nullptr;
     h->xs_elems = 0;
@@ -1077,6 +1080,7 @@ template <class T>
 static void enqueue_factor_plan(wd_handle h, cudaStream_t st, bool prof) {
     T *F = static_cast<T *>(h->d_front);
     T *Dv = static_cast<T *>(h->d_dinv);
+    T *Ld = static_cast<T *>(h->d_ldiag);
     const DevSym &d = h->dsym;
     const bool fp32 = sizeof(T) == 4;
     const Plan &P = fp32 ? h->fplan_tc : h->fplan;
@@ -1087,8 +1091,10 @@ static void enqueue_factor_plan(wd_handle h, cudaStream_t st, bool prof) {
         if (prof) record_event(h->prof_ev[2 * li], st);
         switch (L.kind) {
             case K_INIT: wd::launch_front_init<T>(d, F, it, L.count, st); break;
-            case K_POTRF: wd::launch_potrf<T>(d, F, Dv, it, L.count, h->d_status, st); break;
-            case K_PANEL: wd::launch_panel<T>(d, F, Dv, pk, it, L.count, L.arg, st); break;
+            case K_PANEL:
+                wd::launch_panel<T>(d, F, Dv, Ld, pk, it, L.count, L.arg, h->d_status, st);
+                break;
+            case K_DIAG_COPY: wd::launch_diag_copy<T>(d, F, Ld, it, L.count, st); break;
             case K_UPDATE: wd::launch_schur<T>(d, F, Dv, it, L.count, L.arg, 0, h->d_status, st); break;
             case K_SYRK: wd::launch_schur<T>(d, F, Dv, it, L.count, 0, 1, h->d_status, st); break;
             case K_UPDATE_TC:
@@ -1171,6 +1177,7 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
     if (!h->d_front) {
         CK(h->mem.alloc(&h->d_front, h->front_elems * sizeof(double)), "front pool alloc");
         CK(h->mem.alloc(&h->d_dinv, h->dinv_elems * sizeof(double)), "inverse blocks alloc");
+        CK(h->mem.alloc(&h->d_ldiag, h->dinv_elems * sizeof(double)), "diagonal blocks alloc");
         CK(h->mem.alloc(&h->d_xs, h->xs_elems * sizeof(double)), "super-block inverse alloc");
         CK(h->mem.alloc(&h->d_xts, h->xs_elems * sizeof(double)), "super-block inverse alloc");
         // padding rows stay zero forever: no kernel writes them

@@ -56,14 +56,17 @@ inline void init_kernel_attributes() {
 // ---- factorization (front_kernels.cu) ------------------------------------
 template <class T>
 void launch_front_init(const DevSym &d, T *front, const int4 *items, int count, cudaStream_t st);
-// diagonal block Cholesky + inverse; item = (front, first pivot column)
-template <class T>
-void launch_potrf(const DevSym &d, T *front, T *dinv, const int4 *items, int count,
-                  status_t *status, cudaStream_t st);
+// pivot block kb: every CTA factors and inverts the NB x NB diagonal block;
+// the rb = 0 CTA stores the factor into ldiag and the inverse into dinv (both
+// at dinvoff + (kb / NB) NB^2); then the CTA's rows below: L21 = F21 Linv^T.
 // pk != nullptr (FP32 only): also write the packed tf32 lines of the new panel
 template <class T>
-void launch_panel(const DevSym &d, T *front, const T *dinv, unsigned char *pk, const int4 *items,
-                  int count, int kb, cudaStream_t st);
+void launch_panel(const DevSym &d, T *front, T *dinv, T *ldiag, unsigned char *pk, const int4 *items,
+                  int count, int kb, status_t *status, cudaStream_t st);
+// the factored diagonal blocks from ldiag into the fronts; item = (s, kb)
+template <class T>
+void launch_diag_copy(const DevSym &d, T *front, const T *ldiag, const int4 *items, int count,
+                      cudaStream_t st);
 // mode 0: pivot-column update of step kb; mode 1: final update matrix (syrk)
 template <class T>
 void launch_schur(const DevSym &d, T *front, T *dinv, const int4 *items, int count, int kb,

@@ -202,9 +202,12 @@ struct WarpChol<T, SB> {
     static __device__ __forceinline__ void step(T (&)[SB], T &, int, int, int64_t, status_t *) {}
 };
 
+// Reads the block from F (ld), leaves the factor in A and its inverse in X
+// (shared memory); if `write`, stores the factor to Lout (ld NB, lower part)
+// and the inverse to Dinv.
 template <class T>
-__device__ void block_potrf_inv(T *F, int ld, int nb, int64_t gcol0, status_t *status, T *Dinv,
-                                T *smem) {
+__device__ void block_potrf_inv(const T *F, int ld, int nb, int64_t gcol0, status_t *status, T *Dinv,
+                                T *Lout, bool write, T *smem) {
     T(*A)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
     T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem + NB * (NB + 1));
     T *invd = smem + 2 * NB * (NB + 1);
@@ -347,42 +350,55 @@ __device__ void block_potrf_inv(T *F, int ld, int nb, int64_t gcol0, status_t *s
         }
         __syncthreads();
     }
-    for (int idx = tid; idx < NB * NB; idx += POTRF_THREADS) {
-        const int r = idx % NB, c = idx / NB;
-        if (r >= c && r < nb) F[(int64_t)c * ld + r] = A[r][c];
-        Dinv[idx] = (r >= c) ? X[r][c] : T(0);
+    if (write) {
+        for (int idx = tid; idx < NB * NB; idx += POTRF_THREADS) {
+            const int r = idx % NB, c = idx / NB;
+            Lout[idx] = (r >= c && r < nb) ? A[r][c] : T(0);
+            Dinv[idx] = (r >= c) ? X[r][c] : T(0);
+        }
     }
     __syncthreads();
 }
 
-// diagonal block starting at pivot column j0 = item.y of front item.x
+// the factored diagonal blocks (kept aside while the panels of a step still
+// read the unfactored block) into the fronts: item = (s, first pivot column)
 template <class T>
-__global__ void __launch_bounds__(POTRF_THREADS) potrf_kernel(DevSym d, T *__restrict__ front,
-                                                   T *__restrict__ dinv,
-                                                   const int4 *__restrict__ items,
-                                                   status_t *status) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+__global__ void __launch_bounds__(THREADS) diag_copy_kernel(DevSym d, T *__restrict__ front,
+                                                            const T *__restrict__ ldiag,
+                                                            const int4 *__restrict__ items) {
     const int4 it = items[blockIdx.x];
     const int s = it.x, j0 = it.y;
     const Dims z = dims(d, s);
-    block_potrf_inv<T>(front + d.foff[s] + (int64_t)j0 * z.ld + j0, z.ld, min(NB, z.k - j0),
-                       d.sfirst[s] + j0, status, dinv + d.dinvoff[s] + (int64_t)(j0 / NB) * NB * NB,
-                       reinterpret_cast<T *>(smem_raw));
+    const int nb = min(NB, z.k - j0);
+    const T *Lb = ldiag + d.dinvoff[s] + (int64_t)(j0 / NB) * NB * NB;
+    T *F = front + d.foff[s] + (int64_t)j0 * z.ld + j0;
+    for (int idx = threadIdx.x; idx < NB * NB; idx += THREADS) {
+        const int r = idx % NB, c = idx / NB;
+        if (r >= c && r < nb) F[(int64_t)c * z.ld + r] = Lb[idx];
+    }
 }
 
 // ---------------------------------------------------------------------------
-// panel: rows [r0, r0+RB) of columns [kb, kb+nb):  X := X Linv^T.  The rows
+// potrf + panel of pivot block kb: every CTA factors the NB x NB diagonal block
+// and inverts the factor itself (the pivot chain is latency-bound: doing it
+// redundantly on many SMs costs nothing and saves a dependent launch per
+// step); CTA rb = 0 stores the factor (aside, in ldiag, since other CTAs of
+// the launch may still be reading the unfactored block) and the inverse.
+// Then rows [r0, r0+RB) of columns [kb, kb+nb):  X := X Linv^T.  The rows
 // start at kb+NB, or at kp when kb is the last block (rows [k, kp) are zero
-// padding).
+// padding); a CTA may have no rows (its launch item only factors the block).
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(THREADS) panel_kernel(DevSym d, T *__restrict__ front,
-                                                        const T *__restrict__ dinv,
+                                                        T *__restrict__ dinv, T *__restrict__ ldiag,
                                                         unsigned char *__restrict__ pk,
-                                                        const int4 *__restrict__ items, int kb) {
+                                                        const int4 *__restrict__ items, int kb,
+                                                        status_t *status) {
+    static_assert(THREADS == POTRF_THREADS, "the panel CTA runs the block factorization");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *Xs = reinterpret_cast<T *>(smem_raw);         // [p][r], ld RB
-    T *Ds = Xs + NB * RB;                            // [p][c] = Linv(c, p), ld NB
+    T *Psm = reinterpret_cast<T *>(smem_raw);        // block factorization: A, X (= Linv), invd
+    T(*Xinv)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(Psm + NB * (NB + 1));
+    T *Xs = Psm + 2 * NB * (NB + 1) + NB;             // [p][r], ld RB
     const int4 it = items[blockIdx.x];
     const int s = it.x, rb = it.y;
     const Dims z = dims(d, s);
@@ -391,11 +407,9 @@ __global__ void __launch_bounds__(THREADS) panel_kernel(DevSym d, T *__restrict_
     const int r0 = (t0 == z.k ? z.kp : t0) + rb * RB;
     T *F = front + d.foff[s];
     stage_tile<T, THREADS>(Xs, RB, F + (int64_t)kb * z.ld + r0, z.ld, RB, NB, z.mp - r0, nb);
-    stage_tile<T, THREADS>(Ds, NB, dinv + d.dinvoff[s] + (int64_t)(kb / NB) * NB * NB, NB, NB, NB,
-                           NB, NB);
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
+    const int64_t boff = d.dinvoff[s] + (int64_t)(kb / NB) * NB * NB;
+    block_potrf_inv<T>(F + (int64_t)kb * z.ld + kb, z.ld, nb, d.sfirst[s] + kb, status, dinv + boff,
+                       ldiag + boff, rb == 0, Psm);
     // out[r][c] = sum_{p <= c} X[r][p] Linv(c, p); thread: row tid % 64, 16 cols
     const int tid = threadIdx.x;
     const int r = tid % RB, cg = tid / RB;
@@ -405,7 +419,7 @@ __global__ void __launch_bounds__(THREADS) panel_kernel(DevSym d, T *__restrict_
     for (int p = 0; p < nb; ++p) {
         const T x = Xs[p * RB + r];
 #pragma unroll
-        for (int u = 0; u < NB / 4; ++u) acc[u] += x * Ds[p * NB + cg + 4 * u];
+        for (int u = 0; u < NB / 4; ++u) acc[u] += x * Xinv[cg + 4 * u][p];
     }
     if (r0 + r < z.mp) {
 #pragma unroll
@@ -528,9 +542,7 @@ __global__ void __launch_bounds__(THREADS) schur_kernel(DevSym d, T *__restrict_
 }
 
 template <class T>
-constexpr size_t potrf_smem() { return sizeof(T) * (2 * NB * (NB + 1) + NB); }
-template <class T>
-constexpr size_t panel_smem() { return sizeof(T) * (NB * RB + NB * NB); }
+constexpr size_t panel_smem() { return sizeof(T) * (2 * NB * (NB + 1) + NB + NB * RB); }
 template <class T>
 constexpr size_t schur_smem() { return 2 * sizeof(T) * BK * (BM + BN); }
 
@@ -538,8 +550,6 @@ template <class T>
 void set_smem_attrs() {
     static bool done = false;  // per instantiation and process
     if (done) return;
-    cudaFuncSetAttribute(potrf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)potrf_smem<T>());
     cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)panel_smem<T>());
     cudaFuncSetAttribute(schur_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -562,19 +572,18 @@ void launch_front_init(const DevSym &d, T *front, const int4 *items, int count, 
 }
 
 template <class T>
-void launch_potrf(const DevSym &d, T *front, T *dinv, const int4 *items, int count,
-                  status_t *status, cudaStream_t st) {
+void launch_panel(const DevSym &d, T *front, T *dinv, T *ldiag, unsigned char *pk, const int4 *items,
+                  int count, int kb, status_t *status, cudaStream_t st) {
     if (count <= 0) return;
     set_smem_attrs<T>();
-    potrf_kernel<T><<<count, POTRF_THREADS, potrf_smem<T>(), st>>>(d, front, dinv, items, status);
+    panel_kernel<T><<<count, THREADS, panel_smem<T>(), st>>>(d, front, dinv, ldiag, pk, items, kb, status);
 }
 
 template <class T>
-void launch_panel(const DevSym &d, T *front, const T *dinv, unsigned char *pk, const int4 *items,
-                  int count, int kb, cudaStream_t st) {
+void launch_diag_copy(const DevSym &d, T *front, const T *ldiag, const int4 *items, int count,
+                      cudaStream_t st) {
     if (count <= 0) return;
-    set_smem_attrs<T>();
-    panel_kernel<T><<<count, THREADS, panel_smem<T>(), st>>>(d, front, dinv, pk, items, kb);
+    diag_copy_kernel<T><<<count, THREADS, 0, st>>>(d, front, ldiag, items);
 }
 
 template <class T>
@@ -587,10 +596,10 @@ void launch_schur(const DevSym &d, T *front, T *dinv, const int4 *items, int cou
 
 #define WD_INST(T)                                                                               \
     template void launch_front_init<T>(const DevSym &, T *, const int4 *, int, cudaStream_t);    \
-    template void launch_potrf<T>(const DevSym &, T *, T *, const int4 *, int, status_t *,       \
-                                  cudaStream_t);                                                 \
-    template void launch_panel<T>(const DevSym &, T *, const T *, unsigned char *, const int4 *, \
-                                  int, int, cudaStream_t);                                       \
+    template void launch_panel<T>(const DevSym &, T *, T *, T *, unsigned char *, const int4 *, int,  \
+                                  int, status_t *, cudaStream_t);                                \
+    template void launch_diag_copy<T>(const DevSym &, T *, const T *, const int4 *, int,         \
+                                      cudaStream_t);                                       \
     template void launch_schur<T>(const DevSym &, T *, T *, const int4 *, int, int, int,         \
                                   status_t *, cudaStream_t);
 WD_INST(double)
