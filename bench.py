@@ -72,9 +72,11 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["2d", "2d_small", "1d"], default="2d",
+    p.add_argument("--workload", choices=["2d", "2d_small", "1d", "batch"], default="2d",
                    help="2d: 256x256 cells (N=65,536, the benchmark); 2d_small: 128x128 "
-                        "(N=16,384, for profiler captures); 1d: 1024 cells")
+                        "(N=16,384, for profiler captures); 1d: 1024 cells; batch: the 256 "
+                        "independent 1D/2D instances (N 1024..16384), sharded over the ranks")
+    p.add_argument("--batch-count", type=int, default=256)
     p.add_argument("--nrhs", type=int, default=None)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -206,9 +208,14 @@ def load_peaks():
 
 # ---------------------------------------------------------------------------
 def make_workload(kind: str, nrhs: int | None, device: str):
-    from wdgen import Kernel, compressed_pattern, compressed_values, haar_basis, rhs
+    from wdgen import Kernel, batch_instances, compressed_pattern, compressed_values, haar_basis, rhs
 
-    if kind == "2d":
+    if kind == "batch":
+        # the oracle's sample of the batch: its smallest instance
+        p = min(batch_instances(256, 0), key=lambda q: q["N"])
+        dim, J, ker, nug, nr = p["dim"], p["J"], Kernel("exponential", p["ell"]), p["nugget"], 1
+        name = f"batch_instance_{dim}d_J{J}_exp_l{p['ell']:.3f}"
+    elif kind == "2d":
         dim, J, ker, nug, nr = 2, 8, Kernel("matern32", 0.1), 1e-3, 64
         name = "2d_haar_256x256_matern32_l0.1_nugget1e-3"
     elif kind == "2d_small":
@@ -462,6 +469,147 @@ def run_ours(args):
     dist.close()
 
 
+def run_batch(args):
+    """Independent instances, one right-hand side each, mixed precision with
+    refinement.  Ranks take their longest-processing-time shares of the
+    instances (no data-path collective); value = all instances' factor + solve
+    flops over the slowest rank's time (the total work is fixed: strong scaling)."""
+    import numpy as np
+    import torch
+
+    import paper_2007_01541_gb300 as wd
+    from paper_2007_01541_gb300 import build as wdbuild
+    from paper_2007_01541_gb300.shard import instance_costs, lpt_partition
+    from wdgen import batch_instances, batch_workload, compressed_pattern, haar_basis
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = Dist("nccl")
+    wdbuild.build()
+    params = batch_instances(args.batch_count, 0)
+    cache = {}
+    pats, bases = [], []
+    for p in params:
+        key = (p["dim"], p["J"])
+        if key not in cache:
+            b = haar_basis(*key)
+            cache[key] = (b, compressed_pattern(b))
+        bases.append(cache[key][0])
+        pats.append(cache[key][1])
+    costs = instance_costs(pats, bases)
+    idx = lpt_partition(costs, ws)[rank]
+    w = batch_workload(params=[params[i] for i in idx], nrhs=1, seed=rank, device="cuda")
+    s = wd.Solver().analyze_batch(w.patterns, w.bases)
+    sp = None if args.no_replay else wd.Solver(profile=True).analyze_batch(w.patterns, w.bases)
+    info = s.info()
+    flops_step = info["flops_factor"] + 4.0 * info["nnz_L"]
+    vals = torch.tensor(np.concatenate(w.values), device="cuda")
+    B0 = torch.tensor(np.ascontiguousarray(w.B.T), device="cuda")
+    Bw = torch.empty_like(B0)
+    stream = torch.cuda.current_stream()
+
+    def step(sv):
+        sv.factor(vals, "mixed")
+        Bw.copy_(B0)
+        sv.solve(Bw.T)
+        sv.logdet_batch()
+
+    def timed(sv, K, W):
+        for _ in range(W):
+            step(sv)
+        sv.kernel_stats(reset=True)
+        sv.launch_count(reset=True)
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            step(sv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        return dist.max(e0.elapsed_time(e1) / K), sv.kernel_stats(reset=True), sv.launch_count(reset=True)
+
+    clocks = ClockSampler(gpu_id_for_smi())
+    clocks.start()
+    ms, _, launches = timed(s, args.steps, args.warmup)
+    clk = clocks.stop()
+    be = s.last_solve["backward_error"]
+    kstats = [] if args.no_replay else timed(sp, args.steps, 1)[1]
+    total = dist.sum(flops_step)
+    value = total / (ms / 1e3) / 1e12
+    roof = None
+    top = max(kstats, key=lambda k: k["ms"]) if kstats else None
+    if top:
+        if top["name"].startswith(("spmv_residual", "permute", "transpose", "colmax", "fwd_gather")):
+            peaks = load_peaks()
+            peak = peaks.get("hbm_gbs", 6800.0)
+            ach = top["bytes"] / (top["ms"] / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                    "traffic": None, "kernel": top["name"],
+                    "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+        else:
+            fp64 = top["name"].endswith("_fp64")
+            per_clk = FP64_FLOPS_PER_SM_CLK if fp64 else 2 * FP32_LANES_PER_SM
+            peak = SM_COUNT * per_clk * MAX_SM_MHZ * 1e6 / 1e12
+            ach = top["flops"] / (top["ms"] / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": None, "kernel": top["name"], "peak_source": "derived from unit counts and clock"}
+        roof["launches_per_step"] = top["launches"] / args.steps
+    e2e = None
+    if not args.no_e2e:
+        vh = torch.tensor(np.concatenate(w.values)).pin_memory()
+        Bh0 = torch.tensor(np.ascontiguousarray(w.B.T)).pin_memory()
+        Bh = torch.empty_like(Bh0).pin_memory()
+
+        def step_host():
+            s.factor(vh, "mixed")
+            Bh.copy_(Bh0)
+            s.solve(Bh.T)
+            s.logdet_batch()
+
+        for _ in range(2):
+            step_host()
+        dist.barrier()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        torch.cuda.synchronize()
+        dt = dist.max((time.perf_counter() - t) / args.steps)
+        n_loc = int(w.B.shape[0])
+        e2e = {"value": total / dt / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": 8 * int(vals.numel()) + 8 * n_loc,
+               "d2h_bytes_per_step": 8 * n_loc + 8 * len(idx), "ms_per_step": dt * 1e3}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        i0 = int(np.argmin(costs))
+        cp, ri = pats[i0]
+        from wdgen import Kernel, compressed_values
+        v0 = compressed_values(bases[i0], cp, ri, Kernel("exponential", params[i0]["ell"]), 1e-2)
+        o = oracle.Oracle(cp, ri, bases[i0])
+        t = time.perf_counter()
+        rc = o.factor(v0)
+        dt = time.perf_counter() - t
+        cpu = {"value": costs[i0] / dt / 1e12 if rc == 0 else None, "unit": "TFLOP/s", "cores": 1,
+               "kind": "oracle", "sample": f"left-looking FP64 factor of instance {i0} (N = {cp.size - 1}, "
+                                            f"{costs[i0]:.3e} flop) in {dt:.2f} s; solve not sampled"}
+    if rank == 0:
+        line = {"metric": "factor+solve TFLOP/s of the batch (mixed+IR path) at backward error <= 1e-12",
+                "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": f"batch_{args.batch_count}_instances_1d2d_exp_nugget1e-2_1rhs",
+                           "instances": args.batch_count, "N_total": int(sum(p["N"] for p in params)),
+                           "parallelism": f"lpt-shards x{ws}" if ws > 1 else "single",
+                           "l2": "inputs larger than L2"},
+                "backward_error": be, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk, "top_kernels": _top(kstats, 8)}
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
 def _top(kstats, n):
     out = []
     for k in sorted(kstats, key=lambda k: -k["ms"])[:n]:
@@ -475,6 +623,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -1,0 +1,97 @@
+"""Sharding independent instances over ranks (CPU; world size 2 over gloo).
+
+The partition rule is pinned against brute force on small sets (the greedy
+longest-processing-time load never exceeds 4/3 of the optimum) and by its
+invariants; the two-rank run checks that every instance is handled by
+exactly one rank and that each rank's block-diagonal analysis of its share
+reproduces the single-process analyses of those instances.
+"""
+import itertools
+import os
+import socket
+
+import numpy as np
+
+from wdgen import batch_instances, compressed_pattern, haar_basis
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def test_lpt_partition_invariants_and_bound(wdlib):
+    from paper_2007_01541_gb300.shard import lpt_partition
+    rng = np.random.default_rng(1)
+    for _ in range(30):
+        n = int(rng.integers(1, 9))
+        nr = int(rng.integers(1, 4))
+        costs = rng.integers(1, 50, n).astype(float)
+        shares = lpt_partition(costs, nr)
+        assert sorted(i for sh in shares for i in sh) == list(range(n))
+        assert shares == lpt_partition(costs, nr)            # deterministic
+        loads = [costs[sh].sum() if sh else 0.0 for sh in shares]
+        best = min(max(sum(costs[i] for i in range(n) if a[i] == r) for r in range(nr))
+                   for a in itertools.product(range(nr), repeat=n))
+        assert max(loads) <= 4.0 / 3.0 * best + 1e-9
+    # 7 -> rank 0, 5 -> rank 1, 3 -> rank 1 (5 < 7), 2 -> rank 0 (7 < 8)
+    assert lpt_partition([7, 5, 3, 2], 2) == [[0, 3], [1, 2]]
+
+
+def _worker(rank, ws, port, outq):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws))
+    import torch
+    import torch.distributed as dist
+
+    import paper_2007_01541_gb300 as wd
+    from paper_2007_01541_gb300.shard import local_share
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    params = batch_instances(12, 3)
+    cache = {}
+    pats, bases = [], []
+    for p in params:
+        key = (p["dim"], min(p["J"], 9 if p["dim"] == 1 else 4))   # small sizes for a CPU test
+        if key not in cache:
+            b = haar_basis(*key)
+            cache[key] = (b, compressed_pattern(b))
+        bases.append(cache[key][0])
+        pats.append(cache[key][1])
+    idx, lp, lb = local_share(pats, bases, rank, ws)
+    ok = True
+    if idx:
+        sym = wd.Solver(symbolic_only=True).analyze_batch(lp, lb).symbolic()
+        off = 0
+        for i, (cp, ri) in zip(idx, lp):
+            one = wd.Solver(symbolic_only=True).analyze(cp, ri, bases[i]).symbolic()
+            n = cp.size - 1
+            ok &= bool(np.array_equal(sym["perm"][off:off + n] - off, one["perm"]))
+            off += n
+    mine = torch.zeros(len(params), dtype=torch.int64)
+    mine[idx] = 1
+    dist.all_reduce(mine)
+    flag = torch.tensor([1 if ok else 0])
+    dist.all_reduce(flag, op=dist.ReduceOp.MIN)
+    if rank == 0:
+        outq.put((mine.tolist(), int(flag.item())))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_share_the_batch(wdlib):
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+    assert all(p.exitcode == 0 for p in procs)
+    counts, ok = q.get(timeout=10)
+    assert counts == [1] * 12          # every instance on exactly one rank
+    assert ok == 1
