@@ -169,6 +169,7 @@ struct wd_ctx {
     int64_t *d_batch_coff = nullptr;
     double *d_batch_norm = nullptr;   // per-instance ||A_i||_inf
     double *d_batch_ld = nullptr;     // per-instance log det
+    double *d_batch_sdl = nullptr;    // per-supernode log det terms
     double *d_batch_cm = nullptr;     // per-instance column maxima (solve workspace)
     std::vector<double> batch_normA;
     std::vector<int64_t> h_foff;   // host copies of the front layout
@@ -660,6 +661,7 @@ static wd_status reset_analysis(wd_handle h) {
     h->d_batch_coff = nullptr;
     h->d_batch_norm = nullptr;
     h->d_batch_ld = nullptr;
+    h->d_batch_sdl = nullptr;
     h->d_batch_cm = nullptr;
     h->batch_normA.clear();
     return WD_OK;
@@ -939,6 +941,7 @@ static wd_status finish_analysis(wd_handle h, std::chrono::steady_clock::time_po
         h->d_batch_soff = const_cast<int32_t *>(ps);
         CK(h->mem.alloc((void **)&h->d_batch_norm, h->batch_count * sizeof(double)), "batch alloc");
         CK(h->mem.alloc((void **)&h->d_batch_ld, h->batch_count * sizeof(double)), "batch alloc");
+        CK(h->mem.alloc((void **)&h->d_batch_sdl, std::max(ns, 1) * sizeof(double)), "batch alloc");
     }
     fill_info(h, nnzl, maxm, maxk, t0);
     h->analyzed = true;
@@ -1209,7 +1212,8 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
                              h->d_norm_part, h->d_scalars, st);
     h->launches += h->n_spmv_fin > 0 ? 2 : 1;
     if (h->batch_count > 0) {
-        wd::launch_seg_norm_inf(h->dsym, h->d_batch_coff, h->batch_count, h->d_batch_norm, st);
+        wd::launch_seg_norm_inf(h->dsym, h->d_spmv_chunks, h->n_spmv_chunks, h->d_spmv_fin, h->n_spmv_fin,
+                                h->d_norm_part, h->d_batch_coff, h->batch_count, h->d_batch_norm, st);
         h->launches += 1;
         h->batch_normA.resize(h->batch_count);
         CK(cudaMemcpyAsync(h->batch_normA.data(), h->d_batch_norm, h->batch_count * sizeof(double),
@@ -1535,11 +1539,11 @@ extern "C" wd_status wd_logdet_batch(wd_handle h, double *out) {
     double *dst = h->d_batch_ld;
     if (h->prec == WD_FP64)
         wd::launch_seg_logdet<double>(h->dsym, static_cast<const double *>(h->d_front), h->d_batch_soff,
-                                      h->batch_count, dst, 0);
+                                      h->batch_count, h->d_batch_sdl, dst, 0);
     else
         wd::launch_seg_logdet<float>(h->dsym, static_cast<const float *>(h->d_front), h->d_batch_soff,
-                                     h->batch_count, dst, 0);
-    h->launches += 1;
+                                     h->batch_count, h->d_batch_sdl, dst, 0);
+    h->launches += 2;
     CK(cudaGetLastError(), "logdet launch");
     CK(cudaMemcpy(out, dst, h->batch_count * sizeof(double), cudaMemcpyDeviceToHost), "logdet D2H");
     return WD_OK;

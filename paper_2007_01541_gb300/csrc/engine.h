@@ -208,12 +208,16 @@ void launch_breduce_finish(const DevSym &d, const T *Y, T *Tt, const T *P, const
                            int large, int nrhs, cudaStream_t st);
 
 // ---- per-instance reductions of a block-diagonal batch (batch.cu) ----------
-void launch_seg_norm_inf(const DevSym &d, const int64_t *coff, int count, double *out, cudaStream_t st);
+// out[i] = ||A_i||_inf from the residual product's chunk items (partial:
+// scratch of one double per slot)
+void launch_seg_norm_inf(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin, int nfin,
+                         double *partial, const int64_t *coff, int count, double *out, cudaStream_t st);
 void launch_seg_colmax3(const double *R, const double *X, const double *B, const int64_t *coff, int count,
                         int nrhs, double *out, cudaStream_t st);
+// out[i] = log det A_i (sdl: scratch of one double per supernode)
 template <class T>
-void launch_seg_logdet(const DevSym &d, const T *front, const int32_t *soff, int count, double *out,
-                       cudaStream_t st);
+void launch_seg_logdet(const DevSym &d, const T *front, const int32_t *soff, int count, double *sdl,
+                       double *out, cudaStream_t st);
 
 // ---- allocation-free export of the factor (noalloc.cu) ---------------------
 // the panel offsets sit in a static device array of NOALLOC_MAX_SUPERNODES + 1
