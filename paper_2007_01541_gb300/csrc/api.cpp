@@ -170,6 +170,7 @@ struct wd_ctx {
     double *d_batch_norm = nullptr;   // per-instance ||A_i||_inf
     double *d_batch_ld = nullptr;     // per-instance log det
     double *d_batch_sdl = nullptr;    // per-supernode log det terms
+    unsigned long long *d_spmv_bad = nullptr;   // residual: first bad column index position
     double *d_batch_cm = nullptr;     // per-instance column maxima (solve workspace)
     std::vector<double> batch_normA;
     std::vector<int64_t> h_foff;   // host copies of the front layout
@@ -662,6 +663,7 @@ static wd_status reset_analysis(wd_handle h) {
     h->d_batch_norm = nullptr;
     h->d_batch_ld = nullptr;
     h->d_batch_sdl = nullptr;
+    h->d_spmv_bad = nullptr;
     h->d_batch_cm = nullptr;
     h->batch_normA.clear();
     return WD_OK;
@@ -921,6 +923,7 @@ static wd_status finish_analysis(wd_handle h, std::chrono::steady_clock::time_po
         if (!fin.empty())
             CK(cudaMemcpy(h->d_spmv_fin, fin.data(), fin.size() * sizeof(int4), cudaMemcpyHostToDevice), "upload");
         CK(h->mem.alloc((void **)&h->d_norm_part, std::max(slots, 1) * sizeof(double)), "norm partials");
+        CK(h->mem.alloc((void **)&h->d_spmv_bad, sizeof(unsigned long long)), "spmv check");
     }
     d.csr_val = h->d_csr_val;
     CK(h->mem.alloc((void **)&h->d_status, sizeof(status_t)), "status alloc");
@@ -1326,6 +1329,7 @@ static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cud
                                  double *be_max) {
     const int64_t n = h->S.n;
     const double nf = (double)h->nnz_full;
+    unsigned long long bad = ~0ULL;
     if (nrhs > 8) {
         // many right-hand sides: double-float arithmetic on the FP32 pipes
         prof_single(h, "spmv_residual_df", 0, 0, st, true);
@@ -1333,12 +1337,14 @@ static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cud
                                     h->n_spmv_fin, h->d_csr_vh, h->d_csr_vl, X, h->d_Xh, h->d_Xl, h->d_Bp,
                                     h->d_R, h->d_P, nrhs, st);
         prof_single(h, "spmv_residual_df", 2.0 * nf * nrhs, 12.0 * nf + 24.0 * n * nrhs, st, false);
-        h->launches += 1;
+        h->launches += h->n_spmv_fin > 0 ? 3 : 2;
     } else {
+        CK(cudaMemsetAsync(h->d_spmv_bad, 0xff, sizeof(unsigned long long), st), "spmv check");
         prof_single(h, "spmv_residual_fp64", 0, 0, st, true);
         wd::launch_spmv_residual(h->dsym, h->d_spmv_chunks, h->n_spmv_chunks, h->d_spmv_fin,
-                                 h->n_spmv_fin, X, h->d_Bp, h->d_R, h->d_P, nrhs, st);
+                                 h->n_spmv_fin, X, h->d_Bp, h->d_R, h->d_P, nrhs, h->d_spmv_bad, st);
         prof_single(h, "spmv_residual_fp64", 2.0 * nf * nrhs, 12.0 * nf + 24.0 * n * nrhs, st, false);
+        h->launches += h->n_spmv_fin > 0 ? 2 : 1;
     }
     if (h->batch_count > 0) {
         // per instance and column: each instance is its own system
@@ -1346,9 +1352,13 @@ static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cud
         wd::launch_seg_colmax3(h->d_R, X, h->d_Bp, h->d_batch_coff, cnt, (int)nrhs, h->d_batch_cm, st);
         h->launches += 2;
         std::vector<double> cm(3 * (size_t)cnt * nrhs);
+        if (nrhs <= 8)
+            CK(cudaMemcpyAsync(&bad, h->d_spmv_bad, sizeof(bad), cudaMemcpyDeviceToHost, st), "spmv check");
         CK(cudaMemcpyAsync(cm.data(), h->d_batch_cm, cm.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
            "be D2H");
         CK(cudaStreamSynchronize(st), "backward error");
+        if (bad != ~0ULL)
+            return fail(h, WD_ERR_CUDA, "residual: column index out of range at CSR position " + std::to_string(bad));
         double mx = 0.0;
         for (int i = 0; i < cnt; ++i)
             for (int64_t c = 0; c < nrhs; ++c) {
@@ -1362,8 +1372,12 @@ static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cud
     wd::launch_colmax3(h->d_R, X, h->d_Bp, n, nrhs, h->d_cm, st);
     h->launches += 2;
     std::vector<double> cm(3 * nrhs);
+    if (nrhs <= 8)
+        CK(cudaMemcpyAsync(&bad, h->d_spmv_bad, sizeof(bad), cudaMemcpyDeviceToHost, st), "spmv check");
     CK(cudaMemcpyAsync(cm.data(), h->d_cm, cm.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "be D2H");
     CK(cudaStreamSynchronize(st), "backward error");
+    if (bad != ~0ULL)
+        return fail(h, WD_ERR_CUDA, "residual: column index out of range at CSR position " + std::to_string(bad));
     double mx = 0.0;
     for (int64_t c = 0; c < nrhs; ++c) {
         const double den = h->normA * cm[3 * c + 1] + cm[3 * c + 2];

@@ -118,11 +118,13 @@ void launch_permute_out_rm(const double *X, double *B, int64_t ldb, const int32_
 template <class Tc>
 void launch_transpose(Tc *C, double *Rm, int64_t n, int64_t nrhs, int dir, int accumulate,
                       cudaStream_t st);
-// chunks: (row, first entry, end, slot or -1); fin: (row, first slot, slots)
+// chunks: (row, first entry, end, slot or -1); fin: (row, first slot, slots);
+// bad: smallest CSR position whose column index is outside [0, n) (atomic
+// minimum; the caller sets it to UINT64_MAX first; used for nrhs <= 8)
 constexpr int SPMV_CHUNK = 512;
 void launch_spmv_residual(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin,
                           int nfin, const double *X, const double *Bp, double *R, double *P,
-                          int64_t nrhs, cudaStream_t st);
+                          int64_t nrhs, unsigned long long *bad, cudaStream_t st);
 // the same residual in double-float arithmetic (vh + vl = the CSR values;
 // Xh, Xl: n x nrhs scratch for the split of X)
 void launch_spmv_residual_df(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin, int nfin,

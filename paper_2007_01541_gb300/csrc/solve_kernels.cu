@@ -310,30 +310,61 @@ __global__ void __launch_bounds__(THREADS, 4) spmv_df_kernel(DevSym d, const int
     }
 }
 
-// Few right-hand sides (<= 8): lanes over the entries of the chunk.
+// Few right-hand sides (<= 8): lanes over the entries of the chunk, NR (the
+// number of right-hand sides rounded up to 1, 2, 4 or 8) accumulators per
+// lane and U = 4 entries per lane in flight (their values, columns and x loads
+// are all issued before the first product), which hides the dependent
+// column -> x latency that one entry at a time leaves exposed.  Each lane adds
+// its entries in the same order as one entry per step would.  Every address
+// formed is in range: lanes past the end of the chunk re-read the lane's
+// first entry with weight 0, accumulators past nrhs read right-hand side 0
+// (never written out), and a column index outside [0, n) is skipped and its
+// CSR position recorded in *bad (atomic minimum; the host clears and reads it).
+template <int NR>
 __global__ void __launch_bounds__(THREADS) spmv_narrow_kernel(DevSym d, const int4 *__restrict__ items,
                                                               int count, const double *__restrict__ X,
                                                               const double *__restrict__ Bp,
                                                               double *__restrict__ R,
-                                                              double *__restrict__ P, int nrhs) {
+                                                              double *__restrict__ P, int nrhs,
+                                                              unsigned long long *__restrict__ bad) {
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= count) return;
     const int4 it = items[w];
     const int64_t row = it.x;
     const int slot = it.w;
-    double acc[8];
+    constexpr int U = 4;
+    double acc[NR];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = 0.0;
-    for (int e = it.y + lane; e < it.z; e += 32) {
-        const double v = d.csr_val[e];
-        const double *x = X + (int64_t)d.csr_col[e] * nrhs;
+    for (int c = 0; c < NR; ++c) acc[c] = 0.0;
+    for (int e0 = it.y + lane; e0 < it.z; e0 += 32 * U) {
+        double v[U];
+        int64_t xo[U];
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-            if (c < nrhs) acc[c] += v * x[c];
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + 32 * u;
+            const bool in = e < it.z;
+            const int ec = in ? e : e0;
+            double val = __ldcs(d.csr_val + ec);
+            const int col = __ldcs(d.csr_col + ec);
+            const bool col_ok = (int64_t)(uint32_t)col < d.n;
+            if (!col_ok && in) atomicMin(bad, (unsigned long long)e);
+            if (!in || !col_ok) val = 0.0;
+            v[u] = val;
+            xo[u] = col_ok ? (int64_t)col * nrhs : 0;
+        }
+        double x[U][NR];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < NR; ++c) x[u][c] = X[xo[u] + (c < nrhs ? c : 0)];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < NR; ++c) acc[c] += v[u] * x[u][c];
     }
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < NR; ++c) {
         double a = acc[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -526,10 +557,17 @@ void launch_transpose(Tc *C, double *Rm, int64_t n, int64_t nrhs, int dir, int a
 
 void launch_spmv_residual(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin,
                           int nfin, const double *X, const double *Bp, double *R, double *P,
-                          int64_t nrhs, cudaStream_t st) {
+                          int64_t nrhs, unsigned long long *bad, cudaStream_t st) {
     const int blocks = (int)(((int64_t)nchunks * 32 + THREADS - 1) / THREADS);
-    if (nrhs <= 8)
-        spmv_narrow_kernel<<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, X, Bp, R, P, (int)nrhs);
+    const int nr = (int)nrhs;
+    if (nrhs == 1)
+        spmv_narrow_kernel<1><<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, X, Bp, R, P, nr, bad);
+    else if (nrhs == 2)
+        spmv_narrow_kernel<2><<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, X, Bp, R, P, nr, bad);
+    else if (nrhs <= 4)
+        spmv_narrow_kernel<4><<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, X, Bp, R, P, nr, bad);
+    else if (nrhs <= 8)
+        spmv_narrow_kernel<8><<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, X, Bp, R, P, nr, bad);
     else
         spmv_wide_kernel<<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, X, Bp, R, P, (int)nrhs);
     if (nfin > 0) spmv_finish_kernel<<<nfin, 64, 0, st>>>(fin, nfin, Bp, R, P, (int)nrhs);
