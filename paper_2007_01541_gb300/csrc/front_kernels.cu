@@ -56,6 +56,24 @@ __device__ __forceinline__ void pivot_root(float d, float &s, float &is) {
     s = d * is;
 }
 
+// four consecutive shared-memory elements (16-byte aligned for float,
+// two 16-byte halves for double)
+__device__ __forceinline__ void load4(float (&v)[4], const float *p) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+}
+__device__ __forceinline__ void load4(double (&v)[4], const double *p) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+__device__ __forceinline__ void store4(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double *p, const double (&v)[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+
 // x = hi + lo, hi = x rounded to tf32 (cvt.rna), lo = (x - hi) rounded to tf32
 __device__ __forceinline__ void split_tf32_bits(float x, uint32_t &hi, uint32_t &lo) {
     asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(hi) : "f"(x));
@@ -159,10 +177,12 @@ __global__ void __launch_bounds__(THREADS) front_init_kernel(DevSym d, T *__rest
 //   1. one warp factors the 16 x 16 diagonal sub-block, one row per lane in
 //      registers (shuffles, no block barrier);
 //   2. the rows below are solved against it, one row per thread;
-//   3. the trailing lower part is updated with register tiles of 4 x 4.
-// The inverse: the four 16 x 16 diagonal inverses (one warp each, one column
-// per lane), then X(bi, bj) = -X(bi, bi) sum_k L(bi, k) X(k, bj) for
-// bi = 1, 2, 3.  A pivot that is not positive records its global column in
+//   3. the trailing lower part is updated with register tiles of 2 x 4.
+// The inverse, by 16 x 16 blocks X(i, j) of Linv: the diagonal inverses
+// X(i, i) (one warp each, one column per lane); then W(i, k) = X(i, i) L(i, k)
+// for all i > k at once; then one barrier step per block row i = 1, 2, 3:
+// X(i, j) = -sum_{k=j}^{i-1} W(i, k) X(k, j), which only reads block rows
+// finished before.  A pivot that is not positive records its global column in
 // *status (smallest wins) and is replaced by 1 so that the arithmetic stays
 // finite.  Must be called by a block of POTRF_THREADS threads.
 // ---------------------------------------------------------------------------
@@ -202,24 +222,41 @@ struct WarpChol<T, SB> {
     static __device__ __forceinline__ void step(T (&)[SB], T &, int, int, int64_t, status_t *) {}
 };
 
-// Reads the block from F (ld), leaves the factor in A and its inverse in X
-// (shared memory); if `write`, stores the factor to Lout (ld NB, lower part)
-// and the inverse to Dinv.
+// Shared memory of the block factorization (element offsets): the factor
+// A[NB][NB + 1]; the inverse stored transposed, XT[c * XLD + r] = Linv(r, c),
+// with 16-byte aligned rows (XLD = NB + 4) so that four consecutive entries
+// are one vector load; the reciprocal pivots.  The strictly lower 16 x 16
+// blocks of XT (Linv's zero upper part) hold the products W(i, k).
+constexpr int XLD = NB + 4;
+constexpr int BP_XT = NB * (NB + 1);
+constexpr int BP_INVD = BP_XT + NB * XLD;
+constexpr int BP_ELEMS = BP_INVD + NB;
+
+// Issues, without committing, the cp.async copies of the lower part of the
+// nb x nb block at F (column-major, ld) into A (zero-filled outside it), and
+// zeroes XT.
 template <class T>
-__device__ void block_potrf_inv(const T *F, int ld, int nb, int64_t gcol0, status_t *status, T *Dinv,
-                                T *Lout, bool write, T *smem) {
+__device__ void block_load(const T *F, int ld, int nb, T *smem) {
     T(*A)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
-    T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem + NB * (NB + 1));
-    T *invd = smem + 2 * NB * (NB + 1);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int idx = tid; idx < NB * NB; idx += POTRF_THREADS) {
+    T *XT = smem + BP_XT;
+    for (int idx = threadIdx.x; idx < NB * NB; idx += POTRF_THREADS) {
         const int r = idx % NB, c = idx / NB;
         cp_async_elem(&A[r][c], F + (int64_t)c * ld + r, r >= c && r < nb && c < nb);
-        X[r][c] = T(0);
+        XT[c * XLD + r] = T(0);
     }
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
+}
+
+// Factors the block that block_load brought in (the caller has waited for
+// the copies and synchronised), leaving L in A and Linv in XT; if `write`,
+// stores L to Lout (ld NB, lower part) and Linv to Dinv.  Ends with XT final
+// and visible to the whole block.
+template <class T>
+__device__ void block_potrf_inv(int nb, int64_t gcol0, status_t *status, T *Dinv, T *Lout, bool write,
+                                T *smem) {
+    T(*A)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
+    T *XT = smem + BP_XT;
+    T *invd = smem + BP_INVD;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 #pragma unroll 1
     for (int jb = 0; jb < nb; jb += SB) {
         const int w = min(SB, nb - jb);
@@ -290,7 +327,7 @@ __device__ void block_potrf_inv(const T *F, int ld, int nb, int64_t gcol0, statu
         }
         __syncthreads();
     }
-    // X = A^-1: diagonal 16 x 16 inverses, one warp each, one column per lane
+    // X(i, i): the diagonal 16 x 16 inverses, one warp each, one column per lane
     const int nsb = (nb + SB - 1) / SB;
     if (warp < nsb && lane < SB) {
         const int b0 = warp * SB, wv = min(SB, nb - b0), c = lane;
@@ -308,56 +345,57 @@ __device__ void block_potrf_inv(const T *F, int ld, int nb, int64_t gcol0, statu
         }
 #pragma unroll 16
         for (int r = 0; r < SB; ++r)
-            if (r >= c) X[b0 + r][b0 + c] = x[r];
+            if (r >= c) XT[(b0 + c) * XLD + b0 + r] = x[r];
     }
     __syncthreads();
-    // off-diagonal blocks, one 16 x 16 block row at a time
+    // W(i, k) = X(i, i) L(i, k), i > k, into XT's block (i, k); X(i, i)(r, t) is
+    // zero for t > r, so the sum runs over the whole sub-block
+    {
+        const int r = tid % SB, q = tid / SB;
+        for (int i = 1; i < nsb; ++i)
+            for (int k = 0; k < i; ++k) {
+                T acc0 = T(0), acc1 = T(0);
+#pragma unroll
+                for (int t = 0; t < SB; t += 2) {
+                    acc0 += XT[(SB * i + t) * XLD + SB * i + r] * A[SB * i + t][SB * k + q];
+                    acc1 += XT[(SB * i + t + 1) * XLD + SB * i + r] * A[SB * i + t + 1][SB * k + q];
+                }
+                XT[(SB * i + r) * XLD + SB * k + q] = acc0 + acc1;
+            }
+    }
+    __syncthreads();
+    // X(i, j)(r, c) = -sum_k sum_q W(i, k)(r, q) X(k, j)(q, c); both operands
+    // are rows of XT, read four entries at a time
+    {
+        const int r = tid % SB, c = tid / SB;
 #pragma unroll 1
-    for (int bi = 1; bi < nsb; ++bi) {
-        const int r0 = bi * SB;
-        // Tm(bj) = sum_{p in [bj*16, r0)} L(r0 + r, p) X(p, bj*16 + c)  -> X(r0 + r, bj*16 + c)
-        for (int idx = tid; idx < bi * SB * SB; idx += POTRF_THREADS) {
-            const int bj = idx / (SB * SB), r = idx % SB, c = (idx / SB) % SB;
-            T acc0 = T(0), acc1 = T(0);
-            const int p0 = bj * SB;
-#pragma unroll 4
-            for (int p = p0; p < r0; p += 2) {
-                acc0 += A[r0 + r][p] * X[p][p0 + c];
-                acc1 += A[r0 + r][p + 1] * X[p + 1][p0 + c];
+        for (int i = 1; i < nsb; ++i) {
+            for (int j = 0; j < i; ++j) {
+                T acc[4] = {T(0), T(0), T(0), T(0)};
+                for (int k = j; k < i; ++k) {
+                    const T *w = XT + (SB * i + r) * XLD + SB * k;
+                    const T *x = XT + (SB * j + c) * XLD + SB * k;
+#pragma unroll
+                    for (int q = 0; q < SB; q += 4) {
+                        T wv[4], xv[4];
+                        load4(wv, w + q);
+                        load4(xv, x + q);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) acc[u] += wv[u] * xv[u];
+                    }
+                }
+                XT[(SB * j + c) * XLD + SB * i + r] = -((acc[0] + acc[1]) + (acc[2] + acc[3]));
             }
-            X[r0 + r][p0 + c] = acc0 + acc1;
+            __syncthreads();
         }
-        __syncthreads();
-        constexpr int QMAX = SB * SB * (NB / SB - 1) / POTRF_THREADS;
-        T out[QMAX];
-#pragma unroll 6
-        for (int q = 0; q < QMAX; ++q) {
-            const int idx = tid + q * POTRF_THREADS;
-            const int bj = idx / (SB * SB), r = idx % SB, c = (idx / SB) % SB;
-            T acc = T(0);
-            if (idx < bi * SB * SB) {
-#pragma unroll 4
-                for (int p = 0; p < SB; ++p) acc += X[r0 + r][r0 + p] * X[r0 + p][bj * SB + c];
-            }
-            out[q] = -acc;
-        }
-        __syncthreads();
-#pragma unroll 6
-        for (int q = 0; q < QMAX; ++q) {
-            const int idx = tid + q * POTRF_THREADS;
-            const int bj = idx / (SB * SB), r = idx % SB, c = (idx / SB) % SB;
-            if (idx < bi * SB * SB) X[r0 + r][bj * SB + c] = (r0 + r < nb) ? out[q] : T(0);
-        }
-        __syncthreads();
     }
     if (write) {
         for (int idx = tid; idx < NB * NB; idx += POTRF_THREADS) {
             const int r = idx % NB, c = idx / NB;
             Lout[idx] = (r >= c && r < nb) ? A[r][c] : T(0);
-            Dinv[idx] = (r >= c) ? X[r][c] : T(0);
+            Dinv[idx] = (r >= c) ? XT[c * XLD + r] : T(0);
         }
     }
-    __syncthreads();
 }
 
 // the factored diagonal blocks (kept aside while the panels of a step still
@@ -395,10 +433,10 @@ __global__ void __launch_bounds__(THREADS) panel_kernel(DevSym d, T *__restrict_
                                                         const int4 *__restrict__ items, int kb,
                                                         status_t *status) {
     static_assert(THREADS == POTRF_THREADS, "the panel CTA runs the block factorization");
+    static_assert(RB == 64 && NB == 64 && THREADS == 256, "4 x 4 register tiles cover the 64 x 64 panel block");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *Psm = reinterpret_cast<T *>(smem_raw);        // block factorization: A, X (= Linv), invd
-    T(*Xinv)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(Psm + NB * (NB + 1));
-    T *Xs = Psm + 2 * NB * (NB + 1) + NB;             // [p][r], ld RB
+    T *Psm = reinterpret_cast<T *>(smem_raw);        // block factorization (BP_ELEMS)
+    T *Xs = Psm + BP_ELEMS;                           // [p][r], ld RB
     const int4 it = items[blockIdx.x];
     const int s = it.x, rb = it.y;
     const Dims z = dims(d, s);
@@ -406,35 +444,56 @@ __global__ void __launch_bounds__(THREADS) panel_kernel(DevSym d, T *__restrict_
     const int t0 = kb + nb;
     const int r0 = (t0 == z.k ? z.kp : t0) + rb * RB;
     T *F = front + d.foff[s];
+    // the diagonal block first, in its own group: the pivot chain starts while
+    // the panel rows are still in flight
+    block_load<T>(F + (int64_t)kb * z.ld + kb, z.ld, nb, Psm);
+    cp_async_commit();
     stage_tile<T, THREADS>(Xs, RB, F + (int64_t)kb * z.ld + r0, z.ld, RB, NB, z.mp - r0, nb);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
     const int64_t boff = d.dinvoff[s] + (int64_t)(kb / NB) * NB * NB;
-    block_potrf_inv<T>(F + (int64_t)kb * z.ld + kb, z.ld, nb, d.sfirst[s] + kb, status, dinv + boff,
-                       ldiag + boff, rb == 0, Psm);
-    // out[r][c] = sum_{p <= c} X[r][p] Linv(c, p); thread: row tid % 64, 16 cols
+    block_potrf_inv<T>(nb, d.sfirst[s] + kb, status, dinv + boff, ldiag + boff, rb == 0, Psm);
+    cp_async_wait<0>();
+    __syncthreads();
+    // out[r][c] = sum_{p <= c} X[r][p] Linv(c, p), Linv(c, p) = XT[p][c];
+    // thread: rows 4 (tid % 16) + i, columns 4 (tid / 16) + j, so both
+    // operands of a step p are one 4-wide shared load, and p stops at the
+    // thread's last column (Linv is lower triangular).
     const int tid = threadIdx.x;
-    const int r = tid % RB, cg = tid / RB;
-    T acc[NB / 4];
+    const T *LT = Psm + BP_XT;
+    const int rq = tid % (RB / 4), cq = tid / (RB / 4);
+    T acc[4][4];
 #pragma unroll
-    for (int u = 0; u < NB / 4; ++u) acc[u] = T(0);
-    for (int p = 0; p < nb; ++p) {
-        const T x = Xs[p * RB + r];
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int u = 0; u < NB / 4; ++u) acc[u] += x * Xinv[cg + 4 * u][p];
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    const int pend = min(nb, 4 * cq + 4);
+#pragma unroll 4
+    for (int pp = 0; pp < pend; ++pp) {
+        T xv[4], lv[4];
+        load4(xv, Xs + pp * RB + 4 * rq);
+        load4(lv, LT + pp * XLD + 4 * cq);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += xv[i] * lv[j];
     }
-    if (r0 + r < z.mp) {
+    // through shared memory ([c][r], ld RB) for whole-column stores
+    __syncthreads();
+    T *Os = Xs;
 #pragma unroll
-        for (int u = 0; u < NB / 4; ++u) {
-            const int c = cg + 4 * u;
-            if (c < nb) F[(int64_t)(kb + c) * z.ld + r0 + r] = acc[u];
-        }
+    for (int j = 0; j < 4; ++j) {
+        T o[4] = {acc[0][j], acc[1][j], acc[2][j], acc[3][j]};
+        store4(Os + (4 * cq + j) * RB + 4 * rq, o);
+    }
+    __syncthreads();
+    for (int q = tid; q < RB * NB; q += THREADS) {
+        const int rr = q % RB, c = q / RB;
+        if (c < nb && r0 + rr < z.mp) F[(int64_t)(kb + c) * z.ld + r0 + rr] = Os[c * RB + rr];
     }
     if (pk != nullptr) {
         // packed tf32 hi/lo lines of these rows for the tensor-core updates
-        __syncthreads();
-        T *Os = Xs;  // [c][r], ld RB
-#pragma unroll
-        for (int u = 0; u < NB / 4; ++u) Os[(cg + 4 * u) * RB + r] = acc[u];
-        __syncthreads();
         unsigned char *P = pk + d.pkoff[s];
         const int prow = pack_rows(z.mp);
         for (int q = tid; q < RB * (NB / 4); q += THREADS) {
@@ -542,7 +601,7 @@ __global__ void __launch_bounds__(THREADS) schur_kernel(DevSym d, T *__restrict_
 }
 
 template <class T>
-constexpr size_t panel_smem() { return sizeof(T) * (2 * NB * (NB + 1) + NB + NB * RB); }
+constexpr size_t panel_smem() { return sizeof(T) * (BP_ELEMS + NB * RB); }
 template <class T>
 constexpr size_t schur_smem() { return 2 * sizeof(T) * BK * (BM + BN); }
 
