@@ -191,35 +191,30 @@ constexpr int POTRF_THREADS = 256;
 
 // Pivot C of a 16 x 16 Cholesky held by one warp, one row per lane (v),
 // then pivots C+1, ...: compile-time recursion, so every register index is a
-// constant.
+// constant.  The first pivot that is not positive is kept in `bad` (the caller
+// reports it), so the unrolled chain has no branch.
 template <class T, int C>
 struct WarpChol {
-    static __device__ __forceinline__ void step(T (&v)[SB], T &myinv, int lane, int w,
-                                                int64_t gcol0, status_t *status) {
+    static __device__ __forceinline__ void step(T (&v)[SB], T &myinv, int lane, int w, int &bad) {
         T dc = __shfl_sync(0xffffffffu, v[C], C);
-        if (C < w && !(dc > T(0))) {
-            if (lane == 0) atomicMin(status, (status_t)(gcol0 + C));
-            dc = T(1);
-        }
-        if (C >= w) dc = T(1);
+        const bool fail = C < w && !(dc > T(0));
+        bad = (fail && bad < 0) ? C : bad;
+        dc = (fail || C >= w) ? T(1) : dc;
         T sc, ic;
         pivot_root(dc, sc, ic);
-        if (lane == C) {
-            v[C] = sc;
-            myinv = ic;
-        }
-        else if (lane > C) v[C] *= ic;
+        v[C] = lane == C ? sc : (lane > C ? v[C] * ic : v[C]);
+        myinv = lane == C ? ic : myinv;
 #pragma unroll
         for (int c2 = C + 1; c2 < SB; ++c2) {
             const T lc = __shfl_sync(0xffffffffu, v[C], c2);
             if (lane >= c2) v[c2] -= v[C] * lc;
         }
-        WarpChol<T, C + 1>::step(v, myinv, lane, w, gcol0, status);
+        WarpChol<T, C + 1>::step(v, myinv, lane, w, bad);
     }
 };
 template <class T>
 struct WarpChol<T, SB> {
-    static __device__ __forceinline__ void step(T (&)[SB], T &, int, int, int64_t, status_t *) {}
+    static __device__ __forceinline__ void step(T (&)[SB], T &, int, int, int &) {}
 };
 
 // Shared memory of the block factorization (element offsets): the factor
@@ -264,7 +259,9 @@ __device__ void block_potrf_inv(int nb, int64_t gcol0, status_t *status, T *Dinv
             T v[SB], myinv = T(1);
 #pragma unroll 16
             for (int c = 0; c < SB; ++c) v[c] = (lane < w && c <= lane) ? A[jb + lane][jb + c] : T(0);
-            WarpChol<T, 0>::step(v, myinv, lane, w, gcol0 + jb, status);
+            int bad = -1;
+            WarpChol<T, 0>::step(v, myinv, lane, w, bad);
+            if (bad >= 0 && lane == 0) atomicMin(status, (status_t)(gcol0 + jb + bad));
             if (lane < w) {
 #pragma unroll 16
                 for (int c = 0; c < SB; ++c)
@@ -427,7 +424,7 @@ __global__ void __launch_bounds__(THREADS) diag_copy_kernel(DevSym d, T *__restr
 // padding); a CTA may have no rows (its launch item only factors the block).
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(THREADS) panel_kernel(DevSym d, T *__restrict__ front,
+__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 3 : 1) panel_kernel(DevSym d, T *__restrict__ front,
                                                         T *__restrict__ dinv, T *__restrict__ ldiag,
                                                         unsigned char *__restrict__ pk,
                                                         const int4 *__restrict__ items, int kb,

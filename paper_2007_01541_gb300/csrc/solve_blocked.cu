@@ -388,10 +388,31 @@ __global__ void __launch_bounds__(THREADS, C::MINB) bupdate_kernel(DevSym d, con
         stage_rhs<T, C>(Rs[buf], Y, f + b0, p0, w, c0, nc, n);
         cp_async_commit();
     };
+    T *dst;
+    int64_t ldd;
+    if (seg == 0) {
+        dst = Tt + f + i0;
+        ldd = n;
+    } else {
+        dst = W + d.woff[s] * nrhs + i0;
+        ldd = m - k;
+    }
+    constexpr int PE = C::ROWS * C::RHS / THREADS;   // target elements per thread
+    // FP32 with the small tile has the registers to hold the target early
+    constexpr bool PRE = sizeof(T) == 4 && C::RPW * C::RPL <= 8;
     T acc[C::RPW][C::RPL];
     tile_zero<T, C>(acc);
     const int nchunk = (w + NB - 1) / NB;
     stage(0, 0);
+    // the target tile is read now, while the staging copies are in flight
+    // (same element order as the write-back below: rows contiguous)
+    T tpre[PE];
+#pragma unroll
+    for (int e = 0; e < PE; ++e) {
+        const int idx = threadIdx.x + e * THREADS;
+        const int r = idx % C::ROWS, c = idx / C::ROWS;
+        tpre[e] = (PRE && r < nrow && c < nc) ? dst[r + (int64_t)(c0 + c) * ldd] : T(0);
+    }
     for (int ch = 0; ch < nchunk; ++ch) {
         const int cur = ch & 1;
         if (ch + 1 < nchunk) {
@@ -407,18 +428,14 @@ __global__ void __launch_bounds__(THREADS, C::MINB) bupdate_kernel(DevSym d, con
     T *O = sm;
     tile_to_smem<T, C>(acc, O);
     __syncthreads();
-    T *dst;
-    int64_t ldd;
-    if (seg == 0) {
-        dst = Tt + f + i0;
-        ldd = n;
-    } else {
-        dst = W + d.woff[s] * nrhs + i0;
-        ldd = m - k;
-    }
-    for (int idx = threadIdx.x; idx < C::ROWS * C::RHS; idx += THREADS) {
+#pragma unroll
+    for (int e = 0; e < PE; ++e) {
+        const int idx = threadIdx.x + e * THREADS;
         const int r = idx % C::ROWS, c = idx / C::ROWS;
-        if (r < nrow && c < nc) dst[r + (int64_t)(c0 + c) * ldd] -= O[c * C::LDO + r];
+        if (r < nrow && c < nc) {
+            T *q = dst + r + (int64_t)(c0 + c) * ldd;
+            *q = (PRE ? tpre[e] : *q) - O[c * C::LDO + r];
+        }
     }
 }
 
