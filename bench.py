@@ -38,7 +38,7 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 FP64_FLOPS_PER_SM_CLK = 4     # 2 FP64 FMA per SM per clock (GB300: 1.25 TFLOP/s nominal)
 MAX_SM_MHZ = 2070.0
-DF_OPS_PER_TERM = 15          # FP32 instructions of one double-float multiply-add
+DF_OPS_PER_TERM = 12.75       # FP32 instructions per double-float multiply-add (12, plus a 6-op TwoSum every 8 terms)
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
 # kernel from one ncu capture of the full-size command, with the SHA-1 of the
@@ -378,8 +378,9 @@ def run_ours(args):
                                       "bwd_reduce", "bwd_xapply", "sbinv_stage")) or (
             top["name"].startswith("spmv_residual") and nr >= 8)
         if top["name"] == "spmv_residual_df":
-            # double-float multiply-add: 15 FP32 instructions per (entry, right-hand
-            # side) term (4 for the product, 11 for TwoSum + renormalisation); the
+            # double-float multiply-add: 12 FP32 instructions per (entry, right-hand
+            # side) term (4 for the product, 6 for TwoSum, 2 to collect the error
+            # terms) plus a 6-instruction renormalisation every 8 terms; the
             # bound is the FP32 lane-operation rate
             terms = top["flops"] / 2.0
             peak = SM_COUNT * FP32_LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
@@ -387,7 +388,7 @@ def run_ours(args):
             roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s (FP32 lane operations)",
                     "frac": ach / peak, "traffic": measured_traffic(top["name"]), "kernel": top["name"],
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
-                    "work": "15 FP32 operations per stored entry of A and right-hand side"}
+                    "work": "12.75 FP32 operations per stored entry of A and right-hand side"}
         elif alu:
             fp64 = top["name"].endswith("_fp64")
             per_clk = FP64_FLOPS_PER_SM_CLK if fp64 else 2 * FP32_LANES_PER_SM

@@ -139,7 +139,7 @@ struct wd_ctx {
     void *d_part = nullptr;        // partial sums of the backward split reduction
     int64_t part_elems = 0;
     double *d_B = nullptr, *d_Bp = nullptr, *d_X = nullptr, *d_R = nullptr, *d_cm = nullptr;
-    float *d_Xh = nullptr, *d_Xl = nullptr;   // double-float split of the refinement vectors
+    float2 *d_Xp = nullptr;   // double-float split of the refinement vectors, (hi, lo) pairs
     int64_t W_rows = 0;   // sum of (m_s - k_s)
     int64_t nnz_full = 0;  // stored entries of the full CSR of P A P^T
     int4 *d_spmv_chunks = nullptr, *d_spmv_fin = nullptr;
@@ -1254,7 +1254,7 @@ static wd_status ensure_solve_ws(wd_handle h, int64_t nrhs) {
     h->d_Y = h->d_W = h->d_T = h->d_part = nullptr;
     h->part_elems = 0;
     h->d_B = h->d_Bp = h->d_X = h->d_R = h->d_cm = h->d_P = nullptr;
-    h->d_Xh = h->d_Xl = nullptr;
+    h->d_Xp = nullptr;
     h->splan = Plan();
     h->aplan = Plan();
     h->splan_nrhs = h->aplan_nrhs = -1;
@@ -1266,8 +1266,7 @@ static wd_status ensure_solve_ws(wd_handle h, int64_t nrhs) {
     CK(h->work.alloc((void **)&h->d_B, n * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc((void **)&h->d_Bp, n * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc((void **)&h->d_X, n * nrhs * sizeof(double)), "solve ws");
-    CK(h->work.alloc((void **)&h->d_Xh, n * nrhs * sizeof(float)), "solve ws");
-    CK(h->work.alloc((void **)&h->d_Xl, n * nrhs * sizeof(float)), "solve ws");
+    CK(h->work.alloc((void **)&h->d_Xp, n * nrhs * sizeof(float2)), "solve ws");
     CK(h->work.alloc((void **)&h->d_R, n * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc((void **)&h->d_cm, 3 * nrhs * sizeof(double)), "solve ws");
     CK(h->work.alloc((void **)&h->d_P, std::max(h->n_spmv_slots, 1) * nrhs * sizeof(double)), "solve ws");
@@ -1334,7 +1333,7 @@ static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cud
         // many right-hand sides: double-float arithmetic on the FP32 pipes
         prof_single(h, "spmv_residual_df", 0, 0, st, true);
         wd::launch_spmv_residual_df(h->dsym, h->d_spmv_chunks, h->n_spmv_chunks, h->d_spmv_fin,
-                                    h->n_spmv_fin, h->d_csr_vh, h->d_csr_vl, X, h->d_Xh, h->d_Xl, h->d_Bp,
+                                    h->n_spmv_fin, h->d_csr_vh, h->d_csr_vl, X, h->d_Xp, h->d_Bp,
                                     h->d_R, h->d_P, nrhs, st);
         prof_single(h, "spmv_residual_df", 2.0 * nf * nrhs, 12.0 * nf + 24.0 * n * nrhs, st, false);
         h->launches += h->n_spmv_fin > 0 ? 3 : 2;

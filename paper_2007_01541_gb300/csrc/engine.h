@@ -126,9 +126,9 @@ void launch_spmv_residual(const DevSym &d, const int4 *chunks, int nchunks, cons
                           int nfin, const double *X, const double *Bp, double *R, double *P,
                           int64_t nrhs, unsigned long long *bad, cudaStream_t st);
 // the same residual in double-float arithmetic (vh + vl = the CSR values;
-// Xh, Xl: n x nrhs scratch for the split of X)
+// Xp: n x nrhs scratch for the split of X as (hi, lo) pairs)
 void launch_spmv_residual_df(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin, int nfin,
-                             const float *vh, const float *vl, const double *X, float *Xh, float *Xl,
+                             const float *vh, const float *vl, const double *X, float2 *Xp,
                              const double *Bp, double *R, double *P, int64_t nrhs, cudaStream_t st);
 void launch_norm_inf_rows(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin,
                           int nfin, double *partial, double *out, cudaStream_t st);

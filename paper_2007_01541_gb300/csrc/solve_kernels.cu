@@ -49,15 +49,14 @@ __global__ void gather_values_kernel(const int32_t *__restrict__ src, const doub
     }
 }
 
-// Xh + Xl = X (double-float split of the refinement vectors)
-__global__ void split_df_kernel(const double *__restrict__ X, float *__restrict__ Xh,
-                                float *__restrict__ Xl, int64_t cnt) {
+// Xp[t] = (hi, lo), hi + lo = X[t] (double-float split of the refinement
+// vectors, the two halves side by side so that one 8-byte load fetches both)
+__global__ void split_df_kernel(const double *__restrict__ X, float2 *__restrict__ Xp, int64_t cnt) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt;
          t += (int64_t)gridDim.x * blockDim.x) {
         const double x = X[t];
         const float h = __double2float_rn(x);
-        Xh[t] = h;
-        Xl[t] = __double2float_rn(x - (double)h);
+        Xp[t] = make_float2(h, __double2float_rn(x - (double)h));
     }
 }
 
@@ -208,11 +207,13 @@ __global__ void __launch_bounds__(THREADS) spmv_wide_kernel(DevSym d, const int4
     }
 }
 
-// Double-float accumulator (hi, lo): a value hi + lo with |lo| <= ulp(hi)/2,
-// about 48 significant bits.  Products of double-float operands are formed
-// exactly up to the lo*lo term with FMA (Dekker / Ogita-Rump-Oishi TwoProd),
-// sums with Knuth's TwoSum and a renormalising FastTwoSum, all with
-// explicitly rounded intrinsics so that nothing is contracted.
+// Double-float accumulator (hi, lo), about 48 significant bits.  Products of
+// double-float operands are formed exactly up to the lo*lo term with FMA
+// (Dekker / Ogita-Rump-Oishi TwoProd); a product is added to hi with Knuth's
+// TwoSum and the two error terms are collected in lo without renormalising
+// (the compensated dot product of Ogita, Rump and Oishi); df_renorm folds lo
+// back every few terms so that it stays at the rounding level of hi.  All
+// operations are explicitly rounded intrinsics, so nothing is contracted.
 struct DF {
     float hi, lo;
 };
@@ -223,10 +224,16 @@ __device__ __forceinline__ void df_add_prod(DF &s, float ah, float al, float xh,
     pl = __fmaf_rn(al, xh, pl);
     const float t = __fadd_rn(s.hi, ph);         // TwoSum(s.hi, ph)
     const float z = __fsub_rn(t, s.hi);
-    float e = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(ph, z));
-    e = __fadd_rn(e, __fadd_rn(pl, s.lo));
-    s.hi = __fadd_rn(t, e);                      // FastTwoSum(t, e)
-    s.lo = __fsub_rn(e, __fsub_rn(s.hi, t));
+    const float e = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(ph, z));
+    s.hi = t;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(pl, e));
+}
+// (hi, lo) := TwoSum(hi, lo)
+__device__ __forceinline__ void df_renorm(DF &s) {
+    const float t = __fadd_rn(s.hi, s.lo);
+    const float z = __fsub_rn(t, s.hi);
+    s.lo = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(s.lo, z));
+    s.hi = t;
 }
 // s += u (both double-float)
 __device__ __forceinline__ void df_add(DF &s, DF u) {
@@ -245,8 +252,7 @@ __device__ __forceinline__ void df_add(DF &s, DF u) {
 __global__ void __launch_bounds__(THREADS, 4) spmv_df_kernel(DevSym d, const int4 *__restrict__ items,
                                                           int count, const float *__restrict__ vh,
                                                           const float *__restrict__ vl,
-                                                          const float *__restrict__ Xh,
-                                                          const float *__restrict__ Xl,
+                                                          const float2 *__restrict__ Xp,
                                                           const double *__restrict__ Bp,
                                                           double *__restrict__ R, double *__restrict__ P,
                                                           int nrhs) {
@@ -279,10 +285,12 @@ __global__ void __launch_bounds__(THREADS, 4) spmv_df_kernel(DevSym d, const int
                     ah[q] = __shfl_sync(0xffffffffu, mh, src);
                     al[q] = __shfl_sync(0xffffffffu, ml, src);
                     const bool ok = j + q < cnt;
-                    xh[q][0] = (ok && va) ? Xh[xo + ca] : 0.f;
-                    xl[q][0] = (ok && va) ? Xl[xo + ca] : 0.f;
-                    xh[q][1] = (ok && vb) ? Xh[xo + cb] : 0.f;
-                    xl[q][1] = (ok && vb) ? Xl[xo + cb] : 0.f;
+                    const float2 pa = (ok && va) ? Xp[xo + ca] : make_float2(0.f, 0.f);
+                    const float2 pb = (ok && vb) ? Xp[xo + cb] : make_float2(0.f, 0.f);
+                    xh[q][0] = pa.x;
+                    xl[q][0] = pa.y;
+                    xh[q][1] = pb.x;
+                    xl[q][1] = pb.y;
                 }
 #pragma unroll
                 for (int q = 0; q < NS; ++q) {
@@ -291,6 +299,11 @@ __global__ void __launch_bounds__(THREADS, 4) spmv_df_kernel(DevSym d, const int
                         df_add_prod(b[q], ah[q], al[q], xh[q][1], xl[q][1]);
                     }
                 }
+            }
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                df_renorm(a[q]);
+                df_renorm(b[q]);
             }
         }
         df_add(a[0], a[1]);
@@ -574,12 +587,12 @@ void launch_spmv_residual(const DevSym &d, const int4 *chunks, int nchunks, cons
 }
 
 void launch_spmv_residual_df(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin, int nfin,
-                             const float *vh, const float *vl, const double *X, float *Xh, float *Xl,
+                             const float *vh, const float *vl, const double *X, float2 *Xp,
                              const double *Bp, double *R, double *P, int64_t nrhs, cudaStream_t st) {
     const int64_t cnt = d.n * nrhs;
-    split_df_kernel<<<grid_for(cnt), THREADS, 0, st>>>(X, Xh, Xl, cnt);
+    split_df_kernel<<<grid_for(cnt), THREADS, 0, st>>>(X, Xp, cnt);
     const int blocks = (int)(((int64_t)nchunks * 32 + THREADS - 1) / THREADS);
-    spmv_df_kernel<<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, vh, vl, Xh, Xl, Bp, R, P, (int)nrhs);
+    spmv_df_kernel<<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, vh, vl, Xp, Bp, R, P, (int)nrhs);
     if (nfin > 0) spmv_finish_kernel<<<nfin, 64, 0, st>>>(fin, nfin, Bp, R, P, (int)nrhs);
 }
 
