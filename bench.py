@@ -40,20 +40,25 @@ FP64_FLOPS_PER_SM_CLK = 4     # 2 FP64 FMA per SM per clock (GB300: 1.25 TFLOP/s
 MAX_SM_MHZ = 2070.0
 DF_OPS_PER_TERM = 12.75       # FP32 instructions per double-float multiply-add (12, plus a 6-op TwoSum every 8 terms)
 
+# tf32 / bf16 dense tensor rates (nominal 1.1 and 2.25 PFLOP/s): a tf32
+# contraction's peak is the measured bf16 peak times this ratio
+TF32_PER_BF16 = 1.1 / 2.25
+
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
-# kernel from one ncu capture of the full-size command, with the SHA-1 of the
-# source file the kernel was built from: reported as null once that file has
-# changed (profiles/launches_2d256_mixed.md gives the command).
+# kernel from one ncu capture of the full-size command, keyed by (workload,
+# kernel), with the SHA-1 of the source file the kernel was built from:
+# reported as null once that file has changed (profiles/panel_2d256.md and
+# profiles/launches_2d256_mixed.md give the commands).
 MEASURED_TRAFFIC = {
-    "spmv_residual_df": {"bytes": 357519104 + 39474432,
-                         "source": "paper_2007_01541_gb300/csrc/solve_kernels.cu",
-                         "sha1": "a76c0fe3b457d5403c6d5b631b946989a6d2f2ae"},
+    ("2d", "potrf_panel_fp32"): {"bytes": (286807552 + 143948032) / 124,
+                                 "source": "paper_2007_01541_gb300/csrc/front_kernels.cu",
+                                 "sha1": "efcff68576cc7dc2653dbf7a3d28b0533710c3e9"},
 }
 
 
-def measured_traffic(kernel):
+def measured_traffic(workload, kernel):
     import hashlib
-    t = MEASURED_TRAFFIC.get(kernel)
+    t = MEASURED_TRAFFIC.get((workload, kernel))
     if not t:
         return None
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), t["source"])
@@ -204,6 +209,56 @@ def load_peaks():
         return json.load(open(PEAKS_FILE))
     except Exception:
         return {}
+
+
+# ---------------------------------------------------------------------------
+def roofline(top, nr, workload):
+    """Roofline entry of the dominant kernel `top` (its accumulated launches,
+    event time and algorithmic flops / bytes from the profiled replay)."""
+    peaks = load_peaks()
+    name = top["name"]
+    sec = top["ms"] / 1e3
+    if name.startswith("tc_schur"):
+        # tcgen05 kind::tf32, three MMAs per product (3xTF32): useful flops
+        # against the tf32 rate derived from the measured (sustained) bf16 peak
+        bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+        peak = bf16 * TF32_PER_BF16
+        ach = top["flops"] / sec / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": measured_traffic(workload, name), "kernel": name,
+                "peak_source": ("measured bf16 sustained %.1f x nominal tf32/bf16 1.1/2.25" % bf16)
+                if "bf16_tflops_sustained" in peaks else "fallback 1700 x nominal tf32/bf16 1.1/2.25",
+                "work": "2 k flops per updated lower entry (the 3xTF32 split's extra MMAs count against it)"}
+    if name == "spmv_residual_df":
+        # double-float multiply-add: 12 FP32 instructions per (entry, right-hand
+        # side) term (4 for the product, 6 for TwoSum, 2 to collect the error
+        # terms) plus a 6-instruction renormalisation every 8 terms; the bound
+        # is the FP32 lane-operation rate
+        terms = top["flops"] / 2.0
+        peak = SM_COUNT * FP32_LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
+        ach = DF_OPS_PER_TERM * terms / sec / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s (FP32 lane operations)",
+                "frac": ach / peak, "traffic": measured_traffic(workload, name), "kernel": name,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+                "work": "12.75 FP32 operations per stored entry of A and right-hand side"}
+    # the FP64 residual product with 8 or more right-hand sides does ~10 flops
+    # per byte of A, above GB300's FP64 ridge point: bounded by the FP64 pipe
+    alu = name.startswith(("schur_", "potrf_panel", "fwd_xapply", "fwd_bupdate", "bwd_reduce",
+                           "bwd_xapply", "sbinv_stage")) or (name.startswith("spmv_residual") and nr >= 8)
+    if alu:
+        fp64 = name.endswith("_fp64")
+        per_clk = FP64_FLOPS_PER_SM_CLK if fp64 else 2 * FP32_LANES_PER_SM
+        peak = SM_COUNT * per_clk * MAX_SM_MHZ * 1e6 / 1e12
+        ach = top["flops"] / sec / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": measured_traffic(workload, name), "kernel": name,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if not fp64
+                else "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz"}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    ach = top["bytes"] / sec / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": measured_traffic(workload, name), "kernel": name,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
 
 # ---------------------------------------------------------------------------
@@ -368,42 +423,10 @@ def run_ours(args):
     value = dist.sum(flops_step) / (ms_mixed / 1e3) / 1e12
 
     # roofline of the dominant kernel of the mixed step
-    peaks = load_peaks()
     top = max(kstats, key=lambda k: k["ms"]) if kstats else None
     roof = None
     if top:
-        # the residual product with many right-hand sides does ~10 flops per byte of
-        # A in FP64, above GB300's FP64 ridge point: bounded by the FP64 pipe
-        alu = top["name"].startswith(("schur_", "potrf_panel", "fwd_xapply", "fwd_bupdate",
-                                      "bwd_reduce", "bwd_xapply", "sbinv_stage")) or (
-            top["name"].startswith("spmv_residual") and nr >= 8)
-        if top["name"] == "spmv_residual_df":
-            # double-float multiply-add: 12 FP32 instructions per (entry, right-hand
-            # side) term (4 for the product, 6 for TwoSum, 2 to collect the error
-            # terms) plus a 6-instruction renormalisation every 8 terms; the
-            # bound is the FP32 lane-operation rate
-            terms = top["flops"] / 2.0
-            peak = SM_COUNT * FP32_LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
-            ach = DF_OPS_PER_TERM * terms / (top["ms"] / 1e3) / 1e12
-            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s (FP32 lane operations)",
-                    "frac": ach / peak, "traffic": measured_traffic(top["name"]), "kernel": top["name"],
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
-                    "work": "12.75 FP32 operations per stored entry of A and right-hand side"}
-        elif alu:
-            fp64 = top["name"].endswith("_fp64")
-            per_clk = FP64_FLOPS_PER_SM_CLK if fp64 else 2 * FP32_LANES_PER_SM
-            peak = SM_COUNT * per_clk * MAX_SM_MHZ * 1e6 / 1e12
-            ach = top["flops"] / (top["ms"] / 1e3) / 1e12
-            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None, "kernel": top["name"],
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if not fp64
-                    else "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz"}
-        else:
-            peak = peaks.get("hbm_gbs", 6800.0)
-            ach = top["bytes"] / (top["ms"] / 1e3) / 1e9
-            roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "traffic": None, "kernel": top["name"],
-                    "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+        roof = roofline(top, nr, args.workload)
         roof["launches_per_step"] = top["launches"] / args.steps
         roof["ms_per_launch"] = top["ms"] / max(1, top["launches"])
         roof["timing"] = ("CUDA events around every launch of this kernel during a profiled "
@@ -543,20 +566,7 @@ def run_batch(args):
     roof = None
     top = max(kstats, key=lambda k: k["ms"]) if kstats else None
     if top:
-        if top["name"].startswith(("spmv_residual", "permute", "transpose", "colmax", "fwd_gather")):
-            peaks = load_peaks()
-            peak = peaks.get("hbm_gbs", 6800.0)
-            ach = top["bytes"] / (top["ms"] / 1e3) / 1e9
-            roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                    "traffic": None, "kernel": top["name"],
-                    "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
-        else:
-            fp64 = top["name"].endswith("_fp64")
-            per_clk = FP64_FLOPS_PER_SM_CLK if fp64 else 2 * FP32_LANES_PER_SM
-            peak = SM_COUNT * per_clk * MAX_SM_MHZ * 1e6 / 1e12
-            ach = top["flops"] / (top["ms"] / 1e3) / 1e12
-            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": None, "kernel": top["name"], "peak_source": "derived from unit counts and clock"}
+        roof = roofline(top, 1, "batch")
         roof["launches_per_step"] = top["launches"] / args.steps
     e2e = None
     if not args.no_e2e:
