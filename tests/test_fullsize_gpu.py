@@ -1,0 +1,86 @@
+"""The 2D 256^2 configuration at full size (N = 65,536, Matern-3/2 l = 0.1,
+nugget 1e-3, 64 right-hand sides), in the launch configuration the benchmark
+times: values and right-hand sides on the device, CUDA-graph replay, mixed
+precision with refinement (FP64 beside it).  Needs a GB300.
+
+The oracle cannot factor all 65,536 columns in seconds, so parity is taken on
+what it computes quickly: the first columns of the factor of P A P^T (the
+bottom of the elimination tree, a prefix of about 1.2e10 flops, left-looking
+so that those columns are final) element by element, and the normwise
+backward error of every solution column from the oracle's own FP64 residual.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from wdgen import Kernel, compressed_pattern, compressed_values, haar_basis, rhs
+
+pytestmark = pytest.mark.gpu
+_c = {}
+
+
+def _full():
+    if not _c:
+        b = haar_basis(2, 8)
+        cp, ri = compressed_pattern(b)
+        v = compressed_values(b, cp, ri, Kernel("matern32", 0.1), 1e-3, device="cuda")
+        o = oracle.Oracle(cp, ri, b)
+        c2 = np.cumsum(o.colcount.astype(np.float64) ** 2)
+        ncols = int(np.searchsorted(c2, 1.2e10, side="right"))
+        assert 1000 < ncols < o.n
+        assert o.factor_prefix(v, ncols) == 0
+        _c.update(b=b, cp=cp, ri=ri, v=v, o=o, ncols=ncols, Lo=o.L_values())
+    return _c
+
+
+def _solver(wdlib, torch, c, prec):
+    return wdlib.Solver().analyze(c["cp"], c["ri"], c["b"]).factor(torch.tensor(c["v"], device="cuda"), prec)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 2e-5)])
+def test_fullsize_factor_columns_of_the_oracle_prefix(wdlib, cuda, prec, tol):
+    c = _full()
+    o = c["o"]
+    s = _solver(wdlib, cuda, c, prec)
+    L = s.L_csc_like(o.Lp, o.Li)
+    e = int(o.Lp[c["ncols"]])
+    starts = o.Lp[: c["ncols"]]
+    d2 = np.add.reduceat((L[:e] - c["Lo"][:e]) ** 2, starts)
+    n2 = np.add.reduceat(c["Lo"][:e] ** 2, starts)
+    worst = float(np.sqrt(d2 / n2).max())
+    assert worst <= tol, (prec, worst)
+
+
+def test_fullsize_mixed_solve_64_rhs(wdlib, cuda):
+    torch = cuda
+    c = _full()
+    s = _solver(wdlib, torch, c, "mixed")
+    n = c["o"].n
+    B = rhs(n, 64, seed=0)
+    Bt = torch.tensor(np.ascontiguousarray(B.T), device="cuda")   # (64, n): Bt.T is column-major
+    s.solve(Bt.T)
+    X = Bt.T.cpu().numpy()
+    be = oracle.backward_error(c["cp"], c["ri"], c["v"], X, B)
+    assert be.max() <= 1e-12, be.max()
+    assert s.last_solve["iterations"] >= 1
+    # the library's own (double-float) residual agrees with the oracle's FP64 one
+    assert abs(s.last_solve["backward_error"] - be.max()) <= 5e-15, (s.last_solve, be.max())
+
+
+def test_fullsize_logdet(wdlib, cuda):
+    """FP64: the prefix columns' share 2 sum log L_jj agrees with the oracle's
+    (the diagonal is the first stored entry of a column); mixed: the whole log
+    det agrees with FP64 to the FP32 factor's accuracy."""
+    c = _full()
+    o = c["o"]
+    s64 = _solver(wdlib, cuda, c, "fp64")
+    L = s64.L_csc_like(o.Lp, o.Li)
+    diag = o.Lp[: c["ncols"]]
+    lo = 2.0 * np.log(c["Lo"][diag])
+    part = 2.0 * np.log(L[diag]).sum()
+    assert abs(part - lo.sum()) <= 1e-12 * np.abs(lo).sum(), (part, lo.sum())
+    ld64 = s64.logdet()
+    scale = np.abs(2.0 * np.log(L[o.Lp[:-1]])).sum()     # sum |2 log L_jj| over all columns
+    assert abs(ld64 - 2.0 * np.log(L[o.Lp[:-1]]).sum()) <= 1e-12 * scale
+    ldm = _solver(wdlib, cuda, c, "mixed").logdet()
+    assert abs(ldm - ld64) <= 1e-6 * scale, (ldm, ld64, scale)
