@@ -38,6 +38,7 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 FP64_FLOPS_PER_SM_CLK = 4     # 2 FP64 FMA per SM per clock (GB300: 1.25 TFLOP/s nominal)
 MAX_SM_MHZ = 2070.0
+THETA, THETA_DT = 0.5, 1e-2      # theta workload: Crank-Nicolson, time step
 DF_OPS_PER_TERM = 12.75       # FP32 instructions per double-float multiply-add (12, plus a 6-op TwoSum every 8 terms)
 
 # tf32 / bf16 dense tensor rates (nominal 1.1 and 2.25 PFLOP/s): a tf32
@@ -77,11 +78,13 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["2d", "2d_small", "1d", "batch"], default="2d",
+    p.add_argument("--workload", choices=["2d", "2d_small", "1d", "batch", "theta"], default="2d",
                    help="2d: 256x256 cells (N=65,536, the benchmark); 2d_small: 128x128 "
                         "(N=16,384, for profiler captures); 1d: 1024 cells; batch: the 256 "
                         "independent 1D/2D instances (N 1024..16384), sharded over the ranks")
     p.add_argument("--batch-count", type=int, default=256)
+    p.add_argument("--theta-steps", type=int, default=150,
+                   help="theta workload: time steps per factorization")
     p.add_argument("--nrhs", type=int, default=None)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -273,6 +276,10 @@ def make_workload(kind: str, nrhs: int | None, device: str):
     elif kind == "2d":
         dim, J, ker, nug, nr = 2, 8, Kernel("matern32", 0.1), 1e-3, 64
         name = "2d_haar_256x256_matern32_l0.1_nugget1e-3"
+    elif kind == "theta":
+        # the matrix of the theta-scheme, M = I + theta dt K, for K the 2D 256^2 one
+        dim, J, ker, nug, nr = 2, 8, Kernel("matern32", 0.1), 1e-3, 1
+        name = f"theta_M=I+{THETA * THETA_DT:g}K_2d_haar_256x256_matern32_l0.1_nugget1e-3"
     elif kind == "2d_small":
         dim, J, ker, nug, nr = 2, 7, Kernel("matern32", 0.1), 1e-3, 64
         name = "2d_haar_128x128_matern32_l0.1_nugget1e-3"
@@ -283,6 +290,9 @@ def make_workload(kind: str, nrhs: int | None, device: str):
     b = haar_basis(dim, J)
     cp, ri = compressed_pattern(b)
     vals = compressed_values(b, cp, ri, ker, nug, device=device)
+    if kind == "theta":
+        vals = THETA * THETA_DT * vals
+        vals[cp[:-1]] += 1.0          # the diagonal is the first entry of every column
     B = rhs(b.N, nr, seed=0)
     return dict(name=f"{name}_{nr}rhs", basis=b, colptr=cp, rowidx=ri, values=vals, B=B, nrhs=nr)
 
@@ -493,6 +503,132 @@ def run_ours(args):
     dist.close()
 
 
+def run_theta(args):
+    """Repeated solves of the theta-scheme (Section 5, Eq. (theta), G = I):
+    M = I + theta dt K (K the 2D 256^2 compressed matrix) is factored once,
+    then --theta-steps steps each form (1/theta) U - ((1-theta)/theta) M U +
+    dt F and solve with M, refined to backward error <= 1e-12
+    (wd_theta_step).  One bench step = the factorization plus all time steps;
+    value = (sum_j c_j^2 + steps (4 nnz(L) + 2 nnz(A)) nrhs) / its time."""
+    import numpy as np
+    import torch
+
+    import paper_2007_01541_gb300 as wd
+    from paper_2007_01541_gb300 import build as wdbuild
+    from wdgen import rhs
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = Dist("nccl")
+    wdbuild.build()
+    w = make_workload("theta", args.nrhs, "cuda")
+    N, nr, T = w["basis"].N, w["nrhs"], args.theta_steps
+    s = wd.Solver().analyze(w["colptr"], w["rowidx"], w["basis"])
+    sp = None if args.no_replay else wd.Solver(profile=True).analyze(w["colptr"], w["rowidx"], w["basis"])
+    info = s.info()
+    nnz_a = 2 * int(w["rowidx"].size) - N
+    flops_step = info["flops_factor"] + T * (4.0 * info["nnz_L"] + 2.0 * nnz_a) * nr
+    vals = torch.from_numpy(w["values"]).cuda()
+    U0 = torch.from_numpy(np.ascontiguousarray(w["B"].T)).cuda()       # (nrhs, N): U0.T column-major
+    F = torch.from_numpy(np.ascontiguousarray(rhs(N, nr, seed=1).T)).cuda()
+    Uw = torch.empty_like(U0)
+    stream = torch.cuda.current_stream()
+
+    def job(sv):
+        sv.factor(vals, "mixed")
+        Uw.copy_(U0)
+        for _ in range(T):
+            sv.theta_step(Uw.T, F.T, theta=THETA, dt=THETA_DT)
+
+    def timed(sv, K, W):
+        for _ in range(W):
+            job(sv)
+        sv.kernel_stats(reset=True)
+        sv.launch_count(reset=True)
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            job(sv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        return dist.max(e0.elapsed_time(e1) / K), sv.kernel_stats(reset=True), sv.launch_count(reset=True)
+
+    clocks = ClockSampler(gpu_id_for_smi())
+    clocks.start()
+    ms, _, launches = timed(s, args.steps, args.warmup)
+    clk = clocks.stop()
+    be, its = s.last_solve["backward_error"], s.last_solve["iterations"]
+    # the factorization alone, to report the time of one step
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        s.factor(vals, "mixed")
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_factor = dist.max(f0.elapsed_time(f1) / args.steps)
+    kstats = [] if args.no_replay else timed(sp, args.steps, 1)[1]
+    value = dist.sum(flops_step) / (ms / 1e3) / 1e12
+    roof = None
+    top = max(kstats, key=lambda k: k["ms"]) if kstats else None
+    if top:
+        roof = roofline(top, nr, "theta")
+        roof["launches_per_step"] = top["launches"] / args.steps
+        roof["ms_per_launch"] = top["ms"] / max(1, top["launches"])
+    e2e = None
+    if not args.no_e2e:
+        vh = torch.from_numpy(w["values"]).pin_memory()
+        Uh0 = torch.from_numpy(np.ascontiguousarray(w["B"].T)).pin_memory()
+        Fh = F.cpu().pin_memory()
+        Uh = torch.empty_like(Uh0).pin_memory()
+
+        def job_host():
+            s.factor(vh, "mixed")
+            Uh.copy_(Uh0)
+            for _ in range(T):
+                s.theta_step(Uh.T, Fh.T, theta=THETA, dt=THETA_DT)
+
+        job_host()
+        dist.barrier()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(max(1, args.steps // 2)):
+            job_host()
+        torch.cuda.synchronize()
+        dt = dist.max((time.perf_counter() - t) / max(1, args.steps // 2))
+        e2e = {"value": dist.sum(flops_step) / dt / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": 8 * int(w["rowidx"].size) + T * 2 * 8 * N * nr,
+               "d2h_bytes_per_step": T * 8 * N * nr, "ms_per_step": dt * 1e3}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        o, ncols, fl = cpu_sample(w, args.cpu_flops)
+        t = time.perf_counter()
+        rc = o.factor_prefix(w["values"], ncols)
+        dt = time.perf_counter() - t
+        cpu = {"value": fl / dt / 1e12 if rc == 0 else None, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": (f"left-looking FP64 factor of the first {ncols} of {o.n} columns of P M P^T "
+                          f"({fl:.3e} flop) in {dt:.1f} s; time steps not sampled")}
+    if rank == 0:
+        line = {"metric": f"theta-scheme TFLOP/s (M factored once + {T} steps of product and refined "
+                          f"solve, mixed+IR) at backward error <= 1e-12",
+                "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms, "ms_factor": ms_factor, "ms_per_theta_step": (ms - ms_factor) / T, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": w["name"], "N": N, "nnz_A": nnz_a, "nnz_L": info["nnz_L"], "nrhs": nr,
+                           "theta": THETA, "dt": THETA_DT, "time_steps": T,
+                           "parallelism": "replicas" if ws > 1 else "single",
+                           "l2": "inputs larger than L2 (front pool %.1f GB)" % (info["front_bytes"] / 1e9)},
+                "backward_error": be, "ir_iterations_last_step": its,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "top_kernels": _top(kstats, 12)}
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
 def run_batch(args):
     """Independent instances, one right-hand side each, mixed precision with
     refinement.  Ranks take their longest-processing-time shares of the
@@ -636,6 +772,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "theta":
+        run_theta(args)
     else:
         run_ours(args)
 

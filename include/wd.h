@@ -178,6 +178,24 @@ wd_status wd_factor(wd_handle h, const double *values, int values_on_device, wd_
 wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb, int B_on_device,
                    void *stream, wd_solve_info *info);
 
+/* One step of the theta-scheme for a parabolic problem (Section 5,
+   Eq. (theta)) with an orthonormal basis (mass matrix G = I): the factored
+   matrix is M = I + theta dt K (K the compressed operator, positive
+   semidefinite), and the step is
+     U := M^-1 [ (1/theta) U - ((1 - theta)/theta) M U + dt F ],
+   i.e. (I + theta dt K) U_new = (I - (1 - theta) dt K) U_old + dt F, with
+   F = (1 - theta) f(t_i) + theta f(t_{i+1}) given by the caller (NULL: no
+   source).  The product M U is formed to FP64 accuracy from M's values (as
+   in wd_backward_error); the solve is wd_solve's, refinement included.
+   U (in/out) and F: n x nrhs, column-major, leading dimension ld >= n,
+   original order, both on the device (on_device = 1) or both on the host (0).
+   0 < theta <= 1 (theta = 1: implicit Euler, no product), dt finite and
+   >= 0; otherwise WD_ERR_INVALID_ARG.  Needs a successful wd_factor of M;
+   info as for wd_solve.  Synchronous.  Not in the paper as an interface: the
+   paper states the scheme and factors M once for all steps. */
+wd_status wd_theta_step(wd_handle h, double *U, const double *F, int64_t nrhs, int64_t ld, double theta,
+                        double dt, int on_device, void *stream, wd_solve_info *info);
+
 /* Normwise backward error of given solutions, the test that stops the
    refinement: *be = max over columns of
      ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)

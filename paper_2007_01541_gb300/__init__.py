@@ -30,7 +30,7 @@ EXPORTED = ["wd_default_options", "wd_create", "wd_destroy", "wd_analyze", "wd_s
             "wd_get_info", "wd_factor", "wd_solve", "wd_logdet", "wd_apply_L", "wd_export_L",
             "wd_status_detail", "wd_status_string", "wd_kernel_stats", "wd_launch_count",
             "wd_selinv", "wd_sym_pattern_outer", "wd_value_gradient", "wd_export_L_noalloc",
-            "wd_analyze_batch", "wd_logdet_batch", "wd_backward_error"]
+            "wd_analyze_batch", "wd_logdet_batch", "wd_backward_error", "wd_theta_step"]
 
 
 class WdOptions(ctypes.Structure):
@@ -106,6 +106,8 @@ def load():
         lib.wd_analyze_batch.argtypes = [vp, i32, vp, vp, vp, vp]
         lib.wd_logdet_batch.argtypes = [vp, vp]
         lib.wd_backward_error.argtypes = [vp, vp, vp, i64, i64, ctypes.c_int, vp, ctypes.POINTER(f64)]
+        lib.wd_theta_step.argtypes = [vp, vp, vp, i64, i64, f64, f64, ctypes.c_int, vp,
+                                      ctypes.POINTER(WdSolveInfo)]
         lib.wd_status_detail.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_char_p, ctypes.c_size_t]
         lib.wd_kernel_stats.argtypes = [vp, ctypes.POINTER(WdKernelStat), i32, ctypes.POINTER(i32),
                                         ctypes.c_int]
@@ -302,6 +304,41 @@ class Solver:
                                            X.shape[0], 0, _stream(stream, False),
                                            ctypes.byref(info) if with_info else None))
             out = X
+        self.last_solve = {"iterations": info.iterations, "backward_error": info.backward_error}
+        return out
+
+    def theta_step(self, U, F=None, theta=0.5, dt=1e-2, stream=None):
+        """One theta-scheme step with the factored matrix M = I + theta dt K
+        (wd_theta_step): U := M^-1 [(1/theta) U - ((1-theta)/theta) M U + dt F].
+        A CUDA tensor U (column-major n x nrhs, leading dimension n; F the same
+        shape or None) is updated in place; numpy arrays give a new array."""
+        info = WdSolveInfo()
+        if _is_torch(U):
+            if U.dim() == 1:
+                U = U.unsqueeze(1)
+                F = None if F is None else F.unsqueeze(1)
+            n = U.shape[0]
+            for t in (U,) if F is None else (U, F):
+                if t.stride(0) != 1 or (t.shape[1] > 1 and t.stride(1) != n) or t.shape != U.shape:
+                    raise ValueError("U and F must be column-major n x nrhs with leading dimension n")
+            pu, dev = _ptr(U)
+            pf = None if F is None else _ptr(F)[0]
+            self._check(self._lib.wd_theta_step(self._h, pu, pf, U.shape[1], n, float(theta), float(dt), dev,
+                                                _stream(stream, dev), ctypes.byref(info)))
+            out = U
+        else:
+            Uc = np.array(U, dtype=np.float64, order="F", copy=True)
+            Fc = None if F is None else np.array(F, dtype=np.float64, order="F", copy=True)
+            if Uc.ndim == 1:
+                Uc = Uc[:, None]
+                Fc = None if Fc is None else Fc[:, None]
+            if Fc is not None and Fc.shape != Uc.shape:
+                raise ValueError("F must have U's shape")
+            self._check(self._lib.wd_theta_step(
+                self._h, ctypes.c_void_p(Uc.ctypes.data),
+                None if Fc is None else ctypes.c_void_p(Fc.ctypes.data), Uc.shape[1], Uc.shape[0],
+                float(theta), float(dt), 0, _stream(stream, False), ctypes.byref(info)))
+            out = Uc
         self.last_solve = {"iterations": info.iterations, "backward_error": info.backward_error}
         return out
 

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <thread>
 #include <cstdio>
 #include <cstring>
@@ -1322,13 +1323,12 @@ static wd_status run_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st) {
     return WD_OK;
 }
 
-// R = Bp - A X (FP64, row-major n x nrhs) and the largest normwise backward
-// error over the columns
-static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cudaStream_t st,
-                                 double *be_max) {
+// R = Bp - A X (row-major n x nrhs, factor order) to FP64 accuracy: FP64 up
+// to 8 columns (with the device check of the column indices, read back by the
+// caller from d_spmv_bad), double-float arithmetic beyond
+static wd_status launch_residual(wd_handle h, const double *X, int64_t nrhs, cudaStream_t st) {
     const int64_t n = h->S.n;
     const double nf = (double)h->nnz_full;
-    unsigned long long bad = ~0ULL;
     if (nrhs > 8) {
         // many right-hand sides: double-float arithmetic on the FP32 pipes
         prof_single(h, "spmv_residual_df", 0, 0, st, true);
@@ -1345,6 +1345,18 @@ static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cud
         prof_single(h, "spmv_residual_fp64", 2.0 * nf * nrhs, 12.0 * nf + 24.0 * n * nrhs, st, false);
         h->launches += h->n_spmv_fin > 0 ? 2 : 1;
     }
+    CK(cudaGetLastError(), "residual launch");
+    return WD_OK;
+}
+
+// R = Bp - A X (FP64, row-major n x nrhs) and the largest normwise backward
+// error over the columns
+static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cudaStream_t st,
+                                 double *be_max) {
+    const int64_t n = h->S.n;
+    unsigned long long bad = ~0ULL;
+    wd_status rs = launch_residual(h, X, nrhs, st);
+    if (rs != WD_OK) return rs;
     if (h->batch_count > 0) {
         // per instance and column: each instance is its own system
         const int cnt = h->batch_count;
@@ -1387,19 +1399,8 @@ static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cud
     return WD_OK;
 }
 
-extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb, int B_on_device,
-                              void *stream, wd_solve_info *info) {
-    if (!h) return WD_ERR_INVALID_ARG;
-    if (!h->factored) return fail(h, WD_ERR_STATE, "wd_solve before a successful wd_factor");
-    const int64_t n = h->S.n;
-    if (!B || nrhs < 0 || ldb < n || nrhs > (1 << 20)) return fail(h, WD_ERR_INVALID_ARG, "bad B");
-    if (info) {
-        info->iterations = 0;
-        info->backward_error = -1.0;
-    }
-    if (nrhs == 0) return WD_OK;
-    CK(cudaSetDevice(h->device), "set device");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+// workspaces and the launch plan of solves with nrhs right-hand sides
+static wd_status prepare_solve(wd_handle h, int64_t nrhs) {
     wd_status s = ensure_solve_ws(h, nrhs);
     if (s != WD_OK) return s;
     // 64 x 32 tiles: on the 2D 256^2 case the 128 x 64 tiles lost more to the
@@ -1421,19 +1422,18 @@ extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb,
         h->splan_nrhs = (int)nrhs;
         h->g_solve.reset();
     }
-    double *Bd = B;
-    int64_t ld = ldb;
-    if (!B_on_device) {
-        CK(cudaMemcpy2DAsync(h->d_B, n * sizeof(double), B, ldb * sizeof(double), n * sizeof(double),
-                             nrhs, cudaMemcpyHostToDevice, st),
-           "B H2D");
-        Bd = h->d_B;
-        ld = n;
-    }
+    return WD_OK;
+}
+
+// The solve of the right-hand sides staged in d_Bp (factor order, row-major,
+// FP64): both substitutions, refinement in mixed precision, the result into
+// Bd (device, column-major, ld); when B is a host array (B_on_device = 0,
+// Bd = d_B) it is copied back to B (ldb).  Synchronous.
+static wd_status solve_core(wd_handle h, double *Bd, int64_t ld, double *B, int64_t ldb, int B_on_device,
+                            int64_t nrhs, cudaStream_t st, wd_solve_info *info) {
+    const int64_t n = h->S.n;
     const int nr = (int)nrhs;
-    // right-hand sides in factor order, row-major, FP64
-    wd::launch_permute_in_rm(Bd, ld, h->d_Bp, h->dsym.perm, n, nrhs, st);
-    h->launches += 1;
+    wd_status s;
     if (h->prec == WD_FP64) {
         double *Y = static_cast<double *>(h->d_Y);
         wd::launch_transpose<double>(Y, h->d_Bp, n, nrhs, 0, 0, st);
@@ -1494,6 +1494,92 @@ extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb,
            "B D2H");
     CK(cudaStreamSynchronize(st), "solve");
     return WD_OK;
+}
+
+extern "C" wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb, int B_on_device,
+                              void *stream, wd_solve_info *info) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!h->factored) return fail(h, WD_ERR_STATE, "wd_solve before a successful wd_factor");
+    const int64_t n = h->S.n;
+    if (!B || nrhs < 0 || ldb < n || nrhs > (1 << 20)) return fail(h, WD_ERR_INVALID_ARG, "bad B");
+    if (info) {
+        info->iterations = 0;
+        info->backward_error = -1.0;
+    }
+    if (nrhs == 0) return WD_OK;
+    CK(cudaSetDevice(h->device), "set device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    wd_status s = prepare_solve(h, nrhs);
+    if (s != WD_OK) return s;
+    double *Bd = B;
+    int64_t ld = ldb;
+    if (!B_on_device) {
+        CK(cudaMemcpy2DAsync(h->d_B, n * sizeof(double), B, ldb * sizeof(double), n * sizeof(double),
+                             nrhs, cudaMemcpyHostToDevice, st),
+           "B H2D");
+        Bd = h->d_B;
+        ld = n;
+    }
+    // right-hand sides in factor order, row-major, FP64
+    wd::launch_permute_in_rm(Bd, ld, h->d_Bp, h->dsym.perm, n, nrhs, st);
+    h->launches += 1;
+    return solve_core(h, Bd, ld, B, ldb, B_on_device, nrhs, st, info);
+}
+
+// One theta-scheme step (Section 5, Eq. (theta)) with the factored matrix
+// M = I + theta dt K: U <- M^-1 [(1/theta) U - ((1 - theta)/theta) M U + dt F],
+// which is (I + theta dt K) U_new = (I - (1 - theta) dt K) U + dt F.
+extern "C" wd_status wd_theta_step(wd_handle h, double *U, const double *F, int64_t nrhs, int64_t ld,
+                                   double theta, double dt, int on_device, void *stream,
+                                   wd_solve_info *info) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!h->factored) return fail(h, WD_ERR_STATE, "wd_theta_step before a successful wd_factor");
+    const int64_t n = h->S.n;
+    if (!U || nrhs < 0 || ld < n || nrhs > (1 << 20)) return fail(h, WD_ERR_INVALID_ARG, "bad U");
+    if (!(theta > 0.0 && theta <= 1.0) || !(dt >= 0.0) || !std::isfinite(dt))
+        return fail(h, WD_ERR_INVALID_ARG, "theta must lie in (0, 1] and dt be finite and >= 0");
+    if (info) {
+        info->iterations = 0;
+        info->backward_error = -1.0;
+    }
+    if (nrhs == 0) return WD_OK;
+    CK(cudaSetDevice(h->device), "set device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    wd_status s = prepare_solve(h, nrhs);
+    if (s != WD_OK) return s;
+    double *Ud = U;
+    const double *Fd = F;
+    int64_t ldd = ld;
+    if (!on_device) {
+        // U into d_B, F into d_Y (free until the substitutions start)
+        CK(cudaMemcpy2DAsync(h->d_B, n * sizeof(double), U, ld * sizeof(double), n * sizeof(double), nrhs,
+                             cudaMemcpyHostToDevice, st),
+           "U H2D");
+        if (F) {
+            CK(cudaMemcpy2DAsync(h->d_Y, n * sizeof(double), F, ld * sizeof(double), n * sizeof(double), nrhs,
+                                 cudaMemcpyHostToDevice, st),
+               "F H2D");
+            Fd = static_cast<const double *>(h->d_Y);
+        }
+        Ud = h->d_B;
+        ldd = n;
+    }
+    wd::launch_theta_stage(Ud, Fd, ldd, h->dsym.perm, n, nrhs, 1.0 / theta, (1.0 - theta) / theta, dt, h->d_Bp,
+                           h->d_X, st);
+    h->launches += 1;
+    if (theta < 1.0) {
+        s = launch_residual(h, h->d_X, nrhs, st);
+        if (s != WD_OK) return s;
+        unsigned long long bad = ~0ULL;
+        if (nrhs <= 8)
+            CK(cudaMemcpyAsync(&bad, h->d_spmv_bad, sizeof(bad), cudaMemcpyDeviceToHost, st), "spmv check");
+        CK(cudaMemcpyAsync(h->d_Bp, h->d_R, n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, st),
+           "step right-hand side");
+        CK(cudaStreamSynchronize(st), "theta step");
+        if (bad != ~0ULL)
+            return fail(h, WD_ERR_CUDA, "residual: column index out of range at CSR position " + std::to_string(bad));
+    }
+    return solve_core(h, Ud, ldd, U, ld, on_device, nrhs, st, info);
 }
 
 extern "C" wd_status wd_backward_error(wd_handle h, const double *X, const double *B, int64_t nrhs,

@@ -112,6 +112,10 @@ void launch_apply_L(const DevSym &d, const T *front, const T *Z, T *Out, T *W,
 // refinement vectors are row-major (n x nrhs, right-hand sides contiguous)
 void launch_permute_in_rm(const double *B, int64_t ldb, double *Bp, const int32_t *perm, int64_t n,
                           int64_t nrhs, cudaStream_t st);
+// theta-scheme staging: Bp = a U + g F (F nullable), X = x U, both in factor
+// order, row-major; U, F column-major n x nrhs (ld) in the original order
+void launch_theta_stage(const double *U, const double *F, int64_t ld, const int32_t *perm, int64_t n,
+                        int64_t nrhs, double a, double x, double g, double *Bp, double *X, cudaStream_t st);
 void launch_permute_out_rm(const double *X, double *B, int64_t ldb, const int32_t *perm, int64_t n,
                            int64_t nrhs, cudaStream_t st);
 // dir 0: C (column-major) = Rm; dir 1: Rm (=, or += if accumulate) C

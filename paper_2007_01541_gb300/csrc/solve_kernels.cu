@@ -110,6 +110,24 @@ __global__ void permute_in_rm_kernel(const double *__restrict__ B, int64_t ldb,
     }
 }
 
+// One step of the theta-scheme (Eq. (theta) with G = I), staged in factor
+// order, row-major: Bp[i*nrhs + c] = a U[o] + g F[o] (F nullable) and
+// X[i*nrhs + c] = x U[o], o = perm[i] + c*ld; the residual kernel then forms
+// Bp - M X, the step's right-hand side.
+__global__ void theta_stage_kernel(const double *__restrict__ U, const double *__restrict__ F, int64_t ld,
+                                   const int32_t *__restrict__ perm, int64_t n, int64_t nrhs, double a,
+                                   double x, double g, double *__restrict__ Bp, double *__restrict__ X) {
+    const int64_t tot = n * nrhs;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / nrhs, c = t % nrhs;
+        const int64_t o = perm[i] + c * ld;
+        const double u = U[o];
+        Bp[t] = F ? a * u + g * F[o] : a * u;
+        X[t] = x * u;
+    }
+}
+
 // B[perm[i] + c*ldb] = X[i*nrhs + c]
 __global__ void permute_out_rm_kernel(const double *__restrict__ X, double *__restrict__ B,
                                       int64_t ldb, const int32_t *__restrict__ perm, int64_t n,
@@ -554,6 +572,11 @@ void launch_apply_L(const DevSym &d, const T *front, const T *Z, T *Out, T *W,
 void launch_permute_in_rm(const double *B, int64_t ldb, double *Bp, const int32_t *perm, int64_t n,
                           int64_t nrhs, cudaStream_t st) {
     permute_in_rm_kernel<<<grid_for(n * nrhs), THREADS, 0, st>>>(B, ldb, Bp, perm, n, nrhs);
+}
+
+void launch_theta_stage(const double *U, const double *F, int64_t ld, const int32_t *perm, int64_t n,
+                        int64_t nrhs, double a, double x, double g, double *Bp, double *X, cudaStream_t st) {
+    theta_stage_kernel<<<grid_for(n * nrhs), THREADS, 0, st>>>(U, F, ld, perm, n, nrhs, a, x, g, Bp, X);
 }
 
 void launch_permute_out_rm(const double *X, double *B, int64_t ldb, const int32_t *perm, int64_t n,

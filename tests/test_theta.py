@@ -1,0 +1,102 @@
+"""Theta-scheme steps (Section 5, Eq. (theta), G = I).
+
+CPU: the oracle's step is pinned by two facts of the scheme that do not
+restate its formula: an eigenvector v of K (K v = lambda v) is only scaled,
+by r = (1 - (1 - theta) dt lambda) / (1 + theta dt lambda) per step (source
+0), and u* = K^-1 F is a fixed point of the step.  The library's step is
+checked against argument errors without a GPU.
+
+GPU: wd_theta_step (which forms the step from M alone: (1/theta) U -
+((1 - theta)/theta) M U + dt F) against the oracle's step (which uses K)
+over five steps, FP64 and mixed precision, few and many right-hand sides,
+device and host arrays.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from wdgen import Kernel, compressed_pattern, compressed_values, haar_basis, rhs
+
+
+def _k(dim, J, ker, nug):
+    b = haar_basis(dim, J)
+    cp, ri = compressed_pattern(b)
+    return b, cp, ri, compressed_values(b, cp, ri, ker, nug)
+
+
+@pytest.mark.parametrize("theta,dt", [(0.5, 0.3), (1.0, 2.0), (0.25, 0.05)])
+def test_oracle_step_scales_an_eigenvector(theta, dt):
+    b, cp, ri, k = _k(1, 6, Kernel("exponential", 0.2), 1e-2)
+    K = oracle.sym_lower_to_dense(cp, ri, k)
+    lam, V = np.linalg.eigh(K)
+    o = oracle.Oracle(cp, ri, b)
+    assert o.factor(oracle.theta_matrix(cp, k, theta, dt)) == 0
+    for idx in (0, len(lam) // 2, len(lam) - 1):
+        u = V[:, idx].copy()
+        r = (1 - (1 - theta) * dt * lam[idx]) / (1 + theta * dt * lam[idx])
+        for step in range(1, 4):
+            u = oracle.theta_step(o, cp, ri, k, u[:, None], None, theta, dt)[:, 0]
+            np.testing.assert_allclose(u, r ** step * V[:, idx], rtol=0, atol=1e-12)
+
+
+def test_oracle_step_fixed_point():
+    b, cp, ri, k = _k(2, 4, Kernel("matern32", 0.1), 1e-3)
+    K = oracle.sym_lower_to_dense(cp, ri, k)
+    F = rhs(K.shape[0], 3, seed=4)
+    ustar = np.linalg.solve(K, F)
+    for theta, dt in ((0.5, 0.1), (1.0, 1.0)):
+        o = oracle.Oracle(cp, ri, b)
+        assert o.factor(oracle.theta_matrix(cp, k, theta, dt)) == 0
+        u1 = oracle.theta_step(o, cp, ri, k, ustar, F, theta, dt)
+        assert np.abs(u1 - ustar).max() <= 1e-11 * np.abs(ustar).max()
+
+
+def test_theta_step_argument_errors(wdlib):
+    b, cp, ri, k = _k(1, 6, Kernel("exponential", 0.2), 1e-2)
+    s = wdlib.Solver(symbolic_only=True).analyze(cp, ri, b)
+    with pytest.raises(wdlib.WdError) as e:
+        s.theta_step(np.zeros((cp.size - 1, 1)))
+    assert e.value.status == wdlib.WD_ERR_STATE
+
+
+_cases = {}
+
+
+def _case(name):
+    if name not in _cases:
+        dim, J, ker, nug = {"1d_J10": (1, 10, Kernel("exponential", 0.2), 1e-2),
+                            "2d_J6": (2, 6, Kernel("matern32", 0.1), 1e-3)}[name]
+        _cases[name] = _k(dim, J, ker, nug)
+    return _cases[name]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", ["1d_J10", "2d_J6"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("nrhs,theta", [(1, 0.5), (3, 1.0), (12, 0.5)])
+def test_theta_steps_against_the_oracle(wdlib, cuda, name, prec, nrhs, theta):
+    torch = cuda
+    b, cp, ri, k = _case(name)
+    dt = 0.05
+    m = oracle.theta_matrix(cp, k, theta, dt)
+    o = oracle.Oracle(cp, ri, b)
+    assert o.factor(m) == 0
+    n = cp.size - 1
+    U0 = rhs(n, nrhs, seed=nrhs)
+    F = rhs(n, nrhs, seed=100 + nrhs)
+    s = wdlib.Solver().analyze(cp, ri, b).factor(m, prec)
+    with pytest.raises(wdlib.WdError) as e:
+        s.theta_step(U0, F, theta=0.0, dt=dt)
+    assert e.value.status == wdlib.WD_ERR_INVALID_ARG
+    Uo = U0.copy()
+    Uh = U0.copy()
+    Ud = torch.tensor(np.ascontiguousarray(U0.T), device="cuda").T       # column-major, ld n
+    Fd = torch.tensor(np.ascontiguousarray(F.T), device="cuda").T
+    for _ in range(5):
+        Uo = oracle.theta_step(o, cp, ri, k, Uo, F, theta, dt)
+        Uh = s.theta_step(Uh, F, theta=theta, dt=dt)
+        assert s.last_solve["backward_error"] <= 1e-12
+        s.theta_step(Ud, Fd, theta=theta, dt=dt)
+    scale = np.abs(Uo).max()
+    assert np.abs(Uh - Uo).max() <= 1e-10 * scale
+    assert np.abs(Ud.cpu().numpy() - Uo).max() <= 1e-10 * scale
