@@ -460,6 +460,7 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, int large, Plan &p
     p.slots = 0;
     const int ngg = (nrhs + rgt - 1) / rgt;
     const int TRW = wd::solve_tile_rows(large), TNW = wd::solve_tile_rhs(large);
+    const int TRX = wd::solve_update_rows(large);   // rows per CTA of the xapply / bupdate items
     const int ng = (nrhs + TNW - 1) / TNW;
     const double R = nrhs;
     const int SBW = wd::SB, KSR = wd::SOLVE_KSR;
@@ -488,7 +489,7 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, int large, Plan &p
                 const int s = S.level_nodes[i];
                 if (nsb(s) <= sb) continue;
                 const int w = width(s, sb), wp = wpad(s, sb);
-                for (int rb = 0; rb * TRW < wp; ++rb)
+                for (int rb = 0; rb * TRX < wp; ++rb)
                     for (int g = 0; g < ng; ++g) p.items.push_back({s, sb, rb, g});
                 fl += (double)w * (w + 1) * R;
                 el += (double)w * (w + 1) / 2 + 2.0 * w * R;
@@ -501,9 +502,9 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, int large, Plan &p
                 if (nsb(s) <= sb) continue;
                 const int k = S.k(s), m = S.m(s), w = width(s, sb);
                 const int nJ = k - (sb * SBW + w), nR = m - k;
-                for (int rb = 0; rb * TRW < nJ; ++rb)
+                for (int rb = 0; rb * TRX < nJ; ++rb)
                     for (int g = 0; g < ng; ++g) p.items.push_back({s, sb, rb, g});
-                for (int rb = 0; rb * TRW < nR; ++rb)
+                for (int rb = 0; rb * TRX < nR; ++rb)
                     for (int g = 0; g < ng; ++g) p.items.push_back({s, sb, rb, g + 65536});
                 fl += 2.0 * (nJ + nR) * w * R;
                 el += (double)(nJ + nR) * w + 2.0 * (nJ + nR) * R + w * R;
@@ -551,7 +552,7 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, int large, Plan &p
                 const int s = S.level_nodes[i];
                 if (nsb(s) <= sb) continue;
                 const int w = width(s, sb), wp = wpad(s, sb);
-                for (int rb = 0; rb * TRW < wp; ++rb)
+                for (int rb = 0; rb * TRX < wp; ++rb)
                     for (int g = 0; g < ng; ++g) p.items.push_back({s, sb, rb, g});
                 fl += (double)w * (w + 1) * R;
                 el += (double)w * (w + 1) / 2 + 2.0 * w * R;
@@ -1404,8 +1405,9 @@ static wd_status prepare_solve(wd_handle h, int64_t nrhs) {
     wd_status s = ensure_solve_ws(h, nrhs);
     if (s != WD_OK) return s;
     // 64 x 32 tiles: on the 2D 256^2 case the 128 x 64 tiles lost more to the
-    // halved CTA count of the narrow tree levels than they gained per tile
-    const int large = 0;
+    // halved CTA count of the narrow tree levels than they gained per tile;
+    // up to 8 right-hand sides: matrix-vector shaped kernels, lanes over rows
+    const int large = nrhs <= 8 ? 2 : 0;
     if (h->splan_nrhs != nrhs || h->splan.large != large) {
         build_solve_plan(h->S, (int)nrhs, large, h->splan);
         s = upload_plan(h, h->work, h->splan);

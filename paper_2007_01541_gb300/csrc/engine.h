@@ -197,6 +197,9 @@ void launch_bfwd_gather(const DevSym &d, const T *Y, T *Tt, T *W, const int4 *it
 // sides per CTA, large = 1 -> 128 x 64 (FP32 only); their sizes:
 int solve_tile_rows(int large);
 int solve_tile_rhs(int large);
+// rows per CTA of the xapply / bupdate items (large: 0 = 64 x 32 tiles,
+// 1 = 128 x 64 tiles, 2 = few right-hand sides, 32 rows and lanes over rows)
+int solve_update_rows(int large);
 template <class T>
 void launch_xapply(const DevSym &d, const T *xp, const int64_t *xsoff, const T *in, T *out,
                    const int4 *items, int count, int upper, int large, int nrhs, cudaStream_t st);

@@ -547,6 +547,199 @@ __global__ void __launch_bounds__(THREADS) breduce_finish_kernel(DevSym d, const
     Tt[o] = Y[o] - sum;
 }
 
+// ---------------------------------------------------------------------------
+// Few right-hand sides (nrhs <= 8): the products are matrix-vector shaped, so
+// lanes run over rows (coalesced columns of L or X) instead of right-hand
+// sides.  A CTA covers NRW = 32 rows; its 8 warps split the columns (column p
+// to warp p mod 8), the right-hand-side block is staged in shared memory
+// (V[p * NR + c]), and the warps' partial sums are added in a fixed order.
+// NR = nrhs rounded up to 1, 2, 4 or 8; columns c >= nrhs are zero.
+// ---------------------------------------------------------------------------
+constexpr int NRW = 32;
+constexpr int NWARP = THREADS / 32;
+
+// acc[c] += sum over p in [pa, pb) with p = warp (mod NWARP) of A[p * lda] V[p * NR + c]
+// (A already offset to this lane's row; ok = the row is valid)
+template <class T, int NR>
+__device__ __forceinline__ void narrow_accumulate(T (&acc)[NR], const T *__restrict__ A, int64_t lda, bool ok,
+                                                  const T *V, int pa, int pb) {
+    const int warp = threadIdx.x >> 5;
+    constexpr int U = 4;
+    for (int p0 = pa + warp; p0 < pb; p0 += NWARP * U) {
+        T a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int p = p0 + NWARP * u;
+            a[u] = (ok && p < pb) ? A[(int64_t)p * lda] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int p = min(p0 + NWARP * u, pb - 1);
+#pragma unroll
+            for (int c = 0; c < NR; ++c) acc[c] += a[u] * V[p * NR + c];
+        }
+    }
+}
+
+// the warps' sums of row (tid % 32), column (tid / 32) in warp order, for
+// tid < 32 NR (red: [NWARP][NRW][NR]); call after narrow_accumulate by all threads
+template <class T, int NR>
+__device__ __forceinline__ T narrow_reduce(const T (&acc)[NR], T *red) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < NR; ++c) red[(warp * NRW + lane) * NR + c] = acc[c];
+    __syncthreads();
+    T sum = T(0);
+    if (threadIdx.x < NRW * NR) {
+        const int r = threadIdx.x % NRW, c = threadIdx.x / NRW;
+        for (int g = 0; g < NWARP; ++g) sum += red[(g * NRW + r) * NR + c];
+    }
+    return sum;
+}
+
+// y_B rows [32 rb, 32 rb + 32) = X_B in_B (upper = 0) or X_B^T in_B (upper =
+// 1, the stored transpose); item = (s, sb, rb, 0)
+template <class T, int NR>
+__global__ void __launch_bounds__(THREADS) xapply_narrow_kernel(DevSym d, const T *__restrict__ xp,
+                                                                const int64_t *__restrict__ xsoff,
+                                                                const T *__restrict__ in, T *__restrict__ out,
+                                                                const int4 *__restrict__ items, int upper,
+                                                                int nrhs) {
+    __shared__ T V[SB * NR];
+    __shared__ T red[NWARP * NRW * NR];
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, sb = it.y, rb = it.z;
+    const int k = d.sk[s];
+    const int b0 = sb * SB, w = min(SB, k - b0), wp = (w + NB - 1) / NB * NB;
+    const int64_t n = d.n;
+    const int64_t row0 = d.sfirst[s] + b0;
+    const T *X = xp + xsoff[s] + (int64_t)sb * SB * SB;
+    for (int idx = threadIdx.x; idx < w * NR; idx += THREADS) {
+        const int q = idx / NR, c = idx % NR;
+        V[idx] = c < nrhs ? in[row0 + q + (int64_t)c * n] : T(0);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, r0 = rb * NRW, r = r0 + lane;
+    T acc[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc[c] = T(0);
+    // lower: columns q <= r; upper: q >= r (the stored blocks are zero outside)
+    const int qa = upper ? r0 : 0, qb = upper ? w : min(w, r0 + NRW);
+    narrow_accumulate<T, NR>(acc, X + r, wp, r < w, V, qa, qb);
+    const T sum = narrow_reduce<T, NR>(acc, red);
+    if (threadIdx.x < NRW * NR) {
+        const int rr = r0 + threadIdx.x % NRW, c = threadIdx.x / NRW;
+        if (rr < w && c < nrhs) out[row0 + rr + (int64_t)c * n] = sum;
+    }
+}
+
+// rows below super-block B: target -= L(rows, B) y_B, 32 rows per CTA; item =
+// (s, sb, rb, 65536 * seg): seg 0 = pivot rows after B (target Tt), seg 1 =
+// rows of R (target the update vector W_s)
+template <class T, int NR>
+__global__ void __launch_bounds__(THREADS) bupdate_narrow_kernel(DevSym d, const T *__restrict__ front,
+                                                                 const T *__restrict__ Y, T *__restrict__ Tt,
+                                                                 T *__restrict__ W, const int4 *__restrict__ items,
+                                                                 int nrhs) {
+    __shared__ T V[SB * NR];
+    __shared__ T red[NWARP * NRW * NR];
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, sb = it.y, rb = it.z, seg = it.w >> 16;
+    const int m = d.sm[s], k = d.sk[s], kp = d.skp[s], ld = d.sld[s];
+    const int b0 = sb * SB, w = min(SB, k - b0);
+    const int64_t n = d.n;
+    const int f = d.sfirst[s];
+    const int i0 = seg == 0 ? b0 + w + rb * NRW : rb * NRW;
+    const int nrow = seg == 0 ? k - i0 : (m - k) - i0;
+    const int mrow = seg == 0 ? i0 : kp + i0;
+    T *dst;
+    int64_t ldd;
+    if (seg == 0) {
+        dst = Tt + f + i0;
+        ldd = n;
+    } else {
+        dst = W + d.woff[s] * nrhs + i0;
+        ldd = m - k;
+    }
+    for (int idx = threadIdx.x; idx < w * NR; idx += THREADS) {
+        const int p = idx / NR, c = idx % NR;
+        V[idx] = c < nrhs ? Y[f + b0 + p + (int64_t)c * n] : T(0);
+    }
+    // the target is read while the columns stream in
+    T tpre = T(0);
+    if (threadIdx.x < NRW * NR) {
+        const int r = threadIdx.x % NRW, c = threadIdx.x / NRW;
+        if (r < nrow && c < nrhs) tpre = dst[r + (int64_t)c * ldd];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    T acc[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc[c] = T(0);
+    narrow_accumulate<T, NR>(acc, front + d.foff[s] + (int64_t)b0 * ld + mrow + lane, ld, lane < nrow, V, 0, w);
+    const T sum = narrow_reduce<T, NR>(acc, red);
+    if (threadIdx.x < NRW * NR) {
+        const int r = threadIdx.x % NRW, c = threadIdx.x / NRW;
+        if (r < nrow && c < nrhs) dst[r + (int64_t)c * ldd] = tpre - sum;
+    }
+}
+
+// Partial reduction of t_B = y_B - L(rows below B, B)^T x(rows below) over the
+// rows [ks KSR, (ks + 1) KSR) of the "rows below" list, for the 64 columns
+// j0 = b0 + 64 cb ...: one warp per column (8 columns per warp), lanes over
+// rows; P[slot] holds the sums in the 64 x 32 tile layout ([rhs][column]).
+// item = (s, sb * 8 + cb, 65536 * ks, slot)
+template <class T, int NR>
+__global__ void __launch_bounds__(THREADS) breduce_narrow_kernel(DevSym d, const T *__restrict__ front,
+                                                                 const T *__restrict__ Y, T *__restrict__ P,
+                                                                 const int4 *__restrict__ items, int nrhs) {
+    constexpr int RC = TileS::ROWS, RR = TileS::RHS;     // P tile: RR right-hand sides x RC columns
+    __shared__ T xs[KSR * NR];
+    const int4 it = items[blockIdx.x];
+    const int s = it.x, sb = it.y >> 3, cb = it.y & 7, ks = it.z >> 16;
+    const int m = d.sm[s], k = d.sk[s], kp = d.skp[s], ld = d.sld[s];
+    const int b0 = sb * SB, w = min(SB, k - b0);
+    const int j0 = b0 + cb * RC, nb = min(RC, k - j0);
+    const int64_t n = d.n;
+    const T *F = front + d.foff[s] + (int64_t)j0 * ld;
+    const int32_t *rows = d.rows + d.rowptr[s];
+    const int nJ = k - (b0 + w), nbelow = nJ + (m - k);
+    const int u0 = ks * KSR, nu = min(nbelow, u0 + KSR) - u0;
+    for (int idx = threadIdx.x; idx < nu * NR; idx += THREADS) {
+        const int rr = idx / NR, c = idx % NR;
+        const int u = u0 + rr;
+        const int lr = u < nJ ? b0 + w + u : k + (u - nJ);
+        xs[idx] = c < nrhs ? Y[rows[lr] + (int64_t)c * n] : T(0);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *Pt = P + (int64_t)it.w * RR * RC;
+    for (int q = 0; q < RC / NWARP; ++q) {
+        const int cl = warp * (RC / NWARP) + q;
+        if (cl >= nb) break;
+        T acc[NR];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) acc[c] = T(0);
+        const T *col = F + (int64_t)cl * ld;
+#pragma unroll
+        for (int rr = lane; rr < KSR; rr += 32) {
+            if (rr < nu) {
+                const int u = u0 + rr;
+                const T a = col[u < nJ ? b0 + w + u : kp + (u - nJ)];
+#pragma unroll
+                for (int c = 0; c < NR; ++c) acc[c] += a * xs[rr * NR + c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+            T v = acc[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && c < nrhs) Pt[c * RC + cl] = v;
+        }
+    }
+}
+
 }  // namespace
 
 template <class T, class C>
@@ -568,8 +761,9 @@ void init_blocked_attributes() {
     done = true;
 }
 
-int solve_tile_rows(int large) { return large ? TileL::ROWS : TileS::ROWS; }
-int solve_tile_rhs(int large) { return large ? TileL::RHS : TileS::RHS; }
+int solve_tile_rows(int large) { return large == 1 ? TileL::ROWS : TileS::ROWS; }
+int solve_tile_rhs(int large) { return large == 1 ? TileL::RHS : TileS::RHS; }
+int solve_update_rows(int large) { return large == 2 ? NRW : solve_tile_rows(large); }
 
 template <class T>
 void launch_sbinv_diag(const DevSym &d, const T *dinv, T *xpool, const int64_t *xsoff, const int4 *items,
@@ -624,6 +818,13 @@ template <class T>
 void launch_xapply(const DevSym &d, const T *xp, const int64_t *xsoff, const T *in, T *out,
                    const int4 *items, int count, int upper, int large, int nrhs, cudaStream_t st) {
     if (count <= 0) return;
+    if (large == 2) {
+        if (nrhs == 1) xapply_narrow_kernel<T, 1><<<count, THREADS, 0, st>>>(d, xp, xsoff, in, out, items, upper, nrhs);
+        else if (nrhs == 2) xapply_narrow_kernel<T, 2><<<count, THREADS, 0, st>>>(d, xp, xsoff, in, out, items, upper, nrhs);
+        else if (nrhs <= 4) xapply_narrow_kernel<T, 4><<<count, THREADS, 0, st>>>(d, xp, xsoff, in, out, items, upper, nrhs);
+        else xapply_narrow_kernel<T, 8><<<count, THREADS, 0, st>>>(d, xp, xsoff, in, out, items, upper, nrhs);
+        return;
+    }
     if (large && sizeof(T) == 4) xapply_go<T, TileL>(d, xp, xsoff, in, out, items, count, upper, nrhs, st);
     else xapply_go<T, TileS>(d, xp, xsoff, in, out, items, count, upper, nrhs, st);
 }
@@ -631,6 +832,13 @@ template <class T>
 void launch_bupdate(const DevSym &d, const T *front, const T *Y, T *Tt, T *W, const int4 *items, int count,
                     int large, int nrhs, cudaStream_t st) {
     if (count <= 0) return;
+    if (large == 2) {
+        if (nrhs == 1) bupdate_narrow_kernel<T, 1><<<count, THREADS, 0, st>>>(d, front, Y, Tt, W, items, nrhs);
+        else if (nrhs == 2) bupdate_narrow_kernel<T, 2><<<count, THREADS, 0, st>>>(d, front, Y, Tt, W, items, nrhs);
+        else if (nrhs <= 4) bupdate_narrow_kernel<T, 4><<<count, THREADS, 0, st>>>(d, front, Y, Tt, W, items, nrhs);
+        else bupdate_narrow_kernel<T, 8><<<count, THREADS, 0, st>>>(d, front, Y, Tt, W, items, nrhs);
+        return;
+    }
     if (large && sizeof(T) == 4) bupdate_go<T, TileL>(d, front, Y, Tt, W, items, count, nrhs, st);
     else bupdate_go<T, TileS>(d, front, Y, Tt, W, items, count, nrhs, st);
 }
@@ -638,6 +846,13 @@ template <class T>
 void launch_breduce(const DevSym &d, const T *front, const T *Y, T *P, const int4 *items, int count,
                     int large, int nrhs, cudaStream_t st) {
     if (count <= 0) return;
+    if (large == 2) {
+        if (nrhs == 1) breduce_narrow_kernel<T, 1><<<count, THREADS, 0, st>>>(d, front, Y, P, items, nrhs);
+        else if (nrhs == 2) breduce_narrow_kernel<T, 2><<<count, THREADS, 0, st>>>(d, front, Y, P, items, nrhs);
+        else if (nrhs <= 4) breduce_narrow_kernel<T, 4><<<count, THREADS, 0, st>>>(d, front, Y, P, items, nrhs);
+        else breduce_narrow_kernel<T, 8><<<count, THREADS, 0, st>>>(d, front, Y, P, items, nrhs);
+        return;
+    }
     if (large && sizeof(T) == 4) breduce_go<T, TileL>(d, front, Y, P, items, count, nrhs, st);
     else breduce_go<T, TileS>(d, front, Y, P, items, count, nrhs, st);
 }
@@ -645,7 +860,7 @@ template <class T>
 void launch_breduce_finish(const DevSym &d, const T *Y, T *Tt, const T *P, const int4 *items, int count,
                            int large, int nrhs, cudaStream_t st) {
     if (count <= 0) return;
-    if (large && sizeof(T) == 4) finish_go<T, TileL>(d, Y, Tt, P, items, count, nrhs, st);
+    if (large == 1 && sizeof(T) == 4) finish_go<T, TileL>(d, Y, Tt, P, items, count, nrhs, st);
     else finish_go<T, TileS>(d, Y, Tt, P, items, count, nrhs, st);
 }
 
