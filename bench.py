@@ -47,19 +47,27 @@ TF32_PER_BF16 = 1.1 / 2.25
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
 # kernel from one ncu capture of the full-size command, keyed by (workload,
-# kernel), with the SHA-1 of the source file the kernel was built from:
-# reported as null once that file has changed (profiles/panel_2d256.md and
-# profiles/launches_2d256_mixed.md give the commands).
+# kernel, relax_k, relax_pct), with the SHA-1 of the source file the kernel
+# was built from: reported as null once that file has changed
+# (profiles/panel_2d256.md gives the commands).
 MEASURED_TRAFFIC = {
-    ("2d", "potrf_panel_fp32"): {"bytes": (286807552 + 143948032) / 124,
-                                 "source": "paper_2007_01541_gb300/csrc/front_kernels.cu",
-                                 "sha1": "efcff68576cc7dc2653dbf7a3d28b0533710c3e9"},
+    ("2d", "potrf_panel_fp32", 16, 10): {"bytes": (286807552 + 143948032) / 124,
+                                         "source": "paper_2007_01541_gb300/csrc/front_kernels.cu",
+                                         "sha1": "efcff68576cc7dc2653dbf7a3d28b0533710c3e9"},
 }
 
 
-def measured_traffic(workload, kernel):
+def amalgamation(args):
+    """(relax_k, relax_pct) in effect: the options given, else the library's defaults."""
+    from paper_2007_01541_gb300 import DEFAULTS
+    return (args.relax_k if args.relax_k is not None else DEFAULTS["relax_k"],
+            args.relax_pct if args.relax_pct is not None else DEFAULTS["relax_pct"])
+
+
+def measured_traffic(key, kernel):
     import hashlib
-    t = MEASURED_TRAFFIC.get((workload, kernel))
+    workload, relax = key
+    t = MEASURED_TRAFFIC.get((workload, kernel) + tuple(relax))
     if not t:
         return None
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), t["source"])
@@ -83,6 +91,10 @@ def parse():
                         "(N=16,384, for profiler captures); 1d: 1024 cells; batch: the 256 "
                         "independent 1D/2D instances (N 1024..16384), sharded over the ranks")
     p.add_argument("--batch-count", type=int, default=256)
+    p.add_argument("--relax-k", type=int, default=None,
+                   help="supernode amalgamation: merge while the width is <= this (library default if unset)")
+    p.add_argument("--relax-pct", type=int, default=None,
+                   help="supernode amalgamation: or while explicit zeros stay <= this percent")
     p.add_argument("--theta-steps", type=int, default=150,
                    help="theta workload: time steps per factorization")
     p.add_argument("--nrhs", type=int, default=None)
@@ -215,7 +227,17 @@ def load_peaks():
 
 
 # ---------------------------------------------------------------------------
-def roofline(top, nr, workload):
+def solver_opts(args, **kw):
+    """Solver options: the library's defaults unless --relax-k / --relax-pct are given."""
+    if args.relax_k is not None:
+        kw["relax_k"] = args.relax_k
+    if args.relax_pct is not None:
+        kw["relax_pct"] = args.relax_pct
+    return kw
+
+
+# ---------------------------------------------------------------------------
+def roofline(top, nr, key):
     """Roofline entry of the dominant kernel `top` (its accumulated launches,
     event time and algorithmic flops / bytes from the profiled replay)."""
     peaks = load_peaks()
@@ -228,7 +250,7 @@ def roofline(top, nr, workload):
         peak = bf16 * TF32_PER_BF16
         ach = top["flops"] / sec / 1e12
         return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": measured_traffic(workload, name), "kernel": name,
+                "traffic": measured_traffic(key, name), "kernel": name,
                 "peak_source": ("measured bf16 sustained %.1f x nominal tf32/bf16 1.1/2.25" % bf16)
                 if "bf16_tflops_sustained" in peaks else "fallback 1700 x nominal tf32/bf16 1.1/2.25",
                 "work": "2 k flops per updated lower entry (the 3xTF32 split's extra MMAs count against it)"}
@@ -241,7 +263,7 @@ def roofline(top, nr, workload):
         peak = SM_COUNT * FP32_LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
         ach = DF_OPS_PER_TERM * terms / sec / 1e12
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s (FP32 lane operations)",
-                "frac": ach / peak, "traffic": measured_traffic(workload, name), "kernel": name,
+                "frac": ach / peak, "traffic": measured_traffic(key, name), "kernel": name,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
                 "work": "12.75 FP32 operations per stored entry of A and right-hand side"}
     # the FP64 residual product with 8 or more right-hand sides does ~10 flops
@@ -254,13 +276,13 @@ def roofline(top, nr, workload):
         peak = SM_COUNT * per_clk * MAX_SM_MHZ * 1e6 / 1e12
         ach = top["flops"] / sec / 1e12
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": measured_traffic(workload, name), "kernel": name,
+                "traffic": measured_traffic(key, name), "kernel": name,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if not fp64
                 else "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz"}
     peak = peaks.get("hbm_gbs", 6800.0)
     ach = top["bytes"] / sec / 1e9
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": measured_traffic(workload, name), "kernel": name,
+            "traffic": measured_traffic(key, name), "kernel": name,
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
 
@@ -363,9 +385,9 @@ def run_ours(args):
     wdbuild.build()
     w = make_workload(args.workload, args.nrhs, "cuda")
     N, nr = w["basis"].N, w["nrhs"]
-    s = wd.Solver(profile=False).analyze(w["colptr"], w["rowidx"], w["basis"])
-    sp = None if args.no_replay else wd.Solver(profile=True).analyze(w["colptr"], w["rowidx"],
-                                                                      w["basis"])
+    s = wd.Solver(**solver_opts(args, profile=False)).analyze(w["colptr"], w["rowidx"], w["basis"])
+    sp = None if args.no_replay else wd.Solver(**solver_opts(args, profile=True)).analyze(
+        w["colptr"], w["rowidx"], w["basis"])
     info = s.info()
     flops_factor = info["flops_factor"]
     flops_solve = 4.0 * info["nnz_L"] * nr
@@ -436,7 +458,7 @@ def run_ours(args):
     top = max(kstats, key=lambda k: k["ms"]) if kstats else None
     roof = None
     if top:
-        roof = roofline(top, nr, args.workload)
+        roof = roofline(top, nr, (args.workload, amalgamation(args)))
         roof["launches_per_step"] = top["launches"] / args.steps
         roof["ms_per_launch"] = top["ms"] / max(1, top["launches"])
         roof["timing"] = ("CUDA events around every launch of this kernel during a profiled "
@@ -523,8 +545,9 @@ def run_theta(args):
     wdbuild.build()
     w = make_workload("theta", args.nrhs, "cuda")
     N, nr, T = w["basis"].N, w["nrhs"], args.theta_steps
-    s = wd.Solver().analyze(w["colptr"], w["rowidx"], w["basis"])
-    sp = None if args.no_replay else wd.Solver(profile=True).analyze(w["colptr"], w["rowidx"], w["basis"])
+    s = wd.Solver(**solver_opts(args)).analyze(w["colptr"], w["rowidx"], w["basis"])
+    sp = None if args.no_replay else wd.Solver(**solver_opts(args, profile=True)).analyze(
+        w["colptr"], w["rowidx"], w["basis"])
     info = s.info()
     nnz_a = 2 * int(w["rowidx"].size) - N
     flops_step = info["flops_factor"] + T * (4.0 * info["nnz_L"] + 2.0 * nnz_a) * nr
@@ -576,7 +599,7 @@ def run_theta(args):
     roof = None
     top = max(kstats, key=lambda k: k["ms"]) if kstats else None
     if top:
-        roof = roofline(top, nr, "theta")
+        roof = roofline(top, nr, ("theta", amalgamation(args)))
         roof["launches_per_step"] = top["launches"] / args.steps
         roof["ms_per_launch"] = top["ms"] / max(1, top["launches"])
     e2e = None
@@ -659,8 +682,9 @@ def run_batch(args):
     costs = instance_costs(pats, bases)
     idx = lpt_partition(costs, ws)[rank]
     w = batch_workload(params=[params[i] for i in idx], nrhs=1, seed=rank, device="cuda")
-    s = wd.Solver().analyze_batch(w.patterns, w.bases)
-    sp = None if args.no_replay else wd.Solver(profile=True).analyze_batch(w.patterns, w.bases)
+    s = wd.Solver(**solver_opts(args)).analyze_batch(w.patterns, w.bases)
+    sp = None if args.no_replay else wd.Solver(**solver_opts(args, profile=True)).analyze_batch(w.patterns,
+                                                                                              w.bases)
     info = s.info()
     flops_step = info["flops_factor"] + 4.0 * info["nnz_L"]
     vals = torch.tensor(np.concatenate(w.values), device="cuda")
@@ -702,7 +726,7 @@ def run_batch(args):
     roof = None
     top = max(kstats, key=lambda k: k["ms"]) if kstats else None
     if top:
-        roof = roofline(top, 1, "batch")
+        roof = roofline(top, 1, ("batch", amalgamation(args)))
         roof["launches_per_step"] = top["launches"] / args.steps
     e2e = None
     if not args.no_e2e:

@@ -64,7 +64,7 @@ typedef enum {
 
 typedef struct {
     int32_t nd_leaf;        /* ND stops at <= nd_leaf vertices (default 64)      */
-    int32_t relax_k;        /* amalgamation: merge while width <= relax_k (16)   */
+    int32_t relax_k;        /* amalgamation: merge while width <= relax_k (64)   */
     int32_t relax_pct;      /* ... or explicit zeros <= relax_pct % (10)         */
     int32_t ir_max_iter;    /* refinement steps in WD_MIXED (default 10)         */
     double ir_tol;          /* target normwise backward error (default 1e-12)    */

@@ -123,7 +123,7 @@ class Oracle:
     """Symbolic + numeric sparse Cholesky of a symmetric matrix given by its
     lower CSC (diagonal first in each column, rows sorted, 0-based)."""
 
-    def __init__(self, colptr, rowidx, basis=None, leaf: int = 64, relax_k: int = 16,
+    def __init__(self, colptr, rowidx, basis=None, leaf: int = 64, relax_k: int = 64,
                  relax_pct: int = 10, perm=None):
         self._lib = _load()
         self._ctx = ctypes.c_void_p(self._lib.or_create())

@@ -149,10 +149,17 @@ def _stream(stream, needed):
     return ctypes.c_void_p(0)
 
 
+# symbolic defaults (as wd_default_options): nested-dissection leaf size and
+# the relaxed amalgamation thresholds (merge a child into its parent while
+# the merged width is <= relax_k or the explicit zeros stay <= relax_pct %)
+DEFAULTS = {"nd_leaf": 64, "relax_k": 64, "relax_pct": 10}
+
+
 class Solver:
     """One sparse SPD system: analyze once, factor (re)peatedly, solve many."""
 
-    def __init__(self, nd_leaf=64, relax_k=16, relax_pct=10, ir_max_iter=10, ir_tol=1e-12,
+    def __init__(self, nd_leaf=DEFAULTS["nd_leaf"], relax_k=DEFAULTS["relax_k"],
+                 relax_pct=DEFAULTS["relax_pct"], ir_max_iter=10, ir_tol=1e-12,
                  symbolic_only=False, profile=False, use_graphs=True):
         self._lib = load()
         o = WdOptions()

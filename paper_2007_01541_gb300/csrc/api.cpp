@@ -229,7 +229,7 @@ void wd_default_options(wd_options *o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
     o->nd_leaf = 64;
-    o->relax_k = 16;
+    o->relax_k = 64;
     o->relax_pct = 10;
     o->ir_max_iter = 10;
     o->ir_tol = 1e-12;

@@ -241,7 +241,7 @@ def test_special_case_diagonal_and_tridiagonal():
     # tridiagonal in natural order: no fill, chain etree
     A = 4 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
     cp, ri, v = _dense_to_lower_csc(A)
-    o = oracle.Oracle(cp, ri)
+    o = oracle.Oracle(cp, ri, relax_k=16, relax_pct=10)
     assert o.nnzL == 2 * n - 1
     assert list(o.parent) == list(range(1, n)) + [-1]
     assert o.factor(v) == 0
@@ -249,6 +249,8 @@ def test_special_case_diagonal_and_tridiagonal():
     # the merge scan joins consecutive ones while the width stays <= 16
     # (width 17 would add 136 explicit zeros to a 170-entry trapezoid)
     assert list(o.super_first) == [0, 16, 32, 48, 50]
+    # with width 64 allowed the whole path is one supernode
+    assert list(oracle.Oracle(cp, ri, relax_k=64, relax_pct=10).super_first) == [0, 50]
 
 
 def test_supernode_rows_and_partition():

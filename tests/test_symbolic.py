@@ -14,8 +14,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _compare(wd, cp, ri, basis, **opt):
-    o = oracle.Oracle(cp, ri, basis, leaf=opt.get("nd_leaf", 64), relax_k=opt.get("relax_k", 16),
-                      relax_pct=opt.get("relax_pct", 10))
+    dflt = wd.DEFAULTS
+    o = oracle.Oracle(cp, ri, basis, leaf=opt.get("nd_leaf", dflt["nd_leaf"]),
+                      relax_k=opt.get("relax_k", dflt["relax_k"]), relax_pct=opt.get("relax_pct", dflt["relax_pct"]))
     s = wd.Solver(symbolic_only=True, **opt).analyze(cp, ri, basis)
     sy = s.symbolic()
     for key in ("perm", "parent", "colcount", "super_first", "super_rowptr", "super_rows"):
