@@ -229,6 +229,20 @@ def load_peaks():
 
 
 # ---------------------------------------------------------------------------
+def metric_name(args) -> str:
+    """The metric of a workload's line, the same for both arms."""
+    if args.workload == "batch":
+        return "factor+solve TFLOP/s of the batch (mixed+IR path) at backward error <= 1e-12"
+    if args.workload == "theta":
+        return (f"theta-scheme TFLOP/s (M factored once + {args.theta_steps} steps of product and refined "
+                f"solve, mixed+IR) at backward error <= 1e-12")
+    return "factor+solve TFLOP/s (mixed+IR path; FP64 path beside it) at backward error <= 1e-12"
+
+
+def batch_name(args) -> str:
+    return f"batch_{args.batch_count}_instances_1d2d_exp_nugget1e-2_1rhs"
+
+
 def solver_opts(args, **kw):
     """Solver options: the library's defaults unless --relax-k / --relax-pct are given."""
     if args.relax_k is not None:
@@ -361,11 +375,15 @@ def run_reference(args):
     value = flops * len(times) / tot / 1e12
     sample = (f"left-looking FP64 factor of the first {ncols} of {o.n} columns of P A P^T "
               f"(sum c_j^2 = {flops:.3e} flop, bottom of the elimination tree); solve not sampled")
-    line = {"impl": "reference", "metric": "factor+solve TFLOP/s (mixed+IR path)",
+    if args.workload == "batch":
+        sample = f"{w['name']} (the smallest of the batch): " + sample
+    line = {"impl": "reference", "metric": metric_name(args),
             "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot / len(times) * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["name"], "N": int(o.n), "sample": sample},
+            "scaling": "strong" if args.workload == "batch" else "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": batch_name(args) if args.workload == "batch" else w["name"],
+                       "N": int(o.n), "sample": sample},
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
@@ -507,7 +525,7 @@ def run_ours(args):
 
     if rank == 0:
         line = {
-            "metric": "factor+solve TFLOP/s (mixed+IR path; FP64 path beside it) at backward error <= 1e-12",
+            "metric": metric_name(args),
             "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -638,8 +656,7 @@ def run_theta(args):
                "sample": (f"left-looking FP64 factor of the first {ncols} of {o.n} columns of P M P^T "
                           f"({fl:.3e} flop) in {dt:.1f} s; time steps not sampled")}
     if rank == 0:
-        line = {"metric": f"theta-scheme TFLOP/s (M factored once + {T} steps of product and refined "
-                          f"solve, mixed+IR) at backward error <= 1e-12",
+        line = {"metric": metric_name(args),
                 "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms, "ms_factor": ms_factor, "ms_per_theta_step": (ms - ms_factor) / T, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -769,11 +786,11 @@ def run_batch(args):
                "kind": "oracle", "sample": f"left-looking FP64 factor of instance {i0} (N = {cp.size - 1}, "
                                             f"{costs[i0]:.3e} flop) in {dt:.2f} s; solve not sampled"}
     if rank == 0:
-        line = {"metric": "factor+solve TFLOP/s of the batch (mixed+IR path) at backward error <= 1e-12",
+        line = {"metric": metric_name(args),
                 "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
                 "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": f"batch_{args.batch_count}_instances_1d2d_exp_nugget1e-2_1rhs",
+                "config": {"workload": batch_name(args),
                            "instances": args.batch_count, "N_total": int(sum(p["N"] for p in params)),
                            "parallelism": f"lpt-shards x{ws}" if ws > 1 else "single",
                            "l2": "inputs larger than L2"},
