@@ -74,7 +74,7 @@ def test_factor_fp64_entries(wdlib, cuda, name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("nrhs", [1, 5, 33])
+@pytest.mark.parametrize("nrhs", [1, 2, 5, 33])
 def test_solve_fp64(wdlib, cuda, name, nrhs):
     b, cp, ri, v, o = _case(name)
     s = wdlib.Solver().analyze(cp, ri, b).factor(v, "fp64")
@@ -88,10 +88,11 @@ def test_solve_fp64(wdlib, cuda, name, nrhs):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-def test_solve_mixed_refined(wdlib, cuda, name):
+@pytest.mark.parametrize("nrhs", [2, 7])
+def test_solve_mixed_refined(wdlib, cuda, name, nrhs):
     b, cp, ri, v, o = _case(name)
     s = wdlib.Solver().analyze(cp, ri, b).factor(v, "mixed")
-    B = rhs(o.n, 7, seed=11)
+    B = rhs(o.n, nrhs, seed=11)
     X = s.solve(B)
     be = oracle.backward_error(cp, ri, v, X, B)
     assert be.max() <= 1e-12
