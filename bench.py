@@ -33,7 +33,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# derived ALU peaks (unit counts x maximum SM clock), see the design doc
+# derived ALU peaks: unit counts x maximum SM clock (152 SMs, 128 FP32 lanes
+# and 2 FP64 FMA units per SM on GB300, 2070 MHz)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 FP64_FLOPS_PER_SM_CLK = 4     # 2 FP64 FMA per SM per clock (GB300: 1.25 TFLOP/s nominal)

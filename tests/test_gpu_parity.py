@@ -1,6 +1,8 @@
 """CUDA path against the CPU oracle, through the C ABI (needs a GB300).
 
-Tolerances (derived from the arithmetic):
+Tolerances, derived from the arithmetic: FP64 factor entries differ from the
+oracle's only by summation order (a few thousand terms per entry, cond(A) up to
+~1e3), and the refinement target is a backward error of 1e-12:
   * FP64 factor: per column ||L_gpu(:,j) - L_or(:,j)||_2 <= 1e-10 ||L_or(:,j)||_2;
     amalgamation zeros stay exactly 0.
   * solves: normwise backward error <= 1e-12 per right-hand side, residual in
