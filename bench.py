@@ -94,6 +94,8 @@ def parse():
                         "(N=16,384, for profiler captures); 1d: 1024 cells; batch: the 256 "
                         "independent 1D/2D instances (N 1024..16384), sharded over the ranks")
     p.add_argument("--batch-count", type=int, default=256)
+    p.add_argument("--nd-leaf", type=int, default=None,
+                   help="nested dissection: leaf size (library default if unset)")
     p.add_argument("--relax-k", type=int, default=None,
                    help="supernode amalgamation: merge while the width is <= this (library default if unset)")
     p.add_argument("--relax-pct", type=int, default=None,
@@ -245,7 +247,9 @@ def batch_name(args) -> str:
 
 
 def solver_opts(args, **kw):
-    """Solver options: the library's defaults unless --relax-k / --relax-pct are given."""
+    """Solver options: the library's defaults unless --nd-leaf / --relax-k / --relax-pct are given."""
+    if args.nd_leaf is not None:
+        kw["nd_leaf"] = args.nd_leaf
     if args.relax_k is not None:
         kw["relax_k"] = args.relax_k
     if args.relax_pct is not None:
