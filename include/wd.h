@@ -63,7 +63,7 @@ typedef enum {
 } wd_precision;
 
 typedef struct {
-    int32_t nd_leaf;        /* ND stops at <= nd_leaf vertices (default 64)      */
+    int32_t nd_leaf;        /* ND stops at <= nd_leaf vertices (default 128)     */
     int32_t relax_k;        /* amalgamation: merge while width <= relax_k (64)   */
     int32_t relax_pct;      /* ... or explicit zeros <= relax_pct % (10)         */
     int32_t ir_max_iter;    /* refinement steps in WD_MIXED (default 10)         */

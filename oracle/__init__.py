@@ -99,7 +99,7 @@ def _geom(basis):
     return basis.dim, lev, lo, side, patch
 
 
-def nd_order(colptr, rowidx, basis, leaf: int = 64, want_tree: bool = False):
+def nd_order(colptr, rowidx, basis, leaf: int = 128, want_tree: bool = False):
     """Geometric nested dissection (perm[new] = old) and, optionally, the
     dissection nodes as rows (V1 start, V2 start, S start, S end)."""
     lib = _load()
@@ -123,7 +123,7 @@ class Oracle:
     """Symbolic + numeric sparse Cholesky of a symmetric matrix given by its
     lower CSC (diagonal first in each column, rows sorted, 0-based)."""
 
-    def __init__(self, colptr, rowidx, basis=None, leaf: int = 64, relax_k: int = 64,
+    def __init__(self, colptr, rowidx, basis=None, leaf: int = 128, relax_k: int = 64,
                  relax_pct: int = 10, perm=None):
         self._lib = _load()
         self._ctx = ctypes.c_void_p(self._lib.or_create())

@@ -152,7 +152,7 @@ def _stream(stream, needed):
 # symbolic defaults (as wd_default_options): nested-dissection leaf size and
 # the relaxed amalgamation thresholds (merge a child into its parent while
 # the merged width is <= relax_k or the explicit zeros stay <= relax_pct %)
-DEFAULTS = {"nd_leaf": 64, "relax_k": 64, "relax_pct": 10}
+DEFAULTS = {"nd_leaf": 128, "relax_k": 64, "relax_pct": 10}
 
 
 class Solver:

@@ -228,7 +228,7 @@ const char *wd_status_string(wd_status s) {
 void wd_default_options(wd_options *o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
-    o->nd_leaf = 64;
+    o->nd_leaf = 128;
     o->relax_k = 64;
     o->relax_pct = 10;
     o->ir_max_iter = 10;

@@ -88,15 +88,16 @@ def test_pattern_and_values_match_their_definitions():
 def test_patch_dissection_bitexact_and_separators(wdlib, J):
     b = sphere_basis(J)
     cp, ri = sphere_pattern(b)
-    s = wdlib.Solver(symbolic_only=True).analyze(cp, ri, b)
+    # leaf 64: the smallest sphere (96 vertices) is still dissected
+    s = wdlib.Solver(symbolic_only=True, nd_leaf=64).analyze(cp, ri, b)
     got = s.symbolic()
-    o = oracle.Oracle(cp, ri, b)
+    o = oracle.Oracle(cp, ri, b, leaf=64)
     assert np.array_equal(got["perm"], o.perm)
     assert np.array_equal(got["parent"], o.parent)
     assert np.array_equal(got["colcount"], o.colcount)
     assert np.array_equal(got["super_first"], o.super_first)
     assert np.array_equal(got["super_rows"], o.super_rows)
-    perm, tree = oracle.nd_order(cp, ri, b, want_tree=True)
+    perm, tree = oracle.nd_order(cp, ri, b, leaf=64, want_tree=True)
     assert np.array_equal(perm, o.perm)
     # the root node (recorded last) cuts patches {0, 1} from {2, 3, 4, 5}
     t0, t1, t2, t3 = tree[-1]
