@@ -48,22 +48,23 @@ TF32_PER_BF16 = 1.1 / 2.25
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
 # kernel from one ncu capture of the full-size command, keyed by (workload,
-# kernel, relax_k, relax_pct), with the SHA-1 of the source file the kernel
+# kernel, nd_leaf, relax_k, relax_pct), with the SHA-1 of the source file the kernel
 # was built from: reported as null once that file has changed
 # (profiles/panel_2d256.md gives the commands).
 MEASURED_TRAFFIC = {
-    ("2d", "potrf_panel_fp32", 16, 10): {"bytes": (286807552 + 143948032) / 124,
+    ("2d", "potrf_panel_fp32", 64, 16, 10): {"bytes": (286807552 + 143948032) / 124,
                                          "source": "paper_2007_01541_gb300/csrc/front_kernels.cu",
-                                         "sha1": "efcff68576cc7dc2653dbf7a3d28b0533710c3e9"},    ("2d", "potrf_panel_fp32", 64, 10): {"bytes": (289378048 + 112331776) / 117,
+                                         "sha1": "efcff68576cc7dc2653dbf7a3d28b0533710c3e9"},    ("2d", "potrf_panel_fp32", 64, 64, 10): {"bytes": (289378048 + 112331776) / 117,
                                          "source": "paper_2007_01541_gb300/csrc/front_kernels.cu",
                                          "sha1": "efcff68576cc7dc2653dbf7a3d28b0533710c3e9"},
 }
 
 
 def amalgamation(args):
-    """(relax_k, relax_pct) in effect: the options given, else the library's defaults."""
+    """(nd_leaf, relax_k, relax_pct) in effect: the options given, else the library's defaults."""
     from paper_2007_01541_gb300 import DEFAULTS
-    return (args.relax_k if args.relax_k is not None else DEFAULTS["relax_k"],
+    return (args.nd_leaf if args.nd_leaf is not None else DEFAULTS["nd_leaf"],
+            args.relax_k if args.relax_k is not None else DEFAULTS["relax_k"],
             args.relax_pct if args.relax_pct is not None else DEFAULTS["relax_pct"])
 
 
