@@ -1,0 +1,53 @@
+"""Host logic of bench.py (no GPU): both arms name the same metric per
+workload, the roofline classification of the dominant kernel, and measured
+DRAM traffic applied only at the settings (workload, ND leaf, amalgamation)
+and the kernel source it was captured with."""
+import types
+
+import pytest
+
+import bench
+
+
+def _args(**kw):
+    a = dict(workload="2d", theta_steps=150, batch_count=256, nd_leaf=None, relax_k=None, relax_pct=None)
+    a.update(kw)
+    return types.SimpleNamespace(**a)
+
+
+def test_metric_names_per_workload():
+    names = {w: bench.metric_name(_args(workload=w)) for w in ("2d", "batch", "theta")}
+    assert len(set(names.values())) == 3
+    assert "150 steps" in names["theta"] and "batch" in names["batch"]
+    assert bench.batch_name(_args()) == "batch_256_instances_1d2d_exp_nugget1e-2_1rhs"
+
+
+def test_amalgamation_defaults_and_overrides(wdlib):
+    d = wdlib.DEFAULTS
+    assert bench.amalgamation(_args()) == (d["nd_leaf"], d["relax_k"], d["relax_pct"])
+    assert bench.amalgamation(_args(nd_leaf=64, relax_k=16, relax_pct=10)) == (64, 16, 10)
+
+
+def test_roofline_classification(monkeypatch):
+    monkeypatch.setattr(bench, "load_peaks", lambda: {"hbm_gbs": 6000.0, "bf16_tflops_sustained": 1800.0})
+    key = ("2d", (128, 64, 10))
+    tc = bench.roofline({"name": "tc_schur_syrk_fp32", "ms": 1000.0, "flops": 84e12, "bytes": 0}, 64, key)
+    assert tc["bound"] == "tensor"
+    assert tc["peak"] == pytest.approx(1800.0 * 1.1 / 2.25)
+    assert tc["achieved"] == pytest.approx(84.0)
+    alu = bench.roofline({"name": "potrf_panel_fp32", "ms": 1000.0, "flops": 8e12, "bytes": 0}, 64, key)
+    assert alu["bound"] == "alu" and alu["peak"] == pytest.approx(152 * 256 * 2070e6 / 1e12)
+    df = bench.roofline({"name": "spmv_residual_df", "ms": 1000.0, "flops": 2e12, "bytes": 0}, 64, key)
+    assert df["achieved"] == pytest.approx(bench.DF_OPS_PER_TERM * 1.0)
+    hbm = bench.roofline({"name": "fwd_gather_fp32", "ms": 1000.0, "flops": 0, "bytes": 3e12}, 64, key)
+    assert hbm["bound"] == "hbm" and hbm["frac"] == pytest.approx(0.5)
+
+
+def test_measured_traffic_only_where_it_was_taken(monkeypatch):
+    t = bench.MEASURED_TRAFFIC[("2d", "potrf_panel_fp32", 64, 64, 10)]
+    assert bench.measured_traffic(("2d", (64, 64, 10)), "potrf_panel_fp32") in (t["bytes"], None)
+    assert bench.measured_traffic(("2d", (128, 64, 10)), "potrf_panel_fp32") is None
+    assert bench.measured_traffic(("batch", (64, 64, 10)), "potrf_panel_fp32") is None
+    # a changed source file voids the figure
+    monkeypatch.setitem(bench.MEASURED_TRAFFIC, ("2d", "potrf_panel_fp32", 64, 64, 10), dict(t, sha1="0" * 40))
+    assert bench.measured_traffic(("2d", (64, 64, 10)), "potrf_panel_fp32") is None
