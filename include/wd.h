@@ -130,7 +130,9 @@ void wd_destroy(wd_handle h);
    nested-dissection permutation (Section 4), the elimination tree, column
    counts, supernodes with relaxed amalgamation, extend-add maps and the level
    schedule, and upload the index arrays.  Synchronous.  colptr/rowidx are
-   host arrays.  geom may be NULL: then the identity order is used. */
+   host arrays.  geom may be NULL: then the identity order is used.  Limits:
+   n < 2^31 - 1 and at most 2^31 - 1 entries in the full symmetric matrix
+   (2 nnz - n), else WD_ERR_INVALID_ARG; the same for a batch's total. */
 wd_status wd_analyze(wd_handle h, int64_t n, const int64_t *colptr, const int32_t *rowidx,
                      const wd_geometry *geom);
 

@@ -184,8 +184,9 @@ int analyze(Symbolic &S, int64_t n, const int64_t *cp, const int32_t *ri, int di
             }
     }
     const int64_t nnz = cp[n];
-    if (nnz > INT32_MAX) {
-        msg = "more than 2^31-1 stored entries";
+    // the full symmetric CSR (2 nnz - n entries) is indexed with 32-bit positions
+    if (nnz > INT32_MAX || 2 * nnz - n > INT32_MAX) {
+        msg = "more than 2^31-1 entries in the full symmetric matrix";
         return ERR_INVALID_ARG;
     }
     S.n = n;
@@ -452,7 +453,8 @@ int merge(Symbolic &S, const std::vector<const Symbolic *> &parts, std::string &
         ns += P->ns;
         nlev = std::max(nlev, P->nlevels);
     }
-    if (n > INT32_MAX || nnz > INT32_MAX || ns > INT32_MAX || nrows > INT64_MAX / 2) {
+    if (n > INT32_MAX || nnz > INT32_MAX || 2 * nnz - n > INT32_MAX || ns > INT32_MAX ||
+        nrows > INT64_MAX / 2) {
         msg = "batch too large for 32-bit column / value indices";
         return ERR_INVALID_ARG;
     }
