@@ -14,6 +14,12 @@ far larger than L2, so no L2 flush is needed between steps.
 value = (sum_j c_j^2 + 4 nnz(L) nrhs) / step time, in TFLOP/s, for the mixed
 path.  The FP64 path is measured the same way and reported beside it.
 
+Other workloads (--workload): batch (256 independent 1D / 2D instances, one
+right-hand side each, sharded over ranks by longest-processing-time; strong
+scaling), theta (the theta-scheme: M = I + theta dt K factored once, then
+--theta-steps steps of product and refined solve, one right-hand side),
+2d_small and 1d (smaller cases for profiling).
+
 --impl reference times the CPU oracle (plain left-looking FP64 Cholesky) on
 the host cores, on a bounded prefix of the same factorization.
 """
