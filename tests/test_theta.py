@@ -100,3 +100,24 @@ def test_theta_steps_against_the_oracle(wdlib, cuda, name, prec, nrhs, theta):
     scale = np.abs(Uo).max()
     assert np.abs(Uh - Uo).max() <= 1e-10 * scale
     assert np.abs(Ud.cpu().numpy() - Uo).max() <= 1e-10 * scale
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_theta_step_without_source_and_with_zero_dt(wdlib, cuda, prec):
+    """F = NULL follows the oracle's source-free step; dt = 0 makes M = I and
+    leaves U unchanged."""
+    b, cp, ri, k = _case("1d_J10")
+    n = cp.size - 1
+    U0 = rhs(n, 2, seed=7)
+    theta, dt = 0.5, 0.1
+    m = oracle.theta_matrix(cp, k, theta, dt)
+    o = oracle.Oracle(cp, ri, b)
+    assert o.factor(m) == 0
+    s = wdlib.Solver().analyze(cp, ri, b).factor(m, prec)
+    U = s.theta_step(U0, None, theta=theta, dt=dt)
+    Uo = oracle.theta_step(o, cp, ri, k, U0, None, theta, dt)
+    assert np.abs(U - Uo).max() <= 1e-10 * np.abs(Uo).max()
+    s0 = wdlib.Solver().analyze(cp, ri, b).factor(oracle.theta_matrix(cp, k, theta, 0.0), prec)
+    U1 = s0.theta_step(U0, rhs(n, 2, seed=8), theta=theta, dt=0.0)
+    assert np.abs(U1 - U0).max() <= 1e-13 * np.abs(U0).max()
