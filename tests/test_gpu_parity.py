@@ -264,3 +264,22 @@ def test_backward_error_call_matches_fp64_residual(wdlib, cuda, nrhs, prec):
         ref = oracle.backward_error(cp, ri, v, Xp, B).max()
         got = s.backward_error(Xp, B)
         assert abs(got - ref) <= 1e-6 * ref + 2e-15, (scale, got, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("nrhs", [3, 40])
+def test_solve_device_padded_leading_dimension(wdlib, cuda, prec, nrhs):
+    """A column-major device B with leading dimension n + 5: the solution lands
+    in the first n rows of every column and the padding is left untouched."""
+    torch = cuda
+    b, cp, ri, v, o = _case("2d_J6")
+    s = wdlib.Solver().analyze(cp, ri, b).factor(v, prec)
+    B = rhs(o.n, nrhs, seed=21)
+    store = torch.full((nrhs, o.n + 5), 7.0, dtype=torch.float64, device="cuda")
+    store[:, : o.n] = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    view = store[:, : o.n].T                      # n x nrhs, stride (1, n + 5)
+    assert view.stride() == (1, o.n + 5)
+    s.solve(view)
+    X = view.cpu().numpy()
+    assert oracle.backward_error(cp, ri, v, X, B).max() <= 1e-12
+    assert torch.all(store[:, o.n:] == 7.0)
