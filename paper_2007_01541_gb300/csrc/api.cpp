@@ -61,7 +61,7 @@ struct Plan {
     std::vector<Launch> launches;
     int4 *d_items = nullptr;
     int rgt = 16;            // solve plans: right-hand sides per gather CTA
-    int large = 0;           // solve plans: 128 x 64 product tiles (else 64 x 32)
+    int large = 0;           // solve plans: product mode (0: 64 x 32 tiles, 2: few right-hand sides)
     int64_t slots = 0;       // solve plans: partial-sum slots of the largest split step
 };
 
@@ -1404,9 +1404,8 @@ static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cud
 static wd_status prepare_solve(wd_handle h, int64_t nrhs) {
     wd_status s = ensure_solve_ws(h, nrhs);
     if (s != WD_OK) return s;
-    // 64 x 32 tiles: on the 2D 256^2 case the 128 x 64 tiles lost more to the
-    // halved CTA count of the narrow tree levels than they gained per tile;
-    // up to 8 right-hand sides: matrix-vector shaped kernels, lanes over rows
+    // tiles of 64 rows x 32 right-hand sides; up to 8 right-hand sides:
+    // matrix-vector shaped kernels, lanes over rows
     const int large = nrhs <= 8 ? 2 : 0;
     if (h->splan_nrhs != nrhs || h->splan.large != large) {
         build_solve_plan(h->S, (int)nrhs, large, h->splan);

@@ -193,15 +193,14 @@ void launch_sbinv_transpose(const DevSym &d, const T *xpool, T *xtpool, const in
 template <class T>
 void launch_bfwd_gather(const DevSym &d, const T *Y, T *Tt, T *W, const int4 *items, int count, int rgt,
                         int nrhs, cudaStream_t st);
-// xapply / bupdate / breduce tiles: large = 0 -> 64 rows x 32 right-hand
-// sides per CTA, large = 1 -> 128 x 64 (FP32 only), large = 2 -> up to 8
-// right-hand sides, matrix-vector shaped (32 rows per xapply / bupdate CTA,
-// lanes over rows; breduce keeps the 64-column items and the 64 x 32 partial
-// layout of large = 0); the partial-sum tile sizes:
+// xapply / bupdate / breduce modes ("large"): 0 -> tiles of 64 rows x 32
+// right-hand sides per CTA; 2 -> up to 8 right-hand sides, matrix-vector
+// shaped (32 rows per xapply / bupdate CTA, lanes over rows; breduce keeps the
+// 64-column items and the 64 x 32 partial layout of mode 0); the partial-sum
+// tile sizes (the same for both modes):
 int solve_tile_rows(int large);
 int solve_tile_rhs(int large);
-// rows per CTA of the xapply / bupdate items (large: 0 = 64 x 32 tiles,
-// 1 = 128 x 64 tiles, 2 = few right-hand sides, 32 rows and lanes over rows)
+// rows per CTA of the xapply / bupdate items (mode 0: 64, mode 2: 32)
 int solve_update_rows(int large);
 template <class T>
 void launch_xapply(const DevSym &d, const T *xp, const int64_t *xsoff, const T *in, T *out,

@@ -230,8 +230,9 @@ __global__ void __launch_bounds__(THREADS) bfwd_gather_kernel(DevSym d, const T 
 // with rows contiguous (A[p * lda + row]) and read by a whole warp at once
 // (broadcast 16-byte loads), the right-hand-side tile is staged right-hand-
 // side major with an odd stride (R[c * LDR + p]), so both the staging writes
-// and the reads are free of bank conflicts.  Two shapes: 64 x 32 (few
-// right-hand sides, FP64) and 128 x 64 (FP32 with 64 or more).
+// and the reads are free of bank conflicts.  The shape in use is 64 x 32 (8
+// rows per warp, one right-hand side per lane); 128 x 64 tiles measured slower
+// on the 2D 256^2 case (half the CTAs on the narrow tree levels).
 template <int RPW_, int RPL_>
 struct TileCfg {
     static constexpr int RPW = RPW_;
@@ -242,7 +243,6 @@ struct TileCfg {
     static constexpr int MINB = RPW * RPL > 8 ? 2 : 4;   // resident CTAs per SM (register budget)
 };
 using TileS = TileCfg<8, 1>;
-using TileL = TileCfg<16, 2>;
 constexpr int LDR = NB + 1;                  // stride of a staged right-hand side
 
 template <class T, class C, int LDA>
@@ -756,13 +756,12 @@ void init_blocked_attributes() {
     static bool done = false;
     if (done) return;
     set_blocked_attributes<float, TileS>();
-    set_blocked_attributes<float, TileL>();
     set_blocked_attributes<double, TileS>();
     done = true;
 }
 
-int solve_tile_rows(int large) { return large == 1 ? TileL::ROWS : TileS::ROWS; }
-int solve_tile_rhs(int large) { return large == 1 ? TileL::RHS : TileS::RHS; }
+int solve_tile_rows(int) { return TileS::ROWS; }
+int solve_tile_rhs(int) { return TileS::RHS; }
 int solve_update_rows(int large) { return large == 2 ? NRW : solve_tile_rows(large); }
 
 template <class T>
@@ -825,8 +824,7 @@ void launch_xapply(const DevSym &d, const T *xp, const int64_t *xsoff, const T *
         else xapply_narrow_kernel<T, 8><<<count, THREADS, 0, st>>>(d, xp, xsoff, in, out, items, upper, nrhs);
         return;
     }
-    if (large && sizeof(T) == 4) xapply_go<T, TileL>(d, xp, xsoff, in, out, items, count, upper, nrhs, st);
-    else xapply_go<T, TileS>(d, xp, xsoff, in, out, items, count, upper, nrhs, st);
+    xapply_go<T, TileS>(d, xp, xsoff, in, out, items, count, upper, nrhs, st);
 }
 template <class T>
 void launch_bupdate(const DevSym &d, const T *front, const T *Y, T *Tt, T *W, const int4 *items, int count,
@@ -839,8 +837,7 @@ void launch_bupdate(const DevSym &d, const T *front, const T *Y, T *Tt, T *W, co
         else bupdate_narrow_kernel<T, 8><<<count, THREADS, 0, st>>>(d, front, Y, Tt, W, items, nrhs);
         return;
     }
-    if (large && sizeof(T) == 4) bupdate_go<T, TileL>(d, front, Y, Tt, W, items, count, nrhs, st);
-    else bupdate_go<T, TileS>(d, front, Y, Tt, W, items, count, nrhs, st);
+    bupdate_go<T, TileS>(d, front, Y, Tt, W, items, count, nrhs, st);
 }
 template <class T>
 void launch_breduce(const DevSym &d, const T *front, const T *Y, T *P, const int4 *items, int count,
@@ -853,15 +850,13 @@ void launch_breduce(const DevSym &d, const T *front, const T *Y, T *P, const int
         else breduce_narrow_kernel<T, 8><<<count, THREADS, 0, st>>>(d, front, Y, P, items, nrhs);
         return;
     }
-    if (large && sizeof(T) == 4) breduce_go<T, TileL>(d, front, Y, P, items, count, nrhs, st);
-    else breduce_go<T, TileS>(d, front, Y, P, items, count, nrhs, st);
+    breduce_go<T, TileS>(d, front, Y, P, items, count, nrhs, st);
 }
 template <class T>
 void launch_breduce_finish(const DevSym &d, const T *Y, T *Tt, const T *P, const int4 *items, int count,
-                           int large, int nrhs, cudaStream_t st) {
+                           int, int nrhs, cudaStream_t st) {
     if (count <= 0) return;
-    if (large == 1 && sizeof(T) == 4) finish_go<T, TileL>(d, Y, Tt, P, items, count, nrhs, st);
-    else finish_go<T, TileS>(d, Y, Tt, P, items, count, nrhs, st);
+    finish_go<T, TileS>(d, Y, Tt, P, items, count, nrhs, st);
 }
 
 #define WD_BLOCKED_INST(T)                                                                              \
