@@ -51,3 +51,13 @@ def test_measured_traffic_only_where_it_was_taken(monkeypatch):
     # a changed source file voids the figure
     monkeypatch.setitem(bench.MEASURED_TRAFFIC, ("2d", "potrf_panel_fp32", 64, 64, 10), dict(t, sha1="0" * 40))
     assert bench.measured_traffic(("2d", (64, 64, 10)), "potrf_panel_fp32") is None
+
+
+def test_batch_cpu_baseline_runs_the_oracle_in_parallel_processes():
+    spec = {"dim": 1, "J": 10, "ell": 0.2, "nugget": 1e-2}
+    params = [dict(spec), dict(spec, ell=0.3), dict(spec, J=9)]
+    costs = [2.0, 3.0, 1.0]
+    r = bench.batch_cpu_baseline(params, costs, 2)
+    assert r is not None and r["cores"] == 2 and r["kind"] == "oracle"
+    assert r["value"] > 0 and r["per_process"] > 0
+    assert "(1, 10)" in r["sample"] and "(1, 9)" not in r["sample"]   # the two most expensive
