@@ -36,13 +36,6 @@ constexpr int BM = SCHUR_BM;   // rows of a Schur tile
 constexpr int BN = SCHUR_BN;   // columns of a Schur tile
 constexpr int BK = 32;         // inner-dimension chunk
 
-template <class T>
-__device__ __forceinline__ T dev_sqrt(T x);
-template <>
-__device__ __forceinline__ double dev_sqrt<double>(double x) { return sqrt(x); }
-template <>
-__device__ __forceinline__ float dev_sqrt<float>(float x) { return sqrtf(x); }
-
 // pivot d > 0 -> (sqrt(d), 1/sqrt(d)).  FP64: correctly rounded square root
 // and division.  FP32 (the refined mixed-precision path): the hardware
 // reciprocal square root, which keeps the serial pivot chain short; its few

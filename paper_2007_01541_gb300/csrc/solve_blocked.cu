@@ -22,8 +22,6 @@ namespace wd {
 namespace {
 
 constexpr int THREADS = 256;
-constexpr int RG = 16;      // right-hand sides per CTA
-constexpr int TR = 64;      // rows per CTA
 
 // ---------------------------------------------------------------------------
 // super-block inverses
