@@ -95,3 +95,102 @@ def test_two_ranks_share_the_batch(wdlib):
     counts, ok = q.get(timeout=10)
     assert counts == [1] * 12          # every instance on exactly one rank
     assert ok == 1
+
+
+def _subtree_worker(rank, ws, port, outq):
+    """One matrix split by nested-dissection subtrees: every rank takes its
+    subtrees' blocks A_TT (dense FP64 here) and sends the Schur complements
+    A_BT A_TT^-1 A_TB onto their boundary rows to rank 0, which assembles the
+    top block; log det A = sum_T log det A_TT + log det S checks the plan."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws))
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    import paper_2007_01541_gb300 as wd
+    from paper_2007_01541_gb300.shard import subtree_partition
+    from wdgen import Kernel, compressed_values
+
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    b = haar_basis(2, 5)
+    cp, ri = compressed_pattern(b)
+    v = compressed_values(b, cp, ri, Kernel("matern32", 0.1), 1e-3)
+    sym = wd.Solver(symbolic_only=True).analyze(cp, ri, b).symbolic()
+    part = subtree_partition(sym, ws)
+    perm = sym["perm"]
+    A = oracle.sym_lower_to_dense(cp, ri, v)[np.ix_(perm, perm)]
+    n = A.shape[0]
+    covered = np.zeros(n, bool)
+    for _, c0, c1, _, _ in part["subtrees"]:
+        covered[c0:c1] = True
+    top = np.nonzero(~covered)[0]
+    pos = np.full(n, -1)
+    pos[top] = np.arange(top.size)
+    ok = True
+    local_ld = 0.0
+    S = A[np.ix_(top, top)].copy() if rank == 0 else None
+    for root, c0, c1, r, _ in part["subtrees"]:
+        B = part["boundary"][root]
+        ok &= bool(np.all(pos[B] >= 0))                         # boundary rows lie in the top part
+        if r == rank:
+            T = np.arange(c0, c1)
+            Lt = np.linalg.cholesky(A[np.ix_(T, T)])
+            local_ld += 2.0 * np.log(np.diag(Lt)).sum()
+            W = np.linalg.solve(Lt, A[np.ix_(T, B)])
+            U = torch.from_numpy(W.T @ W)                       # A_BT A_TT^-1 A_TB
+            ok &= U.shape[0] * (U.shape[0] + 1) // 2 == part["send_entries"][root]
+            if rank != 0:
+                dist.send(U, dst=0)
+        if rank == 0:
+            if r != 0:
+                U = torch.empty((B.size, B.size), dtype=torch.float64)
+                dist.recv(U, src=r)
+            S[np.ix_(pos[B], pos[B])] -= U.numpy()
+    ld = torch.tensor([local_ld], dtype=torch.float64)
+    dist.all_reduce(ld)
+    flag = torch.tensor([1 if ok else 0])
+    dist.all_reduce(flag, op=dist.ReduceOp.MIN)
+    if rank == 0:
+        total = float(ld.item()) + 2.0 * np.log(np.diag(np.linalg.cholesky(S))).sum()
+        o = oracle.Oracle(cp, ri, b)
+        assert o.factor(v) == 0
+        outq.put((total, o.logdet(), int(flag.item()), [s[3] for s in part["subtrees"]]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_partition_of_one_matrix_by_subtrees(wdlib):
+    b = haar_basis(2, 5)
+    cp, ri = compressed_pattern(b)
+    from paper_2007_01541_gb300.shard import subtree_partition
+    sym = wdlib.Solver(symbolic_only=True).analyze(cp, ri, b).symbolic()
+    for nr in (1, 2, 3):
+        p = subtree_partition(sym, nr)
+        p2 = subtree_partition(sym, nr)                      # deterministic
+        assert p["subtrees"] == p2["subtrees"] and np.array_equal(p["owner"], p2["owner"])
+        ranges = sorted((c0, c1) for _, c0, c1, _, _ in p["subtrees"])
+        assert all(a[1] <= c[0] for a, c in zip(ranges, ranges[1:]))   # disjoint column ranges
+        assert {s[3] for s in p["subtrees"]} <= set(range(nr))
+        for root, c0, c1, r, _ in p["subtrees"]:
+            sf = sym["super_first"]
+            inside = (sf[:-1] >= c0) & (sf[1:] <= c1)
+            assert np.all(p["owner"][inside] == r)
+            assert np.all(p["boundary"][root] >= c1)                   # rows after the subtree
+
+
+def test_two_ranks_factor_one_matrix_by_subtrees(wdlib):
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_subtree_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+    assert all(p.exitcode == 0 for p in procs)
+    total, ref, ok, ranks = q.get(timeout=10)
+    assert ok == 1
+    assert set(ranks) == {0, 1}                  # both ranks own subtrees
+    assert abs(total - ref) <= 1e-10 * abs(ref), (total, ref)
