@@ -306,3 +306,23 @@ def test_backward_error_definition():
     be = oracle.backward_error(cp, ri, v, x, b)
     # ||A||_inf = 4, ||x|| = 1, ||b|| = 4.5
     assert abs(be[0] - 0.5 / (4.0 + 4.5)) < 1e-16
+
+
+def _amalgamation_cases():
+    g = json.load(open(os.path.join(GOLDEN, "amalgamation.json")))
+    return [(c, r) for c in g["cases"] for r in c["runs"]]
+
+
+@pytest.mark.parametrize("case,run", _amalgamation_cases(),
+                         ids=[f"{c['name'][:4]}-k{r['relax_k']}-p{r['relax_pct']}" for c, r in _amalgamation_cases()])
+def test_amalgamation_percentage_branch(case, run):
+    """Hand-worked merges decided by the explicit-zero percentage (the width
+    threshold lies below every merged width), one run just below and one just
+    above each threshold: an off-by-one in the trapezoid or in the zero count
+    moves a threshold across one of them."""
+    a = case["lower_csc"]
+    o = oracle.Oracle(a["colptr"], a["rowidx"], relax_k=run["relax_k"], relax_pct=run["relax_pct"])
+    assert list(o.perm) == list(range(len(a["colptr"]) - 1))
+    assert list(o.parent) == case["parent"]
+    assert list(o.colcount) == case["colcount"]
+    assert list(o.super_first) == run["super_first"]

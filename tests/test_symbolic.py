@@ -147,3 +147,20 @@ def test_batch_analysis_rejects_bad_instance(wdlib):
     with pytest.raises(wdlib.WdError) as e:
         s.analyze_batch([(cp, ri), (bad, ri)], [b, b])
     assert "instance 1" in str(e.value)
+
+
+def test_symbolic_amalgamation_golden(wdlib):
+    """The library's merge scan on the hand-worked amalgamation cases."""
+    import json
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "amalgamation.json")))
+    for case in g["cases"]:
+        a = case["lower_csc"]
+        cp = np.array(a["colptr"], np.int64)
+        ri = np.array(a["rowidx"], np.int32)
+        for run in case["runs"]:
+            s = wdlib.Solver(symbolic_only=True, relax_k=run["relax_k"],
+                             relax_pct=run["relax_pct"]).analyze(cp, ri)
+            sy = s.symbolic()
+            assert list(sy["parent"]) == case["parent"]
+            assert list(sy["colcount"]) == case["colcount"]
+            assert list(sy["super_first"]) == run["super_first"], (case["name"], run)
