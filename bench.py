@@ -20,8 +20,10 @@ scaling), theta (the theta-scheme: M = I + theta dt K factored once, then
 --theta-steps steps of product and refined solve, one right-hand side),
 2d_small and 1d (smaller cases for profiling).
 
---impl reference times the CPU oracle (plain left-looking FP64 Cholesky) on
-the host cores, on a bounded prefix of the same factorization.
+--impl reference times the CPU oracle (plain left-looking FP64 Cholesky and
+the substitutions) on one host core, each step a bounded share of the same
+factorization and solve: the factor of the first columns of P A P^T and both
+substitutions over them.
 """
 from __future__ import annotations
 
@@ -39,12 +41,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# derived ALU peaks: unit counts x maximum SM clock (152 SMs, 128 FP32 lanes
-# and 2 FP64 FMA units per SM on GB300, 2070 MHz)
-SM_COUNT = 152
+# derived ALU peaks: unit counts per SM x the device's SM count x its maximum
+# SM clock (both read from the device at run time, see device_units)
 FP32_LANES_PER_SM = 128
 FP64_FLOPS_PER_SM_CLK = 4     # 2 FP64 FMA per SM per clock (GB300: 1.25 TFLOP/s nominal)
-MAX_SM_MHZ = 2070.0
 THETA, THETA_DT = 0.5, 1e-2      # theta workload: Crank-Nicolson, time step
 DF_OPS_PER_TERM = 12.75       # FP32 instructions per double-float multiply-add (12, plus a 6-op TwoSum every 8 terms)
 
@@ -53,17 +53,10 @@ DF_OPS_PER_TERM = 12.75       # FP32 instructions per double-float multiply-add 
 TF32_PER_BF16 = 1.1 / 2.25
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
-# kernel from one ncu capture of the full-size command, keyed by (workload,
-# kernel, nd_leaf, relax_k, relax_pct), with the SHA-1 of the source file the kernel
-# was built from: reported as null once that file has changed
-# (profiles/panel_2d256.md gives the commands).
-MEASURED_TRAFFIC = {
-    ("2d", "potrf_panel_fp32", 64, 16, 10): {"bytes": (286807552 + 143948032) / 124,
-                                         "source": "paper_2007_01541_gb300/csrc/front_kernels.cu",
-                                         "sha1": "efcff68576cc7dc2653dbf7a3d28b0533710c3e9"},    ("2d", "potrf_panel_fp32", 64, 64, 10): {"bytes": (289378048 + 112331776) / 117,
-                                         "source": "paper_2007_01541_gb300/csrc/front_kernels.cu",
-                                         "sha1": "efcff68576cc7dc2653dbf7a3d28b0533710c3e9"},
-}
+# kernel from one ncu capture, keyed by (workload, kernel, nd_leaf, relax_k,
+# relax_pct), with the SHA-1 of the source file the kernel was built from:
+# reported as null once that file has changed.
+MEASURED_TRAFFIC = {}
 
 
 def amalgamation(args):
@@ -80,7 +73,7 @@ def measured_traffic(key, kernel):
     t = MEASURED_TRAFFIC.get((workload, kernel) + tuple(relax))
     if not t:
         return None
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), t["source"])
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), t["source"])   # absolute paths stay
     try:
         with open(path, "rb") as f:
             if hashlib.sha1(f.read()).hexdigest() != t["sha1"]:
@@ -231,6 +224,54 @@ def gpu_id_for_smi():
     return v.split(",")[0] if v else None
 
 
+_UNITS = {}
+
+
+def device_units():
+    """(SM count, maximum SM clock in MHz, where the clock came from) of the
+    current device: the SM count from the CUDA device properties, the clock
+    from nvidia-smi (clocks.max.sm), else from MEASURED_PEAKS.json."""
+    if _UNITS:
+        return _UNITS["sms"], _UNITS["mhz"], _UNITS["src"]
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz, src = None, None
+    try:
+        cmd = ["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"]
+        g = gpu_id_for_smi()
+        if g:
+            cmd += ["-i", g]
+        out = subprocess.run(cmd, capture_output=True, text=True, timeout=20).stdout.split()
+        mhz, src = float(out[0]), "nvidia-smi clocks.max.sm"
+    except Exception:
+        pass
+    if mhz is None:
+        mhz = load_peaks().get("sm_max_mhz")
+        src = "MEASURED_PEAKS.json sm_max_mhz" if mhz else None
+    if mhz is None:
+        raise RuntimeError("cannot read the maximum SM clock (nvidia-smi and MEASURED_PEAKS.json failed)")
+    _UNITS.update(sms=sms, mhz=float(mhz), src=src)
+    return sms, float(mhz), src
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (/proc/cpuinfo, else lscpu, else the machine type)."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        for line in subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
 def load_peaks():
     try:
         return json.load(open(PEAKS_FILE))
@@ -288,11 +329,12 @@ def roofline(top, nr, key):
         # terms) plus a 6-instruction renormalisation every 8 terms; the bound
         # is the FP32 lane-operation rate
         terms = top["flops"] / 2.0
-        peak = SM_COUNT * FP32_LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
+        sms, mhz, src = device_units()
+        peak = sms * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
         ach = DF_OPS_PER_TERM * terms / sec / 1e12
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s (FP32 lane operations)",
                 "frac": ach / peak, "traffic": measured_traffic(key, name), "kernel": name,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src})",
                 "work": "12.75 FP32 operations per stored entry of A and right-hand side"}
     # the FP64 residual product with 8 or more right-hand sides does ~10 flops
     # per byte of A, above GB300's FP64 ridge point: bounded by the FP64 pipe
@@ -301,12 +343,13 @@ def roofline(top, nr, key):
     if alu:
         fp64 = name.endswith("_fp64")
         per_clk = FP64_FLOPS_PER_SM_CLK if fp64 else 2 * FP32_LANES_PER_SM
-        peak = SM_COUNT * per_clk * MAX_SM_MHZ * 1e6 / 1e12
+        sms, mhz, src = device_units()
+        peak = sms * per_clk * mhz * 1e6 / 1e12
         ach = top["flops"] / sec / 1e12
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": measured_traffic(key, name), "kernel": name,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if not fp64
-                else "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz"}
+                "peak_source": (f"derived: {sms} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({src})" if not fp64
+                                else f"derived: {sms} SMs x 4 FP64 flop/clk x {mhz:.0f} MHz ({src})")}
     peak = peaks.get("hbm_gbs", 6800.0)
     ach = top["bytes"] / sec / 1e9
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
@@ -347,59 +390,108 @@ def make_workload(kind: str, nrhs: int | None, device: str):
     return dict(name=f"{name}_{nr}rhs", basis=b, colptr=cp, rowidx=ri, values=vals, B=B, nrhs=nr)
 
 
-def cpu_sample(w, budget_flops: float):
-    """Oracle left-looking factor of a prefix of P A P^T's columns, timed."""
+def oracle_sample(w, budget_flops: float, repeats: int = 3, analyze: bool = True):
+    """The CPU oracle on one host core, on a bounded share of the workload's
+    factorization: the full analysis (nested dissection and symbolic, timed
+    for the record), the left-looking FP64 factor of the first columns of
+    P A P^T up to `budget_flops` of sum c_j^2 (the bottom of the elimination
+    tree), and both substitutions over those columns for all right-hand sides
+    (4 nnz(L prefix) nrhs flops, the solve's count restricted to the prefix).
+    Each part is timed `repeats` times and the median kept."""
     import numpy as np
 
     import oracle
 
-    o = oracle.Oracle(w["colptr"], w["rowidx"], w["basis"])
+    ta = []
+    for _ in range(repeats if analyze else 1):
+        t = time.perf_counter()
+        o = oracle.Oracle(w["colptr"], w["rowidx"], w["basis"])
+        ta.append(time.perf_counter() - t)
     c2 = np.cumsum(o.colcount.astype(np.float64) ** 2)
-    ncols = int(np.searchsorted(c2, budget_flops, side="right"))
-    ncols = max(1, min(ncols, o.n))
-    flops = float(c2[ncols - 1])
-    return o, ncols, flops
+    ncols = max(1, min(int(np.searchsorted(c2, budget_flops, side="right")), o.n))
+    ff = float(c2[ncols - 1])
+    nr = int(w["nrhs"])
+    fs = 4.0 * float(o.Lp[ncols]) * nr
+    B = np.asarray(w["B"], dtype=np.float64).reshape(o.n, -1)[:, :nr]
+    Y0 = np.asfortranarray(B[o.perm])
+    tf, ts = [], []
+    for _ in range(repeats):
+        t = time.perf_counter()
+        rc = o.factor_prefix(w["values"], ncols)
+        tf.append(time.perf_counter() - t)
+        if rc != 0:
+            raise RuntimeError(f"oracle factor failed: {rc}")
+        Y = Y0.copy(order="F")
+        t = time.perf_counter()
+        o.solve_prefix(Y, ncols)
+        ts.append(time.perf_counter() - t)
+    mf, ms_, ma = statistics.median(tf), statistics.median(ts), statistics.median(ta)
+    return {"value": (ff + fs) / (mf + ms_) / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": (f"one host core, median of {repeats}: left-looking FP64 factor of the first {ncols} of "
+                       f"{o.n} columns of P A P^T ({ff:.3e} flop of sum c_j^2, bottom of the elimination tree) "
+                       f"in {mf:.2f} s, then both substitutions over those columns with {nr} right-hand sides "
+                       f"({fs:.3e} flop) in {ms_:.2f} s"),
+            "analyze_s": ma if analyze else None, "factor_s": mf, "factor_flops": ff, "solve_s": ms_,
+            "solve_flops": fs, "sample_columns": ncols, "repeats": repeats,
+            "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "nnz_L": int(o.nnzL), "flops_factor": float(c2[-1])}
+
+
+def step_config(args, w, nnz_L: int, flops_factor: float, ws: int) -> dict:
+    """The `config` of a single-matrix workload's line, the same for both arms."""
+    N = w["basis"].N
+    c = {"workload": w["name"], "N": N, "nnz_A": 2 * int(w["rowidx"].size) - N, "nnz_L": int(nnz_L),
+         "flops_factor": float(flops_factor), "nrhs": int(w["nrhs"])}
+    if args.workload == "theta":
+        c.update(theta=THETA, dt=THETA_DT, time_steps=args.theta_steps)
+    c["parallelism"] = "replicas" if ws > 1 else "single"
+    mb = 4e-6 * nnz_L
+    c["l2"] = (("inputs larger than L2 (L alone holds %.1e entries, %.0f MB in FP32)" % (nnz_L, mb))
+               if mb > 129 else ("no L2 flush: a small case whose factor (%.0f MB) fits in L2" % mb))
+    return c
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle (this build's FP64 reference), each
+    step a bounded sample of the workload's factor + solve on one host core."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np
-
     try:
         import torch
         dev = "cuda" if torch.cuda.is_available() else "cpu"
     except Exception:
         dev = "cpu"
-    w = make_workload(args.workload, args.nrhs, dev)
-    o, ncols, flops = cpu_sample(w, args.cpu_flops / 4)
-    times = []
-    for i in range(args.warmup + args.steps):
-        t = time.perf_counter()
-        rc = o.factor_prefix(w["values"], ncols)
-        dt = time.perf_counter() - t
-        if rc != 0:
-            raise RuntimeError(f"oracle factor failed: {rc}")
-        if i >= args.warmup:
-            times.append(dt)
-    tot = sum(times)
-    value = flops * len(times) / tot / 1e12
-    sample = (f"left-looking FP64 factor of the first {ncols} of {o.n} columns of P A P^T "
-              f"(sum c_j^2 = {flops:.3e} flop, bottom of the elimination tree); solve not sampled")
     if args.workload == "batch":
-        sample = f"{w['name']} (the smallest of the batch): " + sample
+        w = make_workload("batch", args.nrhs, dev)
+    else:
+        w = make_workload(args.workload, args.nrhs, dev)
+    budget = args.cpu_flops / 4
+    samples = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(w, budget, repeats=1, analyze=(i == 0))
+        if i >= args.warmup:
+            samples.append(r)
+    tot = sum(r["factor_s"] + r["solve_s"] for r in samples)
+    fl = sum(r["factor_flops"] + r["solve_flops"] for r in samples)
+    value = fl / tot / 1e12
+    last = samples[-1]
+    sample = last["sample"].replace("median of 1: ", "per step: ")
+    if args.workload == "batch":
+        sample = f"{w['name']} (the smallest instance of the batch): " + sample
+        config = {"workload": batch_name(args), "instances": args.batch_count,
+                  "N_total": int(sum(p["N"] for p in __import__("wdgen").batch_instances(args.batch_count, 0))),
+                  "parallelism": "single", "l2": "inputs larger than L2"}
+    else:
+        config = step_config(args, w, last["nnz_L"], last["flops_factor"], 1)
+    cpu = {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample,
+           "nproc": last["nproc"], "cpu_model": last["cpu_model"]}
     line = {"impl": "reference", "metric": metric_name(args),
             "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": tot / len(times) * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": tot / len(samples) * 1e3, "higher_is_better": True,
             "scaling": "strong" if args.workload == "batch" else "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": batch_name(args) if args.workload == "batch" else w["name"],
-                       "N": int(o.n), "sample": sample},
-            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
-            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "data": "synthetic", "config": config, "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -525,15 +617,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        o, ncols, fl = cpu_sample({**w, "values": w["values"]}, args.cpu_flops)
-        t = time.perf_counter()
-        rc = o.factor_prefix(w["values"], ncols)
-        dt = time.perf_counter() - t
-        cpu = {"value": fl / dt / 1e12 if rc == 0 else None, "unit": "TFLOP/s", "cores": 1,
-               "kind": "oracle",
-               "sample": (f"left-looking FP64 factor of the first {ncols} of {o.n} columns of "
-                          f"P A P^T ({fl:.3e} flop, bottom of the elimination tree) in "
-                          f"{dt:.1f} s; solve not sampled")}
+        cpu = oracle_sample(w, args.cpu_flops)
 
     if rank == 0:
         line = {
@@ -541,10 +625,8 @@ def run_ours(args):
             "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": w["name"], "N": N, "nnz_A": 2 * int(w["rowidx"].size) - N,
-                       "nnz_L": info["nnz_L"], "flops_factor": flops_factor, "nrhs": nr,
-                       "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "inputs larger than L2 (front pool %.1f GB)" % (info["front_bytes"] / 1e9)},
+            "config": step_config(args, w, info["nnz_L"], flops_factor, ws),
+            "front_pool_gb": info["front_bytes"] / 1e9,
             "backward_error": solve_info["backward_error"], "ir_iterations": solve_info["iterations"],
             "phases_ms": solve_info["phases_ms"],
             "fp64": res_fp64,
@@ -706,22 +788,14 @@ def run_theta(args):
                "d2h_bytes_per_step": T * 8 * N * nr, "ms_per_step": dt * 1e3}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        o, ncols, fl = cpu_sample(w, args.cpu_flops)
-        t = time.perf_counter()
-        rc = o.factor_prefix(w["values"], ncols)
-        dt = time.perf_counter() - t
-        cpu = {"value": fl / dt / 1e12 if rc == 0 else None, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-               "sample": (f"left-looking FP64 factor of the first {ncols} of {o.n} columns of P M P^T "
-                          f"({fl:.3e} flop) in {dt:.1f} s; time steps not sampled")}
+        cpu = oracle_sample(w, args.cpu_flops)
     if rank == 0:
         line = {"metric": metric_name(args),
                 "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms, "ms_factor": ms_factor, "ms_per_theta_step": (ms - ms_factor) / T, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": w["name"], "N": N, "nnz_A": nnz_a, "nnz_L": info["nnz_L"], "nrhs": nr,
-                           "theta": THETA, "dt": THETA_DT, "time_steps": T,
-                           "parallelism": "replicas" if ws > 1 else "single",
-                           "l2": "inputs larger than L2 (front pool %.1f GB)" % (info["front_bytes"] / 1e9)},
+                "config": step_config(args, w, info["nnz_L"], info["flops_factor"], ws),
+                "front_pool_gb": info["front_bytes"] / 1e9,
                 "backward_error": be, "ir_iterations_last_step": its,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "top_kernels": _top(kstats, 12)}

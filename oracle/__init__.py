@@ -72,6 +72,9 @@ def _load():
             lib.or_get_L.argtypes = [ctypes.c_void_p, _f64p]
             lib.or_solve.restype = ctypes.c_int
             lib.or_solve.argtypes = [ctypes.c_void_p, _f64p, ctypes.c_int64, ctypes.c_int64]
+            lib.or_solve_prefix.restype = ctypes.c_int
+            lib.or_solve_prefix.argtypes = [ctypes.c_void_p, _f64p, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int64]
             lib.or_logdet.restype = ctypes.c_double
             lib.or_logdet.argtypes = [ctypes.c_void_p]
             lib.or_apply_L.restype = ctypes.c_int
@@ -178,6 +181,17 @@ class Oracle:
         rc = int(self._lib.or_factor_cols(self._ctx, _p(v, _f64p), int(ncols)))
         self.factored = rc == 0 and ncols >= self.n
         return rc
+
+    def solve_prefix(self, Y, ncols: int) -> None:
+        """The forward and backward substitution loops of solve() over the
+        first ncols columns only, in place on Y (n x nrhs, factor order,
+        Fortran order): a bounded share of the solve, for timing (valid after
+        factor_prefix(values, ncols))."""
+        if not (Y.flags.f_contiguous and Y.dtype == np.float64 and Y.shape[0] == self.n):
+            raise ValueError("Y must be an n x nrhs Fortran-ordered float64 array")
+        rc = self._lib.or_solve_prefix(self._ctx, _p(Y, _f64p), Y.shape[1], self.n, int(ncols))
+        if rc:
+            raise RuntimeError("solve_prefix: not factored or bad ncols")
 
     def L_values(self) -> np.ndarray:
         x = np.empty(self.nnzL, np.float64)

@@ -640,6 +640,28 @@ int or_solve(const or_ctx *c, double *B, int64_t nrhs, int64_t ldb) {
     return 0;
 }
 
+/* The two substitutions of or_solve restricted to the columns j < ncols of
+   L (final after or_factor_cols(ncols)), on B in factor order.  Not a solve:
+   a bounded share of the solve's work, the same loops over fewer columns,
+   for timing the oracle on large factorizations. */
+int or_solve_prefix(const or_ctx *c, double *B, int64_t nrhs, int64_t ldb, int64_t ncols) {
+    if (!c->Lx || ncols < 0 || ncols > c->n) return -1;
+    for (int64_t r = 0; r < nrhs; ++r) {
+        double *y = B + r * ldb;
+        for (int64_t j = 0; j < ncols; ++j) {
+            y[j] /= c->Lx[c->Lp[j]];
+            double yj = y[j];
+            for (int64_t q = c->Lp[j] + 1; q < c->Lp[j + 1]; ++q) y[c->Li[q]] -= c->Lx[q] * yj;
+        }
+        for (int64_t j = ncols - 1; j >= 0; --j) {
+            double s = y[j];
+            for (int64_t q = c->Lp[j] + 1; q < c->Lp[j + 1]; ++q) s -= c->Lx[q] * y[c->Li[q]];
+            y[j] = s / c->Lx[c->Lp[j]];
+        }
+    }
+    return 0;
+}
+
 /* 2 sum_j log L_jj, Neumaier compensated */
 double or_logdet(const or_ctx *c) {
     double s = 0.0, comp = 0.0;

@@ -30,6 +30,7 @@ def test_amalgamation_defaults_and_overrides(wdlib):
 
 def test_roofline_classification(monkeypatch):
     monkeypatch.setattr(bench, "load_peaks", lambda: {"hbm_gbs": 6000.0, "bf16_tflops_sustained": 1800.0})
+    monkeypatch.setattr(bench, "device_units", lambda: (152, 2070.0, "test"))
     key = ("2d", (128, 64, 10))
     tc = bench.roofline({"name": "tc_schur_syrk_fp32", "ms": 1000.0, "flops": 84e12, "bytes": 0}, 64, key)
     assert tc["bound"] == "tensor"
@@ -43,14 +44,37 @@ def test_roofline_classification(monkeypatch):
     assert hbm["bound"] == "hbm" and hbm["frac"] == pytest.approx(0.5)
 
 
-def test_measured_traffic_only_where_it_was_taken(monkeypatch):
-    t = bench.MEASURED_TRAFFIC[("2d", "potrf_panel_fp32", 64, 64, 10)]
-    assert bench.measured_traffic(("2d", (64, 64, 10)), "potrf_panel_fp32") in (t["bytes"], None)
-    assert bench.measured_traffic(("2d", (128, 64, 10)), "potrf_panel_fp32") is None
-    assert bench.measured_traffic(("batch", (64, 64, 10)), "potrf_panel_fp32") is None
+def test_measured_traffic_only_where_it_was_taken(monkeypatch, tmp_path):
+    src = tmp_path / "k.cu"
+    src.write_text("kernel")
+    import hashlib
+    sha = hashlib.sha1(b"kernel").hexdigest()
+    entry = {"bytes": 1.5e6, "source": str(src), "sha1": sha}
+    monkeypatch.setitem(bench.MEASURED_TRAFFIC, ("2d", "tc_schur_update_fp32", 128, 64, 10), entry)
+    assert bench.measured_traffic(("2d", (128, 64, 10)), "tc_schur_update_fp32") == 1.5e6
+    assert bench.measured_traffic(("2d", (64, 64, 10)), "tc_schur_update_fp32") is None
+    assert bench.measured_traffic(("batch", (128, 64, 10)), "tc_schur_update_fp32") is None
     # a changed source file voids the figure
-    monkeypatch.setitem(bench.MEASURED_TRAFFIC, ("2d", "potrf_panel_fp32", 64, 64, 10), dict(t, sha1="0" * 40))
-    assert bench.measured_traffic(("2d", (64, 64, 10)), "potrf_panel_fp32") is None
+    src.write_text("kernel v2")
+    assert bench.measured_traffic(("2d", (128, 64, 10)), "tc_schur_update_fp32") is None
+    # every committed entry names a source file of the repository
+    for k, t in bench.MEASURED_TRAFFIC.items():
+        if k[1] != "tc_schur_update_fp32":
+            assert t["source"].startswith("paper_2007_01541_gb300/csrc/")
+
+
+def test_reference_arm_and_cpu_baseline_share_the_config(capsys):
+    """The reference arm prints the same metric, unit and config as this
+    build's line for the workload, with the oracle's bounded sample stated."""
+    import json
+    bench.run_reference(_args(workload="1d", nrhs=None, cpu_flops=1e7, steps=2, warmup=1, gpus=1))
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.metric_name(_args(workload="1d"))
+    w = bench.make_workload("1d", None, "cpu")
+    r = bench.oracle_sample(w, 1e7, repeats=1)
+    assert line["config"] == bench.step_config(_args(workload="1d"), w, r["nnz_L"], r["flops_factor"], 1)
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert r["factor_flops"] <= 1e7 and r["solve_flops"] > 0 and r["nproc"] >= 1
 
 
 def test_batch_cpu_baseline_runs_the_oracle_in_parallel_processes():

@@ -326,3 +326,16 @@ def test_amalgamation_percentage_branch(case, run):
     assert list(o.parent) == case["parent"]
     assert list(o.colcount) == case["colcount"]
     assert list(o.super_first) == run["super_first"]
+
+
+def test_solve_prefix_over_all_columns_is_the_solve():
+    """The timing helper runs solve()'s loops over a prefix of the columns:
+    over all of them it is the solve (in factor order)."""
+    name, b, cp, ri, v = WL[0]
+    o = oracle.Oracle(cp, ri, b, leaf=8)
+    assert o.factor(v) == 0
+    B = rhs(o.n, 3, 0)
+    X = o.solve(B)
+    Y = np.asfortranarray(B[o.perm])
+    o.solve_prefix(Y, o.n)
+    np.testing.assert_array_equal(Y, X[o.perm])
