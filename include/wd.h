@@ -278,9 +278,15 @@ wd_status wd_export_L(wd_handle h, double *panels);
    enqueued.  Nothing in the scratch has to start at zero (every call rewrites
    the offsets before reading them).  The first call on a device looks up the
    array's address (cudaGetSymbolAddress), which may load the module: make
-   that first call during set-up, before any stream capture.  Calls whose
-   executions overlap (unordered streams, several host threads) share the
-   scratch and race: order them.  Needs a successful wd_factor. */
+   that first call during set-up, before any stream capture.  The address is
+   cached per device for the life of the process: it does not survive
+   cudaDeviceReset (every handle is invalid after a reset anyway).  Calls
+   whose executions overlap (unordered streams, several host threads) share
+   the scratch and race: order them.  The handle's own later calls that
+   rewrite or free the fronts (wd_factor, wd_analyze, wd_destroy) wait for
+   this call's copy to finish (an event recorded on `stream`).  The caller's
+   current device is restored before returning.  Needs a successful
+   wd_factor. */
 #define WD_NOALLOC_MAX_SUPERNODES 65536
 wd_status wd_export_L_noalloc(wd_handle h, double *panels, void *stream);
 

@@ -125,6 +125,11 @@ struct wd_ctx {
     int64_t pack_total = 0;
     status_t *d_tstatus = nullptr;    // nonzero: a bounded device wait expired
     cudaStream_t cap_stream = nullptr;
+    // wd_export_L_noalloc returns without waiting; this event, recorded on its
+    // stream, orders that read of the fronts before the next call that
+    // rewrites or frees them (wd_factor, wd_analyze, wd_destroy)
+    cudaEvent_t export_ev = nullptr;
+    bool export_pending = false;
     GraphCache g_factor, g_solve;
     status_t *d_status = nullptr;
     double *d_scalars = nullptr;   // [0] = ||A||_inf, [1] = logdet, [2..] partials
@@ -257,12 +262,22 @@ wd_status wd_create(wd_handle *out, const wd_options *opt) {
     return WD_OK;
 }
 
+// waits (host side) for the last wd_export_L_noalloc's read of the fronts
+static void wait_export(wd_handle h) {
+    if (h->export_pending) {
+        cudaEventSynchronize(h->export_ev);
+        h->export_pending = false;
+    }
+}
+
 void wd_destroy(wd_handle h) {
     if (!h) return;
     if (!h->opt.symbolic_only) {
         int prev = 0;
         cudaGetDevice(&prev);
         cudaSetDevice(h->device);
+        wait_export(h);
+        if (h->export_ev) cudaEventDestroy(h->export_ev);
         for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
         for (cudaEvent_t e : h->single_ev)
             if (e) cudaEventDestroy(e);
@@ -627,6 +642,8 @@ static wd_status reset_analysis(wd_handle h) {
         wd::init_kernel_attributes();
         if (!h->cap_stream)
             CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "stream");
+        if (!h->export_ev) CK(cudaEventCreateWithFlags(&h->export_ev, cudaEventDisableTiming), "event");
+        wait_export(h);
     }
     h->analyzed = h->factored = false;
     if (!host_only) {
@@ -1180,6 +1197,7 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
         return fail(h, WD_ERR_INVALID_ARG, "null values or bad precision");
     CK(cudaSetDevice(h->device), "set device");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    wait_export(h);   // a pending allocation-free export still reads the fronts
     h->factored = false;
     const int64_t nnzl = h->S.pcp[h->S.n];
     if (!h->d_front) {
@@ -2056,16 +2074,26 @@ extern "C" wd_status wd_export_L_noalloc(wd_handle h, double *panels, void *stre
         return fail(h, WD_ERR_INVALID_ARG,
                     std::to_string(h->S.ns) + " supernodes exceed the static scratch of " +
                         std::to_string(wd::NOALLOC_MAX_SUPERNODES) + " panel offsets");
+    int prev = -1;
+    CK(cudaGetDevice(&prev), "get device");
     CK(cudaSetDevice(h->device), "set device");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int64_t *poff = nullptr;
-    CK(wd::noalloc_panel_offsets(h->device, &poff), "scratch address");
-    wd::launch_panel_offsets_noalloc(h->dsym, st);
-    if (h->prec == WD_FP64)
-        wd::launch_export_panels<double>(h->dsym, static_cast<const double *>(h->d_front), panels, poff, st);
-    else
-        wd::launch_export_panels<float>(h->dsym, static_cast<const float *>(h->d_front), panels, poff, st);
-    h->launches += 2;
-    CK(cudaGetLastError(), "export launch");
+    cudaError_t e = wd::noalloc_panel_offsets(h->device, &poff);
+    if (e == cudaSuccess) {
+        wd::launch_panel_offsets_noalloc(h->dsym, st);
+        if (h->prec == WD_FP64)
+            wd::launch_export_panels<double>(h->dsym, static_cast<const double *>(h->d_front), panels, poff, st);
+        else
+            wd::launch_export_panels<float>(h->dsym, static_cast<const float *>(h->d_front), panels, poff, st);
+        h->launches += 2;
+        e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            e = cudaEventRecord(h->export_ev, st);
+            if (e == cudaSuccess) h->export_pending = true;
+        }
+    }
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "allocation-free export");
     return WD_OK;
 }

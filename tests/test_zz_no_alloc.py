@@ -22,10 +22,36 @@ def test_noalloc_export_matches_export(wdlib, cuda, prec):
     for _ in range(2):
         out.fill_(float("nan"))
         torch.cuda.current_stream().synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         with torch.cuda.stream(stream):
             s.export_L_noalloc(out, stream=stream.cuda_stream)
         stream.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0      # no device memory was taken
         assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_noalloc_export_is_ordered_before_the_next_factor(wdlib, cuda):
+    """The export returns without waiting; a refactorization with other
+    values issued right after it on another stream must not overwrite the
+    fronts before the export has read them."""
+    torch = cuda
+    b = haar_basis(2, 7)
+    cp, ri = compressed_pattern(b)
+    v1 = compressed_values(b, cp, ri, Kernel("matern32", 0.1), 1e-3)
+    v2 = compressed_values(b, cp, ri, Kernel("matern32", 0.2), 1e-2)
+    s = wdlib.Solver().analyze(cp, ri, b)
+    ref1 = s.factor(v1, "fp64").export_L()
+    ref2 = s.factor(v2, "fp64").export_L()
+    assert not np.array_equal(ref1, ref2)
+    s.factor(v1, "fp64")
+    out = torch.full((ref1.size,), float("nan"), dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    s.export_L_noalloc(out, stream=side.cuda_stream)
+    s.factor(v2, "fp64")                       # default stream, no synchronization in between
+    side.synchronize()
+    assert np.array_equal(out.cpu().numpy(), ref1)
+    assert np.array_equal(s.export_L(), ref2)
 
 
 def test_noalloc_export_rejects_too_many_supernodes(wdlib, cuda):
