@@ -100,6 +100,9 @@ def parse():
                    help="supernode amalgamation: merge while the width is <= this (library default if unset)")
     p.add_argument("--relax-pct", type=int, default=None,
                    help="supernode amalgamation: or while explicit zeros stay <= this percent")
+    p.add_argument("--diag64-min-k", type=int, default=None,
+                   help="mixed precision: factor the diagonal blocks of supernodes at least this wide "
+                        "in FP64 (library default if unset)")
     p.add_argument("--theta-steps", type=int, default=150,
                    help="theta workload: time steps per factorization")
     p.add_argument("--nrhs", type=int, default=None)
@@ -302,6 +305,8 @@ def solver_opts(args, **kw):
         kw["relax_k"] = args.relax_k
     if args.relax_pct is not None:
         kw["relax_pct"] = args.relax_pct
+    if getattr(args, "diag64_min_k", None) is not None:
+        kw["diag64_min_k"] = args.diag64_min_k
     return kw
 
 
@@ -338,7 +343,7 @@ def roofline(top, nr, key):
                 "work": "12.75 FP32 operations per stored entry of A and right-hand side"}
     # the FP64 residual product with 8 or more right-hand sides does ~10 flops
     # per byte of A, above GB300's FP64 ridge point: bounded by the FP64 pipe
-    alu = name.startswith(("schur_", "potrf_panel", "fwd_xapply", "fwd_bupdate", "bwd_reduce",
+    alu = name.startswith(("schur_", "panel", "diag_factor", "fwd_xapply", "fwd_bupdate", "bwd_reduce",
                            "bwd_xapply", "sbinv_stage")) or (name.startswith("spmv_residual") and nr >= 8)
     if alu:
         fp64 = name.endswith("_fp64")

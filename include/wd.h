@@ -75,7 +75,19 @@ typedef struct {
     int32_t profile;        /* 1: bracket every kernel launch of wd_factor and
                                wd_solve with CUDA events on the caller's stream
                                and accumulate per-kernel times (0)            */
-    int32_t reserved[5];
+    int32_t diag64_min_k;   /* WD_MIXED: the diagonal blocks of supernodes of
+                               width >= diag64_min_k are factored (Cholesky and
+                               inverse of the 64 x 64 block) in FP64, then
+                               rounded to FP32; 0: none (default 0)           */
+    int32_t wait_limit;     /* polls before a bounded device wait gives up
+                               (WD_ERR_TIMEOUT); 0: the default (2^26)        */
+    int32_t test_closed_gate; /* test hook, 1: every tensor-core update CTA
+                               also waits for a device word that nothing sets,
+                               so the bounded wait must expire (0)            */
+    int32_t test_fail_alloc; /* test hook, k > 0: the handle's k-th device
+                               allocation fails as if memory ran out
+                               (WD_ERR_OOM); counts from wd_create (0)        */
+    int32_t reserved[1];
 } wd_options;
 
 /* Optional geometry for the nested-dissection ordering.  Per vertex (basis

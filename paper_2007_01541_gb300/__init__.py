@@ -38,7 +38,9 @@ class WdOptions(ctypes.Structure):
                 ("relax_pct", ctypes.c_int32), ("ir_max_iter", ctypes.c_int32),
                 ("ir_tol", ctypes.c_double), ("use_graphs", ctypes.c_int32),
                 ("symbolic_only", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("diag64_min_k", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
+                ("test_closed_gate", ctypes.c_int32), ("test_fail_alloc", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class WdGeometry(ctypes.Structure):
@@ -160,7 +162,8 @@ class Solver:
 
     def __init__(self, nd_leaf=DEFAULTS["nd_leaf"], relax_k=DEFAULTS["relax_k"],
                  relax_pct=DEFAULTS["relax_pct"], ir_max_iter=10, ir_tol=1e-12,
-                 symbolic_only=False, profile=False, use_graphs=True):
+                 symbolic_only=False, profile=False, use_graphs=True, diag64_min_k=None,
+                 wait_limit=0, test_closed_gate=False, test_fail_alloc=0):
         self._lib = load()
         o = WdOptions()
         self._lib.wd_default_options(ctypes.byref(o))
@@ -169,6 +172,11 @@ class Solver:
         o.symbolic_only = 1 if symbolic_only else 0
         o.profile = 1 if profile else 0
         o.use_graphs = 1 if use_graphs else 0
+        if diag64_min_k is not None:
+            o.diag64_min_k = diag64_min_k
+        o.wait_limit = wait_limit
+        o.test_closed_gate = 1 if test_closed_gate else 0
+        o.test_fail_alloc = test_fail_alloc
         self._h = ctypes.c_void_p()
         self._check(self._lib.wd_create(ctypes.byref(self._h), ctypes.byref(o)))
         self.n = None

@@ -25,7 +25,7 @@ namespace {
 constexpr int ROWS_PER_CTA = 256;  // one thread per front row (gather / apply_L)
 
 enum LaunchKind {
-    K_INIT, K_PANEL, K_UPDATE, K_SYRK, K_UPDATE_TC, K_SYRK_TC, K_DIAG_COPY,  // factor
+    K_INIT, K_PANEL, K_UPDATE, K_SYRK, K_UPDATE_TC, K_SYRK_TC, K_DIAG,      // factor
     K_SBINV_DIAG, K_SBINV_STAGE, K_SBINV_T,                    // super-block inverses
     K_FWD_GATHER, K_FWD_XAPPLY, K_FWD_BUPDATE,                 // forward solve
     K_BWD_REDUCE, K_BWD_FINISH, K_BWD_XAPPLY,                  // backward solve
@@ -43,8 +43,8 @@ struct Launch {
 };
 
 const char *kind_name(int k) {
-    static const char *names[] = {"front_init", "potrf_panel", "schur_update", "schur_syrk",
-                                  "tc_schur_update", "tc_schur_syrk", "diag_copy", "sbinv_diag",
+    static const char *names[] = {"front_init", "panel", "schur_update", "schur_syrk",
+                                  "tc_schur_update", "tc_schur_syrk", "diag_factor", "sbinv_diag",
                                   "sbinv_stage", "sbinv_transpose", "fwd_gather", "fwd_xapply",
                                   "fwd_bupdate", "bwd_reduce", "bwd_finish", "bwd_xapply",
                                   "apply_L"};
@@ -77,9 +77,14 @@ struct GraphCache {
 
 struct DevMem {
     std::vector<void *> ptrs;
+    // test hook (wd_options.test_fail_alloc): the handle's allocations so far
+    // and the one that fails as if device memory ran out (0: none)
+    int64_t *count = nullptr;
+    int64_t fail_at = 0;
     cudaError_t alloc(void **p, size_t bytes) {
         *p = nullptr;
         if (bytes == 0) bytes = 16;
+        if (count && ++*count == fail_at) return cudaErrorMemoryAllocation;
         cudaError_t e = cudaMalloc(p, bytes);
         if (e == cudaSuccess) ptrs.push_back(*p);
         return e;
@@ -108,6 +113,7 @@ struct wd_ctx {
     wd::Symbolic S;
     DevMem mem;        // analysis lifetime
     DevMem work;       // numeric workspaces (factor / solve)
+    int64_t allocs = 0;   // device allocations made by this handle (test hook)
     DevSym dsym{};
     int32_t *d_csr_src = nullptr;
     double *d_csr_val = nullptr;
@@ -116,7 +122,6 @@ struct wd_ctx {
     void *d_front = nullptr;
     size_t front_elems = 0;
     void *d_dinv = nullptr;        // inverses of the NB x NB diagonal blocks
-    void *d_ldiag = nullptr;       // factored NB x NB diagonal blocks (before their copy into the fronts)
     size_t dinv_elems = 0;
     void *d_xs = nullptr, *d_xts = nullptr;  // super-block inverses and their transposes
     int64_t *d_xsoff = nullptr;
@@ -124,6 +129,7 @@ struct wd_ctx {
     unsigned char *d_pack = nullptr;  // packed tf32 panel lines (FP32 fronts)
     int64_t pack_total = 0;
     status_t *d_tstatus = nullptr;    // nonzero: a bounded device wait expired
+    unsigned *d_gate = nullptr;       // a device word that stays zero (wd_options.test_closed_gate)
     cudaStream_t cap_stream = nullptr;
     // wd_export_L_noalloc returns without waiting; this event, recorded on its
     // stream, orders that read of the fronts before the next call that
@@ -249,10 +255,13 @@ wd_status wd_create(wd_handle *out, const wd_options *opt) {
     wd_default_options(&h->opt);
     if (opt) h->opt = *opt;
     if (h->opt.nd_leaf < 1 || h->opt.relax_k < 0 || h->opt.relax_pct < 0 || h->opt.ir_max_iter < 0 ||
-        !(h->opt.ir_tol > 0)) {
+        !(h->opt.ir_tol > 0) || h->opt.diag64_min_k < 0 || h->opt.wait_limit < 0 ||
+        h->opt.test_fail_alloc < 0) {
         delete h;
         return WD_ERR_INVALID_ARG;
     }
+    h->mem.count = h->work.count = &h->allocs;
+    h->mem.fail_at = h->work.fail_at = h->opt.test_fail_alloc;
     if (!h->opt.symbolic_only && cudaGetDevice(&h->device) != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -355,11 +364,23 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
             by += 12.0 * (double)(S.pcp[S.sfirst[s + 1]] - S.pcp[S.sfirst[s]]);
         }
         add_launch(p, K_INIT, f0, 0, 0, el, by);
+        // factorization and inverse of a diagonal block of nb columns
+        auto diag_flops = [](double nb) { return 2.0 * nb * nb * nb / 3; };
         int kmax = 0;
         double fl = 0;
         for (int i = b; i < e; ++i) kmax = std::max(kmax, S.k(S.level_nodes[i]));
+        // the first diagonal block of every front of the level
+        f0 = p.items.size();
+        fl = el = 0;
+        for (int i = b; i < e; ++i) {
+            const int s = S.level_nodes[i], nb = std::min(NB, S.k(s));
+            p.items.push_back({s, 0, 0, 0});
+            fl += diag_flops(nb);
+            el += nb * (nb + 1) + 2.0 * NB * NB;
+        }
+        add_launch(p, K_DIAG, f0, 0, fl, el, 0);
         for (int kb = 0; kb < kmax; kb += NB) {
-            // diagonal block factorization (in every CTA) + panel rows
+            // panel rows: L21 = F21 L11^-T with the stored inverse
             f0 = p.items.size();
             fl = el = 0;
             for (int i = b; i < e; ++i) {
@@ -369,12 +390,14 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
                 const int t0 = kb + nb;
                 const int mp = front_order(S, s);
                 const int rs = (t0 == k) ? kpad(k) : t0;
-                const int nrb = std::max(1, (mp - rs + RB - 1) / RB);
+                const int nrb = (mp - rs + RB - 1) / RB;
                 for (int rb = 0; rb < nrb; ++rb) p.items.push_back({s, rb, 0, 0});
-                fl += (double)(m - t0) * nb * nb + 2.0 * nb * nb * nb / 3;
-                el += 2.0 * (m - t0) * nb + nb * (nb + 1) + 2.0 * NB * NB;
+                fl += (double)(m - t0) * nb * nb;
+                el += 2.0 * (m - t0) * nb + (double)NB * NB;
             }
             add_launch(p, K_PANEL, f0, kb, fl, el, 0);
+            // trailing pivot columns; the CTA of tile (0, 0) also factors the
+            // next diagonal block
             f0 = p.items.size();
             fl = el = 0;
             for (int i = b; i < e; ++i) {
@@ -390,8 +413,9 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
                         p.items.push_back({s, ti, tj, 0});
                 const double cw = k - t0, below = m - k;
                 const double ent = cw * (cw + 1) / 2 + below * cw;
-                fl += 2.0 * nb * ent;
-                el += 2.0 * ent + (double)(m - t0) * nb;
+                const int nb2 = std::min(NB, k - t0);
+                fl += 2.0 * nb * ent + diag_flops(nb2);
+                el += 2.0 * ent + (double)(m - t0) * nb + nb2 * (nb2 + 1) + 2.0 * NB * NB;
             }
             add_launch(p, tc ? K_UPDATE_TC : K_UPDATE, f0, kb, fl, el, 0);
         }
@@ -411,16 +435,6 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
             el += 2.0 * tri + (double)u * k;
         }
         add_launch(p, tc ? K_SYRK_TC : K_SYRK, f0, 0, fl, el, 0);
-    }
-    {
-        const size_t f0 = p.items.size();
-        double el = 0;
-        for (int s = 0; s < S.ns; ++s)
-            for (int kb = 0; kb < S.k(s); kb += NB) {
-                p.items.push_back({s, kb, 0, 0});
-                el += 2.0 * NB * NB;
-            }
-        add_launch(p, K_DIAG_COPY, f0, 0, 0, el, 0);
     }
     // explicit inverses of the super-blocks' diagonal blocks (for the solves)
     constexpr int BPS = wd::SB / NB;  // 64-blocks per super-block
@@ -659,7 +673,6 @@ static wd_status reset_analysis(wd_handle h) {
     h->ws_cols = 0;
     h->d_front = nullptr;
     h->d_dinv = nullptr;
-    h->d_ldiag = nullptr;
     h->d_xs = h->d_xts = nullptr;
     h->d_xsoff = nullptr;
     h->xs_elems = 0;
@@ -954,6 +967,10 @@ static wd_status finish_analysis(wd_handle h, std::chrono::steady_clock::time_po
         if (st != WD_OK) return st;
     }
     CK(h->mem.alloc((void **)&h->d_tstatus, sizeof(status_t)), "status alloc");
+    if (h->opt.test_closed_gate) {
+        CK(h->mem.alloc((void **)&h->d_gate, sizeof(unsigned)), "gate alloc");
+        CK(cudaMemset(h->d_gate, 0, sizeof(unsigned)), "gate clear");
+    }
     if (h->batch_count > 0) {
         const int64_t *pc = nullptr;
         const int32_t *ps = nullptr;
@@ -1105,30 +1122,34 @@ template <class T>
 static void enqueue_factor_plan(wd_handle h, cudaStream_t st, bool prof) {
     T *F = static_cast<T *>(h->d_front);
     T *Dv = static_cast<T *>(h->d_dinv);
-    T *Ld = static_cast<T *>(h->d_ldiag);
     const DevSym &d = h->dsym;
     const bool fp32 = sizeof(T) == 4;
     const Plan &P = fp32 ? h->fplan_tc : h->fplan;
     unsigned char *pk = fp32 ? h->d_pack : nullptr;
+    wd::TcArgs ta{};
+    ta.dinv = reinterpret_cast<float *>(Dv);
+    ta.status = h->d_status;
+    ta.tstatus = h->d_tstatus;
+    ta.diag64_min_k = h->opt.diag64_min_k;
+    ta.wait_limit = (uint32_t)std::max(0, h->opt.wait_limit);
+    ta.gate = h->opt.test_closed_gate ? h->d_gate : nullptr;
     size_t li = 0;
     for (const Launch &L : P.launches) {
         const int4 *it = P.d_items + L.off;
         if (prof) record_event(h->prof_ev[2 * li], st);
         switch (L.kind) {
             case K_INIT: wd::launch_front_init<T>(d, F, it, L.count, st); break;
-            case K_PANEL:
-                wd::launch_panel<T>(d, F, Dv, Ld, pk, it, L.count, L.arg, h->d_status, st);
+            case K_DIAG:
+                wd::launch_diag_factor<T>(d, F, Dv, it, L.count, h->opt.diag64_min_k, h->d_status, st);
                 break;
-            case K_DIAG_COPY: wd::launch_diag_copy<T>(d, F, Ld, it, L.count, st); break;
+            case K_PANEL: wd::launch_panel<T>(d, F, Dv, pk, it, L.count, L.arg, st); break;
             case K_UPDATE: wd::launch_schur<T>(d, F, Dv, it, L.count, L.arg, 0, h->d_status, st); break;
             case K_SYRK: wd::launch_schur<T>(d, F, Dv, it, L.count, 0, 1, h->d_status, st); break;
             case K_UPDATE_TC:
-                wd::launch_tc_schur(d, reinterpret_cast<float *>(F), pk, it, L.count, L.arg, 0,
-                                    h->d_tstatus, st);
+                wd::launch_tc_schur(d, reinterpret_cast<float *>(F), pk, it, L.count, L.arg, 0, ta, st);
                 break;
             case K_SYRK_TC:
-                wd::launch_tc_schur(d, reinterpret_cast<float *>(F), pk, it, L.count, 0, 1,
-                                    h->d_tstatus, st);
+                wd::launch_tc_schur(d, reinterpret_cast<float *>(F), pk, it, L.count, 0, 1, ta, st);
                 break;
             case K_SBINV_DIAG:
                 wd::launch_sbinv_diag<T>(d, Dv, static_cast<T *>(h->d_xs), h->d_xsoff, it, L.count, st);
@@ -1203,7 +1224,6 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
     if (!h->d_front) {
         CK(h->mem.alloc(&h->d_front, h->front_elems * sizeof(double)), "front pool alloc");
         CK(h->mem.alloc(&h->d_dinv, h->dinv_elems * sizeof(double)), "inverse blocks alloc");
-        CK(h->mem.alloc(&h->d_ldiag, h->dinv_elems * sizeof(double)), "diagonal blocks alloc");
         CK(h->mem.alloc(&h->d_xs, h->xs_elems * sizeof(double)), "super-block inverse alloc");
         CK(h->mem.alloc(&h->d_xts, h->xs_elems * sizeof(double)), "super-block inverse alloc");
         // padding rows stay zero forever: no kernel writes them

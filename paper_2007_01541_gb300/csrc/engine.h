@@ -56,18 +56,20 @@ inline void init_kernel_attributes() {
 // ---- factorization (front_kernels.cu) ------------------------------------
 template <class T>
 void launch_front_init(const DevSym &d, T *front, const int4 *items, int count, cudaStream_t st);
-// pivot block kb: every CTA factors and inverts the NB x NB diagonal block;
-// the rb = 0 CTA stores the factor into ldiag and the inverse into dinv (both
-// at dinvoff + (kb / NB) NB^2); then the CTA's rows below: L21 = F21 Linv^T.
-// pk != nullptr (FP32 only): also write the packed tf32 lines of the new panel
+// diagonal block (s, kb) of each item: L11 into the front, L11^-1 into dinv
+// at dinvoff + (kb / NB) NB^2; FP32 fronts of width >= diag64_min_k (> 0)
+// factor the block in FP64
 template <class T>
-void launch_panel(const DevSym &d, T *front, T *dinv, T *ldiag, unsigned char *pk, const int4 *items,
-                  int count, int kb, status_t *status, cudaStream_t st);
-// the factored diagonal blocks from ldiag into the fronts; item = (s, kb)
+void launch_diag_factor(const DevSym &d, T *front, T *dinv, const int4 *items, int count, int diag64_min_k,
+                        status_t *status, cudaStream_t st);
+// panel of pivot block kb (L11^-1 in dinv): L21 = F21 L11^-T for the items'
+// 64-row blocks; pk != nullptr (FP32 only): also write the packed tf32 lines
 template <class T>
-void launch_diag_copy(const DevSym &d, T *front, const T *ldiag, const int4 *items, int count,
-                      cudaStream_t st);
-// mode 0: pivot-column update of step kb; mode 1: final update matrix (syrk)
+void launch_panel(const DevSym &d, T *front, const T *dinv, unsigned char *pk, const int4 *items, int count,
+                  int kb, cudaStream_t st);
+// mode 0: pivot-column update of step kb, then the CTA of tile (0, 0) factors
+// diagonal block kb + NB (into the front and dinv); mode 1: final update
+// matrix (syrk)
 template <class T>
 void launch_schur(const DevSym &d, T *front, T *dinv, const int4 *items, int count, int kb,
                   int mode, status_t *status, cudaStream_t st);
@@ -90,10 +92,22 @@ __host__ __device__ inline int64_t pack_bytes(int k, int mp) {
 }
 
 // tensor-core Schur update of FP32 fronts (tc_schur.cu); 128 x 128 tiles;
-// tstatus != 0 after the launch means a bounded wait expired
+// mode 0 also factors the next diagonal block in the CTA of tile (0, 0) (in
+// FP64 for fronts of width >= diag64_min_k > 0).  Bounded waits: wait_limit
+// polls (0: the default); gate != nullptr: every CTA also waits, after its
+// products, for *gate != 0 (a test of the timeout path).  tstatus != 0 after
+// the launch means a bounded wait expired.
 constexpr int TC_BM = 128, TC_BN = 128;
+struct TcArgs {
+    float *dinv;
+    status_t *status;
+    status_t *tstatus;
+    int diag64_min_k;
+    uint32_t wait_limit;
+    const unsigned *gate;
+};
 void launch_tc_schur(const DevSym &d, float *front, const unsigned char *pk, const int4 *items,
-                     int count, int kb, int mode, status_t *tstatus, cudaStream_t st);
+                     int count, int kb, int mode, const TcArgs &a, cudaStream_t st);
 void init_tc_attributes();
 
 // ---- values, solves and reductions (solve_kernels.cu) ---------------------

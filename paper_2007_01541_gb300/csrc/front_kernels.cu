@@ -16,17 +16,20 @@
 //   front_init   assemble A's entries and gather the children's update
 //                matrices through relative row maps (no atomics: every front
 //                entry is written by exactly one thread)
+//   diag_factor  pivot block 0 of every front: L11 = chol(F11) and L11^-1
 //   per pivot block kb = 0, NB, 2NB, ... < k_s:
-//     potrf      Cholesky of the NB x NB diagonal block and the inverse of
-//                that block (kept for the panel and the solves)
 //     panel      L21 := F21 L11^-T  as a product with the stored inverse
-//     update     pivot columns [kb+NB, k) of the trailing rows -= L21 L21^T
+//     update     pivot columns [kb+NB, k) of the trailing rows -= L21 L21^T;
+//                the CTA of the tile holding the next diagonal block then
+//                factors that block (the next step's L11 and L11^-1), so
+//                each step is two dependent launches
 //   syrk         U = F22 - L(R, 0:k) L(R, 0:k)^T, one product with the whole
 //                pivot width as inner dimension
 // Tiles are staged into shared memory with cp.async (many loads in flight
 // per thread) and double buffered along the inner dimension.
 #include "dev_common.cuh"
 #include "engine.h"
+#include "front_block.cuh"
 
 namespace wd {
 namespace {
@@ -36,29 +39,9 @@ constexpr int BM = SCHUR_BM;   // rows of a Schur tile
 constexpr int BN = SCHUR_BN;   // columns of a Schur tile
 constexpr int BK = 32;         // inner-dimension chunk
 
-// pivot d > 0 -> (sqrt(d), 1/sqrt(d)).  FP64: correctly rounded square root
-// and division.  FP32 (the refined mixed-precision path): the hardware
-// reciprocal square root, which keeps the serial pivot chain short; its few
-// ulps of error are far below what iterative refinement removes.
-__device__ __forceinline__ void pivot_root(double d, double &s, double &is) {
-    s = sqrt(d);
-    is = 1.0 / s;
-}
-__device__ __forceinline__ void pivot_root(float d, float &s, float &is) {
-    is = rsqrtf(d);
-    s = d * is;
-}
-
+using blk::load4;
 // four consecutive shared-memory elements (16-byte aligned for float,
 // two 16-byte halves for double)
-__device__ __forceinline__ void load4(float (&v)[4], const float *p) {
-    const float4 t = *reinterpret_cast<const float4 *>(p);
-    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
-}
-__device__ __forceinline__ void load4(double (&v)[4], const double *p) {
-    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
-    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
-}
 __device__ __forceinline__ void store4(float *p, const float (&v)[4]) {
     *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
@@ -163,270 +146,41 @@ __global__ void __launch_bounds__(THREADS) front_init_kernel(DevSym d, T *__rest
 }
 
 // ---------------------------------------------------------------------------
-// Cholesky of an nb x nb diagonal block (nb <= NB = 64) and the inverse of the
-// factor, written zero-padded as an NB x NB lower-triangular matrix
-// (column-major) to Dinv.  Right-looking by sub-blocks of 16 (loop not
-// unrolled, to keep the code small):
-//   1. one warp factors the 16 x 16 diagonal sub-block, one row per lane in
-//      registers (shuffles, no block barrier);
-//   2. the rows below are solved against it, one row per thread;
-//   3. the trailing lower part is updated with register tiles of 2 x 4.
-// The inverse, by 16 x 16 blocks X(i, j) of Linv: the diagonal inverses
-// X(i, i) (one warp each, one column per lane); then W(i, k) = X(i, i) L(i, k)
-// for all i > k at once; then one barrier step per block row i = 1, 2, 3:
-// X(i, j) = -sum_{k=j}^{i-1} W(i, k) X(k, j), which only reads block rows
-// finished before.  A pivot that is not positive records its global column in
-// *status (smallest wins) and is replaced by 1 so that the arithmetic stays
-// finite.  Must be called by a block of POTRF_THREADS threads.
+// diagonal block kb of front s (item = (s, kb)): L11 and L11^-1 (the first
+// pivot block of every front of a level; the later ones are factored by the
+// update launch of the step before).  FP32 fronts whose width is at least
+// diag64_min_k (> 0) factor the block in FP64.
 // ---------------------------------------------------------------------------
-constexpr int SB = 16;
-constexpr int POTRF_THREADS = 256;
-
-// Pivot C of a 16 x 16 Cholesky held by one warp, one row per lane (v),
-// then pivots C+1, ...: compile-time recursion, so every register index is a
-// constant.  The first pivot that is not positive is kept in `bad` (the caller
-// reports it), so the unrolled chain has no branch.
-template <class T, int C>
-struct WarpChol {
-    static __device__ __forceinline__ void step(T (&v)[SB], T &myinv, int lane, int w, int &bad) {
-        T dc = __shfl_sync(0xffffffffu, v[C], C);
-        const bool fail = C < w && !(dc > T(0));
-        bad = (fail && bad < 0) ? C : bad;
-        dc = (fail || C >= w) ? T(1) : dc;
-        T sc, ic;
-        pivot_root(dc, sc, ic);
-        v[C] = lane == C ? sc : (lane > C ? v[C] * ic : v[C]);
-        myinv = lane == C ? ic : myinv;
-#pragma unroll
-        for (int c2 = C + 1; c2 < SB; ++c2) {
-            const T lc = __shfl_sync(0xffffffffu, v[C], c2);
-            if (lane >= c2) v[c2] -= v[C] * lc;
-        }
-        WarpChol<T, C + 1>::step(v, myinv, lane, w, bad);
-    }
-};
 template <class T>
-struct WarpChol<T, SB> {
-    static __device__ __forceinline__ void step(T (&)[SB], T &, int, int, int &) {}
-};
-
-// Shared memory of the block factorization (element offsets): the factor
-// A[NB][NB + 1]; the inverse stored transposed, XT[c * XLD + r] = Linv(r, c),
-// with 16-byte aligned rows (XLD = NB + 4) so that four consecutive entries
-// are one vector load; the reciprocal pivots.  The strictly lower 16 x 16
-// blocks of XT (Linv's zero upper part) hold the products W(i, k).
-constexpr int XLD = NB + 4;
-constexpr int BP_XT = NB * (NB + 1);
-constexpr int BP_INVD = BP_XT + NB * XLD;
-constexpr int BP_ELEMS = BP_INVD + NB;
-
-// Issues, without committing, the cp.async copies of the lower part of the
-// nb x nb block at F (column-major, ld) into A (zero-filled outside it), and
-// zeroes XT.
-template <class T>
-__device__ void block_load(const T *F, int ld, int nb, T *smem) {
-    T(*A)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
-    T *XT = smem + BP_XT;
-    for (int idx = threadIdx.x; idx < NB * NB; idx += POTRF_THREADS) {
-        const int r = idx % NB, c = idx / NB;
-        cp_async_elem(&A[r][c], F + (int64_t)c * ld + r, r >= c && r < nb && c < nb);
-        XT[c * XLD + r] = T(0);
-    }
-}
-
-// Factors the block that block_load brought in (the caller has waited for
-// the copies and synchronised), leaving L in A and Linv in XT; if `write`,
-// stores L to Lout (ld NB, lower part) and Linv to Dinv.  Ends with XT final
-// and visible to the whole block.
-template <class T>
-__device__ void block_potrf_inv(int nb, int64_t gcol0, status_t *status, T *Dinv, T *Lout, bool write,
-                                T *smem) {
-    T(*A)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem);
-    T *XT = smem + BP_XT;
-    T *invd = smem + BP_INVD;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-#pragma unroll 1
-    for (int jb = 0; jb < nb; jb += SB) {
-        const int w = min(SB, nb - jb);
-        if (warp == 0) {
-            T v[SB], myinv = T(1);
-#pragma unroll 16
-            for (int c = 0; c < SB; ++c) v[c] = (lane < w && c <= lane) ? A[jb + lane][jb + c] : T(0);
-            int bad = -1;
-            WarpChol<T, 0>::step(v, myinv, lane, w, bad);
-            if (bad >= 0 && lane == 0) atomicMin(status, (status_t)(gcol0 + jb + bad));
-            if (lane < w) {
-#pragma unroll 16
-                for (int c = 0; c < SB; ++c)
-                    if (c <= lane) A[jb + lane][jb + c] = v[c];
-                invd[jb + lane] = myinv;
-            }
-        }
-        __syncthreads();
-        const int rem = nb - jb - w;
-        if (tid < rem) {
-            const int i = jb + w + tid;
-            T x[SB];
-#pragma unroll 16
-            for (int c = 0; c < SB; ++c) x[c] = A[i][jb + c];
-#pragma unroll 16
-            for (int c = 0; c < SB; ++c) {
-                T acc0 = x[c], acc1 = T(0);
-#pragma unroll 8
-                for (int p = 0; p + 1 < c; p += 2) {
-                    acc0 -= x[p] * A[jb + c][jb + p];
-                    acc1 -= x[p + 1] * A[jb + c][jb + p + 1];
-                }
-                if (c & 1) acc0 -= x[c - 1] * A[jb + c][jb + c - 1];
-                x[c] = (acc0 + acc1) * invd[jb + c];
-            }
-#pragma unroll 16
-            for (int c = 0; c < SB; ++c) A[i][jb + c] = x[c];
-        }
-        __syncthreads();
-        // trailing lower part, 2 x 4 register tiles
-        const int t0 = jb + w, ntr = (rem + 1) / 2, ntc = (rem + 3) / 4;
-        for (int q = tid; q < ntr * ntc; q += POTRF_THREADS) {
-            const int bi = q % ntr, bj = q / ntr;
-            const int r0 = t0 + 2 * bi, c0 = t0 + 4 * bj;
-            if (r0 + 1 < c0) continue;
-            T acc[2][4];
-#pragma unroll 2
-            for (int i = 0; i < 2; ++i)
-#pragma unroll 4
-                for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-#pragma unroll 4
-            for (int p = 0; p < SB; ++p) {
-                T ar[2], ac[4];
-#pragma unroll 2
-                for (int i = 0; i < 2; ++i) ar[i] = A[min(r0 + i, NB - 1)][jb + p];
-#pragma unroll 4
-                for (int j = 0; j < 4; ++j) ac[j] = A[min(c0 + j, NB - 1)][jb + p];
-#pragma unroll 2
-                for (int i = 0; i < 2; ++i)
-#pragma unroll 4
-                    for (int j = 0; j < 4; ++j) acc[i][j] += ar[i] * ac[j];
-            }
-#pragma unroll 2
-            for (int i = 0; i < 2; ++i)
-#pragma unroll 4
-                for (int j = 0; j < 4; ++j) {
-                    const int r = r0 + i, c = c0 + j;
-                    if (r < nb && c <= r) A[r][c] -= acc[i][j];
-                }
-        }
-        __syncthreads();
-    }
-    // X(i, i): the diagonal 16 x 16 inverses, one warp each, one column per lane
-    const int nsb = (nb + SB - 1) / SB;
-    if (warp < nsb && lane < SB) {
-        const int b0 = warp * SB, wv = min(SB, nb - b0), c = lane;
-        T x[SB];
-#pragma unroll 16
-        for (int r = 0; r < SB; ++r) {
-            T acc0 = (r == c) ? T(1) : T(0), acc1 = T(0);
-#pragma unroll 8
-            for (int p = 0; p + 1 < r; p += 2) {
-                acc0 -= A[b0 + r][b0 + p] * x[p];
-                acc1 -= A[b0 + r][b0 + p + 1] * x[p + 1];
-            }
-            if (r & 1) acc0 -= A[b0 + r][b0 + r - 1] * x[r - 1];
-            x[r] = (r < wv && c < wv) ? (acc0 + acc1) * invd[min(b0 + r, NB - 1)] : T(0);
-        }
-#pragma unroll 16
-        for (int r = 0; r < SB; ++r)
-            if (r >= c) XT[(b0 + c) * XLD + b0 + r] = x[r];
-    }
-    __syncthreads();
-    // W(i, k) = X(i, i) L(i, k), i > k, into XT's block (i, k); X(i, i)(r, t) is
-    // zero for t > r, so the sum runs over the whole sub-block
-    {
-        const int r = tid % SB, q = tid / SB;
-        for (int i = 1; i < nsb; ++i)
-            for (int k = 0; k < i; ++k) {
-                T acc0 = T(0), acc1 = T(0);
-#pragma unroll
-                for (int t = 0; t < SB; t += 2) {
-                    acc0 += XT[(SB * i + t) * XLD + SB * i + r] * A[SB * i + t][SB * k + q];
-                    acc1 += XT[(SB * i + t + 1) * XLD + SB * i + r] * A[SB * i + t + 1][SB * k + q];
-                }
-                XT[(SB * i + r) * XLD + SB * k + q] = acc0 + acc1;
-            }
-    }
-    __syncthreads();
-    // X(i, j)(r, c) = -sum_k sum_q W(i, k)(r, q) X(k, j)(q, c); both operands
-    // are rows of XT, read four entries at a time
-    {
-        const int r = tid % SB, c = tid / SB;
-#pragma unroll 1
-        for (int i = 1; i < nsb; ++i) {
-            for (int j = 0; j < i; ++j) {
-                T acc[4] = {T(0), T(0), T(0), T(0)};
-                for (int k = j; k < i; ++k) {
-                    const T *w = XT + (SB * i + r) * XLD + SB * k;
-                    const T *x = XT + (SB * j + c) * XLD + SB * k;
-#pragma unroll
-                    for (int q = 0; q < SB; q += 4) {
-                        T wv[4], xv[4];
-                        load4(wv, w + q);
-                        load4(xv, x + q);
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) acc[u] += wv[u] * xv[u];
-                    }
-                }
-                XT[(SB * j + c) * XLD + SB * i + r] = -((acc[0] + acc[1]) + (acc[2] + acc[3]));
-            }
-            __syncthreads();
-        }
-    }
-    if (write) {
-        for (int idx = tid; idx < NB * NB; idx += POTRF_THREADS) {
-            const int r = idx % NB, c = idx / NB;
-            Lout[idx] = (r >= c && r < nb) ? A[r][c] : T(0);
-            Dinv[idx] = (r >= c) ? XT[c * XLD + r] : T(0);
-        }
-    }
-}
-
-// the factored diagonal blocks (kept aside while the panels of a step still
-// read the unfactored block) into the fronts: item = (s, first pivot column)
-template <class T>
-__global__ void __launch_bounds__(THREADS) diag_copy_kernel(DevSym d, T *__restrict__ front,
-                                                            const T *__restrict__ ldiag,
-                                                            const int4 *__restrict__ items) {
+__global__ void __launch_bounds__(THREADS) diag_factor_kernel(DevSym d, T *__restrict__ front,
+                                                              T *__restrict__ dinv,
+                                                              const int4 *__restrict__ items,
+                                                              int diag64_min_k, status_t *status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int4 it = items[blockIdx.x];
-    const int s = it.x, j0 = it.y;
-    const Dims z = dims(d, s);
-    const int nb = min(NB, z.k - j0);
-    const T *Lb = ldiag + d.dinvoff[s] + (int64_t)(j0 / NB) * NB * NB;
-    T *F = front + d.foff[s] + (int64_t)j0 * z.ld + j0;
-    for (int idx = threadIdx.x; idx < NB * NB; idx += THREADS) {
-        const int r = idx % NB, c = idx / NB;
-        if (r >= c && r < nb) F[(int64_t)c * z.ld + r] = Lb[idx];
-    }
+    const int s = it.x, kb = it.y;
+    if (sizeof(T) == 4 && diag64_min_k > 0 && d.sk[s] >= diag64_min_k)
+        blk::factor_diag_block<double, T, THREADS>(d, front, dinv, s, kb, status, smem_raw);
+    else
+        blk::factor_diag_block<T, T, THREADS>(d, front, dinv, s, kb, status, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
-// potrf + panel of pivot block kb: every CTA factors the NB x NB diagonal block
-// and inverts the factor itself (the pivot chain is latency-bound: doing it
-// redundantly on many SMs costs nothing and saves a dependent launch per
-// step); CTA rb = 0 stores the factor (aside, in ldiag, since other CTAs of
-// the launch may still be reading the unfactored block) and the inverse.
-// Then rows [r0, r0+RB) of columns [kb, kb+nb):  X := X Linv^T.  The rows
-// start at kb+NB, or at kp when kb is the last block (rows [k, kp) are zero
-// padding); a CTA may have no rows (its launch item only factors the block).
+// panel of pivot block kb: rows [r0, r0+RB) of columns [kb, kb+nb) become
+// X := X L11^-T, with L11^-1 already in dinv.  The rows start at kb+NB, or
+// at kp when kb is the last block (rows [k, kp) are zero padding); a CTA may
+// have no rows.
 // ---------------------------------------------------------------------------
+constexpr int XLD = blk::XLD;
 template <class T>
-__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 3 : 1) panel_kernel(DevSym d, T *__restrict__ front,
-                                                        T *__restrict__ dinv, T *__restrict__ ldiag,
+__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2) panel_kernel(DevSym d, T *__restrict__ front,
+                                                        const T *__restrict__ dinv,
                                                         unsigned char *__restrict__ pk,
-                                                        const int4 *__restrict__ items, int kb,
-                                                        status_t *status) {
-    static_assert(THREADS == POTRF_THREADS, "the panel CTA runs the block factorization");
+                                                        const int4 *__restrict__ items, int kb) {
     static_assert(RB == 64 && NB == 64 && THREADS == 256, "4 x 4 register tiles cover the 64 x 64 panel block");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *Psm = reinterpret_cast<T *>(smem_raw);        // block factorization (BP_ELEMS)
-    T *Xs = Psm + BP_ELEMS;                           // [p][r], ld RB
+    T *LT = reinterpret_cast<T *>(smem_raw);         // LT[p * XLD + c] = Linv(c, p)
+    T *Xs = LT + NB * XLD;                            // [p][r], ld RB
     const int4 it = items[blockIdx.x];
     const int s = it.x, rb = it.y;
     const Dims z = dims(d, s);
@@ -434,16 +188,18 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 3 : 1) panel_kernel(
     const int t0 = kb + nb;
     const int r0 = (t0 == z.k ? z.kp : t0) + rb * RB;
     T *F = front + d.foff[s];
-    // the diagonal block first, in its own group: the pivot chain starts while
-    // the panel rows are still in flight
-    block_load<T>(F + (int64_t)kb * z.ld + kb, z.ld, nb, Psm);
-    cp_async_commit();
+    {
+        // Linv is stored column-major (Dv[c + p NB] = Linv(c, p)), so LT's rows
+        // are Dv's columns: 16-byte copies
+        const T *Dv = dinv + d.dinvoff[s] + (int64_t)(kb / NB) * NB * NB;
+        constexpr int V = 16 / sizeof(T);
+        for (int idx = threadIdx.x; idx < NB * NB / V; idx += THREADS) {
+            const int p = idx / (NB / V), c = (idx % (NB / V)) * V;
+            cp_async16(LT + p * XLD + c, Dv + p * NB + c, 16);
+        }
+    }
     stage_tile<T, THREADS>(Xs, RB, F + (int64_t)kb * z.ld + r0, z.ld, RB, NB, z.mp - r0, nb);
     cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    const int64_t boff = d.dinvoff[s] + (int64_t)(kb / NB) * NB * NB;
-    block_potrf_inv<T>(nb, d.sfirst[s] + kb, status, dinv + boff, ldiag + boff, rb == 0, Psm);
     cp_async_wait<0>();
     __syncthreads();
     // out[r][c] = sum_{p <= c} X[r][p] Linv(c, p), Linv(c, p) = XT[p][c];
@@ -451,7 +207,6 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 3 : 1) panel_kernel(
     // operands of a step p are one 4-wide shared load, and p stops at the
     // thread's last column (Linv is lower triangular).
     const int tid = threadIdx.x;
-    const T *LT = Psm + BP_XT;
     const int rq = tid % (RB / 4), cq = tid / (RB / 4);
     T acc[4][4];
 #pragma unroll
@@ -509,12 +264,15 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 3 : 1) panel_kernel(
 // columns ty + 16 j (i < 8, j < 4).
 //   mode 0 (step):  base = kb + NB, ka = kb, K = NB, cmax = k
 //   mode 1 (syrk):  base = kp, ka = 0, K = k, cmax = mp
+// In mode 0 the CTA of tile (0, 0), which holds the whole next diagonal
+// block, then factors that block (L11 and L11^-1 of step kb + NB).
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(THREADS) schur_kernel(DevSym d, T *__restrict__ front,
                                                         T *__restrict__ dinv,
                                                         const int4 *__restrict__ items, int kb,
                                                         int mode, status_t *status) {
+    static_assert(BM >= NB && BN >= NB, "tile (0, 0) covers the next diagonal block");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     T *As[2] = {sm, sm + BK * (BM + BN)};
@@ -588,12 +346,18 @@ __global__ void __launch_bounds__(THREADS) schur_kernel(DevSym d, T *__restrict_
             if (r < z.mp && r >= c) F[(int64_t)c * z.ld + r] -= acc[i][j];
         }
     }
+    if (mode == 0 && ti == 0 && tj == 0 && kb + NB < z.k) {
+        __syncthreads();   // the block's updated entries, written above, visible to the CTA
+        blk::factor_diag_block<T, T, THREADS>(d, front, dinv, s, kb + NB, status, smem_raw);
+    }
 }
 
 template <class T>
-constexpr size_t panel_smem() { return sizeof(T) * (BP_ELEMS + NB * RB); }
+constexpr size_t panel_smem() { return sizeof(T) * (NB * XLD + NB * RB); }
+constexpr size_t cmax_size(size_t a, size_t b) { return a > b ? a : b; }
 template <class T>
-constexpr size_t schur_smem() { return 2 * sizeof(T) * BK * (BM + BN); }
+constexpr size_t schur_smem() { return cmax_size(2 * sizeof(T) * BK * (BM + BN), blk::block_smem_bytes<T>()); }
+constexpr size_t diag_smem() { return blk::block_smem_bytes<double>(); }
 
 template <class T>
 void set_smem_attrs() {
@@ -603,6 +367,8 @@ void set_smem_attrs() {
                          (int)panel_smem<T>());
     cudaFuncSetAttribute(schur_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)schur_smem<T>());
+    cudaFuncSetAttribute(diag_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)diag_smem());
     done = true;
 }
 
@@ -621,18 +387,19 @@ void launch_front_init(const DevSym &d, T *front, const int4 *items, int count, 
 }
 
 template <class T>
-void launch_panel(const DevSym &d, T *front, T *dinv, T *ldiag, unsigned char *pk, const int4 *items,
-                  int count, int kb, status_t *status, cudaStream_t st) {
+void launch_diag_factor(const DevSym &d, T *front, T *dinv, const int4 *items, int count, int diag64_min_k,
+                        status_t *status, cudaStream_t st) {
     if (count <= 0) return;
     set_smem_attrs<T>();
-    panel_kernel<T><<<count, THREADS, panel_smem<T>(), st>>>(d, front, dinv, ldiag, pk, items, kb, status);
+    diag_factor_kernel<T><<<count, THREADS, diag_smem(), st>>>(d, front, dinv, items, diag64_min_k, status);
 }
 
 template <class T>
-void launch_diag_copy(const DevSym &d, T *front, const T *ldiag, const int4 *items, int count,
-                      cudaStream_t st) {
+void launch_panel(const DevSym &d, T *front, const T *dinv, unsigned char *pk, const int4 *items, int count,
+                  int kb, cudaStream_t st) {
     if (count <= 0) return;
-    diag_copy_kernel<T><<<count, THREADS, 0, st>>>(d, front, ldiag, items);
+    set_smem_attrs<T>();
+    panel_kernel<T><<<count, THREADS, panel_smem<T>(), st>>>(d, front, dinv, pk, items, kb);
 }
 
 template <class T>
@@ -645,10 +412,10 @@ void launch_schur(const DevSym &d, T *front, T *dinv, const int4 *items, int cou
 
 #define WD_INST(T)                                                                               \
     template void launch_front_init<T>(const DevSym &, T *, const int4 *, int, cudaStream_t);    \
-    template void launch_panel<T>(const DevSym &, T *, T *, T *, unsigned char *, const int4 *, int,  \
-                                  int, status_t *, cudaStream_t);                                \
-    template void launch_diag_copy<T>(const DevSym &, T *, const T *, const int4 *, int,         \
-                                      cudaStream_t);                                       \
+    template void launch_diag_factor<T>(const DevSym &, T *, T *, const int4 *, int, int, status_t *, \
+                                        cudaStream_t);                                           \
+    template void launch_panel<T>(const DevSym &, T *, const T *, unsigned char *, const int4 *, int, \
+                                  int, cudaStream_t);                                            \
     template void launch_schur<T>(const DevSym &, T *, T *, const int4 *, int, int, int,         \
                                   status_t *, cudaStream_t);
 WD_INST(double)

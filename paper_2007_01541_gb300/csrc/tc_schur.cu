@@ -18,9 +18,16 @@
 //   warps 2-9: epilogue, each thread one row and 64 columns of the tile: its
 //           part of C is loaded into registers while the MMAs run, then
 //           C -= acc (TMEM -> registers), lower part only
-// Every wait is bounded; on expiry the CTA records WD timeout status, still
-// frees its TMEM and returns.
+// In mode 0 (the pivot-column update of step kb) the CTA of tile (0, 0),
+// which holds the whole next diagonal block, then factors that block with all
+// its threads (L11 and L11^-1 of step kb + 64, in FP64 for wide fronts), so
+// the next panel launch only multiplies by the stored inverse.
+//
+// Every wait is bounded (wait_limit polls); on expiry the CTA records the
+// timeout status, waits (with a fixed bound) for its copies and products in
+// flight, frees its TMEM and returns without writing its tile.
 #include "engine.h"
+#include "front_block.cuh"
 #include "tc_common.cuh"
 
 namespace wd {
@@ -31,7 +38,9 @@ constexpr int STAGES = 3;
 constexpr int TILE_BYTES = TBM * TBK * 4;           // 16 KB per operand plane
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;          // A hi, A lo, B hi, B lo
 constexpr int TC_THREADS = 320;
-constexpr uint32_t WAIT_LIMIT = 1u << 26;
+constexpr uint32_t WAIT_LIMIT = 1u << 26;    // default bound of a wait (polls)
+constexpr uint32_t DRAIN_LIMIT = 1u << 26;   // bound of the waits for work in flight after a timeout
+static_assert(STAGES * STAGE_BYTES >= blk::block_smem_bytes<double>(), "the stages hold the block factorization");
 
 __device__ __forceinline__ void bulk_copy(void *dst_smem, const void *src, uint32_t bytes,
                                           uint64_t *bar) {
@@ -49,7 +58,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_schur_kernel(DevSym d, float *__restrict__ front, const unsigned char *__restrict__ pk,
-                    const int4 *__restrict__ items, int kb, int mode, status_t *tstatus) {
+                    const int4 *__restrict__ items, int kb, int mode, TcArgs a) {
+    const uint32_t limit = a.wait_limit ? a.wait_limit : WAIT_LIMIT;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -96,14 +106,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
 
+    int fills[STAGES] = {};   // producer lane: fills issued per stage
     if (warp == 0) {
         if (lane == 0) {
             for (int kt = 0; kt < nk; ++kt) {
                 const int st = kt % STAGES;
-                if (kt >= STAGES && !tc::mbar_wait(&empty[st], ((kt / STAGES) - 1) & 1, WAIT_LIMIT)) {
+                if (kt >= STAGES && !tc::mbar_wait(&empty[st], ((kt / STAGES) - 1) & 1, limit)) {
                     atomicExch(abort_flag, 1);
                     break;
                 }
+                if (*(volatile int *)abort_flag) break;
+                ++fills[st];
                 unsigned char *stg = sm + st * STAGE_BYTES;
                 const int kc = (ka / TBK) + kt;
                 mbar_expect_tx(&full[st], STAGE_BYTES);
@@ -119,7 +132,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             bool ok = true;
             for (int kt = 0; kt < nk; ++kt) {
                 const int st = kt % STAGES;
-                if (!tc::mbar_wait(&full[st], (kt / STAGES) & 1, WAIT_LIMIT)) {
+                if (!tc::mbar_wait(&full[st], (kt / STAGES) & 1, limit)) {
                     atomicExch(abort_flag, 1);
                     ok = false;
                     break;
@@ -138,9 +151,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc::mma_commit(&empty[st]);
             }
-            if (ok) tc::mma_commit(done);
-            else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tc::smem_u32(done))
-                              : "memory");
+            // arrives once every MMA issued above has completed (also after a
+            // timeout, so that no product is in flight when TMEM is freed)
+            tc::mma_commit(done);
+            (void)ok;
         }
     } else {
         // epilogue: warps 2..9; TMEM lane group = warp % 4, column half = (warp - 2) / 4
@@ -155,9 +169,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float cur[64];
 #pragma unroll
         for (int i = 0; i < 64; ++i) cur[i] = (i < nc) ? rowp[i * ld] : 0.0f;
-        const bool ok = tc::mbar_wait(done, 0, WAIT_LIMIT);
+        bool ok = tc::mbar_wait(done, 0, limit);
         tc::tc_fence_after();
-        if (ok && *abort_flag == 0) {
+        if (ok && a.gate != nullptr) {
+            // test of the timeout path: a gate that nothing opens
+            int open = 0;
+            if (lane == 0)
+                for (uint32_t i = 0; i < limit && !open; ++i) {
+                    open = *(volatile const unsigned *)a.gate != 0u;
+                    if (!open) __nanosleep(256);
+                }
+            ok = __shfl_sync(0xffffffffu, open, 0) != 0;
+        }
+        if (ok && *(volatile int *)abort_flag == 0) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 float v[16];
@@ -174,8 +198,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     tc::tc_fence_before();
     __syncthreads();
+    const bool aborted = *(volatile int *)abort_flag != 0;
+    if (aborted && tid == 0) {
+        // after a timeout: every issued fill has landed and every issued MMA
+        // has completed before the shared memory and TMEM are given up
+        for (int st = 0; st < STAGES; ++st)
+            if (fills[st] > 0) tc::mbar_wait(&full[st], (fills[st] - 1) & 1, DRAIN_LIMIT);
+        tc::mbar_wait(done, 0, DRAIN_LIMIT);
+    }
+    __syncthreads();
+    tc::tc_fence_after();
     if (warp == 1) tc::tmem_dealloc(tmem, TBN);
-    if (tid == 0 && *abort_flag) atomicMax(tstatus, 1ull);
+    if (aborted) {
+        if (tid == 0) atomicMax(a.tstatus, 1ull);
+        return;
+    }
+    if (mode == 0 && ti == 0 && tj == 0 && kb + NB < k) {
+        // the next diagonal block lies inside this tile, written above
+        if (a.diag64_min_k > 0 && k >= a.diag64_min_k)
+            blk::factor_diag_block<double, float, TC_THREADS>(d, front, a.dinv, s, kb + NB, a.status, sm);
+        else
+            blk::factor_diag_block<float, float, TC_THREADS>(d, front, a.dinv, s, kb + NB, a.status, sm);
+    }
 }
 
 }  // namespace
@@ -191,10 +235,10 @@ void init_tc_attributes() {
 }
 
 void launch_tc_schur(const DevSym &d, float *front, const unsigned char *pk, const int4 *items,
-                     int count, int kb, int mode, status_t *tstatus, cudaStream_t st) {
+                     int count, int kb, int mode, const TcArgs &a, cudaStream_t st) {
     if (count <= 0) return;
     init_tc_attributes();
-    tc_schur_kernel<<<count, TC_THREADS, tc_schur_smem(), st>>>(d, front, pk, items, kb, mode, tstatus);
+    tc_schur_kernel<<<count, TC_THREADS, tc_schur_smem(), st>>>(d, front, pk, items, kb, mode, a);
 }
 
 }  // namespace wd

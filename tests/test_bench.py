@@ -36,7 +36,7 @@ def test_roofline_classification(monkeypatch):
     assert tc["bound"] == "tensor"
     assert tc["peak"] == pytest.approx(1800.0 * 1.1 / 2.25)
     assert tc["achieved"] == pytest.approx(84.0)
-    alu = bench.roofline({"name": "potrf_panel_fp32", "ms": 1000.0, "flops": 8e12, "bytes": 0}, 64, key)
+    alu = bench.roofline({"name": "panel_fp32", "ms": 1000.0, "flops": 8e12, "bytes": 0}, 64, key)
     assert alu["bound"] == "alu" and alu["peak"] == pytest.approx(152 * 256 * 2070e6 / 1e12)
     df = bench.roofline({"name": "spmv_residual_df", "ms": 1000.0, "flops": 2e12, "bytes": 0}, 64, key)
     assert df["achieved"] == pytest.approx(bench.DF_OPS_PER_TERM * 1.0)

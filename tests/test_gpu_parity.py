@@ -283,3 +283,61 @@ def test_solve_device_padded_leading_dimension(wdlib, cuda, prec, nrhs):
     X = view.cpu().numpy()
     assert oracle.backward_error(cp, ri, v, X, B).max() <= 1e-12
     assert torch.all(store[:, o.n:] == 7.0)
+
+
+def test_mixed_with_fp64_diagonal_blocks(wdlib, cuda):
+    """WD_MIXED with every diagonal block factored in FP64 (diag64_min_k = 1):
+    the factor agrees with the oracle at the mixed tolerance, the refined
+    solve reaches the target, and refinement needs no more steps than with
+    FP32 diagonal blocks."""
+    b, cp, ri, v, o = _case("2d_J6")
+    B = rhs(o.n, 33, seed=2)
+    its = {}
+    for d64 in (0, 1):
+        s = wdlib.Solver(diag64_min_k=d64).analyze(cp, ri, b)
+        s.factor(v, "mixed")
+        L = s.L_csc_like(o.Lp, o.Li)
+        Lo = o.L_values()
+        starts = o.Lp[:-1]
+        rel = np.sqrt(np.add.reduceat((L - Lo) ** 2, starts) / np.add.reduceat(Lo ** 2, starts))
+        assert rel.max() <= 2e-5, (d64, rel.max())
+        X = s.solve(B)
+        assert oracle.backward_error(cp, ri, v, X, B).max() <= 1e-12
+        its[d64] = s.last_solve["iterations"]
+    assert its[1] <= its[0], its
+
+
+def test_fp64_diagonal_block_of_a_leaf_front(wdlib, cuda):
+    """A front without children assembles F11 = fl32(A11) exactly; with FP64
+    diagonal blocks its stored L11 is the FP64 Cholesky factor of that block
+    rounded to FP32 (within one FP32 ulp: the two FP64 factorizations differ
+    only in summation order)."""
+    b, cp, ri, v, o = _case("2d_J6")
+    s = wdlib.Solver(diag64_min_k=1).analyze(cp, ri, b).factor(v, "mixed")
+    sym = s.symbolic()
+    sf, srp = sym["super_first"], sym["super_rowptr"]
+    k = np.diff(sf).astype(np.int64)
+    m = np.diff(srp).astype(np.int64)
+    poff = np.concatenate([[0], np.cumsum(k * m)])
+    col2s = np.repeat(np.arange(k.size), k)
+    has_child = np.zeros(k.size, bool)
+    for t in range(k.size):
+        p = sym["parent"][sf[t + 1] - 1]
+        if p >= 0:
+            has_child[col2s[p]] = True
+    panels = s.export_L()
+    A = oracle.sym_lower_to_dense(cp, ri, v)[np.ix_(o.perm, o.perm)]
+    checked = 0
+    for t in np.flatnonzero(~has_child):
+        nb = int(min(k[t], 64))
+        if nb < 8:
+            continue
+        j0 = int(sf[t])
+        A11 = A[j0:j0 + nb, j0:j0 + nb].astype(np.float32).astype(np.float64)
+        ref = np.linalg.cholesky(A11).astype(np.float32)
+        pan = panels[poff[t]: poff[t + 1]].reshape(int(k[t]), int(m[t])).T   # m x k
+        L11 = pan[:nb, :nb].astype(np.float32)
+        ulp = np.spacing(np.abs(ref))
+        assert np.all(np.abs(L11 - ref) <= ulp), (t, float((np.abs(L11 - ref) / ulp).max()))
+        checked += 1
+    assert checked >= 10

@@ -164,3 +164,10 @@ def test_symbolic_amalgamation_golden(wdlib):
             assert list(sy["parent"]) == case["parent"]
             assert list(sy["colcount"]) == case["colcount"]
             assert list(sy["super_first"]) == run["super_first"], (case["name"], run)
+
+
+def test_invalid_options_are_rejected(wdlib):
+    for kw in (dict(wait_limit=-1), dict(diag64_min_k=-1), dict(test_fail_alloc=-2), dict(nd_leaf=0)):
+        with pytest.raises(wdlib.WdError) as e:
+            wdlib.Solver(symbolic_only=True, **kw)
+        assert e.value.status == wdlib.WD_ERR_INVALID_ARG
