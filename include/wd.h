@@ -87,7 +87,9 @@ typedef struct {
     int32_t test_fail_alloc; /* test hook, k > 0: the handle's k-th device
                                allocation fails as if memory ran out
                                (WD_ERR_OOM); counts from wd_create (0)        */
-    int32_t reserved[1];
+    int32_t solve_simt;     /* WD_MIXED, more than 8 right-hand sides: 1 runs
+                               the solves' products on the FP32 SIMT pipes
+                               instead of the tensor cores (0)                */
 } wd_options;
 
 /* Optional geometry for the nested-dissection ordering.  Per vertex (basis

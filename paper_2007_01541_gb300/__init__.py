@@ -40,7 +40,7 @@ class WdOptions(ctypes.Structure):
                 ("symbolic_only", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("diag64_min_k", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
                 ("test_closed_gate", ctypes.c_int32), ("test_fail_alloc", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("solve_simt", ctypes.c_int32)]
 
 
 class WdGeometry(ctypes.Structure):
@@ -163,7 +163,7 @@ class Solver:
     def __init__(self, nd_leaf=DEFAULTS["nd_leaf"], relax_k=DEFAULTS["relax_k"],
                  relax_pct=DEFAULTS["relax_pct"], ir_max_iter=10, ir_tol=1e-12,
                  symbolic_only=False, profile=False, use_graphs=True, diag64_min_k=None,
-                 wait_limit=0, test_closed_gate=False, test_fail_alloc=0):
+                 wait_limit=0, test_closed_gate=False, test_fail_alloc=0, solve_simt=False):
         self._lib = load()
         o = WdOptions()
         self._lib.wd_default_options(ctypes.byref(o))
@@ -177,6 +177,7 @@ class Solver:
         o.wait_limit = wait_limit
         o.test_closed_gate = 1 if test_closed_gate else 0
         o.test_fail_alloc = test_fail_alloc
+        o.solve_simt = 1 if solve_simt else 0
         self._h = ctypes.c_void_p()
         self._check(self._lib.wd_create(ctypes.byref(self._h), ctypes.byref(o)))
         self.n = None

@@ -492,7 +492,7 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, int large, Plan &p
     const int TRX = wd::solve_update_rows(large);   // rows per CTA of the xapply / bupdate items
     const int ng = (nrhs + TNW - 1) / TNW;
     const double R = nrhs;
-    const int SBW = wd::SB, KSR = wd::SOLVE_KSR;
+    const int SBW = wd::SB, KSR = large == 1 ? wd::SOLVE_KSR_TC : wd::SOLVE_KSR;
     auto nsb = [&](int s) { return (S.k(s) + SBW - 1) / SBW; };
     auto width = [&](int s, int sb) { return std::min(SBW, S.k(s) - sb * SBW); };
     auto wpad = [&](int s, int sb) { return (width(s, sb) + NB - 1) / NB * NB; };
@@ -556,7 +556,11 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, int large, Plan &p
                 if (nsb(s) <= sb) continue;
                 const int m = S.m(s), w = width(s, sb);
                 const int below = m - (sb * SBW + w);
-                const int nsplit = (below + KSR - 1) / KSR;
+                // tensor-core splits run over the front's storage rows from the
+                // 32-row boundary at or above the super-block's end
+                const int kbeg = (sb * SBW + w) & ~31;
+                const int nsplit = large == 1 ? (below > 0 ? (front_order(S, s) - kbeg + KSR - 1) / KSR : 0)
+                                              : (below + KSR - 1) / KSR;
                 for (int cb = 0; cb * TRW < w; ++cb)
                     for (int g = 0; g < ng; ++g) {
                         fin.push_back({s, sb * 8 + cb, g + 65536 * nsplit, slot});
@@ -1329,6 +1333,17 @@ static void enqueue_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st, boo
     const DevSym &d = h->dsym;
     const int rgt = h->splan.rgt;
     const int lg = h->splan.large;
+    // tensor-core products (FP32 only): forward xapply reads X's rows from the
+    // stored X^T, backward reads X^T's rows from X
+    wd::TcSolveArgs ta{};
+    ta.front = reinterpret_cast<const float *>(F);
+    ta.pk = h->d_pack;
+    ta.xsoff = h->d_xsoff;
+    ta.W = reinterpret_cast<float *>(W);
+    ta.tstatus = h->d_tstatus;
+    ta.nrhs = nrhs;
+    ta.wait_limit = (uint32_t)std::max(0, h->opt.wait_limit);
+    const bool tc = lg == 1 && sizeof(T) == 4;
     size_t li = 0;
     for (const Launch &L : h->splan.launches) {
         const int4 *it = h->splan.d_items + L.off;
@@ -1336,13 +1351,49 @@ static void enqueue_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st, boo
         switch (L.kind) {
             case K_FWD_GATHER: wd::launch_bfwd_gather<T>(d, Y, Tt, W, it, L.count, rgt, nrhs, st); break;
             case K_FWD_XAPPLY:
-                wd::launch_xapply<T>(d, Xs, h->d_xsoff, Tt, Y, it, L.count, 0, lg, nrhs, st);
+                if (tc) {
+                    wd::TcSolveArgs a = ta;
+                    a.xp = reinterpret_cast<const float *>(XTs);
+                    a.in = reinterpret_cast<const float *>(Tt);
+                    a.out = reinterpret_cast<float *>(Y);
+                    a.upper = 0;
+                    wd::launch_tc_xapply(d, a, it, L.count, st);
+                } else {
+                    wd::launch_xapply<T>(d, Xs, h->d_xsoff, Tt, Y, it, L.count, 0, lg, nrhs, st);
+                }
                 break;
-            case K_FWD_BUPDATE: wd::launch_bupdate<T>(d, F, Y, Tt, W, it, L.count, lg, nrhs, st); break;
-            case K_BWD_REDUCE: wd::launch_breduce<T>(d, F, Y, P, it, L.count, lg, nrhs, st); break;
+            case K_FWD_BUPDATE:
+                if (tc) {
+                    wd::TcSolveArgs a = ta;
+                    a.in = reinterpret_cast<const float *>(Y);
+                    a.out = reinterpret_cast<float *>(Tt);
+                    wd::launch_tc_bupdate(d, a, it, L.count, st);
+                } else {
+                    wd::launch_bupdate<T>(d, F, Y, Tt, W, it, L.count, lg, nrhs, st);
+                }
+                break;
+            case K_BWD_REDUCE:
+                if (tc) {
+                    wd::TcSolveArgs a = ta;
+                    a.in = reinterpret_cast<const float *>(Y);
+                    a.out = reinterpret_cast<float *>(P);
+                    wd::launch_tc_breduce(d, a, it, L.count, st);
+                } else {
+                    wd::launch_breduce<T>(d, F, Y, P, it, L.count, lg, nrhs, st);
+                }
+                break;
             case K_BWD_FINISH: wd::launch_breduce_finish<T>(d, Y, Tt, P, it, L.count, lg, nrhs, st); break;
             case K_BWD_XAPPLY:
-                wd::launch_xapply<T>(d, XTs, h->d_xsoff, Tt, Y, it, L.count, 1, lg, nrhs, st);
+                if (tc) {
+                    wd::TcSolveArgs a = ta;
+                    a.xp = reinterpret_cast<const float *>(Xs);
+                    a.in = reinterpret_cast<const float *>(Tt);
+                    a.out = reinterpret_cast<float *>(Y);
+                    a.upper = 1;
+                    wd::launch_tc_xapply(d, a, it, L.count, st);
+                } else {
+                    wd::launch_xapply<T>(d, XTs, h->d_xsoff, Tt, Y, it, L.count, 1, lg, nrhs, st);
+                }
                 break;
         }
         if (prof) record_event(h->prof_ev[2 * li + 1], st);
@@ -1442,9 +1493,11 @@ static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cud
 static wd_status prepare_solve(wd_handle h, int64_t nrhs) {
     wd_status s = ensure_solve_ws(h, nrhs);
     if (s != WD_OK) return s;
-    // tiles of 64 rows x 32 right-hand sides; up to 8 right-hand sides:
+    // tiles of 64 rows x 32 right-hand sides; FP32 with more than 8
+    // right-hand sides: tensor-core tiles of 128 rows x 64 right-hand sides
+    // (unless wd_options.solve_simt); up to 8 right-hand sides:
     // matrix-vector shaped kernels, lanes over rows
-    const int large = nrhs <= 8 ? 2 : 0;
+    const int large = nrhs <= 8 ? 2 : (h->prec == WD_MIXED && !h->opt.solve_simt ? 1 : 0);
     if (h->splan_nrhs != nrhs || h->splan.large != large) {
         build_solve_plan(h->S, (int)nrhs, large, h->splan);
         s = upload_plan(h, h->work, h->splan);
@@ -1491,6 +1544,7 @@ static wd_status solve_core(wd_handle h, double *Bd, int64_t ld, double *B, int6
         h->launches += 1;
     } else {
         float *Y = static_cast<float *>(h->d_Y);
+        CK(cudaMemsetAsync(h->d_tstatus, 0, sizeof(status_t), st), "status reset");
         wd::launch_transpose<float>(Y, h->d_Bp, n, nrhs, 0, 0, st);
         s = run_solve_plan<float>(h, Y, nr, st);
         if (s != WD_OK) return s;
@@ -1517,6 +1571,10 @@ static wd_status solve_core(wd_handle h, double *Bd, int64_t ld, double *B, int6
         }
         wd::launch_permute_out_rm(h->d_X, Bd, ld, h->dsym.perm, n, nrhs, st);
         h->launches += 1;
+        status_t tstatus = 0;
+        CK(cudaMemcpyAsync(&tstatus, h->d_tstatus, sizeof(status_t), cudaMemcpyDeviceToHost, st), "status D2H");
+        CK(cudaStreamSynchronize(st), "solve");
+        if (tstatus != 0) return fail(h, WD_ERR_TIMEOUT, "a bounded wait of a tensor-core solve product expired");
         if (be > h->opt.ir_tol) {
             if (!B_on_device)
                 cudaMemcpy2DAsync(B, ldb * sizeof(double), h->d_B, n * sizeof(double), n * sizeof(double),

@@ -45,11 +45,13 @@ void init_front_attributes();
 void init_solve_attributes();
 void init_tc_attributes();
 void init_blocked_attributes();
+void init_tc_solve_attributes();
 inline void init_kernel_attributes() {
     init_front_attributes();
     init_solve_attributes();
     init_tc_attributes();
     init_blocked_attributes();
+    init_tc_solve_attributes();
 }
 
 
@@ -208,7 +210,8 @@ template <class T>
 void launch_bfwd_gather(const DevSym &d, const T *Y, T *Tt, T *W, const int4 *items, int count, int rgt,
                         int nrhs, cudaStream_t st);
 // xapply / bupdate / breduce modes ("large"): 0 -> tiles of 64 rows x 32
-// right-hand sides per CTA; 2 -> up to 8 right-hand sides, matrix-vector
+// right-hand sides per CTA; 1 -> FP32 on the tensor cores, tiles of 128 rows
+// x 64 right-hand sides (tc_solve.cu); 2 -> up to 8 right-hand sides, matrix-vector
 // shaped (32 rows per xapply / bupdate CTA, lanes over rows; breduce keeps the
 // 64-column items and the 64 x 32 partial layout of mode 0); the partial-sum
 // tile sizes (the same for both modes):
@@ -231,6 +234,29 @@ void launch_breduce(const DevSym &d, const T *front, const T *Y, T *P, const int
 template <class T>
 void launch_breduce_finish(const DevSym &d, const T *Y, T *Tt, const T *P, const int4 *items, int count,
                            int large, int nrhs, cudaStream_t st);
+
+// ---- tensor-core products of the solves (tc_solve.cu; FP32 fronts, mode 1) --
+// Tiles of 128 rows (xapply, bupdate) or 128 pivot columns (breduce) x 64
+// right-hand sides; items as in mode 0 with these tile sizes; breduce splits
+// the rows below a super-block into SOLVE_KSR_TC storage rows of the front,
+// counted from the first 32-row boundary at or above the super-block's end.
+constexpr int SOLVE_KSR_TC = 256;
+struct TcSolveArgs {
+    const float *front;           // FP32 fronts
+    const unsigned char *pk;      // packed tf32 lines of L (bupdate's A)
+    const float *xp;              // xapply: forward X^T, backward X (super-block inverses)
+    const int64_t *xsoff;
+    const float *in;              // xapply: t; bupdate: y; breduce: x
+    float *out;                   // xapply: y / x; bupdate: the pending right-hand side; breduce: partials
+    float *W;                     // bupdate: update vectors
+    status_t *tstatus;            // nonzero after the launch: a bounded wait expired
+    int nrhs;
+    int upper;                    // xapply: 0 forward (lower X), 1 backward (X^T)
+    uint32_t wait_limit;          // 0: the default
+};
+void launch_tc_xapply(const DevSym &d, const TcSolveArgs &a, const int4 *items, int count, cudaStream_t st);
+void launch_tc_bupdate(const DevSym &d, const TcSolveArgs &a, const int4 *items, int count, cudaStream_t st);
+void launch_tc_breduce(const DevSym &d, const TcSolveArgs &a, const int4 *items, int count, cudaStream_t st);
 
 // ---- per-instance reductions of a block-diagonal batch (batch.cu) ----------
 // out[i] = ||A_i||_inf from the residual product's chunk items (partial:

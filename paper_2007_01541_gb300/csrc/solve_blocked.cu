@@ -758,8 +758,11 @@ void init_blocked_attributes() {
     done = true;
 }
 
-int solve_tile_rows(int) { return TileS::ROWS; }
-int solve_tile_rhs(int) { return TileS::RHS; }
+// the partial-sum tile of the tensor-core backward products (128 columns x 64
+// right-hand sides); only its ROWS and RHS are used
+using TileTc = TileCfg<16, 2>;
+int solve_tile_rows(int large) { return large == 1 ? TileTc::ROWS : TileS::ROWS; }
+int solve_tile_rhs(int large) { return large == 1 ? TileTc::RHS : TileS::RHS; }
 int solve_update_rows(int large) { return large == 2 ? NRW : solve_tile_rows(large); }
 
 template <class T>
@@ -852,9 +855,10 @@ void launch_breduce(const DevSym &d, const T *front, const T *Y, T *P, const int
 }
 template <class T>
 void launch_breduce_finish(const DevSym &d, const T *Y, T *Tt, const T *P, const int4 *items, int count,
-                           int, int nrhs, cudaStream_t st) {
+                           int large, int nrhs, cudaStream_t st) {
     if (count <= 0) return;
-    finish_go<T, TileS>(d, Y, Tt, P, items, count, nrhs, st);
+    if (large == 1) finish_go<T, TileTc>(d, Y, Tt, P, items, count, nrhs, st);
+    else finish_go<T, TileS>(d, Y, Tt, P, items, count, nrhs, st);
 }
 
 #define WD_BLOCKED_INST(T)                                                                              \

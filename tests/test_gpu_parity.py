@@ -341,3 +341,28 @@ def test_fp64_diagonal_block_of_a_leaf_front(wdlib, cuda):
         assert np.all(np.abs(L11 - ref) <= ulp), (t, float((np.abs(L11 - ref) / ulp).max()))
         checked += 1
     assert checked >= 10
+
+
+@pytest.mark.parametrize("name", ["1d_J10", "2d_J6", "2d_J7_exp"])
+@pytest.mark.parametrize("nrhs", [9, 64, 130])
+def test_tensor_core_solve_products_match_simt(wdlib, cuda, name, nrhs):
+    """Mixed precision, more than 8 right-hand sides: the solves' products on
+    the tensor cores (3xTF32, the default) against the FP32 SIMT kernels, on
+    the unrefined solution (ir_tol = 1 stops before any refinement step): both
+    are FP32-accurate solves of the same FP32 factor, so they agree to a few
+    FP32 roundings times the condition number; refined, both reach 1e-12."""
+    b, cp, ri, v, o = _case(name)
+    B = rhs(o.n, nrhs, seed=3)
+    X = {}
+    for simt in (False, True):
+        s = wdlib.Solver(ir_tol=1.0, solve_simt=simt).analyze(cp, ri, b).factor(v, "mixed")
+        X[simt] = s.solve(B)
+        assert s.last_solve["iterations"] == 0
+    ref = o.solve(B)
+    scale = np.abs(ref).max(0)
+    for simt in (False, True):
+        assert (np.abs(X[simt] - ref).max(0) / scale).max() <= 1e-3
+    assert (np.abs(X[False] - X[True]).max(0) / scale).max() <= 1e-4
+    s = wdlib.Solver().analyze(cp, ri, b).factor(v, "mixed")
+    Xr = s.solve(B)
+    assert oracle.backward_error(cp, ri, v, Xr, B).max() <= 1e-12
