@@ -176,7 +176,10 @@ __device__ __forceinline__ void load_chunk(const DevSym &d, const TcSolveArgs &a
             // t_B (pending right-hand side of the super-block's pivot rows)
             if (vj && kk < g.w) v = a.in[g.f + g.b0 + kk + coff];
         } else if (OP == OP_BUPDATE) {
-            if (vj && kk < g.w) v = a.in[g.f + g.b0 + kk + coff];   // y_B
+            // the chunk index counts the packed panel's 32-column chunks from
+            // the supernode's first column; y_B is indexed inside the super-block
+            const int kr = kk - g.b0;
+            if (vj && kr < g.w) v = a.in[g.f + g.b0 + kr + coff];   // y_B
         } else {
             // x at storage row kk: a pivot row after B, or a row of R
             if (vj && kk >= g.b0 + g.w && kk < g.q1) {
