@@ -47,6 +47,7 @@ FP32_LANES_PER_SM = 128
 FP64_FLOPS_PER_SM_CLK = 4     # 2 FP64 FMA per SM per clock (GB300: 1.25 TFLOP/s nominal)
 THETA, THETA_DT = 0.5, 1e-2      # theta workload: Crank-Nicolson, time step
 DF_OPS_PER_TERM = 12.75       # FP32 instructions per double-float multiply-add (12, plus a 6-op TwoSum every 8 terms)
+DF32_OPS_PER_TERM = 11.75     # the same with x exactly FP32 (one FMA less)
 
 # tf32 / bf16 dense tensor rates (nominal 1.1 and 2.25 PFLOP/s): a tf32
 # contraction's peak is the measured bf16 peak times this ratio
@@ -328,7 +329,7 @@ def roofline(top, nr, key):
                 "peak_source": ("measured bf16 sustained %.1f x nominal tf32/bf16 1.1/2.25" % bf16)
                 if "bf16_tflops_sustained" in peaks else "fallback 1700 x nominal tf32/bf16 1.1/2.25",
                 "work": "2 k flops per updated lower entry (the 3xTF32 split's extra MMAs count against it)"}
-    if name == "spmv_residual_df":
+    if name in ("spmv_residual_df", "spmv_residual_df32"):
         # double-float multiply-add: 12 FP32 instructions per (entry, right-hand
         # side) term (4 for the product, 6 for TwoSum, 2 to collect the error
         # terms) plus a 6-instruction renormalisation every 8 terms; the bound
@@ -336,11 +337,12 @@ def roofline(top, nr, key):
         terms = top["flops"] / 2.0
         sms, mhz, src = device_units()
         peak = sms * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
-        ach = DF_OPS_PER_TERM * terms / sec / 1e12
+        ops = DF_OPS_PER_TERM if name == "spmv_residual_df" else DF32_OPS_PER_TERM
+        ach = ops * terms / sec / 1e12
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s (FP32 lane operations)",
                 "frac": ach / peak, "traffic": measured_traffic(key, name), "kernel": name,
                 "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src})",
-                "work": "12.75 FP32 operations per stored entry of A and right-hand side"}
+                "work": f"{ops} FP32 operations per stored entry of A and right-hand side"}
     # the FP64 residual product with 8 or more right-hand sides does ~10 flops
     # per byte of A, above GB300's FP64 ridge point: bounded by the FP64 pipe
     alu = name.startswith(("schur_", "panel", "diag_factor", "fwd_xapply", "fwd_bupdate", "bwd_reduce",

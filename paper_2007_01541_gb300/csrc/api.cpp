@@ -1416,10 +1416,18 @@ static wd_status run_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st) {
 // R = Bp - A X (row-major n x nrhs, factor order) to FP64 accuracy: FP64 up
 // to 8 columns (with the device check of the column indices, read back by the
 // caller from d_spmv_bad), double-float arithmetic beyond
-static wd_status launch_residual(wd_handle h, const double *X, int64_t nrhs, cudaStream_t st) {
+static wd_status launch_residual(wd_handle h, const double *X, int64_t nrhs, cudaStream_t st,
+                                 const float *Xf = nullptr, const double *S = nullptr) {
     const int64_t n = h->S.n;
     const double nf = (double)h->nnz_full;
-    if (nrhs > 8) {
+    if (nrhs > 8 && Xf != nullptr) {
+        // x exactly FP32: R = S - A x (S = b, or R itself for the recurrence)
+        prof_single(h, "spmv_residual_df32", 0, 0, st, true);
+        wd::launch_spmv_residual_df32(h->dsym, h->d_spmv_chunks, h->n_spmv_chunks, h->d_spmv_fin,
+                                      h->n_spmv_fin, h->d_csr_vh, h->d_csr_vl, Xf, S, h->d_R, h->d_P, nrhs, st);
+        prof_single(h, "spmv_residual_df32", 2.0 * nf * nrhs, 12.0 * nf + 20.0 * n * nrhs, st, false);
+        h->launches += h->n_spmv_fin > 0 ? 2 : 1;
+    } else if (nrhs > 8) {
         // many right-hand sides: double-float arithmetic on the FP32 pipes
         prof_single(h, "spmv_residual_df", 0, 0, st, true);
         wd::launch_spmv_residual_df(h->dsym, h->d_spmv_chunks, h->n_spmv_chunks, h->d_spmv_fin,
@@ -1442,10 +1450,10 @@ static wd_status launch_residual(wd_handle h, const double *X, int64_t nrhs, cud
 // R = Bp - A X (FP64, row-major n x nrhs) and the largest normwise backward
 // error over the columns
 static wd_status backward_errors(wd_handle h, const double *X, int64_t nrhs, cudaStream_t st,
-                                 double *be_max) {
+                                 double *be_max, const float *Xf = nullptr, const double *S = nullptr) {
     const int64_t n = h->S.n;
     unsigned long long bad = ~0ULL;
-    wd_status rs = launch_residual(h, X, nrhs, st);
+    wd_status rs = launch_residual(h, X, nrhs, st, Xf, S);
     if (rs != WD_OK) return rs;
     if (h->batch_count > 0) {
         // per instance and column: each instance is its own system
@@ -1548,19 +1556,26 @@ static wd_status solve_core(wd_handle h, double *Bd, int64_t ld, double *B, int6
         wd::launch_transpose<float>(Y, h->d_Bp, n, nrhs, 0, 0, st);
         s = run_solve_plan<float>(h, Y, nr, st);
         if (s != WD_OK) return s;
-        wd::launch_transpose<float>(Y, h->d_X, n, nrhs, 1, 0, st);
+        // many right-hand sides: the solution and every correction are exactly
+        // FP32, so r_0 = b - A x_0 and r_{k+1} = r_k - A d_k take the FP32
+        // values (Xf, in the double-float split buffer) and never re-read the
+        // refined FP64 x; up to 8: the FP64 residual of x itself
+        float *Xf = nrhs > 8 ? reinterpret_cast<float *>(h->d_Xp) : nullptr;
+        if (Xf) wd::launch_xupdate(Y, h->d_X, Xf, n, nrhs, 0, st);
+        else wd::launch_transpose<float>(Y, h->d_X, n, nrhs, 1, 0, st);
         h->launches += 2;
         CK(cudaGetLastError(), "solve launch");
         double be = 1.0;
         int it = 0;
         for (;;) {
-            s = backward_errors(h, h->d_X, nrhs, st, &be);
+            s = backward_errors(h, h->d_X, nrhs, st, &be, Xf, it == 0 ? h->d_Bp : h->d_R);
             if (s != WD_OK) return s;
             if (be <= h->opt.ir_tol || it >= h->opt.ir_max_iter) break;
             wd::launch_transpose<float>(Y, h->d_R, n, nrhs, 0, 0, st);
             s = run_solve_plan<float>(h, Y, nr, st);
             if (s != WD_OK) return s;
-            wd::launch_transpose<float>(Y, h->d_X, n, nrhs, 1, 1, st);
+            if (Xf) wd::launch_xupdate(Y, h->d_X, Xf, n, nrhs, 1, st);
+            else wd::launch_transpose<float>(Y, h->d_X, n, nrhs, 1, 1, st);
             h->launches += 2;
             CK(cudaGetLastError(), "refinement launch");
             ++it;

@@ -150,6 +150,15 @@ void launch_spmv_residual(const DevSym &d, const int4 *chunks, int nchunks, cons
 void launch_spmv_residual_df(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin, int nfin,
                              const float *vh, const float *vl, const double *X, float2 *Xp,
                              const double *Bp, double *R, double *P, int64_t nrhs, cudaStream_t st);
+// R = S - A x in double-float arithmetic for x exactly FP32 (Xf, row-major
+// n x nrhs): the refinement's first residual (S = b) and its recurrence
+// r <- r - A d (S = R, in place)
+void launch_spmv_residual_df32(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin, int nfin,
+                               const float *vh, const float *vl, const float *Xf, const double *S, double *R,
+                               double *P, int64_t nrhs, cudaStream_t st);
+// Y (FP32, column-major) into X (FP64 row-major; = or +=) and Xf (FP32 row-major)
+void launch_xupdate(const float *Y, double *X, float *Xf, int64_t n, int64_t nrhs, int accumulate,
+                    cudaStream_t st);
 void launch_norm_inf_rows(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin,
                           int nfin, double *partial, double *out, cudaStream_t st);
 void launch_colmax3(const double *R, const double *X, const double *Bp, int64_t n,

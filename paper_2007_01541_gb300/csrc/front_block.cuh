@@ -91,16 +91,29 @@ template <class TC>
 constexpr size_t block_smem_bytes() { return sizeof(TC) * BP_ELEMS; }
 
 // Loads the lower part of the nb x nb block at F (column-major, ld) into A
-// (converted to TC, zero outside the block) and zeroes XT.  Ends with a
-// block barrier.
+// (converted to TC, zero outside the block) and zeroes XT.  All of a thread's
+// loads are issued before the first store, so their latencies overlap.  Ends
+// with a block barrier.
 template <class TC, class TF, int NT>
 __device__ void block_load(const TF *F, int ld, int nb, TC *smem) {
     TC(*A)[NB + 1] = reinterpret_cast<TC(*)[NB + 1]>(smem);
     TC *XT = smem + BP_XT;
-    for (int idx = threadIdx.x; idx < NB * NB; idx += NT) {
+    constexpr int PER = (NB * NB + NT - 1) / NT;
+    TF v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NT;
         const int r = idx % NB, c = idx / NB;
-        A[r][c] = (r >= c && r < nb && c < nb) ? (TC)F[(int64_t)c * ld + r] : TC(0);
-        XT[c * XLD + r] = TC(0);
+        v[u] = (idx < NB * NB && r >= c && r < nb && c < nb) ? F[(int64_t)c * ld + r] : TF(0);
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * NT;
+        if (idx < NB * NB) {
+            const int r = idx % NB, c = idx / NB;
+            A[r][c] = (TC)v[u];
+            XT[c * XLD + r] = TC(0);
+        }
     }
     __syncthreads();
 }

@@ -341,6 +341,129 @@ __global__ void __launch_bounds__(THREADS, 4) spmv_df_kernel(DevSym d, const int
     }
 }
 
+// s += (ah + al) x for x exactly an FP32 value: the product ah x is split
+// exactly (TwoProd), al x is the small correction
+__device__ __forceinline__ void df_add_prod1(DF &s, float ah, float al, float x) {
+    const float ph = __fmul_rn(ah, x);
+    float pl = __fmaf_rn(ah, x, -ph);
+    pl = __fmaf_rn(al, x, pl);
+    const float t = __fadd_rn(s.hi, ph);
+    const float z = __fsub_rn(t, s.hi);
+    const float e = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(ph, z));
+    s.hi = t;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(pl, e));
+}
+
+// R = S - A x for x held exactly in FP32 (row-major Xf), in double-float
+// arithmetic as spmv_df_kernel: the first residual of a mixed-precision solve
+// (x = the FP32 solution, S = b) and every later one by the recurrence
+// r_{k+1} = r_k - A d_k (x = the FP32 correction d_k, S = R in place, so the
+// refined x itself is never re-read).  Half the bytes of x per entry.  S and
+// R may be the same array: each element is read and then written by one
+// thread (chunked rows only write P here).
+__global__ void __launch_bounds__(THREADS, 4) spmv_df32_kernel(DevSym d, const int4 *__restrict__ items,
+                                                            int count, const float *__restrict__ vh,
+                                                            const float *__restrict__ vl,
+                                                            const float *__restrict__ Xf, const double *S,
+                                                            double *R, double *__restrict__ P, int nrhs) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= count) return;
+    const int4 it = items[w];
+    const int64_t row = it.x;
+    const int e0 = it.y, e1 = it.z, slot = it.w;
+    for (int c0 = 0; c0 < nrhs; c0 += 64) {
+        const int ca = c0 + lane, cb = c0 + 32 + lane;
+        const bool va = ca < nrhs, vb = cb < nrhs;
+        constexpr int NS = 4;
+        DF a[NS], b[NS];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) a[q] = b[q] = DF{0.f, 0.f};
+        for (int eb = e0; eb < e1; eb += 32) {
+            const int my = eb + lane, cnt = min(32, e1 - eb);
+            const int col = my < e1 ? d.csr_col[my] : 0;
+            const float mh = my < e1 ? vh[my] : 0.f, ml = my < e1 ? vl[my] : 0.f;
+            for (int j = 0; j < cnt; j += NS) {
+                float xa[NS], xb[NS], ah[NS], al[NS];
+#pragma unroll
+                for (int q = 0; q < NS; ++q) {
+                    const int src = (j + q) & 31;
+                    const int64_t xo = (int64_t)__shfl_sync(0xffffffffu, col, src) * nrhs;
+                    ah[q] = __shfl_sync(0xffffffffu, mh, src);
+                    al[q] = __shfl_sync(0xffffffffu, ml, src);
+                    const bool ok = j + q < cnt;
+                    xa[q] = (ok && va) ? Xf[xo + ca] : 0.f;
+                    xb[q] = (ok && vb) ? Xf[xo + cb] : 0.f;
+                }
+#pragma unroll
+                for (int q = 0; q < NS; ++q) {
+                    if (j + q < cnt) {
+                        df_add_prod1(a[q], ah[q], al[q], xa[q]);
+                        df_add_prod1(b[q], ah[q], al[q], xb[q]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                df_renorm(a[q]);
+                df_renorm(b[q]);
+            }
+        }
+        df_add(a[0], a[1]);
+        df_add(a[2], a[3]);
+        df_add(a[0], a[2]);
+        df_add(b[0], b[1]);
+        df_add(b[2], b[3]);
+        df_add(b[0], b[2]);
+        const double sa = (double)a[0].hi + (double)a[0].lo, sb = (double)b[0].hi + (double)b[0].lo;
+        if (slot < 0) {
+            if (va) R[row * nrhs + ca] = S[row * nrhs + ca] - sa;
+            if (vb) R[row * nrhs + cb] = S[row * nrhs + cb] - sb;
+        } else {
+            if (va) P[(int64_t)slot * nrhs + ca] = sa;
+            if (vb) P[(int64_t)slot * nrhs + cb] = sb;
+        }
+    }
+}
+
+// R = S - sum of a cut row's partial sums, in slot order (S may be R)
+__global__ void spmv_finish_src_kernel(const int4 *__restrict__ items, int count, const double *S, double *R,
+                                       const double *__restrict__ P, int nrhs) {
+    const int i = blockIdx.x;
+    if (i >= count) return;
+    const int4 it = items[i];
+    const int64_t row = it.x;
+    for (int c = threadIdx.x; c < nrhs; c += blockDim.x) {
+        double acc = 0.0;
+        for (int q = 0; q < it.z; ++q) acc += P[(int64_t)(it.y + q) * nrhs + c];
+        R[row * nrhs + c] = S[row * nrhs + c] - acc;
+    }
+}
+
+// The FP32 solution (or correction) Y, column-major n x nrhs, into the
+// row-major FP64 refinement vector X (=, or += if accumulate) and its FP32
+// row-major copy Xf (the x of spmv_df32_kernel)
+__global__ void xupdate_kernel(const float *__restrict__ Y, double *__restrict__ X, float *__restrict__ Xf,
+                               int64_t n, int64_t nrhs, int accumulate) {
+    __shared__ float tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int j = ty; j < 32; j += 8) {
+        const int64_t i = i0 + tx, c = c0 + j;
+        tile[j][tx] = (i < n && c < nrhs) ? Y[i + c * n] : 0.f;
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        const int64_t i = i0 + j, c = c0 + tx;
+        if (i < n && c < nrhs) {
+            const float v = tile[tx][j];
+            const int64_t o = i * nrhs + c;
+            X[o] = accumulate ? X[o] + (double)v : (double)v;
+            Xf[o] = v;
+        }
+    }
+}
+
 // Few right-hand sides (<= 8): lanes over the entries of the chunk, NR (the
 // number of right-hand sides rounded up to 1, 2, 4 or 8) accumulators per
 // lane and U = 4 entries per lane in flight (their values, columns and x loads
@@ -617,6 +740,20 @@ void launch_spmv_residual_df(const DevSym &d, const int4 *chunks, int nchunks, c
     const int blocks = (int)(((int64_t)nchunks * 32 + THREADS - 1) / THREADS);
     spmv_df_kernel<<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, vh, vl, Xp, Bp, R, P, (int)nrhs);
     if (nfin > 0) spmv_finish_kernel<<<nfin, 64, 0, st>>>(fin, nfin, Bp, R, P, (int)nrhs);
+}
+
+void launch_spmv_residual_df32(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin, int nfin,
+                               const float *vh, const float *vl, const float *Xf, const double *S, double *R,
+                               double *P, int64_t nrhs, cudaStream_t st) {
+    const int blocks = (int)(((int64_t)nchunks * 32 + THREADS - 1) / THREADS);
+    spmv_df32_kernel<<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, vh, vl, Xf, S, R, P, (int)nrhs);
+    if (nfin > 0) spmv_finish_src_kernel<<<nfin, 64, 0, st>>>(fin, nfin, S, R, P, (int)nrhs);
+}
+
+void launch_xupdate(const float *Y, double *X, float *Xf, int64_t n, int64_t nrhs, int accumulate,
+                    cudaStream_t st) {
+    const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((nrhs + 31) / 32));
+    xupdate_kernel<<<grid, dim3(32, 8), 0, st>>>(Y, X, Xf, n, nrhs, accumulate);
 }
 
 void launch_norm_inf_rows(const DevSym &d, const int4 *chunks, int nchunks, const int4 *fin,
