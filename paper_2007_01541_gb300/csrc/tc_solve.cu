@@ -17,9 +17,11 @@
 // from the packed tf32 lines the panel kernel wrote; every other operand is
 // read from its FP32 array (the super-block inverses, the fronts' columns, the
 // right-hand-side columns), split by the CTA's threads and stored swizzled.
-// The loads of the next 32-wide chunk of the inner dimension are issued before
-// the current chunk is split and stored; two shared-memory stages alternate,
-// the MMAs of a chunk running while the next one is prepared.
+// The asynchronous copies of a 32-wide chunk of the inner dimension are issued
+// two chunks ahead into a ring of three shared-memory stages, straight to the
+// values' swizzled places; each thread then splits the values it copied in
+// place (hi) and into the lo plane, and one thread issues the chunk's MMAs
+// while the next chunks are in flight.
 //
 // Every wait is bounded; on expiry the CTA records the timeout status, waits
 // (with a fixed bound) for its copies and products in flight, frees its tensor
@@ -36,7 +38,7 @@ constexpr int NTH = 256;
 constexpr int A_BYTES = TM * TK * 4;           // one plane of A: 16 KB
 constexpr int B_BYTES = TN * TK * 4;           // one plane of B: 8 KB
 constexpr int STG_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int NSTG = 2;
+constexpr int NSTG = 3;                         // stages in flight (chunks issued ahead: NSTG - 1)
 constexpr uint32_t WAIT_DEFAULT = 1u << 26;
 constexpr uint32_t DRAIN_LIMIT = 1u << 26;
 
@@ -53,17 +55,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tc::smem_u32(bar)),
                  "r"(bytes)
                  : "memory");
-}
-
-// four values of one operand row -> tf32 hi / lo planes at the swizzled
-// position of (row, k .. k+3) (k a multiple of 4)
-__device__ __forceinline__ void put4(unsigned char *hi, unsigned char *lo, int row, int k, const float (&v)[4]) {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) tc::split_tf32(v[i], h[i], l[i]);
-    const uint32_t off = tc::sw128_offset(row, k);
-    *reinterpret_cast<uint4 *>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4 *>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // Per-item geometry of the three products (see the plan in api.cpp).
@@ -130,17 +121,19 @@ __device__ __forceinline__ Geo geometry(const DevSym &d, const TcSolveArgs &a, i
     return g;
 }
 
-// Loads of chunk c of the FP32 operands into registers: A (16 consecutive
-// inner values of row tid / 2) where it is read from an array, B (8
-// consecutive inner values of right-hand side tid / 4).
+// Issues the asynchronous copies of chunk c of the FP32 operands into a stage,
+// each value to its swizzled place in the hi plane (split later in place):
+// A, where it is read from an array, as 16-byte copies (row tid / 2, inner
+// values (tid % 2) 16 .. +16), B as 4-byte copies (right-hand side tid / 4,
+// inner values (tid % 4) 8 .. +8).  Values outside the operand are zero-filled.
 template <int OP>
-__device__ __forceinline__ void load_chunk(const DevSym &d, const TcSolveArgs &a, const Geo &g, int c,
-                                           float (&ra)[16], float (&rb)[8]) {
+__device__ __forceinline__ void issue_chunk(const DevSym &d, const TcSolveArgs &a, const Geo &g, int c,
+                                            unsigned char *Ah, unsigned char *Bh) {
     const int tid = threadIdx.x;
     const int kk0 = (g.kc0 + c) * TK;   // first inner index of the chunk
     if (OP != OP_BUPDATE) {
         const int r = tid >> 1, kh = (tid & 1) * 16;
-        const float *src = nullptr;
+        const float *src;
         bool ok;
         if (OP == OP_XAPPLY) {
             // row r0 + r of X (forward: the stored X^T, column-major, holds X's
@@ -161,8 +154,7 @@ __device__ __forceinline__ void load_chunk(const DevSym &d, const TcSolveArgs &a
             const int kblk = (kk0 + kh + 4 * q) / NB;
             const bool side = OP != OP_XAPPLY || (a.upper ? kblk >= rblk : kblk <= rblk);
             const bool v = ok && side && kk0 + kh + 4 * q < lim;
-            const float4 t = v ? *reinterpret_cast<const float4 *>(src + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
-            ra[4 * q] = t.x, ra[4 * q + 1] = t.y, ra[4 * q + 2] = t.z, ra[4 * q + 3] = t.w;
+            cp_async16(Ah + tc::sw128_offset(r, kh + 4 * q), v ? src + 4 * q : a.front, v ? 16 : 0);
         }
     }
     const int j = tid >> 2, kq = (tid & 3) * 8;
@@ -171,24 +163,52 @@ __device__ __forceinline__ void load_chunk(const DevSym &d, const TcSolveArgs &a
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int kk = kk0 + kq + q;
-        float v = 0.f;
+        const float *src = nullptr;
         if (OP == OP_XAPPLY) {
             // t_B (pending right-hand side of the super-block's pivot rows)
-            if (vj && kk < g.w) v = a.in[g.f + g.b0 + kk + coff];
+            if (vj && kk < g.w) src = a.in + g.f + g.b0 + kk + coff;
         } else if (OP == OP_BUPDATE) {
             // the chunk index counts the packed panel's 32-column chunks from
             // the supernode's first column; y_B is indexed inside the super-block
             const int kr = kk - g.b0;
-            if (vj && kr < g.w) v = a.in[g.f + g.b0 + kr + coff];   // y_B
+            if (vj && kr < g.w) src = a.in + g.f + g.b0 + kr + coff;
         } else {
             // x at storage row kk: a pivot row after B, or a row of R
             if (vj && kk >= g.b0 + g.w && kk < g.q1) {
-                if (kk < g.k) v = a.in[g.f + kk + coff];
-                else if (kk >= g.kp) v = a.in[d.rows[d.rowptr[g.s] + g.k + (kk - g.kp)] + coff];
+                if (kk < g.k) src = a.in + g.f + kk + coff;
+                else if (kk >= g.kp) src = a.in + d.rows[d.rowptr[g.s] + g.k + (kk - g.kp)] + coff;
             }
         }
-        rb[q] = v;
+        cp_async4(Bh + tc::sw128_offset(j, kq + q), src ? src : a.in, src ? 4 : 0);
     }
+}
+
+// x -> (hi, lo) in place for four values: hi = x rounded to tf32 back into the
+// hi plane, lo = (x - hi) rounded to tf32 into the lo plane
+__device__ __forceinline__ void split4_inplace(unsigned char *hi, unsigned char *lo, uint32_t off) {
+    const uint4 x = *reinterpret_cast<const uint4 *>(hi + off);
+    const float v[4] = {__uint_as_float(x.x), __uint_as_float(x.y), __uint_as_float(x.z), __uint_as_float(x.w)};
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) tc::split_tf32(v[i], h[i], l[i]);
+    *reinterpret_cast<uint4 *>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4 *>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Splits the values this thread copied in issue_chunk (its own copies are
+// complete after cp.async.wait_group, so no barrier is needed before).
+template <int OP>
+__device__ __forceinline__ void split_chunk(unsigned char *Ah, unsigned char *Al, unsigned char *Bh,
+                                            unsigned char *Bl) {
+    const int tid = threadIdx.x;
+    if (OP != OP_BUPDATE) {
+        const int r = tid >> 1, kh = (tid & 1) * 16;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) split4_inplace(Ah, Al, tc::sw128_offset(r, kh + 4 * q));
+    }
+    const int j = tid >> 2, kq = (tid & 3) * 8;
+    split4_inplace(Bh, Bl, tc::sw128_offset(j, kq));
+    split4_inplace(Bh, Bl, tc::sw128_offset(j, kq + 4));
 }
 
 template <int OP>
@@ -222,45 +242,40 @@ __global__ void __launch_bounds__(NTH, 1) tc_solve_kernel(DevSym d, TcSolveArgs 
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    int fills[NSTG] = {0, 0};   // thread 0: bulk fills issued per stage
-    float ra[16], rb[8], na[16], nbv[8];
-    if (g.nchunk > 0) load_chunk<OP>(d, a, g, 0, ra, rb);
     const uint32_t idesc = tc::idesc_tf32(TM, TN);
-    for (int c = 0; c < g.nchunk; ++c) {
-        const int st = c & 1;
-        if (c + 1 < g.nchunk) load_chunk<OP>(d, a, g, c + 1, na, nbv);
-        if (tid == 0 && c >= NSTG && !tc::mbar_wait(&empty[st], ((c >> 1) - 1) & 1, limit))
+    // chunk cc goes to stage cc % NSTG; before it is issued, the MMAs of the
+    // chunk that used the stage last (cc - NSTG) must have completed
+    int issued = 0;
+    auto issue = [&](int cc) {
+        const int st = cc % NSTG;
+        if (cc >= NSTG && !tc::mbar_wait(&empty[st], ((cc / NSTG) - 1) & 1, limit)) {
             atomicExch(abort_flag, 1);
-        __syncthreads();
-        if (*(volatile int *)abort_flag) break;
+            return;
+        }
         unsigned char *stg = sm + st * STG_BYTES;
-        unsigned char *Ah = stg, *Al = stg + A_BYTES, *Bh = stg + 2 * A_BYTES, *Bl = Bh + B_BYTES;
-        if (OP == OP_BUPDATE) {
-            if (tid == 0) {
-                ++fills[st];
-                mbar_expect_tx(&full[st], 2 * A_BYTES);
-                bulk_copy(Ah, P + pack_offset(g.kc0 + c, 0, g.mrow, prow), A_BYTES, &full[st]);
-                bulk_copy(Al, P + pack_offset(g.kc0 + c, 1, g.mrow, prow), A_BYTES, &full[st]);
-            }
-        } else {
-            const int r = tid >> 1, kh = (tid & 1) * 16;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float v4[4] = {ra[4 * q], ra[4 * q + 1], ra[4 * q + 2], ra[4 * q + 3]};
-                put4(Ah, Al, r, kh + 4 * q, v4);
-            }
+        if (OP == OP_BUPDATE && tid == 0) {
+            mbar_expect_tx(&full[st], 2 * A_BYTES);
+            bulk_copy(stg, P + pack_offset(g.kc0 + cc, 0, g.mrow, prow), A_BYTES, &full[st]);
+            bulk_copy(stg + A_BYTES, P + pack_offset(g.kc0 + cc, 1, g.mrow, prow), A_BYTES, &full[st]);
         }
-        {
-            const int j = tid >> 2, kq = (tid & 3) * 8;
-            const float v0[4] = {rb[0], rb[1], rb[2], rb[3]}, v1[4] = {rb[4], rb[5], rb[6], rb[7]};
-            put4(Bh, Bl, j, kq, v0);
-            put4(Bh, Bl, j, kq + 4, v1);
-        }
+        issue_chunk<OP>(d, a, g, cc, stg, stg + 2 * A_BYTES);
+        issued = cc + 1;
+    };
+    for (int cc = 0; cc < NSTG - 1; ++cc) {
+        if (cc < g.nchunk) issue(cc);
+        cp_async_commit();
+    }
+    for (int c = 0; c < g.nchunk; ++c) {
+        const int st = c % NSTG;
+        unsigned char *stg = sm + st * STG_BYTES;
+        cp_async_wait<NSTG - 2>();     // this thread's copies of chunk c have landed
+        split_chunk<OP>(stg, stg + A_BYTES, stg + 2 * A_BYTES, stg + 2 * A_BYTES + B_BYTES);
         tc::fence_async_smem();
         __syncthreads();
+        if (*(volatile int *)abort_flag) break;
         if (tid == 0) {
             bool ok = true;
-            if (OP == OP_BUPDATE) ok = tc::mbar_wait(&full[st], (fills[st] - 1) & 1, limit);
+            if (OP == OP_BUPDATE) ok = tc::mbar_wait(&full[st], (c / NSTG) & 1, limit);
             if (ok) {
                 tc::tc_fence_after();
                 const uint32_t a0 = tc::smem_u32(stg);
@@ -279,11 +294,10 @@ __global__ void __launch_bounds__(NTH, 1) tc_solve_kernel(DevSym d, TcSolveArgs 
             }
             tc::mma_commit(&empty[st]);
         }
-#pragma unroll
-        for (int i = 0; i < 16; ++i) ra[i] = na[i];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) rb[i] = nbv[i];
+        if (c + NSTG - 1 < g.nchunk) issue(c + NSTG - 1);
+        cp_async_commit();
     }
+    cp_async_wait<0>();
     // every MMA issued above has completed once `done` arrives
     if (tid == 0) tc::mma_commit(done);
     if (!tc::mbar_wait(done, 0, limit)) atomicExch(abort_flag, 1);
@@ -337,10 +351,12 @@ __global__ void __launch_bounds__(NTH, 1) tc_solve_kernel(DevSym d, TcSolveArgs 
             for (int i = 0; i < 32; ++i) o[(int64_t)i * TM] = v[i];
         }
     } else if (tid == 0) {
-        // after a timeout: the issued fills have landed and the issued MMAs
-        // have completed before the shared memory and TMEM are given up
-        for (int st = 0; st < NSTG; ++st)
-            if (fills[st] > 0) tc::mbar_wait(&full[st], (fills[st] - 1) & 1, DRAIN_LIMIT);
+        // after a timeout: the issued bulk fills have landed and the issued
+        // MMAs have completed before the shared memory and TMEM are given up
+        // (every thread's own copies were waited for above)
+        if (OP == OP_BUPDATE)
+            for (int cc = (issued > NSTG ? issued - NSTG : 0); cc < issued; ++cc)
+                tc::mbar_wait(&full[cc % NSTG], (cc / NSTG) & 1, DRAIN_LIMIT);
         tc::mbar_wait(done, 0, DRAIN_LIMIT);
         atomicMax(a.tstatus, 1ull);
     }
