@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(THREADS) front_init_kernel(DevSym d, T *__rest
 // update launch of the step before).  FP32 fronts whose width is at least
 // diag64_min_k (> 0) factor the block in FP64.
 // ---------------------------------------------------------------------------
-template <class T>
+template <class T, bool HAS64>
 __global__ void __launch_bounds__(THREADS) diag_factor_kernel(DevSym d, T *__restrict__ front,
                                                               T *__restrict__ dinv,
                                                               const int4 *__restrict__ items,
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(THREADS) diag_factor_kernel(DevSym d, T *__res
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int4 it = items[blockIdx.x];
     const int s = it.x, kb = it.y;
-    if (sizeof(T) == 4 && diag64_min_k > 0 && d.sk[s] >= diag64_min_k)
+    if (HAS64 && sizeof(T) == 4 && diag64_min_k > 0 && d.sk[s] >= diag64_min_k)
         blk::factor_diag_block<double, T, THREADS>(d, front, dinv, s, kb, status, smem_raw);
     else
         blk::factor_diag_block<T, T, THREADS>(d, front, dinv, s, kb, status, smem_raw);
@@ -367,7 +367,9 @@ void set_smem_attrs() {
                          (int)panel_smem<T>());
     cudaFuncSetAttribute(schur_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)schur_smem<T>());
-    cudaFuncSetAttribute(diag_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(diag_factor_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)diag_smem());
+    cudaFuncSetAttribute(diag_factor_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)diag_smem());
     done = true;
 }
@@ -391,7 +393,10 @@ void launch_diag_factor(const DevSym &d, T *front, T *dinv, const int4 *items, i
                         status_t *status, cudaStream_t st) {
     if (count <= 0) return;
     set_smem_attrs<T>();
-    diag_factor_kernel<T><<<count, THREADS, diag_smem(), st>>>(d, front, dinv, items, diag64_min_k, status);
+    if (sizeof(T) == 4 && diag64_min_k > 0)
+        diag_factor_kernel<T, true><<<count, THREADS, diag_smem(), st>>>(d, front, dinv, items, diag64_min_k, status);
+    else
+        diag_factor_kernel<T, false><<<count, THREADS, diag_smem(), st>>>(d, front, dinv, items, diag64_min_k, status);
 }
 
 template <class T>

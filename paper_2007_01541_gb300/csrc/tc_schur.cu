@@ -56,6 +56,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                  : "memory");
 }
 
+// HAS64: the launch may factor diagonal blocks in FP64 (instantiated apart,
+// so that the usual FP32 kernel carries only the FP32 block factorization)
+template <bool HAS64>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_schur_kernel(DevSym d, float *__restrict__ front, const unsigned char *__restrict__ pk,
                     const int4 *__restrict__ items, int kb, int mode, TcArgs a) {
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     if (mode == 0 && ti == 0 && tj == 0 && kb + NB < k) {
         // the next diagonal block lies inside this tile, written above
-        if (a.diag64_min_k > 0 && k >= a.diag64_min_k)
+        if (HAS64 && a.diag64_min_k > 0 && k >= a.diag64_min_k)
             blk::factor_diag_block<double, float, TC_THREADS>(d, front, a.dinv, s, kb + NB, a.status, sm);
         else
             blk::factor_diag_block<float, float, TC_THREADS>(d, front, a.dinv, s, kb + NB, a.status, sm);
@@ -229,7 +232,9 @@ size_t tc_schur_smem() { return (size_t)STAGES * STAGE_BYTES + 1024 + 128; }
 void init_tc_attributes() {
     static bool done = false;
     if (done) return;
-    cudaFuncSetAttribute(tc_schur_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(tc_schur_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tc_schur_smem());
+    cudaFuncSetAttribute(tc_schur_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tc_schur_smem());
     done = true;
 }
@@ -238,7 +243,10 @@ void launch_tc_schur(const DevSym &d, float *front, const unsigned char *pk, con
                      int count, int kb, int mode, const TcArgs &a, cudaStream_t st) {
     if (count <= 0) return;
     init_tc_attributes();
-    tc_schur_kernel<<<count, TC_THREADS, tc_schur_smem(), st>>>(d, front, pk, items, kb, mode, a);
+    if (a.diag64_min_k > 0 && mode == 0)
+        tc_schur_kernel<true><<<count, TC_THREADS, tc_schur_smem(), st>>>(d, front, pk, items, kb, mode, a);
+    else
+        tc_schur_kernel<false><<<count, TC_THREADS, tc_schur_smem(), st>>>(d, front, pk, items, kb, mode, a);
 }
 
 }  // namespace wd
