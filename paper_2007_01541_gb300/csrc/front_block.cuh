@@ -7,7 +7,7 @@
 // and written back: L11 into the front, L11^-1 (zero-padded to NB x NB,
 // column-major) into the inverse store.  Right-looking by sub-blocks of 16:
 //   1. one warp factors the 16 x 16 diagonal sub-block, one row per lane in
-//      registers (shuffles, no block barrier; the pivot runs as a loop);
+//      registers (shuffles, no block barrier);
 //   2. the rows below are solved against it, one row per thread;
 //   3. the trailing lower part is updated with register tiles of 2 x 4.
 // The inverse, by 16 x 16 blocks X(i, j) of L11^-1: the diagonal inverses
@@ -37,6 +37,34 @@ __device__ __forceinline__ void pivot_root(float d, float &s, float &is) {
     is = rsqrtf(d);
     s = d * is;
 }
+
+// Pivot C of a 16 x 16 Cholesky held by one warp, one row per lane (v),
+// then pivots C+1, ...: compile-time recursion, so every register index is a
+// constant.  The first pivot that is not positive is kept in `bad` (the caller
+// reports it), so the unrolled chain has no branch.
+template <class T, int C>
+struct WarpChol {
+    static __device__ __forceinline__ void step(T (&v)[SB], T &myinv, int lane, int w, int &bad) {
+        T dc = __shfl_sync(0xffffffffu, v[C], C);
+        const bool fail = C < w && !(dc > T(0));
+        bad = (fail && bad < 0) ? C : bad;
+        dc = (fail || C >= w) ? T(1) : dc;
+        T sc, ic;
+        pivot_root(dc, sc, ic);
+        v[C] = lane == C ? sc : (lane > C ? v[C] * ic : v[C]);
+        myinv = lane == C ? ic : myinv;
+#pragma unroll
+        for (int c2 = C + 1; c2 < SB; ++c2) {
+            const T lc = __shfl_sync(0xffffffffu, v[C], c2);
+            if (lane >= c2) v[c2] -= v[C] * lc;
+        }
+        WarpChol<T, C + 1>::step(v, myinv, lane, w, bad);
+    }
+};
+template <class T>
+struct WarpChol<T, SB> {
+    static __device__ __forceinline__ void step(T (&)[SB], T &, int, int, int &) {}
+};
 
 // four consecutive shared-memory elements (16-byte aligned for float, two
 // 16-byte halves for double)
@@ -92,10 +120,7 @@ __device__ void block_load(const TF *F, int ld, int nb, TC *smem) {
 
 // Factors the block that block_load brought in, leaving L in A and Linv in
 // XT (visible to the whole block when it returns).  Threads beyond the first
-// 256 take part in the barriers and the strided loops only.  The code is kept
-// compact (runtime loops, short unrolled bodies): it runs once per launch on
-// one SM, where every instruction is fetched cold, so its footprint, not its
-// operation count, sets its time.
+// 256 take part in the barriers and the strided loops only.
 template <class TC, int NT>
 __device__ void block_potrf_inv(int nb, int64_t gcol0, status_t *status, TC *smem) {
     static_assert(NT >= 256, "the 16 x 16 block products use 256 threads");
@@ -107,121 +132,103 @@ __device__ void block_potrf_inv(int nb, int64_t gcol0, status_t *status, TC *sme
     for (int jb = 0; jb < nb; jb += SB) {
         const int w = min(SB, nb - jb);
         if (warp == 0) {
-            // 16 x 16 diagonal block, one row per lane in registers; pivot c
-            // at run time, the row's entries addressed by unrolled selects
-            TC v[SB];
-#pragma unroll
-            for (int t = 0; t < SB; ++t) v[t] = (lane < w && t <= lane) ? A[jb + lane][jb + t] : TC(0);
-            TC myinv = TC(1);
+            TC v[SB], myinv = TC(1);
+#pragma unroll 16
+            for (int c = 0; c < SB; ++c) v[c] = (lane < w && c <= lane) ? A[jb + lane][jb + c] : TC(0);
             int bad = -1;
-#pragma unroll 1
-            for (int c = 0; c < w; ++c) {
-                TC vc = TC(0);
-#pragma unroll
-                for (int t = 0; t < SB; ++t) vc = t == c ? v[t] : vc;
-                TC dc = __shfl_sync(0xffffffffu, vc, c);
-                if (!(dc > TC(0))) {
-                    bad = bad < 0 ? c : bad;
-                    dc = TC(1);
-                }
-                TC sc, ic;
-                pivot_root(dc, sc, ic);
-                vc = lane == c ? sc : (lane > c ? vc * ic : vc);
-                myinv = lane == c ? ic : myinv;
-#pragma unroll
-                for (int t = 0; t < SB; ++t) {
-                    const TC lt = __shfl_sync(0xffffffffu, vc, t);
-                    if (t == c) v[t] = vc;
-                    else if (t > c && lane >= t) v[t] -= vc * lt;
-                }
-            }
+            WarpChol<TC, 0>::step(v, myinv, lane, w, bad);
             if (bad >= 0 && lane == 0) atomicMin(status, (status_t)(gcol0 + jb + bad));
             if (lane < w) {
-#pragma unroll
-                for (int t = 0; t < SB; ++t)
-                    if (t <= lane) A[jb + lane][jb + t] = v[t];
+#pragma unroll 16
+                for (int c = 0; c < SB; ++c)
+                    if (c <= lane) A[jb + lane][jb + c] = v[c];
                 invd[jb + lane] = myinv;
             }
         }
         __syncthreads();
         const int rem = nb - jb - w;
         if (tid < rem) {
-            // row i below: forward substitution against the 16 x 16 factor
             const int i = jb + w + tid;
-#pragma unroll 1
-            for (int c = 0; c < w; ++c) {
-                TC acc0 = A[i][jb + c], acc1 = TC(0);
-                int p = 0;
-#pragma unroll 1
-                for (; p + 1 < c; p += 2) {
-                    acc0 -= A[i][jb + p] * A[jb + c][jb + p];
-                    acc1 -= A[i][jb + p + 1] * A[jb + c][jb + p + 1];
+            TC x[SB];
+#pragma unroll 16
+            for (int c = 0; c < SB; ++c) x[c] = A[i][jb + c];
+#pragma unroll 16
+            for (int c = 0; c < SB; ++c) {
+                TC acc0 = x[c], acc1 = TC(0);
+#pragma unroll 8
+                for (int p = 0; p + 1 < c; p += 2) {
+                    acc0 -= x[p] * A[jb + c][jb + p];
+                    acc1 -= x[p + 1] * A[jb + c][jb + p + 1];
                 }
-                if (p < c) acc0 -= A[i][jb + p] * A[jb + c][jb + p];
-                A[i][jb + c] = (acc0 + acc1) * invd[jb + c];
+                if (c & 1) acc0 -= x[c - 1] * A[jb + c][jb + c - 1];
+                x[c] = (acc0 + acc1) * invd[jb + c];
             }
+#pragma unroll 16
+            for (int c = 0; c < SB; ++c) A[i][jb + c] = x[c];
         }
         __syncthreads();
         // trailing lower part, 2 x 4 register tiles
         const int t0 = jb + w, ntr = (rem + 1) / 2, ntc = (rem + 3) / 4;
-#pragma unroll 1
         for (int q = tid; q < ntr * ntc; q += NT) {
             const int bi = q % ntr, bj = q / ntr;
             const int r0 = t0 + 2 * bi, c0 = t0 + 4 * bj;
             if (r0 + 1 < c0) continue;
-            TC acc[2][4] = {{TC(0), TC(0), TC(0), TC(0)}, {TC(0), TC(0), TC(0), TC(0)}};
+            TC acc[2][4];
+#pragma unroll 2
+            for (int i = 0; i < 2; ++i)
+#pragma unroll 4
+                for (int j = 0; j < 4; ++j) acc[i][j] = TC(0);
 #pragma unroll 4
             for (int p = 0; p < SB; ++p) {
                 TC ar[2], ac[4];
-#pragma unroll
-                for (int i2 = 0; i2 < 2; ++i2) ar[i2] = A[min(r0 + i2, NB - 1)][jb + p];
-#pragma unroll
-                for (int j2 = 0; j2 < 4; ++j2) ac[j2] = A[min(c0 + j2, NB - 1)][jb + p];
-#pragma unroll
-                for (int i2 = 0; i2 < 2; ++i2)
-#pragma unroll
-                    for (int j2 = 0; j2 < 4; ++j2) acc[i2][j2] += ar[i2] * ac[j2];
+#pragma unroll 2
+                for (int i = 0; i < 2; ++i) ar[i] = A[min(r0 + i, NB - 1)][jb + p];
+#pragma unroll 4
+                for (int j = 0; j < 4; ++j) ac[j] = A[min(c0 + j, NB - 1)][jb + p];
+#pragma unroll 2
+                for (int i = 0; i < 2; ++i)
+#pragma unroll 4
+                    for (int j = 0; j < 4; ++j) acc[i][j] += ar[i] * ac[j];
             }
-#pragma unroll
-            for (int i2 = 0; i2 < 2; ++i2)
-#pragma unroll
-                for (int j2 = 0; j2 < 4; ++j2) {
-                    const int r = r0 + i2, c = c0 + j2;
-                    if (r < nb && c <= r) A[r][c] -= acc[i2][j2];
+#pragma unroll 2
+            for (int i = 0; i < 2; ++i)
+#pragma unroll 4
+                for (int j = 0; j < 4; ++j) {
+                    const int r = r0 + i, c = c0 + j;
+                    if (r < nb && c <= r) A[r][c] -= acc[i][j];
                 }
         }
         __syncthreads();
     }
-    // X(i, i): the diagonal 16 x 16 inverses, one warp each, one column per
-    // lane, by forward substitution into XT (XT[c][r] = Linv(r, c))
+    // X(i, i): the diagonal 16 x 16 inverses, one warp each, one column per lane
     const int nsb = (nb + SB - 1) / SB;
     if (warp < nsb && lane < SB) {
         const int b0 = warp * SB, wv = min(SB, nb - b0), c = lane;
-        TC *xc = XT + (b0 + c) * XLD + b0;   // column c of X(i, i), rows 0..15
-#pragma unroll 1
+        TC x[SB];
+#pragma unroll 16
         for (int r = 0; r < SB; ++r) {
             TC acc0 = (r == c) ? TC(1) : TC(0), acc1 = TC(0);
-            int p = c;
-#pragma unroll 1
-            for (; p + 1 < r; p += 2) {
-                acc0 -= A[b0 + r][b0 + p] * xc[p];
-                acc1 -= A[b0 + r][b0 + p + 1] * xc[p + 1];
+#pragma unroll 8
+            for (int p = 0; p + 1 < r; p += 2) {
+                acc0 -= A[b0 + r][b0 + p] * x[p];
+                acc1 -= A[b0 + r][b0 + p + 1] * x[p + 1];
             }
-            if (p < r) acc0 -= A[b0 + r][b0 + p] * xc[p];
-            if (r >= c) xc[r] = (r < wv && c < wv) ? (acc0 + acc1) * invd[min(b0 + r, NB - 1)] : TC(0);
+            if (r & 1) acc0 -= A[b0 + r][b0 + r - 1] * x[r - 1];
+            x[r] = (r < wv && c < wv) ? (acc0 + acc1) * invd[min(b0 + r, NB - 1)] : TC(0);
         }
+#pragma unroll 16
+        for (int r = 0; r < SB; ++r)
+            if (r >= c) XT[(b0 + c) * XLD + b0 + r] = x[r];
     }
     __syncthreads();
     // W(i, k) = X(i, i) L(i, k), i > k, into XT's block (i, k); X(i, i)(r, t) is
     // zero for t > r, so the sum runs over the whole sub-block
     if (tid < SB * SB) {
         const int r = tid % SB, q = tid / SB;
-#pragma unroll 1
         for (int i = 1; i < nsb; ++i)
-#pragma unroll 1
             for (int k = 0; k < i; ++k) {
                 TC acc0 = TC(0), acc1 = TC(0);
-#pragma unroll 4
+#pragma unroll
                 for (int t = 0; t < SB; t += 2) {
                     acc0 += XT[(SB * i + t) * XLD + SB * i + r] * A[SB * i + t][SB * k + q];
                     acc1 += XT[(SB * i + t + 1) * XLD + SB * i + r] * A[SB * i + t + 1][SB * k + q];
@@ -237,10 +244,8 @@ __device__ void block_potrf_inv(int nb, int64_t gcol0, status_t *status, TC *sme
 #pragma unroll 1
         for (int i = 1; i < nsb; ++i) {
             if (tid < SB * SB) {
-#pragma unroll 1
                 for (int j = 0; j < i; ++j) {
                     TC acc[4] = {TC(0), TC(0), TC(0), TC(0)};
-#pragma unroll 1
                     for (int k = j; k < i; ++k) {
                         const TC *wp = XT + (SB * i + r) * XLD + SB * k;
                         const TC *xp = XT + (SB * j + c) * XLD + SB * k;
