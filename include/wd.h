@@ -194,15 +194,24 @@ wd_status wd_factor(wd_handle h, const double *values, int values_on_device, wd_
 wd_status wd_solve(wd_handle h, double *B, int64_t nrhs, int64_t ldb, int B_on_device,
                    void *stream, wd_solve_info *info);
 
+/* The mass matrix G of a non-orthonormal basis for wd_theta_step (Section
+   5, Eq. (theta); its pattern lies inside the system matrix's, Section 6):
+   gvalues are its nnz lower-CSC values in the order of the analyzed rowidx
+   (zero where G has no entry), on the host (on_device = 0) or the device
+   (1); they are copied.  NULL restores G = I.  Needs wd_analyze; stays in
+   effect until the next wd_analyze.  Synchronous. */
+wd_status wd_set_mass(wd_handle h, const double *gvalues, int on_device);
+
 /* One step of the theta-scheme for a parabolic problem (Section 5,
-   Eq. (theta)) with an orthonormal basis (mass matrix G = I): the factored
-   matrix is M = I + theta dt K (K the compressed operator, positive
-   semidefinite), and the step is
-     U := M^-1 [ (1/theta) U - ((1 - theta)/theta) M U + dt F ],
-   i.e. (I + theta dt K) U_new = (I - (1 - theta) dt K) U_old + dt F, with
+   Eq. (theta)): the factored matrix is M = G + theta dt K (K the compressed
+   operator, positive semidefinite; G = I for an orthonormal basis, else the
+   matrix given to wd_set_mass), and the step is
+     U := M^-1 [ (1/theta) G U - ((1 - theta)/theta) M U + dt F ],
+   i.e. (G + theta dt K) U_new = (G - (1 - theta) dt K) U_old + dt F, with
    F = (1 - theta) f(t_i) + theta f(t_{i+1}) given by the caller (NULL: no
-   source).  The product M U is formed to FP64 accuracy from M's values (as
-   in wd_backward_error); the solve is wd_solve's, refinement included.
+   source).  The products M U and G U are formed to FP64 accuracy from the
+   matrices' values (as in wd_backward_error); the solve is wd_solve's,
+   refinement included.
    U (in/out) and F: n x nrhs, column-major, leading dimension ld >= n,
    original order, both on the device (on_device = 1) or both on the host (0).
    0 < theta <= 1 (theta = 1: implicit Euler, no product), dt finite and

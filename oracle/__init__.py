@@ -305,24 +305,30 @@ def backward_error(colptr, rowidx, values, X, B) -> np.ndarray:
     return np.abs(R).max(0) / (an * np.abs(X).max(0) + np.abs(B).max(0))
 
 
-def theta_matrix(colptr, values, theta: float, dt: float) -> np.ndarray:
-    """Lower-CSC values of M = G + theta dt K with G = I (orthonormal basis),
-    the matrix the theta-scheme inverts at every step (Section 5, Eq. (theta));
-    K's values given on the same pattern, diagonal first in each column."""
+def theta_matrix(colptr, values, theta: float, dt: float, g_values=None) -> np.ndarray:
+    """Lower-CSC values of M = G + theta dt K, the matrix the theta-scheme
+    inverts at every step (Section 5, Eq. (theta)); K's values (and G's, if
+    given; G = I otherwise, an orthonormal basis) on the same pattern,
+    diagonal first in each column."""
     m = theta * dt * np.asarray(values, dtype=np.float64)
-    m[np.asarray(colptr[:-1])] += 1.0
+    if g_values is None:
+        m[np.asarray(colptr[:-1])] += 1.0
+    else:
+        m = m + np.asarray(g_values, dtype=np.float64)
     return m
 
 
-def theta_step(o, colptr, rowidx, k_values, U, F, theta: float, dt: float) -> np.ndarray:
-    """One step of Eq. (theta) with G = I and the stiffness matrix K (positive
-    semidefinite; the paper's L_J enters with the opposite sign):
+def theta_step(o, colptr, rowidx, k_values, U, F, theta: float, dt: float, g_values=None) -> np.ndarray:
+    """One step of Eq. (theta) with the mass matrix G (identity if g_values is
+    None) and the stiffness matrix K (positive semidefinite; the paper's L_J
+    enters with the opposite sign):
         G (u_new - u) / dt + K ((1 - theta) u + theta u_new) = F,
     i.e. (G + theta dt K) u_new = (G - (1 - theta) dt K) u + dt F, with the
     oracle `o` factored for M = theta_matrix(...).  U, F: n x nrhs (F may be
     None)."""
     U = np.asarray(U, dtype=np.float64)
-    rhs = U - (1.0 - theta) * dt * sym_spmv(colptr, rowidx, k_values, U)
+    GU = U if g_values is None else sym_spmv(colptr, rowidx, g_values, U)
+    rhs = GU - (1.0 - theta) * dt * sym_spmv(colptr, rowidx, k_values, U)
     if F is not None:
         rhs = rhs + dt * np.asarray(F, dtype=np.float64)
     return o.solve(rhs.reshape(len(colptr) - 1, -1)).reshape(U.shape)

@@ -30,7 +30,7 @@ EXPORTED = ["wd_default_options", "wd_create", "wd_destroy", "wd_analyze", "wd_s
             "wd_get_info", "wd_factor", "wd_solve", "wd_logdet", "wd_apply_L", "wd_export_L",
             "wd_status_detail", "wd_status_string", "wd_kernel_stats", "wd_launch_count",
             "wd_selinv", "wd_sym_pattern_outer", "wd_value_gradient", "wd_export_L_noalloc",
-            "wd_analyze_batch", "wd_logdet_batch", "wd_backward_error", "wd_theta_step"]
+            "wd_analyze_batch", "wd_logdet_batch", "wd_backward_error", "wd_theta_step", "wd_set_mass"]
 
 
 class WdOptions(ctypes.Structure):
@@ -110,6 +110,7 @@ def load():
         lib.wd_backward_error.argtypes = [vp, vp, vp, i64, i64, ctypes.c_int, vp, ctypes.POINTER(f64)]
         lib.wd_theta_step.argtypes = [vp, vp, vp, i64, i64, f64, f64, ctypes.c_int, vp,
                                       ctypes.POINTER(WdSolveInfo)]
+        lib.wd_set_mass.argtypes = [vp, vp, ctypes.c_int]
         lib.wd_status_detail.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_char_p, ctypes.c_size_t]
         lib.wd_kernel_stats.argtypes = [vp, ctypes.POINTER(WdKernelStat), i32, ctypes.POINTER(i32),
                                         ctypes.c_int]
@@ -322,6 +323,19 @@ class Solver:
             out = X
         self.last_solve = {"iterations": info.iterations, "backward_error": info.backward_error}
         return out
+
+    def set_mass(self, gvalues=None):
+        """The mass matrix G (values on the analyzed lower pattern) used by
+        theta_step; None restores G = I."""
+        if gvalues is None:
+            self._check(self._lib.wd_set_mass(self._h, None, 0))
+            return self
+        g = gvalues if _is_torch(gvalues) else np.ascontiguousarray(gvalues, np.float64)
+        if g.shape[0] != self.nnz:
+            raise ValueError("gvalues must hold one value per stored lower entry of the analyzed pattern")
+        p, dev = _ptr(g)
+        self._check(self._lib.wd_set_mass(self._h, p, dev))
+        return self
 
     def theta_step(self, U, F=None, theta=0.5, dt=1e-2, stream=None):
         """One theta-scheme step with the factored matrix M = I + theta dt K

@@ -117,6 +117,8 @@ struct wd_ctx {
     DevSym dsym{};
     int32_t *d_csr_src = nullptr;
     double *d_csr_val = nullptr;
+    double *d_gcsr = nullptr;   // mass matrix G on the full CSR (wd_set_mass; nullptr: G = I)
+    double *mass_buf = nullptr; // its storage (analysis lifetime)
     float *d_csr_vh = nullptr, *d_csr_vl = nullptr;   // double-float split of csr_val
     double *d_values_stage = nullptr;
     void *d_front = nullptr;
@@ -677,6 +679,7 @@ static wd_status reset_analysis(wd_handle h) {
     h->ws_cols = 0;
     h->d_front = nullptr;
     h->d_dinv = nullptr;
+    h->d_gcsr = h->mass_buf = nullptr;
     h->d_xs = h->d_xts = nullptr;
     h->d_xsoff = nullptr;
     h->xs_elems = 0;
@@ -1676,9 +1679,18 @@ extern "C" wd_status wd_theta_step(wd_handle h, double *U, const double *F, int6
         Ud = h->d_B;
         ldd = n;
     }
-    wd::launch_theta_stage(Ud, Fd, ldd, h->dsym.perm, n, nrhs, 1.0 / theta, (1.0 - theta) / theta, dt, h->d_Bp,
-                           h->d_X, st);
-    h->launches += 1;
+    if (h->d_gcsr) {
+        // G != I: Bp = dt F, then Bp += (1/theta) G U (U in factor order, in R)
+        wd::launch_theta_stage(Ud, Fd, ldd, h->dsym.perm, n, nrhs, 0.0, (1.0 - theta) / theta, dt, h->d_Bp,
+                               h->d_X, st);
+        wd::launch_permute_in_rm(Ud, ldd, h->d_R, h->dsym.perm, n, nrhs, st);
+        wd::launch_spmv_axpy(h->dsym, h->d_gcsr, h->d_R, 1.0 / theta, h->d_Bp, nrhs, st);
+        h->launches += 3;
+    } else {
+        wd::launch_theta_stage(Ud, Fd, ldd, h->dsym.perm, n, nrhs, 1.0 / theta, (1.0 - theta) / theta, dt,
+                               h->d_Bp, h->d_X, st);
+        h->launches += 1;
+    }
     if (theta < 1.0) {
         s = launch_residual(h, h->d_X, nrhs, st);
         if (s != WD_OK) return s;
@@ -1692,6 +1704,31 @@ extern "C" wd_status wd_theta_step(wd_handle h, double *U, const double *F, int6
             return fail(h, WD_ERR_CUDA, "residual: column index out of range at CSR position " + std::to_string(bad));
     }
     return solve_core(h, Ud, ldd, U, ld, on_device, nrhs, st, info);
+}
+
+extern "C" wd_status wd_set_mass(wd_handle h, const double *gvalues, int on_device) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!h->analyzed || h->opt.symbolic_only)
+        return fail(h, WD_ERR_STATE, "wd_set_mass before wd_analyze (or on a host-only handle)");
+    CK(cudaSetDevice(h->device), "set device");
+    if (!gvalues) {
+        h->d_gcsr = nullptr;   // the allocation stays with the analysis; G = I from now on
+        return WD_OK;
+    }
+    const int64_t nnzl = h->S.pcp[h->S.n];
+    if (!h->mass_buf) CK(h->mem.alloc((void **)&h->mass_buf, h->nnz_full * sizeof(double)), "mass alloc");
+    const double *src = gvalues;
+    if (!on_device) {
+        if (!h->d_values_stage)
+            CK(h->mem.alloc((void **)&h->d_values_stage, nnzl * sizeof(double)), "stage alloc");
+        CK(cudaMemcpy(h->d_values_stage, gvalues, nnzl * sizeof(double), cudaMemcpyHostToDevice), "G H2D");
+        src = h->d_values_stage;
+    }
+    wd::launch_gather_values(h->d_csr_src, src, h->mass_buf, nullptr, nullptr, h->nnz_full, 0);
+    h->launches += 1;
+    CK(cudaDeviceSynchronize(), "mass gather");
+    h->d_gcsr = h->mass_buf;
+    return WD_OK;
 }
 
 extern "C" wd_status wd_backward_error(wd_handle h, const double *X, const double *B, int64_t nrhs,

@@ -125,6 +125,10 @@ void launch_permute_out(const T *Y, double *B, int64_t ldb, const int32_t *perm,
 template <class T>
 void launch_apply_L(const DevSym &d, const T *front, const T *Z, T *Out, T *W,
                     const int4 *items, int count, int nrhs, cudaStream_t st);
+// Y += alpha G X, G given by its values on the full CSR of P A P^T (FP64,
+// row-major n x nrhs vectors, factor order)
+void launch_spmv_axpy(const DevSym &d, const double *vals, const double *X, double alpha, double *Y,
+                      int64_t nrhs, cudaStream_t st);
 // refinement vectors are row-major (n x nrhs, right-hand sides contiguous)
 void launch_permute_in_rm(const double *B, int64_t ldb, double *Bp, const int32_t *perm, int64_t n,
                           int64_t nrhs, cudaStream_t st);

@@ -110,6 +110,36 @@ __global__ void permute_in_rm_kernel(const double *__restrict__ B, int64_t ldb,
     }
 }
 
+// Y += alpha G X on the full CSR of P A P^T with other values (G's, on the
+// same structure; FP64; X and Y row-major n x nrhs, factor order): one warp
+// per row, lanes over the row's entries, the lanes' sums added by a fixed
+// shuffle tree, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) spmv_axpy_kernel(DevSym d, const double *__restrict__ vals,
+                                                        const double *__restrict__ X, double alpha,
+                                                        double *__restrict__ Y, int nrhs) {
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= d.n) return;
+    const int64_t e0 = d.csr_ptr[row], e1 = d.csr_ptr[row + 1];
+    for (int c0 = 0; c0 < nrhs; c0 += 8) {
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            const double v = vals[e];
+            const int64_t xo = (int64_t)d.csr_col[e] * nrhs;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c0 + c < nrhs) acc[c] += v * X[xo + c0 + c];
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            double t = acc[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0 && c0 + c < nrhs) Y[row * nrhs + c0 + c] += alpha * t;
+        }
+    }
+}
+
 // One step of the theta-scheme (Eq. (theta) with G = I), staged in factor
 // order, row-major: Bp[i*nrhs + c] = a U[o] + g F[o] (F nullable) and
 // X[i*nrhs + c] = x U[o], o = perm[i] + c*ld; the residual kernel then forms
@@ -690,6 +720,12 @@ void launch_apply_L(const DevSym &d, const T *front, const T *Z, T *Out, T *W,
                     const int4 *items, int count, int nrhs, cudaStream_t st) {
     if (count <= 0) return;
     apply_L_kernel<T><<<count, THREADS, 0, st>>>(d, front, Z, Out, W, items, nrhs);
+}
+
+void launch_spmv_axpy(const DevSym &d, const double *vals, const double *X, double alpha, double *Y,
+                      int64_t nrhs, cudaStream_t st) {
+    const int64_t warps = d.n;
+    spmv_axpy_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(d, vals, X, alpha, Y, (int)nrhs);
 }
 
 void launch_permute_in_rm(const double *B, int64_t ldb, double *Bp, const int32_t *perm, int64_t n,

@@ -121,3 +121,103 @@ def test_theta_step_without_source_and_with_zero_dt(wdlib, cuda, prec):
     s0 = wdlib.Solver().analyze(cp, ri, b).factor(oracle.theta_matrix(cp, k, theta, 0.0), prec)
     U1 = s0.theta_step(U0, rhs(n, 2, seed=8), theta=theta, dt=0.0)
     assert np.abs(U1 - U0).max() <= 1e-13 * np.abs(U0).max()
+
+
+# ---- a non-orthonormal basis: mass matrix G != I --------------------------
+
+
+@pytest.mark.parametrize("theta,dt", [(0.5, 0.3), (1.0, 2.0)])
+def test_oracle_step_with_mass_scales_a_generalized_eigenvector(theta, dt):
+    """K v = lambda G v (scipy's generalized symmetric eigensolver): the step
+    with mass matrix G scales v by (1 - (1 - theta) dt lambda) / (1 + theta dt
+    lambda), source 0."""
+    import scipy.linalg as sla
+    from wdgen import mass_matrix
+
+    b, cp, ri, k = _k(1, 6, Kernel("exponential", 0.2), 1e-2)
+    g = mass_matrix(b, cp, ri, 0.3)
+    K = oracle.sym_lower_to_dense(cp, ri, k)
+    G = oracle.sym_lower_to_dense(cp, ri, g)
+    assert np.abs(G - np.eye(G.shape[0])).max() > 0.01          # G is not the identity
+    lam, V = sla.eigh(K, G)
+    o = oracle.Oracle(cp, ri, b)
+    assert o.factor(oracle.theta_matrix(cp, k, theta, dt, g)) == 0
+    for idx in (0, len(lam) // 2, len(lam) - 1):
+        v = V[:, idx] / np.abs(V[:, idx]).max()
+        r = (1 - (1 - theta) * dt * lam[idx]) / (1 + theta * dt * lam[idx])
+        u = v.copy()
+        for step in range(1, 4):
+            u = oracle.theta_step(o, cp, ri, k, u[:, None], None, theta, dt, g)[:, 0]
+            np.testing.assert_allclose(u, r ** step * v, rtol=0, atol=1e-11)
+
+
+def test_oracle_step_with_mass_fixed_point_and_identity():
+    """u* = K^-1 F is a fixed point for any G; G = I given explicitly is the
+    orthonormal step."""
+    from wdgen import mass_matrix
+
+    b, cp, ri, k = _k(2, 4, Kernel("matern32", 0.1), 1e-3)
+    g = mass_matrix(b, cp, ri, 0.25)
+    K = oracle.sym_lower_to_dense(cp, ri, k)
+    F = rhs(K.shape[0], 2, seed=5)
+    ustar = np.linalg.solve(K, F)
+    o = oracle.Oracle(cp, ri, b)
+    assert o.factor(oracle.theta_matrix(cp, k, 0.5, 0.1, g)) == 0
+    u1 = oracle.theta_step(o, cp, ri, k, ustar, F, 0.5, 0.1, g)
+    assert np.abs(u1 - ustar).max() <= 1e-11 * np.abs(ustar).max()
+    eye = np.zeros_like(k)
+    eye[cp[:-1]] = 1.0
+    o1 = oracle.Oracle(cp, ri, b)
+    assert o1.factor(oracle.theta_matrix(cp, k, 0.5, 0.1, eye)) == 0
+    U = rhs(K.shape[0], 2, seed=6)
+    np.testing.assert_allclose(oracle.theta_step(o1, cp, ri, k, U, F, 0.5, 0.1, eye),
+                               oracle.theta_step(o1, cp, ri, k, U, F, 0.5, 0.1), rtol=0, atol=1e-14)
+
+
+def test_mass_matrix_is_spd_on_the_pattern():
+    from wdgen import mass_matrix
+
+    for dim, J in ((1, 7), (2, 4)):
+        b = haar_basis(dim, J)
+        cp, ri = compressed_pattern(b)
+        g = mass_matrix(b, cp, ri, 0.3)
+        G = oracle.sym_lower_to_dense(cp, ri, g)
+        ev = np.linalg.eigvalsh(G)
+        assert ev.min() >= 0.7 - 1e-12 and ev.max() <= 1.3 + 1e-12   # Gershgorin: row sums <= 0.3
+        assert np.count_nonzero(g) > b.N                             # off-diagonal coupling exists
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", ["1d_J10", "2d_J6"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("nrhs,theta", [(1, 0.5), (12, 1.0)])
+def test_theta_steps_with_mass_against_the_oracle(wdlib, cuda, name, prec, nrhs, theta):
+    """wd_set_mass + wd_theta_step (the library forms (1/theta) G U -
+    ((1 - theta)/theta) M U + dt F) against the oracle's step from K and G,
+    five steps; then G = I restored."""
+    from wdgen import mass_matrix
+
+    b, cp, ri, k = _case(name)
+    g = mass_matrix(b, cp, ri, 0.3)
+    dt = 0.05
+    m = oracle.theta_matrix(cp, k, theta, dt, g)
+    o = oracle.Oracle(cp, ri, b)
+    assert o.factor(m) == 0
+    n = cp.size - 1
+    U0 = rhs(n, nrhs, seed=20 + nrhs)
+    F = rhs(n, nrhs, seed=120 + nrhs)
+    s = wdlib.Solver().analyze(cp, ri, b).set_mass(g).factor(m, prec)
+    Uo, Uh = U0.copy(), U0.copy()
+    for _ in range(5):
+        Uo = oracle.theta_step(o, cp, ri, k, Uo, F, theta, dt, g)
+        Uh = s.theta_step(Uh, F, theta=theta, dt=dt)
+        assert s.last_solve["backward_error"] <= 1e-12
+    assert np.abs(Uh - Uo).max() <= 1e-10 * np.abs(Uo).max()
+    # G = I again: the step of M = I + theta dt K
+    mi = oracle.theta_matrix(cp, k, theta, dt)
+    oi = oracle.Oracle(cp, ri, b)
+    assert oi.factor(mi) == 0
+    s.set_mass(None).factor(mi, prec)
+    Ui = s.theta_step(U0, F, theta=theta, dt=dt)
+    Uoi = oracle.theta_step(oi, cp, ri, k, U0, F, theta, dt)
+    assert np.abs(Ui - Uoi).max() <= 1e-10 * np.abs(Uoi).max()

@@ -206,6 +206,41 @@ def compressed_pattern(basis: Basis):
     return colptr, r.astype(np.int32)
 
 
+def mass_matrix(basis: Basis, colptr, rowidx, coupling: float = 0.3) -> np.ndarray:
+    """Lower-CSC values (on the given pattern) of a synthetic mass matrix G of
+    a non-orthonormal basis: the Gram matrix of functions that overlap their
+    same-level neighbours, as piecewise linear or bilinear wavelets do
+    (Section 6), standing in for those bases (not built here).  G has ones on
+    the diagonal and -coupling / max(deg_i, deg_j) between two functions of
+    the same level >= 1 whose closed support boxes touch, deg being the
+    number of such neighbours; every row's off-diagonal sum is at most
+    coupling < 1, so G is symmetric positive definite.  Its pattern lies
+    inside the compressed pattern (touching supports are at distance 0), as
+    the mass matrix's lies inside the system matrix's (Section 6)."""
+    if not 0.0 <= coupling < 1.0:
+        raise ValueError("coupling must lie in [0, 1)")
+    cp = np.asarray(colptr, np.int64)
+    ri = np.asarray(rowidx, np.int64)
+    N = cp.size - 1
+    cols = np.repeat(np.arange(N), np.diff(cp))
+    lev = np.asarray(basis.level)
+    lo = np.asarray(basis.box_lo).reshape(N, -1).astype(np.int64)
+    side = np.asarray(basis.box_side).astype(np.int64)
+    off = ri != cols
+    a, b = ri[off], cols[off]
+    # closed boxes touch iff on every axis the intervals [lo, lo + side] meet
+    touch = np.ones(a.size, bool)
+    for ax in range(lo.shape[1]):
+        touch &= (lo[a, ax] <= lo[b, ax] + side[b]) & (lo[b, ax] <= lo[a, ax] + side[a])
+    nb = touch & (lev[a] == lev[b]) & (lev[a] > 0)
+    deg = np.bincount(a[nb], minlength=N) + np.bincount(b[nb], minlength=N)
+    g = np.zeros(ri.size)
+    g[~off] = 1.0
+    idx = np.flatnonzero(off)[nb]
+    g[idx] = -coupling / np.maximum(deg[a[nb]], deg[b[nb]])
+    return g
+
+
 # --------------------------------------------------------------------------
 # kernels and values
 # --------------------------------------------------------------------------
