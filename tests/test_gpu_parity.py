@@ -366,3 +366,27 @@ def test_tensor_core_solve_products_match_simt(wdlib, cuda, name, nrhs):
     s = wdlib.Solver().analyze(cp, ri, b).factor(v, "mixed")
     Xr = s.solve(B)
     assert oracle.backward_error(cp, ri, v, Xr, B).max() <= 1e-12
+
+
+@pytest.mark.parametrize("dim,J,ker,nug", [(1, 10, Kernel("exponential", 0.2), 1e-2),
+                                           (2, 6, Kernel("exponential", 0.3), 1e-2)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 2e-5)])
+def test_two_term_pattern_factor_and_solve(wdlib, cuda, dim, J, ker, nug, prec, tol):
+    """Matrices on the full two-term compression pattern of Theorem 3.1:
+    factor columns and refined solves against the oracle."""
+    from wdgen import compressed_pattern_two_term
+
+    b = haar_basis(dim, J)
+    cp, ri = compressed_pattern_two_term(b, a=1.5, delta=1.2, q=1.0)
+    v = compressed_values(b, cp, ri, ker, nug)
+    o = oracle.Oracle(cp, ri, b)
+    assert o.factor(v) == 0
+    s = wdlib.Solver().analyze(cp, ri, b).factor(v, prec)
+    L = s.L_csc_like(o.Lp, o.Li)
+    Lo = o.L_values()
+    starts = o.Lp[:-1]
+    rel = np.sqrt(np.add.reduceat((L - Lo) ** 2, starts) / np.add.reduceat(Lo ** 2, starts))
+    assert rel.max() <= tol
+    B = rhs(o.n, 16, seed=9)
+    X = s.solve(B)
+    assert oracle.backward_error(cp, ri, v, X, B).max() <= 1e-12

@@ -171,3 +171,14 @@ def test_invalid_options_are_rejected(wdlib):
         with pytest.raises(wdlib.WdError) as e:
             wdlib.Solver(symbolic_only=True, **kw)
         assert e.value.status == wdlib.WD_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("dim,J", [(1, 10), (2, 5)])
+def test_symbolic_bitexact_two_term_pattern(wdlib, dim, J):
+    """The full two-term compression of Theorem 3.1 gives a sparser coarse
+    coupling; the analysis stays bit-exact with the oracle on it."""
+    from wdgen import compressed_pattern_two_term
+
+    b = haar_basis(dim, J)
+    cp, ri = compressed_pattern_two_term(b, a=1.5, delta=1.2, q=1.0)
+    _compare(wdlib, cp, ri, b)

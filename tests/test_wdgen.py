@@ -132,3 +132,67 @@ def test_kernel_parameter_derivatives(kind, param):
     km = Kernel(kind, **{**dict(ell=0.17, sigma2=1.3), param: getattr(k, param) - h})
     fd = (kp(r) - km(r)) / (2 * h)
     np.testing.assert_allclose(d, fd, rtol=1e-7, atol=1e-9)
+
+
+# ---- the full a-priori compression of Theorem 3.1 (both terms) -------------
+
+
+def _pattern_set(cp, ri):
+    cols = np.repeat(np.arange(cp.size - 1), np.diff(cp))
+    return set(zip(ri.tolist(), cols.tolist()))
+
+
+def test_two_term_cutoff_golden():
+    import json
+    import os
+
+    from wdgen import compressed_pattern_two_term, cutoff_parameters
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "two_term_cutoff.json")))
+    p = g["parameters"]
+    b = haar_basis(p["dim"], p["J"])
+    cp, ri = compressed_pattern_two_term(b, a=p["a"], delta=p["delta"], q=p["q"], dtilde=p["dtilde"])
+    S = _pattern_set(cp, ri)
+    for e in g["entries"]:
+        assert ((e["row"], e["col"]) in S) == e["kept"], e["why"]
+    bs15 = cutoff_parameters(5, 1, 5, 1.5, 1.2, 1.0, 1.0)[1]
+    assert abs(bs15 - 1.5 * 2 ** (-10.2 / 3)) < 1e-15
+    assert cutoff_parameters(5, 5, 5, 1.5, 1.2, 1.0, 1.0) == (0.046875, 0.046875)
+
+
+def test_two_term_cutoff_structure_and_growth():
+    """Diagonal kept, rows sorted, larger a keeps a superset; the number of
+    entries per unknown grows by less and less from level to level (the
+    theorem's O(N) entries), while the first-term mask with a = 2 grows by a
+    constant amount per level."""
+    from wdgen import compressed_pattern_two_term
+
+    prev = None
+    inc1, inc2 = [], []
+    for J in range(6, 12):
+        b = haar_basis(1, J)
+        cp, ri = compressed_pattern_two_term(b, a=1.5, delta=1.2, q=1.0)
+        assert np.all(ri[cp[:-1]] == np.arange(b.N))
+        for c in range(0, b.N, 97):
+            assert np.all(np.diff(ri[cp[c]:cp[c + 1]]) > 0)
+        c1, _ = compressed_pattern(b)
+        anz = (2.0 * cp[-1] - b.N) / b.N, (2.0 * c1[-1] - b.N) / b.N
+        if prev is not None:
+            inc2.append(anz[0] - prev[0])
+            inc1.append(anz[1] - prev[1])
+        prev = anz
+    assert all(x > y for x, y in zip(inc2, inc2[1:]))          # shrinking increments
+    assert inc2[-1] < 0.3 * inc1[-1]
+    b = haar_basis(2, 4)
+    small = _pattern_set(*compressed_pattern_two_term(b, a=1.5, delta=1.2, q=1.0))
+    big = _pattern_set(*compressed_pattern_two_term(b, a=3.0, delta=1.2, q=1.0))
+    assert small < big
+
+
+def test_two_term_cutoff_needs_the_theorems_parameters():
+    from wdgen import compressed_pattern_two_term
+
+    b = haar_basis(1, 4)
+    for kw in (dict(a=1.0, delta=1.2, q=1.0), dict(a=2.0, delta=0.9, q=1.0), dict(a=2.0, delta=1.5, q=0.2)):
+        with pytest.raises(ValueError):
+            compressed_pattern_two_term(b, **kw)

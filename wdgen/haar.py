@@ -241,6 +241,118 @@ def mass_matrix(basis: Basis, colptr, rowidx, coupling: float = 0.3) -> np.ndarr
     return g
 
 
+def cutoff_parameters(J: int, j: int, jp: int, a: float, delta: float, q: float, dtilde: float):
+    """(B_{j,j'}, B^s_{j,j'}) of Theorem 3.1 (Eq. cut-off parameters), in
+    domain units: the support-distance and singular-support-distance bounds
+    of the a-priori compression for an operator of order 2q, wavelets with
+    dtilde vanishing moments, a > 1 and d < delta < dtilde + 2q."""
+    lo, hi = min(j, jp), max(j, jp)
+    b = a * max(2.0 ** (-lo), 2.0 ** ((2 * J * (delta - q) - (j + jp) * (delta + dtilde)) / (2 * (dtilde + q))))
+    bs = a * max(2.0 ** (-hi), 2.0 ** ((2 * J * (delta - q) - (j + jp) * delta - hi * dtilde) / (dtilde + 2 * q)))
+    return b, bs
+
+
+def compressed_pattern_two_term(basis: Basis, a: float, delta: float, q: float, dtilde: float = 1.0,
+                                d: float = 1.0):
+    """Lower CSC pattern of the full a-priori compression of Theorem 3.1 (both
+    terms), for Haar wavelets (d = dtilde = 1) and an operator of order 2q:
+    the entry (lambda, lambda') is dropped iff
+      dist(D_l, D_l') > B_{|l|,|l'|} and |l|, |l'| > 0, or
+      dist(D_l, D_l') <= 2^-min(|l|,|l'|) and the singular support of the
+      coarser of the two is farther than B^s_{|l|,|l'|} from the finer's
+      support (levels equal: this term does not apply),
+    with the supports D and singular supports D^s (box boundaries and the
+    lines where the wavelet changes sign) compared exactly in finest-cell
+    units.  Needs a > 1 and d < delta < dtilde + 2q.  All pairs of two levels
+    are enumerated (blocks of at most 2^22), which suits the small cases it
+    is tested on."""
+    if not (a > 1 and d < delta < dtilde + 2 * q):
+        raise ValueError("Theorem 3.1 needs a > 1 and d < delta < dtilde + 2q")
+    dim, J, N = basis.dim, basis.J, basis.N
+    lev = np.asarray(basis.level)
+    lo = np.asarray(basis.box_lo).reshape(N, -1).astype(np.int64)
+    side = np.asarray(basis.box_side).astype(np.int64)
+    unit = float(1 << J)                                  # cells per domain unit
+    typ = np.zeros(N, np.int64)
+    if dim == 2:
+        first = np.array([_level_offset(2, j) for j in range(J + 1)])
+        typ = np.where(lev > 0, (np.arange(N) - first[lev]) % 3, -1)
+
+    def gap(a0, a1, b0, b1):
+        return np.maximum(np.maximum(b0 - a1, a0 - b1), 0)
+
+    def sing_dist2(ia, ib):
+        """squared distance (cells^2) from the singular support of ia to the support box of ib"""
+        x0, s = lo[ia, 0], side[ia]
+        bx0, bs_ = lo[ib, 0][None, :], side[ib][None, :]
+        if dim == 1:
+            # end points, and the midpoint for a wavelet (level >= 1)
+            best = None
+            for p_, mid in ((x0, False), (x0 + s, False), (x0 + s // 2, True)):
+                g = gap(p_[:, None], p_[:, None], bx0, bx0 + bs_).astype(np.float64)
+                if mid:
+                    g = np.where((lev[ia] > 0)[:, None], g, np.inf)
+                best = g * g if best is None else np.minimum(best, g * g)
+            return best
+        y0 = lo[ia, 1]
+        by0 = lo[ib, 1][None, :]
+        X0, X1, Y0, Y1 = x0[:, None], (x0 + s)[:, None], y0[:, None], (y0 + s)[:, None]
+        Xm, Ym = (x0 + s // 2)[:, None], (y0 + s // 2)[:, None]
+        gxb = gap(X0, X1, bx0, bx0 + bs_)   # x-extent of the box vs the support's x-extent
+        gyb = gap(Y0, Y1, by0, by0 + bs_)
+        segs = []
+        for xc in (X0, X1):                  # vertical boundary edges
+            segs.append((gap(xc, xc, bx0, bx0 + bs_), gyb))
+        for yc in (Y0, Y1):                  # horizontal boundary edges
+            segs.append((gxb, gap(yc, yc, by0, by0 + bs_)))
+        t = typ[ia][:, None]
+        vm = (gap(Xm, Xm, bx0, bx0 + bs_), gyb)     # vertical midline (types 0, 2)
+        hm = (gxb, gap(Ym, Ym, by0, by0 + bs_))     # horizontal midline (types 1, 2)
+        best = None
+        for gx, gy in segs:
+            d2 = (gx * gx + gy * gy).astype(np.float64)
+            best = d2 if best is None else np.minimum(best, d2)
+        d2 = (vm[0] ** 2 + vm[1] ** 2).astype(np.float64)
+        best = np.minimum(best, np.where((t == 0) | (t == 2), d2, np.inf))
+        d2 = (hm[0] ** 2 + hm[1] ** 2).astype(np.float64)
+        best = np.minimum(best, np.where((t == 1) | (t == 2), d2, np.inf))
+        return best
+
+    rows, cols = [], []
+    for j in range(J + 1):
+        A = np.flatnonzero(lev == j)
+        for jp in range(j, J + 1):
+            Bi = np.flatnonzero(lev == jp)
+            bnd, bnds = cutoff_parameters(J, j, jp, a, delta, q, dtilde)
+            near = (unit * 2.0 ** (-min(j, jp))) ** 2
+            step = max(1, (1 << 22) // max(1, Bi.size))
+            for c0 in range(0, A.size, step):
+                ia = A[c0:c0 + step]
+                d2 = np.zeros((ia.size, Bi.size))
+                for ax in range(dim):
+                    g = gap(lo[ia, ax][:, None], (lo[ia, ax] + side[ia])[:, None],
+                            lo[Bi, ax][None, :], (lo[Bi, ax] + side[Bi])[None, :]).astype(np.float64)
+                    d2 += g * g
+                keep = np.ones_like(d2, bool)
+                if j > 0:
+                    keep &= d2 <= (unit * bnd) ** 2
+                if jp > j:
+                    far_sing = sing_dist2(ia, Bi) > (unit * bnds) ** 2
+                    keep &= ~((d2 <= near) & far_sing)
+                ii, kk = np.nonzero(keep)
+                ra, cb = ia[ii], Bi[kk]
+                rows.append(np.maximum(ra, cb))
+                cols.append(np.minimum(ra, cb))
+    r = np.concatenate(rows).astype(np.int64)
+    c = np.concatenate(cols).astype(np.int64)
+    key = np.unique(c * N + r)
+    c = key // N
+    r = key % N
+    colptr = np.zeros(N + 1, np.int64)
+    np.cumsum(np.bincount(c, minlength=N), out=colptr[1:])
+    return colptr, r.astype(np.int32)
+
+
 # --------------------------------------------------------------------------
 # kernels and values
 # --------------------------------------------------------------------------
