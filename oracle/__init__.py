@@ -75,6 +75,13 @@ def _load():
             lib.or_solve_prefix.restype = ctypes.c_int
             lib.or_solve_prefix.argtypes = [ctypes.c_void_p, _f64p, ctypes.c_int64, ctypes.c_int64,
                                              ctypes.c_int64]
+            lib.or_factor_lu.restype = ctypes.c_int64
+            lib.or_factor_lu.argtypes = [ctypes.c_void_p, _f64p, _f64p]
+            lib.or_get_lu.argtypes = [ctypes.c_void_p, _f64p, _f64p]
+            lib.or_solve_lu.restype = ctypes.c_int
+            lib.or_solve_lu.argtypes = [ctypes.c_void_p, _f64p, ctypes.c_int64, ctypes.c_int64]
+            lib.or_logdet_lu.restype = ctypes.c_double
+            lib.or_logdet_lu.argtypes = [ctypes.c_void_p, _i32p]
             lib.or_logdet.restype = ctypes.c_double
             lib.or_logdet.argtypes = [ctypes.c_void_p]
             lib.or_apply_L.restype = ctypes.c_int
@@ -193,6 +200,37 @@ class Oracle:
         if rc:
             raise RuntimeError("solve_prefix: not factored or bad ncols")
 
+    # -- LU without pivoting (nonsymmetric values on the symmetric pattern) ----
+    def factor_lu(self, lower, upper) -> int:
+        """P A P^T = L U, L unit lower triangular, no pivoting.  lower[e] =
+        A[r][c], upper[e] = A[c][r] for every stored lower entry (r, c).
+        Returns 0, or -(j+1) for the first zero pivot (permuted order)."""
+        lo = np.ascontiguousarray(lower, np.float64)
+        up = np.ascontiguousarray(upper, np.float64)
+        return int(self._lib.or_factor_lu(self._ctx, _p(lo, _f64p), _p(up, _f64p)))
+
+    def lu_values(self):
+        """(L, U^T) on the pattern of L (Lp, Li): L with its unit diagonal,
+        column j of U^T = row j of U."""
+        L = np.empty(self.nnzL, np.float64)
+        Ut = np.empty(self.nnzL, np.float64)
+        self._lib.or_get_lu(self._ctx, _p(L, _f64p), _p(Ut, _f64p))
+        return L, Ut
+
+    def solve_lu(self, B) -> np.ndarray:
+        X = np.array(B, dtype=np.float64, order="F", copy=True)
+        if X.ndim == 1:
+            X = X[:, None]
+        if self._lib.or_solve_lu(self._ctx, _p(X, _f64p), X.shape[1], self.n):
+            raise RuntimeError("not LU-factored")
+        return X
+
+    def logdet_lu(self):
+        """(log |det A|, sign of det A)"""
+        sg = np.zeros(1, np.int32)
+        v = float(self._lib.or_logdet_lu(self._ctx, _p(sg, _i32p)))
+        return v, int(sg[0])
+
     def L_values(self) -> np.ndarray:
         x = np.empty(self.nnzL, np.float64)
         self._lib.or_get_L(self._ctx, _p(x, _f64p))
@@ -284,6 +322,45 @@ def sym_spmv(colptr, rowidx, values, X) -> np.ndarray:
     if Xa.ndim == 1:
         return Lo @ Xa + Lo.T @ Xa - d * Xa
     return Lo @ Xa + Lo.T @ Xa - d[:, None] * Xa
+
+
+def nonsym_lower_upper_to_dense(colptr, rowidx, lower, upper) -> np.ndarray:
+    """Dense A from its stored lower entries: A[r][c] = lower[e], A[c][r] =
+    upper[e] for every lower-CSC entry e = (r, c)."""
+    n = len(colptr) - 1
+    A = np.zeros((n, n))
+    cols = np.repeat(np.arange(n), np.diff(colptr))
+    A[cols, rowidx] = upper
+    A[rowidx, cols] = lower
+    return A
+
+
+def nonsym_spmv(colptr, rowidx, lower, upper, X) -> np.ndarray:
+    """A @ X for A given by lower / upper values on a symmetric pattern."""
+    import scipy.sparse as sp
+
+    n = len(colptr) - 1
+    Lo = sp.csc_matrix((np.asarray(lower, np.float64), rowidx, colptr), shape=(n, n))
+    Up = sp.csc_matrix((np.asarray(upper, np.float64), rowidx, colptr), shape=(n, n)).T
+    d = np.asarray(lower, np.float64)[np.asarray(colptr[:-1])]
+    Xa = np.asarray(X, dtype=np.float64)
+    if Xa.ndim == 1:
+        return Lo @ Xa + Up @ Xa - d * Xa
+    return Lo @ Xa + Up @ Xa - d[:, None] * Xa
+
+
+def nonsym_backward_error(colptr, rowidx, lower, upper, X, B) -> np.ndarray:
+    """Normwise backward error per column for the nonsymmetric A."""
+    n = len(colptr) - 1
+    X = np.asarray(X).reshape(n, -1)
+    B = np.asarray(B).reshape(n, -1)
+    R = B - nonsym_spmv(colptr, rowidx, lower, upper, X)
+    cols = np.repeat(np.arange(n), np.diff(colptr))
+    off = rowidx != cols
+    s = np.zeros(n)
+    np.add.at(s, rowidx, np.abs(lower))
+    np.add.at(s, cols[off], np.abs(np.asarray(upper)[off]))
+    return np.abs(R).max(0) / (s.max() * np.abs(X).max(0) + np.abs(B).max(0))
 
 
 def sym_norm_inf(colptr, rowidx, values) -> float:

@@ -56,6 +56,13 @@ typedef struct or_ctx {
     int64_t *srowptr;     /* nsuper + 1 */
     int32_t *srows;
     int factored;
+    /* orientation of every permuted lower entry: 1 when (row, col) of
+       P A P^T is the transposed position (col, row) of its source entry */
+    int8_t *pswap;
+    /* LU without pivoting (or_factor_lu): L with unit diagonal in Lux, U
+       transposed (column j holds row j of U) in Uux, both on L's pattern */
+    double *Lux, *Uux;
+    int lu_factored;
 } or_ctx;
 
 or_ctx *or_create(void) { return (or_ctx *)calloc(1, sizeof(or_ctx)); }
@@ -66,7 +73,16 @@ static void free_numeric(or_ctx *c) {
     c->factored = 0;
 }
 
+static void free_lu(or_ctx *c) {
+    free(c->Lux);
+    free(c->Uux);
+    c->Lux = c->Uux = NULL;
+    c->lu_factored = 0;
+}
+
 static void free_all(or_ctx *c) {
+    free_lu(c);
+    free(c->pswap);
     free(c->perm); free(c->iperm); free(c->pcolptr); free(c->prow); free(c->psrc);
     free(c->Lp); free(c->Li); free(c->parent); free(c->colcount);
     free(c->sfirst); free(c->srowptr); free(c->srows);
@@ -333,6 +349,7 @@ static void permute_lower(or_ctx *c, const int64_t *cp, const int32_t *ri) {
     c->pcolptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     c->prow = (int32_t *)malloc(sizeof(int32_t) * (size_t)nnz);
     c->psrc = (int64_t *)malloc(sizeof(int64_t) * (size_t)nnz);
+    c->pswap = (int8_t *)malloc((size_t)(nnz > 0 ? nnz : 1));
     for (int64_t j = 0; j < n; ++j)
         for (int64_t q = cp[j]; q < cp[j + 1]; ++q) {
             int32_t a = c->iperm[ri[q]], b = c->iperm[j];
@@ -348,6 +365,7 @@ static void permute_lower(or_ctx *c, const int64_t *cp, const int32_t *ri) {
             int64_t d = fill[col]++;
             c->prow[d] = row;
             c->psrc[d] = q;
+            c->pswap[d] = (int8_t)(a < b);
         }
     free(fill);
     /* insertion sort each column by row (columns are short) */
@@ -355,14 +373,17 @@ static void permute_lower(or_ctx *c, const int64_t *cp, const int32_t *ri) {
         for (int64_t q = c->pcolptr[j] + 1; q < c->pcolptr[j + 1]; ++q) {
             int32_t r = c->prow[q];
             int64_t s = c->psrc[q];
+            int8_t w = c->pswap[q];
             int64_t t = q - 1;
             while (t >= c->pcolptr[j] && c->prow[t] > r) {
                 c->prow[t + 1] = c->prow[t];
                 c->psrc[t + 1] = c->psrc[t];
+                c->pswap[t + 1] = c->pswap[t];
                 --t;
             }
             c->prow[t + 1] = r;
             c->psrc[t + 1] = s;
+            c->pswap[t + 1] = w;
         }
     }
 }
@@ -660,6 +681,135 @@ int or_solve_prefix(const or_ctx *c, double *B, int64_t nrhs, int64_t ldb, int64
         }
     }
     return 0;
+}
+
+/* LU factorization without pivoting of a matrix with the analyzed
+   (symmetric) pattern, P A P^T = L U with L unit lower triangular (Section 4:
+   Cholesky and LU share the nested dissection ordering; the pattern of U is
+   that of L transposed).  Input: for every stored lower entry e = (r, c),
+   r >= c, of the analyzed lower CSC, lower[e] = A[r][c] and upper[e] =
+   A[c][r] (the diagonal taken from lower).  Left-looking, column j of L and
+   row j of U together (the Doolittle recurrences):
+     U[j][j] = A[j][j] - sum_{k<j} L[j][k] U[k][j]
+     L[i][j] = (A[i][j] - sum_{k<j} L[i][k] U[k][j]) / U[j][j],   i > j
+     U[j][i] =  A[j][i] - sum_{k<j} L[j][k] U[k][i],               i > j
+   the sums running over the k with L[j][k] != 0 (equivalently U[k][j] != 0),
+   in ascending order.  Returns 0, or -(j+1) for the first zero pivot. */
+int64_t or_factor_lu(or_ctx *c, const double *lower, const double *upper) {
+    int64_t n = c->n;
+    free_lu(c);
+    int64_t nnzl = c->Lp[n];
+    c->Lux = (double *)malloc(sizeof(double) * (size_t)(nnzl > 0 ? nnzl : 1));
+    c->Uux = (double *)malloc(sizeof(double) * (size_t)(nnzl > 0 ? nnzl : 1));
+    double *wl = (double *)calloc((size_t)n, sizeof(double));
+    double *wu = (double *)calloc((size_t)n, sizeof(double));
+    int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int32_t *head = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *link = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *ks = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    for (int64_t j = 0; j < n; ++j) head[j] = -1;
+    int64_t status = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        /* column j of P A P^T from the diagonal down into wl, row j to the
+           right of the diagonal into wu */
+        for (int64_t q = c->pcolptr[j]; q < c->pcolptr[j + 1]; ++q) {
+            int32_t i = c->prow[q];
+            int64_t e = c->psrc[q];
+            if (i == j) {
+                wl[i] = lower[e];
+            } else {
+                wl[i] = c->pswap[q] ? upper[e] : lower[e];
+                wu[i] = c->pswap[q] ? lower[e] : upper[e];
+            }
+        }
+        int64_t nk = 0;
+        for (int32_t k = head[j]; k != -1; k = link[k]) ks[nk++] = k;
+        qsort(ks, (size_t)nk, sizeof(int32_t), cmp_int32);
+        for (int64_t t = 0; t < nk; ++t) {
+            int32_t k = ks[t];
+            int64_t p = next[k];            /* entry (j, k) of L's pattern */
+            double ljk = c->Lux[p], ukj = c->Uux[p];
+            for (int64_t q = p; q < c->Lp[k + 1]; ++q) {
+                int32_t i = c->Li[q];
+                wl[i] -= c->Lux[q] * ukj;
+                if (i > j) wu[i] -= ljk * c->Uux[q];
+            }
+            next[k] = p + 1;
+            if (p + 1 < c->Lp[k + 1]) {
+                int32_t r = c->Li[p + 1];
+                link[k] = head[r];
+                head[r] = k;
+            }
+        }
+        double ujj = wl[j];
+        if (!(ujj != 0.0) || isnan(ujj)) { status = -(j + 1); break; }
+        c->Lux[c->Lp[j]] = 1.0;
+        c->Uux[c->Lp[j]] = ujj;
+        wl[j] = 0.0;
+        for (int64_t q = c->Lp[j] + 1; q < c->Lp[j + 1]; ++q) {
+            int32_t i = c->Li[q];
+            c->Lux[q] = wl[i] / ujj;
+            c->Uux[q] = wu[i];
+            wl[i] = 0.0;
+            wu[i] = 0.0;
+        }
+        next[j] = c->Lp[j] + 1;
+        if (c->Lp[j] + 1 < c->Lp[j + 1]) {
+            int32_t r = c->Li[c->Lp[j] + 1];
+            link[j] = head[r];
+            head[r] = (int32_t)j;
+        }
+    }
+    free(wl); free(wu); free(next); free(head); free(link); free(ks);
+    c->lu_factored = status == 0;
+    return status;
+}
+
+void or_get_lu(const or_ctx *c, double *Lx, double *Ut) {
+    memcpy(Lx, c->Lux, sizeof(double) * (size_t)c->Lp[c->n]);
+    memcpy(Ut, c->Uux, sizeof(double) * (size_t)c->Lp[c->n]);
+}
+
+/* B (n x nrhs, column-major, original order) := A^-1 B with the LU factors:
+   y = L^-1 P b column-oriented (unit diagonal), x = P^T U^-1 y row-oriented */
+int or_solve_lu(const or_ctx *c, double *B, int64_t nrhs, int64_t ldb) {
+    if (!c->lu_factored) return -1;
+    int64_t n = c->n;
+    double *y = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int64_t r = 0; r < nrhs; ++r) {
+        double *b = B + r * ldb;
+        for (int64_t i = 0; i < n; ++i) y[i] = b[c->perm[i]];
+        for (int64_t j = 0; j < n; ++j) {
+            double yj = y[j];
+            for (int64_t q = c->Lp[j] + 1; q < c->Lp[j + 1]; ++q) y[c->Li[q]] -= c->Lux[q] * yj;
+        }
+        for (int64_t j = n - 1; j >= 0; --j) {
+            double s = y[j];
+            for (int64_t q = c->Lp[j] + 1; q < c->Lp[j + 1]; ++q) s -= c->Uux[q] * y[c->Li[q]];
+            y[j] = s / c->Uux[c->Lp[j]];
+        }
+        for (int64_t i = 0; i < n; ++i) b[c->perm[i]] = y[i];
+    }
+    free(y);
+    return 0;
+}
+
+/* log |det A| = sum_j log |U[j][j]| (Neumaier compensated); *sign = the sign
+   of det A (det P = det P^T cancel) */
+double or_logdet_lu(const or_ctx *c, int32_t *sign) {
+    double s = 0.0, comp = 0.0;
+    int32_t sg = 1;
+    for (int64_t j = 0; j < c->n; ++j) {
+        double u = c->Uux[c->Lp[j]];
+        if (u < 0) sg = -sg;
+        double v = log(fabs(u));
+        double t = s + v;
+        if (fabs(s) >= fabs(v)) comp += (s - t) + v;
+        else comp += (v - t) + s;
+        s = t;
+    }
+    *sign = sg;
+    return s + comp;
 }
 
 /* 2 sum_j log L_jj, Neumaier compensated */

@@ -468,6 +468,40 @@ def compressed_values(basis: Basis, colptr, rowidx, kernel: Kernel, nugget: floa
     return vals
 
 
+def compressed_values_nonsym(basis: Basis, colptr, rowidx, kernel: Kernel, nugget: float,
+                             beta: float = 0.5, direction=(1.0, 0.0)):
+    """(lower, upper) values of a nonsymmetric compressed matrix on a lower
+    CSC pattern: lower[e] = A[r][c], upper[e] = A[c][r] for every stored
+    entry e = (r, c).  A = mask(T (K_ss + beta K_a) T^T) + nugget I with the
+    symmetric kernel of compressed_values and the antisymmetric term
+      K_a[c, c'] = sqrt(|c||c'|) ((x_c - x_c') . e / ell) k(x_c, x_c'),
+    e = direction (1D: its first component), a transport-like term that
+    stands in for the double-layer operator's nonsymmetric part (Section 6,
+    PCM example).  The symmetric part of A is the SPD compressed matrix, so A
+    has an LU factorization without pivoting.  Dense, for N up to a few
+    thousand."""
+    dim, J, N = basis.dim, basis.J, basis.N
+    n = 1 << J
+    vol = 1.0 / float(N)
+    X = _cell_centroids(dim, J)
+    D = _dist(X, X, np)
+    e = np.asarray(direction, np.float64)[:dim]
+    proj = X @ e if dim == 2 else X.reshape(-1) * e[0]
+    diff = (proj[:, None] - proj[None, :]) / kernel.ell
+    K = kernel(D, np) * (1.0 + beta * diff) * vol
+    shape = (n,) if dim == 1 else (n, n)
+    M1 = fwt(K.reshape((N,) + shape), dim, J, np)             # K T^T (rows transformed)
+    A = fwt(np.ascontiguousarray(M1.T).reshape((N,) + shape), dim, J, np).T   # T K T^T
+    cp = np.asarray(colptr)
+    ri = np.asarray(rowidx).astype(np.int64)
+    cols = np.repeat(np.arange(N), np.diff(cp))
+    lower = A[ri, cols].copy()
+    upper = A[cols, ri].copy()
+    lower[cp[:-1]] += nugget
+    upper[cp[:-1]] = lower[cp[:-1]]
+    return lower, upper
+
+
 # --------------------------------------------------------------------------
 # workloads
 # --------------------------------------------------------------------------
