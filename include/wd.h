@@ -313,6 +313,37 @@ wd_status wd_export_L(wd_handle h, double *panels);
 #define WD_NOALLOC_MAX_SUPERNODES 65536
 wd_status wd_export_L_noalloc(wd_handle h, double *panels, void *stream);
 
+/* LU factorization without pivoting of a NONSYMMETRIC matrix with the
+   analyzed (symmetric) pattern: P A P^T = L U, L unit lower triangular, on
+   the same nested-dissection ordering and supernodes as the Cholesky path
+   (Section 4, where Cholesky and LU share the ordering and U has the pattern
+   of L transposed; Section 6, the double-layer operator of the PCM example).
+   lower[e] = A[r][c] and upper[e] = A[c][r] for every stored lower entry e =
+   (r, c) of the analyzed lower CSC (nnz doubles each; the diagonal is taken
+   from lower), both on the host (on_device = 0) or the device (1).  FP64.
+   No pivoting: a zero pivot gives WD_ERR_NOT_SPD with its column (permuted
+   order, wd_status_detail); a matrix whose symmetric part is positive
+   definite always factors.  Replaces any Cholesky factor of the handle
+   (wd_solve / wd_logdet need a new wd_factor).  Synchronous. */
+wd_status wd_factor_lu(wd_handle h, const double *lower, const double *upper, int on_device, void *stream);
+
+/* B := A^-1 B with the LU factor: x = P^T U^-1 L^-1 P b (forward
+   substitution with the unit lower L, backward with U), FP64, nrhs columns of
+   leading dimension ldb >= n, original order, on the device (B_on_device =
+   1) or the host (0).  Needs wd_factor_lu.  Synchronous. */
+wd_status wd_solve_lu(wd_handle h, double *B, int64_t nrhs, int64_t ldb, int B_on_device, void *stream);
+
+/* log |det A| = sum_j log |U_jj| (*logabs) and the sign of det A (*sign, +1
+   or -1), from the LU factor.  Synchronous. */
+wd_status wd_logdet_lu(wd_handle h, double *logabs, int32_t *sign);
+
+/* The LU factor as two host arrays of info.nnz_L_stored doubles each, in the
+   layout of wd_export_L (per supernode an m_s x k_s panel, column-major, rows
+   as in super_rows): lpanels holds L (unit diagonal, zero above it),
+   utpanels U^T (entry (r, c) = U[c][row r], zero above the diagonal).
+   Synchronous. */
+wd_status wd_export_LU(wd_handle h, double *lpanels, double *utpanels);
+
 /* Per-kernel statistics accumulated while wd_options.profile = 1: name (the
    kernel and its precision), launches, summed event time, and the
    algorithmic flops and bytes of those launches (flops of the arithmetic the

@@ -30,7 +30,8 @@ EXPORTED = ["wd_default_options", "wd_create", "wd_destroy", "wd_analyze", "wd_s
             "wd_get_info", "wd_factor", "wd_solve", "wd_logdet", "wd_apply_L", "wd_export_L",
             "wd_status_detail", "wd_status_string", "wd_kernel_stats", "wd_launch_count",
             "wd_selinv", "wd_sym_pattern_outer", "wd_value_gradient", "wd_export_L_noalloc",
-            "wd_analyze_batch", "wd_logdet_batch", "wd_backward_error", "wd_theta_step", "wd_set_mass"]
+            "wd_analyze_batch", "wd_logdet_batch", "wd_backward_error", "wd_theta_step", "wd_set_mass",
+            "wd_factor_lu", "wd_solve_lu", "wd_logdet_lu", "wd_export_LU"]
 
 
 class WdOptions(ctypes.Structure):
@@ -111,6 +112,10 @@ def load():
         lib.wd_theta_step.argtypes = [vp, vp, vp, i64, i64, f64, f64, ctypes.c_int, vp,
                                       ctypes.POINTER(WdSolveInfo)]
         lib.wd_set_mass.argtypes = [vp, vp, ctypes.c_int]
+        lib.wd_factor_lu.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+        lib.wd_solve_lu.argtypes = [vp, vp, i64, i64, ctypes.c_int, vp]
+        lib.wd_logdet_lu.argtypes = [vp, ctypes.POINTER(f64), ctypes.POINTER(i32)]
+        lib.wd_export_LU.argtypes = [vp, vp, vp]
         lib.wd_status_detail.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_char_p, ctypes.c_size_t]
         lib.wd_kernel_stats.argtypes = [vp, ctypes.POINTER(WdKernelStat), i32, ctypes.POINTER(i32),
                                         ctypes.c_int]
@@ -323,6 +328,55 @@ class Solver:
             out = X
         self.last_solve = {"iterations": info.iterations, "backward_error": info.backward_error}
         return out
+
+    # -- LU without pivoting (nonsymmetric values on the analyzed pattern) ------
+    def factor_lu(self, lower, upper, stream=None):
+        """P A P^T = L U (FP64, no pivoting).  lower[e] = A[r][c], upper[e] =
+        A[c][r] for every stored lower entry e = (r, c)."""
+        if _is_torch(lower) != _is_torch(upper):
+            raise ValueError("lower and upper must both be numpy arrays or both tensors")
+        lo = lower if _is_torch(lower) else np.ascontiguousarray(lower, np.float64)
+        up = upper if _is_torch(upper) else np.ascontiguousarray(upper, np.float64)
+        if lo.shape[0] != self.nnz or up.shape[0] != self.nnz:
+            raise ValueError("one value per stored lower entry of the analyzed pattern")
+        pl, dev = _ptr(lo)
+        pu, _ = _ptr(up)
+        self._check(self._lib.wd_factor_lu(self._h, pl, pu, dev, _stream(stream, dev)))
+        self.precision = "lu"
+        return self
+
+    def solve_lu(self, B, stream=None):
+        """A^-1 B with the LU factor.  A CUDA tensor (n x nrhs, column-major)
+        is overwritten in place; a numpy array gives a new array."""
+        if _is_torch(B):
+            if B.dim() == 1:
+                B = B.unsqueeze(1)
+            if B.stride(0) != 1:
+                raise ValueError("B must be column-major (stride(0) == 1)")
+            self._check(self._lib.wd_solve_lu(self._h, ctypes.c_void_p(B.data_ptr()), B.shape[1], B.stride(1)
+                                              if B.shape[1] > 1 else self.n, 1, _stream(stream, True)))
+            return B
+        X = np.array(B, dtype=np.float64, order="F", copy=True)
+        if X.ndim == 1:
+            X = X[:, None]
+        self._check(self._lib.wd_solve_lu(self._h, ctypes.c_void_p(X.ctypes.data), X.shape[1], self.n, 0,
+                                          _stream(stream, False)))
+        return X
+
+    def logdet_lu(self):
+        """(log |det A|, sign of det A) from the LU factor."""
+        v = ctypes.c_double()
+        sg = ctypes.c_int32()
+        self._check(self._lib.wd_logdet_lu(self._h, ctypes.byref(v), ctypes.byref(sg)))
+        return v.value, sg.value
+
+    def export_LU(self):
+        """(L, U^T) supernodal panels, each in wd_export_L's layout."""
+        size = self._panel_size()
+        L = np.empty(size, np.float64)
+        Ut = np.empty(size, np.float64)
+        self._check(self._lib.wd_export_LU(self._h, L.ctypes.data, Ut.ctypes.data))
+        return L, Ut
 
     def set_mass(self, gvalues=None):
         """The mass matrix G (values on the analyzed lower pattern) used by
@@ -545,11 +599,13 @@ class Solver:
         m = np.diff(sym["super_rowptr"]).astype(np.int64)
         return int((k * m).sum())
 
-    def L_csc_like(self, Lp, Li):
+    def L_csc_like(self, Lp, Li, panels=None):
         """The factor's entries at the positions of a CSC pattern of L
-        (e.g. the oracle's): values of stored panels, structural entries only."""
+        (e.g. the oracle's): values of stored panels (export_L's, or the given
+        ones in that layout), structural entries only."""
         sym = self.symbolic()
-        panels = self.export_L()
+        if panels is None:
+            panels = self.export_L()
         sf, srp, rows = sym["super_first"], sym["super_rowptr"], sym["super_rows"]
         n = self.n
         col2s = np.repeat(np.arange(sf.size - 1), np.diff(sf))

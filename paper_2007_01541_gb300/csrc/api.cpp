@@ -29,7 +29,9 @@ enum LaunchKind {
     K_SBINV_DIAG, K_SBINV_STAGE, K_SBINV_T,                    // super-block inverses
     K_FWD_GATHER, K_FWD_XAPPLY, K_FWD_BUPDATE,                 // forward solve
     K_BWD_REDUCE, K_BWD_FINISH, K_BWD_XAPPLY,                  // backward solve
-    K_APPLY_L
+    K_APPLY_L,
+    K_LU_INIT, K_LU_DIAG, K_LU_PANEL, K_LU_UPDATE,               // LU factor
+    K_LU_GATHER, K_LU_FWD, K_LU_BWD                              // LU substitutions
 };
 
 struct Launch {
@@ -47,7 +49,8 @@ const char *kind_name(int k) {
                                   "tc_schur_update", "tc_schur_syrk", "diag_factor", "sbinv_diag",
                                   "sbinv_stage", "sbinv_transpose", "fwd_gather", "fwd_xapply",
                                   "fwd_bupdate", "bwd_reduce", "bwd_finish", "bwd_xapply",
-                                  "apply_L"};
+                                  "apply_L", "lu_init", "lu_diag", "lu_panel", "lu_update",
+                                  "lu_gather", "lu_fwd", "lu_bwd"};
     return names[k];
 }
 
@@ -117,6 +120,15 @@ struct wd_ctx {
     DevSym dsym{};
     int32_t *d_csr_src = nullptr;
     double *d_csr_val = nullptr;
+    // LU without pivoting (wd_factor_lu, FP64): position codes of the full
+    // CSR, both values per position, U11^-1 blocks, plans
+    bool lu_factored = false;
+    bool front_dirty = false;   // the fronts' upper parts hold an LU factor
+    std::vector<int8_t> h_csr_code;
+    int8_t *d_lu_code = nullptr;
+    double *d_vrow = nullptr, *d_vcol = nullptr, *d_uinv = nullptr, *d_lu_part = nullptr;
+    double *d_upper_stage = nullptr;
+    Plan fplan_lu, splan_lu_f, splan_lu_b;
     double *d_gcsr = nullptr;   // mass matrix G on the full CSR (wd_set_mass; nullptr: G = I)
     double *mass_buf = nullptr; // its storage (analysis lifetime)
     float *d_csr_vh = nullptr, *d_csr_vl = nullptr;   // double-float split of csr_val
@@ -680,6 +692,12 @@ static wd_status reset_analysis(wd_handle h) {
     h->d_front = nullptr;
     h->d_dinv = nullptr;
     h->d_gcsr = h->mass_buf = nullptr;
+    h->lu_factored = h->front_dirty = false;
+    h->d_lu_code = nullptr;
+    h->d_vrow = h->d_vcol = h->d_uinv = h->d_lu_part = h->d_upper_stage = nullptr;
+    h->fplan_lu = Plan();
+    h->splan_lu_f = Plan();
+    h->splan_lu_b = Plan();
     h->d_xs = h->d_xts = nullptr;
     h->d_xsoff = nullptr;
     h->xs_elems = 0;
@@ -865,20 +883,25 @@ static wd_status finish_analysis(wd_handle h, std::chrono::steady_clock::time_po
     const int64_t nnzf = cptr[n];
     h->nnz_full = nnzf;
     std::vector<int32_t> ccol(nnzf), csrc(nnzf);
+    h->h_csr_code.assign(nnzf, 0);
     {
         std::vector<int64_t> fill(cptr.begin(), cptr.end() - 1);
         // row i gets, in column order: entries (i, j<i) from lower columns j,
-        // then the diagonal and (i, j>i) from lower column i
+        // then the diagonal and (i, j>i) from lower column i.  The code of a
+        // position tells a nonsymmetric matrix's values apart (LU): which of
+        // the source's two values is the entry and which its transpose
         for (int64_t j = 0; j < n; ++j)
             for (int64_t e = S.pcp[j] + 1; e < S.pcp[j + 1]; ++e) {
                 const int32_t i = S.prow[e];
                 ccol[fill[i]] = (int32_t)j;
+                h->h_csr_code[fill[i]] = S.pswap[e] ? 1 : 0;
                 csrc[fill[i]++] = S.psrc[e];
             }
         for (int64_t j = 0; j < n; ++j) {
             cdiag[j] = fill[j];
             for (int64_t e = S.pcp[j]; e < S.pcp[j + 1]; ++e) {
                 ccol[fill[j]] = S.prow[e];
+                h->h_csr_code[fill[j]] = S.prow[e] == j ? 2 : (S.pswap[e] ? 0 : 1);
                 csrc[fill[j]++] = S.psrc[e];
             }
         }
@@ -1227,6 +1250,12 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     wait_export(h);   // a pending allocation-free export still reads the fronts
     h->factored = false;
+    h->lu_factored = false;
+    if (h->front_dirty && h->d_front) {
+        // an LU factor filled the upper parts that the Cholesky kernels keep zero
+        CK(cudaMemsetAsync(h->d_front, 0, h->front_elems * sizeof(double), st), "front pool clear");
+        h->front_dirty = false;
+    }
     const int64_t nnzl = h->S.pcp[h->S.n];
     if (!h->d_front) {
         CK(h->mem.alloc(&h->d_front, h->front_elems * sizeof(double)), "front pool alloc");
@@ -2195,6 +2224,270 @@ extern "C" wd_status wd_value_gradient(wd_handle h, double g_logdet, const doubl
     if (!h) return WD_ERR_INVALID_ARG;
     if (!h->factored) return fail(h, WD_ERR_STATE, "wd_value_gradient before a successful wd_factor");
     return pattern_outer(h, G, X, ncols, ld, -1.0, g_logdet, out, on_device, stream);
+}
+
+// ---------------------------------------------------------------------------
+// LU without pivoting (FP64)
+// ---------------------------------------------------------------------------
+static void build_lu_plans(const wd::Symbolic &S, Plan &fp, Plan &sf, Plan &sb) {
+    fp = Plan();
+    sf = Plan();
+    sb = Plan();
+    constexpr int TL = 64;
+    for (int l = 0; l < S.nlevels; ++l) {
+        const int b = S.level_ptr[l], e = S.level_ptr[l + 1];
+        size_t f0 = fp.items.size();
+        double el = 0;
+        for (int i = b; i < e; ++i) {
+            const int s = S.level_nodes[i];
+            const int mp = front_order(S, s);
+            for (int q = 0; q < (mp + 7) / 8 * 8; ++q) fp.items.push_back({s, q < mp ? q : -1, 0, 0});
+            el += (double)mp * mp;
+        }
+        add_launch(fp, K_LU_INIT, f0, 0, 0, el, 0);
+        int kmax = 0;
+        for (int i = b; i < e; ++i) kmax = std::max(kmax, S.k(S.level_nodes[i]));
+        for (int kb = 0; kb < kmax; kb += NB) {
+            f0 = fp.items.size();
+            double fl = 0;
+            for (int i = b; i < e; ++i) {
+                const int s = S.level_nodes[i];
+                if (S.k(s) <= kb) continue;
+                const double nb = std::min(NB, S.k(s) - kb);
+                fp.items.push_back({s, 0, 0, 0});
+                fl += 2.0 * nb * nb * nb / 3 + 2.0 * nb * nb * nb / 3;
+            }
+            add_launch(fp, K_LU_DIAG, f0, kb, fl, 0, 0);
+            f0 = fp.items.size();
+            fl = 0;
+            for (int i = b; i < e; ++i) {
+                const int s = S.level_nodes[i], k = S.k(s);
+                if (k <= kb) continue;
+                const int nb = std::min(NB, k - kb), t0 = kb + nb, mp = front_order(S, s);
+                const int start = (t0 == k) ? kpad(k) : t0;
+                const int nblk = (mp - start + TL - 1) / TL;
+                for (int side = 0; side < 2; ++side)
+                    for (int q = 0; q < nblk; ++q) fp.items.push_back({s, q, side, 0});
+                fl += 2.0 * (double)(S.m(s) - t0) * nb * nb;
+            }
+            add_launch(fp, K_LU_PANEL, f0, kb, fl, 0, 0);
+            f0 = fp.items.size();
+            fl = 0;
+            for (int i = b; i < e; ++i) {
+                const int s = S.level_nodes[i], k = S.k(s);
+                if (k <= kb) continue;
+                const int nb = std::min(NB, k - kb), base = kb + nb, mp = front_order(S, s);
+                const int T = (mp - base + TL - 1) / TL;
+                for (int tj = 0; tj < T; ++tj)
+                    for (int ti = 0; ti < T; ++ti) fp.items.push_back({s, ti, tj, 0});
+                const double r = S.m(s) - base;
+                fl += 2.0 * r * r * nb;
+            }
+            add_launch(fp, K_LU_UPDATE, f0, kb, fl, 0, 0);
+        }
+        // substitutions: gather, then the pivot blocks of the level in order
+        f0 = sf.items.size();
+        for (int i = b; i < e; ++i) {
+            const int s = S.level_nodes[i];
+            for (int rc = 0; rc * 32 < S.m(s); ++rc) sf.items.push_back({s, rc, 0, 0});
+        }
+        add_launch(sf, K_LU_GATHER, f0, 0, 0, 0, 0);
+        for (int kb = 0; kb < kmax; kb += NB) {
+            f0 = sf.items.size();
+            for (int i = b; i < e; ++i) {
+                const int s = S.level_nodes[i], k = S.k(s);
+                if (k <= kb) continue;
+                const int t0 = kb + std::min(NB, k - kb);
+                const int nblk = 1 + (S.m(s) - t0 + TL - 1) / TL;
+                for (int q = 0; q < nblk; ++q) sf.items.push_back({s, q, 0, 0});
+            }
+            add_launch(sf, K_LU_FWD, f0, kb, 0, 0, 0);
+        }
+    }
+    for (int l = S.nlevels - 1; l >= 0; --l) {
+        const int b = S.level_ptr[l], e = S.level_ptr[l + 1];
+        int kmax = 0;
+        for (int i = b; i < e; ++i) kmax = std::max(kmax, S.k(S.level_nodes[i]));
+        for (int kb = (kmax - 1) / NB * NB; kb >= 0; kb -= NB) {
+            const size_t f0 = sb.items.size();
+            for (int i = b; i < e; ++i) {
+                const int s = S.level_nodes[i];
+                if (S.k(s) > kb) sb.items.push_back({s, 0, 0, 0});
+            }
+            add_launch(sb, K_LU_BWD, f0, kb, 0, 0, 0);
+        }
+    }
+}
+
+extern "C" wd_status wd_factor_lu(wd_handle h, const double *lower, const double *upper, int on_device,
+                                  void *stream) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!h->analyzed || h->opt.symbolic_only)
+        return fail(h, WD_ERR_STATE, "wd_factor_lu before wd_analyze (or on a host-only handle)");
+    if (!lower || !upper) return fail(h, WD_ERR_INVALID_ARG, "null values");
+    if (h->batch_count > 0) return fail(h, WD_ERR_INVALID_ARG, "wd_factor_lu takes a single matrix");
+    CK(cudaSetDevice(h->device), "set device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    wait_export(h);
+    h->factored = false;
+    h->lu_factored = false;
+    const int64_t nnzl = h->S.pcp[h->S.n];
+    if (!h->d_front) {
+        CK(h->mem.alloc(&h->d_front, h->front_elems * sizeof(double)), "front pool alloc");
+        CK(h->mem.alloc(&h->d_dinv, h->dinv_elems * sizeof(double)), "inverse blocks alloc");
+        CK(h->mem.alloc(&h->d_xs, h->xs_elems * sizeof(double)), "super-block inverse alloc");
+        CK(h->mem.alloc(&h->d_xts, h->xs_elems * sizeof(double)), "super-block inverse alloc");
+        CK(cudaMemsetAsync(h->d_front, 0, h->front_elems * sizeof(double), st), "front pool clear");
+    }
+    if (!h->d_uinv) {
+        CK(h->mem.alloc((void **)&h->d_uinv, h->dinv_elems * sizeof(double)), "inverse blocks alloc");
+        CK(h->mem.alloc((void **)&h->d_vrow, h->nnz_full * sizeof(double)), "values alloc");
+        CK(h->mem.alloc((void **)&h->d_vcol, h->nnz_full * sizeof(double)), "values alloc");
+        CK(h->mem.alloc((void **)&h->d_lu_part, 2 * 64 * sizeof(double)), "logdet alloc");
+        const int8_t *p = nullptr;
+        wd_status us = upload(h, h->h_csr_code, &p);
+        if (us != WD_OK) return us;
+        h->d_lu_code = const_cast<int8_t *>(p);
+        build_lu_plans(h->S, h->fplan_lu, h->splan_lu_f, h->splan_lu_b);
+        for (Plan *P : {&h->fplan_lu, &h->splan_lu_f, &h->splan_lu_b}) {
+            wd_status ps = upload_plan(h, h->mem, *P);
+            if (ps != WD_OK) return ps;
+        }
+    }
+    const double *lo = lower, *up = upper;
+    if (!on_device) {
+        if (!h->d_values_stage)
+            CK(h->mem.alloc((void **)&h->d_values_stage, nnzl * sizeof(double)), "stage alloc");
+        if (!h->d_upper_stage)
+            CK(h->mem.alloc((void **)&h->d_upper_stage, nnzl * sizeof(double)), "stage alloc");
+        CK(cudaMemcpyAsync(h->d_values_stage, lower, nnzl * sizeof(double), cudaMemcpyHostToDevice, st), "H2D");
+        CK(cudaMemcpyAsync(h->d_upper_stage, upper, nnzl * sizeof(double), cudaMemcpyHostToDevice, st), "H2D");
+        lo = h->d_values_stage;
+        up = h->d_upper_stage;
+    }
+    wd::launch_lu_gather(h->d_csr_src, h->d_lu_code, lo, up, h->d_vrow, h->d_vcol, h->nnz_full, st);
+    CK(cudaMemsetAsync(h->d_status, 0xFF, sizeof(status_t), st), "status reset");
+    h->front_dirty = true;
+    double *F = static_cast<double *>(h->d_front);
+    double *Li = static_cast<double *>(h->d_dinv);
+    const DevSym &d = h->dsym;
+    const Plan &P = h->fplan_lu;
+    for (const Launch &L : P.launches) {
+        const int4 *it = P.d_items + L.off;
+        switch (L.kind) {
+            case K_LU_INIT: wd::launch_lu_init(d, F, h->d_vrow, h->d_vcol, it, L.count, st); break;
+            case K_LU_DIAG: wd::launch_lu_diag(d, F, Li, h->d_uinv, it, L.count, L.arg, h->d_status, st); break;
+            case K_LU_PANEL: wd::launch_lu_panel(d, F, Li, h->d_uinv, it, L.count, L.arg, st); break;
+            case K_LU_UPDATE: wd::launch_lu_update(d, F, it, L.count, L.arg, st); break;
+        }
+    }
+    h->launches += 1 + (int64_t)P.launches.size();
+    CK(cudaGetLastError(), "LU factor launch");
+    status_t status = 0;
+    CK(cudaMemcpyAsync(&status, h->d_status, sizeof(status_t), cudaMemcpyDeviceToHost, st), "status D2H");
+    CK(cudaStreamSynchronize(st), "LU factor");
+    if (status != ~0ULL)
+        return fail(h, WD_ERR_NOT_SPD, "zero pivot at column " + std::to_string(status) + " (LU without pivoting)",
+                    (int64_t)status);
+    h->lu_factored = true;
+    return WD_OK;
+}
+
+extern "C" wd_status wd_solve_lu(wd_handle h, double *B, int64_t nrhs, int64_t ldb, int B_on_device,
+                                 void *stream) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!h->lu_factored) return fail(h, WD_ERR_STATE, "wd_solve_lu before a successful wd_factor_lu");
+    const int64_t n = h->S.n;
+    if (!B || nrhs < 0 || ldb < n || nrhs > (1 << 20)) return fail(h, WD_ERR_INVALID_ARG, "bad B");
+    if (nrhs == 0) return WD_OK;
+    CK(cudaSetDevice(h->device), "set device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    constexpr int CH = 16;                      // right-hand sides per pass
+    wd_status s = ensure_solve_ws(h, CH);
+    if (s != WD_OK) return s;
+    double *Bd = B;          // host arrays go through d_B in chunks of CH columns
+    const int64_t ld = ldb;
+    double *Y = static_cast<double *>(h->d_Y), *Tt = static_cast<double *>(h->d_T);
+    double *W = static_cast<double *>(h->d_W);
+    const double *F = static_cast<const double *>(h->d_front);
+    const double *Li = static_cast<const double *>(h->d_dinv);
+    const DevSym &d = h->dsym;
+    for (int64_t c0 = 0; c0 < nrhs; c0 += CH) {
+        const int nc = (int)std::min<int64_t>(CH, nrhs - c0);
+        if (B_on_device) {
+            wd::launch_permute_in<double>(Bd + c0 * ld, ld, Y, d.perm, n, nc, st);
+        } else {
+            CK(cudaMemcpy2DAsync(h->d_B, n * sizeof(double), B + c0 * ldb, ldb * sizeof(double), n * sizeof(double),
+                                 nc, cudaMemcpyHostToDevice, st),
+               "B H2D");
+            wd::launch_permute_in<double>(h->d_B, n, Y, d.perm, n, nc, st);
+        }
+        for (const Launch &L : h->splan_lu_f.launches) {
+            const int4 *it = h->splan_lu_f.d_items + L.off;
+            if (L.kind == K_LU_GATHER) wd::launch_bfwd_gather<double>(d, Y, Tt, W, it, L.count, 16, nc, st);
+            else wd::launch_lu_fwd(d, F, Li, Y, Tt, W, it, L.count, L.arg, nc, st);
+        }
+        for (const Launch &L : h->splan_lu_b.launches)
+            wd::launch_lu_bwd(d, F, h->d_uinv, Y, h->splan_lu_b.d_items + L.off, L.count, L.arg, nc, st);
+        if (B_on_device) {
+            wd::launch_permute_out<double>(Y, Bd + c0 * ld, ld, d.perm, n, nc, st);
+        } else {
+            wd::launch_permute_out<double>(Y, h->d_B, n, d.perm, n, nc, st);
+            CK(cudaMemcpy2DAsync(B + c0 * ldb, ldb * sizeof(double), h->d_B, n * sizeof(double), n * sizeof(double),
+                                 nc, cudaMemcpyDeviceToHost, st),
+               "B D2H");
+        }
+        h->launches += 2 + (int64_t)h->splan_lu_f.launches.size() + (int64_t)h->splan_lu_b.launches.size();
+    }
+    CK(cudaGetLastError(), "LU solve launch");
+    CK(cudaStreamSynchronize(st), "LU solve");
+    return WD_OK;
+}
+
+extern "C" wd_status wd_logdet_lu(wd_handle h, double *logabs, int32_t *sign) {
+    if (!h || !logabs || !sign) return WD_ERR_INVALID_ARG;
+    if (!h->lu_factored) return fail(h, WD_ERR_STATE, "wd_logdet_lu before a successful wd_factor_lu");
+    CK(cudaSetDevice(h->device), "set device");
+    constexpr int NBLK = 64;
+    wd::launch_lu_logdet(h->dsym, static_cast<const double *>(h->d_front), h->d_lu_part, NBLK, 0);
+    double part[2 * NBLK];
+    CK(cudaMemcpy(part, h->d_lu_part, sizeof(part), cudaMemcpyDeviceToHost), "logdet D2H");
+    double sum = 0.0, neg = 0.0;
+    for (int b = 0; b < NBLK; ++b) {
+        sum += part[b];
+        neg += part[NBLK + b];
+    }
+    *logabs = sum;
+    *sign = ((int64_t)neg % 2 == 0) ? 1 : -1;
+    return WD_OK;
+}
+
+extern "C" wd_status wd_export_LU(wd_handle h, double *lpanels, double *utpanels) {
+    if (!h || !lpanels || !utpanels) return WD_ERR_INVALID_ARG;
+    if (!h->lu_factored) return fail(h, WD_ERR_STATE, "wd_export_LU before a successful wd_factor_lu");
+    CK(cudaSetDevice(h->device), "set device");
+    const wd::Symbolic &S = h->S;
+    std::vector<int64_t> poff(S.ns);
+    int64_t tot = 0;
+    for (int s = 0; s < S.ns; ++s) {
+        poff[s] = tot;
+        tot += (int64_t)S.m(s) * S.k(s);
+    }
+    int64_t *d_poff = nullptr;
+    double *d_out = nullptr;
+    CK(cudaMalloc((void **)&d_poff, S.ns * sizeof(int64_t)), "export alloc");
+    if (cudaMalloc((void **)&d_out, 2 * tot * sizeof(double)) != cudaSuccess) {
+        cudaFree(d_poff);
+        return cuda_fail(h, cudaErrorMemoryAllocation, "export alloc");
+    }
+    cudaMemcpy(d_poff, poff.data(), S.ns * sizeof(int64_t), cudaMemcpyHostToDevice);
+    wd::launch_lu_export(h->dsym, static_cast<const double *>(h->d_front), d_out, d_out + tot, d_poff, 0);
+    cudaError_t e = cudaMemcpy(lpanels, d_out, tot * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(utpanels, d_out + tot, tot * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d_out);
+    cudaFree(d_poff);
+    if (e != cudaSuccess) return cuda_fail(h, e, "export");
+    return WD_OK;
 }
 
 extern "C" wd_status wd_export_L_noalloc(wd_handle h, double *panels, void *stream) {

@@ -46,12 +46,14 @@ void init_solve_attributes();
 void init_tc_attributes();
 void init_blocked_attributes();
 void init_tc_solve_attributes();
+void init_lu_attributes();
 inline void init_kernel_attributes() {
     init_front_attributes();
     init_solve_attributes();
     init_tc_attributes();
     init_blocked_attributes();
     init_tc_solve_attributes();
+    init_lu_attributes();
 }
 
 
@@ -282,6 +284,34 @@ void launch_seg_colmax3(const double *R, const double *X, const double *B, const
 template <class T>
 void launch_seg_logdet(const DevSym &d, const T *front, const int32_t *soff, int count, double *sdl,
                        double *out, cudaStream_t st);
+
+// ---- LU without pivoting, FP64 (lu.cu) --------------------------------------
+// code[e] of a full-CSR position: 0 -> (entry, transposed) = (lower, upper)
+// of its source, 1 -> (upper, lower), 2 -> (lower, lower) (the diagonal)
+void launch_lu_gather(const int32_t *src, const int8_t *code, const double *lower, const double *upper,
+                      double *vrow, double *vcol, int64_t nnz, cudaStream_t st);
+void launch_lu_init(const DevSym &d, double *front, const double *vrow, const double *vcol, const int4 *items,
+                    int count, cudaStream_t st);
+void launch_lu_diag(const DevSym &d, double *front, double *linv, double *uinv, const int4 *items, int count,
+                    int kb, status_t *status, cudaStream_t st);
+// items (s, block, side): side 0 rows below the pivot block, side 1 columns right of it
+void launch_lu_panel(const DevSym &d, double *front, const double *linv, const double *uinv, const int4 *items,
+                     int count, int kb, cudaStream_t st);
+// items (s, ti, tj): 64 x 64 tiles of the trailing square of step kb
+void launch_lu_update(const DevSym &d, double *front, const int4 *items, int count, int kb, cudaStream_t st);
+// substitutions on Y (n x nrhs, nrhs <= 64, column-major, factor order):
+// forward items (s, block) (block 0: y of the pivot block; >= 1: 64 later rows),
+// backward items (s, 0, 0, 0)
+void launch_lu_fwd(const DevSym &d, const double *front, const double *linv, double *Y, double *Tt, double *W,
+                   const int4 *items, int count, int kb, int nrhs, cudaStream_t st);
+void launch_lu_bwd(const DevSym &d, const double *front, const double *uinv, double *Y, const int4 *items,
+                   int count, int kb, int nrhs, cudaStream_t st);
+// partial[b] = sum of log |U_jj| over a grid-stride share of the supernodes,
+// partial[nblocks + b] = the number of negative pivots there
+void launch_lu_logdet(const DevSym &d, const double *front, double *partial, int nblocks, cudaStream_t st);
+// factor panels for export: L with its unit diagonal, and U^T, each m_s x k_s per supernode
+void launch_lu_export(const DevSym &d, const double *front, double *lpan, double *upan, const int64_t *poff,
+                      cudaStream_t st);
 
 // ---- allocation-free export of the factor (noalloc.cu) ---------------------
 // the panel offsets sit in a static device array of NOALLOC_MAX_SUPERNODES + 1

@@ -231,9 +231,11 @@ int analyze(Symbolic &S, int64_t n, const int64_t *cp, const int32_t *ri, int di
         for (int64_t j = 0; j < n; ++j) std::sort(ent.begin() + S.pcp[j], ent.begin() + S.pcp[j + 1]);
         S.prow.resize(nnz);
         S.psrc.resize(nnz);
+        S.pswap.resize(nnz);
         for (int64_t e = 0; e < nnz; ++e) {
             S.prow[e] = ent[e].first;
             S.psrc[e] = ent[e].second;
+            S.pswap[e] = (int8_t)(S.iperm[ri[ent[e].second]] != ent[e].first);
         }
     }
 
@@ -467,6 +469,7 @@ int merge(Symbolic &S, const std::vector<const Symbolic *> &parts, std::string &
     S.pcp.reserve(n + 1);
     S.prow.reserve(nnz);
     S.psrc.reserve(nnz);
+    S.pswap.reserve(nnz);
     S.alrow.reserve(nnz);
     S.sfirst.reserve(ns + 1);
     S.srowptr.assign(1, 0);
@@ -489,6 +492,7 @@ int merge(Symbolic &S, const std::vector<const Symbolic *> &parts, std::string &
         for (size_t e = 0; e < P->prow.size(); ++e) {
             S.prow.push_back(P->prow[e] + coff);
             S.psrc.push_back((int32_t)(P->psrc[e] + voff));
+            S.pswap.push_back(P->pswap[e]);
             S.alrow.push_back(P->alrow[e]);
         }
         for (int32_t t = 0; t < P->ns; ++t) {

@@ -16,6 +16,10 @@ struct Symbolic {
     std::vector<int64_t> pcp;
     std::vector<int32_t> prow;
     std::vector<int32_t> psrc;
+    // 1 where the entry (row, col) of P A P^T is the transposed position of
+    // its source entry (the caller's row maps to the column), for
+    // nonsymmetric values given as both triangles
+    std::vector<int8_t> pswap;
 
     // supernodes (contiguous column ranges)
     int32_t ns = 0;
