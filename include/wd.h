@@ -307,7 +307,9 @@ wd_status wd_export_L(wd_handle h, double *panels);
    whose executions overlap (unordered streams, several host threads) share
    the scratch and race: order them.  The handle's own later calls that
    rewrite or free the fronts (wd_factor, wd_analyze, wd_destroy) wait for
-   this call's copy to finish (an event recorded on `stream`).  The caller's
+   this call's copy to finish (an event recorded on `stream`; not when
+   `stream` is capturing a CUDA graph, whose launches the caller orders: the
+   call can be captured, it makes no allocation or synchronizing call).  The caller's
    current device is restored before returning.  Needs a successful
    wd_factor. */
 #define WD_NOALLOC_MAX_SUPERNODES 65536

@@ -66,6 +66,7 @@ struct Plan {
     int rgt = 16;            // solve plans: right-hand sides per gather CTA
     int large = 0;           // solve plans: product mode (0: 64 x 32 tiles, 2: few right-hand sides)
     int64_t slots = 0;       // solve plans: partial-sum slots of the largest split step
+    int64_t ksplit = 0;      // solve plans: CTAs of the largest launch split over the inner dimension
 };
 
 struct GraphCache {
@@ -164,6 +165,13 @@ struct wd_ctx {
     void *d_Y = nullptr, *d_W = nullptr, *d_T = nullptr;
     void *d_part = nullptr;        // partial sums of the backward split reduction
     int64_t part_elems = 0;
+    // tensor-core solve products split over the inner dimension: one partial
+    // tile per CTA and one arrival counter per output tile (kept at zero
+    // between launches)
+    float *d_ksw = nullptr;
+    int *d_kcnt = nullptr;
+    int64_t ksw_items = 0;
+    int sms = 152;                 // multiprocessors of the device
     double *d_B = nullptr, *d_Bp = nullptr, *d_X = nullptr, *d_R = nullptr, *d_cm = nullptr;
     float2 *d_Xp = nullptr;   // double-float split of the refinement vectors, (hi, lo) pairs
     int64_t W_rows = 0;   // sum of (m_s - k_s)
@@ -276,7 +284,9 @@ wd_status wd_create(wd_handle *out, const wd_options *opt) {
     }
     h->mem.count = h->work.count = &h->allocs;
     h->mem.fail_at = h->work.fail_at = h->opt.test_fail_alloc;
-    if (!h->opt.symbolic_only && cudaGetDevice(&h->device) != cudaSuccess) {
+    if (!h->opt.symbolic_only &&
+        (cudaGetDevice(&h->device) != cudaSuccess ||
+         cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)) {
         cudaGetLastError();
         delete h;
         return WD_ERR_CUDA;
@@ -494,9 +504,31 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
     }
 }
 
-static void build_solve_plan(const wd::Symbolic &S, int nrhs, int large, Plan &p) {
+// Tensor-core product launches with few output tiles split the inner
+// dimension (up to 512 columns of a super-block) over up to four CTAs per
+// tile, so that a launch fills about one wave of the device; the item's z
+// carries the split (row block | split << 16 | splits << 24).
+static void split_inner(Plan &p, size_t f0, int sms) {
+    const int64_t tiles = (int64_t)(p.items.size() - f0);
+    if (tiles <= 0 || 2 * tiles > sms) return;
+    const int nks = (int)std::min<int64_t>(4, sms / tiles);
+    std::vector<int4> split;
+    split.reserve(tiles * nks);
+    for (size_t i = f0; i < p.items.size(); ++i)
+        for (int ks = 0; ks < nks; ++ks) {
+            int4 q = p.items[i];
+            q.z = q.z | (ks << 16) | (nks << 24);
+            split.push_back(q);
+        }
+    p.items.resize(f0);
+    p.items.insert(p.items.end(), split.begin(), split.end());
+    p.ksplit = std::max<int64_t>(p.ksplit, (int64_t)split.size());
+}
+
+static void build_solve_plan(const wd::Symbolic &S, int nrhs, int large, int sms, Plan &p) {
     p.items.clear();
     p.launches.clear();
+    p.ksplit = 0;
     const int rgt = nrhs >= 48 ? 64 : 16;   // right-hand sides per gather CTA
     p.rgt = rgt;
     p.large = large;
@@ -537,6 +569,7 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, int large, Plan &p
                 fl += (double)w * (w + 1) * R;
                 el += (double)w * (w + 1) / 2 + 2.0 * w * R;
             }
+            if (large == 1) split_inner(p, f0, sms);
             add_launch(p, K_FWD_XAPPLY, f0, sb, fl, el, 0);
             f0 = p.items.size();
             el = fl = 0;
@@ -552,6 +585,7 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, int large, Plan &p
                 fl += 2.0 * (nJ + nR) * w * R;
                 el += (double)(nJ + nR) * w + 2.0 * (nJ + nR) * R + w * R;
             }
+            if (large == 1) split_inner(p, f0, sms);
             add_launch(p, K_FWD_BUPDATE, f0, sb, fl, el, 0);
         }
     }
@@ -604,6 +638,7 @@ static void build_solve_plan(const wd::Symbolic &S, int nrhs, int large, Plan &p
                 fl += (double)w * (w + 1) * R;
                 el += (double)w * (w + 1) / 2 + 2.0 * w * R;
             }
+            if (large == 1) split_inner(p, f0, sms);
             add_launch(p, K_BWD_XAPPLY, f0, sb, fl, el, 0);
         }
     }
@@ -689,6 +724,9 @@ static wd_status reset_analysis(wd_handle h) {
     h->aplan = Plan();
     h->splan_nrhs = h->aplan_nrhs = -1;
     h->ws_cols = 0;
+    h->d_ksw = nullptr;
+    h->d_kcnt = nullptr;
+    h->ksw_items = 0;
     h->d_front = nullptr;
     h->d_dinv = nullptr;
     h->d_gcsr = h->mass_buf = nullptr;
@@ -1331,6 +1369,9 @@ static wd_status ensure_solve_ws(wd_handle h, int64_t nrhs) {
     h->part_elems = 0;
     h->d_B = h->d_Bp = h->d_X = h->d_R = h->d_cm = h->d_P = nullptr;
     h->d_Xp = nullptr;
+    h->d_ksw = nullptr;
+    h->d_kcnt = nullptr;
+    h->ksw_items = 0;
     h->splan = Plan();
     h->aplan = Plan();
     h->splan_nrhs = h->aplan_nrhs = -1;
@@ -1375,6 +1416,8 @@ static void enqueue_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st, boo
     ta.tstatus = h->d_tstatus;
     ta.nrhs = nrhs;
     ta.wait_limit = (uint32_t)std::max(0, h->opt.wait_limit);
+    ta.ksw = h->d_ksw;
+    ta.kcnt = h->d_kcnt;
     const bool tc = lg == 1 && sizeof(T) == 4;
     size_t li = 0;
     for (const Launch &L : h->splan.launches) {
@@ -1539,9 +1582,20 @@ static wd_status prepare_solve(wd_handle h, int64_t nrhs) {
     // matrix-vector shaped kernels, lanes over rows
     const int large = nrhs <= 8 ? 2 : (h->prec == WD_MIXED && !h->opt.solve_simt ? 1 : 0);
     if (h->splan_nrhs != nrhs || h->splan.large != large) {
-        build_solve_plan(h->S, (int)nrhs, large, h->splan);
+        build_solve_plan(h->S, (int)nrhs, large, h->sms, h->splan);
         s = upload_plan(h, h->work, h->splan);
         if (s != WD_OK) return s;
+        if (h->splan.ksplit > h->ksw_items) {
+            if (h->d_ksw) h->work.release(h->d_ksw);
+            if (h->d_kcnt) h->work.release(h->d_kcnt);
+            h->d_ksw = nullptr;
+            h->d_kcnt = nullptr;
+            h->ksw_items = 0;
+            CK(h->work.alloc((void **)&h->d_ksw, h->splan.ksplit * wd::TC_SOLVE_TILE * sizeof(float)), "solve ws");
+            CK(h->work.alloc((void **)&h->d_kcnt, h->splan.ksplit * sizeof(int)), "solve ws");
+            CK(cudaMemset(h->d_kcnt, 0, h->splan.ksplit * sizeof(int)), "solve ws clear");
+            h->ksw_items = h->splan.ksplit;
+        }
         const int64_t need = std::max<int64_t>(h->splan.slots, 1) * wd::solve_tile_rows(large) *
                              wd::solve_tile_rhs(large);
         if (need > h->part_elems) {
@@ -2511,7 +2565,11 @@ extern "C" wd_status wd_export_L_noalloc(wd_handle h, double *panels, void *stre
             wd::launch_export_panels<float>(h->dsym, static_cast<const float *>(h->d_front), panels, poff, st);
         h->launches += 2;
         e = cudaGetLastError();
-        if (e == cudaSuccess) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (e == cudaSuccess) e = cudaStreamIsCapturing(st, &cs);
+        if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+            // (a captured export runs when its graph is launched: ordering
+            // those launches is the caller's)
             e = cudaEventRecord(h->export_ev, st);
             if (e == cudaSuccess) h->export_pending = true;
         }

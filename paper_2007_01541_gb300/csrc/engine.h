@@ -268,7 +268,10 @@ struct TcSolveArgs {
     int nrhs;
     int upper;                    // xapply: 0 forward (lower X), 1 backward (X^T)
     uint32_t wait_limit;          // 0: the default
+    float *ksw;                   // split inner dimension: one partial tile per CTA
+    int *kcnt;                    // split inner dimension: arrivals per output tile (zero between launches)
 };
+constexpr int TC_SOLVE_TILE = 128 * 64;   // entries of one output tile of the tensor-core solve products
 void launch_tc_xapply(const DevSym &d, const TcSolveArgs &a, const int4 *items, int count, cudaStream_t st);
 void launch_tc_bupdate(const DevSym &d, const TcSolveArgs &a, const int4 *items, int count, cudaStream_t st);
 void launch_tc_breduce(const DevSym &d, const TcSolveArgs &a, const int4 *items, int count, cudaStream_t st);

@@ -23,9 +23,18 @@
 // place (hi) and into the lo plane, and one thread issues the chunk's MMAs
 // while the next chunks are in flight.
 //
+// A launch with few output tiles (the top of the tree: a few super-blocks of
+// one or two fronts) splits the inner dimension of xapply and bupdate over up
+// to four CTAs per tile: each computes the product over its part of the
+// chunks, and the last CTA of the tile to arrive (an atomic counter, no
+// waiting) adds the partial tiles in a fixed order and writes the result.
+// The serial chain of chunks per CTA, which sets the time of these launches,
+// shrinks by the split factor.
+//
 // Every wait is bounded; on expiry the CTA records the timeout status, waits
 // (with a fixed bound) for its copies and products in flight, frees its tensor
-// memory and returns without writing.
+// memory and returns without writing (the output of a split tile whose CTA
+// timed out is unspecified; the call reports the timeout).
 #include "dev_common.cuh"
 #include "engine.h"
 #include "tc_common.cuh"
@@ -63,6 +72,7 @@ struct Geo {
     int b0, w, wp;       // super-block: first column, width, width rounded to 64
     int c0, nc;          // right-hand sides of the tile
     int kc0, nchunk;     // first 32-wide chunk of the inner dimension (in its own index), chunks
+    int ks, nks;         // xapply / bupdate: this CTA's part of the inner dimension, parts
     // xapply
     int r0;
     // bupdate
@@ -88,8 +98,15 @@ __device__ __forceinline__ Geo geometry(const DevSym &d, const TcSolveArgs &a, i
     const int gt = OP == OP_BREDUCE ? (it.z & 0xFFFF) : (it.w & 0xFFFF);
     g.c0 = gt * TN;
     g.nc = min(TN, a.nrhs - g.c0);
+    g.ks = 0;
+    g.nks = 1;
+    if (OP != OP_BREDUCE) {
+        g.ks = (it.z >> 16) & 0xFF;
+        g.nks = max(1, it.z >> 24);
+    }
+    const int rb = it.z & 0xFFFF;
     if (OP == OP_XAPPLY) {
-        g.r0 = it.z * TM;
+        g.r0 = rb * TM;
         // lower (forward): columns [0, r0 + TM); upper (backward): [r0, wp)
         const int ka = a.upper ? g.r0 : 0, kb = a.upper ? g.wp : min(g.wp, g.r0 + TM);
         g.kc0 = ka / TK;
@@ -97,11 +114,11 @@ __device__ __forceinline__ Geo geometry(const DevSym &d, const TcSolveArgs &a, i
     } else if (OP == OP_BUPDATE) {
         g.seg = it.w >> 16;
         if (g.seg == 0) {
-            g.i0 = g.b0 + g.w + it.z * TM;   // pivot rows after B
+            g.i0 = g.b0 + g.w + rb * TM;     // pivot rows after B
             g.nrow = g.k - g.i0;
             g.mrow = g.i0;
         } else {
-            g.i0 = it.z * TM;                // rows of R
+            g.i0 = rb * TM;                  // rows of R
             g.nrow = (g.m - g.k) - g.i0;
             g.mrow = g.kp + g.i0;
         }
@@ -117,6 +134,13 @@ __device__ __forceinline__ Geo geometry(const DevSym &d, const TcSolveArgs &a, i
         g.kc0 = g.q0 / TK;
         g.nchunk = (g.q1 - g.q0 + TK - 1) / TK;
         g.slot = it.w;
+    }
+    if (g.nks > 1) {
+        // chunks [ks cps, (ks + 1) cps) of the inner dimension
+        const int cps = (g.nchunk + g.nks - 1) / g.nks;
+        const int cb = min(g.nchunk, g.ks * cps);
+        g.kc0 += cb;
+        g.nchunk = min(g.nchunk - cb, cps);
     }
     return g;
 }
@@ -221,6 +245,7 @@ __global__ void __launch_bounds__(NTH, 1) tc_solve_kernel(DevSym d, TcSolveArgs 
     uint64_t *done = empty + NSTG;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
     int *abort_flag = reinterpret_cast<int *>(tslot + 1);
+    int *last_flag = abort_flag + 1;
     const uint32_t limit = a.wait_limit ? a.wait_limit : WAIT_DEFAULT;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const Geo g = geometry<OP>(d, a, items[blockIdx.x]);
@@ -304,25 +329,68 @@ __global__ void __launch_bounds__(NTH, 1) tc_solve_kernel(DevSym d, TcSolveArgs 
     tc::tc_fence_after();
     __syncthreads();
     const bool aborted = *(volatile int *)abort_flag != 0;
-    if (!aborted) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (its 32 rows of the
-        // tile) and right-hand sides 32 (w / 4) .. +32
-        const int lg = warp & 3, half = warp >> 2;
-        const int r = 32 * lg + lane;
-        float v[32];
-        if (g.nchunk > 0) {
-            float t[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 32 * half, t);
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (its 32 rows of the
+    // tile) and right-hand sides 32 (w / 4) .. +32
+    const int lg = warp & 3, half = warp >> 2;
+    const int r = 32 * lg + lane;
+    const int jb = 32 * half;
+    float v[32];
+    if (!aborted && g.nchunk > 0) {
+        float t[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 32 * half, t);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = t[i];
-            tc::tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 32 * half + 16, t);
+        for (int i = 0; i < 16; ++i) v[i] = t[i];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 32 * half + 16, t);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[16 + i] = t[i];
-        } else {
+        for (int i = 0; i < 16; ++i) v[16 + i] = t[i];
+    } else {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = 0.f;
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+    }
+    if (aborted && tid == 0) {
+        // after a timeout: the issued bulk fills have landed and the issued
+        // MMAs have completed before the shared memory and TMEM are given up
+        // (every thread's own copies were waited for above)
+        if (OP == OP_BUPDATE)
+            for (int cc = (issued > NSTG ? issued - NSTG : 0); cc < issued; ++cc)
+                tc::mbar_wait(&full[cc % NSTG], (cc / NSTG) & 1, DRAIN_LIMIT);
+        tc::mbar_wait(done, 0, DRAIN_LIMIT);
+        atomicMax(a.tstatus, 1ull);
+    }
+    bool write = !aborted;
+    if (OP != OP_BREDUCE && g.nks > 1) {
+        // split inner dimension: every CTA of the tile stores its partial
+        // product and counts itself in; the last to arrive adds the partials
+        // in split order (the same sum whichever CTA is last) and writes the
+        // tile, then resets the counter for the next launch.  A CTA that
+        // timed out takes part with a zero partial (the call reports the
+        // timeout; its output is unspecified).
+        const int tile = blockIdx.x - g.ks;
+        float *mine = a.ksw + (int64_t)blockIdx.x * TC_SOLVE_TILE + r;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) mine[(jb + i) * TM] = v[i];
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) *last_flag = atomicAdd(a.kcnt + tile, 1) == g.nks - 1;
+        __syncthreads();
+        write = *(volatile int *)last_flag != 0;
+        if (write) {
+            __threadfence();
+            const float *base = a.ksw + (int64_t)tile * TC_SOLVE_TILE + r;
+            float acc[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+            for (int q = 0; q < g.nks; ++q) {
+                const volatile float *pq = base + (int64_t)q * TC_SOLVE_TILE;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) acc[i] += pq[(jb + i) * TM];
+            }
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = acc[i];
+            if (tid == 0) a.kcnt[tile] = 0;
         }
-        const int jb = 32 * half;
+    }
+    if (write) {
         if (OP == OP_XAPPLY) {
             if (g.r0 + r < g.w) {
                 float *o = a.out + g.f + g.b0 + g.r0 + r + (int64_t)g.c0 * d.n;
@@ -350,15 +418,6 @@ __global__ void __launch_bounds__(NTH, 1) tc_solve_kernel(DevSym d, TcSolveArgs 
 #pragma unroll
             for (int i = 0; i < 32; ++i) o[(int64_t)i * TM] = v[i];
         }
-    } else if (tid == 0) {
-        // after a timeout: the issued bulk fills have landed and the issued
-        // MMAs have completed before the shared memory and TMEM are given up
-        // (every thread's own copies were waited for above)
-        if (OP == OP_BUPDATE)
-            for (int cc = (issued > NSTG ? issued - NSTG : 0); cc < issued; ++cc)
-                tc::mbar_wait(&full[cc % NSTG], (cc / NSTG) & 1, DRAIN_LIMIT);
-        tc::mbar_wait(done, 0, DRAIN_LIMIT);
-        atomicMax(a.tstatus, 1ull);
     }
     tc::tc_fence_before();
     __syncthreads();

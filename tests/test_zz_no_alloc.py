@@ -78,3 +78,28 @@ def test_noalloc_export_needs_factor(wdlib, cuda):
     with pytest.raises(wdlib.WdError) as e:
         s.export_L_noalloc(torch.empty(s._panel_size(), dtype=torch.float64, device="cuda"))
     assert e.value.status == wdlib.WD_ERR_STATE
+
+
+def test_noalloc_export_can_be_captured_in_a_cuda_graph(wdlib, cuda):
+    """Stream capture rejects cudaMalloc, cudaFree and synchronizing calls: a
+    capture of the export that succeeds and replays to the same panels shows
+    the call makes none of them."""
+    torch = cuda
+    b = haar_basis(2, 6)
+    cp, ri = compressed_pattern(b)
+    v = compressed_values(b, cp, ri, Kernel("matern32", 0.1), 1e-3)
+    s = wdlib.Solver().analyze(cp, ri, b).factor(v, "fp64")
+    ref = s.export_L()
+    out = torch.empty(ref.size, dtype=torch.float64, device="cuda")
+    s.export_L_noalloc(out, stream=torch.cuda.current_stream().cuda_stream)   # warm-up: module, address
+    torch.cuda.synchronize()
+    out.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        s.export_L_noalloc(out, stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert np.array_equal(out.cpu().numpy(), ref)
