@@ -456,6 +456,88 @@ __global__ void __launch_bounds__(THREADS, 4) spmv_df32_kernel(DevSym d, const i
     }
 }
 
+// The same product for a multiple of 4 right-hand sides: a half-warp covers 64
+// right-hand sides with one 16-byte load of x per lane, the two halves of the
+// warp take alternate entries of the row chunk (their sums are added at the
+// end), and the x row and the value of the next entry are fetched before the
+// current one is accumulated.  Fewer instructions per (entry, right-hand
+// side) term than the lane-per-right-hand-side form: one shuffle triple per
+// four terms and one load per four.
+__device__ __forceinline__ void spmv_x4_fetch(const int32_t col, const float mh, const float ml, int src,
+                                              const float *__restrict__ Xf, int nrhs, int c, bool vc, float4 &x,
+                                              float &ah, float &al) {
+    const int cc = __shfl_sync(0xffffffffu, col, src);
+    ah = __shfl_sync(0xffffffffu, mh, src);
+    al = __shfl_sync(0xffffffffu, ml, src);
+    x = vc ? *reinterpret_cast<const float4 *>(Xf + (int64_t)cc * nrhs + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ void spmv_x4_acc(DF (&a)[4], float ah, float al, float4 x) {
+    df_add_prod1(a[0], ah, al, x.x);
+    df_add_prod1(a[1], ah, al, x.y);
+    df_add_prod1(a[2], ah, al, x.z);
+    df_add_prod1(a[3], ah, al, x.w);
+}
+
+__global__ void __launch_bounds__(THREADS, 4) spmv_df32x4_kernel(DevSym d, const int4 *__restrict__ items,
+                                                              int count, const float *__restrict__ vh,
+                                                              const float *__restrict__ vl,
+                                                              const float *__restrict__ Xf, const double *S,
+                                                              double *R, double *__restrict__ P, int nrhs) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    if (w >= count) return;
+    const int4 it = items[w];
+    const int64_t row = it.x;
+    const int e0 = it.y, e1 = it.z, slot = it.w;
+    for (int c0 = 0; c0 < nrhs; c0 += 64) {
+        const int c = c0 + 4 * hl;
+        const bool vc = c < nrhs;
+        DF a0[4], a1[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a0[q] = a1[q] = DF{0.f, 0.f};
+        for (int eb = e0; eb < e1; eb += 32) {
+            // entry eb + lane's column and value; lanes past the chunk hold
+            // column 0 and value 0 (their products are exact zeros)
+            const int my = eb + lane, cnt = min(32, e1 - eb);
+            const int32_t col = my < e1 ? d.csr_col[my] : 0;
+            const float mh = my < e1 ? vh[my] : 0.f, ml = my < e1 ? vl[my] : 0.f;
+            const int npair = (cnt + 1) >> 1;   // entry 2 jj + half of the group
+            float4 x;
+            float ah, al;
+            spmv_x4_fetch(col, mh, ml, half, Xf, nrhs, c, vc, x, ah, al);
+            for (int jj = 0; jj < npair; jj += 2) {
+                float4 xn;
+                float ahn, aln;
+                if (jj + 1 < npair) spmv_x4_fetch(col, mh, ml, 2 * (jj + 1) + half, Xf, nrhs, c, vc, xn, ahn, aln);
+                spmv_x4_acc(a0, ah, al, x);
+                if (jj + 1 < npair) {
+                    if (jj + 2 < npair) spmv_x4_fetch(col, mh, ml, 2 * (jj + 2) + half, Xf, nrhs, c, vc, x, ah, al);
+                    spmv_x4_acc(a1, ahn, aln, xn);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                df_renorm(a0[q]);
+                df_renorm(a1[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            df_add(a0[q], a1[q]);
+            const DF o{__shfl_xor_sync(0xffffffffu, a0[q].hi, 16), __shfl_xor_sync(0xffffffffu, a0[q].lo, 16)};
+            df_add(a0[q], o);
+        }
+        if (half == 0 && vc) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const double sq = (double)a0[q].hi + (double)a0[q].lo;
+                if (slot < 0) R[row * nrhs + c + q] = S[row * nrhs + c + q] - sq;
+                else P[(int64_t)slot * nrhs + c + q] = sq;
+            }
+        }
+    }
+}
+
 // R = S - sum of a cut row's partial sums, in slot order (S may be R)
 __global__ void spmv_finish_src_kernel(const int4 *__restrict__ items, int count, const double *S, double *R,
                                        const double *__restrict__ P, int nrhs) {
@@ -782,7 +864,10 @@ void launch_spmv_residual_df32(const DevSym &d, const int4 *chunks, int nchunks,
                                const float *vh, const float *vl, const float *Xf, const double *S, double *R,
                                double *P, int64_t nrhs, cudaStream_t st) {
     const int blocks = (int)(((int64_t)nchunks * 32 + THREADS - 1) / THREADS);
-    spmv_df32_kernel<<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, vh, vl, Xf, S, R, P, (int)nrhs);
+    if (nrhs % 4 == 0)
+        spmv_df32x4_kernel<<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, vh, vl, Xf, S, R, P, (int)nrhs);
+    else
+        spmv_df32_kernel<<<blocks, THREADS, 0, st>>>(d, chunks, nchunks, vh, vl, Xf, S, R, P, (int)nrhs);
     if (nfin > 0) spmv_finish_src_kernel<<<nfin, 64, 0, st>>>(fin, nfin, S, R, P, (int)nrhs);
 }
 
