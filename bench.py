@@ -57,7 +57,14 @@ TF32_PER_BF16 = 1.1 / 2.25
 # kernel from one ncu capture, keyed by (workload, kernel, nd_leaf, relax_k,
 # relax_pct), with the SHA-1 of the source file the kernel was built from:
 # reported as null once that file has changed.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # 2D 256^2, tc_schur_kernel in its pivot-block update mode: 112 launches of
+    # one timed step, dram__bytes_read.sum + dram__bytes_write.sum averaged over
+    # the launches (a one-pass capture, gpu__time_duration.sum beside it)
+    ("2d", "tc_schur_update_fp32", 128, 64, 10): {
+        "bytes": 1.432e7, "source": "paper_2007_01541_gb300/csrc/tc_schur.cu",
+        "sha1": "8ef397c4b80e9b17fb26b02b8d48367e5067f5c1"},
+}
 
 
 def amalgamation(args):
