@@ -221,3 +221,45 @@ def test_theta_steps_with_mass_against_the_oracle(wdlib, cuda, name, prec, nrhs,
     Ui = s.theta_step(U0, F, theta=theta, dt=dt)
     Uoi = oracle.theta_step(oi, cp, ri, k, U0, F, theta, dt)
     assert np.abs(Ui - Uoi).max() <= 1e-10 * np.abs(Uoi).max()
+
+
+@pytest.mark.parametrize("dim,J", [(1, 8), (2, 5)])
+def test_mass_matrix_on_its_own_pattern_has_less_fill(wdlib, dim, J):
+    """G analyzed on its own (sparser) pattern gets its own ordering, with far
+    less fill than G ordered as the system matrix (Section 6); the oracle's
+    factor of G on its own pattern reproduces G."""
+    from wdgen import mass_matrix, own_pattern
+
+    b = haar_basis(dim, J)
+    cp, ri = compressed_pattern(b)
+    g = mass_matrix(b, cp, ri, 0.3)
+    gcp, gri, gv = own_pattern(cp, ri, g)
+    assert gri.size < ri.size
+    nnz_as_A = wdlib.Solver(symbolic_only=True).analyze(cp, ri, b).info()["nnz_L"]
+    nnz_own = wdlib.Solver(symbolic_only=True).analyze(gcp, gri, b).info()["nnz_L"]
+    assert nnz_own < nnz_as_A
+    o = oracle.Oracle(gcp, gri, b)
+    assert o.factor(gv) == 0
+    G = oracle.sym_lower_to_dense(gcp, gri, gv)
+    Ld = o.L_dense()
+    PG = G[np.ix_(o.perm, o.perm)]
+    assert np.abs(Ld @ Ld.T - PG).max() <= 1e-13
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_mass_matrix_inverse_on_its_own_ordering(wdlib, cuda, prec):
+    """G^-1 applied by a handle analyzed on G's own pattern (its own ordering):
+    backward error <= 1e-12 against G, and the same solution as the oracle's."""
+    from wdgen import mass_matrix, own_pattern
+
+    b = haar_basis(2, 6)
+    cp, ri = compressed_pattern(b)
+    gcp, gri, gv = own_pattern(cp, ri, mass_matrix(b, cp, ri, 0.3))
+    s = wdlib.Solver().analyze(gcp, gri, b).factor(gv, prec)
+    B = rhs(b.N, 4, seed=7)
+    X = s.solve(B)
+    assert oracle.backward_error(gcp, gri, gv, X, B).max() <= 1e-12
+    o = oracle.Oracle(gcp, gri, b)
+    assert o.factor(gv) == 0
+    assert np.abs(X - o.solve(B)).max() <= 1e-10 * np.abs(X).max()

@@ -241,6 +241,21 @@ def mass_matrix(basis: Basis, colptr, rowidx, coupling: float = 0.3) -> np.ndarr
     return g
 
 
+def own_pattern(colptr, rowidx, values):
+    """(colptr, rowidx, values) of the stored nonzeros of a lower CSC matrix
+    given on a larger pattern (the diagonal is always kept): the mass matrix
+    on its own, sparser pattern, which its own analysis orders apart from the
+    system matrix (Section 6)."""
+    cp = np.asarray(colptr, np.int64)
+    ri = np.asarray(rowidx, np.int64)
+    v = np.asarray(values, np.float64)
+    N = cp.size - 1
+    cols = np.repeat(np.arange(N), np.diff(cp))
+    keep = (v != 0.0) | (ri == cols)
+    ncp = np.concatenate([[0], np.cumsum(np.bincount(cols[keep], minlength=N))]).astype(np.int64)
+    return ncp, ri[keep].astype(np.int32), v[keep]
+
+
 def cutoff_parameters(J: int, j: int, jp: int, a: float, delta: float, q: float, dtilde: float):
     """(B_{j,j'}, B^s_{j,j'}) of Theorem 3.1 (Eq. cut-off parameters), in
     domain units: the support-distance and singular-support-distance bounds
