@@ -590,6 +590,22 @@ def run_ours(args):
                     "tflops": dist.sum(flops_step) / (ms64 / 1e3) / 1e12,
                     "backward_error": si64["backward_error"], "phases_ms": si64["phases_ms"],
                     "top_kernels": _top(kst64, 4)}
+        # the FP64 factorization with its Schur updates on the tensor cores
+        # (bf16 slices): same arithmetic bar, no refinement
+        s_tc = wd.Solver(**solver_opts(args, profile=False), fp64_tc_schur=True).analyze(
+            w["colptr"], w["rowidx"], w["basis"])
+        ms64t, _, _, si64t = timed(s_tc, "fp64", max(2, args.steps // 2), 2)
+        kst64t = []
+        if not args.no_replay:
+            sp_tc = wd.Solver(**solver_opts(args, profile=True), fp64_tc_schur=True).analyze(
+                w["colptr"], w["rowidx"], w["basis"])
+            kst64t = timed(sp_tc, "fp64", 1, 1)[1]
+            sp_tc.close()
+        s_tc.close()
+        res_fp64["tensor_core_updates"] = {
+            "ms_per_step": ms64t, "tflops": dist.sum(flops_step) / (ms64t / 1e3) / 1e12,
+            "backward_error": si64t["backward_error"], "phases_ms": si64t["phases_ms"],
+            "speedup_vs_fp64": ms64 / ms64t, "top_kernels": _top(kst64t, 4)}
     value = dist.sum(flops_step) / (ms_mixed / 1e3) / 1e12
 
     # roofline of the dominant kernel of the mixed step

@@ -90,6 +90,14 @@ typedef struct {
     int32_t solve_simt;     /* WD_MIXED, more than 8 right-hand sides: 1 runs
                                the solves' products on the FP32 SIMT pipes
                                instead of the tensor cores (0)                */
+    int32_t fp64_tc_schur;  /* WD_FP64: 1 runs the Schur updates (C -= L21
+                               L21^T, Section 4) on the tensor cores with the
+                               FP64 values split into eight bf16 slices of 7
+                               bits per 64-column block and row (products
+                               accumulated exactly, combined in FP64; error
+                               within FP64's own bound for these sums); the
+                               panels, diagonal blocks and solves stay FP64.
+                               0: FP64 on the SIMT pipes (0)                 */
 } wd_options;
 
 /* Optional geometry for the nested-dissection ordering.  Per vertex (basis

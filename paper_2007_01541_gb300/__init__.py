@@ -41,7 +41,7 @@ class WdOptions(ctypes.Structure):
                 ("symbolic_only", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("diag64_min_k", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
                 ("test_closed_gate", ctypes.c_int32), ("test_fail_alloc", ctypes.c_int32),
-                ("solve_simt", ctypes.c_int32)]
+                ("solve_simt", ctypes.c_int32), ("fp64_tc_schur", ctypes.c_int32)]
 
 
 class WdGeometry(ctypes.Structure):
@@ -169,7 +169,8 @@ class Solver:
     def __init__(self, nd_leaf=DEFAULTS["nd_leaf"], relax_k=DEFAULTS["relax_k"],
                  relax_pct=DEFAULTS["relax_pct"], ir_max_iter=10, ir_tol=1e-12,
                  symbolic_only=False, profile=False, use_graphs=True, diag64_min_k=None,
-                 wait_limit=0, test_closed_gate=False, test_fail_alloc=0, solve_simt=False):
+                 wait_limit=0, test_closed_gate=False, test_fail_alloc=0, solve_simt=False,
+                 fp64_tc_schur=False):
         self._lib = load()
         o = WdOptions()
         self._lib.wd_default_options(ctypes.byref(o))
@@ -184,6 +185,7 @@ class Solver:
         o.test_closed_gate = 1 if test_closed_gate else 0
         o.test_fail_alloc = test_fail_alloc
         o.solve_simt = 1 if solve_simt else 0
+        o.fp64_tc_schur = 1 if fp64_tc_schur else 0
         self._h = ctypes.c_void_p()
         self._check(self._lib.wd_create(ctypes.byref(self._h), ctypes.byref(o)))
         self.n = None

@@ -31,7 +31,8 @@ enum LaunchKind {
     K_BWD_REDUCE, K_BWD_FINISH, K_BWD_XAPPLY,                  // backward solve
     K_APPLY_L,
     K_LU_INIT, K_LU_DIAG, K_LU_PANEL, K_LU_UPDATE,               // LU factor
-    K_LU_GATHER, K_LU_FWD, K_LU_BWD                              // LU substitutions
+    K_LU_GATHER, K_LU_FWD, K_LU_BWD,                             // LU substitutions
+    K_OZ_SLICE, K_OZ_UPDATE, K_OZ_SYRK                           // FP64 updates on the tensor cores
 };
 
 struct Launch {
@@ -50,7 +51,8 @@ const char *kind_name(int k) {
                                   "sbinv_stage", "sbinv_transpose", "fwd_gather", "fwd_xapply",
                                   "fwd_bupdate", "bwd_reduce", "bwd_finish", "bwd_xapply",
                                   "apply_L", "lu_init", "lu_diag", "lu_panel", "lu_update",
-                                  "lu_gather", "lu_fwd", "lu_bwd"};
+                                  "lu_gather", "lu_fwd", "lu_bwd", "oz_slice", "oz_schur_update",
+                                  "oz_schur_syrk"};
     return names[k];
 }
 
@@ -140,6 +142,12 @@ struct wd_ctx {
     size_t dinv_elems = 0;
     void *d_xs = nullptr, *d_xts = nullptr;  // super-block inverses and their transposes
     int64_t *d_xsoff = nullptr;
+    // FP64 updates on the tensor cores: bf16 slice planes and row-scale
+    // exponents per supernode and 64-column block (wd_options.fp64_tc_schur)
+    unsigned char *d_oz_sl = nullptr;
+    int16_t *d_oz_ex = nullptr;
+    int64_t *d_oz_soff = nullptr, *d_oz_eoff = nullptr;
+    int64_t oz_sl_bytes = 0, oz_ex_elems = 0;
     size_t xs_elems = 0;
     unsigned char *d_pack = nullptr;  // packed tf32 panel lines (FP32 fronts)
     int64_t pack_total = 0;
@@ -278,7 +286,7 @@ wd_status wd_create(wd_handle *out, const wd_options *opt) {
     if (opt) h->opt = *opt;
     if (h->opt.nd_leaf < 1 || h->opt.relax_k < 0 || h->opt.relax_pct < 0 || h->opt.ir_max_iter < 0 ||
         !(h->opt.ir_tol > 0) || h->opt.diag64_min_k < 0 || h->opt.wait_limit < 0 ||
-        h->opt.test_fail_alloc < 0) {
+        h->opt.test_fail_alloc < 0 || h->opt.fp64_tc_schur < 0 || h->opt.fp64_tc_schur > 1) {
         delete h;
         return WD_ERR_INVALID_ARG;
     }
@@ -365,7 +373,9 @@ static int kpad(int k) { return (k + 31) / 32 * 32; }
 // rows of a front: pivot rows, zero padding to a multiple of 32, rows below
 static int front_order(const wd::Symbolic &S, int s) { return kpad(S.k(s)) + S.m(s) - S.k(s); }
 
-static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
+// oz (FP64 fronts): the Schur updates through bf16 slices on the tensor
+// cores, each panel launch followed by the slicing of its rows.
+static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc, bool oz = false) {
     const int SCHUR_BM = tc ? wd::TC_BM : wd::SCHUR_BM;
     const int SCHUR_BN = tc ? wd::TC_BN : wd::SCHUR_BN;
     p.items.clear();
@@ -420,6 +430,15 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
                 el += 2.0 * (m - t0) * nb + (double)NB * NB;
             }
             add_launch(p, K_PANEL, f0, kb, fl, el, 0);
+            if (oz) {
+                // the same rows, sliced for the updates
+                const size_t g0 = p.items.size(), g1 = p.items.size() - f0;
+                for (size_t q = 0; q < g1; ++q) {
+                    const int4 itq = p.items[f0 + q];
+                    p.items.push_back(itq);
+                }
+                add_launch(p, K_OZ_SLICE, g0, kb, 0, el, 0);
+            }
             // trailing pivot columns; the CTA of tile (0, 0) also factors the
             // next diagonal block
             f0 = p.items.size();
@@ -441,7 +460,7 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
                 fl += 2.0 * nb * ent + diag_flops(nb2);
                 el += 2.0 * ent + (double)(m - t0) * nb + nb2 * (nb2 + 1) + 2.0 * NB * NB;
             }
-            add_launch(p, tc ? K_UPDATE_TC : K_UPDATE, f0, kb, fl, el, 0);
+            add_launch(p, tc ? K_UPDATE_TC : (oz ? K_OZ_UPDATE : K_UPDATE), f0, kb, fl, el, 0);
         }
         f0 = p.items.size();
         fl = el = 0;
@@ -458,7 +477,7 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc) {
             fl += 2.0 * k * tri;
             el += 2.0 * tri + (double)u * k;
         }
-        add_launch(p, tc ? K_SYRK_TC : K_SYRK, f0, 0, fl, el, 0);
+        add_launch(p, tc ? K_SYRK_TC : (oz ? K_OZ_SYRK : K_SYRK), f0, 0, fl, el, 0);
     }
     // explicit inverses of the super-blocks' diagonal blocks (for the solves)
     constexpr int BPS = wd::SB / NB;  // 64-blocks per super-block
@@ -738,6 +757,10 @@ static wd_status reset_analysis(wd_handle h) {
     h->splan_lu_b = Plan();
     h->d_xs = h->d_xts = nullptr;
     h->d_xsoff = nullptr;
+    h->d_oz_sl = nullptr;
+    h->d_oz_ex = nullptr;
+    h->d_oz_soff = h->d_oz_eoff = nullptr;
+    h->oz_sl_bytes = h->oz_ex_elems = 0;
     h->xs_elems = 0;
     h->d_values_stage = nullptr;
     h->front_elems = 0;
@@ -944,7 +967,7 @@ static wd_status finish_analysis(wd_handle h, std::chrono::steady_clock::time_po
             }
         }
     }
-    build_factor_plan(S, h->fplan, false);
+    build_factor_plan(S, h->fplan, false, h->opt.fp64_tc_schur != 0);
     build_factor_plan(S, h->fplan_tc, true);
     if (host_only) {
         fill_info(h, nnzl, maxm, maxk, t0);
@@ -988,6 +1011,24 @@ static wd_status finish_analysis(wd_handle h, std::chrono::steady_clock::time_po
         const int64_t *p = nullptr;
         UP(xsoff, p);
         h->d_xsoff = const_cast<int64_t *>(p);
+    }
+    if (h->opt.fp64_tc_schur) {
+        std::vector<int64_t> so(ns), eo(ns);
+        int64_t sb = 0, eb = 0;
+        for (int s = 0; s < ns; ++s) {
+            const int64_t nblk = (sk[s] + NB - 1) / NB, srow = wd::pack_rows(skp[s] + sm[s] - sk[s]);
+            so[s] = sb;
+            eo[s] = eb;
+            sb += nblk * 8 * srow * 128;
+            eb += nblk * srow;
+        }
+        h->oz_sl_bytes = std::max<int64_t>(sb, 128);
+        h->oz_ex_elems = std::max<int64_t>(eb, 1);
+        const int64_t *p = nullptr;
+        UP(so, p);
+        h->d_oz_soff = const_cast<int64_t *>(p);
+        UP(eo, p);
+        h->d_oz_eoff = const_cast<int64_t *>(p);
     }
     {
         const int32_t *p = nullptr;
@@ -1201,6 +1242,15 @@ static void enqueue_factor_plan(wd_handle h, cudaStream_t st, bool prof) {
     ta.diag64_min_k = h->opt.diag64_min_k;
     ta.wait_limit = (uint32_t)std::max(0, h->opt.wait_limit);
     ta.gate = h->opt.test_closed_gate ? h->d_gate : nullptr;
+    wd::OzArgs oa{};
+    oa.sl = h->d_oz_sl;
+    oa.ex = h->d_oz_ex;
+    oa.soff = h->d_oz_soff;
+    oa.eoff = h->d_oz_eoff;
+    oa.dinv = reinterpret_cast<double *>(Dv);
+    oa.status = h->d_status;
+    oa.tstatus = h->d_tstatus;
+    oa.wait_limit = ta.wait_limit;
     size_t li = 0;
     for (const Launch &L : P.launches) {
         const int4 *it = P.d_items + L.off;
@@ -1219,6 +1269,13 @@ static void enqueue_factor_plan(wd_handle h, cudaStream_t st, bool prof) {
             case K_SYRK_TC:
                 wd::launch_tc_schur(d, reinterpret_cast<float *>(F), pk, it, L.count, 0, 1, ta, st);
                 break;
+            case K_OZ_SLICE:
+                wd::launch_oz_slice(d, reinterpret_cast<const double *>(F), oa, it, L.count, L.arg, st);
+                break;
+            case K_OZ_UPDATE:
+                wd::launch_oz_schur(d, reinterpret_cast<double *>(F), it, L.count, L.arg, 0, oa, st);
+                break;
+            case K_OZ_SYRK: wd::launch_oz_schur(d, reinterpret_cast<double *>(F), it, L.count, 0, 1, oa, st); break;
             case K_SBINV_DIAG:
                 wd::launch_sbinv_diag<T>(d, Dv, static_cast<T *>(h->d_xs), h->d_xsoff, it, L.count, st);
                 break;
@@ -1302,6 +1359,14 @@ extern "C" wd_status wd_factor(wd_handle h, const double *values, int values_on_
         CK(h->mem.alloc(&h->d_xts, h->xs_elems * sizeof(double)), "super-block inverse alloc");
         // padding rows stay zero forever: no kernel writes them
         CK(cudaMemsetAsync(h->d_front, 0, h->front_elems * sizeof(double), st), "front pool clear");
+    }
+    if (prec == WD_FP64 && h->opt.fp64_tc_schur && !h->d_oz_sl) {
+        CK(h->mem.alloc((void **)&h->d_oz_sl, h->oz_sl_bytes), "slice planes alloc");
+        CK(h->mem.alloc((void **)&h->d_oz_ex, h->oz_ex_elems * sizeof(int16_t)), "slice scales alloc");
+        // rows no slicing writes (padding, the window past the front) stay zero
+        CK(cudaMemsetAsync(h->d_oz_sl, 0, h->oz_sl_bytes, st), "slice planes clear");
+        CK(cudaMemsetAsync(h->d_oz_ex, 0, h->oz_ex_elems * sizeof(int16_t), st), "slice scales clear");
+        h->g_factor.reset();
     }
     if (prec == WD_MIXED && !h->d_pack) {
         CK(h->mem.alloc((void **)&h->d_pack, h->pack_total), "packed panel alloc");

@@ -47,6 +47,7 @@ void init_tc_attributes();
 void init_blocked_attributes();
 void init_tc_solve_attributes();
 void init_lu_attributes();
+void init_oz_attributes();
 inline void init_kernel_attributes() {
     init_front_attributes();
     init_solve_attributes();
@@ -54,6 +55,7 @@ inline void init_kernel_attributes() {
     init_blocked_attributes();
     init_tc_solve_attributes();
     init_lu_attributes();
+    init_oz_attributes();
 }
 
 
@@ -113,6 +115,27 @@ struct TcArgs {
 void launch_tc_schur(const DevSym &d, float *front, const unsigned char *pk, const int4 *items,
                      int count, int kb, int mode, const TcArgs &a, cudaStream_t st);
 void init_tc_attributes();
+
+// FP64 Schur updates through bf16 slices on the tensor cores (oz_schur.cu):
+// per supernode s and 64-column pivot block b, eight planes of 128-byte lines
+// (one per front row, pack_rows(mp) rows) at sl + soff[s] + ((b * 8 + q) *
+// pack_rows(mp) + row) * 128, and the row scales' exponents at ex + eoff[s] +
+// b * pack_rows(mp) + row
+struct OzArgs {
+    unsigned char *sl;
+    int16_t *ex;
+    const int64_t *soff;
+    const int64_t *eoff;
+    double *dinv;
+    status_t *status;
+    status_t *tstatus;
+    uint32_t wait_limit;
+};
+void launch_oz_slice(const DevSym &d, const double *front, const OzArgs &a, const int4 *items, int count, int kb,
+                     cudaStream_t st);
+void launch_oz_schur(const DevSym &d, double *front, const int4 *items, int count, int kb, int mode,
+                     const OzArgs &a, cudaStream_t st);
+void init_oz_attributes();
 
 // ---- values, solves and reductions (solve_kernels.cu) ---------------------
 // csr_val = values in CSR order; hi / lo (nullable): its double-float split

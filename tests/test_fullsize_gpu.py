@@ -31,10 +31,14 @@ def _full():
 
 
 def _solver(wdlib, torch, c, prec):
-    return wdlib.Solver().analyze(c["cp"], c["ri"], c["b"]).factor(torch.tensor(c["v"], device="cuda"), prec)
+    # "fp64_tc": the FP64 factorization with its Schur updates on the tensor
+    # cores (bf16 slices), held to the FP64 bar
+    opts = {"fp64_tc_schur": True} if prec == "fp64_tc" else {}
+    p = "fp64" if prec == "fp64_tc" else prec
+    return wdlib.Solver(**opts).analyze(c["cp"], c["ri"], c["b"]).factor(torch.tensor(c["v"], device="cuda"), p)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 2e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp64_tc", 1e-10), ("mixed", 2e-5)])
 def test_fullsize_factor_every_column(wdlib, cuda, prec, tol):
     """||L_gpu[:, j] - L_oracle[:, j]||_2 <= tol ||L_oracle[:, j]||_2 for all
     65,536 columns; the last supernode (the root separator) is also checked on

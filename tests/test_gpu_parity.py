@@ -390,3 +390,47 @@ def test_two_term_pattern_factor_and_solve(wdlib, cuda, dim, J, ker, nug, prec, 
     B = rhs(o.n, 16, seed=9)
     X = s.solve(B)
     assert oracle.backward_error(cp, ri, v, X, B).max() <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# FP64 factorization with the Schur updates on the tensor cores (bf16 slices,
+# exact products, FP64 combination): the FP64 bar
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", list(CASES))
+def test_factor_fp64_tensor_core_updates(wdlib, cuda, name):
+    b, cp, ri, v, o = _case(name)
+    s = wdlib.Solver(fp64_tc_schur=True).analyze(cp, ri, b)
+    s.factor(v, "fp64")
+    L = s.L_csc_like(o.Lp, o.Li)
+    Lo = o.L_values()
+    for j in range(o.n):
+        a, e = o.Lp[j], o.Lp[j + 1]
+        assert np.linalg.norm(L[a:e] - Lo[a:e]) <= 1e-10 * np.linalg.norm(Lo[a:e]), j
+    ref = o.logdet()
+    assert abs(s.logdet() - ref) <= 1e-12 * abs(ref)
+    B = rhs(o.n, 5, seed=11)
+    X = s.solve(B)
+    assert oracle.backward_error(cp, ri, v, X, B).max() <= 1e-12
+    assert s.last_solve["iterations"] == 0
+
+
+@pytest.mark.parametrize("tc", [False, True])
+def test_fp64_factor_of_a_matrix_with_large_and_small_rows(wdlib, cuda, tc):
+    """D A D with D = 2^k_i, k_i in -20..20 (exact scaling): its factor is
+    D L, L the factor of A, so D^-1 times the computed factor is held to the
+    FP64 bar against the oracle's L -- the slices' per-row scales must follow
+    the rows' sizes (an error relative to the scaled factor's columns would
+    not be a fair bar: FP64's own error in entry (i, j) scales with D_i)."""
+    b, cp, ri, v, o = _case("2d_J5")
+    rng = np.random.default_rng(3)
+    dsc = 2.0 ** rng.integers(-20, 21, size=o.n)
+    cols = np.repeat(np.arange(o.n), np.diff(cp))
+    vs = v * dsc[ri] * dsc[cols]
+    s = wdlib.Solver(fp64_tc_schur=tc).analyze(cp, ri, b).factor(vs, "fp64")
+    assert np.array_equal(s.symbolic()["perm"], o.perm)
+    dp = dsc[o.perm]                               # D in the factor's order
+    L = s.L_csc_like(o.Lp, o.Li) / dp[o.Li]
+    Lo = o.L_values()
+    for j in range(o.n):
+        a, e = o.Lp[j], o.Lp[j + 1]
+        assert np.linalg.norm(L[a:e] - Lo[a:e]) <= 1e-10 * np.linalg.norm(Lo[a:e]), j
