@@ -23,9 +23,10 @@
 // instructions (128 x 64 x 16 each) into eight TMEM accumulators of 64
 // columns (all 512 columns of the SM's tensor memory).  The epilogue reads
 // them, adds the eight terms in double-float arithmetic on the FP32 pipes
-// (exact powers of two as scales, TwoSum), and adds the result, scaled by
-// 2^(e_r + e_c), to an FP64 register accumulator with two FP64 multiply-adds;
-// after the last block C -= acc in FP64.
+// (exact powers of two as scales, TwoSum), turns the pair into two doubles
+// scaled by 2^(e_r + e_c) with integer operations on the bits, and adds them
+// to an FP64 register accumulator (two FP64 additions: GB300's FP64 pipe is
+// the scarce one); after the last block C -= acc in FP64.
 //
 // One CTA per 128 x 64 output tile (the tiles of the SIMT FP64 kernel):
 //   warp 0: producer (bulk copies of the 8 + 8 slice planes of a block)
@@ -77,6 +78,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // 2^e as a double (0 below the normal range)
 __device__ __forceinline__ double pow2(int e) {
     return e < -1022 ? 0.0 : __longlong_as_double((long long)(1023 + min(e, 1023)) << 52);
+}
+
+// f 2^e as a double, built from f's bits on the integer pipes (no FP64
+// conversion or multiply): zero and FP32 subnormals give 0, so do results
+// below the FP64 normal range
+__device__ __forceinline__ double f2d_scaled(float f, int e) {
+    const uint32_t u = __float_as_uint(f);
+    const int ex = (int)((u >> 23) & 0xFFu) - 127 + 1023 + e;
+    const bool zero = ((u >> 23) & 0xFFu) == 0u || ex < 1;
+    const uint64_t bits = ((uint64_t)(u >> 31) << 63) | ((uint64_t)min(ex, 2046) << 52) |
+                          ((uint64_t)(u & 0x7FFFFFu) << 29);
+    return zero ? 0.0 : __longlong_as_double((long long)bits);
 }
 
 __device__ __forceinline__ void two_sum(float &h, float &l, float t) {
@@ -261,9 +274,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_schur_kernel(DevSym d, doubl
                     float h = D[NACC - 1][cc] * 0x1p-63f, l = 0.0f;
 #pragma unroll
                     for (int dd = NACC - 2; dd >= 0; --dd) two_sum(h, l, D[dd][cc] * __int_as_float((127 - 7 * (dd + 2)) << 23));
-                    const double sc = pow2(er + Eb[cb + 8 * g + cc]);
-                    acc[8 * g + cc] = fma((double)h, sc, acc[8 * g + cc]);
-                    acc[8 * g + cc] = fma((double)l, sc, acc[8 * g + cc]);
+                    const int esc = er + Eb[cb + 8 * g + cc];
+                    acc[8 * g + cc] += f2d_scaled(h, esc);
+                    acc[8 * g + cc] += f2d_scaled(l, esc);
                 }
             }
             tc::tc_fence_before();
