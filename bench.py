@@ -111,6 +111,9 @@ def parse():
     p.add_argument("--diag64-min-k", type=int, default=None,
                    help="mixed precision: factor the diagonal blocks of supernodes at least this wide "
                         "in FP64 (library default if unset)")
+    p.add_argument("--step-launches", action="store_true",
+                   help="factor the pivot columns with a (panel, update) launch pair per 64-column block "
+                        "instead of one launch per level")
     p.add_argument("--theta-steps", type=int, default=150,
                    help="theta workload: time steps per factorization")
     p.add_argument("--nrhs", type=int, default=None)
@@ -315,6 +318,8 @@ def solver_opts(args, **kw):
         kw["relax_pct"] = args.relax_pct
     if getattr(args, "diag64_min_k", None) is not None:
         kw["diag64_min_k"] = args.diag64_min_k
+    if getattr(args, "step_launches", False):
+        kw["step_launches"] = True
     return kw
 
 
@@ -325,7 +330,7 @@ def roofline(top, nr, key):
     peaks = load_peaks()
     name = top["name"]
     sec = top["ms"] / 1e3
-    if name.startswith("tc_schur"):
+    if name.startswith(("tc_schur", "tc_chain")):
         # tcgen05 kind::tf32, three MMAs per product (3xTF32): useful flops
         # against the tf32 rate derived from the measured (sustained) bf16 peak
         bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
@@ -335,7 +340,11 @@ def roofline(top, nr, key):
                 "traffic": measured_traffic(key, name), "kernel": name,
                 "peak_source": ("measured bf16 sustained %.1f x nominal tf32/bf16 1.1/2.25" % bf16)
                 if "bf16_tflops_sustained" in peaks else "fallback 1700 x nominal tf32/bf16 1.1/2.25",
-                "work": "2 k flops per updated lower entry (the 3xTF32 split's extra MMAs count against it)"}
+                "work": ("2 k flops per updated lower entry (the 3xTF32 split's extra MMAs count against it)"
+                         if name.startswith("tc_schur") else
+                         "sum over 64-column pivot blocks of the pivot-column update (2 nb per updated lower "
+                         "entry), the panel (nb^2 per row below) and the diagonal block (2 nb^3 / 3); the "
+                         "3xTF32 split's extra MMAs count against it")}
     if name in ("spmv_residual_df", "spmv_residual_df32"):
         # double-float multiply-add: 12 FP32 instructions per (entry, right-hand
         # side) term (4 for the product, 6 for TwoSum, 2 to collect the error

@@ -98,6 +98,12 @@ typedef struct {
                                within FP64's own bound for these sums); the
                                panels, diagonal blocks and solves stay FP64.
                                0: FP64 on the SIMT pipes (0)                 */
+    int32_t step_launches;  /* WD_MIXED: 1 factors each level's pivot columns
+                               with two launches per 64-column pivot block
+                               (panel, then update); 0: one launch per level
+                               whose CTAs take the blocks' tasks in dependency
+                               order and wait (bounded) for what they read (0).
+                               diag64_min_k > 0 implies 1                    */
 } wd_options;
 
 /* Optional geometry for the nested-dissection ordering.  Per vertex (basis

@@ -41,7 +41,8 @@ class WdOptions(ctypes.Structure):
                 ("symbolic_only", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("diag64_min_k", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
                 ("test_closed_gate", ctypes.c_int32), ("test_fail_alloc", ctypes.c_int32),
-                ("solve_simt", ctypes.c_int32), ("fp64_tc_schur", ctypes.c_int32)]
+                ("solve_simt", ctypes.c_int32), ("fp64_tc_schur", ctypes.c_int32),
+                ("step_launches", ctypes.c_int32)]
 
 
 class WdGeometry(ctypes.Structure):
@@ -170,7 +171,7 @@ class Solver:
                  relax_pct=DEFAULTS["relax_pct"], ir_max_iter=10, ir_tol=1e-12,
                  symbolic_only=False, profile=False, use_graphs=True, diag64_min_k=None,
                  wait_limit=0, test_closed_gate=False, test_fail_alloc=0, solve_simt=False,
-                 fp64_tc_schur=False):
+                 fp64_tc_schur=False, step_launches=False):
         self._lib = load()
         o = WdOptions()
         self._lib.wd_default_options(ctypes.byref(o))
@@ -186,6 +187,7 @@ class Solver:
         o.test_fail_alloc = test_fail_alloc
         o.solve_simt = 1 if solve_simt else 0
         o.fp64_tc_schur = 1 if fp64_tc_schur else 0
+        o.step_launches = 1 if step_launches else 0
         self._h = ctypes.c_void_p()
         self._check(self._lib.wd_create(ctypes.byref(self._h), ctypes.byref(o)))
         self.n = None

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwd.so")
 SOURCES = ["csrc/symbolic.cpp", "csrc/api.cpp", "csrc/front_kernels.cu", "csrc/solve_kernels.cu",
-           "csrc/tc_schur.cu", "csrc/selinv.cu",
+           "csrc/tc_schur.cu", "csrc/tc_chain.cu", "csrc/selinv.cu",
            "csrc/noalloc.cu", "csrc/batch.cu", "csrc/solve_blocked.cu", "csrc/tc_solve.cu",
            "csrc/lu.cu", "csrc/oz_schur.cu"]
 HEADERS = ["csrc/symbolic.h", "csrc/engine.h", "csrc/dev_common.cuh", "csrc/tc_common.cuh",

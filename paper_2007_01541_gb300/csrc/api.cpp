@@ -32,7 +32,8 @@ enum LaunchKind {
     K_APPLY_L,
     K_LU_INIT, K_LU_DIAG, K_LU_PANEL, K_LU_UPDATE,               // LU factor
     K_LU_GATHER, K_LU_FWD, K_LU_BWD,                             // LU substitutions
-    K_OZ_SLICE, K_OZ_UPDATE, K_OZ_SYRK                           // FP64 updates on the tensor cores
+    K_OZ_SLICE, K_OZ_UPDATE, K_OZ_SYRK,                          // FP64 updates on the tensor cores
+    K_CHAIN_TC                                                   // pivot columns of a level, one launch
 };
 
 struct Launch {
@@ -52,7 +53,7 @@ const char *kind_name(int k) {
                                   "fwd_bupdate", "bwd_reduce", "bwd_finish", "bwd_xapply",
                                   "apply_L", "lu_init", "lu_diag", "lu_panel", "lu_update",
                                   "lu_gather", "lu_fwd", "lu_bwd", "oz_slice", "oz_schur_update",
-                                  "oz_schur_syrk"};
+                                  "oz_schur_syrk", "tc_chain"};
     return names[k];
 }
 
@@ -151,6 +152,14 @@ struct wd_ctx {
     size_t xs_elems = 0;
     unsigned char *d_pack = nullptr;  // packed tf32 panel lines (FP32 fronts)
     int64_t pack_total = 0;
+    // one launch per level for the FP32 fronts' pivot columns: dependency
+    // words of every supernode (offsets chain_flagoff), then one task counter
+    // per level and the launch-wide abort word; zeroed before each factor
+    bool chain = false;
+    unsigned *d_chain_flags = nullptr;
+    int64_t *d_chain_flagoff = nullptr;
+    unsigned char *d_chain_lpack = nullptr;   // L11^-1 blocks as tensor-core operands (32 KB each)
+    int64_t chain_words = 0, chain_ctr = 0;
     status_t *d_tstatus = nullptr;    // nonzero: a bounded device wait expired
     unsigned *d_gate = nullptr;       // a device word that stays zero (wd_options.test_closed_gate)
     cudaStream_t cap_stream = nullptr;
@@ -286,7 +295,8 @@ wd_status wd_create(wd_handle *out, const wd_options *opt) {
     if (opt) h->opt = *opt;
     if (h->opt.nd_leaf < 1 || h->opt.relax_k < 0 || h->opt.relax_pct < 0 || h->opt.ir_max_iter < 0 ||
         !(h->opt.ir_tol > 0) || h->opt.diag64_min_k < 0 || h->opt.wait_limit < 0 ||
-        h->opt.test_fail_alloc < 0 || h->opt.fp64_tc_schur < 0 || h->opt.fp64_tc_schur > 1) {
+        h->opt.test_fail_alloc < 0 || h->opt.fp64_tc_schur < 0 || h->opt.fp64_tc_schur > 1 ||
+        h->opt.step_launches < 0 || h->opt.step_launches > 1) {
         delete h;
         return WD_ERR_INVALID_ARG;
     }
@@ -375,7 +385,10 @@ static int front_order(const wd::Symbolic &S, int s) { return kpad(S.k(s)) + S.m
 
 // oz (FP64 fronts): the Schur updates through bf16 slices on the tensor
 // cores, each panel launch followed by the slicing of its rows.
-static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc, bool oz = false) {
+// chain (FP32 fronts on the tensor cores): the pivot columns of a level in
+// one launch of dependency-ordered tasks (tc_chain.cu) instead of the diagonal
+// block launch and a (panel, update) launch pair per pivot block.
+static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc, bool oz = false, bool chain = false) {
     const int SCHUR_BM = tc ? wd::TC_BM : wd::SCHUR_BM;
     const int SCHUR_BN = tc ? wd::TC_BN : wd::SCHUR_BN;
     p.items.clear();
@@ -403,6 +416,37 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc, bool oz =
         int kmax = 0;
         double fl = 0;
         for (int i = b; i < e; ++i) kmax = std::max(kmax, S.k(S.level_nodes[i]));
+        if (tc && chain) {
+            // tasks (s, c, ti): column block c, row tile ti (128 rows from row
+            // 64 c); in order of c, then ti, then front, so that every task
+            // depends only on earlier ones
+            f0 = p.items.size();
+            fl = el = 0;
+            for (int cbk = 0; cbk * NB < kmax; ++cbk) {
+                int tmax = 0;
+                for (int i = b; i < e; ++i) {
+                    const int s = S.level_nodes[i];
+                    if (S.k(s) > cbk * NB) tmax = std::max(tmax, (front_order(S, s) - cbk * NB + 127) / 128);
+                }
+                for (int ti = 0; ti < tmax; ++ti)
+                    for (int i = b; i < e; ++i) {
+                        const int s = S.level_nodes[i];
+                        if (S.k(s) > cbk * NB && cbk * NB + ti * 128 < front_order(S, s))
+                            p.items.push_back({s, cbk, ti, 0});
+                    }
+            }
+            for (int i = b; i < e; ++i) {
+                const int s = S.level_nodes[i], k = S.k(s), m = S.m(s);
+                for (int kb = 0; kb < k; kb += NB) {
+                    const int nb = std::min(NB, k - kb), t0 = kb + nb;
+                    const double cw = k - t0, below = m - k;
+                    const double ent = cw * (cw + 1) / 2 + below * cw;
+                    fl += diag_flops(nb) + (double)(m - t0) * nb * nb + 2.0 * nb * ent;
+                    el += 2.0 * (m - kb) * nb;
+                }
+            }
+            add_launch(p, K_CHAIN_TC, f0, l, fl, el, 0);
+        } else {
         // the first diagonal block of every front of the level
         f0 = p.items.size();
         fl = el = 0;
@@ -461,6 +505,7 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc, bool oz =
                 el += 2.0 * ent + (double)(m - t0) * nb + nb2 * (nb2 + 1) + 2.0 * NB * NB;
             }
             add_launch(p, tc ? K_UPDATE_TC : (oz ? K_OZ_UPDATE : K_UPDATE), f0, kb, fl, el, 0);
+        }
         }
         f0 = p.items.size();
         fl = el = 0;
@@ -739,6 +784,10 @@ static wd_status reset_analysis(wd_handle h) {
     h->fplan = Plan();
     h->fplan_tc = Plan();
     h->d_pack = nullptr;
+    h->d_chain_flags = nullptr;
+    h->d_chain_flagoff = nullptr;
+    h->d_chain_lpack = nullptr;
+    h->chain_words = h->chain_ctr = 0;
     h->splan = Plan();
     h->aplan = Plan();
     h->splan_nrhs = h->aplan_nrhs = -1;
@@ -968,7 +1017,18 @@ static wd_status finish_analysis(wd_handle h, std::chrono::steady_clock::time_po
         }
     }
     build_factor_plan(S, h->fplan, false, h->opt.fp64_tc_schur != 0);
-    build_factor_plan(S, h->fplan_tc, true);
+    h->chain = !h->opt.step_launches && h->opt.diag64_min_k <= 0;
+    build_factor_plan(S, h->fplan_tc, true, false, h->chain);
+    std::vector<int64_t> chain_off(ns);
+    {
+        int64_t cw = 0;
+        for (int s = 0; s < ns; ++s) {
+            chain_off[s] = cw;
+            cw += wd::chain_flag_words(sk[s], skp[s] + sm[s] - sk[s]);
+        }
+        h->chain_ctr = cw;
+        h->chain_words = cw + S.nlevels + 1;
+    }
     if (host_only) {
         fill_info(h, nnzl, maxm, maxk, t0);
         h->analyzed = true;
@@ -1007,6 +1067,13 @@ static wd_status finish_analysis(wd_handle h, std::chrono::steady_clock::time_po
     UP(dioff, d.dinvoff);
     UP(pkoff, d.pkoff);
     UP(S.perm, d.perm);
+    {
+        const int64_t *p = nullptr;
+        UP(chain_off, p);
+        h->d_chain_flagoff = const_cast<int64_t *>(p);
+        CK(h->mem.alloc((void **)&h->d_chain_flags, h->chain_words * sizeof(unsigned)), "dependency words alloc");
+        CK(h->mem.alloc((void **)&h->d_chain_lpack, (h->dinv_elems / (NB * NB)) * (size_t)32768), "operand alloc");
+    }
     {
         const int64_t *p = nullptr;
         UP(xsoff, p);
@@ -1251,11 +1318,27 @@ static void enqueue_factor_plan(wd_handle h, cudaStream_t st, bool prof) {
     oa.status = h->d_status;
     oa.tstatus = h->d_tstatus;
     oa.wait_limit = ta.wait_limit;
+    wd::ChainArgs ca{};
+    ca.dinv = reinterpret_cast<float *>(Dv);
+    ca.lpack = h->d_chain_lpack;
+    ca.status = h->d_status;
+    ca.tstatus = h->d_tstatus;
+    ca.wait_limit = ta.wait_limit;
+    ca.gate = ta.gate;
+    ca.flags = h->d_chain_flags;
+    ca.flagoff = h->d_chain_flagoff;
+    ca.counter = h->d_chain_flags + h->chain_ctr;
+    ca.gabort = h->d_chain_flags + h->chain_words - 1;
+    if (fp32 && h->chain)
+        cudaMemsetAsync(h->d_chain_flags, 0, h->chain_words * sizeof(unsigned), st);
     size_t li = 0;
     for (const Launch &L : P.launches) {
         const int4 *it = P.d_items + L.off;
         if (prof) record_event(h->prof_ev[2 * li], st);
         switch (L.kind) {
+            case K_CHAIN_TC:
+                wd::launch_tc_chain(d, reinterpret_cast<float *>(F), pk, it, L.count, L.arg, ca, st);
+                break;
             case K_INIT: wd::launch_front_init<T>(d, F, it, L.count, st); break;
             case K_DIAG:
                 wd::launch_diag_factor<T>(d, F, Dv, it, L.count, h->opt.diag64_min_k, h->d_status, st);

@@ -48,6 +48,7 @@ void init_blocked_attributes();
 void init_tc_solve_attributes();
 void init_lu_attributes();
 void init_oz_attributes();
+void init_chain_attributes();
 inline void init_kernel_attributes() {
     init_front_attributes();
     init_solve_attributes();
@@ -56,6 +57,7 @@ inline void init_kernel_attributes() {
     init_tc_solve_attributes();
     init_lu_attributes();
     init_oz_attributes();
+    init_chain_attributes();
 }
 
 
@@ -115,6 +117,36 @@ struct TcArgs {
 void launch_tc_schur(const DevSym &d, float *front, const unsigned char *pk, const int4 *items,
                      int count, int kb, int mode, const TcArgs &a, cudaStream_t st);
 void init_tc_attributes();
+
+// Pivot columns of the FP32 fronts of one level in one launch (tc_chain.cu):
+// items (s, c, ti) in dependency order (column block c, then row tile ti of
+// 128 rows from row 64c, then front); each task forms its tile of the pivot
+// columns with a tensor-core product over all earlier column blocks, the
+// ti = 0 task factors the diagonal block (L11, L11^-1 into dinv) and every
+// task writes its panel rows (front and packed tf32 lines).  Dependency
+// words: flags + flagoff[s], ready[j * nrb + rb] for row block rb of column
+// block j (nrb = ceil(mp / 64) + 1), then diag[j]; counter[level] hands out
+// the tasks; all of them zero before the launch.  Bounded waits as in the
+// Schur kernel; *gabort != 0 after a timeout in any CTA.
+struct ChainArgs {
+    float *dinv;
+    unsigned char *lpack;   // L11^-1 of every diagonal block as a tf32 hi / lo operand (32 KB each,
+                            // block c of supernode s at (dinvoff[s] / NB^2 + c) x 32 KB)
+    status_t *status;
+    status_t *tstatus;
+    uint32_t wait_limit;
+    const unsigned *gate;
+    unsigned *flags;
+    const int64_t *flagoff;
+    unsigned *counter;
+    unsigned *gabort;
+};
+__host__ __device__ inline int64_t chain_flag_words(int k, int mp) {
+    const int64_t ncb = (k + NB - 1) / NB, nrb = (mp + NB - 1) / NB + 1;
+    return ncb * nrb + ncb;
+}
+void launch_tc_chain(const DevSym &d, float *front, unsigned char *pk, const int4 *items, int count, int level,
+                     const ChainArgs &a, cudaStream_t st);
 
 // FP64 Schur updates through bf16 slices on the tensor cores (oz_schur.cu):
 // per supernode s and 64-column pivot block b, eight planes of 128-byte lines

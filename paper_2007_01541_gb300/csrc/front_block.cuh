@@ -26,45 +26,18 @@ namespace blk {
 constexpr int SB = 16;
 
 // pivot d > 0 -> (sqrt(d), 1/sqrt(d)).  FP64: correctly rounded square root
-// and division.  FP32 (the refined mixed-precision path): the hardware
-// reciprocal square root, which keeps the serial pivot chain short; its few
-// ulps of error are far below what iterative refinement removes.
+// and division.  FP32 (the refined mixed-precision path): the hardware's
+// approximate reciprocal square root (rsqrt.approx, pivots are never
+// subnormal here), which keeps the serial pivot chain short; its few ulps of
+// error are far below what iterative refinement removes.
 __device__ __forceinline__ void pivot_root(double d, double &s, double &is) {
     s = sqrt(d);
     is = 1.0 / s;
 }
 __device__ __forceinline__ void pivot_root(float d, float &s, float &is) {
-    is = rsqrtf(d);
+    asm("rsqrt.approx.ftz.f32 %0, %1;\n" : "=f"(is) : "f"(d));
     s = d * is;
 }
-
-// Pivot C of a 16 x 16 Cholesky held by one warp, one row per lane (v),
-// then pivots C+1, ...: compile-time recursion, so every register index is a
-// constant.  The first pivot that is not positive is kept in `bad` (the caller
-// reports it), so the unrolled chain has no branch.
-template <class T, int C>
-struct WarpChol {
-    static __device__ __forceinline__ void step(T (&v)[SB], T &myinv, int lane, int w, int &bad) {
-        T dc = __shfl_sync(0xffffffffu, v[C], C);
-        const bool fail = C < w && !(dc > T(0));
-        bad = (fail && bad < 0) ? C : bad;
-        dc = (fail || C >= w) ? T(1) : dc;
-        T sc, ic;
-        pivot_root(dc, sc, ic);
-        v[C] = lane == C ? sc : (lane > C ? v[C] * ic : v[C]);
-        myinv = lane == C ? ic : myinv;
-#pragma unroll
-        for (int c2 = C + 1; c2 < SB; ++c2) {
-            const T lc = __shfl_sync(0xffffffffu, v[C], c2);
-            if (lane >= c2) v[c2] -= v[C] * lc;
-        }
-        WarpChol<T, C + 1>::step(v, myinv, lane, w, bad);
-    }
-};
-template <class T>
-struct WarpChol<T, SB> {
-    static __device__ __forceinline__ void step(T (&)[SB], T &, int, int, int &) {}
-};
 
 // four consecutive shared-memory elements (16-byte aligned for float, two
 // 16-byte halves for double)
@@ -77,16 +50,56 @@ __device__ __forceinline__ void load4(double (&v)[4], const double *p) {
     v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
 }
 
+// Pivot C of a 16 x 16 Cholesky held by one warp, one row per lane (v),
+// then pivots C+1, ...: compile-time recursion, so every register index is a
+// constant.  dc is pivot C's value, broadcast.  The first pivot that is not
+// positive is kept in `bad` (the caller reports it) and replaced by 1, so the
+// unrolled chain has no branch.  The next pivot is updated and broadcast
+// before the rest of the column (lane C+1 holds both of its factors), and the
+// column itself goes to every lane through shared memory (col, 16 elements,
+// 16-byte aligned, private to the warp): one store and four vector loads
+// instead of fifteen shuffles.
+template <class T, int C>
+struct WarpChol {
+    static __device__ __forceinline__ void step(T (&v)[SB], T &myinv, int lane, int w, int &bad, T dc, T *col) {
+        bad = (C < w && !(dc > T(0)) && bad < 0) ? C : bad;
+        dc = (C < w && dc > T(0)) ? dc : T(1);
+        T sc, ic;
+        pivot_root(dc, sc, ic);
+        v[C] = lane == C ? sc : (lane > C ? v[C] * ic : v[C]);
+        myinv = lane == C ? ic : myinv;
+        T dn = T(0);
+        if (C + 1 < SB) dn = __shfl_sync(0xffffffffu, v[C + 1 < SB ? C + 1 : C] - v[C] * v[C], C + 1 < SB ? C + 1 : C);
+        if (lane < SB) col[lane] = v[C];
+        __syncwarp();
+#pragma unroll
+        for (int q = (C + 1) / 4 * 4; q < SB; q += 4) {
+            T t[4];
+            load4(t, col + q);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (q + u > C && lane >= q + u) v[q + u] -= v[C] * t[u];
+        }
+        __syncwarp();
+        WarpChol<T, C + 1>::step(v, myinv, lane, w, bad, dn, col);
+    }
+};
+template <class T>
+struct WarpChol<T, SB> {
+    static __device__ __forceinline__ void step(T (&)[SB], T &, int, int, int &, T, T *) {}
+};
+
 // Shared memory of the block factorization (element offsets, in TC): the
 // factor A[NB][NB + 1]; the inverse stored transposed, XT[c * XLD + r] =
 // Linv(r, c), with 16-byte aligned rows (XLD = NB + 4) so that four
-// consecutive entries are one vector load; the reciprocal pivots.  The
-// strictly lower 16 x 16 blocks of XT (Linv's zero upper part) hold the
-// products W(i, k).
+// consecutive entries are one vector load; the reciprocal pivots; the warp
+// Cholesky's column buffer.  The strictly lower 16 x 16 blocks of XT (Linv's
+// zero upper part) hold the products W(i, k).
 constexpr int XLD = NB + 4;
 constexpr int BP_XT = NB * (NB + 1);
 constexpr int BP_INVD = BP_XT + NB * XLD;
-constexpr int BP_ELEMS = BP_INVD + NB;
+constexpr int BP_COL = BP_INVD + NB;      // the pivot column broadcast of the warp Cholesky
+constexpr int BP_ELEMS = BP_COL + SB;
 template <class TC>
 constexpr size_t block_smem_bytes() { return sizeof(TC) * BP_ELEMS; }
 
@@ -118,6 +131,9 @@ __device__ void block_load(const TF *F, int ld, int nb, TC *smem) {
     __syncthreads();
 }
 
+template <class TC, int NT>
+__device__ void block_inverse(int nb, const TC (*A)[NB + 1], TC *XT, const TC *invd);
+
 // Factors the block that block_load brought in, leaving L in A and Linv in
 // XT (visible to the whole block when it returns).  Threads beyond the first
 // 256 take part in the barriers and the strided loops only.
@@ -136,7 +152,7 @@ __device__ void block_potrf_inv(int nb, int64_t gcol0, status_t *status, TC *sme
 #pragma unroll 16
             for (int c = 0; c < SB; ++c) v[c] = (lane < w && c <= lane) ? A[jb + lane][jb + c] : TC(0);
             int bad = -1;
-            WarpChol<TC, 0>::step(v, myinv, lane, w, bad);
+            WarpChol<TC, 0>::step(v, myinv, lane, w, bad, __shfl_sync(0xffffffffu, v[0], 0), smem + BP_COL);
             if (bad >= 0 && lane == 0) atomicMin(status, (status_t)(gcol0 + jb + bad));
             if (lane < w) {
 #pragma unroll 16
@@ -200,6 +216,16 @@ __device__ void block_potrf_inv(int nb, int64_t gcol0, status_t *status, TC *sme
         }
         __syncthreads();
     }
+    block_inverse<TC, NT>(nb, A, XT, invd);
+}
+
+// L11^-1 of the factor in A (rows and columns [0, nb)) into XT (XT[c * XLD +
+// r] = Linv(r, c); XT zero on entry), from the reciprocal pivots invd.  All
+// NT >= 256 threads take part; the result is visible to the whole block on
+// return.
+template <class TC, int NT>
+__device__ void block_inverse(int nb, const TC (*A)[NB + 1], TC *XT, const TC *invd) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // X(i, i): the diagonal 16 x 16 inverses, one warp each, one column per lane
     const int nsb = (nb + SB - 1) / SB;
     if (warp < nsb && lane < SB) {

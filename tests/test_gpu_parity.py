@@ -226,13 +226,16 @@ def test_profiled_and_direct_launches(wdlib, cuda, graphs):
     assert s.launch_count() > 0
 
 
+@pytest.mark.parametrize("step_launches", [False, True])
 @pytest.mark.parametrize("name", ["1d_J10", "2d_J6", "2d_J7_exp"])
-def test_factor_mixed_entries(wdlib, cuda, name):
+def test_factor_mixed_entries(wdlib, cuda, name, step_launches):
     """FP32 fronts with tensor-core (3xTF32) Schur updates: every column of L
     within 2e-5 of the FP64 oracle (relative 2-norm), amalgamation zeros
-    exactly 0 in the 1D case."""
+    exactly 0 in the 1D case.  Both schedules of the pivot columns: one
+    launch per level of dependency-ordered tasks (the default), and a
+    (panel, update) launch pair per 64-column pivot block."""
     b, cp, ri, v, o = _case(name)
-    s = wdlib.Solver().analyze(cp, ri, b)
+    s = wdlib.Solver(step_launches=step_launches).analyze(cp, ri, b)
     s.factor(v, "mixed")
     L = s.L_csc_like(o.Lp, o.Li)
     Lo = o.L_values()
