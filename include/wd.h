@@ -353,6 +353,41 @@ wd_status wd_solve_lu(wd_handle h, double *B, int64_t nrhs, int64_t ldb, int B_o
    or -1), from the LU factor.  Synchronous. */
 wd_status wd_logdet_lu(wd_handle h, double *logabs, int32_t *sign);
 
+/* Schedule of the mixed-precision factorization's pivot columns, one flag per
+   elimination-tree level (info.nlevels, deepest level first): 0 = one launch
+   of dependency-ordered tasks for the level, 1 = a (panel, update) launch
+   pair per 64-column pivot block.  Both compute P A P^T = L L^T (Section 4)
+   with the same arithmetic; the choice only changes the time, and a tuner
+   picks it by measurement.  Set after wd_analyze (which resets every flag
+   to 0); takes effect at the next wd_factor.  With wd_options.step_launches
+   = 1 or diag64_min_k > 0 every level uses launch pairs and
+   wd_get_level_schedule reports 1 for all.  WD_ERR_INVALID_ARG for a wrong
+   count or a flag other than 0 / 1; synchronous. */
+wd_status wd_set_level_schedule(wd_handle h, const int8_t *step, int32_t nlevels);
+wd_status wd_get_level_schedule(wd_handle h, int8_t *step, int32_t nlevels);
+
+/* LDL^T without pivoting of a SYMMETRIC matrix that need not be positive
+   definite: P A P^T = L D L^T, L unit lower triangular on the analyzed
+   pattern, D diagonal.  The paper factors the compressed matrix by a Cholesky
+   decomposition or, more generally, an LU decomposition on the same ordering
+   (Introduction; Section 4); for a symmetric matrix the LU decomposition
+   without pivoting is L (D L^T), so this runs the LU factorization of
+   wd_factor_lu on the values given once (lower CSC, nnz doubles, host or
+   device as on_device) and keeps U = D L^T.  FP64.  A zero pivot gives
+   WD_ERR_NOT_SPD with its column (permuted order); a negative pivot does
+   not stop it.  Solve with wd_solve_lu, log |det A| and its sign with
+   wd_logdet_lu, the inertia with wd_inertia, the factors with wd_export_LU
+   (L, and D on the diagonal of U^T).  Replaces any other factor of the
+   handle.  Synchronous. */
+wd_status wd_factor_ldlt(wd_handle h, const double *values, int on_device, void *stream);
+
+/* Inertia of A from the pivots of the last wd_factor_ldlt (Sylvester's law:
+   the numbers of positive and negative entries of D are those of A's
+   eigenvalues; no pivot is zero after a successful factorization).  Host
+   outputs, each may be NULL.  WD_ERR_STATE without an LDL^T factor.
+   Synchronous. */
+wd_status wd_inertia(wd_handle h, int64_t *npos, int64_t *nneg);
+
 /* The LU factor as two host arrays of info.nnz_L_stored doubles each, in the
    layout of wd_export_L (per supernode an m_s x k_s panel, column-major, rows
    as in super_rows): lpanels holds L (unit diagonal, zero above it),

@@ -82,6 +82,13 @@ def _load():
             lib.or_solve_lu.argtypes = [ctypes.c_void_p, _f64p, ctypes.c_int64, ctypes.c_int64]
             lib.or_logdet_lu.restype = ctypes.c_double
             lib.or_logdet_lu.argtypes = [ctypes.c_void_p, _i32p]
+            lib.or_factor_ldlt.restype = ctypes.c_int64
+            lib.or_factor_ldlt.argtypes = [ctypes.c_void_p, _f64p]
+            lib.or_get_ldlt.argtypes = [ctypes.c_void_p, _f64p, _f64p]
+            lib.or_solve_ldlt.restype = ctypes.c_int
+            lib.or_solve_ldlt.argtypes = [ctypes.c_void_p, _f64p, ctypes.c_int64, ctypes.c_int64]
+            lib.or_logdet_ldlt.restype = ctypes.c_double
+            lib.or_logdet_ldlt.argtypes = [ctypes.c_void_p, _i32p, ctypes.POINTER(ctypes.c_int64)]
             lib.or_logdet.restype = ctypes.c_double
             lib.or_logdet.argtypes = [ctypes.c_void_p]
             lib.or_apply_L.restype = ctypes.c_int
@@ -230,6 +237,37 @@ class Oracle:
         sg = np.zeros(1, np.int32)
         v = float(self._lib.or_logdet_lu(self._ctx, _p(sg, _i32p)))
         return v, int(sg[0])
+
+    # -- LDL^T without pivoting (symmetric, possibly indefinite) ---------------
+    def factor_ldlt(self, values) -> int:
+        """P A P^T = L D L^T, L unit lower triangular, D diagonal, no
+        pivoting.  Returns 0, or -(j+1) for the first zero pivot (permuted
+        order)."""
+        v = np.ascontiguousarray(values, np.float64)
+        return int(self._lib.or_factor_ldlt(self._ctx, _p(v, _f64p)))
+
+    def ldlt_values(self):
+        """(L on the pattern of L (Lp, Li) with its unit diagonal, d (n))"""
+        L = np.empty(self.nnzL, np.float64)
+        d = np.empty(self.n, np.float64)
+        self._lib.or_get_ldlt(self._ctx, _p(L, _f64p), _p(d, _f64p))
+        return L, d
+
+    def solve_ldlt(self, B) -> np.ndarray:
+        X = np.array(B, dtype=np.float64, order="F", copy=True)
+        if X.ndim == 1:
+            X = X[:, None]
+        if self._lib.or_solve_ldlt(self._ctx, _p(X, _f64p), X.shape[1], self.n):
+            raise RuntimeError("not LDL^T-factored")
+        return X
+
+    def logdet_ldlt(self):
+        """(log |det A|, sign of det A, number of negative pivots = number of
+        negative eigenvalues of A)"""
+        sg = np.zeros(1, np.int32)
+        neg = ctypes.c_int64(0)
+        v = float(self._lib.or_logdet_ldlt(self._ctx, _p(sg, _i32p), ctypes.byref(neg)))
+        return v, int(sg[0]), int(neg.value)
 
     def L_values(self) -> np.ndarray:
         x = np.empty(self.nnzL, np.float64)

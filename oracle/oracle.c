@@ -63,6 +63,10 @@ typedef struct or_ctx {
        transposed (column j holds row j of U) in Uux, both on L's pattern */
     double *Lux, *Uux;
     int lu_factored;
+    /* LDL^T without pivoting (or_factor_ldlt): L with unit diagonal on L's
+       pattern, d_j stored in place of L's diagonal entry */
+    double *Ldx;
+    int ldlt_factored;
 } or_ctx;
 
 or_ctx *or_create(void) { return (or_ctx *)calloc(1, sizeof(or_ctx)); }
@@ -80,8 +84,15 @@ static void free_lu(or_ctx *c) {
     c->lu_factored = 0;
 }
 
+static void free_ldlt(or_ctx *c) {
+    free(c->Ldx);
+    c->Ldx = NULL;
+    c->ldlt_factored = 0;
+}
+
 static void free_all(or_ctx *c) {
     free_lu(c);
+    free_ldlt(c);
     free(c->pswap);
     free(c->perm); free(c->iperm); free(c->pcolptr); free(c->prow); free(c->psrc);
     free(c->Lp); free(c->Li); free(c->parent); free(c->colcount);
@@ -809,6 +820,123 @@ double or_logdet_lu(const or_ctx *c, int32_t *sign) {
         s = t;
     }
     *sign = sg;
+    return s + comp;
+}
+
+/* LDL^T without pivoting of a symmetric (possibly indefinite) matrix, the
+   symmetric case of the LU decomposition (Section 4: "a Cholesky
+   decomposition or an LU decomposition" on the same ordering):
+   P A P^T = L D L^T, L unit lower triangular on L's pattern, D diagonal.
+   Left-looking, column by column, as or_factor_cols but with the pivot kept
+   as d_j instead of its square root:
+     w = column j of P A P^T (rows >= j);
+     for each k < j with L_jk != 0, ascending: w_i -= L_ik d_k L_jk (i >= j);
+     d_j = w_j (zero or NaN: the first such column is reported);
+     L_ij = w_i / d_j.
+   Returns 0, or -(j+1) for the first zero pivot (permuted order). */
+int64_t or_factor_ldlt(or_ctx *c, const double *values) {
+    int64_t n = c->n;
+    free_ldlt(c);
+    int64_t nnzl = c->Lp[n];
+    c->Ldx = (double *)malloc(sizeof(double) * (size_t)(nnzl > 0 ? nnzl : 1));
+    double *w = (double *)calloc((size_t)n, sizeof(double));
+    int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int32_t *head = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *link = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *ks = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    for (int64_t j = 0; j < n; ++j) head[j] = -1;
+    int64_t status = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        for (int64_t q = c->pcolptr[j]; q < c->pcolptr[j + 1]; ++q) w[c->prow[q]] = values[c->psrc[q]];
+        int64_t nk = 0;
+        for (int32_t k = head[j]; k != -1; k = link[k]) ks[nk++] = k;
+        qsort(ks, (size_t)nk, sizeof(int32_t), cmp_int32);
+        for (int64_t t = 0; t < nk; ++t) {
+            int32_t k = ks[t];
+            int64_t p = next[k];                            /* entry (j, k) */
+            double s = c->Ldx[c->Lp[k]] * c->Ldx[p];        /* d_k L_jk */
+            for (int64_t q = p; q < c->Lp[k + 1]; ++q) w[c->Li[q]] -= c->Ldx[q] * s;
+            next[k] = p + 1;
+            if (p + 1 < c->Lp[k + 1]) {
+                int32_t r = c->Li[p + 1];
+                link[k] = head[r];
+                head[r] = k;
+            }
+        }
+        double d = w[j];
+        if (!(d != 0.0) || isnan(d)) { status = -(j + 1); break; }
+        c->Ldx[c->Lp[j]] = d;
+        w[j] = 0.0;
+        for (int64_t q = c->Lp[j] + 1; q < c->Lp[j + 1]; ++q) {
+            int32_t i = c->Li[q];
+            c->Ldx[q] = w[i] / d;
+            w[i] = 0.0;
+        }
+        next[j] = c->Lp[j] + 1;
+        if (next[j] < c->Lp[j + 1]) {
+            int32_t r = c->Li[next[j]];
+            link[j] = head[r];
+            head[r] = (int32_t)j;
+        }
+    }
+    free(w); free(next); free(head); free(link); free(ks);
+    if (status) { free_ldlt(c); return status; }
+    c->ldlt_factored = 1;
+    return 0;
+}
+
+/* L (unit diagonal stored as 1) and d on L's pattern */
+void or_get_ldlt(const or_ctx *c, double *Lx, double *d) {
+    for (int64_t j = 0; j < c->n; ++j) {
+        d[j] = c->Ldx[c->Lp[j]];
+        Lx[c->Lp[j]] = 1.0;
+        for (int64_t q = c->Lp[j] + 1; q < c->Lp[j + 1]; ++q) Lx[q] = c->Ldx[q];
+    }
+}
+
+/* B := A^-1 B with the LDL^T factors: y = L^-1 P b (column-oriented), y /= d,
+   x = P^T L^-T y (row-oriented) */
+int or_solve_ldlt(const or_ctx *c, double *B, int64_t nrhs, int64_t ldb) {
+    if (!c->ldlt_factored) return -1;
+    int64_t n = c->n;
+    double *y = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int64_t r = 0; r < nrhs; ++r) {
+        double *b = B + r * ldb;
+        for (int64_t i = 0; i < n; ++i) y[i] = b[c->perm[i]];
+        for (int64_t j = 0; j < n; ++j) {
+            double yj = y[j];
+            for (int64_t q = c->Lp[j] + 1; q < c->Lp[j + 1]; ++q) y[c->Li[q]] -= c->Ldx[q] * yj;
+        }
+        for (int64_t j = 0; j < n; ++j) y[j] /= c->Ldx[c->Lp[j]];
+        for (int64_t j = n - 1; j >= 0; --j) {
+            double s = y[j];
+            for (int64_t q = c->Lp[j] + 1; q < c->Lp[j + 1]; ++q) s -= c->Ldx[q] * y[c->Li[q]];
+            y[j] = s;
+        }
+        for (int64_t i = 0; i < n; ++i) b[c->perm[i]] = y[i];
+    }
+    free(y);
+    return 0;
+}
+
+/* log |det A| = sum_j log |d_j| (Neumaier compensated); *sign = sign of
+   det A; *nneg = number of negative d_j, which by Sylvester's law of inertia
+   is the number of negative eigenvalues of A */
+double or_logdet_ldlt(const or_ctx *c, int32_t *sign, int64_t *nneg) {
+    double s = 0.0, comp = 0.0;
+    int32_t sg = 1;
+    int64_t neg = 0;
+    for (int64_t j = 0; j < c->n; ++j) {
+        double d = c->Ldx[c->Lp[j]];
+        if (d < 0) { sg = -sg; ++neg; }
+        double v = log(fabs(d));
+        double t = s + v;
+        if (fabs(s) >= fabs(v)) comp += (s - t) + v;
+        else comp += (v - t) + s;
+        s = t;
+    }
+    *sign = sg;
+    *nneg = neg;
     return s + comp;
 }
 

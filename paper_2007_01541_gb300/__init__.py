@@ -31,7 +31,8 @@ EXPORTED = ["wd_default_options", "wd_create", "wd_destroy", "wd_analyze", "wd_s
             "wd_status_detail", "wd_status_string", "wd_kernel_stats", "wd_launch_count",
             "wd_selinv", "wd_sym_pattern_outer", "wd_value_gradient", "wd_export_L_noalloc",
             "wd_analyze_batch", "wd_logdet_batch", "wd_backward_error", "wd_theta_step", "wd_set_mass",
-            "wd_factor_lu", "wd_solve_lu", "wd_logdet_lu", "wd_export_LU"]
+            "wd_factor_lu", "wd_solve_lu", "wd_logdet_lu", "wd_export_LU", "wd_factor_ldlt", "wd_inertia",
+            "wd_set_level_schedule", "wd_get_level_schedule"]
 
 
 class WdOptions(ctypes.Structure):
@@ -117,6 +118,10 @@ def load():
         lib.wd_solve_lu.argtypes = [vp, vp, i64, i64, ctypes.c_int, vp]
         lib.wd_logdet_lu.argtypes = [vp, ctypes.POINTER(f64), ctypes.POINTER(i32)]
         lib.wd_export_LU.argtypes = [vp, vp, vp]
+        lib.wd_factor_ldlt.argtypes = [vp, vp, ctypes.c_int, vp]
+        lib.wd_set_level_schedule.argtypes = [vp, vp, i32]
+        lib.wd_get_level_schedule.argtypes = [vp, vp, i32]
+        lib.wd_inertia.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         lib.wd_status_detail.argtypes = [vp, ctypes.POINTER(i64), ctypes.c_char_p, ctypes.c_size_t]
         lib.wd_kernel_stats.argtypes = [vp, ctypes.POINTER(WdKernelStat), i32, ctypes.POINTER(i32),
                                         ctypes.c_int]
@@ -188,6 +193,9 @@ class Solver:
         o.solve_simt = 1 if solve_simt else 0
         o.fp64_tc_schur = 1 if fp64_tc_schur else 0
         o.step_launches = 1 if step_launches else 0
+        # the options that shape the analysis and the factor's launch plan
+        self.options = dict(nd_leaf=nd_leaf, relax_k=relax_k, relax_pct=relax_pct,
+                            diag64_min_k=o.diag64_min_k, step_launches=o.step_launches)
         self._h = ctypes.c_void_p()
         self._check(self._lib.wd_create(ctypes.byref(self._h), ctypes.byref(o)))
         self.n = None
@@ -348,6 +356,40 @@ class Solver:
         self._check(self._lib.wd_factor_lu(self._h, pl, pu, dev, _stream(stream, dev)))
         self.precision = "lu"
         return self
+
+    def level_schedule(self) -> list:
+        """Per elimination-tree level (deepest first): 0 = one launch of
+        dependency-ordered tasks for the level's pivot columns, 1 = a
+        (panel, update) launch pair per 64-column pivot block."""
+        n = self.info()["nlevels"]
+        a = np.zeros(max(n, 1), np.int8)
+        self._check(self._lib.wd_get_level_schedule(self._h, a.ctypes.data, n))
+        return [int(x) for x in a[:n]]
+
+    def set_level_schedule(self, flags):
+        a = np.ascontiguousarray(flags, np.int8)
+        self._check(self._lib.wd_set_level_schedule(self._h, a.ctypes.data, int(a.size)))
+        return self
+
+    def factor_ldlt(self, values, stream=None):
+        """P A P^T = L D L^T for a symmetric, possibly indefinite matrix
+        (FP64, no pivoting; the LU factorization with U = D L^T).  Solve
+        with solve_lu, log |det| with logdet_lu, the inertia with inertia()."""
+        v = values if _is_torch(values) else np.ascontiguousarray(values, np.float64)
+        if v.shape[0] != self.nnz:
+            raise ValueError("one value per stored lower entry of the analyzed pattern")
+        p, dev = _ptr(v)
+        self._check(self._lib.wd_factor_ldlt(self._h, p, dev, _stream(stream, dev)))
+        self.precision = "lu"
+        return self
+
+    def inertia(self):
+        """(number of positive, number of negative eigenvalues of A) from the
+        pivots of the last factor_ldlt."""
+        pos = ctypes.c_int64()
+        neg = ctypes.c_int64()
+        self._check(self._lib.wd_inertia(self._h, ctypes.byref(pos), ctypes.byref(neg)))
+        return pos.value, neg.value
 
     def solve_lu(self, B, stream=None):
         """A^-1 B with the LU factor.  A CUDA tensor (n x nrhs, column-major)

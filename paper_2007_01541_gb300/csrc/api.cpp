@@ -127,6 +127,7 @@ struct wd_ctx {
     // LU without pivoting (wd_factor_lu, FP64): position codes of the full
     // CSR, both values per position, U11^-1 blocks, plans
     bool lu_factored = false;
+    bool ldlt = false;          // the LU factor is that of a symmetric matrix (wd_factor_ldlt)
     bool front_dirty = false;   // the fronts' upper parts hold an LU factor
     std::vector<int8_t> h_csr_code;
     int8_t *d_lu_code = nullptr;
@@ -156,6 +157,7 @@ struct wd_ctx {
     // words of every supernode (offsets chain_flagoff), then one task counter
     // per level and the launch-wide abort word; zeroed before each factor
     bool chain = false;
+    std::vector<int8_t> level_step;   // per level: 1 keeps the launch pairs (wd_set_level_schedule)
     unsigned *d_chain_flags = nullptr;
     int64_t *d_chain_flagoff = nullptr;
     unsigned char *d_chain_lpack = nullptr;   // L11^-1 blocks as tensor-core operands (32 KB each)
@@ -388,7 +390,10 @@ static int front_order(const wd::Symbolic &S, int s) { return kpad(S.k(s)) + S.m
 // chain (FP32 fronts on the tensor cores): the pivot columns of a level in
 // one launch of dependency-ordered tasks (tc_chain.cu) instead of the diagonal
 // block launch and a (panel, update) launch pair per pivot block.
-static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc, bool oz = false, bool chain = false) {
+// level_step (nullable, one flag per level): levels whose flag is set keep
+// the (panel, update) launch pairs although chain is on.
+static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc, bool oz = false, bool chain = false,
+                              const int8_t *level_step = nullptr) {
     const int SCHUR_BM = tc ? wd::TC_BM : wd::SCHUR_BM;
     const int SCHUR_BN = tc ? wd::TC_BN : wd::SCHUR_BN;
     p.items.clear();
@@ -416,7 +421,7 @@ static void build_factor_plan(const wd::Symbolic &S, Plan &p, bool tc, bool oz =
         int kmax = 0;
         double fl = 0;
         for (int i = b; i < e; ++i) kmax = std::max(kmax, S.k(S.level_nodes[i]));
-        if (tc && chain) {
+        if (tc && chain && !(level_step && level_step[l])) {
             // tasks (s, c, ti): column block c, row tile ti (128 rows from row
             // 64 c); in order of c, then ti, then front, so that every task
             // depends only on earlier ones
@@ -1018,6 +1023,7 @@ static wd_status finish_analysis(wd_handle h, std::chrono::steady_clock::time_po
     }
     build_factor_plan(S, h->fplan, false, h->opt.fp64_tc_schur != 0);
     h->chain = !h->opt.step_launches && h->opt.diag64_min_k <= 0;
+    h->level_step.assign(S.nlevels, 0);
     build_factor_plan(S, h->fplan_tc, true, false, h->chain);
     std::vector<int64_t> chain_off(ns);
     {
@@ -2533,6 +2539,7 @@ extern "C" wd_status wd_factor_lu(wd_handle h, const double *lower, const double
     wait_export(h);
     h->factored = false;
     h->lu_factored = false;
+    h->ldlt = false;
     const int64_t nnzl = h->S.pcp[h->S.n];
     if (!h->d_front) {
         CK(h->mem.alloc(&h->d_front, h->front_elems * sizeof(double)), "front pool alloc");
@@ -2595,6 +2602,71 @@ extern "C" wd_status wd_factor_lu(wd_handle h, const double *lower, const double
     return WD_OK;
 }
 
+extern "C" wd_status wd_set_level_schedule(wd_handle h, const int8_t *step, int32_t nlevels) {
+    if (!h || !step) return WD_ERR_INVALID_ARG;
+    if (!h->analyzed) return fail(h, WD_ERR_STATE, "wd_set_level_schedule before wd_analyze");
+    if (nlevels != h->S.nlevels) return fail(h, WD_ERR_INVALID_ARG, "one flag per level of the analysis");
+    for (int32_t l = 0; l < nlevels; ++l)
+        if (step[l] != 0 && step[l] != 1) return fail(h, WD_ERR_INVALID_ARG, "level flags are 0 or 1");
+    h->level_step.assign(step, step + nlevels);
+    build_factor_plan(h->S, h->fplan_tc, true, false, h->chain, h->level_step.data());
+    if (!h->opt.symbolic_only) {
+        CK(cudaSetDevice(h->device), "set device");
+        wait_export(h);
+        const wd_status us = upload_plan(h, h->mem, h->fplan_tc);
+        if (us != WD_OK) return us;
+        h->g_factor.reset();
+        h->factored = false;
+    }
+    return WD_OK;
+}
+
+extern "C" wd_status wd_get_level_schedule(wd_handle h, int8_t *step, int32_t nlevels) {
+    if (!h || !step) return WD_ERR_INVALID_ARG;
+    if (!h->analyzed) return fail(h, WD_ERR_STATE, "wd_get_level_schedule before wd_analyze");
+    if (nlevels != h->S.nlevels) return fail(h, WD_ERR_INVALID_ARG, "one flag per level of the analysis");
+    for (int32_t l = 0; l < nlevels; ++l) step[l] = h->chain ? h->level_step[l] : 1;
+    return WD_OK;
+}
+
+extern "C" wd_status wd_factor_ldlt(wd_handle h, const double *values, int on_device, void *stream) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    // the LU decomposition without pivoting of the symmetric matrix: L, and
+    // U = D L^T (the same values for both triangles)
+    const wd_status s = wd_factor_lu(h, values, values, on_device, stream);
+    h->ldlt = s == WD_OK;
+    return s;
+}
+
+// number of negative pivots of the LU factor (grid-stride partial counts)
+static wd_status lu_pivot_stats(wd_handle h, double *logabs, int64_t *nneg) {
+    CK(cudaSetDevice(h->device), "set device");
+    constexpr int NBLK = 64;
+    wd::launch_lu_logdet(h->dsym, static_cast<const double *>(h->d_front), h->d_lu_part, NBLK, 0);
+    double part[2 * NBLK];
+    CK(cudaMemcpy(part, h->d_lu_part, sizeof(part), cudaMemcpyDeviceToHost), "logdet D2H");
+    double sum = 0.0, neg = 0.0;
+    for (int b = 0; b < NBLK; ++b) {
+        sum += part[b];
+        neg += part[NBLK + b];
+    }
+    *logabs = sum;
+    *nneg = (int64_t)neg;
+    return WD_OK;
+}
+
+extern "C" wd_status wd_inertia(wd_handle h, int64_t *npos, int64_t *nneg) {
+    if (!h) return WD_ERR_INVALID_ARG;
+    if (!h->lu_factored || !h->ldlt) return fail(h, WD_ERR_STATE, "wd_inertia before a successful wd_factor_ldlt");
+    double la = 0.0;
+    int64_t neg = 0;
+    const wd_status s = lu_pivot_stats(h, &la, &neg);
+    if (s != WD_OK) return s;
+    if (npos) *npos = h->S.n - neg;
+    if (nneg) *nneg = neg;
+    return WD_OK;
+}
+
 extern "C" wd_status wd_solve_lu(wd_handle h, double *B, int64_t nrhs, int64_t ldb, int B_on_device,
                                  void *stream) {
     if (!h) return WD_ERR_INVALID_ARG;
@@ -2649,18 +2721,10 @@ extern "C" wd_status wd_solve_lu(wd_handle h, double *B, int64_t nrhs, int64_t l
 extern "C" wd_status wd_logdet_lu(wd_handle h, double *logabs, int32_t *sign) {
     if (!h || !logabs || !sign) return WD_ERR_INVALID_ARG;
     if (!h->lu_factored) return fail(h, WD_ERR_STATE, "wd_logdet_lu before a successful wd_factor_lu");
-    CK(cudaSetDevice(h->device), "set device");
-    constexpr int NBLK = 64;
-    wd::launch_lu_logdet(h->dsym, static_cast<const double *>(h->d_front), h->d_lu_part, NBLK, 0);
-    double part[2 * NBLK];
-    CK(cudaMemcpy(part, h->d_lu_part, sizeof(part), cudaMemcpyDeviceToHost), "logdet D2H");
-    double sum = 0.0, neg = 0.0;
-    for (int b = 0; b < NBLK; ++b) {
-        sum += part[b];
-        neg += part[NBLK + b];
-    }
-    *logabs = sum;
-    *sign = ((int64_t)neg % 2 == 0) ? 1 : -1;
+    int64_t neg = 0;
+    const wd_status s = lu_pivot_stats(h, logabs, &neg);
+    if (s != WD_OK) return s;
+    *sign = (neg % 2 == 0) ? 1 : -1;
     return WD_OK;
 }
 
