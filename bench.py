@@ -52,6 +52,10 @@ DF32_OPS_PER_TERM = 11.75     # the same with x exactly FP32 (one FMA less)
 # tf32 / bf16 dense tensor rates (nominal 1.1 and 2.25 PFLOP/s): a tf32
 # contraction's peak is the measured bf16 peak times this ratio
 TF32_PER_BF16 = 1.1 / 2.25
+# flop budget of each step of the reference arm (the oracle's factor of the
+# first columns plus both substitutions over them), so that the whole
+# --steps K --warmup W run stays within minutes
+REF_STEP_FLOPS = 3e9
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
 # kernel from one ncu capture, keyed by (workload, kernel, nd_leaf, relax_k,
@@ -96,7 +100,7 @@ def measured_traffic(key, kernel):
     return t["bytes"]
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=5)
@@ -129,9 +133,10 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-replay", action="store_true",
                    help="skip the profiled replay (per-kernel events)")
-    p.add_argument("--cpu-flops", type=float, default=1.2e10,
-                   help="flop budget of the oracle's bounded sample")
-    return p.parse_args()
+    p.add_argument("--cpu-flops", type=float, default=0.0,
+                   help="flop budget of the oracle's cpu_baseline sample (0: the whole factorization and "
+                        "both substitutions, once)")
+    return p.parse_args(argv)
 
 
 # ---------------------------------------------------------------------------
@@ -421,13 +426,13 @@ def make_workload(kind: str, nrhs: int | None, device: str):
 
 
 def oracle_sample(w, budget_flops: float, repeats: int = 3, analyze: bool = True):
-    """The CPU oracle on one host core, on a bounded share of the workload's
-    factorization: the full analysis (nested dissection and symbolic, timed
-    for the record), the left-looking FP64 factor of the first columns of
-    P A P^T up to `budget_flops` of sum c_j^2 (the bottom of the elimination
-    tree), and both substitutions over those columns for all right-hand sides
-    (4 nnz(L prefix) nrhs flops, the solve's count restricted to the prefix).
-    Each part is timed `repeats` times and the median kept."""
+    """The CPU oracle on one host core: the full analysis (nested dissection
+    and symbolic, timed for the record), then either (budget_flops <= 0) the
+    whole left-looking FP64 factorization of P A P^T and both substitutions
+    for all right-hand sides, once, or a bounded share of them: the factor of
+    the first columns up to `budget_flops` of sum c_j^2 (the bottom of the
+    elimination tree) and both substitutions over those columns (4 nnz(L
+    prefix) nrhs flops), each part timed `repeats` times, the median kept."""
     import numpy as np
 
     import oracle
@@ -438,7 +443,11 @@ def oracle_sample(w, budget_flops: float, repeats: int = 3, analyze: bool = True
         o = oracle.Oracle(w["colptr"], w["rowidx"], w["basis"])
         ta.append(time.perf_counter() - t)
     c2 = np.cumsum(o.colcount.astype(np.float64) ** 2)
-    ncols = max(1, min(int(np.searchsorted(c2, budget_flops, side="right")), o.n))
+    whole = budget_flops <= 0
+    if whole:
+        ncols, repeats = o.n, 1
+    else:
+        ncols = max(1, min(int(np.searchsorted(c2, budget_flops, side="right")), o.n))
     ff = float(c2[ncols - 1])
     nr = int(w["nrhs"])
     fs = 4.0 * float(o.Lp[ncols]) * nr
@@ -457,10 +466,13 @@ def oracle_sample(w, budget_flops: float, repeats: int = 3, analyze: bool = True
         ts.append(time.perf_counter() - t)
     mf, ms_, ma = statistics.median(tf), statistics.median(ts), statistics.median(ta)
     return {"value": (ff + fs) / (mf + ms_) / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": (f"one host core, median of {repeats}: left-looking FP64 factor of the first {ncols} of "
-                       f"{o.n} columns of P A P^T ({ff:.3e} flop of sum c_j^2, bottom of the elimination tree) "
-                       f"in {mf:.2f} s, then both substitutions over those columns with {nr} right-hand sides "
-                       f"({fs:.3e} flop) in {ms_:.2f} s"),
+            "sample": ((f"one host core, once: the whole left-looking FP64 factorization of P A P^T ({ff:.3e} "
+                        f"flop of sum c_j^2) in {mf:.2f} s, then both substitutions with {nr} right-hand sides "
+                        f"({fs:.3e} flop) in {ms_:.2f} s") if whole else
+                       (f"one host core, median of {repeats}: left-looking FP64 factor of the first {ncols} of "
+                        f"{o.n} columns of P A P^T ({ff:.3e} flop of sum c_j^2, bottom of the elimination tree) "
+                        f"in {mf:.2f} s, then both substitutions over those columns with {nr} right-hand sides "
+                        f"({fs:.3e} flop) in {ms_:.2f} s")),
             "analyze_s": ma if analyze else None, "factor_s": mf, "factor_flops": ff, "solve_s": ms_,
             "solve_flops": fs, "sample_columns": ncols, "repeats": repeats,
             "nproc": os.cpu_count(), "cpu_model": cpu_model(),
@@ -496,7 +508,7 @@ def run_reference(args):
         w = make_workload("batch", args.nrhs, dev)
     else:
         w = make_workload(args.workload, args.nrhs, dev)
-    budget = args.cpu_flops / 4
+    budget = args.cpu_flops / 4 if args.cpu_flops > 0 else REF_STEP_FLOPS
     samples = []
     for i in range(args.warmup + args.steps):
         r = oracle_sample(w, budget, repeats=1, analyze=(i == 0))

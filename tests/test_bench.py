@@ -85,3 +85,13 @@ def test_batch_cpu_baseline_runs_the_oracle_in_parallel_processes():
     assert r is not None and r["cores"] == 2 and r["kind"] == "oracle"
     assert r["value"] > 0 and r["per_process"] > 0
     assert "(1, 10)" in r["sample"] and "(1, 9)" not in r["sample"]   # the two most expensive
+
+
+def test_cpu_baseline_default_is_the_whole_factorization_and_solve():
+    """With no flop budget the cpu_baseline times the oracle's whole
+    factorization and both whole substitutions, once."""
+    w = bench.make_workload("1d", None, "cpu")
+    r = bench.oracle_sample(w, bench.parse([]).cpu_flops)
+    assert r["sample_columns"] == w["basis"].N and r["repeats"] == 1
+    assert r["factor_flops"] == r["flops_factor"] and "whole" in r["sample"]
+    assert abs(r["solve_flops"] - 4.0 * r["nnz_L"] * w["nrhs"]) <= 1e-9 * r["solve_flops"]
