@@ -1315,6 +1315,7 @@ static void enqueue_factor_plan(wd_handle h, cudaStream_t st, bool prof) {
     ta.diag64_min_k = h->opt.diag64_min_k;
     ta.wait_limit = (uint32_t)std::max(0, h->opt.wait_limit);
     ta.gate = h->opt.test_closed_gate ? h->d_gate : nullptr;
+    ta.ctas = h->sms;       // the fronts' trailing blocks: one persistent CTA per SM
     wd::OzArgs oa{};
     oa.sl = h->d_oz_sl;
     oa.ex = h->d_oz_ex;

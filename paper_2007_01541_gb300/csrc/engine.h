@@ -113,6 +113,7 @@ struct TcArgs {
     int diag64_min_k;
     uint32_t wait_limit;
     const unsigned *gate;
+    int ctas;               // mode 1: > 0 runs the persistent kernel on this many CTAs (one per SM)
 };
 void launch_tc_schur(const DevSym &d, float *front, const unsigned char *pk, const int4 *items,
                      int count, int kb, int mode, const TcArgs &a, cudaStream_t st);

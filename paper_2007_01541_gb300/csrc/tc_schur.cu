@@ -225,6 +225,193 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
+
+// The fronts' trailing blocks (mode 1, U = F22 - L21 L21^T with K = k) as a
+// persistent launch: one CTA per SM takes the tiles blockIdx.x, blockIdx.x +
+// gridDim.x, ...  The stage ring runs on across tiles, and two TMEM
+// accumulators alternate, so a tile's epilogue (read-modify-write of its
+// part of C) overlaps the next tile's copies and products; the per-CTA
+// set-up (barriers, TMEM allocation) is paid once per SM instead of once per
+// tile, which is what the many narrow fronts of the deep levels (K <= 64,
+// two chunks per tile) spent their time on.  Arithmetic and bounded waits as
+// in tc_schur_kernel.
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_syrk_persistent_kernel(DevSym d, float *__restrict__ front, const unsigned char *__restrict__ pk,
+                              const int4 *__restrict__ items, int count, TcArgs a) {
+    const uint32_t limit = a.wait_limit ? a.wait_limit : WAIT_LIMIT;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;      // accumulator b holds a finished tile
+    uint64_t *tempty = tfull + 2;          // accumulator b has been read
+    uint64_t *done = tempty + 2;           // every issued MMA has completed
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int i = 0; i < STAGES; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&tfull[i], 1);
+            tc::mbar_init(&tempty[i], 8);   // one arrival per epilogue warp
+        }
+        tc::mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 1) tc::tmem_alloc(tslot, 2 * TBN);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    int fills[STAGES] = {};   // producer lane: fills issued per stage
+    if (warp == 0) {
+        if (lane == 0) {
+            int kt = 0;   // chunk counter across the CTA's tiles
+            for (int t = blockIdx.x; t < count && !*(volatile int *)abort_flag; t += gridDim.x) {
+                const int4 it = items[t];
+                const int s = it.x, k = d.sk[s], m = d.sm[s], kp = d.skp[s];
+                const int mp = kp + m - k;
+                const int r0 = kp + it.y * TBM, c0 = kp + it.z * TBN;
+                const int nk = (k + TBK - 1) / TBK, prow = pack_rows(mp);
+                const unsigned char *P = pk + d.pkoff[s];
+                bool stop = false;
+                for (int kc = 0; kc < nk; ++kc, ++kt) {
+                    const int st = kt % STAGES;
+                    if (kt >= STAGES && !tc::mbar_wait(&empty[st], ((kt / STAGES) - 1) & 1, limit)) {
+                        atomicExch(abort_flag, 1);
+                        stop = true;
+                        break;
+                    }
+                    if (*(volatile int *)abort_flag) {
+                        stop = true;
+                        break;
+                    }
+                    ++fills[st];
+                    unsigned char *stg = sm + st * STAGE_BYTES;
+                    mbar_expect_tx(&full[st], STAGE_BYTES);
+                    bulk_copy(stg, P + pack_offset(kc, 0, r0, prow), TILE_BYTES, &full[st]);
+                    bulk_copy(stg + TILE_BYTES, P + pack_offset(kc, 1, r0, prow), TILE_BYTES, &full[st]);
+                    bulk_copy(stg + 2 * TILE_BYTES, P + pack_offset(kc, 0, c0, prow), TILE_BYTES, &full[st]);
+                    bulk_copy(stg + 3 * TILE_BYTES, P + pack_offset(kc, 1, c0, prow), TILE_BYTES, &full[st]);
+                }
+                if (stop) break;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_tf32(TBM, TBN);
+            int kt = 0, i = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < count && ok; t += gridDim.x, ++i) {
+                const int k = d.sk[items[t].x];
+                const int nk = (k + TBK - 1) / TBK;
+                const int b = i & 1;
+                if (i >= 2 && !tc::mbar_wait(&tempty[b], ((i >> 1) - 1) & 1, limit)) {
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(TBN * b);
+                for (int kc = 0; kc < nk; ++kc, ++kt) {
+                    const int st = kt % STAGES;
+                    if (!tc::mbar_wait(&full[st], (kt / STAGES) & 1, limit) || *(volatile int *)abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t a0 = tc::smem_u32(sm + st * STAGE_BYTES);
+#pragma unroll
+                    for (int j = 0; j < TBK / 8; ++j) {
+                        const uint64_t ah = tc::desc_kmajor_sw128(a0 + 32 * j);
+                        const uint64_t al = tc::desc_kmajor_sw128(a0 + TILE_BYTES + 32 * j);
+                        const uint64_t bh = tc::desc_kmajor_sw128(a0 + 2 * TILE_BYTES + 32 * j);
+                        const uint64_t bl = tc::desc_kmajor_sw128(a0 + 3 * TILE_BYTES + 32 * j);
+                        tc::mma_tf32(acc, ah, bh, idesc, (kc > 0 || j > 0) ? 1u : 0u);
+                        tc::mma_tf32(acc, ah, bl, idesc, 1u);
+                        tc::mma_tf32(acc, al, bh, idesc, 1u);
+                    }
+                    tc::mma_commit(&empty[st]);
+                }
+                if (ok) tc::mma_commit(&tfull[b]);
+            }
+            if (!ok) atomicExch(abort_flag, 1);
+            // arrives once every MMA issued above has completed
+            tc::mma_commit(done);
+        }
+    } else {
+        // epilogue: warps 2..9; TMEM lane group = warp % 4, column half = (warp - 2) / 4
+        const int lg = warp & 3, half = (warp - 2) >> 2;
+        int i = 0;
+        for (int t = blockIdx.x; t < count; t += gridDim.x, ++i) {
+            const int4 it = items[t];
+            const int s = it.x, k = d.sk[s], m = d.sm[s], kp = d.skp[s], ld = d.sld[s];
+            const int mp = kp + m - k;
+            const int r0 = kp + it.y * TBM, c0 = kp + it.z * TBN;
+            const int r = r0 + 32 * lg + lane;
+            const int cb0 = c0 + 64 * half;
+            float *rowp = front + d.foff[s] + (int64_t)cb0 * ld + r;
+            const int cend = min(64, mp - cb0);
+            const int nc = (r < mp) ? max(0, min(cend, r - cb0 + 1)) : 0;
+            float cur[64];
+#pragma unroll
+            for (int q = 0; q < 64; ++q) cur[q] = (q < nc) ? rowp[q * ld] : 0.0f;
+            const int b = i & 1;
+            bool ok = tc::mbar_wait(&tfull[b], (i >> 1) & 1, limit);
+            tc::tc_fence_after();
+            if (ok && a.gate != nullptr) {
+                // test of the timeout path: a gate that nothing opens
+                int open = 0;
+                if (lane == 0)
+                    for (uint32_t g = 0; g < limit && !open; ++g) {
+                        open = *(volatile const unsigned *)a.gate != 0u;
+                        if (!open) __nanosleep(256);
+                    }
+                ok = __shfl_sync(0xffffffffu, open, 0) != 0;
+            }
+            ok = __all_sync(0xffffffffu, ok && *(volatile int *)abort_flag == 0);
+            if (!ok) {
+                if (lane == 0) atomicExch(abort_flag, 1);
+                break;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(TBN * b) + 64 * half + 16 * q, v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) cur[16 * q + j] -= v[j];
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&tempty[b]);
+#pragma unroll
+            for (int q = 0; q < 64; ++q)
+                if (q < nc) rowp[q * ld] = cur[q];
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    const bool aborted = *(volatile int *)abort_flag != 0;
+    if (tid == 0) {
+        // every issued fill has landed and every issued MMA has completed
+        // before the shared memory and TMEM are given up (after a timeout;
+        // otherwise these waits return at once)
+        if (aborted)
+            for (int st = 0; st < STAGES; ++st)
+                if (fills[st] > 0) tc::mbar_wait(&full[st], (fills[st] - 1) & 1, DRAIN_LIMIT);
+        tc::mbar_wait(done, 0, DRAIN_LIMIT);
+        if (aborted) atomicMax(a.tstatus, 1ull);
+    }
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 1) tc::tmem_dealloc(tmem, 2 * TBN);
+}
 }  // namespace
 
 size_t tc_schur_smem() { return (size_t)STAGES * STAGE_BYTES + 1024 + 128; }
@@ -236,6 +423,8 @@ void init_tc_attributes() {
                          (int)tc_schur_smem());
     cudaFuncSetAttribute(tc_schur_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tc_schur_smem());
+    cudaFuncSetAttribute(tc_syrk_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tc_schur_smem());
     done = true;
 }
 
@@ -243,6 +432,11 @@ void launch_tc_schur(const DevSym &d, float *front, const unsigned char *pk, con
                      int count, int kb, int mode, const TcArgs &a, cudaStream_t st) {
     if (count <= 0) return;
     init_tc_attributes();
+    if (mode == 1 && a.ctas > 0) {
+        tc_syrk_persistent_kernel<<<min(count, a.ctas), TC_THREADS, tc_schur_smem(), st>>>(d, front, pk, items, count,
+                                                                                          a);
+        return;
+    }
     if (a.diag64_min_k > 0 && mode == 0)
         tc_schur_kernel<true><<<count, TC_THREADS, tc_schur_smem(), st>>>(d, front, pk, items, kb, mode, a);
     else
