@@ -1573,6 +1573,7 @@ static void enqueue_solve_plan(wd_handle h, T *Y, int nrhs, cudaStream_t st, boo
     ta.wait_limit = (uint32_t)std::max(0, h->opt.wait_limit);
     ta.ksw = h->d_ksw;
     ta.kcnt = h->d_kcnt;
+    ta.sms = h->sms;
     const bool tc = lg == 1 && sizeof(T) == 4;
     size_t li = 0;
     for (const Launch &L : h->splan.launches) {

@@ -425,15 +425,23 @@ __global__ void __launch_bounds__(THREADS, C::MINB) bupdate_kernel(DevSym d, con
     }
     T *O = sm;
     tile_to_smem<T, C>(acc, O);
+    if (!PRE) {
+        // every old target value is read before the first store: a store may
+        // alias a later element's load through the runtime stride, which
+        // would make each read-modify-write a memory round trip of its own
+#pragma unroll
+        for (int e = 0; e < PE; ++e) {
+            const int idx = threadIdx.x + e * THREADS;
+            const int r = idx % C::ROWS, c = idx / C::ROWS;
+            tpre[e] = (r < nrow && c < nc) ? dst[r + (int64_t)(c0 + c) * ldd] : T(0);
+        }
+    }
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < PE; ++e) {
         const int idx = threadIdx.x + e * THREADS;
         const int r = idx % C::ROWS, c = idx / C::ROWS;
-        if (r < nrow && c < nc) {
-            T *q = dst + r + (int64_t)(c0 + c) * ldd;
-            *q = (PRE ? tpre[e] : *q) - O[c * C::LDO + r];
-        }
+        if (r < nrow && c < nc) dst[r + (int64_t)(c0 + c) * ldd] = tpre[e] - O[c * C::LDO + r];
     }
 }
 

@@ -18,10 +18,14 @@
 // read from its FP32 array (the super-block inverses, the fronts' columns, the
 // right-hand-side columns), split by the CTA's threads and stored swizzled.
 // The asynchronous copies of a 32-wide chunk of the inner dimension are issued
-// two chunks ahead into a ring of three shared-memory stages, straight to the
-// values' swizzled places; each thread then splits the values it copied in
-// place (hi) and into the lo plane, and one thread issues the chunk's MMAs
-// while the next chunks are in flight.
+// ahead into a ring of shared-memory stages, straight to the values' swizzled
+// places; each thread then splits the values it copied in place (hi) and into
+// the lo plane, and one thread issues the chunk's MMAs while the next chunks
+// are in flight.  The ring has three stages, two chunks ahead (144 KB), except
+// in a bupdate launch of more CTAs than SMs (the many short products of the
+// lower levels, a few chunks each): there it has two stages, one chunk ahead
+// (96 KB), so that two CTAs share an SM and one's set-up, waits and epilogue
+// overlap the other's copies.  The stage count changes no arithmetic.
 //
 // A launch with few output tiles (the top of the tree: a few super-blocks of
 // one or two fronts) splits the inner dimension of xapply and bupdate over up
@@ -47,7 +51,7 @@ constexpr int NTH = 256;
 constexpr int A_BYTES = TM * TK * 4;           // one plane of A: 16 KB
 constexpr int B_BYTES = TN * TK * 4;           // one plane of B: 8 KB
 constexpr int STG_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int NSTG = 3;                         // stages in flight (chunks issued ahead: NSTG - 1)
+constexpr int NSTG = 3;                         // most stages of the ring (chunks issued ahead: stages - 1)
 constexpr uint32_t WAIT_DEFAULT = 1u << 26;
 constexpr uint32_t DRAIN_LIMIT = 1u << 26;
 
@@ -236,11 +240,12 @@ __device__ __forceinline__ void split_chunk(unsigned char *Ah, unsigned char *Al
 }
 
 template <int OP>
-__global__ void __launch_bounds__(NTH, 1) tc_solve_kernel(DevSym d, TcSolveArgs a, const int4 *__restrict__ items) {
+__global__ void __launch_bounds__(NTH, 2) tc_solve_kernel(DevSym d, TcSolveArgs a, const int4 *__restrict__ items) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint64_t *full = reinterpret_cast<uint64_t *>(sm + NSTG * STG_BYTES);
+    const int nst = a.stages;   // 2 or 3 (the launcher's choice; the dynamic shared memory holds nst stages)
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + nst * STG_BYTES);
     uint64_t *empty = full + NSTG;
     uint64_t *done = empty + NSTG;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
@@ -268,12 +273,12 @@ __global__ void __launch_bounds__(NTH, 1) tc_solve_kernel(DevSym d, TcSolveArgs 
     const uint32_t tmem = *tslot;
 
     const uint32_t idesc = tc::idesc_tf32(TM, TN);
-    // chunk cc goes to stage cc % NSTG; before it is issued, the MMAs of the
-    // chunk that used the stage last (cc - NSTG) must have completed
+    // chunk cc goes to stage cc % nst; before it is issued, the MMAs of the
+    // chunk that used the stage last (cc - nst) must have completed
     int issued = 0;
     auto issue = [&](int cc) {
-        const int st = cc % NSTG;
-        if (cc >= NSTG && !tc::mbar_wait(&empty[st], ((cc / NSTG) - 1) & 1, limit)) {
+        const int st = cc % nst;
+        if (cc >= nst && !tc::mbar_wait(&empty[st], ((cc / nst) - 1) & 1, limit)) {
             atomicExch(abort_flag, 1);
             return;
         }
@@ -286,21 +291,24 @@ __global__ void __launch_bounds__(NTH, 1) tc_solve_kernel(DevSym d, TcSolveArgs 
         issue_chunk<OP>(d, a, g, cc, stg, stg + 2 * A_BYTES);
         issued = cc + 1;
     };
-    for (int cc = 0; cc < NSTG - 1; ++cc) {
+    for (int cc = 0; cc < nst - 1; ++cc) {
         if (cc < g.nchunk) issue(cc);
         cp_async_commit();
     }
     for (int c = 0; c < g.nchunk; ++c) {
-        const int st = c % NSTG;
+        const int st = c % nst;
         unsigned char *stg = sm + st * STG_BYTES;
-        cp_async_wait<NSTG - 2>();     // this thread's copies of chunk c have landed
+        // this thread's copies of chunk c have landed (at most nst - 2 later
+        // groups still pending)
+        if (nst == 3) cp_async_wait<1>();
+        else cp_async_wait<0>();
         split_chunk<OP>(stg, stg + A_BYTES, stg + 2 * A_BYTES, stg + 2 * A_BYTES + B_BYTES);
         tc::fence_async_smem();
         __syncthreads();
         if (*(volatile int *)abort_flag) break;
         if (tid == 0) {
             bool ok = true;
-            if (OP == OP_BUPDATE) ok = tc::mbar_wait(&full[st], (c / NSTG) & 1, limit);
+            if (OP == OP_BUPDATE) ok = tc::mbar_wait(&full[st], (c / nst) & 1, limit);
             if (ok) {
                 tc::tc_fence_after();
                 const uint32_t a0 = tc::smem_u32(stg);
@@ -319,7 +327,7 @@ __global__ void __launch_bounds__(NTH, 1) tc_solve_kernel(DevSym d, TcSolveArgs 
             }
             tc::mma_commit(&empty[st]);
         }
-        if (c + NSTG - 1 < g.nchunk) issue(c + NSTG - 1);
+        if (c + nst - 1 < g.nchunk) issue(c + nst - 1);
         cp_async_commit();
     }
     cp_async_wait<0>();
@@ -352,8 +360,8 @@ __global__ void __launch_bounds__(NTH, 1) tc_solve_kernel(DevSym d, TcSolveArgs 
         // MMAs have completed before the shared memory and TMEM are given up
         // (every thread's own copies were waited for above)
         if (OP == OP_BUPDATE)
-            for (int cc = (issued > NSTG ? issued - NSTG : 0); cc < issued; ++cc)
-                tc::mbar_wait(&full[cc % NSTG], (cc / NSTG) & 1, DRAIN_LIMIT);
+            for (int cc = (issued > nst ? issued - nst : 0); cc < issued; ++cc)
+                tc::mbar_wait(&full[cc % nst], (cc / nst) & 1, DRAIN_LIMIT);
         tc::mbar_wait(done, 0, DRAIN_LIMIT);
         atomicMax(a.tstatus, 1ull);
     }
@@ -409,9 +417,20 @@ __global__ void __launch_bounds__(NTH, 1) tc_solve_kernel(DevSym d, TcSolveArgs 
                     o = a.W + d.woff[g.s] * a.nrhs + g.i0 + r + (int64_t)g.c0 * (g.m - g.k);
                     ldd = g.m - g.k;
                 }
+                // 16 old values are read before the first of their stores: a
+                // store may alias a later column's load through the runtime
+                // stride, which would make each of the 32 read-modify-writes
+                // a memory round trip of its own
 #pragma unroll
-                for (int i = 0; i < 32; ++i)
-                    if (jb + i < g.nc) o[(int64_t)(jb + i) * ldd] -= v[i];
+                for (int h = 0; h < 32; h += 16) {
+                    float old[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        old[i] = jb + h + i < g.nc ? o[(int64_t)(jb + h + i) * ldd] : 0.f;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (jb + h + i < g.nc) o[(int64_t)(jb + h + i) * ldd] = old[i] - v[h + i];
+                }
             }
         } else {
             float *o = a.out + ((int64_t)g.slot * TN + jb) * TM + r;
@@ -425,14 +444,25 @@ __global__ void __launch_bounds__(NTH, 1) tc_solve_kernel(DevSym d, TcSolveArgs 
     if (warp == 0) tc::tmem_dealloc(tmem, TN);
 }
 
-constexpr size_t tc_solve_smem() { return (size_t)NSTG * STG_BYTES + 1024 + 128; }
+constexpr size_t tc_solve_smem(int nst) { return (size_t)nst * STG_BYTES + 1024 + 128; }
 
 template <int OP>
 void set_attr() {
     static bool done = false;
     if (done) return;
-    cudaFuncSetAttribute(tc_solve_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_solve_smem());
+    cudaFuncSetAttribute(tc_solve_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tc_solve_smem(NSTG));
+    cudaFuncSetAttribute(tc_solve_kernel<OP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
     done = true;
+}
+
+// bupdate with more CTAs than SMs (its inner dimension is one super-block,
+// a few chunks at the lower levels): two stages, two CTAs per SM; else three
+TcSolveArgs with_stages(const TcSolveArgs &a, int count, bool two) {
+    TcSolveArgs b = a;
+    b.stages = (two && a.sms > 0 && count > a.sms) ? 2 : NSTG;
+    return b;
 }
 
 }  // namespace
@@ -446,17 +476,20 @@ void init_tc_solve_attributes() {
 void launch_tc_xapply(const DevSym &d, const TcSolveArgs &a, const int4 *items, int count, cudaStream_t st) {
     if (count <= 0) return;
     set_attr<OP_XAPPLY>();
-    tc_solve_kernel<OP_XAPPLY><<<count, NTH, tc_solve_smem(), st>>>(d, a, items);
+    const TcSolveArgs b = with_stages(a, count, false);
+    tc_solve_kernel<OP_XAPPLY><<<count, NTH, tc_solve_smem(b.stages), st>>>(d, b, items);
 }
 void launch_tc_bupdate(const DevSym &d, const TcSolveArgs &a, const int4 *items, int count, cudaStream_t st) {
     if (count <= 0) return;
     set_attr<OP_BUPDATE>();
-    tc_solve_kernel<OP_BUPDATE><<<count, NTH, tc_solve_smem(), st>>>(d, a, items);
+    const TcSolveArgs b = with_stages(a, count, true);
+    tc_solve_kernel<OP_BUPDATE><<<count, NTH, tc_solve_smem(b.stages), st>>>(d, b, items);
 }
 void launch_tc_breduce(const DevSym &d, const TcSolveArgs &a, const int4 *items, int count, cudaStream_t st) {
     if (count <= 0) return;
     set_attr<OP_BREDUCE>();
-    tc_solve_kernel<OP_BREDUCE><<<count, NTH, tc_solve_smem(), st>>>(d, a, items);
+    const TcSolveArgs b = with_stages(a, count, false);
+    tc_solve_kernel<OP_BREDUCE><<<count, NTH, tc_solve_smem(b.stages), st>>>(d, b, items);
 }
 
 }  // namespace wd
