@@ -326,8 +326,7 @@ struct TcSolveArgs {
     uint32_t wait_limit;          // 0: the default
     float *ksw;                   // split inner dimension: one partial tile per CTA
     int *kcnt;                    // split inner dimension: arrivals per output tile (zero between launches)
-    int sms;                      // the device's SMs: a launch of more CTAs than SMs runs two per SM
-    int stages;                   // set by the launcher: shared-memory stages of the CTA's ring (2 or 3)
+    int sms;                      // the device's SMs: a bupdate launch of more CTAs than SMs runs two per SM
 };
 constexpr int TC_SOLVE_TILE = 128 * 64;   // entries of one output tile of the tensor-core solve products
 void launch_tc_xapply(const DevSym &d, const TcSolveArgs &a, const int4 *items, int count, cudaStream_t st);

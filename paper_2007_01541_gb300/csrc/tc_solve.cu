@@ -239,12 +239,14 @@ __device__ __forceinline__ void split_chunk(unsigned char *Ah, unsigned char *Al
     split4_inplace(Bh, Bl, tc::sw128_offset(j, kq + 4));
 }
 
-template <int OP>
-__global__ void __launch_bounds__(NTH, 2) tc_solve_kernel(DevSym d, TcSolveArgs a, const int4 *__restrict__ items) {
+// NS: stages of the ring (3, or 2 for bupdate launches of more CTAs than SMs)
+template <int OP, int NS>
+__global__ void __launch_bounds__(NTH, NS == 2 ? 2 : 1) tc_solve_kernel(DevSym d, TcSolveArgs a,
+                                                                       const int4 *__restrict__ items) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const int nst = a.stages;   // 2 or 3 (the launcher's choice; the dynamic shared memory holds nst stages)
+    constexpr int nst = NS;     // the dynamic shared memory holds nst stages
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + nst * STG_BYTES);
     uint64_t *empty = full + NSTG;
     uint64_t *done = empty + NSTG;
@@ -298,10 +300,7 @@ __global__ void __launch_bounds__(NTH, 2) tc_solve_kernel(DevSym d, TcSolveArgs 
     for (int c = 0; c < g.nchunk; ++c) {
         const int st = c % nst;
         unsigned char *stg = sm + st * STG_BYTES;
-        // this thread's copies of chunk c have landed (at most nst - 2 later
-        // groups still pending)
-        if (nst == 3) cp_async_wait<1>();
-        else cp_async_wait<0>();
+        cp_async_wait<nst - 2>();     // this thread's copies of chunk c have landed
         split_chunk<OP>(stg, stg + A_BYTES, stg + 2 * A_BYTES, stg + 2 * A_BYTES + B_BYTES);
         tc::fence_async_smem();
         __syncthreads();
@@ -446,50 +445,47 @@ __global__ void __launch_bounds__(NTH, 2) tc_solve_kernel(DevSym d, TcSolveArgs 
 
 constexpr size_t tc_solve_smem(int nst) { return (size_t)nst * STG_BYTES + 1024 + 128; }
 
-template <int OP>
+template <int OP, int NS>
 void set_attr() {
     static bool done = false;
     if (done) return;
-    cudaFuncSetAttribute(tc_solve_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)tc_solve_smem(NSTG));
-    cudaFuncSetAttribute(tc_solve_kernel<OP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(tc_solve_kernel<OP, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tc_solve_smem(NS));
+    cudaFuncSetAttribute(tc_solve_kernel<OP, NS>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          (int)cudaSharedmemCarveoutMaxShared);
     done = true;
-}
-
-// bupdate with more CTAs than SMs (its inner dimension is one super-block,
-// a few chunks at the lower levels): two stages, two CTAs per SM; else three
-TcSolveArgs with_stages(const TcSolveArgs &a, int count, bool two) {
-    TcSolveArgs b = a;
-    b.stages = (two && a.sms > 0 && count > a.sms) ? 2 : NSTG;
-    return b;
 }
 
 }  // namespace
 
 void init_tc_solve_attributes() {
-    set_attr<OP_XAPPLY>();
-    set_attr<OP_BUPDATE>();
-    set_attr<OP_BREDUCE>();
+    set_attr<OP_XAPPLY, NSTG>();
+    set_attr<OP_BUPDATE, NSTG>();
+    set_attr<OP_BUPDATE, 2>();
+    set_attr<OP_BREDUCE, NSTG>();
 }
 
 void launch_tc_xapply(const DevSym &d, const TcSolveArgs &a, const int4 *items, int count, cudaStream_t st) {
     if (count <= 0) return;
-    set_attr<OP_XAPPLY>();
-    const TcSolveArgs b = with_stages(a, count, false);
-    tc_solve_kernel<OP_XAPPLY><<<count, NTH, tc_solve_smem(b.stages), st>>>(d, b, items);
+    set_attr<OP_XAPPLY, NSTG>();
+    tc_solve_kernel<OP_XAPPLY, NSTG><<<count, NTH, tc_solve_smem(NSTG), st>>>(d, a, items);
 }
 void launch_tc_bupdate(const DevSym &d, const TcSolveArgs &a, const int4 *items, int count, cudaStream_t st) {
     if (count <= 0) return;
-    set_attr<OP_BUPDATE>();
-    const TcSolveArgs b = with_stages(a, count, true);
-    tc_solve_kernel<OP_BUPDATE><<<count, NTH, tc_solve_smem(b.stages), st>>>(d, b, items);
+    // more CTAs than SMs (the lower levels: one super-block, a few chunks
+    // per CTA): two stages, two CTAs per SM
+    if (a.sms > 0 && count > a.sms) {
+        set_attr<OP_BUPDATE, 2>();
+        tc_solve_kernel<OP_BUPDATE, 2><<<count, NTH, tc_solve_smem(2), st>>>(d, a, items);
+    } else {
+        set_attr<OP_BUPDATE, NSTG>();
+        tc_solve_kernel<OP_BUPDATE, NSTG><<<count, NTH, tc_solve_smem(NSTG), st>>>(d, a, items);
+    }
 }
 void launch_tc_breduce(const DevSym &d, const TcSolveArgs &a, const int4 *items, int count, cudaStream_t st) {
     if (count <= 0) return;
-    set_attr<OP_BREDUCE>();
-    const TcSolveArgs b = with_stages(a, count, false);
-    tc_solve_kernel<OP_BREDUCE><<<count, NTH, tc_solve_smem(b.stages), st>>>(d, b, items);
+    set_attr<OP_BREDUCE, NSTG>();
+    tc_solve_kernel<OP_BREDUCE, NSTG><<<count, NTH, tc_solve_smem(NSTG), st>>>(d, a, items);
 }
 
 }  // namespace wd
